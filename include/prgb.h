@@ -1,0 +1,225 @@
+/*
+ * prgb.h -- C ABI of the componentwise PageRank library for GB300 (sm_103a).
+ *
+ * The library computes the non-normalised PageRank R of Def. 3.5 of
+ * Engstrom & Silvestrov, "Graph partitioning and a componentwise PageRank
+ * algorithm" (arXiv 1609.09068): the solution of (I - c A^T) R = u, where
+ * A_ij = 1/outdeg(i) for each edge i -> j, dangling rows of A are zero and
+ * 0 < c < 1.  Self-loops are ignored (Sec. 4.1 and Sec. 5.2).
+ *
+ * It follows the paper's three steps (Sec. 4): component finding
+ * (SCC/CAC partition with levels, Sec. 3 Theorem 3.1 and Sec. 4.1), an
+ * intermediate layout step (Sec. 4.2) and the level-by-level PageRank step
+ * (Sec. 4.3).  pr_partition_create performs the first two, pr_solve the
+ * third.  pr_global_power is the paper's baseline (the power series on the
+ * whole graph, Sec. 4.3.2) and pr_residual_l1 evaluates the residual of the
+ * defining system.
+ *
+ * Conventions shared by every entry point
+ *   - Graphs are CSR out-adjacency: rowptr[n+1] (int32, rowptr[0] = 0,
+ *     non-decreasing, rowptr[n] = nnz) and col[nnz] (int32 in [0, n)),
+ *     column indices strictly increasing inside each row (simple graph,
+ *     Sec. 3).  A self-loop i -> i may be present; it is ignored.
+ *   - Indices are int32, so n < 2^31 and nnz < 2^31.
+ *   - Pointers are borrowed: the library never frees caller memory and
+ *     keeps no pointer to it after a call returns.  "device" means memory
+ *     the current CUDA device can address (cudaMalloc, cudaMallocAsync or
+ *     torch CUDA tensors); "host" means ordinary or pinned host memory.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; calls that return host results
+ *     synchronise that stream before returning.
+ *   - Every call returns a pr_status.  PR_ECUDA means a CUDA runtime call
+ *     failed (pr_last_cuda_error gives its code); PR_ETIMEOUT means a
+ *     device-side wait reached its time limit (about two seconds) and the
+ *     kernel returned early; the CUDA context stays usable after both.
+ *   - The library allocates device memory with cudaMallocAsync on the
+ *     caller's stream and releases it the same way.
+ */
+#ifndef PRGB_H
+#define PRGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PR_OK = 0,
+    PR_EINVAL = 1,     /* bad argument or malformed CSR */
+    PR_ENOMEM = 2,     /* device allocation failed */
+    PR_ECUDA = 3,      /* a CUDA runtime call failed */
+    PR_ENOCONV = 4,    /* max_iter reached; R holds the partial sum */
+    PR_ETIMEOUT = 5,   /* a bounded device-side wait expired */
+    PR_EINTERNAL = 6   /* an internal consistency check failed */
+} pr_status;
+
+/* CSR out-adjacency of the graph (see conventions above). */
+typedef struct pr_csr {
+    int32_t n;             /* number of vertices, >= 0 */
+    int64_t nnz;           /* number of stored edges (self-loops included) */
+    const int32_t *rowptr; /* [n+1] */
+    const int32_t *col;    /* [nnz] */
+    int32_t on_host;       /* 0: rowptr/col are device pointers; 1: host
+                              pointers, copied to the device inside the call */
+} pr_csr;
+
+/* Opaque prepared graph: the validated, loop-free out-adjacency plus the
+ * in-adjacency (CSC) built once by pr_graph_create (the graph model of
+ * Sec. 3 and Def. 3.4).  Owned by the library until pr_graph_destroy. */
+typedef struct pr_graph_s pr_graph;
+
+/* Opaque partition: the SCC/CAC components, their levels and the permuted
+ * layout the solver streams.  Owned by the library until
+ * pr_partition_destroy; it refers to its pr_graph, which must outlive it. */
+typedef struct pr_partition_s pr_partition;
+
+/* Component types (Sec. 3 Def. 3.1-3.2; 1-vertex components are CACs). */
+#define PR_TYPE_CAC 0
+#define PR_TYPE_SCC 1
+
+/* Stopping norms for the SCC power series (Sec. 4.3.2). */
+#define PR_NORM_L1 0   /* stop after adding P with ||P||_1 <= tol*|C|/n */
+#define PR_NORM_LINF 1 /* the paper's rule: iterate while max(P) >= tol */
+
+/* Arithmetic of the solve. */
+#define PR_PREC_FP64 0  /* FP64 throughout */
+
+typedef struct pr_solve_opts {
+    int32_t norm;                /* PR_NORM_L1 (default) or PR_NORM_LINF */
+    int32_t max_iter;            /* per component; <= 0 selects 10000 */
+    int32_t precision;           /* PR_PREC_FP64 */
+    int32_t io_on_host;          /* 1: u and R are host pointers (copied in
+                                    and out inside the call) */
+    const int32_t *replay_iters; /* optional HOST array [n_comp]: run exactly
+                                    this many series iterations per SCC
+                                    component instead of the stopping rule
+                                    (index = canonical component id); for
+                                    pr_global_power, element 0 is used */
+} pr_solve_opts;
+
+typedef struct pr_solve_stats {
+    int32_t iters_max;    /* largest per-component (or global) iteration count */
+    int32_t n_levels;     /* levels walked by the solve */
+    int64_t edge_visits;  /* edges read by the gather, CAC and SpMV kernels */
+    int64_t launches;     /* kernels launched by the call */
+    int32_t *comp_iters;  /* optional caller-owned HOST array [n_comp];
+                             filled with per-component iteration counts when
+                             non-NULL (0 for CACs and 1-vertex components) */
+} pr_solve_stats;
+
+/*
+ * pr_graph_create -- validate a CSR and prepare it (Sec. 3: simple digraph;
+ * Sec. 4.1 / 5.2: self-loops ignored): loop-free out-degrees and
+ * out-adjacency, and the in-adjacency with sources ascending in each column.
+ *   csr    : the graph (device or host arrays, see pr_csr.on_host).
+ *   stream : CUDA stream.
+ *   out    : receives a new graph handle on PR_OK (NULL otherwise).
+ * Errors: PR_EINVAL for n < 0, nnz < 0 or >= 2^31, NULL arrays with n > 0, or
+ * a malformed CSR (rowptr[0] != 0, rowptr[n] != nnz, non-monotone rowptr,
+ * column out of range, unsorted or duplicate columns in a row); PR_ENOMEM,
+ * PR_ECUDA.  Synchronises the stream.
+ */
+pr_status pr_graph_create(const pr_csr *csr, void *stream, pr_graph **out);
+
+/* Release a graph (asynchronously, on the stream it was created on, which
+ * must still exist).  Partitions built on it must be destroyed first.  NULL is
+ * accepted. */
+void pr_graph_destroy(pr_graph *g);
+
+/*
+ * pr_partition_create -- component finding and intermediate step
+ * (Sec. 4.1-4.2).
+ *   g      : a prepared graph; it must outlive the partition.
+ *   flags  : reserved, pass 0.
+ *   stream : CUDA stream.
+ *   out    : receives a new partition handle on PR_OK (NULL otherwise).
+ * The partition is the unique SCC/CAC partition of Theorem 3.1 with
+ * 0-based levels (Def. 3.3).  Component ids are canonical: sorted by level
+ * descending, size descending, smallest vertex id ascending.
+ * Errors: PR_EINVAL for a NULL graph or output, or flags != 0; PR_ENOMEM,
+ * PR_ECUDA, PR_ETIMEOUT, PR_EINTERNAL.  Synchronises the stream (component
+ * counts are read back).
+ */
+pr_status pr_partition_create(const pr_graph *g, uint32_t flags, void *stream, pr_partition **out);
+
+/*
+ * pr_partition_query -- copy the partition out, one entry per vertex in the
+ * caller's original vertex order.
+ *   comp_id [n] int32 (device), type [n] uint8 PR_TYPE_* (device),
+ *   level [n] int32 (device): any of them may be NULL to skip it.
+ *   n_comp, n_levels: host int32 outputs, may be NULL.
+ * Errors: PR_EINVAL for a NULL partition; PR_ECUDA.
+ */
+pr_status pr_partition_query(const pr_partition *part, int32_t *comp_id, uint8_t *type,
+                             int32_t *level, int32_t *n_comp, int32_t *n_levels, void *stream);
+
+/*
+ * pr_partition_info -- host-side counts: n, loop-free edge count, number of
+ * components, levels, SCC components, and vertices in SCC components.
+ * Any output may be NULL.
+ */
+pr_status pr_partition_info(const pr_partition *part, int32_t *n, int64_t *m, int32_t *n_comp,
+                            int32_t *n_levels, int32_t *n_scc, int32_t *n_scc_vertices);
+
+/* Release the partition's device memory (asynchronously, on the stream it
+ * was created on, which must still exist). NULL is accepted. */
+void pr_partition_destroy(pr_partition *part);
+
+/*
+ * pr_solve -- the PageRank step of Sec. 4.3 on a partition.
+ *   part   : from pr_partition_create.
+ *   c      : damping factor, 0 < c < 1 (Def. 3.4).
+ *   u      : [n] float64 weight vector W of Def. 3.5, finite and >= 0, in the
+ *            original vertex order (device, or host with io_on_host = 1).
+ *   tol    : > 0.  With PR_NORM_L1 each SCC component C stops after adding a
+ *            series term of L1 norm <= tol*|C|/n, which bounds the L1
+ *            residual of the whole solve by c*tol; CACs and 1-vertex
+ *            components are solved exactly (Sec. 4.3 items 1-2).
+ *   opts   : NULL for defaults.
+ *   R      : [n] float64 output in the original vertex order (device, or
+ *            host with io_on_host = 1), caller-owned.
+ *   stats  : optional host output.
+ * Levels are solved from the highest down; all components of one level run
+ * concurrently (Sec. 4.3, last paragraph).  Synchronises the stream.
+ * Errors: PR_EINVAL (bad c, tol, u; NULL pointers; replay array with a
+ * negative entry), PR_ENOCONV (R holds the partial sums, stats are valid),
+ * PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT.
+ */
+pr_status pr_solve(const pr_partition *part, double c, const double *u, double tol,
+                   const pr_solve_opts *opts, double *R, pr_solve_stats *stats, void *stream);
+
+/*
+ * pr_global_power -- the baseline of Sec. 4.3.2 / Sec. 5.2 method 1: the
+ * power series P_0 = u, P_{k+1} = c A^T P_k, R = sum_k P_k on the whole
+ * graph, stopping after adding P with ||P||_1 <= tol (PR_NORM_L1) or when
+ * max(P) < tol (PR_NORM_LINF).  Arguments as for pr_solve, on a prepared
+ * graph.  Synchronises the stream.
+ */
+pr_status pr_global_power(const pr_graph *g, double c, const double *u, double tol,
+                          const pr_solve_opts *opts, double *R, pr_solve_stats *stats,
+                          void *stream);
+
+/*
+ * pr_residual_l1 -- || u + c A^T (R ./ outdeg) - R ||_1 in FP64, the residual
+ * of the system of Def. 3.5 (dangling vertices contribute no inflow).
+ *   g : prepared graph; c as above; u, R : [n] float64 DEVICE pointers in the
+ *   original vertex order.
+ *   out_host : receives the residual.
+ * Deterministic: the same inputs give the same bits.  Synchronises the
+ * stream.
+ */
+pr_status pr_residual_l1(const pr_graph *g, double c, const double *u, const double *R,
+                         double *out_host, void *stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *pr_status_str(pr_status s);
+
+/* The cudaError_t of the most recent PR_ECUDA in this thread (0 if none). */
+int pr_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRGB_H */

@@ -1,0 +1,309 @@
+"""Componentwise PageRank on GB300: thin Python binding of ``libprgb.so``.
+
+The C library (``include/prgb.h``) does all the work in CUDA kernels; this
+module only marshals arguments with ctypes.  PyTorch provides device memory
+and the current stream.  There is no CPU fallback: if the library is missing
+or cannot be loaded, every call raises.
+
+Pipeline (Sec. 4 of arXiv 1609.09068):
+
+    g = graph(rowptr, col)          # validated, loop-free graph + CSC
+    p = partition(g)                # SCC/CAC partition with levels + layout
+    R = solve(p, 0.85, u, 1e-10)    # level-by-level PageRank step
+    Rg, k = global_power(g, 0.85, u, 1e-10)   # the baseline power series
+    r = residual_l1(g, 0.85, u, R)  # || u + c A^T (R/outdeg) - R ||_1
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = [
+    "PrError", "Graph", "Partition", "graph", "partition", "solve", "global_power",
+    "residual_l1", "load_library", "library_path", "TYPE_CAC", "TYPE_SCC",
+    "NORM_L1", "NORM_LINF",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libprgb.so")
+
+TYPE_CAC = 0
+TYPE_SCC = 1
+NORM_L1 = 0
+NORM_LINF = 1
+PREC_FP64 = 0
+
+_STATUS = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOMEM", 3: "PR_ECUDA", 4: "PR_ENOCONV",
+           5: "PR_ETIMEOUT", 6: "PR_EINTERNAL"}
+
+
+class PrError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        self.name = _STATUS.get(code, str(code))
+        super().__init__(f"{where}: {self.name}")
+
+
+class _Csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("on_host", C.c_int32)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("norm", C.c_int32), ("max_iter", C.c_int32), ("precision", C.c_int32),
+                ("io_on_host", C.c_int32), ("replay_iters", C.c_void_p)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("iters_max", C.c_int32), ("n_levels", C.c_int32), ("edge_visits", C.c_int64),
+                ("launches", C.c_int64), ("comp_iters", C.c_void_p)]
+
+
+_lib = None
+
+# name -> (restype, argtypes), mirroring include/prgb.h
+_SIGS = {
+    "pr_graph_create": (C.c_int, [C.POINTER(_Csr), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "pr_graph_destroy": (None, [C.c_void_p]),
+    "pr_partition_create": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "pr_partition_query": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
+    "pr_partition_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pr_partition_destroy": (None, [C.c_void_p]),
+    "pr_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.POINTER(_Opts),
+                           C.c_void_p, C.POINTER(_Stats), C.c_void_p]),
+    "pr_global_power": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.POINTER(_Opts),
+                                  C.c_void_p, C.POINTER(_Stats), C.c_void_p]),
+    "pr_residual_l1": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                                 C.POINTER(C.c_double), C.c_void_p]),
+    "pr_status_str": (C.c_char_p, [C.c_int]),
+    "pr_last_cuda_error": (C.c_int, []),
+}
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libprgb.so (built by ``_build.build()``); raises if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: run __graft_entry__.build() first")
+        lib = C.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise PrError(rc, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev_i32(x):
+    torch = _torch()
+    t = torch.as_tensor(x)
+    if t.dtype != torch.int32:
+        t = t.to(torch.int32)
+    if not t.is_cuda:
+        t = t.cuda()
+    return t.contiguous()
+
+
+def _dev_f64(x):
+    torch = _torch()
+    t = torch.as_tensor(x)
+    if t.dtype != torch.float64:
+        t = t.to(torch.float64)
+    if not t.is_cuda:
+        t = t.cuda()
+    return t.contiguous()
+
+
+class Graph:
+    """Prepared graph (``pr_graph``): validated CSR, loop-free, with CSC."""
+
+    def __init__(self, rowptr, col, on_host=False):
+        lib = load_library()
+        self._h = C.c_void_p()
+        if on_host:
+            rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+            cl = np.ascontiguousarray(col, dtype=np.int32)
+            keep = (rp, cl)
+            csr = _Csr(rp.shape[0] - 1, cl.shape[0], rp.ctypes.data, cl.ctypes.data, 1)
+        else:
+            rp = _dev_i32(rowptr)
+            cl = _dev_i32(col)
+            keep = (rp, cl)
+            csr = _Csr(rp.shape[0] - 1, cl.shape[0], rp.data_ptr(), cl.data_ptr() if cl.numel() else None, 0)
+        self.n = int(csr.n)
+        rc = lib.pr_graph_create(C.byref(csr), _stream(), C.byref(self._h))
+        del keep
+        _check(rc, "pr_graph_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load_library().pr_graph_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Partition:
+    """SCC/CAC partition with levels and the solver layout (``pr_partition``)."""
+
+    def __init__(self, g: Graph):
+        lib = load_library()
+        self.graph = g  # the partition refers to the graph's buffers
+        self._h = C.c_void_p()
+        _check(lib.pr_partition_create(g.handle, 0, _stream(), C.byref(self._h)), "pr_partition_create")
+        n, m, nc, nl, ns, nsv = (C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32(),
+                                 C.c_int32())
+        _check(lib.pr_partition_info(self._h, C.byref(n), C.byref(m), C.byref(nc), C.byref(nl),
+                                     C.byref(ns), C.byref(nsv)), "pr_partition_info")
+        self.n, self.m, self.n_comp, self.n_levels = n.value, m.value, nc.value, nl.value
+        self.n_scc, self.n_scc_vertices = ns.value, nsv.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def query(self):
+        """(comp_id int32, type uint8, level int32) CUDA tensors, original order."""
+        torch = _torch()
+        comp = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        typ = torch.empty(self.n, dtype=torch.uint8, device="cuda")
+        lev = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        nc, nl = C.c_int32(), C.c_int32()
+        _check(load_library().pr_partition_query(self._h, comp.data_ptr() if self.n else None,
+                                                 typ.data_ptr() if self.n else None,
+                                                 lev.data_ptr() if self.n else None,
+                                                 C.byref(nc), C.byref(nl), _stream()),
+               "pr_partition_query")
+        return comp, typ, lev
+
+    def close(self):
+        if self._h:
+            load_library().pr_partition_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def graph(rowptr, col, on_host=False):
+    return Graph(rowptr, col, on_host=on_host)
+
+
+def partition(g: Graph):
+    return Partition(g)
+
+
+def _opts(norm, max_iter, io_on_host, replay):
+    o = _Opts(int(norm), int(max_iter), PREC_FP64, int(io_on_host), None)
+    keep = None
+    if replay is not None:
+        keep = np.ascontiguousarray(replay, dtype=np.int32)
+        o.replay_iters = keep.ctypes.data
+    return o, keep
+
+
+def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iters=None,
+          with_stats=False, allow_noconv=False):
+    """Sec. 4.3 solve on device tensors; returns R (float64, original order).
+
+    ``u`` may be a CUDA tensor or a numpy array (host I/O through the C ABI's
+    io_on_host path; R is then returned as numpy)."""
+    lib = load_library()
+    on_host = isinstance(u, np.ndarray)
+    o, keep = _opts(norm, max_iter, on_host, replay_iters)
+    comp_iters = np.zeros(max(part.n_comp, 1), np.int32)
+    st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data)
+    if on_host:
+        uh = np.ascontiguousarray(u, dtype=np.float64)
+        R = np.empty(part.n, np.float64)
+        rc = lib.pr_solve(part.handle, float(c), uh.ctypes.data, float(tol), C.byref(o),
+                          R.ctypes.data, C.byref(st), _stream())
+    else:
+        torch = _torch()
+        ud = _dev_f64(u)
+        R = torch.empty(part.n, dtype=torch.float64, device="cuda")
+        rc = lib.pr_solve(part.handle, float(c), ud.data_ptr() if part.n else None, float(tol),
+                          C.byref(o), R.data_ptr() if part.n else None, C.byref(st), _stream())
+    if not (allow_noconv and rc == 4):
+        _check(rc, "pr_solve")
+    del keep
+    if with_stats:
+        return R, {"iters_max": st.iters_max, "n_levels": st.n_levels, "edge_visits": st.edge_visits,
+                   "launches": st.launches, "comp_iters": comp_iters[: part.n_comp].copy(),
+                   "status": rc}
+    return R
+
+
+def global_power(g: Graph, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iters=None,
+                 with_stats=False, allow_noconv=False):
+    """Baseline power series on the whole graph; returns (R, iterations)."""
+    lib = load_library()
+    on_host = isinstance(u, np.ndarray)
+    rep = None if replay_iters is None else [int(replay_iters)]
+    o, keep = _opts(norm, max_iter, on_host, rep)
+    st = _Stats(0, 0, 0, 0, None)
+    if on_host:
+        uh = np.ascontiguousarray(u, dtype=np.float64)
+        R = np.empty(g.n, np.float64)
+        rc = lib.pr_global_power(g.handle, float(c), uh.ctypes.data, float(tol), C.byref(o),
+                                 R.ctypes.data, C.byref(st), _stream())
+    else:
+        torch = _torch()
+        ud = _dev_f64(u)
+        R = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        rc = lib.pr_global_power(g.handle, float(c), ud.data_ptr() if g.n else None, float(tol),
+                                 C.byref(o), R.data_ptr() if g.n else None, C.byref(st), _stream())
+    if not (allow_noconv and rc == 4):
+        _check(rc, "pr_global_power")
+    del keep
+    if with_stats:
+        return R, st.iters_max, {"edge_visits": st.edge_visits, "status": rc}
+    return R, st.iters_max
+
+
+def residual_l1(g: Graph, c, u, R):
+    """|| u + c A^T (R/outdeg) - R ||_1 in FP64 on the device."""
+    lib = load_library()
+    ud = _dev_f64(u)
+    Rd = _dev_f64(R)
+    out = C.c_double(0.0)
+    _check(lib.pr_residual_l1(g.handle, float(c), ud.data_ptr() if g.n else None,
+                              Rd.data_ptr() if g.n else None, C.byref(out), _stream()),
+           "pr_residual_l1")
+    return out.value

@@ -1,0 +1,313 @@
+// api.cu -- the extern "C" entry points declared in include/prgb.h.
+#include <math.h>
+#include <stdint.h>
+
+#include <new>
+
+#include "common.cuh"
+#include "global.cuh"
+#include "solve.cuh"
+
+namespace prgb {
+int last_cuda_error();
+pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wave, int32_t max_wave, Arena& tmp,
+                       Ctl* ctl);
+
+// keep freed stream-ordered memory cached in the device's default pool so
+// repeated calls do not return it to the driver
+static void tune_pool() {
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+
+static pr_status finish_sync(cudaStream_t s, Ctl* ctl, int* flags_out) {
+  int h[2] = {0, 0};
+  PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaMemcpyAsync(&h[1], &ctl->flags[0], 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  if (flags_out) *flags_out = h[1];
+  return (pr_status)h[0];
+}
+
+}  // namespace prgb
+
+using namespace prgb;
+
+extern "C" {
+
+const char* pr_status_str(pr_status s) {
+  switch (s) {
+    case PR_OK: return "ok";
+    case PR_EINVAL: return "invalid argument";
+    case PR_ENOMEM: return "out of device memory";
+    case PR_ECUDA: return "CUDA runtime error";
+    case PR_ENOCONV: return "not converged within max_iter";
+    case PR_ETIMEOUT: return "device-side wait timed out";
+    case PR_EINTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+int pr_last_cuda_error(void) { return prgb::last_cuda_error(); }
+
+pr_status pr_graph_create(const pr_csr* csr, void* stream, pr_graph** out) {
+  if (!out) return PR_EINVAL;
+  *out = nullptr;
+  if (!csr || csr->n < 0 || csr->nnz < 0 || csr->nnz >= ((int64_t)1 << 31)) return PR_EINVAL;
+  if (csr->n > 0 && (!csr->rowptr || (csr->nnz > 0 && !csr->col))) return PR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  tune_pool();
+  pr_graph_s* G = new (std::nothrow) pr_graph_s;
+  if (!G) return PR_ENOMEM;
+  G->stream = s;
+  G->keep = new (std::nothrow) Arena(s);
+  if (!G->keep) {
+    delete G;
+    return PR_ENOMEM;
+  }
+  pr_status st;
+  {
+    Arena tmp(s);
+    Ctl* ctl = nullptr;
+    st = tmp.alloc(&ctl, 1);
+    if (st == PR_OK) {
+      cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+      st = ingest(csr, &G->g, *G->keep, tmp, ctl);
+    }
+    if (st == PR_OK) {
+      int e = 0;
+      st = finish_sync(s, ctl, &e);
+    }
+  }
+  if (st != PR_OK) {
+    delete G->keep;
+    delete G;
+    return st;
+  }
+  *out = G;
+  return PR_OK;
+}
+
+void pr_graph_destroy(pr_graph* g) {
+  if (!g) return;
+  delete g->keep;
+  delete g;
+}
+
+pr_status pr_partition_create(const pr_graph* g, uint32_t flags, void* stream, pr_partition** out) {
+  if (!out) return PR_EINVAL;
+  *out = nullptr;
+  if (!g || flags != 0) return PR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  tune_pool();
+  pr_partition_s* P = new (std::nothrow) pr_partition_s;
+  if (!P) return PR_ENOMEM;
+  P->stream = s;
+  P->keep = new (std::nothrow) Arena(s);
+  if (!P->keep) {
+    delete P;
+    return PR_ENOMEM;
+  }
+  P->g = g->g;
+  const int32_t n = P->g.n;
+  pr_status st = PR_OK;
+  {
+    Arena tmp(s);
+    Ctl* ctl = nullptr;
+    int32_t *rep = nullptr, *crep = nullptr, *wave = nullptr;
+    int32_t max_wave = 0;
+    if (st == PR_OK) st = tmp.alloc(&ctl, 1);
+    if (st == PR_OK) st = P->keep->alloc(&P->comp_id, (size_t)n);
+    if (st == PR_OK) st = P->keep->alloc(&P->type, (size_t)n);
+    if (st == PR_OK) st = P->keep->alloc(&P->level, (size_t)n);
+    if (st == PR_OK) st = tmp.alloc(&rep, (size_t)n);
+    if (st == PR_OK) st = tmp.alloc(&crep, (size_t)n);
+    if (st == PR_OK) st = tmp.alloc(&wave, (size_t)n);
+    if (st == PR_OK && cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) st = PR_ECUDA;
+    if (st == PR_OK) st = scc_detect(P->g, rep, tmp, ctl);
+    if (st == PR_OK) st = levels_and_merge(P->g, rep, crep, P->level, P->type, wave, &max_wave, tmp, ctl);
+    if (st == PR_OK) st = build_layout(P, crep, wave, max_wave, tmp, ctl);
+    if (st == PR_OK) st = finish_sync(s, ctl, nullptr);
+  }
+  if (st != PR_OK) {
+    delete P->keep;
+    delete P;
+    return st;
+  }
+  *out = P;
+  return PR_OK;
+}
+
+pr_status pr_partition_query(const pr_partition* part, int32_t* comp_id, uint8_t* type, int32_t* level,
+                             int32_t* n_comp, int32_t* n_levels, void* stream) {
+  if (!part) return PR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)part->g.n;
+  if (n > 0) {
+    if (comp_id) PRGB_CUDA(cudaMemcpyAsync(comp_id, part->comp_id, n * 4, cudaMemcpyDeviceToDevice, s));
+    if (type) PRGB_CUDA(cudaMemcpyAsync(type, part->type, n, cudaMemcpyDeviceToDevice, s));
+    if (level) PRGB_CUDA(cudaMemcpyAsync(level, part->level, n * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  if (n_comp) *n_comp = part->n_comp;
+  if (n_levels) *n_levels = part->n_levels;
+  return PR_OK;
+}
+
+pr_status pr_partition_info(const pr_partition* part, int32_t* n, int64_t* m, int32_t* n_comp, int32_t* n_levels,
+                            int32_t* n_scc, int32_t* n_scc_vertices) {
+  if (!part) return PR_EINVAL;
+  if (n) *n = part->g.n;
+  if (m) *m = part->g.m;
+  if (n_comp) *n_comp = part->n_comp;
+  if (n_levels) *n_levels = part->n_levels;
+  if (n_scc) *n_scc = part->n_scc;
+  if (n_scc_vertices) *n_scc_vertices = part->n_scc_vertices;
+  return PR_OK;
+}
+
+void pr_partition_destroy(pr_partition* part) {
+  if (!part) return;
+  delete part->keep;
+  delete part;
+}
+
+static pr_status check_solve_args(double c, const double* u, double tol, const double* R) {
+  if (!(c > 0.0 && c < 1.0) || !(tol > 0.0) || !isfinite(tol)) return PR_EINVAL;
+  if (!u || !R) return PR_EINVAL;
+  return PR_OK;
+}
+
+pr_status pr_solve(const pr_partition* part, double c, const double* u, double tol, const pr_solve_opts* opts,
+                   double* R, pr_solve_stats* stats, void* stream) {
+  if (!part) return PR_EINVAL;
+  const int32_t n = part->g.n;
+  if (n > 0) PRGB_TRY(check_solve_args(c, u, tol, R));
+  pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr};
+  if (opts) o = *opts;
+  if (o.max_iter <= 0) o.max_iter = 10000;
+  if (o.norm != PR_NORM_L1 && o.norm != PR_NORM_LINF) return PR_EINVAL;
+  if (o.precision != PR_PREC_FP64) return PR_EINVAL;
+  if (o.replay_iters) {
+    for (int32_t k = 0; k < part->n_comp; k++)
+      if (o.replay_iters[k] < 0 || o.replay_iters[k] > 1000000) return PR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t K = part->n_comp;
+  Arena tmp(s);
+  Ctl* ctl = nullptr;
+  int32_t* iters = nullptr;
+  int32_t* replay = nullptr;
+  const double* du = u;
+  double* dR = R;
+  PRGB_TRY(tmp.alloc(&ctl, 1));
+  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  PRGB_TRY(tmp.alloc(&iters, (size_t)K));
+  if (K > 0) PRGB_CUDA(cudaMemsetAsync(iters, 0, (size_t)K * 4, s));
+  if (o.replay_iters && K > 0) {
+    PRGB_TRY(tmp.alloc(&replay, (size_t)K));
+    PRGB_CUDA(cudaMemcpyAsync(replay, o.replay_iters, (size_t)K * 4, cudaMemcpyHostToDevice, s));
+  }
+  if (o.io_on_host && n > 0) {
+    double *tu = nullptr, *tR = nullptr;
+    PRGB_TRY(tmp.alloc(&tu, (size_t)n));
+    PRGB_TRY(tmp.alloc(&tR, (size_t)n));
+    PRGB_CUDA(cudaMemcpyAsync(tu, u, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    du = tu;
+    dR = tR;
+  }
+  int64_t launches = 0;
+  PRGB_TRY(run_solve(part, c, du, tol, o.norm, o.max_iter, replay, dR, iters, tmp, ctl, &launches));
+  if (o.io_on_host && n > 0) PRGB_CUDA(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  int flags = 0;
+  PRGB_TRY(finish_sync(s, ctl, &flags));
+  if (stats) {
+    stats->n_levels = part->n_levels;
+    stats->launches = launches;
+    stats->iters_max = 0;
+    stats->edge_visits = 0;
+    if (K > 0) {
+      int32_t* h = stats->comp_iters;
+      std::vector<int32_t> local;
+      if (!h) {
+        local.resize(K);
+        h = local.data();
+      }
+      PRGB_CUDA(cudaMemcpyAsync(h, iters, (size_t)K * 4, cudaMemcpyDeviceToHost, s));
+      PRGB_TRY(solve_edge_visits(part, iters, &stats->edge_visits, tmp));  // synchronises
+      for (int32_t k = 0; k < K; k++) stats->iters_max = h[k] > stats->iters_max ? h[k] : stats->iters_max;
+    }
+  }
+  return flags ? PR_ENOCONV : PR_OK;
+}
+
+pr_status pr_global_power(const pr_graph* g, double c, const double* u, double tol, const pr_solve_opts* opts,
+                          double* R, pr_solve_stats* stats, void* stream) {
+  if (!g) return PR_EINVAL;
+  const int32_t n = g->g.n;
+  if (n > 0) PRGB_TRY(check_solve_args(c, u, tol, R));
+  pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr};
+  if (opts) o = *opts;
+  if (o.max_iter <= 0) o.max_iter = 10000;
+  if (o.norm != PR_NORM_L1 && o.norm != PR_NORM_LINF) return PR_EINVAL;
+  if (o.precision != PR_PREC_FP64) return PR_EINVAL;
+  int fixed = -1;
+  if (o.replay_iters) {
+    fixed = o.replay_iters[0];
+    if (fixed < 0 || fixed > 1000000) return PR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena tmp(s);
+  Ctl* ctl = nullptr;
+  PRGB_TRY(tmp.alloc(&ctl, 1));
+  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  const double* du = u;
+  double* dR = R;
+  if (o.io_on_host && n > 0) {
+    double *tu = nullptr, *tR = nullptr;
+    PRGB_TRY(tmp.alloc(&tu, (size_t)n));
+    PRGB_TRY(tmp.alloc(&tR, (size_t)n));
+    PRGB_CUDA(cudaMemcpyAsync(tu, u, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    du = tu;
+    dR = tR;
+  }
+  int iters = 0;
+  pr_status st = run_global(g->g, c, du, tol, o.norm, o.max_iter, fixed, dR, &iters, tmp, ctl);
+  if (st != PR_OK && st != PR_ENOCONV) return st;
+  if (o.io_on_host && n > 0) {
+    PRGB_CUDA(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    PRGB_CUDA(cudaStreamSynchronize(s));
+  }
+  if (stats) {
+    stats->iters_max = iters;
+    stats->n_levels = 1;
+    stats->launches = 1;
+    stats->edge_visits = (int64_t)iters * g->g.m;
+    if (stats->comp_iters) stats->comp_iters[0] = iters;
+  }
+  return st;
+}
+
+pr_status pr_residual_l1(const pr_graph* g, double c, const double* u, const double* R, double* out_host,
+                         void* stream) {
+  if (!g || !out_host) return PR_EINVAL;
+  if (g->g.n > 0 && (!u || !R)) return PR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena tmp(s);
+  double* part = nullptr;
+  double* out = nullptr;
+  PRGB_TRY(tmp.alloc(&part, (size_t)residual_grid()));
+  PRGB_TRY(tmp.alloc(&out, 1));
+  PRGB_TRY(run_residual(g->g, c, u, R, part, out, s));
+  PRGB_CUDA(cudaMemcpyAsync(out_host, out, 8, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  return PR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,307 @@
+// common.cuh -- internal definitions shared by the CUDA translation units of
+// the componentwise PageRank library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "prgb.h"
+
+namespace prgb {
+
+constexpr int kWarp = 32;
+constexpr int kBlock = 256;                 // threads per block for most kernels
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded device waits: 2 s
+
+// ---------------------------------------------------------------------------
+// status plumbing
+// ---------------------------------------------------------------------------
+void set_last_cuda_error(cudaError_t e);
+
+#define PRGB_TRY(expr)                                   \
+  do {                                                   \
+    pr_status st_ = (expr);                              \
+    if (st_ != PR_OK) return st_;                        \
+  } while (0)
+
+#define PRGB_CUDA(expr)                                  \
+  do {                                                   \
+    cudaError_t e_ = (expr);                             \
+    if (e_ != cudaSuccess) {                             \
+      ::prgb::set_last_cuda_error(e_);                   \
+      return e_ == cudaErrorMemoryAllocation ? PR_ENOMEM : PR_ECUDA; \
+    }                                                    \
+  } while (0)
+
+#define PRGB_LAUNCH() PRGB_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// device control block: error word and grid-barrier state.  One per call
+// site that needs it, zeroed before each persistent launch.
+// ---------------------------------------------------------------------------
+struct Ctl {
+  int err;               // pr_status written by kernels (first error wins)
+  int where;             // diagnostic: which wait expired
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int cnt[8];            // frontier counters (rotating)
+  int flags[8];          // misc flags (e.g. not-converged)
+  double dsum[4];
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int vload(const int* p) { return *(volatile const int*)p; }
+__device__ __forceinline__ unsigned int vloadu(const unsigned int* p) {
+  return *(volatile const unsigned int*)p;
+}
+
+__device__ __forceinline__ void set_err(Ctl* ctl, int code, int where) {
+  if (atomicCAS(&ctl->err, 0, code) == 0) ctl->where = where;
+}
+
+// Grid-wide barrier for cooperative launches, with a bounded wait: after
+// kWaitNs the waiting block records PR_ETIMEOUT and leaves.  Returns false
+// when any block has recorded an error, so that callers can return early.
+// The Ctl block must have bar_count == 0 when the kernel starts.
+__device__ __forceinline__ bool grid_sync(Ctl* ctl, int where) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int nb = gridDim.x;
+    const unsigned int gen = vloadu(&ctl->bar_gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == nb - 1) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (vloadu(&ctl->bar_gen) == gen) {
+        if (vload(&ctl->err) != 0) break;
+        __nanosleep(32);
+        if (globaltimer_ns() - t0 > kWaitNs) {
+          set_err(ctl, PR_ETIMEOUT, where);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return vload(&ctl->err) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int G>
+__device__ __forceinline__ double group_max(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum with a fixed reduction tree (deterministic for a fixed
+// blockDim).  scratch: at least blockDim/32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+  v = group_sum<32>(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+  if (w == 0) t = group_sum<32>(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* scratch) {
+  v = group_max<32>(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+  if (w == 0) t = group_max<32>(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// stream-ordered device buffers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+class Arena {
+ public:
+  explicit Arena(cudaStream_t s) : s_(s) {}
+  ~Arena() { release(); }
+  template <typename T>
+  pr_status alloc(T** out, size_t count) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, s_);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e);
+      *out = nullptr;
+      return PR_ENOMEM;
+    }
+    bufs_.push_back(p);
+    *out = static_cast<T*>(p);
+    return PR_OK;
+  }
+  void release() {
+    for (void* p : bufs_) cudaFreeAsync(p, s_);
+    bufs_.clear();
+  }
+  cudaStream_t stream() const { return s_; }
+
+ private:
+  cudaStream_t s_;
+  std::vector<void*> bufs_;
+};
+
+// zero the barrier counter and the frontier counters (not the error word)
+// before a persistent launch
+inline pr_status reset_ctl(Ctl* ctl, cudaStream_t s) {
+  PRGB_CUDA(cudaMemsetAsync(&ctl->bar_count, 0, sizeof(unsigned int), s));
+  PRGB_CUDA(cudaMemsetAsync(ctl->cnt, 0, sizeof(ctl->cnt), s));
+  return PR_OK;
+}
+
+// number of SMs of the current device (cached per device)
+int num_sms();
+
+// cooperative launch with as many co-resident blocks as fit (capped per SM)
+pr_status launch_coop(const void* kernel, int block, size_t smem, cudaStream_t s, void** args,
+                      int max_per_sm, int* grid_out);
+
+// ---------------------------------------------------------------------------
+// primitives (prims.cu)
+// ---------------------------------------------------------------------------
+// out[0] = 0, out[i+1] = in[0] + ... + in[i]  (out has n+1 entries)
+pr_status scan_i32(const int32_t* in, int32_t* out, int64_t n, Arena& a);
+pr_status scan_u8(const uint8_t* in, int32_t* out, int64_t n, Arena& a);
+// Stable LSD radix sort of (key, val) pairs on the low key_bits bits of key.
+// Result is left in keys/vals; keys_tmp/vals_tmp are scratch of n entries.
+pr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                           int64_t n, int key_bits, Arena& a);
+int bits_for(uint32_t max_value);
+pr_status iota_u32(uint32_t* out, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// loop-free device graph
+// ---------------------------------------------------------------------------
+struct DevGraph {
+  int32_t n = 0;
+  int64_t m = 0;            // loop-free edges
+  int32_t* optr = nullptr;  // [n+1] out-edges, targets ascending
+  int32_t* oidx = nullptr;  // [m]
+  int32_t* iptr = nullptr;  // [n+1] in-edges, sources ascending
+  int32_t* iidx = nullptr;  // [m]
+  int32_t* outdeg = nullptr;  // [n]
+};
+
+// ingest.cu: validate the CSR, drop loops, build out- and in-adjacency.
+// Buffers of g are allocated from `keep`; scratch from `tmp`.
+pr_status ingest(const pr_csr* csr, DevGraph* g, Arena& keep, Arena& tmp, Ctl* ctl);
+
+// scc.cu: rep[v] = representative (largest vertex id) of v's SCC.
+pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl);
+
+// levels.cu: levels, merge flags and CAC grouping (Theorem 3.1 restated
+// per condensation node).  Outputs per vertex: crep (smallest vertex of the
+// final component), level, type (PR_TYPE_*), wave (longest path to a sink
+// in the condensation, counted in nodes).
+pr_status levels_and_merge(const DevGraph& g, const int32_t* rep, int32_t* crep, int32_t* level,
+                           uint8_t* type, int32_t* wave, int32_t* max_wave, Arena& tmp, Ctl* ctl);
+
+// large components: solved by grid-wide cooperative kernels
+struct LargeComp {
+  int32_t c;       // canonical component id
+  int32_t off;     // first permuted vertex
+  int32_t size;
+  int32_t type;
+  int32_t sub_begin, sub_end;  // sub-level range (CAC topological waves)
+  int32_t level_idx;           // processing index of its level (0 = highest)
+  int32_t pad;
+};
+
+// per level (in processing order): component ranges by class
+//   [cbeg, cta) large, [cta, warp) one CTA each, [warp, single) one warp
+//   each, [single, cend) 1-vertex components
+struct LevelRange {
+  int32_t cbeg, cta, warp, single, cend;
+  int32_t vbeg, vsingle, vend;  // permuted vertex range of the level / its singletons
+};
+
+constexpr int kWarpCompMax = 32;    // components of <= 32 vertices: one warp
+constexpr int kCtaCompMax = 2048;   // components of <= 2048 vertices: one CTA
+
+}  // namespace prgb
+
+// The opaque handles of the C ABI.
+struct pr_graph_s {
+  cudaStream_t stream = nullptr;
+  prgb::Arena* keep = nullptr;  // owns the buffers of g
+  prgb::DevGraph g;
+};
+
+struct pr_partition_s {
+  cudaStream_t stream = nullptr;
+  prgb::Arena* keep = nullptr;   // owns every device buffer below
+  prgb::DevGraph g;
+  int32_t n_comp = 0, n_levels = 0, n_scc = 0, n_scc_vertices = 0;
+  // per original vertex
+  int32_t* comp_id = nullptr;
+  uint8_t* type = nullptr;
+  int32_t* level = nullptr;
+  // permuted layout (p = permuted position)
+  int32_t* perm = nullptr;     // [n] p -> v
+  int32_t* p_outdeg = nullptr; // [n]
+  int32_t* int_ptr = nullptr;  // [n+1] internal in-edges (same component)
+  int32_t* int_idx = nullptr;  //       permuted source positions
+  int32_t* ext_ptr = nullptr;  // [n+1] external in-edges (higher levels)
+  int32_t* ext_idx = nullptr;
+  int32_t* c_off = nullptr;    // [K+1] component -> first permuted vertex
+  int32_t* c_sub = nullptr;    // [K+1] component -> first sub-level
+  int32_t* sub_ptr = nullptr;  // [S+1] sub-level -> first permuted vertex
+  uint8_t* c_type = nullptr;   // [K]
+  int32_t n_sub = 0;
+  int64_t m_int = 0, m_ext = 0;
+  int32_t max_large = 0;       // largest vertex count among large components
+  std::vector<prgb::LevelRange> levels;  // host, processing order
+  std::vector<prgb::LargeComp> large;    // host
+};

@@ -1,0 +1,400 @@
+// layout.cu -- the intermediate step of Sec. 4.2 on the device.
+//
+// * Canonical component ids: components sorted by level descending, then
+//   size descending (Sec. 4.2), ties by smallest vertex ascending.  Two
+//   stable radix sorts (size, then level) over the component list, which is
+//   built in ascending smallest-vertex order.
+// * Permutation: vertices ordered by (component id, wave descending, vertex
+//   id).  Each component is a contiguous range; inside a CAC the wave order
+//   is a topological order (an edge v -> w inside a CAC has wave(v) >
+//   wave(w)), so runs of equal wave ("sub-levels") can be solved one after
+//   the other in a single pass, as the CAC BFS of Sec. 4.3.1 does.
+// * Per permuted vertex: internal in-edges (same component) and external
+//   in-edges (from components of higher levels), both as permuted source
+//   positions in CSC order; these are the edge lists "within each component"
+//   and "between levels" of Sec. 4.2.
+// * Per level: the components split by size class (grid-wide / one CTA /
+//   one warp / 1-vertex collection; Sec. 4.2 groups the 1-vertex components
+//   of a level together).
+#include "common.cuh"
+
+namespace prgb {
+
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+static unsigned grid1(int64_t n) {
+  int64_t g = (n + kBlock - 1) / kBlock;
+  int64_t cap = (int64_t)num_sms() * 16;
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+static unsigned gridw(int64_t n) {
+  int64_t g = (n * 32 + kBlock - 1) / kBlock;
+  int64_t cap = (int64_t)num_sms() * 16;
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+__global__ void csize_k(int32_t n, const int32_t* crep, const int32_t* level, int32_t* csize, uint8_t* isrep,
+                        Ctl* ctl) {
+  for (int64_t v = gtid(); v < n; v += gstride()) {
+    atomicAdd(&csize[crep[v]], 1);
+    isrep[v] = crep[v] == (int32_t)v;
+    atomicMax(&ctl->cnt[5], level[v]);
+  }
+}
+
+__global__ void compact_reps_k(int32_t n, const uint8_t* isrep, const int32_t* ridx, const int32_t* csize,
+                               uint32_t* keys, uint32_t* vals) {
+  for (int64_t v = gtid(); v < n; v += gstride()) {
+    if (isrep[v]) {
+      const int k = ridx[v];
+      vals[k] = (uint32_t)v;
+      keys[k] = (uint32_t)(n - csize[v]);  // size descending
+    }
+  }
+}
+
+__global__ void level_keys_k(int32_t K, const uint32_t* vals, const int32_t* level, int32_t maxl, uint32_t* keys) {
+  for (int64_t k = gtid(); k < K; k += gstride()) keys[k] = (uint32_t)(maxl - level[vals[k]]);
+}
+
+__global__ void comp_of_rep_k(int32_t K, const uint32_t* vals, int32_t* comp_of_rep) {
+  for (int64_t k = gtid(); k < K; k += gstride()) comp_of_rep[vals[k]] = (int32_t)k;
+}
+
+__global__ void vertex_comp_k(int32_t n, const int32_t* crep, const int32_t* comp_of_rep, const int32_t* wave,
+                              int32_t maxw, int32_t* comp_id, uint32_t* keys, uint32_t* vals) {
+  for (int64_t v = gtid(); v < n; v += gstride()) {
+    comp_id[v] = comp_of_rep[crep[v]];
+    keys[v] = (uint32_t)(maxw - wave[v]);  // wave descending
+    vals[v] = (uint32_t)v;
+  }
+}
+
+__global__ void comp_keys_k(int32_t n, const uint32_t* vals, const int32_t* comp_id, uint32_t* keys) {
+  for (int64_t i = gtid(); i < n; i += gstride()) keys[i] = (uint32_t)comp_id[vals[i]];
+}
+
+__global__ void perm_tables_k(int32_t n, const uint32_t* perm_u, const int32_t* comp_id, const int32_t* wave,
+                              const int32_t* outdeg, const uint8_t* type, const int32_t* level, int32_t* perm,
+                              int32_t* pos, int32_t* p_outdeg, int32_t* c_off, uint8_t* c_type, int32_t* c_level,
+                              uint8_t* subflag) {
+  for (int64_t p = gtid(); p < n; p += gstride()) {
+    const int v = (int)perm_u[p];
+    perm[p] = v;
+    pos[v] = (int32_t)p;
+    p_outdeg[p] = outdeg[v];
+    const int c = comp_id[v];
+    bool first = (p == 0) || comp_id[perm_u[p - 1]] != c;
+    if (first) {
+      c_off[c] = (int32_t)p;
+      c_type[c] = type[v];
+      c_level[c] = level[v];
+    }
+    subflag[p] = first || wave[perm_u[p - 1]] != wave[v];
+  }
+}
+
+__global__ void sub_tables_k(int32_t n, int32_t K, const uint8_t* subflag, const int32_t* subidx,
+                             const int32_t* c_off, int32_t* sub_ptr, int32_t* c_sub) {
+  for (int64_t p = gtid(); p < n; p += gstride())
+    if (subflag[p]) sub_ptr[subidx[p]] = (int32_t)p;
+  for (int64_t c = gtid(); c < K; c += gstride()) c_sub[c] = subidx[c_off[c]];
+}
+
+// warp per permuted vertex: count internal / external in-edges
+__global__ void edge_count_k(int32_t n, const int32_t* perm, const int32_t* iptr, const int32_t* iidx,
+                             const int32_t* comp_id, int32_t* icnt, int32_t* ecnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = gtid() >> 5, nw = gstride() >> 5;
+  for (int64_t p = w0; p < n; p += nw) {
+    const int v = perm[p];
+    const int cv = comp_id[v];
+    int in = 0, ex = 0;
+    for (int e = iptr[v] + lane; e < iptr[v + 1]; e += 32) {
+      if (comp_id[iidx[e]] == cv) in++; else ex++;
+    }
+    in = __reduce_add_sync(0xffffffffu, in);
+    ex = __reduce_add_sync(0xffffffffu, ex);
+    if (lane == 0) {
+      icnt[p] = in;
+      ecnt[p] = ex;
+    }
+  }
+}
+
+// warp per permuted vertex: order-preserving split of the in-edges
+__global__ void edge_fill_k(int32_t n, const int32_t* perm, const int32_t* pos, const int32_t* iptr,
+                            const int32_t* iidx, const int32_t* comp_id, const int32_t* int_ptr,
+                            const int32_t* ext_ptr, int32_t* int_idx, int32_t* ext_idx) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const int64_t w0 = gtid() >> 5, nw = gstride() >> 5;
+  for (int64_t p = w0; p < n; p += nw) {
+    const int v = perm[p];
+    const int cv = comp_id[v];
+    int oi = int_ptr[p], oe = ext_ptr[p];
+    const int b = iptr[v], e_end = iptr[v + 1];
+    for (int base = b; base < e_end; base += 32) {
+      const int e = base + lane;
+      const bool ok = e < e_end;
+      int u = ok ? iidx[e] : 0;
+      const bool in = ok && comp_id[u] == cv;
+      const bool ex = ok && !in;
+      const unsigned bi = __ballot_sync(0xffffffffu, in);
+      const unsigned be = __ballot_sync(0xffffffffu, ex);
+      if (in) int_idx[oi + __popc(bi & lt)] = pos[u];
+      if (ex) ext_idx[oe + __popc(be & lt)] = pos[u];
+      oi += __popc(bi);
+      oe += __popc(be);
+    }
+  }
+}
+
+__device__ __forceinline__ int size_class(int sz) {
+  if (sz > kCtaCompMax) return 0;
+  if (sz > kWarpCompMax) return 1;
+  if (sz > 1) return 2;
+  return 3;
+}
+
+__global__ void level_begin_k(int32_t K, const int32_t* c_level, int32_t maxl, int32_t* lvl_cbeg) {
+  for (int64_t c = gtid(); c < K; c += gstride())
+    if (c == 0 || c_level[c - 1] != c_level[c]) lvl_cbeg[maxl - c_level[c]] = (int32_t)c;
+}
+
+__global__ void class_begin_k(int32_t K, const int32_t* c_level, const int32_t* c_off, int32_t maxl,
+                              int32_t* cls /* [nlev][4] */) {
+  for (int64_t c = gtid(); c < K; c += gstride()) {
+    const int li = maxl - c_level[c];
+    const int cl = size_class(c_off[c + 1] - c_off[c]);
+    for (int k = 1; k <= cl; k++) atomicMin(&cls[li * 4 + k], (int)c);
+  }
+}
+
+__global__ void level_ranges_k(int32_t nlev, int32_t K, const int32_t* lvl_cbeg, const int32_t* cls,
+                               const int32_t* c_off, LevelRange* out) {
+  for (int64_t li = gtid(); li < nlev; li += gstride()) {
+    LevelRange r;
+    r.cbeg = lvl_cbeg[li];
+    r.cend = lvl_cbeg[li + 1];
+    r.cta = min(cls[li * 4 + 1], r.cend);
+    r.warp = min(cls[li * 4 + 2], r.cend);
+    r.single = min(cls[li * 4 + 3], r.cend);
+    const bool ok = r.cbeg >= 0 && r.cbeg <= K && r.cend >= 0 && r.cend <= K && r.single >= 0;
+    // a missing level leaves -1 here; the host check rejects it
+    r.vbeg = ok ? c_off[r.cbeg] : -1;
+    r.vsingle = ok ? c_off[r.single] : -1;
+    r.vend = ok ? c_off[r.cend] : -1;
+    out[li] = r;
+  }
+}
+
+__global__ void large_flags_k(int32_t K, const int32_t* c_off, uint8_t* flag) {
+  for (int64_t c = gtid(); c < K; c += gstride()) flag[c] = size_class(c_off[c + 1] - c_off[c]) == 0;
+}
+
+__global__ void large_fill_k(int32_t K, const uint8_t* flag, const int32_t* lidx, const int32_t* c_off,
+                             const int32_t* c_sub, const uint8_t* c_type, const int32_t* c_level, int32_t maxl,
+                             LargeComp* out) {
+  for (int64_t c = gtid(); c < K; c += gstride()) {
+    if (!flag[c]) continue;
+    LargeComp L;
+    L.c = (int32_t)c;
+    L.off = c_off[c];
+    L.size = c_off[c + 1] - c_off[c];
+    L.type = c_type[c];
+    L.sub_begin = c_sub[c];
+    L.sub_end = c_sub[c + 1];
+    L.level_idx = maxl - c_level[c];
+    L.pad = 0;
+    out[lidx[c]] = L;
+  }
+}
+
+__global__ void scc_count_k(int32_t K, const uint8_t* c_type, const int32_t* c_off, Ctl* ctl) {
+  int cnt = 0, verts = 0;
+  for (int64_t c = gtid(); c < K; c += gstride())
+    if (c_type[c] == PR_TYPE_SCC) {
+      cnt++;
+      verts += c_off[c + 1] - c_off[c];
+    }
+  if (cnt) {
+    atomicAdd(&ctl->cnt[3], cnt);
+    atomicAdd(&ctl->cnt[4], verts);
+  }
+}
+
+pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wave, int32_t max_wave, Arena& tmp,
+                       Ctl* ctl) {
+  cudaStream_t s = tmp.stream();
+  Arena& keep = *P->keep;
+  const DevGraph& g = P->g;
+  const int32_t n = g.n;
+  P->n_comp = 0;
+  P->n_levels = 0;
+  if (n == 0) return PR_OK;
+  int32_t* csize;
+  uint8_t* isrep;
+  int32_t* ridx;
+  PRGB_TRY(tmp.alloc(&csize, n));
+  PRGB_TRY(tmp.alloc(&isrep, n));
+  PRGB_TRY(tmp.alloc(&ridx, (size_t)n + 1));
+  PRGB_CUDA(cudaMemsetAsync(csize, 0, (size_t)n * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  csize_k<<<grid1(n), kBlock, 0, s>>>(n, crep, P->level, csize, isrep, ctl);
+  PRGB_LAUNCH();
+  PRGB_TRY(scan_u8(isrep, ridx, n, tmp));
+  int32_t hK = 0, hmaxl = 0;
+  PRGB_CUDA(cudaMemcpyAsync(&hK, ridx + n, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaMemcpyAsync(&hmaxl, &ctl->cnt[5], 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  const int32_t K = hK, maxl = hmaxl, nlev = maxl + 1;
+  P->n_comp = K;
+  P->n_levels = nlev;
+  uint32_t *ck, *cv, *ckt, *cvt;
+  PRGB_TRY(tmp.alloc(&ck, K));
+  PRGB_TRY(tmp.alloc(&cv, K));
+  PRGB_TRY(tmp.alloc(&ckt, K));
+  PRGB_TRY(tmp.alloc(&cvt, K));
+  compact_reps_k<<<grid1(n), kBlock, 0, s>>>(n, isrep, ridx, csize, ck, cv);
+  PRGB_LAUNCH();
+  PRGB_TRY(radix_sort_pairs(ck, cv, ckt, cvt, K, bits_for((uint32_t)n), tmp));
+  level_keys_k<<<grid1(K), kBlock, 0, s>>>(K, cv, P->level, maxl, ck);
+  PRGB_LAUNCH();
+  PRGB_TRY(radix_sort_pairs(ck, cv, ckt, cvt, K, bits_for((uint32_t)maxl), tmp));
+  int32_t* comp_of_rep;
+  PRGB_TRY(tmp.alloc(&comp_of_rep, n));
+  comp_of_rep_k<<<grid1(K), kBlock, 0, s>>>(K, cv, comp_of_rep);
+  PRGB_LAUNCH();
+  // permutation by (component, wave desc, vertex)
+  uint32_t *vk, *vv, *vkt, *vvt;
+  PRGB_TRY(tmp.alloc(&vk, n));
+  PRGB_TRY(tmp.alloc(&vv, n));
+  PRGB_TRY(tmp.alloc(&vkt, n));
+  PRGB_TRY(tmp.alloc(&vvt, n));
+  vertex_comp_k<<<grid1(n), kBlock, 0, s>>>(n, crep, comp_of_rep, wave, max_wave, P->comp_id, vk, vv);
+  PRGB_LAUNCH();
+  PRGB_TRY(radix_sort_pairs(vk, vv, vkt, vvt, n, bits_for((uint32_t)max_wave), tmp));
+  comp_keys_k<<<grid1(n), kBlock, 0, s>>>(n, vv, P->comp_id, vk);
+  PRGB_LAUNCH();
+  PRGB_TRY(radix_sort_pairs(vk, vv, vkt, vvt, n, bits_for((uint32_t)(K - 1)), tmp));
+  int32_t* pos;
+  int32_t* c_level;
+  uint8_t* subflag;
+  int32_t* subidx;
+  PRGB_TRY(keep.alloc(&P->perm, n));
+  PRGB_TRY(keep.alloc(&P->p_outdeg, n));
+  PRGB_TRY(keep.alloc(&P->c_off, (size_t)K + 1));
+  PRGB_TRY(keep.alloc(&P->c_sub, (size_t)K + 1));
+  PRGB_TRY(keep.alloc(&P->c_type, K));
+  PRGB_TRY(tmp.alloc(&pos, n));
+  PRGB_TRY(tmp.alloc(&c_level, K));
+  PRGB_TRY(tmp.alloc(&subflag, n));
+  PRGB_TRY(tmp.alloc(&subidx, (size_t)n + 1));
+  perm_tables_k<<<grid1(n), kBlock, 0, s>>>(n, vv, P->comp_id, wave, g.outdeg, P->type, P->level, P->perm, pos,
+                                            P->p_outdeg, P->c_off, P->c_type, c_level, subflag);
+  PRGB_LAUNCH();
+  PRGB_CUDA(cudaMemcpyAsync(P->c_off + K, &n, 4, cudaMemcpyHostToDevice, s));
+  PRGB_TRY(scan_u8(subflag, subidx, n, tmp));
+  int32_t S = 0;
+  PRGB_CUDA(cudaMemcpyAsync(&S, subidx + n, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  P->n_sub = S;
+  PRGB_TRY(keep.alloc(&P->sub_ptr, (size_t)S + 1));
+  sub_tables_k<<<grid1(n), kBlock, 0, s>>>(n, K, subflag, subidx, P->c_off, P->sub_ptr, P->c_sub);
+  PRGB_LAUNCH();
+  PRGB_CUDA(cudaMemcpyAsync(P->sub_ptr + S, &n, 4, cudaMemcpyHostToDevice, s));
+  PRGB_CUDA(cudaMemcpyAsync(P->c_sub + K, &S, 4, cudaMemcpyHostToDevice, s));
+  // internal / external in-edges
+  int32_t *icnt, *ecnt;
+  PRGB_TRY(tmp.alloc(&icnt, n));
+  PRGB_TRY(tmp.alloc(&ecnt, n));
+  PRGB_TRY(keep.alloc(&P->int_ptr, (size_t)n + 1));
+  PRGB_TRY(keep.alloc(&P->ext_ptr, (size_t)n + 1));
+  edge_count_k<<<gridw(n), kBlock, 0, s>>>(n, P->perm, g.iptr, g.iidx, P->comp_id, icnt, ecnt);
+  PRGB_LAUNCH();
+  PRGB_TRY(scan_i32(icnt, P->int_ptr, n, tmp));
+  PRGB_TRY(scan_i32(ecnt, P->ext_ptr, n, tmp));
+  int32_t mi = 0, me = 0;
+  PRGB_CUDA(cudaMemcpyAsync(&mi, P->int_ptr + n, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaMemcpyAsync(&me, P->ext_ptr + n, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  P->m_int = mi;
+  P->m_ext = me;
+  PRGB_TRY(keep.alloc(&P->int_idx, (size_t)(mi > 0 ? mi : 1)));
+  PRGB_TRY(keep.alloc(&P->ext_idx, (size_t)(me > 0 ? me : 1)));
+  edge_fill_k<<<gridw(n), kBlock, 0, s>>>(n, P->perm, pos, g.iptr, g.iidx, P->comp_id, P->int_ptr, P->ext_ptr,
+                                          P->int_idx, P->ext_idx);
+  PRGB_LAUNCH();
+  // level ranges and size classes
+  int32_t *lvl_cbeg, *cls;
+  LevelRange* dlev;
+  PRGB_TRY(tmp.alloc(&lvl_cbeg, (size_t)nlev + 1));
+  PRGB_TRY(tmp.alloc(&cls, (size_t)nlev * 4));
+  PRGB_TRY(tmp.alloc(&dlev, nlev));
+  PRGB_CUDA(cudaMemsetAsync(lvl_cbeg, 0xff, ((size_t)nlev + 1) * 4, s));
+  level_begin_k<<<grid1(K), kBlock, 0, s>>>(K, c_level, maxl, lvl_cbeg);
+  PRGB_LAUNCH();
+  PRGB_CUDA(cudaMemcpyAsync(lvl_cbeg + nlev, &K, 4, cudaMemcpyHostToDevice, s));
+  PRGB_CUDA(cudaMemsetAsync(cls, 0x7f, (size_t)nlev * 16, s));
+  class_begin_k<<<grid1(K), kBlock, 0, s>>>(K, c_level, P->c_off, maxl, cls);
+  PRGB_LAUNCH();
+  level_ranges_k<<<grid1(nlev), kBlock, 0, s>>>(nlev, K, lvl_cbeg, cls, P->c_off, dlev);
+  PRGB_LAUNCH();
+  uint8_t* lflag;
+  int32_t* lidx;
+  PRGB_TRY(tmp.alloc(&lflag, K));
+  PRGB_TRY(tmp.alloc(&lidx, (size_t)K + 1));
+  large_flags_k<<<grid1(K), kBlock, 0, s>>>(K, P->c_off, lflag);
+  PRGB_LAUNCH();
+  PRGB_TRY(scan_u8(lflag, lidx, K, tmp));
+  int32_t nlarge = 0;
+  PRGB_CUDA(cudaMemcpyAsync(&nlarge, lidx + K, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaMemsetAsync(&ctl->cnt[3], 0, 8, s));
+  scc_count_k<<<grid1(K), kBlock, 0, s>>>(K, P->c_type, P->c_off, ctl);
+  PRGB_LAUNCH();
+  int32_t hs[2] = {0, 0};
+  PRGB_CUDA(cudaMemcpyAsync(hs, &ctl->cnt[3], 8, cudaMemcpyDeviceToHost, s));
+  P->levels.resize(nlev);
+  PRGB_CUDA(cudaMemcpyAsync(P->levels.data(), dlev, sizeof(LevelRange) * nlev, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  P->n_scc = hs[0];
+  P->n_scc_vertices = hs[1];
+  P->large.resize(nlarge);
+  P->max_large = 0;
+  if (nlarge > 0) {
+    LargeComp* dl;
+    PRGB_TRY(tmp.alloc(&dl, nlarge));
+    large_fill_k<<<grid1(K), kBlock, 0, s>>>(K, lflag, lidx, P->c_off, P->c_sub, P->c_type, c_level, maxl, dl);
+    PRGB_LAUNCH();
+    PRGB_CUDA(cudaMemcpyAsync(P->large.data(), dl, sizeof(LargeComp) * nlarge, cudaMemcpyDeviceToHost, s));
+    PRGB_CUDA(cudaStreamSynchronize(s));
+    for (const LargeComp& L : P->large) P->max_large = L.size > P->max_large ? L.size : P->max_large;
+  }
+  // host-side consistency checks of everything the solver will index with
+  int32_t prev_end = 0, prev_vend = 0;
+  for (int32_t li = 0; li < nlev; li++) {
+    const LevelRange& r = P->levels[li];
+    const bool ok = r.cbeg == prev_end && r.cbeg <= r.cta && r.cta <= r.warp && r.warp <= r.single &&
+                    r.single <= r.cend && r.cend <= K && r.cend > r.cbeg && r.vbeg == prev_vend &&
+                    r.vbeg <= r.vsingle && r.vsingle <= r.vend && r.vend <= n && r.vend - r.vsingle == r.cend - r.single;
+    if (!ok) return PR_EINTERNAL;
+    prev_end = r.cend;
+    prev_vend = r.vend;
+  }
+  if (prev_end != K || prev_vend != n) return PR_EINTERNAL;
+  int32_t prev_li = 0;
+  for (const LargeComp& L : P->large) {
+    if (L.c < 0 || L.c >= K || L.off < 0 || L.size <= kCtaCompMax || (int64_t)L.off + L.size > n ||
+        L.sub_begin < 0 || L.sub_begin >= L.sub_end || L.sub_end > S || L.level_idx < prev_li ||
+        L.level_idx >= nlev)
+      return PR_EINTERNAL;
+    const LevelRange& r = P->levels[L.level_idx];
+    if (L.c < r.cbeg || L.c >= r.cta) return PR_EINTERNAL;
+    prev_li = L.level_idx;
+  }
+  return PR_OK;
+}
+
+}  // namespace prgb

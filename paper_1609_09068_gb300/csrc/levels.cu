@@ -1,0 +1,285 @@
+// levels.cu -- levels (Def. 3.3) and the CAC merges of Theorem 3.1 on the
+// device.
+//
+// The DFS of Sec. 4.1 finishes a vertex after all its successors, and then:
+//   * an SCC (size >= 2) gets level 0 without external out-edges, else
+//     1 + the largest level among the components it points to;
+//   * a 1-vertex component v gets L = 1 + the largest level among the
+//     components it points to (0 for none).  If L > 0 and no component it
+//     points to at level L-1 is an SCC, v merges with all the CACs it points
+//     to at level L-1 and takes level L-1; otherwise it stays at level L.
+// A node's result depends only on its successors' final results, so the
+// same rule runs here in Kahn order on the condensation (sinks first), one
+// wave per longest-path step.  The successors' information is folded into
+// one integer per node with atomicMax: 2*level + (successor is an SCC).
+// The merges themselves are unions of v with its merge partners, done
+// afterwards with a lock-free union-find (hook the larger root under the
+// smaller), so a CAC's root is its smallest vertex.
+#include "common.cuh"
+
+namespace prgb {
+
+constexpr int kChunk = 256;  // in-edge entries per work item
+
+__device__ __forceinline__ int gwarp_l() { return (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+__device__ __forceinline__ int nwarps_l() { return (int)(((int64_t)gridDim.x * blockDim.x) >> 5); }
+
+__global__ void count_nodes_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx, int32_t n,
+                              const int32_t* __restrict__ rep, int32_t* nsize, int32_t* smin, int32_t* pending,
+                              int32_t* cin_cnt) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t u = gwarp_l(); u < n; u += nwarps_l()) {
+    const int U = rep[u];
+    if (lane == 0) {
+      atomicAdd(&nsize[U], 1);
+      atomicMin(&smin[U], (int)u);
+    }
+    int ext = 0;
+    for (int e = optr[u] + lane; e < optr[u + 1]; e += 32) {
+      const int W = rep[oidx[e]];
+      if (W != U) {
+        ext++;
+        atomicAdd(&cin_cnt[W], 1);
+      }
+    }
+    ext = (int)group_sum<32>((double)ext);
+    if (lane == 0 && ext) atomicAdd(&pending[U], ext);
+  }
+}
+
+__global__ void fill_cin_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx, int32_t n,
+                           const int32_t* __restrict__ rep, int32_t* cursor, int32_t* cin_src) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t u = gwarp_l(); u < n; u += nwarps_l()) {
+    const int U = rep[u];
+    for (int e = optr[u] + lane; e < optr[u + 1]; e += 32) {
+      const int W = rep[oidx[e]];
+      if (W != U) cin_src[atomicAdd(&cursor[W], 1)] = U;
+    }
+  }
+}
+
+// finalize node X: read the folded successor key, decide level and merge,
+// and queue X's in-edge chunks for the next wave
+__device__ void finalize_node(int X, int wave, const int32_t* nsize, int32_t* key, int32_t* level_node,
+                              int32_t* wave_node, uint8_t* merged, const int32_t* cin_ptr, int* fr_node,
+                              int* fr_chunk, int* counter, int cap, Ctl* ctl) {
+  __threadfence();
+  const int k = atomicAdd(&key[X], 0);
+  const bool scc = nsize[X] >= 2;
+  int lvl = 0, m = 0;
+  if (k >= 0) {
+    const int L = (k >> 1) + 1;
+    if (scc || (k & 1)) {
+      lvl = L;
+    } else {
+      lvl = L - 1;
+      m = 1;
+    }
+  }
+  level_node[X] = lvl;
+  wave_node[X] = wave;
+  merged[X] = (uint8_t)m;
+  const int len = cin_ptr[X + 1] - cin_ptr[X];
+  if (len > 0) {
+    const int nch = (len + kChunk - 1) / kChunk;
+    const int pos = atomicAdd(counter, nch);
+    if (pos + nch > cap) {
+      set_err(ctl, PR_EINTERNAL, 200);
+      return;
+    }
+    for (int j = 0; j < nch; j++) {
+      fr_node[pos + j] = X;
+      fr_chunk[pos + j] = j;
+    }
+  }
+}
+
+__global__ void kahn_k(int32_t n, const int32_t* __restrict__ rep, const int32_t* __restrict__ nsize,
+                       int32_t* pending, int32_t* key, int32_t* level_node, int32_t* wave_node, uint8_t* merged,
+                       const int32_t* __restrict__ cin_ptr, const int32_t* __restrict__ cin_src, int* fa_node,
+                       int* fa_chunk, int* fb_node, int* fb_chunk, int cap, Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int gw = gwarp_l(), nw = nwarps_l();
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (rep[v] == (int32_t)v && pending[v] == 0)
+      finalize_node((int)v, 0, nsize, key, level_node, wave_node, merged, cin_ptr, fa_node, fa_chunk,
+                    &ctl->cnt[0], cap, ctl);
+  }
+  if (!grid_sync(ctl, 210)) return;
+  for (int wave = 0;; wave++) {
+    int* cn = (wave & 1) ? fb_node : fa_node;
+    int* cc = (wave & 1) ? fb_chunk : fa_chunk;
+    int* nn = (wave & 1) ? fa_node : fb_node;
+    int* nc = (wave & 1) ? fa_chunk : fb_chunk;
+    const int ccur = wave % 3, cnxt = (wave + 1) % 3, cclr = (wave + 2) % 3;
+    const int cnt = vload(&ctl->cnt[ccur]);
+    if (cnt == 0) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[cclr] = 0;
+    for (int i = gw; i < cnt; i += nw) {
+      const int X = cn[i];
+      const int j = cc[i];
+      const int val = 2 * level_node[X] + (nsize[X] >= 2 ? 1 : 0);
+      const int b = cin_ptr[X] + j * kChunk;
+      const int e_end = min(cin_ptr[X + 1], b + kChunk);
+      for (int e = b + lane; e < e_end; e += 32) {
+        const int U = cin_src[e];
+        atomicMax(&key[U], val);
+        __threadfence();
+        if (atomicSub(&pending[U], 1) == 1)
+          finalize_node(U, wave + 1, nsize, key, level_node, wave_node, merged, cin_ptr, nn, nc,
+                        &ctl->cnt[cnxt], cap, ctl);
+      }
+    }
+    if (!grid_sync(ctl, 211)) return;
+  }
+}
+
+// lock-free union-find with parent[x] <= x (roots are the smallest ids)
+__device__ __forceinline__ int uf_find(int* par, int v) {
+  int cur = par[v];
+  if (cur != v) {
+    int next, prev = v;
+    while (cur > (next = par[cur])) {
+      par[prev] = next;
+      prev = cur;
+      cur = next;
+    }
+  }
+  return cur;
+}
+
+__device__ __forceinline__ void uf_union(int* par, int a, int b) {
+  int ra = uf_find(par, a), rb = uf_find(par, b);
+  for (int guard = 0; ra != rb && guard < (1 << 22); guard++) {
+    if (ra < rb) {
+      const int ret = atomicCAS(&par[rb], rb, ra);
+      if (ret == rb) break;
+      rb = ret;
+    } else {
+      const int ret = atomicCAS(&par[ra], ra, rb);
+      if (ret == ra) break;
+      ra = ret;
+    }
+  }
+}
+
+__global__ void merge_unions_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx, int32_t n,
+                               const int32_t* __restrict__ rep, const int32_t* __restrict__ nsize,
+                               const int32_t* __restrict__ level_node, const uint8_t* __restrict__ merged,
+                               int* par) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t v = gwarp_l(); v < n; v += nwarps_l()) {
+    if (!merged[v] || rep[v] != (int32_t)v || nsize[v] != 1) continue;
+    const int lv = level_node[v];
+    for (int e = optr[v] + lane; e < optr[v + 1]; e += 32) {
+      const int w = oidx[e];
+      const int W = rep[w];
+      if (nsize[W] == 1 && level_node[W] == lv) uf_union(par, (int)v, w);
+    }
+  }
+}
+
+__global__ void finish_vertices_k(int32_t n, const int32_t* __restrict__ rep, const int32_t* __restrict__ nsize,
+                                  const int32_t* __restrict__ smin, const int32_t* __restrict__ level_node,
+                                  const int32_t* __restrict__ wave_node, int* par, int32_t* crep,
+                                  int32_t* level, uint8_t* type, int32_t* wave, Ctl* ctl) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int X = rep[v];
+    const bool scc = nsize[X] >= 2;
+    crep[v] = scc ? smin[X] : uf_find(par, (int)v);
+    const int lv = level_node[X];
+    if (lv < 0) set_err(ctl, PR_EINTERNAL, 220);  // a node was never finalised
+    level[v] = lv;
+    type[v] = scc ? PR_TYPE_SCC : PR_TYPE_CAC;
+    wave[v] = wave_node[X];
+    atomicMax(&ctl->cnt[6], wave_node[X]);
+  }
+}
+
+__global__ void iota_i32_k(int* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int)i;
+}
+
+static unsigned grid_w(int64_t n) {  // one warp per item
+  int64_t g = (n * 32 + kBlock - 1) / kBlock;
+  int64_t cap = (int64_t)num_sms() * 16;
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+static unsigned grid_t(int64_t n) {  // one thread per item
+  int64_t g = (n + kBlock - 1) / kBlock;
+  int64_t cap = (int64_t)num_sms() * 16;
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+pr_status levels_and_merge(const DevGraph& g, const int32_t* rep, int32_t* crep, int32_t* level, uint8_t* type,
+                           int32_t* wave, int32_t* max_wave, Arena& tmp, Ctl* ctl) {
+  cudaStream_t s = tmp.stream();
+  const int32_t n = g.n;
+  *max_wave = 0;
+  if (n == 0) return PR_OK;
+  int32_t *nsize, *smin, *pending, *cin_cnt, *cin_ptr, *cursor, *cin_src, *key, *level_node, *wave_node, *par;
+  uint8_t* merged;
+  PRGB_TRY(tmp.alloc(&nsize, n));
+  PRGB_TRY(tmp.alloc(&smin, n));
+  PRGB_TRY(tmp.alloc(&pending, n));
+  PRGB_TRY(tmp.alloc(&cin_cnt, n));
+  PRGB_TRY(tmp.alloc(&cin_ptr, (size_t)n + 1));
+  PRGB_TRY(tmp.alloc(&cursor, (size_t)n + 1));
+  PRGB_TRY(tmp.alloc(&key, n));
+  PRGB_TRY(tmp.alloc(&level_node, n));
+  PRGB_TRY(tmp.alloc(&wave_node, n));
+  PRGB_TRY(tmp.alloc(&par, n));
+  PRGB_TRY(tmp.alloc(&merged, n));
+  PRGB_CUDA(cudaMemsetAsync(nsize, 0, (size_t)n * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(smin, 0x7f, (size_t)n * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(pending, 0, (size_t)n * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(cin_cnt, 0, (size_t)n * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(key, 0xff, (size_t)n * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(level_node, 0xff, (size_t)n * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(wave_node, 0xff, (size_t)n * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(merged, 0, (size_t)n, s));
+  count_nodes_k<<<grid_w(n), kBlock, 0, s>>>(g.optr, g.oidx, n, rep, nsize, smin, pending, cin_cnt);
+  PRGB_LAUNCH();
+  PRGB_TRY(scan_i32(cin_cnt, cin_ptr, n, tmp));
+  int32_t m_ext = 0;
+  PRGB_CUDA(cudaMemcpyAsync(&m_ext, cin_ptr + n, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  PRGB_TRY(tmp.alloc(&cin_src, (size_t)(m_ext > 0 ? m_ext : 1)));
+  PRGB_CUDA(cudaMemcpyAsync(cursor, cin_ptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, s));
+  fill_cin_k<<<grid_w(n), kBlock, 0, s>>>(g.optr, g.oidx, n, rep, cursor, cin_src);
+  PRGB_LAUNCH();
+  // frontier capacity: every node is queued once, in ceil(len/kChunk) items
+  const int cap = (int)((int64_t)n + (int64_t)m_ext / kChunk + 1);
+  int *fa_node, *fa_chunk, *fb_node, *fb_chunk;
+  PRGB_TRY(tmp.alloc(&fa_node, cap));
+  PRGB_TRY(tmp.alloc(&fa_chunk, cap));
+  PRGB_TRY(tmp.alloc(&fb_node, cap));
+  PRGB_TRY(tmp.alloc(&fb_chunk, cap));
+  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  {
+    int32_t nn = n;
+    int cp = cap;
+    void* args[] = {&nn, &rep, &nsize, &pending, &key, &level_node, &wave_node, &merged, &cin_ptr, &cin_src,
+                    &fa_node, &fa_chunk, &fb_node, &fb_chunk, &cp, &ctl};
+    PRGB_TRY(launch_coop((const void*)kahn_k, kBlock, 0, s, args, 4, nullptr));
+  }
+  iota_i32_k<<<grid_t(n), kBlock, 0, s>>>(par, n);
+  PRGB_LAUNCH();
+  merge_unions_k<<<grid_w(n), kBlock, 0, s>>>(g.optr, g.oidx, n, rep, nsize, level_node, merged, par);
+  PRGB_LAUNCH();
+  PRGB_CUDA(cudaMemsetAsync(&ctl->cnt[6], 0, sizeof(int), s));
+  finish_vertices_k<<<grid_t(n), kBlock, 0, s>>>(n, rep, nsize, smin, level_node, wave_node, par, crep, level,
+                                                 type, wave, ctl);
+  PRGB_LAUNCH();
+  int h[2] = {0, 0};
+  PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaMemcpyAsync(&h[1], &ctl->cnt[6], sizeof(int), cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  if (h[0]) return (pr_status)h[0];
+  *max_wave = h[1];
+  return PR_OK;
+}
+
+}  // namespace prgb

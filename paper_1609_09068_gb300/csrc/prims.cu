@@ -1,0 +1,263 @@
+// prims.cu -- scan, stable radix sort and launch helpers used by the
+// partitioner and the layout step (Sec. 4.2 notes that sorting by level and
+// size can be done without comparisons; a radix sort is that kind of sort).
+#include <mutex>
+
+#include "common.cuh"
+
+namespace prgb {
+
+static thread_local int g_last_cuda_error = 0;
+void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = static_cast<int>(e); }
+int last_cuda_error() { return g_last_cuda_error; }
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 1;
+  }
+  return cached[dev];
+}
+
+pr_status launch_coop(const void* kernel, int block, size_t smem, cudaStream_t s, void** args,
+                      int max_per_sm, int* grid_out) {
+  int per_sm = 0;
+  PRGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
+  if (per_sm <= 0) return PR_EINTERNAL;
+  if (max_per_sm > 0 && per_sm > max_per_sm) per_sm = max_per_sm;
+  const int grid = per_sm * num_sms();
+  if (grid_out) *grid_out = grid;
+  PRGB_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(block), args, smem, s));
+  return PR_OK;
+}
+
+int bits_for(uint32_t max_value) {
+  int b = 0;
+  while (b < 32 && (max_value >> b) != 0) b++;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan (out has n+1 entries): tile reduce, scan of tile sums,
+// tile scan with the tile offset.
+// ---------------------------------------------------------------------------
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kBlock * kScanItems;  // 4096
+
+template <typename T>
+__global__ void scan_reduce_k(const T* __restrict__ in, int64_t n, int32_t* __restrict__ tile_sums) {
+  __shared__ double sh[kBlock / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
+    if (i < n) s += (int32_t)in[i];
+  }
+  // integer reduce through the double helper is exact for |s| < 2^53
+  double t = block_sum((double)s, sh);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = (int32_t)t;
+}
+
+// single block: exclusive scan of tile sums in place
+__global__ void scan_tiles_k(int32_t* __restrict__ sums, int64_t ntiles) {
+  __shared__ int32_t sh[kBlock];
+  int32_t carry = 0;
+  for (int64_t b = 0; b < ntiles; b += kBlock) {
+    int64_t i = b + threadIdx.x;
+    int32_t v = (i < ntiles) ? sums[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < kBlock; o <<= 1) {
+      int32_t t = (threadIdx.x >= o) ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    int32_t incl = sh[threadIdx.x];
+    if (i < ntiles) sums[i] = carry + incl - v;
+    int32_t tot = sh[kBlock - 1];
+    __syncthreads();
+    carry += tot;
+  }
+}
+
+template <typename T>
+__global__ void scan_tile_k(const T* __restrict__ in, int64_t n, const int32_t* __restrict__ tile_off,
+                            int32_t* __restrict__ out) {
+  __shared__ int32_t sh[kBlock];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int32_t v[kScanItems];
+  int32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t i = base + k;
+    v[k] = (i < n) ? (int32_t)in[i] : 0;
+    s += v[k];
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < kBlock; o <<= 1) {
+    int32_t t = (threadIdx.x >= o) ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int32_t run = tile_off[blockIdx.x] + sh[threadIdx.x] - s;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t i = base + k;
+    run += v[k];
+    if (i < n) out[i + 1] = run;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+}
+
+template <typename T>
+static pr_status scan_impl(const T* in, int32_t* out, int64_t n, Arena& a) {
+  cudaStream_t s = a.stream();
+  if (n <= 0) {
+    PRGB_CUDA(cudaMemsetAsync(out, 0, sizeof(int32_t), s));
+    return PR_OK;
+  }
+  const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  int32_t* sums = nullptr;
+  PRGB_TRY(a.alloc(&sums, (size_t)ntiles));
+  scan_reduce_k<T><<<(unsigned)ntiles, kBlock, 0, s>>>(in, n, sums);
+  PRGB_LAUNCH();
+  scan_tiles_k<<<1, kBlock, 0, s>>>(sums, ntiles);
+  PRGB_LAUNCH();
+  scan_tile_k<T><<<(unsigned)ntiles, kBlock, 0, s>>>(in, n, sums, out);
+  PRGB_LAUNCH();
+  return PR_OK;
+}
+
+pr_status scan_i32(const int32_t* in, int32_t* out, int64_t n, Arena& a) { return scan_impl(in, out, n, a); }
+pr_status scan_u8(const uint8_t* in, int32_t* out, int64_t n, Arena& a) { return scan_impl(in, out, n, a); }
+
+__global__ void iota_k(uint32_t* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)i;
+}
+
+static unsigned grid_for(int64_t n, int block = kBlock) {
+  int64_t g = (n + block - 1) / block;
+  int64_t cap = (int64_t)num_sms() * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+pr_status iota_u32(uint32_t* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return PR_OK;
+  iota_k<<<grid_for(n), kBlock, 0, s>>>(out, n);
+  PRGB_LAUNCH();
+  return PR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort, 8 bits per pass.  A tile is 8 warps x 256 items;
+// warp w owns items [w*256, w*256+256) of the tile, processed in 8 rounds of
+// 32 consecutive items, so (warp, round, lane) is the input order and the
+// local rank below preserves it.
+// ---------------------------------------------------------------------------
+constexpr int kRadixWarps = 8;
+constexpr int kRadixRounds = 8;
+constexpr int kRadixTile = kRadixWarps * kRadixRounds * 32;  // 2048
+
+__global__ void radix_hist_k(const uint32_t* __restrict__ keys, int64_t n, int shift, int ntiles,
+                             int32_t* __restrict__ hist) {
+  __shared__ int32_t h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  for (int k = threadIdx.x; k < kRadixTile; k += blockDim.x) {
+    int64_t i = base + k;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+__global__ void radix_scatter_k(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                int shift, int ntiles, const int32_t* __restrict__ offs) {
+  __shared__ int32_t wcnt[kRadixWarps][256];
+  __shared__ int32_t base[256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) base[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+  __syncthreads();
+  const int64_t w0 = (int64_t)blockIdx.x * kRadixTile + warp * (kRadixRounds * 32);
+  uint32_t k[kRadixRounds], v[kRadixRounds];
+  int d[kRadixRounds];
+#pragma unroll
+  for (int r = 0; r < kRadixRounds; r++) {
+    const int64_t i = w0 + r * 32 + lane;
+    const bool ok = i < n;
+    k[r] = ok ? kin[i] : 0u;
+    v[r] = ok ? vin[i] : 0u;
+    d[r] = ok ? (int)((k[r] >> shift) & 255u) : 256 + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
+    if (ok && lane == __ffs(peers) - 1) wcnt[warp][d[r]] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int dd = threadIdx.x; dd < 256; dd += blockDim.x) {
+    int run = 0;
+    for (int w = 0; w < kRadixWarps; w++) {
+      int c = wcnt[w][dd];
+      wcnt[w][dd] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int r = 0; r < kRadixRounds; r++) {
+    const bool ok = d[r] < 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
+    if (ok) {
+      const int pos = base[d[r]] + wcnt[warp][d[r]] + __popc(peers & lt);
+      kout[pos] = k[r];
+      vout[pos] = v[r];
+    }
+    __syncwarp();
+    if (ok && lane == __ffs(peers) - 1) wcnt[warp][d[r]] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+pr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                           int64_t n, int key_bits, Arena& a) {
+  if (n <= 1 || key_bits <= 0) return PR_OK;
+  if (n >= (int64_t)1 << 31) return PR_EINVAL;
+  cudaStream_t s = a.stream();
+  const int ntiles = (int)((n + kRadixTile - 1) / kRadixTile);
+  int32_t *hist = nullptr, *offs = nullptr;
+  PRGB_TRY(a.alloc(&hist, (size_t)ntiles * 256));
+  PRGB_TRY(a.alloc(&offs, (size_t)ntiles * 256 + 1));
+  uint32_t *ka = keys, *va = vals, *kb = keys_tmp, *vb = vals_tmp;
+  for (int shift = 0; shift < key_bits; shift += 8) {
+    radix_hist_k<<<ntiles, kBlock, 0, s>>>(ka, n, shift, ntiles, hist);
+    PRGB_LAUNCH();
+    PRGB_TRY(scan_i32(hist, offs, (int64_t)ntiles * 256, a));
+    radix_scatter_k<<<ntiles, kRadixWarps * 32, 0, s>>>(ka, va, kb, vb, n, shift, ntiles, offs);
+    PRGB_LAUNCH();
+    uint32_t* t;
+    t = ka; ka = kb; kb = t;
+    t = va; va = vb; vb = t;
+  }
+  if (ka != keys) {
+    PRGB_CUDA(cudaMemcpyAsync(keys, ka, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    PRGB_CUDA(cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  return PR_OK;
+}
+
+}  // namespace prgb

@@ -1,0 +1,171 @@
+// scc.cu -- strongly connected components (Def. 3.1) on the device.
+//
+// The paper finds SCCs with a Tarjan DFS (Sec. 4.1), which is sequential.
+// Here: (1) trim -- repeatedly remove vertices with no remaining in- or
+// out-edge; each is a 1-vertex SCC (it lies on no cycle, Sec. 3 remark on
+// 1-vertex SCCs); (2) signature rounds on what is left: every vertex v gets
+// in(v) = largest id that reaches v and out(v) = largest id reachable from
+// v, both over the "alive" edges.  If in(v) == out(v) = m then m and v reach
+// each other, so v lies in the SCC of m, and m is that SCC's largest id.
+// Edges whose endpoints got different signatures cannot lie inside an SCC;
+// they die and the next round works inside the pieces that remain.  Every
+// round settles at least the SCC of each piece's largest vertex.
+//
+// Result: rep[v] = largest vertex id of v's SCC.
+#include "common.cuh"
+
+namespace prgb {
+
+__device__ __forceinline__ int gwarp() { return (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+__device__ __forceinline__ int nwarps() { return (int)(((int64_t)gridDim.x * blockDim.x) >> 5); }
+
+// ---- trim: Kahn peeling in both directions, one persistent launch ---------
+__global__ void trim_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx,
+                       const int32_t* __restrict__ iptr, const int32_t* __restrict__ iidx, int32_t n,
+                       int32_t* rem_out, int32_t* rem_in, int32_t* state, int32_t* rep, int32_t* fa,
+                       int32_t* fb, Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int gw = gwarp(), nw = nwarps();
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int ro = optr[v + 1] - optr[v], ri = iptr[v + 1] - iptr[v];
+    rem_out[v] = ro;
+    rem_in[v] = ri;
+    rep[v] = -1;
+    state[v] = (ro == 0 || ri == 0) ? 1 : 0;
+    if (ro == 0 || ri == 0) fa[atomicAdd(&ctl->cnt[0], 1)] = (int32_t)v;
+  }
+  if (!grid_sync(ctl, 100)) return;
+  for (int wave = 0;; wave++) {
+    int* cur = (wave & 1) ? fb : fa;
+    int* nxt = (wave & 1) ? fa : fb;
+    const int ccur = wave % 3, cnxt = (wave + 1) % 3, cclr = (wave + 2) % 3;
+    const int cnt = vload(&ctl->cnt[ccur]);
+    if (cnt == 0) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[cclr] = 0;
+    for (int i = gw; i < cnt; i += nw) {
+      const int v = cur[i];
+      if (lane == 0) rep[v] = v;
+      for (int e = optr[v] + lane; e < optr[v + 1]; e += 32) {
+        const int w = oidx[e];
+        if (atomicSub(&rem_in[w], 1) == 1 && atomicCAS(&state[w], 0, 1) == 0)
+          nxt[atomicAdd(&ctl->cnt[cnxt], 1)] = w;
+      }
+      for (int e = iptr[v] + lane; e < iptr[v + 1]; e += 32) {
+        const int u = iidx[e];
+        if (atomicSub(&rem_out[u], 1) == 1 && atomicCAS(&state[u], 0, 1) == 0)
+          nxt[atomicAdd(&ctl->cnt[cnxt], 1)] = u;
+      }
+    }
+    if (!grid_sync(ctl, 101)) return;
+  }
+}
+
+// ---- max-label propagation over alive edges, frontier driven --------------
+// dir 0: along out-edges (sig = largest id reaching v); dir 1: along in-edges.
+__global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
+                            const int32_t* __restrict__ rep, const int32_t* __restrict__ pin,
+                            const int32_t* __restrict__ pout, int32_t* sig, int32_t* stamp, int32_t* fa,
+                            int32_t* fb, Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int gw = gwarp(), nw = nwarps();
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    stamp[v] = -1;
+    if (rep[v] < 0) {
+      sig[v] = (int32_t)v;
+      fa[atomicAdd(&ctl->cnt[0], 1)] = (int32_t)v;
+    }
+  }
+  if (!grid_sync(ctl, 110)) return;
+  for (int wave = 0;; wave++) {
+    int* cur = (wave & 1) ? fb : fa;
+    int* nxt = (wave & 1) ? fa : fb;
+    const int ccur = wave % 3, cnxt = (wave + 1) % 3, cclr = (wave + 2) % 3;
+    const int cnt = vload(&ctl->cnt[ccur]);
+    if (cnt == 0) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[cclr] = 0;
+    for (int i = gw; i < cnt; i += nw) {
+      const int u = cur[i];
+      const int su = vload(&sig[u]);
+      const int a = pin[u], b = pout[u];
+      for (int e = ptr[u] + lane; e < ptr[u + 1]; e += 32) {
+        const int w = idx[e];
+        if (rep[w] >= 0 || pin[w] != a || pout[w] != b) continue;
+        if (vload(&sig[w]) >= su) continue;
+        const int old = atomicMax(&sig[w], su);
+        if (old < su && atomicExch(&stamp[w], wave) != wave) nxt[atomicAdd(&ctl->cnt[cnxt], 1)] = w;
+      }
+    }
+    if (!grid_sync(ctl, 111)) return;
+  }
+}
+
+__global__ void assign_k(int32_t n, int32_t* rep, int32_t* pin, int32_t* pout, const int32_t* sin,
+                         const int32_t* sout, Ctl* ctl) {
+  int left = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (rep[v] >= 0) continue;
+    if (sin[v] == sout[v]) {
+      rep[v] = sin[v];
+    } else {
+      pin[v] = sin[v];
+      pout[v] = sout[v];
+      left++;
+    }
+  }
+  if (left) atomicAdd(&ctl->cnt[7], left);
+}
+
+static unsigned grid_n(int64_t n) {
+  int64_t g = (n + kBlock - 1) / kBlock;
+  int64_t cap = (int64_t)num_sms() * 16;
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
+  cudaStream_t s = tmp.stream();
+  const int32_t n = g.n;
+  if (n == 0) return PR_OK;
+  int32_t *rem_out, *rem_in, *state, *fa, *fb, *sin, *sout, *pin, *pout, *stamp;
+  PRGB_TRY(tmp.alloc(&rem_out, n));
+  PRGB_TRY(tmp.alloc(&rem_in, n));
+  PRGB_TRY(tmp.alloc(&state, n));
+  PRGB_TRY(tmp.alloc(&fa, n));
+  PRGB_TRY(tmp.alloc(&fb, n));
+  PRGB_TRY(tmp.alloc(&sin, n));
+  PRGB_TRY(tmp.alloc(&sout, n));
+  PRGB_TRY(tmp.alloc(&pin, n));
+  PRGB_TRY(tmp.alloc(&pout, n));
+  PRGB_TRY(tmp.alloc(&stamp, n));
+  PRGB_CUDA(cudaMemsetAsync(pin, 0xff, (size_t)n * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(pout, 0xff, (size_t)n * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  {
+    DevGraph gg = g;
+    int32_t nn = n;
+    void* args[] = {&gg.optr, &gg.oidx, &gg.iptr, &gg.iidx, &nn, &rem_out, &rem_in, &state, &rep, &fa, &fb, &ctl};
+    PRGB_TRY(launch_coop((const void*)trim_k, kBlock, 0, s, args, 4, nullptr));
+  }
+  for (int round = 0; round < 20000; round++) {
+    for (int dir = 0; dir < 2; dir++) {
+      PRGB_TRY(reset_ctl(ctl, s));
+      const int32_t* ptr = dir == 0 ? g.optr : g.iptr;
+      const int32_t* idx = dir == 0 ? g.oidx : g.iidx;
+      int32_t* sig = dir == 0 ? sin : sout;
+      int32_t nn = n;
+      void* args[] = {&ptr, &idx, &nn, &rep, &pin, &pout, &sig, &stamp, &fa, &fb, &ctl};
+      PRGB_TRY(launch_coop((const void*)propagate_k, kBlock, 0, s, args, 4, nullptr));
+    }
+    PRGB_CUDA(cudaMemsetAsync(&ctl->cnt[7], 0, sizeof(int), s));
+    assign_k<<<grid_n(n), kBlock, 0, s>>>(n, rep, pin, pout, sin, sout, ctl);
+    PRGB_LAUNCH();
+    int h[2] = {0, 0};
+    PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PRGB_CUDA(cudaMemcpyAsync(&h[1], &ctl->cnt[7], sizeof(int), cudaMemcpyDeviceToHost, s));
+    PRGB_CUDA(cudaStreamSynchronize(s));
+    if (h[0]) return (pr_status)h[0];
+    if (h[1] == 0) return PR_OK;
+  }
+  return PR_EINTERNAL;
+}
+
+}  // namespace prgb

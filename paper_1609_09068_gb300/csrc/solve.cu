@@ -1,0 +1,471 @@
+// solve.cu -- the PageRank step of Sec. 4.3 on the permuted layout.
+//
+// Levels run from the highest down (Sec. 4.3 steps 1-4).  Inside a level all
+// components are independent and run concurrently (Sec. 4.3 last paragraph):
+//   * 1-vertex components (Sec. 4.3 item 1, loops ignored): R = W;
+//   * CACs (item 2, Sec. 4.3.1): one pass in topological order, sub-level by
+//     sub-level: R_v = W_v + c * sum_{j->v inside} R_j / outdeg(j);
+//   * SCCs (item 4, Sec. 4.3.2): power series P_0 = W, P_{k+1} = c A^T P_k,
+//     R = sum_k P_k, stopping after adding P with ||P||_1 <= tol*|C|/n (or the
+//     paper's max(P) < tol).
+// The weight update of Eq. (PR:levels) is done as a pull: every vertex of a
+// level gathers W_v = u_v + c * sum over external in-edges of R_j/outdeg(j)
+// from levels already solved, fused into the kernel that solves it.
+//
+// Kernel classes by component size: one warp (<= 32 vertices, one vertex per
+// lane, z in shared memory), one CTA (<= 2048 vertices, z in shared memory),
+// and grid-wide cooperative kernels with bounded grid barriers for the rest.
+// z = R/outdeg (or P/outdeg during the series) is the only per-vertex vector
+// gathered: A_ij = 1/outdeg(i) depends on the source only, so no edge values
+// are stored.
+#include "common.cuh"
+#include "solve.cuh"
+
+namespace prgb {
+
+__device__ __forceinline__ double zdiv(double x, int deg) { return deg > 0 ? x / (double)deg : 0.0; }
+
+__device__ __forceinline__ bool keep_going(double s, double tau, int norm) {
+  return norm == PR_NORM_LINF ? (s >= tau) : (s > tau);
+}
+
+// A local index outside [0, sz) would mean a broken layout: record it and
+// read slot 0 instead of touching memory out of bounds.
+__device__ __forceinline__ int local_or_err(const SolveArgs& a, int q, int sz) {
+  if ((unsigned)q >= (unsigned)sz) {
+    set_err(a.ctl, PR_EINTERNAL, 301);
+    return 0;
+  }
+  return q;
+}
+
+__device__ __forceinline__ double check_u(const SolveArgs& a, double uu) {
+  if (!(uu >= 0.0) || !isfinite(uu)) set_err(a.ctl, PR_EINVAL, 300);
+  return uu;
+}
+
+// ---------------------------------------------------------------------------
+// one warp per component of 2..32 vertices
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) solve_warp_k(SolveArgs a, int32_t cbeg, int32_t cend) {
+  __shared__ double zsh[kBlock / 32][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int c = cbeg + (int)blockIdx.x * (kBlock / 32) + wib;
+  if (c >= cend) return;  // warp-uniform
+  double* z = zsh[wib];
+  const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
+  const bool act = lane < sz;
+  const int p = off + lane;
+  const int deg = act ? a.p_outdeg[p] : 0;
+  double W = 0.0;
+  if (act) {
+    double g = 0.0;
+    for (int e = a.ext_ptr[p]; e < a.ext_ptr[p + 1]; e++) g += a.zr[a.ext_idx[e]];
+    W = check_u(a, a.u[a.perm[p]]) + a.c * g;
+  }
+  const int ib = act ? a.int_ptr[p] : 0, ie = act ? a.int_ptr[p + 1] : 0;
+  double R = W;
+  int k = 0;
+  if (a.c_type[c] == PR_TYPE_CAC) {
+    const int sb = a.c_sub[c], se = a.c_sub[c + 1];
+    for (int s = sb; s < se; s++) {
+      const int lo = a.sub_ptr[s], hi = a.sub_ptr[s + 1];
+      if (act && p >= lo && p < hi) {
+        double acc = 0.0;
+        for (int e = ib; e < ie; e++) acc += z[local_or_err(a, a.int_idx[e] - off, sz)];
+        R = W + a.c * acc;
+        z[lane] = zdiv(R, deg);
+      }
+      __syncwarp();
+    }
+  } else {
+    const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
+    const int fixed = a.replay ? a.replay[c] : -1;
+    if (act) z[lane] = zdiv(W, deg);
+    __syncwarp();
+    for (;;) {
+      double acc = 0.0;
+      for (int e = ib; e < ie; e++) acc += z[local_or_err(a, a.int_idx[e] - off, sz)];
+      const double pn = a.c * acc;
+      __syncwarp();
+      if (act) {
+        z[lane] = zdiv(pn, deg);
+        R += pn;
+      }
+      __syncwarp();
+      k++;
+      if (fixed >= 0) {
+        if (k >= fixed) break;
+        continue;
+      }
+      const double s = a.norm == PR_NORM_L1 ? group_sum<32>(pn) : group_max<32>(pn);
+      if (!keep_going(s, tau, a.norm)) break;
+      if (k >= a.max_iter) {
+        if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
+        break;
+      }
+    }
+  }
+  if (act) {
+    a.R[p] = R;
+    a.zr[p] = zdiv(R, deg);
+  }
+  if (lane == 0) a.iters[c] = k;
+}
+
+// ---------------------------------------------------------------------------
+// one CTA per component of 33..kCtaCompMax vertices
+// ---------------------------------------------------------------------------
+constexpr int kRpt = kCtaCompMax / kBlock;  // rows per thread
+
+__global__ void __launch_bounds__(kBlock) solve_cta_k(SolveArgs a, int32_t cbeg) {
+  __shared__ double z[kCtaCompMax];
+  __shared__ double red[kBlock / 32];
+  const int c = cbeg + (int)blockIdx.x;
+  const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
+  double W[kRpt], Rr[kRpt];
+  int deg[kRpt];
+#pragma unroll
+  for (int r = 0; r < kRpt; r++) {
+    const int i = threadIdx.x + r * kBlock;
+    W[r] = 0.0;
+    deg[r] = 0;
+    if (i < sz) {
+      const int p = off + i;
+      deg[r] = a.p_outdeg[p];
+      double g = 0.0;
+      for (int e = a.ext_ptr[p]; e < a.ext_ptr[p + 1]; e++) g += a.zr[a.ext_idx[e]];
+      W[r] = check_u(a, a.u[a.perm[p]]) + a.c * g;
+    }
+    Rr[r] = W[r];
+  }
+  int k = 0;
+  if (a.c_type[c] == PR_TYPE_CAC) {
+    const int sb = a.c_sub[c], se = a.c_sub[c + 1];
+    for (int s = sb; s < se; s++) {
+      const int lo = a.sub_ptr[s] - off, hi = a.sub_ptr[s + 1] - off;
+#pragma unroll
+      for (int r = 0; r < kRpt; r++) {
+        const int i = threadIdx.x + r * kBlock;
+        if (i >= lo && i < hi) {
+          const int p = off + i;
+          double acc = 0.0;
+          for (int e = a.int_ptr[p]; e < a.int_ptr[p + 1]; e++) acc += z[local_or_err(a, a.int_idx[e] - off, sz)];
+          Rr[r] = W[r] + a.c * acc;
+          z[i] = zdiv(Rr[r], deg[r]);
+        }
+      }
+      __syncthreads();
+    }
+  } else {
+    const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
+    const int fixed = a.replay ? a.replay[c] : -1;
+#pragma unroll
+    for (int r = 0; r < kRpt; r++) {
+      const int i = threadIdx.x + r * kBlock;
+      if (i < sz) z[i] = zdiv(W[r], deg[r]);
+    }
+    __syncthreads();
+    for (;;) {
+      double pn[kRpt];
+      double local = 0.0;
+#pragma unroll
+      for (int r = 0; r < kRpt; r++) {
+        const int i = threadIdx.x + r * kBlock;
+        pn[r] = 0.0;
+        if (i < sz) {
+          const int p = off + i;
+          double acc = 0.0;
+          for (int e = a.int_ptr[p]; e < a.int_ptr[p + 1]; e++) acc += z[local_or_err(a, a.int_idx[e] - off, sz)];
+          pn[r] = a.c * acc;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < kRpt; r++) {
+        const int i = threadIdx.x + r * kBlock;
+        if (i < sz) {
+          z[i] = zdiv(pn[r], deg[r]);
+          Rr[r] += pn[r];
+          local = a.norm == PR_NORM_L1 ? local + pn[r] : fmax(local, pn[r]);
+        }
+      }
+      // block_sum / block_max end with __syncthreads, which also publishes z
+      const double s = a.norm == PR_NORM_L1 ? block_sum(local, red) : block_max(local, red);
+      k++;
+      if (fixed >= 0) {
+        if (k >= fixed) break;
+        continue;
+      }
+      if (!keep_going(s, tau, a.norm)) break;
+      if (k >= a.max_iter) {
+        if (threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
+        break;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRpt; r++) {
+    const int i = threadIdx.x + r * kBlock;
+    if (i < sz) {
+      a.R[off + i] = Rr[r];
+      a.zr[off + i] = zdiv(Rr[r], deg[r]);
+    }
+  }
+  if (threadIdx.x == 0) a.iters[c] = k;
+}
+
+// ---------------------------------------------------------------------------
+// collection of 1-vertex components of a level: R = W (8 lanes per vertex)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) solve_single_k(SolveArgs a, int32_t vbeg, int32_t vend) {
+  const int lane8 = threadIdx.x & 7;
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  const int64_t wb = g0 - ((threadIdx.x & 31) >> 3);  // first group of this warp
+  for (int64_t base = wb; base + vbeg < vend; base += ng) {
+    const int64_t p = vbeg + base + ((threadIdx.x & 31) >> 3);
+    double acc = 0.0;
+    if (p < vend)
+      for (int e = a.ext_ptr[p] + lane8; e < a.ext_ptr[p + 1]; e += 8) acc += a.zr[a.ext_idx[e]];
+    acc = group_sum<8>(acc);
+    if (p < vend && lane8 == 0) {
+      const double W = check_u(a, a.u[a.perm[p]]) + a.c * acc;
+      a.R[p] = W;
+      a.zr[p] = zdiv(W, a.p_outdeg[p]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// grid-wide kernels for large components (cooperative launch)
+// ---------------------------------------------------------------------------
+constexpr int kG = 8;  // lanes per row
+
+// gather W for the rows of a component; R[p] = W and z0[p - off] = W/outdeg
+__device__ __forceinline__ void gather_rows(const SolveArgs& a, int off, int sz, double* z0) {
+  const int lane = threadIdx.x & (kG - 1);
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kG;
+  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / kG;
+  const int64_t wb = g0 - ((threadIdx.x & 31) / kG);
+  for (int64_t base = wb; base < sz; base += ng) {
+    const int64_t i = base + ((threadIdx.x & 31) / kG);
+    const int p = off + (int)i;
+    double acc = 0.0;
+    if (i < sz)
+      for (int e = a.ext_ptr[p] + lane; e < a.ext_ptr[p + 1]; e += kG) acc += a.zr[a.ext_idx[e]];
+    acc = group_sum<kG>(acc);
+    if (i < sz && lane == 0) {
+      const double W = check_u(a, a.u[a.perm[p]]) + a.c * acc;
+      a.R[p] = W;
+      if (z0) z0[i] = zdiv(W, a.p_outdeg[p]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeComp L, double* zA, double* zB,
+                                                            double* part) {
+  __shared__ double red[kBlock / 32];
+  const int off = L.off, sz = L.size;
+  gather_rows(a, off, sz, zA);
+  if (!grid_sync(a.ctl, 310)) return;
+  const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
+  const int fixed = a.replay ? a.replay[L.c] : -1;
+  const int lane = threadIdx.x & (kG - 1);
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kG;
+  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / kG;
+  const int64_t wb = g0 - ((threadIdx.x & 31) / kG);
+  int k = 0;
+  for (;;) {
+    const double* cur = (k & 1) ? zB : zA;
+    double* nxt = (k & 1) ? zA : zB;
+    double local = 0.0;
+    for (int64_t base = wb; base < sz; base += ng) {
+      const int64_t i = base + ((threadIdx.x & 31) / kG);
+      const int p = off + (int)i;
+      double acc = 0.0;
+      if (i < sz)
+        for (int e = a.int_ptr[p] + lane; e < a.int_ptr[p + 1]; e += kG)
+          acc += cur[local_or_err(a, a.int_idx[e] - off, sz)];
+      acc = group_sum<kG>(acc);
+      if (i < sz && lane == 0) {
+        const double pn = a.c * acc;
+        a.R[p] += pn;
+        nxt[i] = zdiv(pn, a.p_outdeg[p]);
+        local = a.norm == PR_NORM_L1 ? local + pn : fmax(local, pn);
+      }
+    }
+    const double bs = a.norm == PR_NORM_L1 ? block_sum(local, red) : block_max(local, red);
+    double* slot = part + (size_t)(k & 1) * gridDim.x;
+    if (threadIdx.x == 0) slot[blockIdx.x] = bs;
+    if (!grid_sync(a.ctl, 311)) return;
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      t = a.norm == PR_NORM_L1 ? t + slot[b] : fmax(t, slot[b]);
+    const double s = a.norm == PR_NORM_L1 ? block_sum(t, red) : block_max(t, red);
+    k++;
+    if (fixed >= 0) {
+      if (k >= fixed) break;
+      continue;
+    }
+    if (!keep_going(s, tau, a.norm)) break;
+    if (k >= a.max_iter) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
+      break;
+    }
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x)
+    a.zr[off + i] = zdiv(a.R[off + i], a.p_outdeg[off + i]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.iters[L.c] = k;
+}
+
+__global__ void __launch_bounds__(kBlock) solve_large_cac_k(SolveArgs a, LargeComp L) {
+  gather_rows(a, L.off, L.size, nullptr);  // R[p] = W
+  if (!grid_sync(a.ctl, 320)) return;
+  const int lane = threadIdx.x & (kG - 1);
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kG;
+  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / kG;
+  const int64_t wb = g0 - ((threadIdx.x & 31) / kG);
+  for (int s = L.sub_begin; s < L.sub_end; s++) {
+    const int lo = a.sub_ptr[s], hi = a.sub_ptr[s + 1];
+    for (int64_t base = wb; base < hi - lo; base += ng) {
+      const int64_t i = base + ((threadIdx.x & 31) / kG);
+      const int p = lo + (int)i;
+      double acc = 0.0;
+      if (p < hi)
+        for (int e = a.int_ptr[p] + lane; e < a.int_ptr[p + 1]; e += kG) acc += a.zr[a.int_idx[e]];
+      acc = group_sum<kG>(acc);
+      if (p < hi && lane == 0) {
+        const double Rv = a.R[p] + a.c * acc;
+        a.R[p] = Rv;
+        a.zr[p] = zdiv(Rv, a.p_outdeg[p]);
+      }
+    }
+    if (!grid_sync(a.ctl, 321)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.iters[L.c] = 0;
+}
+
+__global__ void scatter_out_k(int32_t n, const int32_t* perm, const double* Rp, double* R) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    R[perm[p]] = Rp[p];
+}
+
+// edge reads of the solve: ext edges once, CAC internal edges once, SCC
+// internal edges once per iteration
+__global__ void edge_visits_k(int32_t K, const int32_t* c_off, const uint8_t* c_type, const int32_t* int_ptr,
+                              const int32_t* ext_ptr, const int32_t* iters, unsigned long long* out) {
+  unsigned long long loc = 0;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < K; c += (int64_t)gridDim.x * blockDim.x) {
+    const int b = c_off[c], e = c_off[c + 1];
+    const long long mi = int_ptr[e] - int_ptr[b], me = ext_ptr[e] - ext_ptr[b];
+    loc += (unsigned long long)(me + (c_type[c] == PR_TYPE_SCC ? mi * (long long)iters[c] : mi));
+  }
+  atomicAdd(out, loc);
+}
+
+}  // namespace prgb
+
+namespace prgb {
+
+static unsigned grid_cap(int64_t blocks) {
+  int64_t cap = (int64_t)num_sms() * 32;
+  return (unsigned)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+}
+
+pr_status run_solve(const pr_partition_s* P, double c, const double* u, double tol, int norm, int max_iter,
+                    const int32_t* replay, double* R, int32_t* iters_dev, Arena& tmp, Ctl* ctl,
+                    int64_t* launches) {
+  cudaStream_t s = tmp.stream();
+  const int32_t n = P->g.n;
+  int64_t nl = 0;
+  if (n == 0) {
+    *launches = 0;
+    return PR_OK;
+  }
+  SolveArgs a;
+  a.n = n;
+  a.c = c;
+  a.tol = tol;
+  a.norm = norm;
+  a.max_iter = max_iter;
+  a.u = u;
+  a.perm = P->perm;
+  a.p_outdeg = P->p_outdeg;
+  a.int_ptr = P->int_ptr;
+  a.int_idx = P->int_idx;
+  a.ext_ptr = P->ext_ptr;
+  a.ext_idx = P->ext_idx;
+  a.c_off = P->c_off;
+  a.c_sub = P->c_sub;
+  a.sub_ptr = P->sub_ptr;
+  a.c_type = P->c_type;
+  a.replay = replay;
+  a.iters = iters_dev;
+  a.ctl = ctl;
+  PRGB_TRY(tmp.alloc(&a.R, n));
+  PRGB_TRY(tmp.alloc(&a.zr, n));
+  double *zA = nullptr, *zB = nullptr, *part = nullptr;
+  if (P->max_large > 0) {
+    PRGB_TRY(tmp.alloc(&zA, P->max_large));
+    PRGB_TRY(tmp.alloc(&zB, P->max_large));
+    PRGB_TRY(tmp.alloc(&part, (size_t)2 * num_sms() * 8));
+  }
+  size_t li_large = 0;
+  for (size_t li = 0; li < P->levels.size(); li++) {
+    const LevelRange& r = P->levels[li];
+    while (li_large < P->large.size() && P->large[li_large].level_idx == (int)li) {
+      LargeComp L = P->large[li_large++];
+      PRGB_TRY(reset_ctl(ctl, s));
+      if (L.type == PR_TYPE_SCC) {
+        void* args[] = {&a, &L, &zA, &zB, &part};
+        PRGB_TRY(launch_coop((const void*)solve_large_scc_k, kBlock, 0, s, args, 4, nullptr));
+      } else {
+        void* args[] = {&a, &L};
+        PRGB_TRY(launch_coop((const void*)solve_large_cac_k, kBlock, 0, s, args, 4, nullptr));
+      }
+      nl++;
+    }
+    if (r.warp > r.cta) {
+      solve_cta_k<<<r.warp - r.cta, kBlock, 0, s>>>(a, r.cta);
+      PRGB_LAUNCH();
+      nl++;
+    }
+    if (r.single > r.warp) {
+      const int nw = r.single - r.warp;
+      solve_warp_k<<<(nw + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(a, r.warp, r.single);
+      PRGB_LAUNCH();
+      nl++;
+    }
+    if (r.vend > r.vsingle) {
+      const int64_t nv = r.vend - r.vsingle;
+      solve_single_k<<<grid_cap((nv * 8 + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, r.vsingle, r.vend);
+      PRGB_LAUNCH();
+      nl++;
+    }
+  }
+  scatter_out_k<<<grid_cap((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, P->perm, a.R, R);
+  PRGB_LAUNCH();
+  nl++;
+  *launches = nl;
+  return PR_OK;
+}
+
+pr_status solve_edge_visits(const pr_partition_s* P, const int32_t* iters_dev, int64_t* out, Arena& tmp) {
+  cudaStream_t s = tmp.stream();
+  *out = 0;
+  if (P->n_comp == 0) return PR_OK;
+  unsigned long long* d = nullptr;
+  PRGB_TRY(tmp.alloc(&d, 1));
+  PRGB_CUDA(cudaMemsetAsync(d, 0, 8, s));
+  edge_visits_k<<<grid_cap((P->n_comp + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+      P->n_comp, P->c_off, P->c_type, P->int_ptr, P->ext_ptr, iters_dev, d);
+  PRGB_LAUNCH();
+  unsigned long long h = 0;
+  PRGB_CUDA(cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  *out = (int64_t)h;
+  return PR_OK;
+}
+
+}  // namespace prgb
