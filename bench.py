@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Benchmark of the componentwise PageRank hot path on GB300.
+
+One step = the whole path on one synthetic graph already resident in HBM:
+prepare the graph (validate, drop loops, CSC), partition it into SCCs/CACs
+with levels and lay it out, solve level by level to an L1 residual budget of
+1e-10, and check the residual.  The global power series (the paper's
+baseline) is timed the same way in a second loop.
+
+value = graph edges / time per step (GTEPS: edges of the input solved to
+residual 1e-10 per second), summed over ranks.  Each rank solves its own
+replica (independent problems, no collective on the data path).
+
+--impl reference times the CPU oracle (the plain C implementation the tests
+use) on the machine's host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "componentwise PageRank GTEPS & time-to-1e-10 vs global power iter, 1 GB300"
+UNIT = "GTEPS"
+C = 0.85
+TOL = 1e-10
+FLUSH_BYTES = 256 << 20
+
+WORKLOADS = {
+    "web": ("web_like: n=1,000,000, mean out-degree 8, Zipf(2.1) degrees, giant SCC 40%, "
+            "~18k small log-normal SCCs, CAC trees/chains, 15% dangling, 28 layers, u=1/n, "
+            "c=0.85, L1 tol 1e-10, FP64"),
+    "small": ("small_planted: n=10,000, ~50k edges, 200 SCCs, 2,000 acyclic, 10 layers, "
+              "u=1/n, c=0.85, L1 tol 1e-10, FP64"),
+    "deep": ("deep_dag: n=4,000,000, ~28M edges, 200 forced levels, 200-400 SCCs per level, "
+             "CAC chains 1-50, u~U[0,1] normalised, c=0.85, L1 tol 1e-10, FP64"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="web")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--breakdown", action="store_true", help="print per-phase times to stderr")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+def oracle_step(g):
+    import oracle
+    t0 = time.perf_counter()
+    q = oracle.partition(g.rowptr, g.col)
+    oracle.solve_cw(g.rowptr, g.col, q, C, g.u, TOL)
+    return time.perf_counter() - t0
+
+
+def reference_sample(args):
+    """The workload itself when K+W oracle steps fit in ~3 minutes, else the
+    same generator at a proportionally smaller n (same shape)."""
+    g = gg.config(args.workload)
+    t = oracle_step(g)  # also the first warm-up step
+    budget = 180.0
+    if (args.steps + args.warmup) * t <= budget or args.workload == "small":
+        return g, t, "full workload"
+    scale = budget / ((args.steps + args.warmup) * t)
+    n = max(10_000, int(g.n * scale))
+    if args.workload == "web":
+        g2 = gg.web_like(n=n, n_small=max(100, int(20_000 * n / 1_000_000)))
+    else:
+        g2 = gg.deep_dag(n=n, levels=max(10, int(200 * min(1.0, n / 4_000_000))))
+    return g2, None, f"same generator at n={n} (bounded sample)"
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    g, first, sample = reference_sample(args)
+    for _ in range(max(0, args.warmup - (1 if first is not None else 0))):
+        oracle_step(g)
+    times = [oracle_step(g) for _ in range(args.steps)]
+    t = sum(times) / len(times)
+    value = g.nnz / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "n": g.n, "nnz": g.nnz, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample}: oracle partition + componentwise solve, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1609_09068_gb300 as prgb
+    from paper_1609_09068_gb300 import _build
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if not _build.up_to_date():
+        _build.build()
+    prgb.load_library()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    g = gg.config(args.workload)
+    E = g.nnz
+    rowptr = torch.from_numpy(g.rowptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    u = torch.from_numpy(g.u).cuda()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def cw_step():
+        e = [ev() for _ in range(5)]
+        e[0].record()
+        G = prgb.graph(rowptr, col)
+        e[1].record()
+        P = prgb.partition(G)
+        e[2].record()
+        R, st = prgb.solve(P, C, u, TOL, with_stats=True, timing=True)
+        e[3].record()
+        res = prgb.residual_l1(G, C, u, R)
+        e[4].record()
+        return e, st, res, P
+
+    def global_step():
+        e = [ev() for _ in range(4)]
+        e[0].record()
+        G = prgb.graph(rowptr, col)
+        e[1].record()
+        R, k, st = prgb.global_power(G, C, u, TOL, with_stats=True, timing=True)
+        e[2].record()
+        res = prgb.residual_l1(G, C, u, R)
+        e[3].record()
+        return e, st, res, k
+
+    for _ in range(args.warmup):
+        cw_step()
+        global_step()
+    torch.cuda.synchronize()
+
+    # ---- componentwise: the timed region -----------------------------------
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = prgb.launch_count()
+    recs = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # 256 MiB write: the graph leaves L2 before each step
+        recs.append(cw_step())
+    torch.cuda.synchronize()
+    barrier()
+    launches = prgb.launch_count() - l0
+    clk = clocks.stop()
+    phase = np.array([[recs[i][0][j].elapsed_time(recs[i][0][j + 1]) for j in range(4)]
+                      for i in range(args.steps)])
+    t_step = max_over_ranks(float(phase.sum(axis=1).mean()))
+    stats = [r[1] for r in recs]
+    residual = max(r[2] for r in recs)
+    P = recs[-1][3]
+    value = world * E / (t_step * 1e-3) / 1e9
+
+    # ---- global power series on the same GPU --------------------------------
+    grecs = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        grecs.append(global_step())
+    torch.cuda.synchronize()
+    gph = np.array([[grecs[i][0][j].elapsed_time(grecs[i][0][j + 1]) for j in range(3)]
+                    for i in range(args.steps)])
+    t_global = max_over_ranks(float(gph.sum(axis=1).mean()))
+    t_global_solve = float(gph[:, 1].mean())
+    g_iters = grecs[-1][3]
+    g_res = max(r[2] for r in grecs)
+    gk_ms = float(np.mean([r[1]["kernel_ms"] for r in grecs]))
+    gk_bytes = float(np.mean([r[1]["kernel_bytes"] for r in grecs]))
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    rp_h = torch.from_numpy(g.rowptr).pin_memory().numpy()
+    col_h = torch.from_numpy(g.col).pin_memory().numpy()
+    u_h = torch.from_numpy(g.u).pin_memory().numpy()
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, b = ev(), ev()
+        a.record()
+        Gh = prgb.graph(rp_h, col_h, on_host=True)
+        Ph = prgb.partition(Gh)
+        Rh = prgb.solve(Ph, C, u_h, TOL)
+        b.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+        assert isinstance(Rh, np.ndarray)
+    t_e2e = max_over_ranks(float(np.mean(e2e_ms)))
+    h2d = g.rowptr.nbytes + g.col.nbytes + g.u.nbytes
+    d2h = g.u.nbytes
+
+    # ---- roofline of the dominant SpMV kernel --------------------------------
+    peaks, peak_kind = measured_peaks()
+    k_ms = float(np.mean([s["kernel_ms"] for s in stats]))
+    k_bytes = float(np.mean([s["kernel_bytes"] for s in stats]))
+    achieved = k_bytes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "solve_large_scc_k (grid-wide SCC power series)",
+                "peak_kind": f"{peak_kind} copy bandwidth", "kernel_ms_per_step": k_ms,
+                "algorithmic_bytes_per_step": k_bytes,
+                "launches_per_step": float(np.mean([s["kernel_launches"] for s in stats]))}
+
+    # ---- CPU oracle on the host cores ---------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t_cpu = oracle_step(g)
+        cpu = {"value": E / t_cpu / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one full step of the same workload: oracle partition (Tarjan DFS) + "
+                         f"componentwise solve, single thread, {t_cpu:.1f} s"}
+
+    ph = phase.mean(axis=0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "n": g.n, "nnz": E, "c": C, "tol": TOL,
+                   "norm": "L1", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed before each step by a 256 MiB device write outside the timed events"},
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+        "e2e": {"value": world * E / (t_e2e * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "breakdown_ms": {"graph_prepare": float(ph[0]), "partition": float(ph[1]),
+                         "solve": float(ph[2]), "residual_check": float(ph[3])},
+        "solve": {"iters_max": max(s["iters_max"] for s in stats), "levels": P.n_levels,
+                  "components": P.n_comp, "scc_components": P.n_scc,
+                  "edge_visits": stats[-1]["edge_visits"],
+                  "traversed_gteps": stats[-1]["edge_visits"] / (ph[2] * 1e-3) / 1e9,
+                  "residual_l1": residual},
+        "global_power": {"ms_per_step": t_global, "solve_ms": t_global_solve, "iters": g_iters,
+                         "value": world * E / (t_global * 1e-3) / 1e9, "residual_l1": g_res,
+                         "kernel_gbs": gk_bytes / (gk_ms * 1e-3) / 1e9 if gk_ms > 0 else None},
+        "speedup_vs_global": {"step": t_global / t_step, "solve_only": t_global_solve / float(ph[2])},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if args.breakdown:
+            print(json.dumps({"phase_ms_per_step": phase.tolist(), "global_ms": gph.tolist(),
+                              "e2e_ms": e2e_ms}), file=sys.stderr)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

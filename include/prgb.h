@@ -106,6 +106,14 @@ typedef struct pr_solve_stats {
     int32_t *comp_iters;  /* optional caller-owned HOST array [n_comp];
                              filled with per-component iteration counts when
                              non-NULL (0 for CACs and 1-vertex components) */
+    int32_t timing;       /* in: 1 = time the grid-wide power-series kernels
+                             with CUDA events on the call's stream */
+    float kernel_ms;      /* out (timing = 1): their summed device time */
+    int64_t kernel_bytes; /* out (timing = 1): their algorithmic bytes: per
+                             sweep 4 B per edge + 40 B per row (index, z
+                             gather, R read/write, z write, row pointer and
+                             out-degree), plus the inflow gather */
+    int64_t kernel_launches; /* out (timing = 1): number of such launches */
 } pr_solve_stats;
 
 /*
@@ -211,6 +219,10 @@ pr_status pr_global_power(const pr_graph *g, double c, const double *u, double t
  */
 pr_status pr_residual_l1(const pr_graph *g, double c, const double *u, const double *R,
                          double *out_host, void *stream);
+
+/* Number of kernels this library has launched in this process so far (all
+ * entry points, all threads).  Lets a caller count the kernels of a region. */
+int64_t pr_launch_count(void);
 
 /* Human-readable name of a status code (static storage). */
 const char *pr_status_str(pr_status s);

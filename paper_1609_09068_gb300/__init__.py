@@ -22,7 +22,7 @@ import numpy as np
 
 __all__ = [
     "PrError", "Graph", "Partition", "graph", "partition", "solve", "global_power",
-    "residual_l1", "load_library", "library_path", "TYPE_CAC", "TYPE_SCC",
+    "residual_l1", "load_library", "library_path", "launch_count", "TYPE_CAC", "TYPE_SCC",
     "NORM_L1", "NORM_LINF",
 ]
 
@@ -58,7 +58,8 @@ class _Opts(C.Structure):
 
 class _Stats(C.Structure):
     _fields_ = [("iters_max", C.c_int32), ("n_levels", C.c_int32), ("edge_visits", C.c_int64),
-                ("launches", C.c_int64), ("comp_iters", C.c_void_p)]
+                ("launches", C.c_int64), ("comp_iters", C.c_void_p), ("timing", C.c_int32),
+                ("kernel_ms", C.c_float), ("kernel_bytes", C.c_int64), ("kernel_launches", C.c_int64)]
 
 
 _lib = None
@@ -82,6 +83,7 @@ _SIGS = {
                                  C.POINTER(C.c_double), C.c_void_p]),
     "pr_status_str": (C.c_char_p, [C.c_int]),
     "pr_last_cuda_error": (C.c_int, []),
+    "pr_launch_count": (C.c_int64, []),
 }
 
 
@@ -238,8 +240,19 @@ def _opts(norm, max_iter, io_on_host, replay):
     return o, keep
 
 
+def launch_count():
+    """Kernels launched by the library in this process so far."""
+    return int(load_library().pr_launch_count())
+
+
+def _stats_dict(st):
+    return {"iters_max": st.iters_max, "n_levels": st.n_levels, "edge_visits": st.edge_visits,
+            "launches": st.launches, "kernel_ms": st.kernel_ms, "kernel_bytes": st.kernel_bytes,
+            "kernel_launches": st.kernel_launches}
+
+
 def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iters=None,
-          with_stats=False, allow_noconv=False):
+          with_stats=False, allow_noconv=False, timing=False):
     """Sec. 4.3 solve on device tensors; returns R (float64, original order).
 
     ``u`` may be a CUDA tensor or a numpy array (host I/O through the C ABI's
@@ -248,7 +261,7 @@ def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
     on_host = isinstance(u, np.ndarray)
     o, keep = _opts(norm, max_iter, on_host, replay_iters)
     comp_iters = np.zeros(max(part.n_comp, 1), np.int32)
-    st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data)
+    st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data, int(timing), 0.0, 0, 0)
     if on_host:
         uh = np.ascontiguousarray(u, dtype=np.float64)
         R = np.empty(part.n, np.float64)
@@ -264,20 +277,20 @@ def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
         _check(rc, "pr_solve")
     del keep
     if with_stats:
-        return R, {"iters_max": st.iters_max, "n_levels": st.n_levels, "edge_visits": st.edge_visits,
-                   "launches": st.launches, "comp_iters": comp_iters[: part.n_comp].copy(),
-                   "status": rc}
+        d = _stats_dict(st)
+        d.update(comp_iters=comp_iters[: part.n_comp].copy(), status=rc)
+        return R, d
     return R
 
 
 def global_power(g: Graph, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iters=None,
-                 with_stats=False, allow_noconv=False):
+                 with_stats=False, allow_noconv=False, timing=False):
     """Baseline power series on the whole graph; returns (R, iterations)."""
     lib = load_library()
     on_host = isinstance(u, np.ndarray)
     rep = None if replay_iters is None else [int(replay_iters)]
     o, keep = _opts(norm, max_iter, on_host, rep)
-    st = _Stats(0, 0, 0, 0, None)
+    st = _Stats(0, 0, 0, 0, None, int(timing), 0.0, 0, 0)
     if on_host:
         uh = np.ascontiguousarray(u, dtype=np.float64)
         R = np.empty(g.n, np.float64)
@@ -293,7 +306,9 @@ def global_power(g: Graph, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
         _check(rc, "pr_global_power")
     del keep
     if with_stats:
-        return R, st.iters_max, {"edge_visits": st.edge_visits, "status": rc}
+        d = _stats_dict(st)
+        d.update(status=rc)
+        return R, st.iters_max, d
     return R, st.iters_max
 
 

@@ -10,6 +10,7 @@
 
 namespace prgb {
 int last_cuda_error();
+long long launch_count();
 pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wave, int32_t max_wave, Arena& tmp,
                        Ctl* ctl);
 
@@ -56,6 +57,8 @@ const char* pr_status_str(pr_status s) {
 }
 
 int pr_last_cuda_error(void) { return prgb::last_cuda_error(); }
+
+int64_t pr_launch_count(void) { return (int64_t)prgb::launch_count(); }
 
 pr_status pr_graph_create(const pr_csr* csr, void* stream, pr_graph** out) {
   if (!out) return PR_EINVAL;
@@ -223,7 +226,10 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
     dR = tR;
   }
   int64_t launches = 0;
-  PRGB_TRY(run_solve(part, c, du, tol, o.norm, o.max_iter, replay, dR, iters, tmp, ctl, &launches));
+  KernelTiming kt;
+  const bool timing = stats && stats->timing;
+  PRGB_TRY(run_solve(part, c, du, tol, o.norm, o.max_iter, replay, dR, iters, tmp, ctl, &launches,
+                     timing ? &kt : nullptr));
   if (o.io_on_host && n > 0) PRGB_CUDA(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
   int flags = 0;
   PRGB_TRY(finish_sync(s, ctl, &flags));
@@ -242,6 +248,20 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
       PRGB_CUDA(cudaMemcpyAsync(h, iters, (size_t)K * 4, cudaMemcpyDeviceToHost, s));
       PRGB_TRY(solve_edge_visits(part, iters, &stats->edge_visits, tmp));  // synchronises
       for (int32_t k = 0; k < K; k++) stats->iters_max = h[k] > stats->iters_max ? h[k] : stats->iters_max;
+      if (timing) {
+        stats->kernel_ms = 0.0f;
+        stats->kernel_bytes = 0;
+        stats->kernel_launches = (int64_t)kt.comps.size();
+        for (size_t i = 0; i < kt.comps.size(); i++) {
+          float ms = 0.0f;
+          PRGB_CUDA(cudaEventElapsedTime(&ms, kt.start[i], kt.stop[i]));
+          stats->kernel_ms += ms;
+          const LargeComp& L = kt.comps[i];
+          const int64_t it = h[L.c];
+          stats->kernel_bytes += it * (4 * (int64_t)L.m_int + 40 * (int64_t)L.size) + 52 * (int64_t)L.size +
+                                 12 * (int64_t)L.m_ext;
+        }
+      }
     }
   }
   return flags ? PR_ENOCONV : PR_OK;
@@ -278,7 +298,10 @@ pr_status pr_global_power(const pr_graph* g, double c, const double* u, double t
     dR = tR;
   }
   int iters = 0;
-  pr_status st = run_global(g->g, c, du, tol, o.norm, o.max_iter, fixed, dR, &iters, tmp, ctl);
+  float kms = 0.0f;
+  const bool timing = stats && stats->timing;
+  pr_status st = run_global(g->g, c, du, tol, o.norm, o.max_iter, fixed, dR, &iters, tmp, ctl,
+                            timing ? &kms : nullptr);
   if (st != PR_OK && st != PR_ENOCONV) return st;
   if (o.io_on_host && n > 0) {
     PRGB_CUDA(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
@@ -290,6 +313,11 @@ pr_status pr_global_power(const pr_graph* g, double c, const double* u, double t
     stats->launches = 1;
     stats->edge_visits = (int64_t)iters * g->g.m;
     if (stats->comp_iters) stats->comp_iters[0] = iters;
+    if (timing) {
+      stats->kernel_ms = kms;
+      stats->kernel_launches = 1;
+      stats->kernel_bytes = (int64_t)iters * (4 * g->g.m + 40 * (int64_t)g->g.n) + 28 * (int64_t)g->g.n;
+    }
   }
   return st;
 }
@@ -304,7 +332,7 @@ pr_status pr_residual_l1(const pr_graph* g, double c, const double* u, const dou
   double* out = nullptr;
   PRGB_TRY(tmp.alloc(&part, (size_t)residual_grid()));
   PRGB_TRY(tmp.alloc(&out, 1));
-  PRGB_TRY(run_residual(g->g, c, u, R, part, out, s));
+  PRGB_TRY(run_residual(g->g, c, u, R, part, out, tmp));
   PRGB_CUDA(cudaMemcpyAsync(out_host, out, 8, cudaMemcpyDeviceToHost, s));
   PRGB_CUDA(cudaStreamSynchronize(s));
   return PR_OK;

@@ -35,7 +35,12 @@ void set_last_cuda_error(cudaError_t e);
     }                                                    \
   } while (0)
 
-#define PRGB_LAUNCH() PRGB_CUDA(cudaGetLastError())
+void count_launch();
+#define PRGB_LAUNCH()            \
+  do {                           \
+    ::prgb::count_launch();      \
+    PRGB_CUDA(cudaGetLastError()); \
+  } while (0)
 
 // ---------------------------------------------------------------------------
 // device control block: error word and grid-barrier state.  One per call
@@ -155,6 +160,34 @@ __device__ __forceinline__ double block_max(double v, double* scratch) {
   return r;
 }
 
+// Warp-aggregated frontier push.  All 32 lanes must call it; a lane with
+// want set appends nch items (v, 0), ..., (v, nch-1).  One atomic per warp.
+__device__ __forceinline__ void warp_push(bool want, int v, int nch, int* fv, int* fc, int* counter, int cap,
+                                          Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int cnt = want ? nch : 0;
+  int inc = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  const int total = __shfl_sync(0xffffffffu, inc, 31);
+  if (total == 0) return;
+  int base = 0;
+  if (lane == 31) base = atomicAdd(counter, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  if (base + total > cap) {
+    if (lane == 0) set_err(ctl, PR_EINTERNAL, 50);
+    return;
+  }
+  const int pos = base + inc - cnt;
+  for (int j = 0; j < cnt; j++) {
+    fv[pos + j] = v;
+    fc[pos + j] = j;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // stream-ordered device buffers
 // ---------------------------------------------------------------------------
@@ -232,7 +265,28 @@ struct DevGraph {
   int32_t* iptr = nullptr;  // [n+1] in-edges, sources ascending
   int32_t* iidx = nullptr;  // [m]
   int32_t* outdeg = nullptr;  // [n]
+  // rows of the CSC with more in-edges than the SpMV chunk (see spmv.cuh)
+  int32_t* heavy_rows = nullptr;
+  int32_t* heavy_choff = nullptr;
+  int32_t* heavy_chrow = nullptr;
+  int32_t nheavy = 0, nchunks = 0;
+  int32_t* lorder = nullptr;  // [n] rows ordered by in-degree class (heavy last)
+  double* inv = nullptr;      // [n] 1/outdeg, 0 for dangling vertices
 };
+
+// Rows [0, nrows) of ptr ordered by (group[row], in-degree class), stable
+// (group may be null).  Used to give the 32 rows of a warp similar lengths.
+pr_status build_lorder(const int32_t* ptr, int32_t nrows, const int32_t* group, int32_t group_max, Arena& keep,
+                       Arena& tmp, int32_t** lorder);
+// inv[i] = 1/deg[i] (0 where deg is 0)
+pr_status build_inv(const int32_t* deg, int32_t n, Arena& keep, double** inv, cudaStream_t s);
+
+// List the rows r in [0, nrows) of ptr with ptr[r+1]-ptr[r] > kHeavy
+// (ascending), their chunk offsets (exclusive prefix of ceil(deg/kHeavy))
+// and, per chunk, its heavy-row index; reads the two counts back
+// (synchronises).
+pr_status build_heavy(const int32_t* ptr, int32_t nrows, Arena& keep, Arena& tmp, int32_t** rows,
+                      int32_t** choff, int32_t** chrow, int32_t* nheavy, int32_t* nchunks);
 
 // ingest.cu: validate the CSR, drop loops, build out- and in-adjacency.
 // Buffers of g are allocated from `keep`; scratch from `tmp`.
@@ -256,7 +310,10 @@ struct LargeComp {
   int32_t type;
   int32_t sub_begin, sub_end;  // sub-level range (CAC topological waves)
   int32_t level_idx;           // processing index of its level (0 = highest)
-  int32_t pad;
+  int32_t m_int;               // internal in-edges
+  int32_t m_ext;               // external in-edges
+  int32_t heavy_begin, heavy_end;  // slice of the partition's heavy-row list
+  int32_t chunk_begin, chunk_end;  // its chunk range
 };
 
 // per level (in processing order): component ranges by class
@@ -302,6 +359,13 @@ struct pr_partition_s {
   int32_t n_sub = 0;
   int64_t m_int = 0, m_ext = 0;
   int32_t max_large = 0;       // largest vertex count among large components
+  int32_t* heavy_rows = nullptr;   // permuted rows with > kHeavy internal in-edges
+  int32_t* heavy_choff = nullptr;
+  int32_t* heavy_chrow = nullptr;
+  int32_t* lorder = nullptr;       // [n] positions by (component, internal in-degree class)
+  double* p_inv = nullptr;         // [n] 1/outdeg by position
+  int32_t nheavy = 0, nchunks = 0;
+  int32_t max_heavy = 0, max_chunks = 0;  // largest slice over the large components
   std::vector<prgb::LevelRange> levels;  // host, processing order
   std::vector<prgb::LargeComp> large;    // host
 };

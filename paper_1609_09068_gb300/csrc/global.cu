@@ -3,17 +3,18 @@
 // (I - cA^T) R = u (Def. 3.5).
 #include "common.cuh"
 #include "global.cuh"
+#include "spmv.cuh"
 
 namespace prgb {
 
-constexpr int kGG = 8;  // lanes per row
 
 __device__ __forceinline__ double gdiv(double x, int deg) { return deg > 0 ? x / (double)deg : 0.0; }
 
 // P_0 = u, R = u; repeat P <- c A^T P, R += P; stop after adding P with
 // ||P||_1 <= tol (L1) or when max(P) < tol (the paper's rule).  One
 // cooperative launch; the stopping sum is reduced deterministically (block
-// partials summed in block order by every block).
+// partials summed in block order by every block, heavy rows by the fixed
+// tree of spmv.cuh).
 __global__ void __launch_bounds__(kBlock) global_power_k(GlobalArgs a) {
   __shared__ double red[kBlock / 32];
   const int n = a.n;
@@ -21,39 +22,33 @@ __global__ void __launch_bounds__(kBlock) global_power_k(GlobalArgs a) {
     const double uu = a.u[i];
     if (!(uu >= 0.0) || !isfinite(uu)) set_err(a.ctl, PR_EINVAL, 400);
     a.R[i] = uu;
-    a.zA[i] = gdiv(uu, a.outdeg[i]);
+    a.zA[i] = uu * a.inv[i];
   }
   if (!grid_sync(a.ctl, 401)) return;
-  const int lane = threadIdx.x & (kGG - 1);
-  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kGG;
-  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / kGG;
-  const int64_t wb = g0 - ((threadIdx.x & 31) / kGG);
+  const bool l1 = a.norm == PR_NORM_L1;
+  const int nlight = n - a.hv.nheavy;
   int k = 0;
   for (;;) {
     const double* cur = (k & 1) ? a.zB : a.zA;
     double* nxt = (k & 1) ? a.zA : a.zB;
     double local = 0.0;
-    for (int64_t base = wb; base < n; base += ng) {
-      const int64_t i = base + ((threadIdx.x & 31) / kGG);
-      double acc = 0.0;
-      if (i < n)
-        for (int e = a.iptr[i] + lane; e < a.iptr[i + 1]; e += kGG) acc += cur[a.iidx[e]];
-      acc = group_sum<kGG>(acc);
-      if (i < n && lane == 0) {
-        const double pn = a.c * acc;
-        a.R[i] += pn;
-        nxt[i] = gdiv(pn, a.outdeg[i]);
-        local = a.norm == PR_NORM_L1 ? local + pn : fmax(local, pn);
-      }
-    }
-    const double bs = a.norm == PR_NORM_L1 ? block_sum(local, red) : block_max(local, red);
+    auto fin = [&](int row, double acc, bool heavy) -> double {
+      const double pn = a.c * acc;
+      a.R[row] += pn;
+      nxt[row] = pn * a.inv[row];
+      if (!heavy) local = fold2(local, pn, l1);
+      return pn;
+    };
+    auto val = [&](int e) -> double { return cur[a.iidx[e]]; };
+    balanced_sweep(a.iptr, a.lorder, nlight, a.hv, a.hs, k & 1, l1, fin, val);
+    const double bs = l1 ? block_sum(local, red) : block_max(local, red);
     double* slot = a.part + (size_t)(k & 1) * gridDim.x;
     if (threadIdx.x == 0) slot[blockIdx.x] = bs;
     if (!grid_sync(a.ctl, 402)) return;
     double t = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      t = a.norm == PR_NORM_L1 ? t + slot[b] : fmax(t, slot[b]);
-    const double s = a.norm == PR_NORM_L1 ? block_sum(t, red) : block_max(t, red);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t = fold2(t, __ldcg(&slot[b]), l1);
+    double s = l1 ? block_sum(t, red) : block_max(t, red);
+    if (a.hv.nheavy > 0) s = fold2(s, __ldcg(&a.hs.total[k & 1]), l1);
     k++;
     if (a.fixed >= 0) {
       if (k >= a.fixed) break;
@@ -68,47 +63,47 @@ __global__ void __launch_bounds__(kBlock) global_power_k(GlobalArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->cnt[7] = k;
 }
 
-// sum_i |u_i + c * sum_{j -> i} R_j / outdeg(j) - R_i|, block partials
+// sum_i |u_i + c * sum_{j -> i} R_j / outdeg(j) - R_i| with the division
+// written out per edge (the defining expression), block partials plus the
+// heavy rows' fold in hs.total[0]
 __global__ void __launch_bounds__(kBlock) residual_k(int32_t n, const int32_t* __restrict__ iptr,
                                                      const int32_t* __restrict__ iidx,
-                                                     const int32_t* __restrict__ outdeg, double c,
-                                                     const double* __restrict__ u, const double* __restrict__ R,
-                                                     double* __restrict__ part) {
+                                                     const int32_t* __restrict__ outdeg,
+                                                     const int32_t* __restrict__ lorder, HeavyRows hv,
+                                                     HeavyScratch hs, double c, const double* __restrict__ u,
+                                                     const double* __restrict__ R, double* __restrict__ part) {
   __shared__ double red[kBlock / 32];
-  const int lane = threadIdx.x & (kGG - 1);
-  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kGG;
-  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / kGG;
-  const int64_t wb = g0 - ((threadIdx.x & 31) / kGG);
   double local = 0.0;
-  for (int64_t base = wb; base < n; base += ng) {
-    const int64_t i = base + ((threadIdx.x & 31) / kGG);
-    double acc = 0.0;
-    if (i < n)
-      for (int e = iptr[i] + lane; e < iptr[i + 1]; e += kGG) {
-        const int j = iidx[e];
-        acc += R[j] / (double)outdeg[j];
-      }
-    acc = group_sum<kGG>(acc);
-    if (i < n && lane == 0) local += fabs(u[i] + c * acc - R[i]);
-  }
+  auto fin = [&](int row, double acc, bool heavy) -> double {
+    const double r = fabs(u[row] + c * acc - R[row]);
+    if (!heavy) local += r;
+    return r;
+  };
+  auto val = [&](int e) -> double {
+    const int j = iidx[e];
+    return R[j] / (double)outdeg[j];
+  };
+  balanced_sweep(iptr, lorder, n - hv.nheavy, hv, hs, 0, true, fin, val);
   const double bs = block_sum(local, red);
   if (threadIdx.x == 0) part[blockIdx.x] = bs;
 }
 
-__global__ void __launch_bounds__(kBlock) sum_parts_k(const double* __restrict__ part, int np, double* out) {
+__global__ void __launch_bounds__(kBlock) sum_parts_k(const double* __restrict__ part, int np,
+                                                      const double* __restrict__ heavy_total, double* out) {
   __shared__ double red[kBlock / 32];
   double t = 0.0;
   for (int b = threadIdx.x; b < np; b += blockDim.x) t += part[b];
   t = block_sum(t, red);
-  if (threadIdx.x == 0) *out = t;
+  if (threadIdx.x == 0) *out = heavy_total ? t + *heavy_total : t;
 }
 
 int residual_grid() { return num_sms() * 4; }
 
 pr_status run_global(const DevGraph& g, double c, const double* u, double tol, int norm, int max_iter, int fixed,
-                     double* R, int* iters, Arena& tmp, Ctl* ctl) {
+                     double* R, int* iters, Arena& tmp, Ctl* ctl, float* kernel_ms) {
   cudaStream_t s = tmp.stream();
   *iters = 0;
+  if (kernel_ms) *kernel_ms = 0.0f;
   if (g.n == 0) return PR_OK;
   GlobalArgs a;
   a.n = g.n;
@@ -126,14 +121,36 @@ pr_status run_global(const DevGraph& g, double c, const double* u, double tol, i
   PRGB_TRY(tmp.alloc(&a.zA, g.n));
   PRGB_TRY(tmp.alloc(&a.zB, g.n));
   PRGB_TRY(tmp.alloc(&a.part, (size_t)2 * num_sms() * 8));
+  a.hv.rows = g.heavy_rows;
+  a.hv.choff = g.heavy_choff;
+  a.hv.nheavy = g.nheavy;
+  a.hv.nchunks = g.nchunks;
+  a.hv.chrow = g.heavy_chrow;
+  a.hv.cbase = 0;
+  a.hv.hbase = 0;
+  a.lorder = g.lorder;
+  a.inv = g.inv;
+  PRGB_TRY(alloc_heavy_scratch(&a.hs, g.nheavy, g.nchunks, tmp));
   PRGB_TRY(reset_ctl(ctl, s));
   void* args[] = {&a};
-  PRGB_TRY(launch_coop((const void*)global_power_k, kBlock, 0, s, args, 4, nullptr));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (kernel_ms) {
+    PRGB_CUDA(cudaEventCreate(&e0));
+    PRGB_CUDA(cudaEventCreate(&e1));
+    PRGB_CUDA(cudaEventRecord(e0, s));
+  }
+  pr_status ls = launch_coop((const void*)global_power_k, kBlock, 0, s, args, 4, nullptr);
+  if (kernel_ms && ls == PR_OK) cudaEventRecord(e1, s);
   int h[3] = {0, 0, 0};
   PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, 4, cudaMemcpyDeviceToHost, s));
   PRGB_CUDA(cudaMemcpyAsync(&h[1], &ctl->flags[0], 4, cudaMemcpyDeviceToHost, s));
   PRGB_CUDA(cudaMemcpyAsync(&h[2], &ctl->cnt[7], 4, cudaMemcpyDeviceToHost, s));
-  PRGB_CUDA(cudaStreamSynchronize(s));
+  cudaError_t se = cudaStreamSynchronize(s);
+  if (kernel_ms && ls == PR_OK && se == cudaSuccess) cudaEventElapsedTime(kernel_ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ls != PR_OK) return ls;
+  PRGB_CUDA(se);
   *iters = h[2];
   if (h[0]) return (pr_status)h[0];
   if (h[1]) return PR_ENOCONV;
@@ -141,11 +158,20 @@ pr_status run_global(const DevGraph& g, double c, const double* u, double tol, i
 }
 
 pr_status run_residual(const DevGraph& g, double c, const double* u, const double* R, double* part, double* out_dev,
-                       cudaStream_t s) {
+                       Arena& tmp) {
+  cudaStream_t s = tmp.stream();
   const int np = residual_grid();
-  residual_k<<<np, kBlock, 0, s>>>(g.n, g.iptr, g.iidx, g.outdeg, c, u, R, part);
+  HeavyRows hv;
+  hv.rows = g.heavy_rows;
+  hv.choff = g.heavy_choff;
+  hv.chrow = g.heavy_chrow;
+  hv.nheavy = g.nheavy;
+  hv.nchunks = g.nchunks;
+  HeavyScratch hs;
+  PRGB_TRY(alloc_heavy_scratch(&hs, g.nheavy, g.nchunks, tmp));
+  residual_k<<<np, kBlock, 0, s>>>(g.n, g.iptr, g.iidx, g.outdeg, g.lorder, hv, hs, c, u, R, part);
   PRGB_LAUNCH();
-  sum_parts_k<<<1, kBlock, 0, s>>>(part, np, out_dev);
+  sum_parts_k<<<1, kBlock, 0, s>>>(part, np, g.nheavy > 0 ? hs.total : nullptr, out_dev);
   PRGB_LAUNCH();
   return PR_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "spmv.cuh"
 
 namespace prgb {
 
@@ -10,6 +11,8 @@ struct GlobalArgs {
   const int32_t* iptr;
   const int32_t* iidx;
   const int32_t* outdeg;
+  const int32_t* lorder;
+  const double* inv;
   const double* u;
   double c, tol;
   int norm, max_iter, fixed;
@@ -17,17 +20,21 @@ struct GlobalArgs {
   double* zA;
   double* zB;
   double* part;
+  HeavyRows hv;
+  HeavyScratch hs;
   Ctl* ctl;
 };
 
+// kernel_ms (nullable): device time of the power-series kernel (CUDA events)
 pr_status run_global(const DevGraph& g, double c, const double* u, double tol, int norm, int max_iter, int fixed,
-                     double* R, int* iters, Arena& tmp, Ctl* ctl);
+                     double* R, int* iters, Arena& tmp, Ctl* ctl, float* kernel_ms);
 
 // number of block partials the residual kernel writes
 int residual_grid();
 
-// residual into out_dev (device double), using part[residual_grid()] scratch
+// residual into out_dev (device double), using part[residual_grid()] and
+// heavy-row scratch from tmp
 pr_status run_residual(const DevGraph& g, double c, const double* u, const double* R, double* part, double* out_dev,
-                       cudaStream_t s);
+                       Arena& tmp);
 
 }  // namespace prgb

@@ -3,6 +3,7 @@
 // ignore them), out-degree without loops, and the in-adjacency (CSC) with
 // sources ascending inside each column (stable radix sort by target).
 #include "common.cuh"
+#include "spmv.cuh"
 
 namespace prgb {
 
@@ -123,6 +124,10 @@ pr_status ingest(const pr_csr* csr, DevGraph* g, Arena& keep, Arena& tmp, Ctl* c
   // each column's sources in ascending order.
   PRGB_TRY(radix_sort_pairs(kd, vs, kt, vt, m, bits_for((uint32_t)(n > 0 ? n - 1 : 0)), tmp));
   if (m > 0) PRGB_CUDA(cudaMemcpyAsync(g->iidx, vs, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
+  PRGB_TRY(build_heavy(g->iptr, n, keep, tmp, &g->heavy_rows, &g->heavy_choff, &g->heavy_chrow, &g->nheavy,
+                        &g->nchunks));
+  PRGB_TRY(build_lorder(g->iptr, n, nullptr, 0, keep, tmp, &g->lorder));
+  PRGB_TRY(build_inv(g->outdeg, n, keep, &g->inv, s));
   return PR_OK;
 }
 

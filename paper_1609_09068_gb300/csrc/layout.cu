@@ -16,7 +16,10 @@
 // * Per level: the components split by size class (grid-wide / one CTA /
 //   one warp / 1-vertex collection; Sec. 4.2 groups the 1-vertex components
 //   of a level together).
+#include <algorithm>
+
 #include "common.cuh"
+#include "spmv.cuh"
 
 namespace prgb {
 
@@ -190,13 +193,17 @@ __global__ void level_ranges_k(int32_t nlev, int32_t K, const int32_t* lvl_cbeg,
   }
 }
 
+__global__ void pos_comp_k(int32_t n, const int32_t* perm, const int32_t* comp_id, int32_t* pc) {
+  for (int64_t p = gtid(); p < n; p += gstride()) pc[p] = comp_id[perm[p]];
+}
+
 __global__ void large_flags_k(int32_t K, const int32_t* c_off, uint8_t* flag) {
   for (int64_t c = gtid(); c < K; c += gstride()) flag[c] = size_class(c_off[c + 1] - c_off[c]) == 0;
 }
 
 __global__ void large_fill_k(int32_t K, const uint8_t* flag, const int32_t* lidx, const int32_t* c_off,
                              const int32_t* c_sub, const uint8_t* c_type, const int32_t* c_level, int32_t maxl,
-                             LargeComp* out) {
+                             const int32_t* int_ptr, const int32_t* ext_ptr, LargeComp* out) {
   for (int64_t c = gtid(); c < K; c += gstride()) {
     if (!flag[c]) continue;
     LargeComp L;
@@ -207,7 +214,9 @@ __global__ void large_fill_k(int32_t K, const uint8_t* flag, const int32_t* lidx
     L.sub_begin = c_sub[c];
     L.sub_end = c_sub[c + 1];
     L.level_idx = maxl - c_level[c];
-    L.pad = 0;
+    L.m_int = int_ptr[c_off[c + 1]] - int_ptr[c_off[c]];
+    L.m_ext = ext_ptr[c_off[c + 1]] - ext_ptr[c_off[c]];
+    L.heavy_begin = L.heavy_end = L.chunk_begin = L.chunk_end = 0;
     out[lidx[c]] = L;
   }
 }
@@ -310,6 +319,7 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   int32_t *icnt, *ecnt;
   PRGB_TRY(tmp.alloc(&icnt, n));
   PRGB_TRY(tmp.alloc(&ecnt, n));
+  PRGB_TRY(build_inv(P->p_outdeg, n, keep, &P->p_inv, s));
   PRGB_TRY(keep.alloc(&P->int_ptr, (size_t)n + 1));
   PRGB_TRY(keep.alloc(&P->ext_ptr, (size_t)n + 1));
   edge_count_k<<<gridw(n), kBlock, 0, s>>>(n, P->perm, g.iptr, g.iidx, P->comp_id, icnt, ecnt);
@@ -366,11 +376,35 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   if (nlarge > 0) {
     LargeComp* dl;
     PRGB_TRY(tmp.alloc(&dl, nlarge));
-    large_fill_k<<<grid1(K), kBlock, 0, s>>>(K, lflag, lidx, P->c_off, P->c_sub, P->c_type, c_level, maxl, dl);
+    large_fill_k<<<grid1(K), kBlock, 0, s>>>(K, lflag, lidx, P->c_off, P->c_sub, P->c_type, c_level, maxl,
+                                             P->int_ptr, P->ext_ptr, dl);
     PRGB_LAUNCH();
     PRGB_CUDA(cudaMemcpyAsync(P->large.data(), dl, sizeof(LargeComp) * nlarge, cudaMemcpyDeviceToHost, s));
     PRGB_CUDA(cudaStreamSynchronize(s));
     for (const LargeComp& L : P->large) P->max_large = L.size > P->max_large ? L.size : P->max_large;
+    // heavy rows of the internal CSC, sliced per large component, and the
+    // light rows of each component ordered by in-degree class
+    PRGB_TRY(build_heavy(P->int_ptr, n, keep, tmp, &P->heavy_rows, &P->heavy_choff, &P->heavy_chrow, &P->nheavy,
+                          &P->nchunks));
+    int32_t* pc;
+    PRGB_TRY(tmp.alloc(&pc, n));
+    pos_comp_k<<<grid1(n), kBlock, 0, s>>>(n, P->perm, P->comp_id, pc);
+    PRGB_LAUNCH();
+    PRGB_TRY(build_lorder(P->int_ptr, n, pc, K - 1, keep, tmp, &P->lorder));
+    std::vector<int32_t> hrows(P->nheavy), hcho(P->nheavy + 1);
+    if (P->nheavy > 0) {
+      PRGB_CUDA(cudaMemcpyAsync(hrows.data(), P->heavy_rows, (size_t)P->nheavy * 4, cudaMemcpyDeviceToHost, s));
+    }
+    PRGB_CUDA(cudaMemcpyAsync(hcho.data(), P->heavy_choff, ((size_t)P->nheavy + 1) * 4, cudaMemcpyDeviceToHost, s));
+    PRGB_CUDA(cudaStreamSynchronize(s));
+    for (LargeComp& L : P->large) {
+      L.heavy_begin = (int32_t)(std::lower_bound(hrows.begin(), hrows.end(), L.off) - hrows.begin());
+      L.heavy_end = (int32_t)(std::lower_bound(hrows.begin(), hrows.end(), L.off + L.size) - hrows.begin());
+      L.chunk_begin = hcho[L.heavy_begin];
+      L.chunk_end = hcho[L.heavy_end];
+      P->max_heavy = std::max(P->max_heavy, L.heavy_end - L.heavy_begin);
+      P->max_chunks = std::max(P->max_chunks, L.chunk_end - L.chunk_begin);
+    }
   }
   // host-side consistency checks of everything the solver will index with
   int32_t prev_end = 0, prev_vend = 0;

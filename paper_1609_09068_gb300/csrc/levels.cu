@@ -59,11 +59,10 @@ __global__ void fill_cin_k(const int32_t* __restrict__ optr, const int32_t* __re
   }
 }
 
-// finalize node X: read the folded successor key, decide level and merge,
-// and queue X's in-edge chunks for the next wave
-__device__ void finalize_node(int X, int wave, const int32_t* nsize, int32_t* key, int32_t* level_node,
-                              int32_t* wave_node, uint8_t* merged, const int32_t* cin_ptr, int* fr_node,
-                              int* fr_chunk, int* counter, int cap, Ctl* ctl) {
+// finalize node X: read the folded successor key, decide level and merge.
+// Returns the number of in-edge chunks to queue for the next wave.
+__device__ int finalize_node(int X, int wave, const int32_t* nsize, int32_t* key, int32_t* level_node,
+                             int32_t* wave_node, uint8_t* merged, const int32_t* cin_ptr) {
   __threadfence();
   const int k = atomicAdd(&key[X], 0);
   const bool scc = nsize[X] >= 2;
@@ -81,18 +80,7 @@ __device__ void finalize_node(int X, int wave, const int32_t* nsize, int32_t* ke
   wave_node[X] = wave;
   merged[X] = (uint8_t)m;
   const int len = cin_ptr[X + 1] - cin_ptr[X];
-  if (len > 0) {
-    const int nch = (len + kChunk - 1) / kChunk;
-    const int pos = atomicAdd(counter, nch);
-    if (pos + nch > cap) {
-      set_err(ctl, PR_EINTERNAL, 200);
-      return;
-    }
-    for (int j = 0; j < nch; j++) {
-      fr_node[pos + j] = X;
-      fr_chunk[pos + j] = j;
-    }
-  }
+  return (len + kChunk - 1) / kChunk;
 }
 
 __global__ void kahn_k(int32_t n, const int32_t* __restrict__ rep, const int32_t* __restrict__ nsize,
@@ -101,10 +89,12 @@ __global__ void kahn_k(int32_t n, const int32_t* __restrict__ rep, const int32_t
                        int* fa_chunk, int* fb_node, int* fb_chunk, int cap, Ctl* ctl) {
   const int lane = threadIdx.x & 31;
   const int gw = gwarp_l(), nw = nwarps_l();
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    if (rep[v] == (int32_t)v && pending[v] == 0)
-      finalize_node((int)v, 0, nsize, key, level_node, wave_node, merged, cin_ptr, fa_node, fa_chunk,
-                    &ctl->cnt[0], cap, ctl);
+  for (int64_t vb = (int64_t)gw * 32; vb < n; vb += (int64_t)nw * 32) {
+    const int64_t v = vb + lane;
+    int nch = 0;
+    if (v < n && rep[v] == (int32_t)v && pending[v] == 0)
+      nch = finalize_node((int)v, 0, nsize, key, level_node, wave_node, merged, cin_ptr);
+    warp_push(nch > 0, (int)v, nch, fa_node, fa_chunk, &ctl->cnt[0], cap, ctl);
   }
   if (!grid_sync(ctl, 210)) return;
   for (int wave = 0;; wave++) {
@@ -122,13 +112,17 @@ __global__ void kahn_k(int32_t n, const int32_t* __restrict__ rep, const int32_t
       const int val = 2 * level_node[X] + (nsize[X] >= 2 ? 1 : 0);
       const int b = cin_ptr[X] + j * kChunk;
       const int e_end = min(cin_ptr[X + 1], b + kChunk);
-      for (int e = b + lane; e < e_end; e += 32) {
-        const int U = cin_src[e];
-        atomicMax(&key[U], val);
-        __threadfence();
-        if (atomicSub(&pending[U], 1) == 1)
-          finalize_node(U, wave + 1, nsize, key, level_node, wave_node, merged, cin_ptr, nn, nc,
-                        &ctl->cnt[cnxt], cap, ctl);
+      for (int base = b; base < e_end; base += 32) {
+        const int e = base + lane;
+        int U = 0, nch = 0;
+        if (e < e_end) {
+          U = cin_src[e];
+          atomicMax(&key[U], val);
+          __threadfence();
+          if (atomicSub(&pending[U], 1) == 1)
+            nch = finalize_node(U, wave + 1, nsize, key, level_node, wave_node, merged, cin_ptr);
+        }
+        warp_push(nch > 0, U, nch, nn, nc, &ctl->cnt[cnxt], cap, ctl);
       }
     }
     if (!grid_sync(ctl, 211)) return;

@@ -1,13 +1,17 @@
 // prims.cu -- scan, stable radix sort and launch helpers used by the
 // partitioner and the layout step (Sec. 4.2 notes that sorting by level and
 // size can be done without comparisons; a radix sort is that kind of sort).
-#include <mutex>
+#include <atomic>
 
 #include "common.cuh"
+#include "spmv.cuh"
 
 namespace prgb {
 
 static thread_local int g_last_cuda_error = 0;
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = static_cast<int>(e); }
 int last_cuda_error() { return g_last_cuda_error; }
 
@@ -33,6 +37,7 @@ pr_status launch_coop(const void* kernel, int block, size_t smem, cudaStream_t s
   const int grid = per_sm * num_sms();
   if (grid_out) *grid_out = grid;
   PRGB_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(block), args, smem, s));
+  count_launch();
   return PR_OK;
 }
 
@@ -257,6 +262,115 @@ pr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, u
     PRGB_CUDA(cudaMemcpyAsync(keys, ka, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     PRGB_CUDA(cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
   }
+  return PR_OK;
+}
+
+}  // namespace prgb
+
+namespace prgb {
+
+__global__ void heavy_flags_k(const int32_t* __restrict__ ptr, int32_t nrows, uint8_t* flag, int32_t* nch) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
+    const int d = ptr[i + 1] - ptr[i];
+    const bool h = d > kHeavy;
+    flag[i] = h;
+    nch[i] = h ? (d + kChunkH - 1) / kChunkH : 0;
+  }
+}
+
+__global__ void heavy_fill_k(int32_t nrows, const uint8_t* flag, const int32_t* hidx, const int32_t* cho_all,
+                             int32_t* rows, int32_t* choff) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
+    if (flag[i]) {
+      rows[hidx[i]] = (int32_t)i;
+      choff[hidx[i]] = cho_all[i];
+    }
+  }
+}
+
+__global__ void heavy_chrow_k(int32_t nheavy, const int32_t* choff, int32_t* chrow) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += (int64_t)gridDim.x * blockDim.x)
+    for (int c = choff[h]; c < choff[h + 1]; c++) chrow[c] = (int32_t)h;
+}
+
+pr_status build_heavy(const int32_t* ptr, int32_t nrows, Arena& keep, Arena& tmp, int32_t** rows,
+                      int32_t** choff, int32_t** chrow, int32_t* nheavy, int32_t* nchunks) {
+  cudaStream_t s = tmp.stream();
+  *nheavy = 0;
+  *nchunks = 0;
+  uint8_t* flag;
+  int32_t *nch, *hidx, *cho_all;
+  PRGB_TRY(tmp.alloc(&flag, (size_t)nrows + 1));
+  PRGB_TRY(tmp.alloc(&nch, (size_t)nrows + 1));
+  PRGB_TRY(tmp.alloc(&hidx, (size_t)nrows + 1));
+  PRGB_TRY(tmp.alloc(&cho_all, (size_t)nrows + 1));
+  if (nrows > 0) {
+    heavy_flags_k<<<grid_for(nrows), kBlock, 0, s>>>(ptr, nrows, flag, nch);
+    PRGB_LAUNCH();
+  }
+  PRGB_TRY(scan_u8(flag, hidx, nrows, tmp));
+  PRGB_TRY(scan_i32(nch, cho_all, nrows, tmp));
+  int32_t h[2] = {0, 0};
+  PRGB_CUDA(cudaMemcpyAsync(&h[0], hidx + nrows, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaMemcpyAsync(&h[1], cho_all + nrows, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  *nheavy = h[0];
+  *nchunks = h[1];
+  PRGB_TRY(keep.alloc(rows, (size_t)h[0] + 1));
+  PRGB_TRY(keep.alloc(choff, (size_t)h[0] + 1));
+  if (h[0] > 0) {
+    heavy_fill_k<<<grid_for(nrows), kBlock, 0, s>>>(nrows, flag, hidx, cho_all, *rows, *choff);
+    PRGB_LAUNCH();
+  }
+  PRGB_CUDA(cudaMemcpyAsync(*choff + h[0], &h[1], 4, cudaMemcpyHostToDevice, s));
+  PRGB_TRY(keep.alloc(chrow, (size_t)h[1] + 1));
+  if (h[0] > 0) {
+    heavy_chrow_k<<<grid_for(h[0]), kBlock, 0, s>>>(h[0], *choff, *chrow);
+    PRGB_LAUNCH();
+  }
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  return PR_OK;
+}
+
+}  // namespace prgb
+
+namespace prgb {
+
+__global__ void lorder_keys_k(const int32_t* __restrict__ ptr, int32_t nrows, const int32_t* __restrict__ group,
+                              uint32_t* keys, uint32_t* vals) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = group ? (uint32_t)group[i] : 0u;
+    keys[i] = (g << 4) | (uint32_t)deg_class(ptr[i + 1] - ptr[i]);
+    vals[i] = (uint32_t)i;
+  }
+}
+
+pr_status build_lorder(const int32_t* ptr, int32_t nrows, const int32_t* group, int32_t group_max, Arena& keep,
+                       Arena& tmp, int32_t** lorder) {
+  cudaStream_t s = tmp.stream();
+  const int gbits = group ? bits_for((uint32_t)group_max) : 0;
+  if (gbits + 4 > 32) return PR_EINVAL;
+  uint32_t *k, *kt, *vt;
+  PRGB_TRY(tmp.alloc(&k, (size_t)nrows + 1));
+  PRGB_TRY(tmp.alloc(&kt, (size_t)nrows + 1));
+  PRGB_TRY(tmp.alloc(&vt, (size_t)nrows + 1));
+  PRGB_TRY(keep.alloc(lorder, (size_t)nrows + 1));
+  if (nrows == 0) return PR_OK;
+  lorder_keys_k<<<grid_for(nrows), kBlock, 0, s>>>(ptr, nrows, group, k, reinterpret_cast<uint32_t*>(*lorder));
+  PRGB_LAUNCH();
+  return radix_sort_pairs(k, reinterpret_cast<uint32_t*>(*lorder), kt, vt, nrows, gbits + 4, tmp);
+}
+
+__global__ void inv_deg_k(const int32_t* __restrict__ deg, int32_t n, double* inv) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    inv[i] = deg[i] > 0 ? 1.0 / (double)deg[i] : 0.0;
+}
+
+pr_status build_inv(const int32_t* deg, int32_t n, Arena& keep, double** inv, cudaStream_t s) {
+  PRGB_TRY(keep.alloc(inv, (size_t)n + 1));
+  if (n == 0) return PR_OK;
+  inv_deg_k<<<grid_for(n), kBlock, 0, s>>>(deg, n, *inv);
+  PRGB_LAUNCH();
   return PR_OK;
 }
 

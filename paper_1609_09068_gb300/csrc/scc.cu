@@ -19,41 +19,65 @@ namespace prgb {
 __device__ __forceinline__ int gwarp() { return (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
 __device__ __forceinline__ int nwarps() { return (int)(((int64_t)gridDim.x * blockDim.x) >> 5); }
 
+constexpr int kChunkE = 256;  // edges per frontier item
+
+__device__ __forceinline__ int nchunks_of(int d) { return (d + kChunkE - 1) / kChunkE; }
+
 // ---- trim: Kahn peeling in both directions, one persistent launch ---------
+// Items are (vertex, chunk): chunks [0, co) cover the out-edges and
+// [co, co + ci) the in-edges, kChunkE edges each.
+__device__ __forceinline__ int trim_chunks(const int32_t* optr, const int32_t* iptr, int v) {
+  const int n = nchunks_of(optr[v + 1] - optr[v]) + nchunks_of(iptr[v + 1] - iptr[v]);
+  return n > 0 ? n : 1;
+}
+
 __global__ void trim_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx,
                        const int32_t* __restrict__ iptr, const int32_t* __restrict__ iidx, int32_t n,
-                       int32_t* rem_out, int32_t* rem_in, int32_t* state, int32_t* rep, int32_t* fa,
-                       int32_t* fb, Ctl* ctl) {
+                       int32_t* rem_out, int32_t* rem_in, int32_t* state, int32_t* rep, int* fav, int* fac,
+                       int* fbv, int* fbc, int cap, Ctl* ctl) {
   const int lane = threadIdx.x & 31;
   const int gw = gwarp(), nw = nwarps();
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int ro = optr[v + 1] - optr[v], ri = iptr[v + 1] - iptr[v];
-    rem_out[v] = ro;
-    rem_in[v] = ri;
-    rep[v] = -1;
-    state[v] = (ro == 0 || ri == 0) ? 1 : 0;
-    if (ro == 0 || ri == 0) fa[atomicAdd(&ctl->cnt[0], 1)] = (int32_t)v;
+  for (int64_t vb = (int64_t)gw * 32; vb < n; vb += (int64_t)nw * 32) {
+    const int64_t v = vb + lane;
+    bool want = false;
+    if (v < n) {
+      const int ro = optr[v + 1] - optr[v], ri = iptr[v + 1] - iptr[v];
+      rem_out[v] = ro;
+      rem_in[v] = ri;
+      rep[v] = -1;
+      want = (ro == 0 || ri == 0);
+      state[v] = want ? 1 : 0;
+    }
+    warp_push(want, (int)v, want ? trim_chunks(optr, iptr, (int)v) : 0, fav, fac, &ctl->cnt[0], cap, ctl);
   }
   if (!grid_sync(ctl, 100)) return;
   for (int wave = 0;; wave++) {
-    int* cur = (wave & 1) ? fb : fa;
-    int* nxt = (wave & 1) ? fa : fb;
+    int* cv = (wave & 1) ? fbv : fav;
+    int* cc = (wave & 1) ? fbc : fac;
+    int* nv = (wave & 1) ? fav : fbv;
+    int* nc = (wave & 1) ? fac : fbc;
     const int ccur = wave % 3, cnxt = (wave + 1) % 3, cclr = (wave + 2) % 3;
     const int cnt = vload(&ctl->cnt[ccur]);
     if (cnt == 0) break;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[cclr] = 0;
     for (int i = gw; i < cnt; i += nw) {
-      const int v = cur[i];
-      if (lane == 0) rep[v] = v;
-      for (int e = optr[v] + lane; e < optr[v + 1]; e += 32) {
-        const int w = oidx[e];
-        if (atomicSub(&rem_in[w], 1) == 1 && atomicCAS(&state[w], 0, 1) == 0)
-          nxt[atomicAdd(&ctl->cnt[cnxt], 1)] = w;
-      }
-      for (int e = iptr[v] + lane; e < iptr[v + 1]; e += 32) {
-        const int u = iidx[e];
-        if (atomicSub(&rem_out[u], 1) == 1 && atomicCAS(&state[u], 0, 1) == 0)
-          nxt[atomicAdd(&ctl->cnt[cnxt], 1)] = u;
+      const int v = cv[i];
+      const int j = cc[i];
+      if (j == 0 && lane == 0) rep[v] = v;
+      const int co = nchunks_of(optr[v + 1] - optr[v]);
+      const bool out = j < co;
+      const int e0 = out ? optr[v] + j * kChunkE : iptr[v] + (j - co) * kChunkE;
+      const int e1 = out ? min(optr[v + 1], e0 + kChunkE) : min(iptr[v + 1], e0 + kChunkE);
+      for (int base = e0; base < e1; base += 32) {
+        const int e = base + lane;
+        bool want = false;
+        int w = 0;
+        if (e < e1) {
+          w = out ? oidx[e] : iidx[e];
+          int* rem = out ? rem_in : rem_out;
+          want = atomicSub(&rem[w], 1) == 1 && atomicCAS(&state[w], 0, 1) == 0;
+        }
+        warp_push(want, w, want ? trim_chunks(optr, iptr, w) : 0, nv, nc, &ctl->cnt[cnxt], cap, ctl);
       }
     }
     if (!grid_sync(ctl, 101)) return;
@@ -62,37 +86,60 @@ __global__ void trim_k(const int32_t* __restrict__ optr, const int32_t* __restri
 
 // ---- max-label propagation over alive edges, frontier driven --------------
 // dir 0: along out-edges (sig = largest id reaching v); dir 1: along in-edges.
+// Frontier items are (vertex, chunk of kChunkE edges), so the adjacency of a
+// hub is spread over many warps.
 __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
                             const int32_t* __restrict__ rep, const int32_t* __restrict__ pin,
-                            const int32_t* __restrict__ pout, int32_t* sig, int32_t* stamp, int32_t* fa,
-                            int32_t* fb, Ctl* ctl) {
+                            const int32_t* __restrict__ pout, int32_t* sig, int32_t* stamp, int* fav, int* fac,
+                            int* fbv, int* fbc, int cap, Ctl* ctl) {
   const int lane = threadIdx.x & 31;
   const int gw = gwarp(), nw = nwarps();
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    stamp[v] = -1;
-    if (rep[v] < 0) {
-      sig[v] = (int32_t)v;
-      fa[atomicAdd(&ctl->cnt[0], 1)] = (int32_t)v;
+  for (int64_t vb = (int64_t)gw * 32; vb < n; vb += (int64_t)nw * 32) {
+    const int64_t v = vb + lane;
+    bool want = false;
+    int nch = 0;
+    if (v < n) {
+      stamp[v] = -1;
+      if (rep[v] < 0) {
+        sig[v] = (int32_t)v;
+        nch = nchunks_of(ptr[v + 1] - ptr[v]);
+        want = nch > 0;
+      }
     }
+    warp_push(want, (int)v, nch, fav, fac, &ctl->cnt[0], cap, ctl);
   }
   if (!grid_sync(ctl, 110)) return;
   for (int wave = 0;; wave++) {
-    int* cur = (wave & 1) ? fb : fa;
-    int* nxt = (wave & 1) ? fa : fb;
+    int* cv = (wave & 1) ? fbv : fav;
+    int* cc = (wave & 1) ? fbc : fac;
+    int* nv = (wave & 1) ? fav : fbv;
+    int* nc = (wave & 1) ? fac : fbc;
     const int ccur = wave % 3, cnxt = (wave + 1) % 3, cclr = (wave + 2) % 3;
     const int cnt = vload(&ctl->cnt[ccur]);
     if (cnt == 0) break;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[cclr] = 0;
     for (int i = gw; i < cnt; i += nw) {
-      const int u = cur[i];
+      const int u = cv[i];
+      const int j = cc[i];
       const int su = vload(&sig[u]);
       const int a = pin[u], b = pout[u];
-      for (int e = ptr[u] + lane; e < ptr[u + 1]; e += 32) {
-        const int w = idx[e];
-        if (rep[w] >= 0 || pin[w] != a || pout[w] != b) continue;
-        if (vload(&sig[w]) >= su) continue;
-        const int old = atomicMax(&sig[w], su);
-        if (old < su && atomicExch(&stamp[w], wave) != wave) nxt[atomicAdd(&ctl->cnt[cnxt], 1)] = w;
+      const int e0 = ptr[u] + j * kChunkE;
+      const int e1 = min(ptr[u + 1], e0 + kChunkE);
+      for (int base = e0; base < e1; base += 32) {
+        const int e = base + lane;
+        bool want = false;
+        int w = 0, nch = 0;
+        if (e < e1) {
+          w = idx[e];
+          if (rep[w] < 0 && pin[w] == a && pout[w] == b && vload(&sig[w]) < su) {
+            const int old = atomicMax(&sig[w], su);
+            if (old < su && atomicExch(&stamp[w], wave) != wave) {
+              nch = nchunks_of(ptr[w + 1] - ptr[w]);
+              want = nch > 0;
+            }
+          }
+        }
+        warp_push(want, w, nch, nv, nc, &ctl->cnt[cnxt], cap, ctl);
       }
     }
     if (!grid_sync(ctl, 111)) return;
@@ -125,12 +172,16 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
   cudaStream_t s = tmp.stream();
   const int32_t n = g.n;
   if (n == 0) return PR_OK;
-  int32_t *rem_out, *rem_in, *state, *fa, *fb, *sin, *sout, *pin, *pout, *stamp;
+  int32_t *rem_out, *rem_in, *state, *sin, *sout, *pin, *pout, *stamp;
+  int *fav, *fac, *fbv, *fbc;
+  const int cap = (int)(2 * (int64_t)n + 2 * g.m / kChunkE + 2);
+  PRGB_TRY(tmp.alloc(&fav, cap));
+  PRGB_TRY(tmp.alloc(&fac, cap));
+  PRGB_TRY(tmp.alloc(&fbv, cap));
+  PRGB_TRY(tmp.alloc(&fbc, cap));
   PRGB_TRY(tmp.alloc(&rem_out, n));
   PRGB_TRY(tmp.alloc(&rem_in, n));
   PRGB_TRY(tmp.alloc(&state, n));
-  PRGB_TRY(tmp.alloc(&fa, n));
-  PRGB_TRY(tmp.alloc(&fb, n));
   PRGB_TRY(tmp.alloc(&sin, n));
   PRGB_TRY(tmp.alloc(&sout, n));
   PRGB_TRY(tmp.alloc(&pin, n));
@@ -142,7 +193,9 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
   {
     DevGraph gg = g;
     int32_t nn = n;
-    void* args[] = {&gg.optr, &gg.oidx, &gg.iptr, &gg.iidx, &nn, &rem_out, &rem_in, &state, &rep, &fa, &fb, &ctl};
+    int cp = cap;
+    void* args[] = {&gg.optr, &gg.oidx, &gg.iptr, &gg.iidx, &nn, &rem_out, &rem_in, &state, &rep,
+                    &fav, &fac, &fbv, &fbc, &cp, &ctl};
     PRGB_TRY(launch_coop((const void*)trim_k, kBlock, 0, s, args, 4, nullptr));
   }
   for (int round = 0; round < 20000; round++) {
@@ -152,7 +205,8 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
       const int32_t* idx = dir == 0 ? g.oidx : g.iidx;
       int32_t* sig = dir == 0 ? sin : sout;
       int32_t nn = n;
-      void* args[] = {&ptr, &idx, &nn, &rep, &pin, &pout, &sig, &stamp, &fa, &fb, &ctl};
+      int cp = cap;
+      void* args[] = {&ptr, &idx, &nn, &rep, &pin, &pout, &sig, &stamp, &fav, &fac, &fbv, &fbc, &cp, &ctl};
       PRGB_TRY(launch_coop((const void*)propagate_k, kBlock, 0, s, args, 4, nullptr));
     }
     PRGB_CUDA(cudaMemsetAsync(&ctl->cnt[7], 0, sizeof(int), s));

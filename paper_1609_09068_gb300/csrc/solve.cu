@@ -20,10 +20,12 @@
 // are stored.
 #include "common.cuh"
 #include "solve.cuh"
+#include "spmv.cuh"
 
 namespace prgb {
 
-__device__ __forceinline__ double zdiv(double x, int deg) { return deg > 0 ? x / (double)deg : 0.0; }
+// z = x / outdeg as x * (1/outdeg): the reciprocal is precomputed once per
+// vertex, because FP64 division is expensive on this part.
 
 __device__ __forceinline__ bool keep_going(double s, double tau, int norm) {
   return norm == PR_NORM_LINF ? (s >= tau) : (s > tau);
@@ -45,25 +47,36 @@ __device__ __forceinline__ double check_u(const SolveArgs& a, double uu) {
 }
 
 // ---------------------------------------------------------------------------
-// one warp per component of 2..32 vertices
+// one warp per component of 2..32 vertices, one vertex per lane.  The
+// component's internal in-edges (at most 32*31) are staged in shared memory
+// as 8-bit local indices, so each series iteration reads shared memory only.
 // ---------------------------------------------------------------------------
+constexpr int kWarpEdges = kWarpCompMax * (kWarpCompMax - 1);
+
 __global__ void __launch_bounds__(kBlock) solve_warp_k(SolveArgs a, int32_t cbeg, int32_t cend) {
   __shared__ double zsh[kBlock / 32][32];
+  __shared__ uint8_t ish[kBlock / 32][kWarpEdges];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int c = cbeg + (int)blockIdx.x * (kBlock / 32) + wib;
   if (c >= cend) return;  // warp-uniform
   double* z = zsh[wib];
+  uint8_t* ix = ish[wib];
   const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
   const bool act = lane < sz;
   const int p = off + lane;
-  const int deg = act ? a.p_outdeg[p] : 0;
+  const double inv = act ? a.p_inv[p] : 0.0;
+  const int ib0 = a.int_ptr[off];
+  const int m = a.int_ptr[off + sz] - ib0;
+  for (int e = lane; e < m && e < kWarpEdges; e += 32) ix[e] = (uint8_t)local_or_err(a, a.int_idx[ib0 + e] - off, sz);
+  if (m > kWarpEdges) set_err(a.ctl, PR_EINTERNAL, 302);
   double W = 0.0;
   if (act) {
     double g = 0.0;
     for (int e = a.ext_ptr[p]; e < a.ext_ptr[p + 1]; e++) g += a.zr[a.ext_idx[e]];
     W = check_u(a, a.u[a.perm[p]]) + a.c * g;
   }
-  const int ib = act ? a.int_ptr[p] : 0, ie = act ? a.int_ptr[p + 1] : 0;
+  const int ib = act ? a.int_ptr[p] - ib0 : 0, ie = act ? min(a.int_ptr[p + 1] - ib0, kWarpEdges) : 0;
+  __syncwarp();
   double R = W;
   int k = 0;
   if (a.c_type[c] == PR_TYPE_CAC) {
@@ -72,24 +85,24 @@ __global__ void __launch_bounds__(kBlock) solve_warp_k(SolveArgs a, int32_t cbeg
       const int lo = a.sub_ptr[s], hi = a.sub_ptr[s + 1];
       if (act && p >= lo && p < hi) {
         double acc = 0.0;
-        for (int e = ib; e < ie; e++) acc += z[local_or_err(a, a.int_idx[e] - off, sz)];
+        for (int e = ib; e < ie; e++) acc += z[ix[e]];
         R = W + a.c * acc;
-        z[lane] = zdiv(R, deg);
+        z[lane] = R * inv;
       }
       __syncwarp();
     }
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const int fixed = a.replay ? a.replay[c] : -1;
-    if (act) z[lane] = zdiv(W, deg);
+    if (act) z[lane] = W * inv;
     __syncwarp();
     for (;;) {
       double acc = 0.0;
-      for (int e = ib; e < ie; e++) acc += z[local_or_err(a, a.int_idx[e] - off, sz)];
+      for (int e = ib; e < ie; e++) acc += z[ix[e]];
       const double pn = a.c * acc;
       __syncwarp();
       if (act) {
-        z[lane] = zdiv(pn, deg);
+        z[lane] = pn * inv;
         R += pn;
       }
       __syncwarp();
@@ -108,109 +121,116 @@ __global__ void __launch_bounds__(kBlock) solve_warp_k(SolveArgs a, int32_t cbeg
   }
   if (act) {
     a.R[p] = R;
-    a.zr[p] = zdiv(R, deg);
+    a.zr[p] = R * inv;
   }
   if (lane == 0) a.iters[c] = k;
 }
 
 // ---------------------------------------------------------------------------
-// one CTA per component of 33..kCtaCompMax vertices
+// one CTA of 1024 threads per component of 33..kCtaCompMax vertices, one row
+// per thread (two at most).  The component's internal in-edges are staged in
+// shared memory as 16-bit local indices with local row offsets, next to R
+// and the double-buffered z, so the series runs from shared memory only.  A
+// component with more internal edges than the staging area reads its
+// indices from global memory instead.
 // ---------------------------------------------------------------------------
-constexpr int kRpt = kCtaCompMax / kBlock;  // rows per thread
+constexpr int kCtaThreads = 1024;
+constexpr int kCtaEdgeCap = 24576;  // two CTAs fit in one SM's shared memory
+constexpr int kCtaRows = kCtaCompMax / kCtaThreads;
+constexpr size_t kCtaSmem = (size_t)kCtaCompMax * (3 * sizeof(double) + sizeof(int)) + sizeof(int) +
+                            (size_t)kCtaEdgeCap * sizeof(uint16_t);
 
-__global__ void __launch_bounds__(kBlock) solve_cta_k(SolveArgs a, int32_t cbeg) {
-  __shared__ double z[kCtaCompMax];
-  __shared__ double red[kBlock / 32];
+__global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t cbeg) {
+  extern __shared__ double sm[];
+  double* Rs = sm;
+  double* z = sm + kCtaCompMax;
+  double* iv = sm + 2 * kCtaCompMax;
+  int* ip = reinterpret_cast<int*>(sm + 3 * kCtaCompMax);  // [sz+1] local edge offsets
+  uint16_t* ix = reinterpret_cast<uint16_t*>(ip + kCtaCompMax + 1);
+  __shared__ double red[kCtaThreads / 32];
   const int c = cbeg + (int)blockIdx.x;
   const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
-  double W[kRpt], Rr[kRpt];
-  int deg[kRpt];
-#pragma unroll
-  for (int r = 0; r < kRpt; r++) {
-    const int i = threadIdx.x + r * kBlock;
-    W[r] = 0.0;
-    deg[r] = 0;
-    if (i < sz) {
-      const int p = off + i;
-      deg[r] = a.p_outdeg[p];
-      double g = 0.0;
-      for (int e = a.ext_ptr[p]; e < a.ext_ptr[p + 1]; e++) g += a.zr[a.ext_idx[e]];
-      W[r] = check_u(a, a.u[a.perm[p]]) + a.c * g;
-    }
-    Rr[r] = W[r];
+  const int ib = a.int_ptr[off];
+  const int m = a.int_ptr[off + sz] - ib;
+  const bool staged = m <= kCtaEdgeCap;
+  const bool scc = a.c_type[c] == PR_TYPE_SCC;
+  for (int i = threadIdx.x; i <= sz; i += blockDim.x) ip[i] = a.int_ptr[off + i] - ib;
+  if (staged)
+    for (int e = threadIdx.x; e < m; e += blockDim.x) ix[e] = (uint16_t)local_or_err(a, a.int_idx[ib + e] - off, sz);
+  // inflow gather: W = u + c * sum over external in-edges
+  for (int i = threadIdx.x; i < sz; i += blockDim.x) {
+    const int p = off + i;
+    double g = 0.0;
+    for (int e = a.ext_ptr[p]; e < a.ext_ptr[p + 1]; e++) g += a.zr[a.ext_idx[e]];
+    const double inv = a.p_inv[p];
+    const double W = check_u(a, a.u[a.perm[p]]) + a.c * g;
+    iv[i] = inv;
+    Rs[i] = W;
+    z[i] = W * inv;
   }
+  __syncthreads();
+  auto row_sum = [&](int i) -> double {
+    double acc = 0.0;
+    const int e0 = ip[i], e1 = ip[i + 1];
+    if (staged) {
+#pragma unroll 4
+      for (int e = e0; e < e1; e++) acc += z[ix[e]];
+    } else {
+      for (int e = e0; e < e1; e++) acc += z[local_or_err(a, a.int_idx[ib + e] - off, sz)];
+    }
+    return acc;
+  };
   int k = 0;
-  if (a.c_type[c] == PR_TYPE_CAC) {
+  if (!scc) {
+    // CAC: one pass, sub-level by sub-level (topological order)
     const int sb = a.c_sub[c], se = a.c_sub[c + 1];
-    for (int s = sb; s < se; s++) {
-      const int lo = a.sub_ptr[s] - off, hi = a.sub_ptr[s + 1] - off;
-#pragma unroll
-      for (int r = 0; r < kRpt; r++) {
-        const int i = threadIdx.x + r * kBlock;
-        if (i >= lo && i < hi) {
-          const int p = off + i;
-          double acc = 0.0;
-          for (int e = a.int_ptr[p]; e < a.int_ptr[p + 1]; e++) acc += z[local_or_err(a, a.int_idx[e] - off, sz)];
-          Rr[r] = W[r] + a.c * acc;
-          z[i] = zdiv(Rr[r], deg[r]);
-        }
+    for (int s2 = sb; s2 < se; s2++) {
+      const int lo = a.sub_ptr[s2] - off, hi = a.sub_ptr[s2 + 1] - off;
+      for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double Rv = Rs[i] + a.c * row_sum(i);
+        Rs[i] = Rv;
+        z[i] = Rv * iv[i];
       }
       __syncthreads();
     }
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const int fixed = a.replay ? a.replay[c] : -1;
-#pragma unroll
-    for (int r = 0; r < kRpt; r++) {
-      const int i = threadIdx.x + r * kBlock;
-      if (i < sz) z[i] = zdiv(W[r], deg[r]);
-    }
-    __syncthreads();
     for (;;) {
-      double pn[kRpt];
+      double pn[kCtaRows];
       double local = 0.0;
 #pragma unroll
-      for (int r = 0; r < kRpt; r++) {
-        const int i = threadIdx.x + r * kBlock;
-        pn[r] = 0.0;
-        if (i < sz) {
-          const int p = off + i;
-          double acc = 0.0;
-          for (int e = a.int_ptr[p]; e < a.int_ptr[p + 1]; e++) acc += z[local_or_err(a, a.int_idx[e] - off, sz)];
-          pn[r] = a.c * acc;
-        }
+      for (int r = 0; r < kCtaRows; r++) {
+        const int i = threadIdx.x + r * kCtaThreads;
+        pn[r] = i < sz ? a.c * row_sum(i) : 0.0;
       }
-      __syncthreads();
+      __syncthreads();  // every row has read z before it is overwritten
 #pragma unroll
-      for (int r = 0; r < kRpt; r++) {
-        const int i = threadIdx.x + r * kBlock;
+      for (int r = 0; r < kCtaRows; r++) {
+        const int i = threadIdx.x + r * kCtaThreads;
         if (i < sz) {
-          z[i] = zdiv(pn[r], deg[r]);
-          Rr[r] += pn[r];
+          Rs[i] += pn[r];
+          z[i] = pn[r] * iv[i];
           local = a.norm == PR_NORM_L1 ? local + pn[r] : fmax(local, pn[r]);
         }
       }
-      // block_sum / block_max end with __syncthreads, which also publishes z
-      const double s = a.norm == PR_NORM_L1 ? block_sum(local, red) : block_max(local, red);
+      // the reduction ends with __syncthreads, which also publishes z
+      const double s2 = a.norm == PR_NORM_L1 ? block_sum(local, red) : block_max(local, red);
       k++;
       if (fixed >= 0) {
         if (k >= fixed) break;
         continue;
       }
-      if (!keep_going(s, tau, a.norm)) break;
+      if (!keep_going(s2, tau, a.norm)) break;
       if (k >= a.max_iter) {
         if (threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
         break;
       }
     }
   }
-#pragma unroll
-  for (int r = 0; r < kRpt; r++) {
-    const int i = threadIdx.x + r * kBlock;
-    if (i < sz) {
-      a.R[off + i] = Rr[r];
-      a.zr[off + i] = zdiv(Rr[r], deg[r]);
-    }
+  for (int i = threadIdx.x; i < sz; i += blockDim.x) {
+    a.R[off + i] = Rs[i];
+    a.zr[off + i] = Rs[i] * iv[i];
   }
   if (threadIdx.x == 0) a.iters[c] = k;
 }
@@ -232,7 +252,7 @@ __global__ void __launch_bounds__(kBlock) solve_single_k(SolveArgs a, int32_t vb
     if (p < vend && lane8 == 0) {
       const double W = check_u(a, a.u[a.perm[p]]) + a.c * acc;
       a.R[p] = W;
-      a.zr[p] = zdiv(W, a.p_outdeg[p]);
+      a.zr[p] = W * a.p_inv[p];
     }
   }
 }
@@ -258,51 +278,44 @@ __device__ __forceinline__ void gather_rows(const SolveArgs& a, int off, int sz,
     if (i < sz && lane == 0) {
       const double W = check_u(a, a.u[a.perm[p]]) + a.c * acc;
       a.R[p] = W;
-      if (z0) z0[i] = zdiv(W, a.p_outdeg[p]);
+      if (z0) z0[i] = W * a.p_inv[p];
     }
   }
 }
 
 __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeComp L, double* zA, double* zB,
-                                                            double* part) {
+                                                            double* part, HeavyRows hv, HeavyScratch hs) {
   __shared__ double red[kBlock / 32];
   const int off = L.off, sz = L.size;
+  const int nlight = sz - hv.nheavy;
+  const int* lorder = a.lorder + off;
   gather_rows(a, off, sz, zA);
   if (!grid_sync(a.ctl, 310)) return;
   const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
   const int fixed = a.replay ? a.replay[L.c] : -1;
-  const int lane = threadIdx.x & (kG - 1);
-  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kG;
-  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / kG;
-  const int64_t wb = g0 - ((threadIdx.x & 31) / kG);
+  const bool l1 = a.norm == PR_NORM_L1;
   int k = 0;
   for (;;) {
     const double* cur = (k & 1) ? zB : zA;
     double* nxt = (k & 1) ? zA : zB;
     double local = 0.0;
-    for (int64_t base = wb; base < sz; base += ng) {
-      const int64_t i = base + ((threadIdx.x & 31) / kG);
-      const int p = off + (int)i;
-      double acc = 0.0;
-      if (i < sz)
-        for (int e = a.int_ptr[p] + lane; e < a.int_ptr[p + 1]; e += kG)
-          acc += cur[local_or_err(a, a.int_idx[e] - off, sz)];
-      acc = group_sum<kG>(acc);
-      if (i < sz && lane == 0) {
-        const double pn = a.c * acc;
-        a.R[p] += pn;
-        nxt[i] = zdiv(pn, a.p_outdeg[p]);
-        local = a.norm == PR_NORM_L1 ? local + pn : fmax(local, pn);
-      }
-    }
-    const double bs = a.norm == PR_NORM_L1 ? block_sum(local, red) : block_max(local, red);
+    auto fin = [&](int row, double acc, bool heavy) -> double {
+      const double pn = a.c * acc;
+      a.R[row] += pn;
+      nxt[row - off] = pn * a.p_inv[row];
+      if (!heavy) local = fold2(local, pn, l1);
+      return pn;
+    };
+    auto val = [&](int e) -> double { return cur[local_or_err(a, a.int_idx[e] - off, sz)]; };
+    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, k & 1, l1, fin, val);
+    const double bs = l1 ? block_sum(local, red) : block_max(local, red);
     double* slot = part + (size_t)(k & 1) * gridDim.x;
     if (threadIdx.x == 0) slot[blockIdx.x] = bs;
     if (!grid_sync(a.ctl, 311)) return;
     double t = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      t = a.norm == PR_NORM_L1 ? t + slot[b] : fmax(t, slot[b]);
-    const double s = a.norm == PR_NORM_L1 ? block_sum(t, red) : block_max(t, red);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t = fold2(t, __ldcg(&slot[b]), l1);
+    double s = l1 ? block_sum(t, red) : block_max(t, red);
+    if (hv.nheavy > 0) s = fold2(s, __ldcg(&hs.total[k & 1]), l1);
     k++;
     if (fixed >= 0) {
       if (k >= fixed) break;
@@ -315,7 +328,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
     }
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x)
-    a.zr[off + i] = zdiv(a.R[off + i], a.p_outdeg[off + i]);
+    a.zr[off + i] = a.R[off + i] * a.p_inv[off + i];
   if (blockIdx.x == 0 && threadIdx.x == 0) a.iters[L.c] = k;
 }
 
@@ -338,7 +351,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_cac_k(SolveArgs a, LargeCo
       if (p < hi && lane == 0) {
         const double Rv = a.R[p] + a.c * acc;
         a.R[p] = Rv;
-        a.zr[p] = zdiv(Rv, a.p_outdeg[p]);
+        a.zr[p] = Rv * a.p_inv[p];
       }
     }
     if (!grid_sync(a.ctl, 321)) return;
@@ -375,7 +388,7 @@ static unsigned grid_cap(int64_t blocks) {
 
 pr_status run_solve(const pr_partition_s* P, double c, const double* u, double tol, int norm, int max_iter,
                     const int32_t* replay, double* R, int32_t* iters_dev, Arena& tmp, Ctl* ctl,
-                    int64_t* launches) {
+                    int64_t* launches, KernelTiming* timing) {
   cudaStream_t s = tmp.stream();
   const int32_t n = P->g.n;
   int64_t nl = 0;
@@ -392,6 +405,8 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
   a.u = u;
   a.perm = P->perm;
   a.p_outdeg = P->p_outdeg;
+  a.p_inv = P->p_inv;
+  a.lorder = P->lorder;
   a.int_ptr = P->int_ptr;
   a.int_idx = P->int_idx;
   a.ext_ptr = P->ext_ptr;
@@ -406,10 +421,17 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
   PRGB_TRY(tmp.alloc(&a.R, n));
   PRGB_TRY(tmp.alloc(&a.zr, n));
   double *zA = nullptr, *zB = nullptr, *part = nullptr;
+  HeavyScratch hs;
   if (P->max_large > 0) {
     PRGB_TRY(tmp.alloc(&zA, P->max_large));
     PRGB_TRY(tmp.alloc(&zB, P->max_large));
     PRGB_TRY(tmp.alloc(&part, (size_t)2 * num_sms() * 8));
+    PRGB_TRY(alloc_heavy_scratch(&hs, P->max_heavy, P->max_chunks, tmp));
+  }
+  static bool cta_attr = false;
+  if (!cta_attr) {
+    PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
+    cta_attr = true;
   }
   size_t li_large = 0;
   for (size_t li = 0; li < P->levels.size(); li++) {
@@ -418,8 +440,26 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       LargeComp L = P->large[li_large++];
       PRGB_TRY(reset_ctl(ctl, s));
       if (L.type == PR_TYPE_SCC) {
-        void* args[] = {&a, &L, &zA, &zB, &part};
+        HeavyRows hv;
+        hv.rows = P->heavy_rows + L.heavy_begin;
+        hv.choff = P->heavy_choff + L.heavy_begin;
+        hv.chrow = P->heavy_chrow;
+        hv.nheavy = L.heavy_end - L.heavy_begin;
+        hv.nchunks = L.chunk_end - L.chunk_begin;
+        hv.cbase = L.chunk_begin;
+        hv.hbase = L.heavy_begin;
+        void* args[] = {&a, &L, &zA, &zB, &part, &hv, &hs};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timing) {
+          PRGB_CUDA(cudaEventCreate(&e0));
+          timing->start.push_back(e0);
+          PRGB_CUDA(cudaEventCreate(&e1));
+          timing->stop.push_back(e1);
+          timing->comps.push_back(L);
+          PRGB_CUDA(cudaEventRecord(e0, s));
+        }
         PRGB_TRY(launch_coop((const void*)solve_large_scc_k, kBlock, 0, s, args, 4, nullptr));
+        if (timing) PRGB_CUDA(cudaEventRecord(e1, s));
       } else {
         void* args[] = {&a, &L};
         PRGB_TRY(launch_coop((const void*)solve_large_cac_k, kBlock, 0, s, args, 4, nullptr));
@@ -427,7 +467,7 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       nl++;
     }
     if (r.warp > r.cta) {
-      solve_cta_k<<<r.warp - r.cta, kBlock, 0, s>>>(a, r.cta);
+      solve_cta_k<<<r.warp - r.cta, kCtaThreads, kCtaSmem, s>>>(a, r.cta);
       PRGB_LAUNCH();
       nl++;
     }
