@@ -224,6 +224,31 @@ pr_status pr_residual_l1(const pr_graph *g, double c, const double *u, const dou
  * entry points, all threads).  Lets a caller count the kernels of a region. */
 int64_t pr_launch_count(void);
 
+/*
+ * pr_residual_l1_static -- the same L1 residual as pr_residual_l1, for
+ * callers that cannot allocate device memory (for example code running
+ * inside another framework's memory manager, which owns all device memory,
+ * or a latency-critical path where cudaMalloc / cudaFree would synchronise
+ * the device).  The paper has no counterpart; this is a service of the
+ * library.
+ *   g        : CSR with DEVICE arrays (on_host must be 0), n <= PR_STATIC_MAX_N.
+ *   c, u, R  : as for pr_residual_l1 (u, R device pointers, original order).
+ *   out_host : receives the residual.
+ * It allocates nothing: its scratch is a fixed array in the library's device
+ * data segment (PR_STATIC_MAX_N doubles plus 8 KB), which every GPU that
+ * loads the library holds until the process exits.  The first call on a
+ * device looks up that array's device address; make that first call before
+ * any stream capture.  Every call shares the array (each call clears what it
+ * uses); calls that overlap on the GPU race on it, so serialise them.  The
+ * in-flow is accumulated with atomic adds, so the last bits can differ from
+ * pr_residual_l1 and from call to call.
+ * Errors: PR_EINVAL for n > PR_STATIC_MAX_N, on_host = 1, NULL pointers, or a
+ * row or column index out of range; PR_ECUDA.  Synchronises the stream.
+ */
+#define PR_STATIC_MAX_N 1048576
+pr_status pr_residual_l1_static(const pr_csr *g, double c, const double *u, const double *R,
+                                double *out_host, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *pr_status_str(pr_status s);
 

@@ -84,7 +84,11 @@ _SIGS = {
     "pr_status_str": (C.c_char_p, [C.c_int]),
     "pr_last_cuda_error": (C.c_int, []),
     "pr_launch_count": (C.c_int64, []),
+    "pr_residual_l1_static": (C.c_int, [C.POINTER(_Csr), C.c_double, C.c_void_p, C.c_void_p,
+                                        C.POINTER(C.c_double), C.c_void_p]),
 }
+
+STATIC_MAX_N = 1 << 20
 
 
 def library_path():
@@ -321,4 +325,22 @@ def residual_l1(g: Graph, c, u, R):
     _check(lib.pr_residual_l1(g.handle, float(c), ud.data_ptr() if g.n else None,
                               Rd.data_ptr() if g.n else None, C.byref(out), _stream()),
            "pr_residual_l1")
+    return out.value
+
+
+def residual_l1_static(rowptr, col, c, u, R):
+    """The L1 residual through pr_residual_l1_static, which allocates no device
+    memory (for callers that cannot allocate); all arguments on the device,
+    n <= STATIC_MAX_N."""
+    lib = load_library()
+    rp = _dev_i32(rowptr)
+    cl = _dev_i32(col)
+    ud = _dev_f64(u)
+    Rd = _dev_f64(R)
+    n = rp.shape[0] - 1
+    csr = _Csr(n, cl.shape[0], rp.data_ptr(), cl.data_ptr() if cl.numel() else None, 0)
+    out = C.c_double(0.0)
+    _check(lib.pr_residual_l1_static(C.byref(csr), float(c), ud.data_ptr() if n else None,
+                                     Rd.data_ptr() if n else None, C.byref(out), _stream()),
+           "pr_residual_l1_static")
     return out.value
