@@ -126,6 +126,37 @@ __device__ __forceinline__ double group_max(double v) {
   return v;
 }
 
+template <int G>
+__device__ __forceinline__ float group_sumf(float v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int G>
+__device__ __forceinline__ float group_maxf(float v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide FP32 sum / max (fixed tree); scratch: blockDim/32 floats.
+__device__ __forceinline__ float block_sumf(float v, float* scratch, bool is_max) {
+  v = is_max ? group_maxf<32>(v) : group_sumf<32>(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  float t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0f;
+  if (w == 0) t = is_max ? group_maxf<32>(t) : group_sumf<32>(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  const float r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
 // Block-wide sum with a fixed reduction tree (deterministic for a fixed
 // blockDim).  scratch: at least blockDim/32 doubles of shared memory.
 __device__ __forceinline__ double block_sum(double v, double* scratch) {
@@ -317,15 +348,21 @@ struct LargeComp {
 };
 
 // per level (in processing order): component ranges by class
-//   [cbeg, cta) large, [cta, warp) one CTA each, [warp, single) one warp
-//   each, [single, cend) 1-vertex components
+//   [cbeg, clu) grid-wide, [clu, cta) one cluster of CTAs each, [cta, warp)
+//   one CTA each, [warp, single) one warp each, [single, cend) 1-vertex
 struct LevelRange {
-  int32_t cbeg, cta, warp, single, cend;
+  int32_t cbeg, clu, cta, warp, single, cend;
+  int32_t clu_max;              // vertices of the largest cluster-class component
   int32_t vbeg, vsingle, vend;  // permuted vertex range of the level / its singletons
+  // rows of the level with more than kHeavy external in-edges: a slice of
+  // the partition's external heavy-row list, and its chunk range
+  int32_t xh_begin, xh_end, xc_begin, xc_end;
 };
 
-constexpr int kWarpCompMax = 32;    // components of <= 32 vertices: one warp
-constexpr int kCtaCompMax = 2048;   // components of <= 2048 vertices: one CTA
+constexpr int kWarpCompMax = 32;     // components of <= 32 vertices: one warp
+constexpr int kCtaCompMax = 256;     // <= 256 vertices: one CTA
+constexpr int kCluCompMax = 16384;   // <= 16384 vertices: one cluster of 8 CTAs
+constexpr int kNumClasses = 5;       // grid-wide, cluster, CTA, warp, 1-vertex
 
 }  // namespace prgb
 
@@ -364,6 +401,12 @@ struct pr_partition_s {
   int32_t* heavy_chrow = nullptr;
   int32_t* lorder = nullptr;       // [n] positions by (component, internal in-degree class)
   double* p_inv = nullptr;         // [n] 1/outdeg by position
+  int32_t* xheavy_rows = nullptr;  // positions with > kHeavy external in-edges
+  int32_t* xheavy_choff = nullptr;
+  int32_t* xheavy_chrow = nullptr;
+  int32_t nxheavy = 0, nxchunks = 0;
+  int32_t max_xheavy = 0, max_xchunks = 0;  // largest slice over the levels
+  int32_t* xlorder = nullptr;      // [n] positions by (level, external in-degree class)
   int32_t nheavy = 0, nchunks = 0;
   int32_t max_heavy = 0, max_chunks = 0;  // largest slice over the large components
   std::vector<prgb::LevelRange> levels;  // host, processing order

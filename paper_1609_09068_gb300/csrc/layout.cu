@@ -155,10 +155,11 @@ __global__ void edge_fill_k(int32_t n, const int32_t* perm, const int32_t* pos, 
 }
 
 __device__ __forceinline__ int size_class(int sz) {
-  if (sz > kCtaCompMax) return 0;
-  if (sz > kWarpCompMax) return 1;
-  if (sz > 1) return 2;
-  return 3;
+  if (sz > kCluCompMax) return 0;
+  if (sz > kCtaCompMax) return 1;
+  if (sz > kWarpCompMax) return 2;
+  if (sz > 1) return 3;
+  return 4;
 }
 
 __global__ void level_begin_k(int32_t K, const int32_t* c_level, int32_t maxl, int32_t* lvl_cbeg) {
@@ -167,11 +168,11 @@ __global__ void level_begin_k(int32_t K, const int32_t* c_level, int32_t maxl, i
 }
 
 __global__ void class_begin_k(int32_t K, const int32_t* c_level, const int32_t* c_off, int32_t maxl,
-                              int32_t* cls /* [nlev][4] */) {
+                              int32_t* cls /* [nlev][kNumClasses] */) {
   for (int64_t c = gtid(); c < K; c += gstride()) {
     const int li = maxl - c_level[c];
     const int cl = size_class(c_off[c + 1] - c_off[c]);
-    for (int k = 1; k <= cl; k++) atomicMin(&cls[li * 4 + k], (int)c);
+    for (int k = 1; k <= cl; k++) atomicMin(&cls[li * kNumClasses + k], (int)c);
   }
 }
 
@@ -181,10 +182,12 @@ __global__ void level_ranges_k(int32_t nlev, int32_t K, const int32_t* lvl_cbeg,
     LevelRange r;
     r.cbeg = lvl_cbeg[li];
     r.cend = lvl_cbeg[li + 1];
-    r.cta = min(cls[li * 4 + 1], r.cend);
-    r.warp = min(cls[li * 4 + 2], r.cend);
-    r.single = min(cls[li * 4 + 3], r.cend);
-    const bool ok = r.cbeg >= 0 && r.cbeg <= K && r.cend >= 0 && r.cend <= K && r.single >= 0;
+    r.clu = min(cls[li * kNumClasses + 1], r.cend);
+    r.cta = min(cls[li * kNumClasses + 2], r.cend);
+    r.warp = min(cls[li * kNumClasses + 3], r.cend);
+    r.single = min(cls[li * kNumClasses + 4], r.cend);
+    const bool ok = r.cbeg >= 0 && r.cbeg <= K && r.cend >= 0 && r.cend <= K && r.single >= 0 && r.clu >= 0;
+    r.clu_max = (ok && r.cta > r.clu) ? c_off[r.clu + 1] - c_off[r.clu] : 0;
     // a missing level leaves -1 here; the host check rejects it
     r.vbeg = ok ? c_off[r.cbeg] : -1;
     r.vsingle = ok ? c_off[r.single] : -1;
@@ -195,6 +198,10 @@ __global__ void level_ranges_k(int32_t nlev, int32_t K, const int32_t* lvl_cbeg,
 
 __global__ void pos_comp_k(int32_t n, const int32_t* perm, const int32_t* comp_id, int32_t* pc) {
   for (int64_t p = gtid(); p < n; p += gstride()) pc[p] = comp_id[perm[p]];
+}
+
+__global__ void pos_level_k(int32_t n, const int32_t* perm, const int32_t* level, int32_t maxl, int32_t* pl) {
+  for (int64_t p = gtid(); p < n; p += gstride()) pl[p] = maxl - level[perm[p]];
 }
 
 __global__ void large_flags_k(int32_t K, const int32_t* c_off, uint8_t* flag) {
@@ -341,13 +348,13 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   int32_t *lvl_cbeg, *cls;
   LevelRange* dlev;
   PRGB_TRY(tmp.alloc(&lvl_cbeg, (size_t)nlev + 1));
-  PRGB_TRY(tmp.alloc(&cls, (size_t)nlev * 4));
+  PRGB_TRY(tmp.alloc(&cls, (size_t)nlev * kNumClasses));
   PRGB_TRY(tmp.alloc(&dlev, nlev));
   PRGB_CUDA(cudaMemsetAsync(lvl_cbeg, 0xff, ((size_t)nlev + 1) * 4, s));
   level_begin_k<<<grid1(K), kBlock, 0, s>>>(K, c_level, maxl, lvl_cbeg);
   PRGB_LAUNCH();
   PRGB_CUDA(cudaMemcpyAsync(lvl_cbeg + nlev, &K, 4, cudaMemcpyHostToDevice, s));
-  PRGB_CUDA(cudaMemsetAsync(cls, 0x7f, (size_t)nlev * 16, s));
+  PRGB_CUDA(cudaMemsetAsync(cls, 0x7f, (size_t)nlev * kNumClasses * 4, s));
   class_begin_k<<<grid1(K), kBlock, 0, s>>>(K, c_level, P->c_off, maxl, cls);
   PRGB_LAUNCH();
   level_ranges_k<<<grid1(nlev), kBlock, 0, s>>>(nlev, K, lvl_cbeg, cls, P->c_off, dlev);
@@ -406,11 +413,36 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
       P->max_chunks = std::max(P->max_chunks, L.chunk_end - L.chunk_begin);
     }
   }
+  // rows with many external in-edges (the inflow gather of Eq. PR:levels)
+  // and the light rows of each level ordered by external in-degree class
+  {
+    PRGB_TRY(build_heavy(P->ext_ptr, n, keep, tmp, &P->xheavy_rows, &P->xheavy_choff, &P->xheavy_chrow,
+                         &P->nxheavy, &P->nxchunks));
+    int32_t* pl;
+    PRGB_TRY(tmp.alloc(&pl, n));
+    pos_level_k<<<grid1(n), kBlock, 0, s>>>(n, P->perm, P->level, maxl, pl);
+    PRGB_LAUNCH();
+    PRGB_TRY(build_lorder(P->ext_ptr, n, pl, nlev - 1, keep, tmp, &P->xlorder));
+    std::vector<int32_t> xrows(P->nxheavy), xcho(P->nxheavy + 1);
+    if (P->nxheavy > 0)
+      PRGB_CUDA(cudaMemcpyAsync(xrows.data(), P->xheavy_rows, (size_t)P->nxheavy * 4, cudaMemcpyDeviceToHost, s));
+    PRGB_CUDA(cudaMemcpyAsync(xcho.data(), P->xheavy_choff, ((size_t)P->nxheavy + 1) * 4, cudaMemcpyDeviceToHost, s));
+    PRGB_CUDA(cudaStreamSynchronize(s));
+    for (LevelRange& r : P->levels) {
+      r.xh_begin = (int32_t)(std::lower_bound(xrows.begin(), xrows.end(), r.vbeg) - xrows.begin());
+      r.xh_end = (int32_t)(std::lower_bound(xrows.begin(), xrows.end(), r.vend) - xrows.begin());
+      r.xc_begin = xcho[r.xh_begin];
+      r.xc_end = xcho[r.xh_end];
+      P->max_xheavy = std::max(P->max_xheavy, r.xh_end - r.xh_begin);
+      P->max_xchunks = std::max(P->max_xchunks, r.xc_end - r.xc_begin);
+    }
+  }
   // host-side consistency checks of everything the solver will index with
   int32_t prev_end = 0, prev_vend = 0;
   for (int32_t li = 0; li < nlev; li++) {
     const LevelRange& r = P->levels[li];
-    const bool ok = r.cbeg == prev_end && r.cbeg <= r.cta && r.cta <= r.warp && r.warp <= r.single &&
+    const bool ok = r.cbeg == prev_end && r.cbeg <= r.clu && r.clu <= r.cta && r.cta <= r.warp && r.warp <= r.single &&
+                    r.clu_max >= 0 && r.clu_max <= kCluCompMax &&
                     r.single <= r.cend && r.cend <= K && r.cend > r.cbeg && r.vbeg == prev_vend &&
                     r.vbeg <= r.vsingle && r.vsingle <= r.vend && r.vend <= n && r.vend - r.vsingle == r.cend - r.single;
     if (!ok) return PR_EINTERNAL;
@@ -420,12 +452,12 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   if (prev_end != K || prev_vend != n) return PR_EINTERNAL;
   int32_t prev_li = 0;
   for (const LargeComp& L : P->large) {
-    if (L.c < 0 || L.c >= K || L.off < 0 || L.size <= kCtaCompMax || (int64_t)L.off + L.size > n ||
+    if (L.c < 0 || L.c >= K || L.off < 0 || L.size <= kCluCompMax || (int64_t)L.off + L.size > n ||
         L.sub_begin < 0 || L.sub_begin >= L.sub_end || L.sub_end > S || L.level_idx < prev_li ||
         L.level_idx >= nlev)
       return PR_EINTERNAL;
     const LevelRange& r = P->levels[L.level_idx];
-    if (L.c < r.cbeg || L.c >= r.cta) return PR_EINTERNAL;
+    if (L.c < r.cbeg || L.c >= r.clu) return PR_EINTERNAL;
     prev_li = L.level_idx;
   }
   return PR_OK;

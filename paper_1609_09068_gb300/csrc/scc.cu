@@ -146,6 +146,87 @@ __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __re
   }
 }
 
+// ---- FW-BW for the largest SCC ---------------------------------------------
+// pivot: the unassigned vertex with the largest in-degree x out-degree
+__global__ void pivot_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ iptr, int32_t n,
+                        const int32_t* __restrict__ rep, unsigned long long* best) {
+  unsigned long long loc = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (rep[v] >= 0) continue;
+    const long long p = (long long)(optr[v + 1] - optr[v]) * (long long)(iptr[v + 1] - iptr[v]);
+    const unsigned long long key = ((unsigned long long)(p > 0x7fffffffLL ? 0x7fffffffLL : p) << 32) |
+                                   (unsigned long long)(uint32_t)v;
+    loc = key > loc ? key : loc;
+  }
+  if (loc) atomicMax(best, loc);
+}
+
+// Reachability from pivot among unassigned vertices: mark[v] = tag for every
+// vertex reached along (ptr, idx); when need is set, only vertices with
+// need[v] == tag_need are entered (the backward pass stays inside the
+// forward set).
+__global__ void reach_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n, int pivot,
+                        const int32_t* __restrict__ rep, int32_t* mark, int tag, const int32_t* __restrict__ need,
+                        int tag_need, int* fav, int* fac, int* fbv, int* fbc, int cap, Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int gw = gwarp(), nw = nwarps();
+  if (gw == 0) {
+    const int nch = nchunks_of(ptr[pivot + 1] - ptr[pivot]);
+    if (lane == 0) mark[pivot] = tag;
+    warp_push(lane == 0 && nch > 0, pivot, nch, fav, fac, &ctl->cnt[0], cap, ctl);
+  }
+  if (!grid_sync(ctl, 120)) return;
+  for (int wave = 0;; wave++) {
+    int* cv = (wave & 1) ? fbv : fav;
+    int* cc = (wave & 1) ? fbc : fac;
+    int* nv = (wave & 1) ? fav : fbv;
+    int* nc = (wave & 1) ? fac : fbc;
+    const int ccur = wave % 3, cnxt = (wave + 1) % 3, cclr = (wave + 2) % 3;
+    const int cnt = vload(&ctl->cnt[ccur]);
+    if (cnt == 0) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[cclr] = 0;
+    for (int i = gw; i < cnt; i += nw) {
+      const int u = cv[i];
+      const int j = cc[i];
+      const int e0 = ptr[u] + j * kChunkE;
+      const int e1 = min(ptr[u + 1], e0 + kChunkE);
+      for (int base = e0; base < e1; base += 32) {
+        const int e = base + lane;
+        bool want = false;
+        int w = 0, nch = 0;
+        if (e < e1) {
+          w = idx[e];
+          if (rep[w] < 0 && (need == nullptr || need[w] == tag_need) && atomicExch(&mark[w], tag) != tag) {
+            nch = nchunks_of(ptr[w + 1] - ptr[w]);
+            want = nch > 0;
+          }
+        }
+        warp_push(want, w, nch, nv, nc, &ctl->cnt[cnxt], cap, ctl);
+      }
+    }
+    if (!grid_sync(ctl, 121)) return;
+  }
+}
+
+// the SCC of the pivot is F and B: find its largest id, then assign it and
+// split the rest into "in F" / "not in F" pieces for the signature rounds
+__global__ void fwbw_max_k(int32_t n, const int32_t* fw, const int32_t* bw, int* best) {
+  int loc = -1;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    if (fw[v] == 1 && bw[v] == 2) loc = (int)v;
+  if (loc >= 0) atomicMax(best, loc);
+}
+
+__global__ void fwbw_assign_k(int32_t n, const int32_t* fw, const int32_t* bw, const int* best, int32_t* rep,
+                              int32_t* pin) {
+  const int r = *best;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (rep[v] >= 0) continue;
+    if (fw[v] == 1 && bw[v] == 2) rep[v] = r;
+    else pin[v] = fw[v] == 1 ? -2 : -1;
+  }
+}
+
 __global__ void assign_k(int32_t n, int32_t* rep, int32_t* pin, int32_t* pout, const int32_t* sin,
                          const int32_t* sout, Ctl* ctl) {
   int left = 0;
@@ -197,6 +278,45 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
     void* args[] = {&gg.optr, &gg.oidx, &gg.iptr, &gg.iidx, &nn, &rem_out, &rem_in, &state, &rep,
                     &fav, &fac, &fbv, &fbc, &cp, &ctl};
     PRGB_TRY(launch_coop((const void*)trim_k, kBlock, 0, s, args, 4, nullptr));
+  }
+  // FW-BW from the best-connected unassigned vertex takes out the giant SCC
+  {
+    unsigned long long* best;
+    int* bmax;
+    int32_t *fw, *bw;
+    PRGB_TRY(tmp.alloc(&best, 1));
+    PRGB_TRY(tmp.alloc(&bmax, 1));
+    PRGB_TRY(tmp.alloc(&fw, n));
+    PRGB_TRY(tmp.alloc(&bw, n));
+    PRGB_CUDA(cudaMemsetAsync(best, 0, 8, s));
+    PRGB_CUDA(cudaMemsetAsync(bmax, 0xff, 4, s));
+    PRGB_CUDA(cudaMemsetAsync(fw, 0, (size_t)n * 4, s));
+    PRGB_CUDA(cudaMemsetAsync(bw, 0, (size_t)n * 4, s));
+    pivot_k<<<grid_n(n), kBlock, 0, s>>>(g.optr, g.iptr, n, rep, best);
+    PRGB_LAUNCH();
+    unsigned long long hb = 0;
+    PRGB_CUDA(cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, s));
+    PRGB_CUDA(cudaStreamSynchronize(s));
+    if (hb != 0) {
+      int pv = (int)(uint32_t)(hb & 0xffffffffu);
+      int32_t nn = n;
+      int cp = cap;
+      for (int dir = 0; dir < 2; dir++) {
+        PRGB_TRY(reset_ctl(ctl, s));
+        const int32_t* ptr = dir == 0 ? g.optr : g.iptr;
+        const int32_t* idx = dir == 0 ? g.oidx : g.iidx;
+        int32_t* mark = dir == 0 ? fw : bw;
+        int tag = dir == 0 ? 1 : 2;
+        const int32_t* need = dir == 0 ? nullptr : fw;
+        int tag_need = 1;
+        void* args[] = {&ptr, &idx, &nn, &pv, &rep, &mark, &tag, &need, &tag_need, &fav, &fac, &fbv, &fbc, &cp, &ctl};
+        PRGB_TRY(launch_coop((const void*)reach_k, kBlock, 0, s, args, 4, nullptr));
+      }
+      fwbw_max_k<<<grid_n(n), kBlock, 0, s>>>(n, fw, bw, bmax);
+      PRGB_LAUNCH();
+      fwbw_assign_k<<<grid_n(n), kBlock, 0, s>>>(n, fw, bw, bmax, rep, pin);
+      PRGB_LAUNCH();
+    }
   }
   for (int round = 0; round < 20000; round++) {
     for (int dir = 0; dir < 2; dir++) {

@@ -18,9 +18,15 @@
 // z = R/outdeg (or P/outdeg during the series) is the only per-vertex vector
 // gathered: A_ij = 1/outdeg(i) depends on the source only, so no edge values
 // are stored.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "common.cuh"
 #include "solve.cuh"
 #include "spmv.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace prgb {
 
@@ -29,6 +35,18 @@ namespace prgb {
 
 __device__ __forceinline__ bool keep_going(double s, double tau, int norm) {
   return norm == PR_NORM_LINF ? (s >= tau) : (s > tau);
+}
+
+// The warp and CTA kernels reduce the stopping norm in FP32: FP64 shuffles
+// and adds cost more than the rows themselves on this part.  The FP32 sum
+// of n non-negative terms is within n * 2^-24 of the FP64 one, so a relative
+// margin of 1e-4 on the test keeps the FP64 norm at or below the threshold
+// whenever the series stops (it may run one iteration longer than an exact
+// test would).
+constexpr double kNormMargin = 1.0 + 1e-4;
+__device__ __forceinline__ bool keep_going32(float s, double tau, int norm) {
+  const double sd = (double)s * kNormMargin;
+  return norm == PR_NORM_LINF ? (sd >= tau) : (sd > tau);
 }
 
 // A local index outside [0, sz) would mean a broken layout: record it and
@@ -52,12 +70,13 @@ __device__ __forceinline__ double check_u(const SolveArgs& a, double uu) {
 // as 8-bit local indices, so each series iteration reads shared memory only.
 // ---------------------------------------------------------------------------
 constexpr int kWarpEdges = kWarpCompMax * (kWarpCompMax - 1);
+constexpr int kWarpBlock = 64;  // two components per block, spread over many SMs
 
-__global__ void __launch_bounds__(kBlock) solve_warp_k(SolveArgs a, int32_t cbeg, int32_t cend) {
-  __shared__ double zsh[kBlock / 32][32];
-  __shared__ uint8_t ish[kBlock / 32][kWarpEdges];
+__global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t cbeg, int32_t cend) {
+  __shared__ double zsh[kWarpBlock / 32][32];
+  __shared__ uint8_t ish[kWarpBlock / 32][kWarpEdges];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int c = cbeg + (int)blockIdx.x * (kBlock / 32) + wib;
+  const int c = cbeg + (int)blockIdx.x * (kWarpBlock / 32) + wib;
   if (c >= cend) return;  // warp-uniform
   double* z = zsh[wib];
   uint8_t* ix = ish[wib];
@@ -69,12 +88,7 @@ __global__ void __launch_bounds__(kBlock) solve_warp_k(SolveArgs a, int32_t cbeg
   const int m = a.int_ptr[off + sz] - ib0;
   for (int e = lane; e < m && e < kWarpEdges; e += 32) ix[e] = (uint8_t)local_or_err(a, a.int_idx[ib0 + e] - off, sz);
   if (m > kWarpEdges) set_err(a.ctl, PR_EINTERNAL, 302);
-  double W = 0.0;
-  if (act) {
-    double g = 0.0;
-    for (int e = a.ext_ptr[p]; e < a.ext_ptr[p + 1]; e++) g += a.zr[a.ext_idx[e]];
-    W = check_u(a, a.u[a.perm[p]]) + a.c * g;
-  }
+  const double W = act ? a.W[p] : 0.0;
   const int ib = act ? a.int_ptr[p] - ib0 : 0, ie = act ? min(a.int_ptr[p + 1] - ib0, kWarpEdges) : 0;
   __syncwarp();
   double R = W;
@@ -97,9 +111,15 @@ __global__ void __launch_bounds__(kBlock) solve_warp_k(SolveArgs a, int32_t cbeg
     if (act) z[lane] = W * inv;
     __syncwarp();
     for (;;) {
-      double acc = 0.0;
-      for (int e = ib; e < ie; e++) acc += z[ix[e]];
-      const double pn = a.c * acc;
+      // two partial sums halve the chain of dependent FP64 adds
+      double acc0 = 0.0, acc1 = 0.0;
+      int e = ib;
+      for (; e + 1 < ie; e += 2) {
+        acc0 += z[ix[e]];
+        acc1 += z[ix[e + 1]];
+      }
+      if (e < ie) acc0 += z[ix[e]];
+      const double pn = a.c * (acc0 + acc1);
       __syncwarp();
       if (act) {
         z[lane] = pn * inv;
@@ -111,8 +131,9 @@ __global__ void __launch_bounds__(kBlock) solve_warp_k(SolveArgs a, int32_t cbeg
         if (k >= fixed) break;
         continue;
       }
-      const double s = a.norm == PR_NORM_L1 ? group_sum<32>(pn) : group_max<32>(pn);
-      if (!keep_going(s, tau, a.norm)) break;
+      const float pf = (float)pn;
+      const float s = a.norm == PR_NORM_L1 ? group_sumf<32>(pf) : group_maxf<32>(pf);
+      if (!keep_going32(s, tau, a.norm)) break;
       if (k >= a.max_iter) {
         if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
         break;
@@ -127,15 +148,15 @@ __global__ void __launch_bounds__(kBlock) solve_warp_k(SolveArgs a, int32_t cbeg
 }
 
 // ---------------------------------------------------------------------------
-// one CTA of 1024 threads per component of 33..kCtaCompMax vertices, one row
-// per thread (two at most).  The component's internal in-edges are staged in
+// one CTA of 256 threads per component of 33..kCtaCompMax vertices, one row
+// per thread.  The component's internal in-edges are staged in
 // shared memory as 16-bit local indices with local row offsets, next to R
 // and the double-buffered z, so the series runs from shared memory only.  A
 // component with more internal edges than the staging area reads its
 // indices from global memory instead.
 // ---------------------------------------------------------------------------
-constexpr int kCtaThreads = 1024;
-constexpr int kCtaEdgeCap = 24576;  // two CTAs fit in one SM's shared memory
+constexpr int kCtaThreads = 256;
+constexpr int kCtaEdgeCap = 8192;
 constexpr int kCtaRows = kCtaCompMax / kCtaThreads;
 constexpr size_t kCtaSmem = (size_t)kCtaCompMax * (3 * sizeof(double) + sizeof(int)) + sizeof(int) +
                             (size_t)kCtaEdgeCap * sizeof(uint16_t);
@@ -147,7 +168,7 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
   double* iv = sm + 2 * kCtaCompMax;
   int* ip = reinterpret_cast<int*>(sm + 3 * kCtaCompMax);  // [sz+1] local edge offsets
   uint16_t* ix = reinterpret_cast<uint16_t*>(ip + kCtaCompMax + 1);
-  __shared__ double red[kCtaThreads / 32];
+  __shared__ float red[kCtaThreads / 32];
   const int c = cbeg + (int)blockIdx.x;
   const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
   const int ib = a.int_ptr[off];
@@ -157,13 +178,11 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
   for (int i = threadIdx.x; i <= sz; i += blockDim.x) ip[i] = a.int_ptr[off + i] - ib;
   if (staged)
     for (int e = threadIdx.x; e < m; e += blockDim.x) ix[e] = (uint16_t)local_or_err(a, a.int_idx[ib + e] - off, sz);
-  // inflow gather: W = u + c * sum over external in-edges
+  // inflow-adjusted weights from the level's gather
   for (int i = threadIdx.x; i < sz; i += blockDim.x) {
     const int p = off + i;
-    double g = 0.0;
-    for (int e = a.ext_ptr[p]; e < a.ext_ptr[p + 1]; e++) g += a.zr[a.ext_idx[e]];
     const double inv = a.p_inv[p];
-    const double W = check_u(a, a.u[a.perm[p]]) + a.c * g;
+    const double W = a.W[p];
     iv[i] = inv;
     Rs[i] = W;
     z[i] = W * inv;
@@ -215,13 +234,13 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
         }
       }
       // the reduction ends with __syncthreads, which also publishes z
-      const double s2 = a.norm == PR_NORM_L1 ? block_sum(local, red) : block_max(local, red);
+      const float s2 = block_sumf((float)local, red, a.norm != PR_NORM_L1);
       k++;
       if (fixed >= 0) {
         if (k >= fixed) break;
         continue;
       }
-      if (!keep_going(s2, tau, a.norm)) break;
+      if (!keep_going32(s2, tau, a.norm)) break;
       if (k >= a.max_iter) {
         if (threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
         break;
@@ -236,25 +255,169 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
 }
 
 // ---------------------------------------------------------------------------
-// collection of 1-vertex components of a level: R = W (8 lanes per vertex)
+// one cluster of kClu CTAs (on kClu SMs) per component of
+// kCtaCompMax+1..kCluCompMax vertices.  Rank r owns the component-local rows
+// [r*chunk, (r+1)*chunk) with chunk a power of two; z lives in distributed
+// shared memory (each rank holds its rows' z, double-buffered), a row reads
+// the z of any rank through the cluster's shared-memory window, and one
+// hardware cluster barrier per iteration publishes the new z and the rank
+// partials of the stopping norm.  This spreads a component's FP64 work over
+// kClu SMs instead of one.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) solve_single_k(SolveArgs a, int32_t vbeg, int32_t vend) {
-  const int lane8 = threadIdx.x & 7;
-  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 3;
-  const int64_t wb = g0 - ((threadIdx.x & 31) >> 3);  // first group of this warp
-  for (int64_t base = wb; base + vbeg < vend; base += ng) {
-    const int64_t p = vbeg + base + ((threadIdx.x & 31) >> 3);
-    double acc = 0.0;
-    if (p < vend)
-      for (int e = a.ext_ptr[p] + lane8; e < a.ext_ptr[p + 1]; e += 8) acc += a.zr[a.ext_idx[e]];
-    acc = group_sum<8>(acc);
-    if (p < vend && lane8 == 0) {
-      const double W = check_u(a, a.u[a.perm[p]]) + a.c * acc;
-      a.R[p] = W;
-      a.zr[p] = W * a.p_inv[p];
+constexpr int kClu = 8;
+constexpr int kCluThreads = 256;
+constexpr int kCluEdgesPerRow = 8;  // staged edges per row (more are read from global memory)
+
+__host__ __device__ __forceinline__ int clu_shift(int sz) {
+  int sh = 0;
+  while ((kClu << sh) < sz) sh++;
+  return sh;
+}
+
+__host__ __device__ __forceinline__ size_t clu_smem(int chunk) {
+  return (size_t)chunk * (4 * sizeof(double) + sizeof(int)) + 2 * sizeof(int) + 2 * sizeof(float) +
+         (size_t)chunk * kCluEdgesPerRow * sizeof(uint16_t);
+}
+
+__global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
+    solve_clu_k(SolveArgs a, int32_t cbeg, int32_t chunk_max) {
+  extern __shared__ double cs[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  double* zA = cs;
+  double* zB = cs + chunk_max;
+  double* Rs = cs + 2 * chunk_max;
+  double* iv = cs + 3 * chunk_max;
+  int* ip = reinterpret_cast<int*>(cs + 4 * chunk_max);         // [chunk_max + 1]
+  float* part = reinterpret_cast<float*>(ip + chunk_max + 2);   // [2]
+  uint16_t* ix = reinterpret_cast<uint16_t*>(part + 2);         // [chunk_max * kCluEdgesPerRow]
+  __shared__ float red[kCluThreads / 32];
+  __shared__ double* remA[kClu];
+  __shared__ double* remB[kClu];
+  __shared__ float* remP[kClu];
+  const int c = cbeg + (int)(blockIdx.x / kClu);
+  const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
+  const int sh = clu_shift(sz);
+  const int chunk = 1 << sh;
+  const int r0 = rank * chunk;
+  const int nr = max(0, min(sz, r0 + chunk) - r0);
+  if (threadIdx.x < kClu) {
+    remA[threadIdx.x] = cl.map_shared_rank(zA, (int)threadIdx.x);
+    remB[threadIdx.x] = cl.map_shared_rank(zB, (int)threadIdx.x);
+    remP[threadIdx.x] = cl.map_shared_rank(part, (int)threadIdx.x);
+  }
+  // stage this rank's rows: local edge offsets and component-local indices
+  const int ib = a.int_ptr[off + r0];
+  const int m = nr > 0 ? a.int_ptr[off + r0 + nr] - ib : 0;
+  const bool staged = m <= chunk_max * kCluEdgesPerRow;
+  for (int i = threadIdx.x; i <= nr; i += blockDim.x) ip[i] = a.int_ptr[off + r0 + i] - ib;
+  if (staged)
+    for (int e = threadIdx.x; e < m; e += blockDim.x) ix[e] = (uint16_t)local_or_err(a, a.int_idx[ib + e] - off, sz);
+  // inflow-adjusted weights of this rank's rows
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    const int p = off + r0 + i;
+    const double inv = a.p_inv[p];
+    const double W = a.W[p];
+    iv[i] = inv;
+    Rs[i] = W;
+    zA[i] = W * inv;
+  }
+  cl.sync();
+  const int mask = chunk - 1;
+  auto row_sum = [&](double* const* rem, int i) -> double {
+    double acc0 = 0.0, acc1 = 0.0;
+    const int e0 = ip[i], e1 = ip[i + 1];
+    int e = e0;
+    if (staged) {
+      for (; e + 1 < e1; e += 2) {
+        const int q0 = ix[e], q1 = ix[e + 1];
+        acc0 += rem[q0 >> sh][q0 & mask];
+        acc1 += rem[q1 >> sh][q1 & mask];
+      }
+      if (e < e1) {
+        const int q = ix[e];
+        acc0 += rem[q >> sh][q & mask];
+      }
+    } else {
+      for (; e < e1; e++) {
+        const int q = local_or_err(a, a.int_idx[ib + e] - off, sz);
+        acc0 += rem[q >> sh][q & mask];
+      }
+    }
+    return acc0 + acc1;
+  };
+  int k = 0;
+  if (a.c_type[c] != PR_TYPE_SCC) {
+    // CAC: one pass, sub-level by sub-level, one cluster barrier each
+    const int sb = a.c_sub[c], se = a.c_sub[c + 1];
+    for (int s2 = sb; s2 < se; s2++) {
+      const int lo = max(a.sub_ptr[s2] - off - r0, 0), hi = min(a.sub_ptr[s2 + 1] - off - r0, nr);
+      for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double Rv = Rs[i] + a.c * row_sum(remA, i);
+        Rs[i] = Rv;
+        zA[i] = Rv * iv[i];
+      }
+      cl.sync();
+    }
+  } else {
+    const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
+    const int fixed = a.replay ? a.replay[c] : -1;
+    const bool is_max = a.norm != PR_NORM_L1;
+    for (;;) {
+      double* const* rem = (k & 1) ? remB : remA;
+      double* nxt = (k & 1) ? zA : zB;
+      float local = 0.0f;
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        const double pn = a.c * row_sum(rem, i);
+        Rs[i] += pn;
+        nxt[i] = pn * iv[i];
+        local = is_max ? fmaxf(local, (float)pn) : local + (float)pn;
+      }
+      const float bs = block_sumf(local, red, is_max);
+      if (threadIdx.x == 0) part[k & 1] = bs;
+      cl.sync();  // publishes nxt and the rank partials
+      float s2 = 0.0f;
+      for (int r = 0; r < kClu; r++) s2 = is_max ? fmaxf(s2, remP[r][k & 1]) : s2 + remP[r][k & 1];
+      k++;
+      if (fixed >= 0) {
+        if (k >= fixed) break;
+        continue;
+      }
+      if (!keep_going32(s2, tau, a.norm)) break;
+      if (k >= a.max_iter) {
+        if (rank == 0 && threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
+        break;
+      }
     }
   }
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    a.R[off + r0 + i] = Rs[i];
+    a.zr[off + r0 + i] = Rs[i] * iv[i];
+  }
+  if (rank == 0 && threadIdx.x == 0) a.iters[c] = k;
+  cl.sync();  // no rank leaves while another may still read its shared memory
+}
+
+// ---------------------------------------------------------------------------
+// inflow gather of one level (Eq. PR:levels as a pull): for every vertex of
+// the level, W = u + c * sum over external in-edges of R_j / outdeg(j), with
+// the balanced sweep (hubs receive tens of thousands of external edges).
+// The level's 1-vertex components are finished here (R = W, Sec. 4.3 item 1).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) gather_level_k(SolveArgs a, LevelRange r, HeavyRows hv,
+                                                         HeavyScratch hs) {
+  auto fin = [&](int row, double acc, bool) -> double {
+    const double W = check_u(a, a.u[a.perm[row]]) + a.c * acc;
+    a.W[row] = W;
+    if (row >= r.vsingle) {
+      a.R[row] = W;
+      a.zr[row] = W * a.p_inv[row];
+    }
+    return 0.0;
+  };
+  auto val = [&](int e) -> double { return a.zr[a.ext_idx[e]]; };
+  const int nlight = (r.vend - r.vbeg) - (r.xh_end - r.xh_begin);
+  balanced_sweep(a.ext_ptr, a.xlorder + r.vbeg, nlight, hv, hs, 0, true, fin, val);
 }
 
 // ---------------------------------------------------------------------------
@@ -262,24 +425,13 @@ __global__ void __launch_bounds__(kBlock) solve_single_k(SolveArgs a, int32_t vb
 // ---------------------------------------------------------------------------
 constexpr int kG = 8;  // lanes per row
 
-// gather W for the rows of a component; R[p] = W and z0[p - off] = W/outdeg
-__device__ __forceinline__ void gather_rows(const SolveArgs& a, int off, int sz, double* z0) {
-  const int lane = threadIdx.x & (kG - 1);
-  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kG;
-  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / kG;
-  const int64_t wb = g0 - ((threadIdx.x & 31) / kG);
-  for (int64_t base = wb; base < sz; base += ng) {
-    const int64_t i = base + ((threadIdx.x & 31) / kG);
+// R[p] = W[p] and z0[p - off] = W/outdeg for the rows of a component
+__device__ __forceinline__ void load_rows(const SolveArgs& a, int off, int sz, double* z0) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
     const int p = off + (int)i;
-    double acc = 0.0;
-    if (i < sz)
-      for (int e = a.ext_ptr[p] + lane; e < a.ext_ptr[p + 1]; e += kG) acc += a.zr[a.ext_idx[e]];
-    acc = group_sum<kG>(acc);
-    if (i < sz && lane == 0) {
-      const double W = check_u(a, a.u[a.perm[p]]) + a.c * acc;
-      a.R[p] = W;
-      if (z0) z0[i] = W * a.p_inv[p];
-    }
+    const double W = a.W[p];
+    a.R[p] = W;
+    if (z0) z0[i] = W * a.p_inv[p];
   }
 }
 
@@ -289,7 +441,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
   const int off = L.off, sz = L.size;
   const int nlight = sz - hv.nheavy;
   const int* lorder = a.lorder + off;
-  gather_rows(a, off, sz, zA);
+  load_rows(a, off, sz, zA);
   if (!grid_sync(a.ctl, 310)) return;
   const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
   const int fixed = a.replay ? a.replay[L.c] : -1;
@@ -333,7 +485,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
 }
 
 __global__ void __launch_bounds__(kBlock) solve_large_cac_k(SolveArgs a, LargeComp L) {
-  gather_rows(a, L.off, L.size, nullptr);  // R[p] = W
+  load_rows(a, L.off, L.size, nullptr);  // R[p] = W
   if (!grid_sync(a.ctl, 320)) return;
   const int lane = threadIdx.x & (kG - 1);
   const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kG;
@@ -418,17 +570,21 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
   a.replay = replay;
   a.iters = iters_dev;
   a.ctl = ctl;
+  a.xlorder = P->xlorder;
   PRGB_TRY(tmp.alloc(&a.R, n));
   PRGB_TRY(tmp.alloc(&a.zr, n));
+  PRGB_TRY(tmp.alloc(&a.W, n));
   double *zA = nullptr, *zB = nullptr, *part = nullptr;
-  HeavyScratch hs;
+  HeavyScratch hs;  // shared by the level gathers and the grid-wide series (left zeroed after each)
+  PRGB_TRY(alloc_heavy_scratch(&hs, std::max(P->max_heavy, P->max_xheavy), std::max(P->max_chunks, P->max_xchunks),
+                               tmp));
   if (P->max_large > 0) {
     PRGB_TRY(tmp.alloc(&zA, P->max_large));
     PRGB_TRY(tmp.alloc(&zB, P->max_large));
     PRGB_TRY(tmp.alloc(&part, (size_t)2 * num_sms() * 8));
-    PRGB_TRY(alloc_heavy_scratch(&hs, P->max_heavy, P->max_chunks, tmp));
   }
   static bool cta_attr = false;
+  static size_t clu_attr = 48 * 1024;
   if (!cta_attr) {
     PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
     cta_attr = true;
@@ -436,6 +592,20 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
   size_t li_large = 0;
   for (size_t li = 0; li < P->levels.size(); li++) {
     const LevelRange& r = P->levels[li];
+    {
+      HeavyRows xv;
+      xv.rows = P->xheavy_rows + r.xh_begin;
+      xv.choff = P->xheavy_choff + r.xh_begin;
+      xv.chrow = P->xheavy_chrow;
+      xv.nheavy = r.xh_end - r.xh_begin;
+      xv.nchunks = r.xc_end - r.xc_begin;
+      xv.cbase = r.xc_begin;
+      xv.hbase = r.xh_begin;
+      const int64_t work = (int64_t)(r.vend - r.vbeg) + (int64_t)xv.nchunks * 32;
+      gather_level_k<<<grid_cap((work + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, r, xv, hs);
+      PRGB_LAUNCH();
+      nl++;
+    }
     while (li_large < P->large.size() && P->large[li_large].level_idx == (int)li) {
       LargeComp L = P->large[li_large++];
       PRGB_TRY(reset_ctl(ctl, s));
@@ -466,6 +636,17 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       }
       nl++;
     }
+    if (r.cta > r.clu) {
+      const int chunk = 1 << clu_shift(r.clu_max);
+      const size_t smem = clu_smem(chunk);
+      if (smem > clu_attr) {
+        PRGB_CUDA(cudaFuncSetAttribute(solve_clu_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        clu_attr = smem;
+      }
+      solve_clu_k<<<(r.cta - r.clu) * kClu, kCluThreads, smem, s>>>(a, r.clu, chunk);
+      PRGB_LAUNCH();
+      nl++;
+    }
     if (r.warp > r.cta) {
       solve_cta_k<<<r.warp - r.cta, kCtaThreads, kCtaSmem, s>>>(a, r.cta);
       PRGB_LAUNCH();
@@ -473,13 +654,7 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
     }
     if (r.single > r.warp) {
       const int nw = r.single - r.warp;
-      solve_warp_k<<<(nw + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(a, r.warp, r.single);
-      PRGB_LAUNCH();
-      nl++;
-    }
-    if (r.vend > r.vsingle) {
-      const int64_t nv = r.vend - r.vsingle;
-      solve_single_k<<<grid_cap((nv * 8 + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, r.vsingle, r.vend);
+      solve_warp_k<<<(nw + kWarpBlock / 32 - 1) / (kWarpBlock / 32), kWarpBlock, 0, s>>>(a, r.warp, r.single);
       PRGB_LAUNCH();
       nl++;
     }

@@ -25,6 +25,8 @@ struct SolveArgs {
   const int32_t* sub_ptr;
   const uint8_t* c_type;
   const int32_t* replay;    // [K] fixed iteration counts, or nullptr
+  const int32_t* xlorder;   // [n] positions by (level, external in-degree class)
+  double* W;                // [n] inflow-adjusted weights by position
   double* R;                // [n] by position
   double* zr;               // [n] R/outdeg by position
   int32_t* iters;           // [K]

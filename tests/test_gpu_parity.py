@@ -291,3 +291,43 @@ def test_deep_dag_full_size(prgb):
     G, P, q = assert_partition_equal(prgb, g.rowptr, g.col)
     assert P.n_levels == 200
     assert_solve_parity(prgb, g, G, P, q)
+
+
+@pytest.mark.parametrize("k", [20, 200, 5_000, 20_000])
+def test_chain_in_every_size_class(prgb, k):
+    """A chain is one CAC: warp (<=32), CTA (<=256), cluster (<=16384) and
+    grid-wide classes all reproduce R_i = (1 - c^i)/(1 - c)."""
+    import torch
+    rp, col = gg.csr_from_edges(k, np.arange(k - 1), np.arange(1, k))
+    G, P, q = assert_partition_equal(prgb, rp, col)
+    R = prgb.solve(P, C, torch.ones(k, dtype=torch.float64, device="cuda"), 1e-10).cpu().numpy()
+    i = np.arange(1, k + 1)
+    np.testing.assert_allclose(R, (1 - C ** i) / (1 - C), rtol=1e-13)
+
+
+@pytest.mark.parametrize("n,seed", [(3_000, 31), (40_000, 32)])
+def test_random_dags(prgb, n, seed):
+    """Acyclic graphs: every component is a CAC (of many sizes, merged
+    across levels), solved exactly in one pass."""
+    rng = np.random.default_rng(seed)
+    m = 3 * n
+    a = rng.integers(0, n, m)
+    b = rng.integers(0, n, m)
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    keep = lo != hi
+    rp, col = gg.csr_from_edges(n, hi[keep], lo[keep])
+    u = rng.random(n)
+    g = gg.Graph(n, rp, col, u / u.sum(), "dag")
+    G, P, q = assert_partition_equal(prgb, rp, col)
+    assert P.n_scc == 0
+    assert_solve_parity(prgb, g, G, P, q)
+
+
+def test_mid_size_sccs_use_clusters(prgb):
+    """SCCs of 300-10000 vertices (cluster class) in a layered graph."""
+    g = gg.small_planted(seed=33, n=40_000, n_scc=20, scc_vertices=30_000, n_dangling=4_000, layers=6,
+                         target_edges=200_000)
+    G, P, q = assert_partition_equal(prgb, g.rowptr, g.col)
+    sizes = np.bincount(q.comp[q.type == 1])
+    assert np.count_nonzero((sizes > 256) & (sizes <= 16384)) >= 10
+    assert_solve_parity(prgb, g, G, P, q)
