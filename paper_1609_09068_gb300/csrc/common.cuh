@@ -54,6 +54,8 @@ struct Ctl {
   int cnt[8];            // frontier counters (rotating)
   int flags[8];          // misc flags (e.g. not-converged)
   double dsum[4];
+  int bwave[2];          // wave barriers: next wave and its frontier size,
+  int bcnt[2];           //   published by the last block to arrive
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

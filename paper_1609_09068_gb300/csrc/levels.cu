@@ -16,6 +16,7 @@
 // afterwards with a lock-free union-find (hook the larger root under the
 // smaller), so a CAC's root is its smallest vertex.
 #include "common.cuh"
+#include "waves.cuh"
 
 namespace prgb {
 
@@ -63,7 +64,6 @@ __global__ void fill_cin_k(const int32_t* __restrict__ optr, const int32_t* __re
 // Returns the number of in-edge chunks to queue for the next wave.
 __device__ int finalize_node(int X, int wave, const int32_t* nsize, int32_t* key, int32_t* level_node,
                              int32_t* wave_node, uint8_t* merged, const int32_t* cin_ptr) {
-  __threadfence();
   const int k = atomicAdd(&key[X], 0);
   const bool scc = nsize[X] >= 2;
   int lvl = 0, m = 0;
@@ -83,6 +83,36 @@ __device__ int finalize_node(int X, int wave, const int32_t* nsize, int32_t* key
   return (len + kChunk - 1) / kChunk;
 }
 
+// fetch-and-add with acquire-release ordering at device scope: the last
+// decrement of a node's pending count then sees every successor's key update
+__device__ __forceinline__ int atomic_add_acq_rel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+struct KahnK {
+  const int32_t* nsize;
+  int32_t *pending, *key, *level_node, *wave_node;
+  uint8_t* merged;
+  const int32_t *cin_ptr, *cin_src;
+  __device__ void range(int X, int j, int* e0, int* e1) const {
+    *e0 = cin_ptr[X] + j * kChunk;
+    *e1 = min(cin_ptr[X + 1], *e0 + kChunk);
+  }
+  __device__ int4 pre(int X, int, bool) const {
+    return make_int4(2 * level_node[X] + (nsize[X] >= 2 ? 1 : 0), 0, 0, 0);
+  }
+  __device__ bool edge(int e, int4 p, int wave, int* w, int* nch) const {
+    const int U = cin_src[e];
+    *w = U;
+    atomicMax(&key[U], p.x);
+    if (atomic_add_acq_rel(&pending[U], -1) != 1) return false;
+    *nch = finalize_node(U, wave + 1, nsize, key, level_node, wave_node, merged, cin_ptr);
+    return *nch > 0;
+  }
+};
+
 __global__ void kahn_k(int32_t n, const int32_t* __restrict__ rep, const int32_t* __restrict__ nsize,
                        int32_t* pending, int32_t* key, int32_t* level_node, int32_t* wave_node, uint8_t* merged,
                        const int32_t* __restrict__ cin_ptr, const int32_t* __restrict__ cin_src, int* fa_node,
@@ -96,37 +126,9 @@ __global__ void kahn_k(int32_t n, const int32_t* __restrict__ rep, const int32_t
       nch = finalize_node((int)v, 0, nsize, key, level_node, wave_node, merged, cin_ptr);
     warp_push(nch > 0, (int)v, nch, fa_node, fa_chunk, &ctl->cnt[0], cap, ctl);
   }
-  if (!grid_sync(ctl, 210)) return;
-  for (int wave = 0;; wave++) {
-    int* cn = (wave & 1) ? fb_node : fa_node;
-    int* cc = (wave & 1) ? fb_chunk : fa_chunk;
-    int* nn = (wave & 1) ? fa_node : fb_node;
-    int* nc = (wave & 1) ? fa_chunk : fb_chunk;
-    const int ccur = wave % 3, cnxt = (wave + 1) % 3, cclr = (wave + 2) % 3;
-    const int cnt = vload(&ctl->cnt[ccur]);
-    if (cnt == 0) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[cclr] = 0;
-    for (int i = gw; i < cnt; i += nw) {
-      const int X = cn[i];
-      const int j = cc[i];
-      const int val = 2 * level_node[X] + (nsize[X] >= 2 ? 1 : 0);
-      const int b = cin_ptr[X] + j * kChunk;
-      const int e_end = min(cin_ptr[X + 1], b + kChunk);
-      for (int base = b; base < e_end; base += 32) {
-        const int e = base + lane;
-        int U = 0, nch = 0;
-        if (e < e_end) {
-          U = cin_src[e];
-          atomicMax(&key[U], val);
-          __threadfence();
-          if (atomicSub(&pending[U], 1) == 1)
-            nch = finalize_node(U, wave + 1, nsize, key, level_node, wave_node, merged, cin_ptr);
-        }
-        warp_push(nch > 0, U, nch, nn, nc, &ctl->cnt[cnxt], cap, ctl);
-      }
-    }
-    if (!grid_sync(ctl, 211)) return;
-  }
+  const Frontier f{fa_node, fa_chunk, fb_node, fb_chunk, cap};
+  KahnK k{nsize, pending, key, level_node, wave_node, merged, cin_ptr, cin_src};
+  run_waves(ctl, f, 211, k);
 }
 
 // lock-free union-find with parent[x] <= x (roots are the smallest ids)

@@ -13,6 +13,7 @@
 //
 // Result: rep[v] = largest vertex id of v's SCC.
 #include "common.cuh"
+#include "waves.cuh"
 
 namespace prgb {
 
@@ -30,6 +31,35 @@ __device__ __forceinline__ int trim_chunks(const int32_t* optr, const int32_t* i
   const int n = nchunks_of(optr[v + 1] - optr[v]) + nchunks_of(iptr[v + 1] - iptr[v]);
   return n > 0 ? n : 1;
 }
+
+struct TrimK {
+  const int32_t *optr, *oidx, *iptr, *iidx;
+  int32_t *rem_out, *rem_in, *state, *rep;
+  __device__ void range(int v, int j, int* e0, int* e1) const {
+    const int co = nchunks_of(optr[v + 1] - optr[v]);
+    if (j < co) {
+      *e0 = optr[v] + j * kChunkE;
+      *e1 = min(optr[v + 1], *e0 + kChunkE);
+    } else {
+      *e0 = iptr[v] + (j - co) * kChunkE;
+      *e1 = min(iptr[v + 1], *e0 + kChunkE);
+    }
+  }
+  __device__ int4 pre(int v, int j, bool first) const {
+    if (j == 0 && first) rep[v] = v;
+    return make_int4(j < nchunks_of(optr[v + 1] - optr[v]) ? 1 : 0, 0, 0, 0);
+  }
+  __device__ bool edge(int e, int4 p, int, int* w, int* nch) const {
+    const bool out = p.x != 0;
+    *w = out ? oidx[e] : iidx[e];
+    int32_t* rem = out ? rem_in : rem_out;
+    if (atomicSub(&rem[*w], 1) == 1 && atomicCAS(&state[*w], 0, 1) == 0) {
+      *nch = trim_chunks(optr, iptr, *w);
+      return true;
+    }
+    return false;
+  }
+};
 
 __global__ void trim_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx,
                        const int32_t* __restrict__ iptr, const int32_t* __restrict__ iidx, int32_t n,
@@ -50,44 +80,36 @@ __global__ void trim_k(const int32_t* __restrict__ optr, const int32_t* __restri
     }
     warp_push(want, (int)v, want ? trim_chunks(optr, iptr, (int)v) : 0, fav, fac, &ctl->cnt[0], cap, ctl);
   }
-  if (!grid_sync(ctl, 100)) return;
-  for (int wave = 0;; wave++) {
-    int* cv = (wave & 1) ? fbv : fav;
-    int* cc = (wave & 1) ? fbc : fac;
-    int* nv = (wave & 1) ? fav : fbv;
-    int* nc = (wave & 1) ? fac : fbc;
-    const int ccur = wave % 3, cnxt = (wave + 1) % 3, cclr = (wave + 2) % 3;
-    const int cnt = vload(&ctl->cnt[ccur]);
-    if (cnt == 0) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[cclr] = 0;
-    for (int i = gw; i < cnt; i += nw) {
-      const int v = cv[i];
-      const int j = cc[i];
-      if (j == 0 && lane == 0) rep[v] = v;
-      const int co = nchunks_of(optr[v + 1] - optr[v]);
-      const bool out = j < co;
-      const int e0 = out ? optr[v] + j * kChunkE : iptr[v] + (j - co) * kChunkE;
-      const int e1 = out ? min(optr[v + 1], e0 + kChunkE) : min(iptr[v + 1], e0 + kChunkE);
-      for (int base = e0; base < e1; base += 32) {
-        const int e = base + lane;
-        bool want = false;
-        int w = 0;
-        if (e < e1) {
-          w = out ? oidx[e] : iidx[e];
-          int* rem = out ? rem_in : rem_out;
-          want = atomicSub(&rem[w], 1) == 1 && atomicCAS(&state[w], 0, 1) == 0;
-        }
-        warp_push(want, w, want ? trim_chunks(optr, iptr, w) : 0, nv, nc, &ctl->cnt[cnxt], cap, ctl);
-      }
-    }
-    if (!grid_sync(ctl, 101)) return;
-  }
+  const Frontier f{fav, fac, fbv, fbc, cap};
+  TrimK k{optr, oidx, iptr, iidx, rem_out, rem_in, state, rep};
+  run_waves(ctl, f, 101, k);
 }
 
 // ---- max-label propagation over alive edges, frontier driven --------------
 // dir 0: along out-edges (sig = largest id reaching v); dir 1: along in-edges.
 // Frontier items are (vertex, chunk of kChunkE edges), so the adjacency of a
 // hub is spread over many warps.
+struct PropK {
+  const int32_t *ptr, *idx, *rep, *pin, *pout;
+  int32_t *sig, *stamp;
+  __device__ void range(int u, int j, int* e0, int* e1) const {
+    *e0 = ptr[u] + j * kChunkE;
+    *e1 = min(ptr[u + 1], *e0 + kChunkE);
+  }
+  __device__ int4 pre(int u, int, bool) const { return make_int4(vload(&sig[u]), pin[u], pout[u], 0); }
+  __device__ bool edge(int e, int4 p, int wave, int* w, int* nch) const {
+    *w = idx[e];
+    const int x = *w;
+    if (rep[x] >= 0 || pin[x] != p.y || pout[x] != p.z || vload(&sig[x]) >= p.x) return false;
+    const int old = atomicMax(&sig[x], p.x);
+    if (old < p.x && atomicExch(&stamp[x], wave) != wave) {
+      *nch = nchunks_of(ptr[x + 1] - ptr[x]);
+      return *nch > 0;
+    }
+    return false;
+  }
+};
+
 __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
                             const int32_t* __restrict__ rep, const int32_t* __restrict__ pin,
                             const int32_t* __restrict__ pout, int32_t* sig, int32_t* stamp, int* fav, int* fac,
@@ -108,42 +130,9 @@ __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __re
     }
     warp_push(want, (int)v, nch, fav, fac, &ctl->cnt[0], cap, ctl);
   }
-  if (!grid_sync(ctl, 110)) return;
-  for (int wave = 0;; wave++) {
-    int* cv = (wave & 1) ? fbv : fav;
-    int* cc = (wave & 1) ? fbc : fac;
-    int* nv = (wave & 1) ? fav : fbv;
-    int* nc = (wave & 1) ? fac : fbc;
-    const int ccur = wave % 3, cnxt = (wave + 1) % 3, cclr = (wave + 2) % 3;
-    const int cnt = vload(&ctl->cnt[ccur]);
-    if (cnt == 0) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[cclr] = 0;
-    for (int i = gw; i < cnt; i += nw) {
-      const int u = cv[i];
-      const int j = cc[i];
-      const int su = vload(&sig[u]);
-      const int a = pin[u], b = pout[u];
-      const int e0 = ptr[u] + j * kChunkE;
-      const int e1 = min(ptr[u + 1], e0 + kChunkE);
-      for (int base = e0; base < e1; base += 32) {
-        const int e = base + lane;
-        bool want = false;
-        int w = 0, nch = 0;
-        if (e < e1) {
-          w = idx[e];
-          if (rep[w] < 0 && pin[w] == a && pout[w] == b && vload(&sig[w]) < su) {
-            const int old = atomicMax(&sig[w], su);
-            if (old < su && atomicExch(&stamp[w], wave) != wave) {
-              nch = nchunks_of(ptr[w + 1] - ptr[w]);
-              want = nch > 0;
-            }
-          }
-        }
-        warp_push(want, w, nch, nv, nc, &ctl->cnt[cnxt], cap, ctl);
-      }
-    }
-    if (!grid_sync(ctl, 111)) return;
-  }
+  const Frontier f{fav, fac, fbv, fbc, cap};
+  PropK k{ptr, idx, rep, pin, pout, sig, stamp};
+  run_waves(ctl, f, 111, k);
 }
 
 // ---- FW-BW for the largest SCC ---------------------------------------------
@@ -161,6 +150,26 @@ __global__ void pivot_k(const int32_t* __restrict__ optr, const int32_t* __restr
   if (loc) atomicMax(best, loc);
 }
 
+struct ReachK {
+  const int32_t *ptr, *idx, *rep;
+  int32_t* mark;
+  int tag;
+  const int32_t* need;
+  int tag_need;
+  __device__ void range(int u, int j, int* e0, int* e1) const {
+    *e0 = ptr[u] + j * kChunkE;
+    *e1 = min(ptr[u + 1], *e0 + kChunkE);
+  }
+  __device__ int4 pre(int, int, bool) const { return make_int4(0, 0, 0, 0); }
+  __device__ bool edge(int e, int4, int, int* w, int* nch) const {
+    *w = idx[e];
+    const int x = *w;
+    if (rep[x] >= 0 || (need != nullptr && need[x] != tag_need) || atomicExch(&mark[x], tag) == tag) return false;
+    *nch = nchunks_of(ptr[x + 1] - ptr[x]);
+    return *nch > 0;
+  }
+};
+
 // Reachability from pivot among unassigned vertices: mark[v] = tag for every
 // vertex reached along (ptr, idx); when need is set, only vertices with
 // need[v] == tag_need are entered (the backward pass stays inside the
@@ -175,37 +184,9 @@ __global__ void reach_k(const int32_t* __restrict__ ptr, const int32_t* __restri
     if (lane == 0) mark[pivot] = tag;
     warp_push(lane == 0 && nch > 0, pivot, nch, fav, fac, &ctl->cnt[0], cap, ctl);
   }
-  if (!grid_sync(ctl, 120)) return;
-  for (int wave = 0;; wave++) {
-    int* cv = (wave & 1) ? fbv : fav;
-    int* cc = (wave & 1) ? fbc : fac;
-    int* nv = (wave & 1) ? fav : fbv;
-    int* nc = (wave & 1) ? fac : fbc;
-    const int ccur = wave % 3, cnxt = (wave + 1) % 3, cclr = (wave + 2) % 3;
-    const int cnt = vload(&ctl->cnt[ccur]);
-    if (cnt == 0) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[cclr] = 0;
-    for (int i = gw; i < cnt; i += nw) {
-      const int u = cv[i];
-      const int j = cc[i];
-      const int e0 = ptr[u] + j * kChunkE;
-      const int e1 = min(ptr[u + 1], e0 + kChunkE);
-      for (int base = e0; base < e1; base += 32) {
-        const int e = base + lane;
-        bool want = false;
-        int w = 0, nch = 0;
-        if (e < e1) {
-          w = idx[e];
-          if (rep[w] < 0 && (need == nullptr || need[w] == tag_need) && atomicExch(&mark[w], tag) != tag) {
-            nch = nchunks_of(ptr[w + 1] - ptr[w]);
-            want = nch > 0;
-          }
-        }
-        warp_push(want, w, nch, nv, nc, &ctl->cnt[cnxt], cap, ctl);
-      }
-    }
-    if (!grid_sync(ctl, 121)) return;
-  }
+  const Frontier f{fav, fac, fbv, fbc, cap};
+  ReachK k{ptr, idx, rep, mark, tag, need, tag_need};
+  run_waves(ctl, f, 121, k);
 }
 
 // the SCC of the pivot is F and B: find its largest id, then assign it and

@@ -533,6 +533,28 @@ __global__ void edge_visits_k(int32_t K, const int32_t* c_off, const uint8_t* c_
 
 namespace prgb {
 
+// three non-blocking side streams and the fork / join events of a solve
+struct SideStreams {
+  cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
+  pr_status create() {
+    for (int q = 0; q < 3; q++) {
+      PRGB_CUDA(cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking));
+      PRGB_CUDA(cudaEventCreateWithFlags(&join[q], cudaEventDisableTiming));
+    }
+    PRGB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    return PR_OK;
+  }
+  ~SideStreams() {
+    for (int q = 0; q < 3; q++) {
+      if (st[q]) cudaStreamDestroy(st[q]);
+      if (join[q]) cudaEventDestroy(join[q]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  }
+};
+
 static unsigned grid_cap(int64_t blocks) {
   int64_t cap = (int64_t)num_sms() * 32;
   return (unsigned)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
@@ -585,6 +607,11 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
   }
   static bool cta_attr = false;
   static size_t clu_attr = 48 * 1024;
+  // The cluster, CTA and warp kernels of a level are independent: they run on
+  // three side streams, forked after the level's gather and joined before
+  // the next level, so one kernel's tail overlaps the others.
+  SideStreams side;
+  PRGB_TRY(side.create());
   if (!cta_attr) {
     PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
     cta_attr = true;
@@ -636,27 +663,41 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       }
       nl++;
     }
+    PRGB_CUDA(cudaEventRecord(side.fork, s));
+    bool joined[3] = {false, false, false};
     if (r.cta > r.clu) {
+      PRGB_CUDA(cudaStreamWaitEvent(side.st[0], side.fork, 0));
+      joined[0] = true;
       const int chunk = 1 << clu_shift(r.clu_max);
       const size_t smem = clu_smem(chunk);
       if (smem > clu_attr) {
         PRGB_CUDA(cudaFuncSetAttribute(solve_clu_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         clu_attr = smem;
       }
-      solve_clu_k<<<(r.cta - r.clu) * kClu, kCluThreads, smem, s>>>(a, r.clu, chunk);
+      solve_clu_k<<<(r.cta - r.clu) * kClu, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
       PRGB_LAUNCH();
       nl++;
     }
     if (r.warp > r.cta) {
-      solve_cta_k<<<r.warp - r.cta, kCtaThreads, kCtaSmem, s>>>(a, r.cta);
+      PRGB_CUDA(cudaStreamWaitEvent(side.st[1], side.fork, 0));
+      joined[1] = true;
+      solve_cta_k<<<r.warp - r.cta, kCtaThreads, kCtaSmem, side.st[1]>>>(a, r.cta);
       PRGB_LAUNCH();
       nl++;
     }
     if (r.single > r.warp) {
       const int nw = r.single - r.warp;
-      solve_warp_k<<<(nw + kWarpBlock / 32 - 1) / (kWarpBlock / 32), kWarpBlock, 0, s>>>(a, r.warp, r.single);
+      PRGB_CUDA(cudaStreamWaitEvent(side.st[2], side.fork, 0));
+      joined[2] = true;
+      solve_warp_k<<<(nw + kWarpBlock / 32 - 1) / (kWarpBlock / 32), kWarpBlock, 0, side.st[2]>>>(a, r.warp,
+                                                                                                  r.single);
       PRGB_LAUNCH();
       nl++;
+    }
+    for (int q = 0; q < 3; q++) {
+      if (!joined[q]) continue;
+      PRGB_CUDA(cudaEventRecord(side.join[q], side.st[q]));
+      PRGB_CUDA(cudaStreamWaitEvent(s, side.join[q], 0));
     }
   }
   scatter_out_k<<<grid_cap((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, P->perm, a.R, R);

@@ -1,0 +1,156 @@
+// waves.cuh -- frontier waves inside one cooperative launch, shared by the
+// partitioner's kernels (trim, reachability, label propagation, Kahn order).
+//
+// A frontier item is (vertex, chunk of its adjacency).  A large frontier is
+// processed by the whole grid, one bounded grid barrier per wave.  Once the
+// frontier holds fewer than kSmallFrontier items, block 0 runs the next
+// waves alone with block barriers while the other blocks wait at the grid
+// barrier; it joins them again when the frontier grows, empties, or after
+// kLocalWaves waves (well inside the barrier's time limit).  Long chains of
+// tiny waves -- the common tail -- then cost a block barrier each instead of
+// a grid barrier.
+#pragma once
+
+#include "common.cuh"
+
+namespace prgb {
+
+constexpr int kSmallFrontier = 64;
+constexpr int kLocalWaves = 4096;
+
+struct Frontier {
+  int* av;
+  int* ac;
+  int* bv;
+  int* bc;
+  int cap;
+};
+
+// Appends (w, 0..nch-1) to the next frontier; all 32 lanes call it.
+struct Pusher {
+  int* v;
+  int* c;
+  int* counter;
+  int cap;
+  Ctl* ctl;
+  __device__ __forceinline__ void operator()(bool want, int w, int nch) const {
+    warp_push(want, w, nch, v, c, counter, cap, ctl);
+  }
+};
+
+// One wave: each warp takes one item at a time and walks its (at most
+// kChunkE) edges 32 at a time, so index loads stay coalesced.  The kernel
+// supplies
+//   K::range(v, j, &e0, &e1)      edges of item (v, j)
+//   K::pre(v, j) -> int4          per-item data (read by every lane)
+//   K::edge(e, pre, wave, &w, &nch) -> bool   visit edge e; true pushes w
+//                                 (with nch chunks) into the next frontier
+template <class K>
+__device__ __forceinline__ void one_wave(Ctl* ctl, const Frontier& f, int wave, int cnt, int w0, int nws,
+                                         const K& k) {
+  const int lane = threadIdx.x & 31;
+  const int* cv = (wave & 1) ? f.bv : f.av;
+  const int* cc = (wave & 1) ? f.bc : f.ac;
+  Pusher push{(wave & 1) ? f.av : f.bv, (wave & 1) ? f.ac : f.bc, &ctl->cnt[(wave + 1) % 3], f.cap, ctl};
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[(wave + 2) % 3] = 0;
+  for (int i = w0; i < cnt; i += nws) {
+    const int v = cv[i], j = cc[i];
+    int e0, e1;
+    k.range(v, j, &e0, &e1);
+    const int4 pre = k.pre(v, j, lane == 0);
+    for (int base = e0; base < e1; base += 32) {
+      const int e = base + lane;
+      bool want = false;
+      int w = 0, nch = 0;
+      if (e < e1) want = k.edge(e, pre, wave, &w, &nch);
+      push(want, w, want ? nch : 0);
+    }
+  }
+}
+
+// Grid barrier that also publishes the next wave and its frontier size.
+// The last block to arrive reads them (next >= 0: the wave all blocks agree
+// on; next < 0: the wave block 0 left in flags[7]) into a slot chosen by the
+// barrier's generation, so no block ever reads a counter that another block
+// may already be changing.  Bounded like grid_sync.
+struct WaveState {
+  int wave;
+  int cnt;
+};
+
+__device__ __forceinline__ bool wave_barrier(Ctl* ctl, int where, int next, WaveState* out) {
+  __shared__ int sh[2];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int gen = vloadu(&ctl->bar_gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      const int w = next >= 0 ? next : vload(&ctl->flags[7]);
+      ctl->bwave[gen & 1] = w;
+      ctl->bcnt[gen & 1] = atomicAdd(&ctl->cnt[w % 3], 0);
+      __threadfence();
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (vloadu(&ctl->bar_gen) == gen) {
+        if (vload(&ctl->err) != 0) break;
+        __nanosleep(32);
+        if (globaltimer_ns() - t0 > kWaitNs) {
+          set_err(ctl, PR_ETIMEOUT, where);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    sh[0] = vload(&ctl->bwave[gen & 1]);
+    sh[1] = vload(&ctl->bcnt[gen & 1]);
+  }
+  __syncthreads();
+  out->wave = sh[0];
+  out->cnt = sh[1];
+  return vload(&ctl->err) == 0;
+}
+
+// Runs waves until the frontier is empty.  The caller has filled the first
+// frontier (wave 0) into (av, ac), counting it in ctl->cnt[0]; this starts
+// with the barrier that publishes it.  Returns false when a barrier failed.
+template <class K>
+__device__ bool run_waves(Ctl* ctl, const Frontier& f, int where, const K& item) {
+  const int gw = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+  const int lw0 = threadIdx.x >> 5, lnw = blockDim.x >> 5;
+  WaveState st;
+  if (!wave_barrier(ctl, where, 0, &st)) return false;
+  for (;;) {
+    if (st.cnt == 0) return true;
+    if (st.cnt >= kSmallFrontier) {
+      one_wave(ctl, f, st.wave, st.cnt, gw, nw, item);
+      if (!wave_barrier(ctl, where, st.wave + 1, &st)) return false;
+      continue;
+    }
+    // small frontier: block 0 alone, block barriers; the others wait below
+    if (blockIdx.x == 0) {
+      __shared__ int shc;
+      int wave = st.wave, c = st.cnt;
+      for (int k = 0; k < kLocalWaves; k++) {
+        one_wave(ctl, f, wave, c, lw0, lnw, item);
+        __syncthreads();
+        wave++;
+        if (threadIdx.x == 0) shc = atomicAdd(&ctl->cnt[wave % 3], 0);
+        __syncthreads();
+        c = shc;
+        if (c == 0 || c >= kSmallFrontier) break;
+      }
+      if (threadIdx.x == 0) {
+        ctl->flags[7] = wave;
+        __threadfence();
+      }
+    }
+    if (!wave_barrier(ctl, where + 1, -1, &st)) return false;
+  }
+}
+
+}  // namespace prgb
