@@ -84,11 +84,26 @@ typedef struct pr_partition_s pr_partition;
 
 /* Arithmetic of the solve. */
 #define PR_PREC_FP64 0  /* FP64 throughout */
+#define PR_PREC_MIXED 1 /* pr_solve only, with PR_NORM_L1 and no replay: each
+                           SCC series runs in FP32 (values, z = P/outdeg and
+                           accumulation), then an FP64 residual
+                           r = W + cA^T(R/outdeg) - R of the component is
+                           formed; while ||r||_1 > tol*|C|/n the correction
+                           (I - cA^T)D = r is summed by the same FP32 series
+                           and R += D in FP64.  The inflow gather, CACs and
+                           1-vertex components stay FP64.  Every SCC ends
+                           with an FP64 residual within its budget, so the
+                           L1 residual of R is at most tol (plus FP64
+                           rounding of the gather) as in FP64 mode; R differs
+                           from the FP64 result by at most 2*tol/(1-c) in L1.
+                           PR_ENOCONV when six corrections do not meet the
+                           budget (tol below ~1e-13 ||R||_1) or max_iter
+                           sweeps are reached. */
 
 typedef struct pr_solve_opts {
     int32_t norm;                /* PR_NORM_L1 (default) or PR_NORM_LINF */
     int32_t max_iter;            /* per component; <= 0 selects 10000 */
-    int32_t precision;           /* PR_PREC_FP64 */
+    int32_t precision;           /* PR_PREC_FP64 (default) or PR_PREC_MIXED */
     int32_t io_on_host;          /* 1: u and R are host pointers (copied in
                                     and out inside the call) */
     const int32_t *replay_iters; /* optional HOST array [n_comp]: run exactly
@@ -114,6 +129,11 @@ typedef struct pr_solve_stats {
                              gather, R read/write, z write, row pointer and
                              out-degree), plus the inflow gather */
     int64_t kernel_launches; /* out (timing = 1): number of such launches */
+    int32_t fp64_sweeps_max; /* PR_PREC_MIXED: the most FP64 residual sweeps
+                                of any SCC (included in iters_max and
+                                comp_iters, which count all sweeps) */
+    int64_t fp64_edge_visits; /* PR_PREC_MIXED: edges read by FP64 residual
+                                 sweeps (included in edge_visits) */
 } pr_solve_stats;
 
 /*

@@ -23,7 +23,7 @@ import numpy as np
 __all__ = [
     "PrError", "Graph", "Partition", "graph", "partition", "solve", "global_power",
     "residual_l1", "load_library", "library_path", "launch_count", "TYPE_CAC", "TYPE_SCC",
-    "NORM_L1", "NORM_LINF",
+    "NORM_L1", "NORM_LINF", "PREC_FP64", "PREC_MIXED",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -34,6 +34,7 @@ TYPE_SCC = 1
 NORM_L1 = 0
 NORM_LINF = 1
 PREC_FP64 = 0
+PREC_MIXED = 1
 
 _STATUS = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOMEM", 3: "PR_ECUDA", 4: "PR_ENOCONV",
            5: "PR_ETIMEOUT", 6: "PR_EINTERNAL"}
@@ -59,7 +60,8 @@ class _Opts(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [("iters_max", C.c_int32), ("n_levels", C.c_int32), ("edge_visits", C.c_int64),
                 ("launches", C.c_int64), ("comp_iters", C.c_void_p), ("timing", C.c_int32),
-                ("kernel_ms", C.c_float), ("kernel_bytes", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("kernel_ms", C.c_float), ("kernel_bytes", C.c_int64), ("kernel_launches", C.c_int64),
+                ("fp64_sweeps_max", C.c_int32), ("fp64_edge_visits", C.c_int64)]
 
 
 _lib = None
@@ -235,8 +237,8 @@ def partition(g: Graph):
     return Partition(g)
 
 
-def _opts(norm, max_iter, io_on_host, replay):
-    o = _Opts(int(norm), int(max_iter), PREC_FP64, int(io_on_host), None)
+def _opts(norm, max_iter, io_on_host, replay, precision=PREC_FP64):
+    o = _Opts(int(norm), int(max_iter), int(precision), int(io_on_host), None)
     keep = None
     if replay is not None:
         keep = np.ascontiguousarray(replay, dtype=np.int32)
@@ -252,20 +254,22 @@ def launch_count():
 def _stats_dict(st):
     return {"iters_max": st.iters_max, "n_levels": st.n_levels, "edge_visits": st.edge_visits,
             "launches": st.launches, "kernel_ms": st.kernel_ms, "kernel_bytes": st.kernel_bytes,
-            "kernel_launches": st.kernel_launches}
+            "kernel_launches": st.kernel_launches, "fp64_sweeps_max": st.fp64_sweeps_max,
+            "fp64_edge_visits": st.fp64_edge_visits}
 
 
 def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iters=None,
-          with_stats=False, allow_noconv=False, timing=False):
+          with_stats=False, allow_noconv=False, timing=False, precision=PREC_FP64):
     """Sec. 4.3 solve on device tensors; returns R (float64, original order).
 
     ``u`` may be a CUDA tensor or a numpy array (host I/O through the C ABI's
-    io_on_host path; R is then returned as numpy)."""
+    io_on_host path; R is then returned as numpy).  ``precision=PREC_MIXED``
+    runs the SCC series in FP32 with FP64 residual refinement."""
     lib = load_library()
     on_host = isinstance(u, np.ndarray)
-    o, keep = _opts(norm, max_iter, on_host, replay_iters)
+    o, keep = _opts(norm, max_iter, on_host, replay_iters, precision)
     comp_iters = np.zeros(max(part.n_comp, 1), np.int32)
-    st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data, int(timing), 0.0, 0, 0)
+    st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data, int(timing), 0.0, 0, 0, 0, 0)
     if on_host:
         uh = np.ascontiguousarray(u, dtype=np.float64)
         R = np.empty(part.n, np.float64)
@@ -294,7 +298,7 @@ def global_power(g: Graph, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
     on_host = isinstance(u, np.ndarray)
     rep = None if replay_iters is None else [int(replay_iters)]
     o, keep = _opts(norm, max_iter, on_host, rep)
-    st = _Stats(0, 0, 0, 0, None, int(timing), 0.0, 0, 0)
+    st = _Stats(0, 0, 0, 0, None, int(timing), 0.0, 0, 0, 0, 0)
     if on_host:
         uh = np.ascontiguousarray(u, dtype=np.float64)
         R = np.empty(g.n, np.float64)

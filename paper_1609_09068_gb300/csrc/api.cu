@@ -196,7 +196,9 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
   if (opts) o = *opts;
   if (o.max_iter <= 0) o.max_iter = 10000;
   if (o.norm != PR_NORM_L1 && o.norm != PR_NORM_LINF) return PR_EINVAL;
-  if (o.precision != PR_PREC_FP64) return PR_EINVAL;
+  if (o.precision != PR_PREC_FP64 && o.precision != PR_PREC_MIXED) return PR_EINVAL;
+  const bool mixed = o.precision == PR_PREC_MIXED;
+  if (mixed && (o.norm != PR_NORM_L1 || o.replay_iters)) return PR_EINVAL;
   if (o.replay_iters) {
     for (int32_t k = 0; k < part->n_comp; k++)
       if (o.replay_iters[k] < 0 || o.replay_iters[k] > 1000000) return PR_EINVAL;
@@ -211,8 +213,13 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
   double* dR = R;
   PRGB_TRY(tmp.alloc(&ctl, 1));
   PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  int32_t* iters64 = nullptr;
   PRGB_TRY(tmp.alloc(&iters, (size_t)K));
   if (K > 0) PRGB_CUDA(cudaMemsetAsync(iters, 0, (size_t)K * 4, s));
+  if (mixed) {
+    PRGB_TRY(tmp.alloc(&iters64, (size_t)K));
+    if (K > 0) PRGB_CUDA(cudaMemsetAsync(iters64, 0, (size_t)K * 4, s));
+  }
   if (o.replay_iters && K > 0) {
     PRGB_TRY(tmp.alloc(&replay, (size_t)K));
     PRGB_CUDA(cudaMemcpyAsync(replay, o.replay_iters, (size_t)K * 4, cudaMemcpyHostToDevice, s));
@@ -228,7 +235,7 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
   int64_t launches = 0;
   KernelTiming kt;
   const bool timing = stats && stats->timing;
-  PRGB_TRY(run_solve(part, c, du, tol, o.norm, o.max_iter, replay, dR, iters, tmp, ctl, &launches,
+  PRGB_TRY(run_solve(part, c, du, tol, o.norm, o.max_iter, replay, mixed, dR, iters, iters64, tmp, ctl, &launches,
                      timing ? &kt : nullptr));
   if (o.io_on_host && n > 0) PRGB_CUDA(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
   int flags = 0;
@@ -238,16 +245,25 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
     stats->launches = launches;
     stats->iters_max = 0;
     stats->edge_visits = 0;
+    stats->fp64_sweeps_max = 0;
+    stats->fp64_edge_visits = 0;
     if (K > 0) {
       int32_t* h = stats->comp_iters;
-      std::vector<int32_t> local;
+      std::vector<int32_t> local, h64;
       if (!h) {
         local.resize(K);
         h = local.data();
       }
       PRGB_CUDA(cudaMemcpyAsync(h, iters, (size_t)K * 4, cudaMemcpyDeviceToHost, s));
-      PRGB_TRY(solve_edge_visits(part, iters, &stats->edge_visits, tmp));  // synchronises
+      if (mixed) {
+        h64.resize(K);
+        PRGB_CUDA(cudaMemcpyAsync(h64.data(), iters64, (size_t)K * 4, cudaMemcpyDeviceToHost, s));
+      }
+      PRGB_TRY(solve_edge_visits(part, iters, iters64, &stats->edge_visits, &stats->fp64_edge_visits,
+                                 tmp));  // synchronises
       for (int32_t k = 0; k < K; k++) stats->iters_max = h[k] > stats->iters_max ? h[k] : stats->iters_max;
+      for (int32_t k = 0; k < (int32_t)h64.size(); k++)
+        stats->fp64_sweeps_max = h64[k] > stats->fp64_sweeps_max ? h64[k] : stats->fp64_sweeps_max;
       if (timing) {
         stats->kernel_ms = 0.0f;
         stats->kernel_bytes = 0;
@@ -258,8 +274,12 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
           stats->kernel_ms += ms;
           const LargeComp& L = kt.comps[i];
           const int64_t it = h[L.c];
-          stats->kernel_bytes += it * (4 * (int64_t)L.m_int + 40 * (int64_t)L.size) + 52 * (int64_t)L.size +
-                                 12 * (int64_t)L.m_ext;
+          // FP32 sweeps move 4 B per edge + 24 B per row (z gather and
+          // write, F read/write, row pointer, 1/outdeg in FP32)
+          const int64_t it64 = mixed ? h64[L.c] : it;
+          stats->kernel_bytes += it64 * (4 * (int64_t)L.m_int + 40 * (int64_t)L.size) +
+                                 (it - it64) * (4 * (int64_t)L.m_int + 24 * (int64_t)L.size) +
+                                 52 * (int64_t)L.size + 12 * (int64_t)L.m_ext;
         }
       }
     }

@@ -128,6 +128,14 @@ __device__ __forceinline__ double group_max(double v) {
   return v;
 }
 
+// FP32 overload: a float argument must not be widened to the FP64 version
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <int G>
 __device__ __forceinline__ float group_sumf(float v) {
 #pragma unroll

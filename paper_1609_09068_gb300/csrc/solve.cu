@@ -21,6 +21,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "solve.cuh"
@@ -49,6 +50,24 @@ __device__ __forceinline__ bool keep_going32(float s, double tau, int norm) {
   return norm == PR_NORM_LINF ? (sd >= tau) : (sd > tau);
 }
 
+// Mixed precision (the SCC series only; the gather, CACs and 1-vertex
+// components stay FP64).  Per SCC C with budget tau = tol*|C|/n:
+//   1. the series P_0 = W, P_{k+1} = c A^T P_k, F = sum P_k in FP32 values
+//      and FP32 accumulation, until the FP32 norm of P falls to
+//      max(tau, kMixKappa * ||W||_1): below that FP32 rounding of F
+//      dominates what further terms would add;
+//   2. R += F in FP64 and the FP64 residual r = W + c A^T (R/outdeg) - R,
+//      its L1 norm rho; done when rho <= tau;
+//   3. otherwise solve (I - c A^T) D = r by the same series in FP32 from
+//      P_0 = r (signed), until the FP32 norm of P falls to
+//      max(tau/2, kMixKappa * rho); F = D, back to 2.
+// Each FP32 pass gains about six digits, so one or two rounds of 2-3 meet
+// any budget above ~1e-13 ||R||_1; after kMixRounds residuals above tau the
+// component is reported as not converged (PR_ENOCONV).  The final per-SCC
+// residual check is FP64, so the L1 residual budget holds as in FP64 mode.
+constexpr float kMixKappa = 8.0f * 5.9604645e-8f;  // 8 * 2^-24
+constexpr int kMixRounds = 6;
+
 // A local index outside [0, sz) would mean a broken layout: record it and
 // read slot 0 instead of touching memory out of bounds.
 __device__ __forceinline__ int local_or_err(const SolveArgs& a, int q, int sz) {
@@ -72,8 +91,71 @@ __device__ __forceinline__ double check_u(const SolveArgs& a, double uu) {
 constexpr int kWarpEdges = kWarpCompMax * (kWarpCompMax - 1);
 constexpr int kWarpBlock = 64;  // two components per block, spread over many SMs
 
+// FP32 series with FP64 residual refinement (see kMixKappa) for one warp's
+// component; W is this lane's weight.  Returns the result R of this lane and
+// counts the sweeps in *k (all) and *k64 (FP64 residual sweeps).
+__device__ double warp_series_mixed(const SolveArgs& a, bool act, double W, double inv, const uint8_t* ix, int ib,
+                                    int ie, double* z, float* zf, double tau, int* k, int* k64) {
+  const int lane = threadIdx.x & 31;
+  const float cf = (float)a.c;
+  const float invf = (float)inv;
+  float F = act ? (float)W : 0.0f;
+  if (act) zf[lane] = (float)(W * inv);
+  const double wsum = group_sum<32>(act ? W : 0.0);
+  float thr = (float)fmax(tau, (double)kMixKappa * wsum);
+  double R = 0.0;
+  int rounds = 0;
+  __syncwarp();
+  for (;;) {
+    for (;;) {
+      float acc0 = 0.0f, acc1 = 0.0f;
+      int e = ib;
+      for (; e + 1 < ie; e += 2) {
+        acc0 += zf[ix[e]];
+        acc1 += zf[ix[e + 1]];
+      }
+      if (e < ie) acc0 += zf[ix[e]];
+      const float pn = cf * (acc0 + acc1);
+      __syncwarp();
+      if (act) {
+        zf[lane] = pn * invf;
+        F += pn;
+      }
+      __syncwarp();
+      ++*k;
+      if (group_sumf<32>(fabsf(pn)) <= thr) break;
+      if (*k >= a.max_iter) {
+        if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
+        return R + (double)F;
+      }
+    }
+    R += (double)F;
+    if (act) z[lane] = R * inv;
+    __syncwarp();
+    double acc = 0.0;
+    for (int e = ib; e < ie; e++) acc += z[ix[e]];
+    const double r = act ? W + a.c * acc - R : 0.0;
+    ++*k;
+    ++*k64;
+    const double rho = group_sum<32>(fabs(r));
+    if (rho <= tau) break;
+    if (++rounds >= kMixRounds || *k >= a.max_iter) {
+      if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
+      break;
+    }
+    F = (float)r;
+    __syncwarp();  // every lane has read z before the next residual rewrites it
+    if (act) zf[lane] = (float)(r * inv);
+    thr = fmaxf(0.5f * (float)tau, kMixKappa * (float)rho);
+    __syncwarp();
+  }
+  return R;
+}
+
+template <bool kMixed>
 __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t cbeg, int32_t cend) {
   __shared__ double zsh[kWarpBlock / 32][32];
+  __shared__ float zfsh[kWarpBlock / 32][32];
   __shared__ uint8_t ish[kWarpBlock / 32][kWarpEdges];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int c = cbeg + (int)blockIdx.x * (kWarpBlock / 32) + wib;
@@ -92,7 +174,7 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
   const int ib = act ? a.int_ptr[p] - ib0 : 0, ie = act ? min(a.int_ptr[p + 1] - ib0, kWarpEdges) : 0;
   __syncwarp();
   double R = W;
-  int k = 0;
+  int k = 0, k64 = 0;
   if (a.c_type[c] == PR_TYPE_CAC) {
     const int sb = a.c_sub[c], se = a.c_sub[c + 1];
     for (int s = sb; s < se; s++) {
@@ -105,6 +187,9 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
       }
       __syncwarp();
     }
+  } else if (kMixed) {
+    const double tau = a.tol * (double)sz / (double)a.n;
+    R = warp_series_mixed(a, act, W, inv, ix, ib, ie, z, zfsh[wib], tau, &k, &k64);
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const int fixed = a.replay ? a.replay[c] : -1;
@@ -144,7 +229,10 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
     a.R[p] = R;
     a.zr[p] = R * inv;
   }
-  if (lane == 0) a.iters[c] = k;
+  if (lane == 0) {
+    a.iters[c] = k;
+    if (kMixed) a.iters64[c] = k64;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -160,7 +248,10 @@ constexpr int kCtaEdgeCap = 8192;
 constexpr int kCtaRows = kCtaCompMax / kCtaThreads;
 constexpr size_t kCtaSmem = (size_t)kCtaCompMax * (3 * sizeof(double) + sizeof(int)) + sizeof(int) +
                             (size_t)kCtaEdgeCap * sizeof(uint16_t);
+constexpr size_t kCtaSmemMixed = kCtaSmem + (size_t)kCtaCompMax * sizeof(float);
+static_assert(kCtaRows == 1, "the mixed-precision CTA series keeps one row per thread");
 
+template <bool kMixed>
 __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t cbeg) {
   extern __shared__ double sm[];
   double* Rs = sm;
@@ -168,7 +259,9 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
   double* iv = sm + 2 * kCtaCompMax;
   int* ip = reinterpret_cast<int*>(sm + 3 * kCtaCompMax);  // [sz+1] local edge offsets
   uint16_t* ix = reinterpret_cast<uint16_t*>(ip + kCtaCompMax + 1);
+  float* zf = reinterpret_cast<float*>(ix + kCtaEdgeCap);  // [kCtaCompMax], mixed precision only
   __shared__ float red[kCtaThreads / 32];
+  __shared__ double red64[kCtaThreads / 32];
   const int c = cbeg + (int)blockIdx.x;
   const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
   const int ib = a.int_ptr[off];
@@ -199,7 +292,18 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
     }
     return acc;
   };
-  int k = 0;
+  auto row_sumf = [&](int i) -> float {
+    float acc = 0.0f;
+    const int e0 = ip[i], e1 = ip[i + 1];
+    if (staged) {
+#pragma unroll 4
+      for (int e = e0; e < e1; e++) acc += zf[ix[e]];
+    } else {
+      for (int e = e0; e < e1; e++) acc += zf[local_or_err(a, a.int_idx[ib + e] - off, sz)];
+    }
+    return acc;
+  };
+  int k = 0, k64 = 0;
   if (!scc) {
     // CAC: one pass, sub-level by sub-level (topological order)
     const int sb = a.c_sub[c], se = a.c_sub[c + 1];
@@ -212,6 +316,56 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
       }
       __syncthreads();
     }
+  } else if (kMixed) {
+    // FP32 series with FP64 residual refinement (see kMixKappa); row i of
+    // thread i
+    const int i = threadIdx.x;
+    const bool act = i < sz;
+    const double tau = a.tol * (double)sz / (double)a.n;
+    const float cf = (float)a.c;
+    const double W = act ? Rs[i] : 0.0, inv = act ? iv[i] : 0.0;
+    const float invf = (float)inv;
+    float F = act ? (float)W : 0.0f;
+    if (act) zf[i] = (float)(W * inv);
+    float thr = (float)fmax(tau, (double)kMixKappa * block_sum(W, red64));  // publishes zf
+    double R = 0.0;
+    int rounds = 0;
+    for (;;) {
+      for (;;) {
+        const float pn = act ? cf * row_sumf(i) : 0.0f;
+        __syncthreads();  // every row has read zf before it is overwritten
+        if (act) {
+          zf[i] = pn * invf;
+          F += pn;
+        }
+        const float s2 = block_sumf(fabsf(pn), red, false);  // publishes zf
+        k++;
+        if (s2 <= thr) break;
+        if (k >= a.max_iter) {
+          if (threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
+          rounds = -1;
+          break;
+        }
+      }
+      R += (double)F;
+      if (rounds < 0) break;
+      if (act) z[i] = R * inv;
+      __syncthreads();
+      const double r = act ? W + a.c * row_sum(i) - R : 0.0;
+      const double rho = block_sum(fabs(r), red64);  // also orders the z reads before later writes
+      k++;
+      k64++;
+      if (rho <= tau) break;
+      if (++rounds >= kMixRounds || k >= a.max_iter) {
+        if (threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
+        break;
+      }
+      F = (float)r;
+      if (act) zf[i] = (float)(r * inv);
+      thr = fmaxf(0.5f * (float)tau, kMixKappa * (float)rho);
+      __syncthreads();
+    }
+    if (act) Rs[i] = R;
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const int fixed = a.replay ? a.replay[c] : -1;
@@ -247,11 +401,15 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
       }
     }
   }
+  __syncthreads();
   for (int i = threadIdx.x; i < sz; i += blockDim.x) {
     a.R[off + i] = Rs[i];
     a.zr[off + i] = Rs[i] * iv[i];
   }
-  if (threadIdx.x == 0) a.iters[c] = k;
+  if (threadIdx.x == 0) {
+    a.iters[c] = k;
+    if (kMixed && scc) a.iters64[c] = k64;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -274,27 +432,63 @@ __host__ __device__ __forceinline__ int clu_shift(int sz) {
   return sh;
 }
 
-__host__ __device__ __forceinline__ size_t clu_smem(int chunk) {
-  return (size_t)chunk * (4 * sizeof(double) + sizeof(int)) + 2 * sizeof(int) + 2 * sizeof(float) +
+// Shared memory of one rank for rows [0, chunk): doubles first (zA, zB, R,
+// 1/outdeg, two FP64 partials), then ints (local edge offsets), floats (two
+// FP32 partials; with mixed precision the FP32 z pair, F and 1/outdeg), and
+// the 16-bit staged indices.
+struct CluSmem {
+  double *zA, *zB, *Rs, *iv, *dpart;
+  int* ip;
+  float *part, *fA, *fB, *F, *ivf;
+  uint16_t* ix;
+};
+
+__host__ __device__ __forceinline__ size_t clu_smem(int chunk, bool mixed) {
+  return (size_t)chunk * 4 * sizeof(double) + 2 * sizeof(double) + ((size_t)chunk + 2) * sizeof(int) +
+         2 * sizeof(float) + (mixed ? (size_t)chunk * 4 * sizeof(float) : 0) +
          (size_t)chunk * kCluEdgesPerRow * sizeof(uint16_t);
 }
 
+__device__ __forceinline__ CluSmem clu_carve(double* base, int chunk, bool mixed) {
+  CluSmem m;
+  m.zA = base;
+  m.zB = base + chunk;
+  m.Rs = base + 2 * chunk;
+  m.iv = base + 3 * chunk;
+  m.dpart = base + 4 * chunk;
+  m.ip = reinterpret_cast<int*>(base + 4 * chunk + 2);
+  m.part = reinterpret_cast<float*>(m.ip + chunk + 2);
+  float* f = m.part + 2;
+  m.fA = mixed ? f : nullptr;
+  m.fB = mixed ? f + chunk : nullptr;
+  m.F = mixed ? f + 2 * chunk : nullptr;
+  m.ivf = mixed ? f + 3 * chunk : nullptr;
+  m.ix = reinterpret_cast<uint16_t*>(f + (mixed ? 4 * chunk : 0));
+  return m;
+}
+
+template <bool kMixed>
 __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     solve_clu_k(SolveArgs a, int32_t cbeg, int32_t chunk_max) {
   extern __shared__ double cs[];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  double* zA = cs;
-  double* zB = cs + chunk_max;
-  double* Rs = cs + 2 * chunk_max;
-  double* iv = cs + 3 * chunk_max;
-  int* ip = reinterpret_cast<int*>(cs + 4 * chunk_max);         // [chunk_max + 1]
-  float* part = reinterpret_cast<float*>(ip + chunk_max + 2);   // [2]
-  uint16_t* ix = reinterpret_cast<uint16_t*>(part + 2);         // [chunk_max * kCluEdgesPerRow]
+  const CluSmem sm = clu_carve(cs, chunk_max, kMixed);
+  double* zA = sm.zA;
+  double* zB = sm.zB;
+  double* Rs = sm.Rs;
+  double* iv = sm.iv;
+  int* ip = sm.ip;
+  float* part = sm.part;
+  uint16_t* ix = sm.ix;
   __shared__ float red[kCluThreads / 32];
+  __shared__ double red64[kCluThreads / 32];
   __shared__ double* remA[kClu];
   __shared__ double* remB[kClu];
   __shared__ float* remP[kClu];
+  __shared__ double* remD[kClu];
+  __shared__ float* remFA[kClu];
+  __shared__ float* remFB[kClu];
   const int c = cbeg + (int)(blockIdx.x / kClu);
   const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
   const int sh = clu_shift(sz);
@@ -305,6 +499,11 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     remA[threadIdx.x] = cl.map_shared_rank(zA, (int)threadIdx.x);
     remB[threadIdx.x] = cl.map_shared_rank(zB, (int)threadIdx.x);
     remP[threadIdx.x] = cl.map_shared_rank(part, (int)threadIdx.x);
+    remD[threadIdx.x] = cl.map_shared_rank(sm.dpart, (int)threadIdx.x);
+    if (kMixed) {
+      remFA[threadIdx.x] = cl.map_shared_rank(sm.fA, (int)threadIdx.x);
+      remFB[threadIdx.x] = cl.map_shared_rank(sm.fB, (int)threadIdx.x);
+    }
   }
   // stage this rank's rows: local edge offsets and component-local indices
   const int ib = a.int_ptr[off + r0];
@@ -324,8 +523,11 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
   }
   cl.sync();
   const int mask = chunk - 1;
-  auto row_sum = [&](double* const* rem, int i) -> double {
-    double acc0 = 0.0, acc1 = 0.0;
+  // sum of z over row i's in-edges, z read from every rank's slice
+  auto row_sum = [&](auto const* rem, int i) {
+    using T = typename std::remove_pointer<typename std::remove_const<
+        typename std::remove_pointer<decltype(rem)>::type>::type>::type;
+    T acc0 = 0, acc1 = 0;
     const int e0 = ip[i], e1 = ip[i + 1];
     int e = e0;
     if (staged) {
@@ -346,7 +548,7 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     }
     return acc0 + acc1;
   };
-  int k = 0;
+  int k = 0, k64 = 0;
   if (a.c_type[c] != PR_TYPE_SCC) {
     // CAC: one pass, sub-level by sub-level, one cluster barrier each
     const int sb = a.c_sub[c], se = a.c_sub[c + 1];
@@ -358,6 +560,86 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
         zA[i] = Rv * iv[i];
       }
       cl.sync();
+    }
+  } else if (kMixed) {
+    // FP32 series with FP64 residual refinement (see kMixKappa).  F holds
+    // the FP32 sum of the current pass, Rs the FP64 result so far.
+    const double tau = a.tol * (double)sz / (double)a.n;
+    const float cf = (float)a.c;
+    float* F = sm.F;
+    float* ivf = sm.ivf;
+    double wl = 0.0;
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+      const double W = Rs[i];
+      F[i] = (float)W;
+      sm.fA[i] = (float)(W * iv[i]);
+      ivf[i] = (float)iv[i];
+      Rs[i] = 0.0;
+      wl += W;
+    }
+    const double wb = block_sum(wl, red64);
+    if (threadIdx.x == 0) sm.dpart[0] = wb;
+    cl.sync();  // publishes fA and the partials
+    double wsum = 0.0;
+    for (int r = 0; r < kClu; r++) wsum += remD[r][0];
+    float thr = (float)fmax(tau, (double)kMixKappa * wsum);
+    int zc = 0, dq = 1, rounds = 0;
+    for (;;) {
+      bool stop = false;
+      for (;;) {
+        float* const* rem = zc ? remFB : remFA;
+        float* nxt = zc ? sm.fA : sm.fB;
+        float local = 0.0f;
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+          const float pn = cf * row_sum(rem, i);
+          F[i] += pn;
+          nxt[i] = pn * ivf[i];
+          local += fabsf(pn);
+        }
+        const float bs = block_sumf(local, red, false);
+        if (threadIdx.x == 0) part[k & 1] = bs;
+        cl.sync();  // publishes nxt and the rank partials
+        float s2 = 0.0f;
+        for (int r = 0; r < kClu; r++) s2 += remP[r][k & 1];
+        k++;
+        zc ^= 1;
+        if (s2 <= thr) break;
+        if (k >= a.max_iter) {
+          if (rank == 0 && threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
+          stop = true;
+          break;
+        }
+      }
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        const double R = Rs[i] + (double)F[i];
+        Rs[i] = R;
+        zA[i] = R * iv[i];
+      }
+      if (stop) break;
+      cl.sync();  // publishes zA
+      // FP64 residual; r becomes the start of the next correction pass
+      float* cur = zc ? sm.fB : sm.fA;
+      double rl = 0.0;
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        const double r = a.W[off + r0 + i] + a.c * row_sum(remA, i) - Rs[i];
+        F[i] = (float)r;
+        cur[i] = (float)(r * iv[i]);
+        rl += fabs(r);
+      }
+      const double rb = block_sum(rl, red64);
+      if (threadIdx.x == 0) sm.dpart[dq] = rb;
+      cl.sync();  // publishes cur and the partials
+      double rho = 0.0;
+      for (int r = 0; r < kClu; r++) rho += remD[r][dq];
+      dq ^= 1;
+      k++;
+      k64++;
+      if (rho <= tau) break;
+      if (++rounds >= kMixRounds || k >= a.max_iter) {
+        if (rank == 0 && threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
+        break;
+      }
+      thr = fmaxf(0.5f * (float)tau, kMixKappa * (float)rho);
     }
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
@@ -394,7 +676,10 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     a.R[off + r0 + i] = Rs[i];
     a.zr[off + r0 + i] = Rs[i] * iv[i];
   }
-  if (rank == 0 && threadIdx.x == 0) a.iters[c] = k;
+  if (rank == 0 && threadIdx.x == 0) {
+    a.iters[c] = k;
+    if (kMixed && a.c_type[c] == PR_TYPE_SCC) a.iters64[c] = k64;
+  }
   cl.sync();  // no rank leaves while another may still read its shared memory
 }
 
@@ -484,6 +769,111 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
   if (blockIdx.x == 0 && threadIdx.x == 0) a.iters[L.c] = k;
 }
 
+// The grid-wide series in mixed precision (see kMixKappa).  Buffers: fz
+// holds the FP32 z pair (2 * size floats), F the FP32 sum of the current
+// pass; a.R the FP64 result so far and a.zr its R/outdeg for the residual.
+__device__ __forceinline__ double grid_fold(const SolveArgs& a, double* part, int slot, double local,
+                                            double* red, int where) {
+  const double bs = block_sum(local, red);
+  double* sl = part + (size_t)slot * gridDim.x;
+  if (threadIdx.x == 0) sl[blockIdx.x] = bs;
+  if (!grid_sync(a.ctl, where)) return -1.0;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&sl[b]);
+  return block_sum(t, red);
+}
+
+__global__ void __launch_bounds__(kBlock) solve_large_scc_mx_k(SolveArgs a, LargeComp L, float* fz, float* F,
+                                                               double* part, HeavyRows hv, HeavyScratch hs) {
+  __shared__ double red[kBlock / 32];
+  const int off = L.off, sz = L.size;
+  const int nlight = sz - hv.nheavy;
+  const int* lorder = a.lorder + off;
+  const double tau = a.tol * (double)sz / (double)a.n;
+  const float cf = (float)a.c;
+  float* const zf0 = fz;
+  float* const zf1 = fz + sz;
+  double wl = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = off + (int)i;
+    const double W = a.W[p];
+    F[i] = (float)W;
+    zf0[i] = (float)(W * a.p_inv[p]);
+    a.R[p] = 0.0;
+    wl += W;
+  }
+  const double wsum = grid_fold(a, part, 0, wl, red, 330);
+  if (wsum < 0.0) return;
+  float thr = (float)fmax(tau, (double)kMixKappa * wsum);
+  int k = 0, k64 = 0, zc = 0, slot = 1, rounds = 0;
+  for (;;) {
+    bool stop = false;
+    for (;;) {
+      const float* cur = zc ? zf1 : zf0;
+      float* nxt = zc ? zf0 : zf1;
+      double local = 0.0;
+      auto fin = [&](int row, float acc, bool heavy) -> double {
+        const float pn = cf * acc;
+        F[row - off] += pn;
+        nxt[row - off] = pn * a.p_invf[row];
+        if (!heavy) local += (double)fabsf(pn);
+        return (double)fabsf(pn);
+      };
+      auto val = [&](int e) -> float { return cur[local_or_err(a, a.int_idx[e] - off, sz)]; };
+      balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, slot & 1, true, fin, val);
+      double s = grid_fold(a, part, slot & 1, local, red, 331);
+      if (s < 0.0) return;
+      if (hv.nheavy > 0) s += __ldcg(&hs.total[slot & 1]);
+      slot++;
+      k++;
+      zc ^= 1;
+      if (s <= (double)thr) break;
+      if (k >= a.max_iter) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
+        stop = true;
+        break;
+      }
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const int p = off + (int)i;
+      const double R = a.R[p] + (double)F[i];
+      a.R[p] = R;
+      a.zr[p] = R * a.p_inv[p];
+    }
+    if (stop) break;
+    if (!grid_sync(a.ctl, 332)) return;
+    // FP64 residual; r starts the next correction pass
+    float* cur = zc ? zf1 : zf0;
+    double local = 0.0;
+    auto fin = [&](int row, double acc, bool heavy) -> double {
+      const double r = a.W[row] + a.c * acc - a.R[row];
+      F[row - off] = (float)r;
+      cur[row - off] = (float)(r * a.p_inv[row]);
+      if (!heavy) local += fabs(r);
+      return fabs(r);
+    };
+    auto val = [&](int e) -> double { return a.zr[a.int_idx[e]]; };
+    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, slot & 1, true, fin, val);
+    double rho = grid_fold(a, part, slot & 1, local, red, 333);
+    if (rho < 0.0) return;
+    if (hv.nheavy > 0) rho += __ldcg(&hs.total[slot & 1]);
+    slot++;
+    k++;
+    k64++;
+    if (rho <= tau) break;
+    if (++rounds >= kMixRounds || k >= a.max_iter) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
+      break;
+    }
+    thr = fmaxf(0.5f * (float)tau, kMixKappa * (float)rho);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.iters[L.c] = k;
+    a.iters64[L.c] = k64;
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) solve_large_cac_k(SolveArgs a, LargeComp L) {
   load_rows(a, L.off, L.size, nullptr);  // R[p] = W
   if (!grid_sync(a.ctl, 320)) return;
@@ -519,14 +909,18 @@ __global__ void scatter_out_k(int32_t n, const int32_t* perm, const double* Rp, 
 // edge reads of the solve: ext edges once, CAC internal edges once, SCC
 // internal edges once per iteration
 __global__ void edge_visits_k(int32_t K, const int32_t* c_off, const uint8_t* c_type, const int32_t* int_ptr,
-                              const int32_t* ext_ptr, const int32_t* iters, unsigned long long* out) {
-  unsigned long long loc = 0;
+                              const int32_t* ext_ptr, const int32_t* iters, const int32_t* iters64,
+                              unsigned long long* out) {
+  unsigned long long loc = 0, loc64 = 0;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < K; c += (int64_t)gridDim.x * blockDim.x) {
     const int b = c_off[c], e = c_off[c + 1];
     const long long mi = int_ptr[e] - int_ptr[b], me = ext_ptr[e] - ext_ptr[b];
-    loc += (unsigned long long)(me + (c_type[c] == PR_TYPE_SCC ? mi * (long long)iters[c] : mi));
+    const bool scc = c_type[c] == PR_TYPE_SCC;
+    loc += (unsigned long long)(me + (scc ? mi * (long long)iters[c] : mi));
+    if (iters64 && scc) loc64 += (unsigned long long)(mi * (long long)iters64[c]);
   }
   atomicAdd(out, loc);
+  if (iters64) atomicAdd(out + 1, loc64);
 }
 
 }  // namespace prgb
@@ -560,9 +954,14 @@ static unsigned grid_cap(int64_t blocks) {
   return (unsigned)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
 }
 
+__global__ void to_float_k(int32_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
 pr_status run_solve(const pr_partition_s* P, double c, const double* u, double tol, int norm, int max_iter,
-                    const int32_t* replay, double* R, int32_t* iters_dev, Arena& tmp, Ctl* ctl,
-                    int64_t* launches, KernelTiming* timing) {
+                    const int32_t* replay, bool mixed, double* R, int32_t* iters_dev, int32_t* iters64_dev,
+                    Arena& tmp, Ctl* ctl, int64_t* launches, KernelTiming* timing) {
   cudaStream_t s = tmp.stream();
   const int32_t n = P->g.n;
   int64_t nl = 0;
@@ -593,6 +992,16 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
   a.iters = iters_dev;
   a.ctl = ctl;
   a.xlorder = P->xlorder;
+  a.p_invf = nullptr;
+  a.iters64 = iters64_dev;
+  if (mixed) {
+    float* invf = nullptr;
+    PRGB_TRY(tmp.alloc(&invf, n));
+    to_float_k<<<grid_cap((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, P->p_inv, invf);
+    PRGB_LAUNCH();
+    nl++;
+    a.p_invf = invf;
+  }
   PRGB_TRY(tmp.alloc(&a.R, n));
   PRGB_TRY(tmp.alloc(&a.zr, n));
   PRGB_TRY(tmp.alloc(&a.W, n));
@@ -606,14 +1015,16 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
     PRGB_TRY(tmp.alloc(&part, (size_t)2 * num_sms() * 8));
   }
   static bool cta_attr = false;
-  static size_t clu_attr = 48 * 1024;
+  static size_t clu_attr[2] = {48 * 1024, 48 * 1024};
   // The cluster, CTA and warp kernels of a level are independent: they run on
   // three side streams, forked after the level's gather and joined before
   // the next level, so one kernel's tail overlaps the others.
   SideStreams side;
   PRGB_TRY(side.create());
   if (!cta_attr) {
-    PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
+    PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
+    PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kCtaSmemMixed));
     cta_attr = true;
   }
   size_t li_large = 0;
@@ -645,7 +1056,10 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
         hv.nchunks = L.chunk_end - L.chunk_begin;
         hv.cbase = L.chunk_begin;
         hv.hbase = L.heavy_begin;
-        void* args[] = {&a, &L, &zA, &zB, &part, &hv, &hs};
+        float* fz = reinterpret_cast<float*>(zA);
+        float* F = reinterpret_cast<float*>(zB);
+        void* args64[] = {&a, &L, &zA, &zB, &part, &hv, &hs};
+        void* args32[] = {&a, &L, &fz, &F, &part, &hv, &hs};
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (timing) {
           PRGB_CUDA(cudaEventCreate(&e0));
@@ -655,7 +1069,10 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
           timing->comps.push_back(L);
           PRGB_CUDA(cudaEventRecord(e0, s));
         }
-        PRGB_TRY(launch_coop((const void*)solve_large_scc_k, kBlock, 0, s, args, 4, nullptr));
+        if (mixed)
+          PRGB_TRY(launch_coop((const void*)solve_large_scc_mx_k, kBlock, 0, s, args32, 4, nullptr));
+        else
+          PRGB_TRY(launch_coop((const void*)solve_large_scc_k, kBlock, 0, s, args64, 4, nullptr));
         if (timing) PRGB_CUDA(cudaEventRecord(e1, s));
       } else {
         void* args[] = {&a, &L};
@@ -669,19 +1086,26 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       PRGB_CUDA(cudaStreamWaitEvent(side.st[0], side.fork, 0));
       joined[0] = true;
       const int chunk = 1 << clu_shift(r.clu_max);
-      const size_t smem = clu_smem(chunk);
-      if (smem > clu_attr) {
-        PRGB_CUDA(cudaFuncSetAttribute(solve_clu_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        clu_attr = smem;
+      const size_t smem = clu_smem(chunk, mixed);
+      if (smem > clu_attr[mixed]) {
+        PRGB_CUDA(cudaFuncSetAttribute(mixed ? solve_clu_k<true> : solve_clu_k<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        clu_attr[mixed] = smem;
       }
-      solve_clu_k<<<(r.cta - r.clu) * kClu, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
+      if (mixed)
+        solve_clu_k<true><<<(r.cta - r.clu) * kClu, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
+      else
+        solve_clu_k<false><<<(r.cta - r.clu) * kClu, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
       PRGB_LAUNCH();
       nl++;
     }
     if (r.warp > r.cta) {
       PRGB_CUDA(cudaStreamWaitEvent(side.st[1], side.fork, 0));
       joined[1] = true;
-      solve_cta_k<<<r.warp - r.cta, kCtaThreads, kCtaSmem, side.st[1]>>>(a, r.cta);
+      if (mixed)
+        solve_cta_k<true><<<r.warp - r.cta, kCtaThreads, kCtaSmemMixed, side.st[1]>>>(a, r.cta);
+      else
+        solve_cta_k<false><<<r.warp - r.cta, kCtaThreads, kCtaSmem, side.st[1]>>>(a, r.cta);
       PRGB_LAUNCH();
       nl++;
     }
@@ -689,8 +1113,11 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       const int nw = r.single - r.warp;
       PRGB_CUDA(cudaStreamWaitEvent(side.st[2], side.fork, 0));
       joined[2] = true;
-      solve_warp_k<<<(nw + kWarpBlock / 32 - 1) / (kWarpBlock / 32), kWarpBlock, 0, side.st[2]>>>(a, r.warp,
-                                                                                                  r.single);
+      const unsigned nb = (nw + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
+      if (mixed)
+        solve_warp_k<true><<<nb, kWarpBlock, 0, side.st[2]>>>(a, r.warp, r.single);
+      else
+        solve_warp_k<false><<<nb, kWarpBlock, 0, side.st[2]>>>(a, r.warp, r.single);
       PRGB_LAUNCH();
       nl++;
     }
@@ -707,20 +1134,23 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
   return PR_OK;
 }
 
-pr_status solve_edge_visits(const pr_partition_s* P, const int32_t* iters_dev, int64_t* out, Arena& tmp) {
+pr_status solve_edge_visits(const pr_partition_s* P, const int32_t* iters_dev, const int32_t* iters64_dev,
+                            int64_t* out, int64_t* out64, Arena& tmp) {
   cudaStream_t s = tmp.stream();
   *out = 0;
+  if (out64) *out64 = 0;
   if (P->n_comp == 0) return PR_OK;
   unsigned long long* d = nullptr;
-  PRGB_TRY(tmp.alloc(&d, 1));
-  PRGB_CUDA(cudaMemsetAsync(d, 0, 8, s));
+  PRGB_TRY(tmp.alloc(&d, 2));
+  PRGB_CUDA(cudaMemsetAsync(d, 0, 16, s));
   edge_visits_k<<<grid_cap((P->n_comp + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-      P->n_comp, P->c_off, P->c_type, P->int_ptr, P->ext_ptr, iters_dev, d);
+      P->n_comp, P->c_off, P->c_type, P->int_ptr, P->ext_ptr, iters_dev, iters64_dev, d);
   PRGB_LAUNCH();
-  unsigned long long h = 0;
-  PRGB_CUDA(cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s));
+  unsigned long long h[2] = {0, 0};
+  PRGB_CUDA(cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, s));
   PRGB_CUDA(cudaStreamSynchronize(s));
-  *out = (int64_t)h;
+  *out = (int64_t)h[0];
+  if (out64) *out64 = (int64_t)h[1];
   return PR_OK;
 }
 

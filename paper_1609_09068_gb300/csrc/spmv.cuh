@@ -82,6 +82,9 @@ __device__ __forceinline__ double fold2(double a, double b, bool l1) { return l1
 // row, fin(row, acc, heavy) is called exactly once and returns the value to
 // fold into the sweep's norm; light rows fold it themselves (in the caller's
 // per-thread accumulator), heavy rows are folded here into hs.total[parity].
+// The edge sums are accumulated in the type val returns (double, or float
+// for the FP32 sweeps of the mixed-precision solve); chunk partials and the
+// heavy-row folds are kept in FP64.
 template <class Fin, class Val>
 __device__ __forceinline__ void balanced_sweep(const int32_t* __restrict__ ptr, const int32_t* __restrict__ lorder,
                                                int nlight, const HeavyRows& hv, const HeavyScratch& hs, int parity,
@@ -89,6 +92,7 @@ __device__ __forceinline__ void balanced_sweep(const int32_t* __restrict__ ptr, 
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  using T = decltype(val(0));
   const int ngroups = (hv.nheavy + kHGroup - 1) / kHGroup;
   // heavy chunks first, so that the long rows start early
   for (int64_t ch = gw; ch < hv.nchunks; ch += nw) {
@@ -98,7 +102,7 @@ __device__ __forceinline__ void balanced_sweep(const int32_t* __restrict__ ptr, 
     const int j = cha - hv.choff[h];
     const int e0 = ptr[row] + j * kChunkH;
     const int e1 = min(ptr[row + 1], e0 + kChunkH);
-    double acc = 0.0;
+    T acc = 0;
 #pragma unroll
     for (int k = 0; k < kChunkH / 32; k++) {
       const int e = e0 + k * 32 + lane;
@@ -108,7 +112,7 @@ __device__ __forceinline__ void balanced_sweep(const int32_t* __restrict__ ptr, 
     const int nch = hv.choff[h + 1] - hv.choff[h];
     int last = 0;
     if (lane == 0) {
-      hs.part[ch] = acc;
+      hs.part[ch] = (double)acc;
       __threadfence();
       last = atomicAdd(&hs.cnt[h], 1) == nch - 1;
     }
@@ -122,7 +126,7 @@ __device__ __forceinline__ void balanced_sweep(const int32_t* __restrict__ ptr, 
     int glast = 0;
     if (lane == 0) {
       hs.cnt[h] = 0;
-      hs.pn[h] = fin(row, t, true);
+      hs.pn[h] = fin(row, (T)t, true);
       __threadfence();
       const int g = h / kHGroup;
       const int gsz = min(kHGroup, hv.nheavy - g * kHGroup);
@@ -160,7 +164,7 @@ __device__ __forceinline__ void balanced_sweep(const int32_t* __restrict__ ptr, 
     if (i < nlight) {
       const int row = lorder[i];
       const int b = ptr[row], e = ptr[row + 1];
-      double acc = 0.0;
+      T acc = 0;
 #pragma unroll 4
       for (int q = b; q < e; q++) acc += val(q);
       fin(row, acc, false);
