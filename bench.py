@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="web")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--breakdown", action="store_true", help="print per-phase times to stderr")
+    ap.add_argument("--breakdown", action="store_true", help="(per-step times always go to stderr)")
     return ap.parse_args()
 
 
@@ -97,7 +97,7 @@ class Clocks:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
-        time.sleep(0.3)
+        time.sleep(1.0)  # let the sampler start up before the timed region
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
@@ -386,9 +386,9 @@ def run_ours(args):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-        if args.breakdown:
-            print(json.dumps({"phase_ms_per_step": phase.tolist(), "global_ms": gph.tolist(),
-                              "e2e_ms": e2e_ms}), file=sys.stderr)
+        print(json.dumps({"phase_ms_per_step": np.round(phase, 3).tolist(),
+                          "global_ms_per_step": np.round(gph, 3).tolist(),
+                          "e2e_ms": np.round(e2e_ms, 3).tolist()}), file=sys.stderr)
     if dist is not None:
         dist.destroy_process_group()
     return 0

@@ -39,11 +39,21 @@ static unsigned gridw(int64_t n) {
 
 __global__ void csize_k(int32_t n, const int32_t* crep, const int32_t* level, int32_t* csize, uint8_t* isrep,
                         Ctl* ctl) {
-  for (int64_t v = gtid(); v < n; v += gstride()) {
-    atomicAdd(&csize[crep[v]], 1);
-    isrep[v] = crep[v] == (int32_t)v;
-    atomicMax(&ctl->cnt[5], level[v]);
+  // lanes of the same component share one atomic; one level maximum per warp
+  int lmax = -1;
+  const int lane = threadIdx.x & 31;
+  for (int64_t vb = gtid() - lane; vb < n; vb += gstride()) {
+    const int64_t v = vb + lane;
+    const int r = v < n ? crep[v] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, r);
+    if (r >= 0 && lane == __ffs(same) - 1) atomicAdd(&csize[r], __popc(same));
+    if (v < n) {
+      isrep[v] = r == (int32_t)v;
+      lmax = max(lmax, level[v]);
+    }
   }
+  lmax = __reduce_max_sync(0xffffffffu, lmax);
+  if (lane == 0 && lmax >= 0) atomicMax(&ctl->cnt[5], lmax);
 }
 
 __global__ void compact_reps_k(int32_t n, const uint8_t* isrep, const int32_t* ridx, const int32_t* csize,
@@ -169,10 +179,17 @@ __global__ void level_begin_k(int32_t K, const int32_t* c_level, int32_t maxl, i
 
 __global__ void class_begin_k(int32_t K, const int32_t* c_level, const int32_t* c_off, int32_t maxl,
                               int32_t* cls /* [nlev][kNumClasses] */) {
+  // Within a level the classes do not decrease (sizes descend), so class k
+  // of a level begins at the first component whose class is >= k: that is
+  // c for every k in (class of c's predecessor in the level, class of c].
+  // Each slot is written once; slots of classes a level lacks at its end
+  // keep their initial value.
   for (int64_t c = gtid(); c < K; c += gstride()) {
     const int li = maxl - c_level[c];
     const int cl = size_class(c_off[c + 1] - c_off[c]);
-    for (int k = 1; k <= cl; k++) atomicMin(&cls[li * kNumClasses + k], (int)c);
+    const bool first = c == 0 || c_level[c - 1] != c_level[c];
+    const int pcl = first ? 0 : size_class(c_off[c] - c_off[c - 1]);
+    for (int k = pcl + 1; k <= cl; k++) cls[li * kNumClasses + k] = (int)c;
   }
 }
 

@@ -29,12 +29,22 @@ __global__ void count_nodes_k(const int32_t* __restrict__ optr, const int32_t* _
                               const int32_t* __restrict__ rep, int32_t* nsize, int32_t* smin, int32_t* pending,
                               int32_t* cin_cnt) {
   const int lane = threadIdx.x & 31;
+  // node sizes and smallest members: one thread per vertex, lanes of the
+  // same node combined first (a giant SCC would otherwise take one atomic
+  // per member on a single address)
+  for (int64_t vb = (int64_t)gwarp_l() * 32; vb < n; vb += (int64_t)nwarps_l() * 32) {
+    const int64_t v = vb + lane;
+    const int U = v < n ? rep[v] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, U);
+    const int lead = __ffs(same) - 1;
+    const int mn = __reduce_min_sync(same, (int)v);
+    if (U >= 0 && lane == lead) {
+      atomicAdd(&nsize[U], __popc(same));
+      atomicMin(&smin[U], mn);
+    }
+  }
   for (int64_t u = gwarp_l(); u < n; u += nwarps_l()) {
     const int U = rep[u];
-    if (lane == 0) {
-      atomicAdd(&nsize[U], 1);
-      atomicMin(&smin[U], (int)u);
-    }
     int ext = 0;
     for (int e = optr[u] + lane; e < optr[u + 1]; e += 32) {
       const int W = rep[oidx[e]];
@@ -43,7 +53,7 @@ __global__ void count_nodes_k(const int32_t* __restrict__ optr, const int32_t* _
         atomicAdd(&cin_cnt[W], 1);
       }
     }
-    ext = (int)group_sum<32>((double)ext);
+    ext = __reduce_add_sync(0xffffffffu, ext);
     if (lane == 0 && ext) atomicAdd(&pending[U], ext);
   }
 }

@@ -100,7 +100,10 @@ struct PropK {
   __device__ bool edge(int e, int4 p, int wave, int* w, int* nch) const {
     *w = idx[e];
     const int x = *w;
-    if (rep[x] >= 0 || pin[x] != p.y || pout[x] != p.z || vload(&sig[x]) >= p.x) return false;
+    // four independent loads in flight at once (a short-circuit test would
+    // serialise them)
+    const int rx = rep[x], px = pin[x], qx = pout[x], sx = vload(&sig[x]);
+    if ((rx >= 0) | (px != p.y) | (qx != p.z) | (sx >= p.x)) return false;
     const int old = atomicMax(&sig[x], p.x);
     if (old < p.x && atomicExch(&stamp[x], wave) != wave) {
       *nch = nchunks_of(ptr[x + 1] - ptr[x]);
@@ -147,7 +150,13 @@ __global__ void pivot_k(const int32_t* __restrict__ optr, const int32_t* __restr
                                    (unsigned long long)(uint32_t)v;
     loc = key > loc ? key : loc;
   }
-  if (loc) atomicMax(best, loc);
+  // one atomic per warp: a grid of single-address atomics would serialise
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, loc, o);
+    loc = t > loc ? t : loc;
+  }
+  if ((threadIdx.x & 31) == 0 && loc) atomicMax(best, loc);
 }
 
 struct ReachK {
@@ -164,7 +173,8 @@ struct ReachK {
   __device__ bool edge(int e, int4, int, int* w, int* nch) const {
     *w = idx[e];
     const int x = *w;
-    if (rep[x] >= 0 || (need != nullptr && need[x] != tag_need) || atomicExch(&mark[x], tag) == tag) return false;
+    const int rx = rep[x], nx = need != nullptr ? need[x] : tag_need, mx = vload(&mark[x]);
+    if ((rx >= 0) | (nx != tag_need) | (mx == tag) || atomicExch(&mark[x], tag) == tag) return false;
     *nch = nchunks_of(ptr[x + 1] - ptr[x]);
     return *nch > 0;
   }
@@ -195,7 +205,8 @@ __global__ void fwbw_max_k(int32_t n, const int32_t* fw, const int32_t* bw, int*
   int loc = -1;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
     if (fw[v] == 1 && bw[v] == 2) loc = (int)v;
-  if (loc >= 0) atomicMax(best, loc);
+  loc = __reduce_max_sync(0xffffffffu, loc);
+  if ((threadIdx.x & 31) == 0 && loc >= 0) atomicMax(best, loc);
 }
 
 __global__ void fwbw_assign_k(int32_t n, const int32_t* fw, const int32_t* bw, const int* best, int32_t* rep,

@@ -38,11 +38,17 @@ struct Pusher {
   }
 };
 
-// One wave: each warp takes one item at a time and walks its (at most
-// kChunkE) edges 32 at a time, so index loads stay coalesced.  The kernel
-// supplies
+// One wave.  Each warp takes `per` items, per = ceil(items / warps) capped
+// at 32, so that every warp has work however small the frontier; they are
+// strided by the number of warps, so that the consecutive chunks of a hub
+// go to different warps.  A warp lays its items' edge ranges end to end
+// (a prefix sum over the run, one item per lane) and walks the concatenation
+// 32 edges at a time; each lane finds the item of its edge by a binary
+// search over the prefix sums.  A warp thus keeps 32 edges' loads in flight
+// whether its items have one edge each or hundreds.  The kernel supplies
 //   K::range(v, j, &e0, &e1)      edges of item (v, j)
-//   K::pre(v, j) -> int4          per-item data (read by every lane)
+//   K::pre(v, j, first) -> int4   per-item data; called once per item with
+//                                 first = true
 //   K::edge(e, pre, wave, &w, &nch) -> bool   visit edge e; true pushes w
 //                                 (with nch chunks) into the next frontier
 template <class K>
@@ -53,16 +59,39 @@ __device__ __forceinline__ void one_wave(Ctl* ctl, const Frontier& f, int wave, 
   const int* cc = (wave & 1) ? f.bc : f.ac;
   Pusher push{(wave & 1) ? f.av : f.bv, (wave & 1) ? f.ac : f.bc, &ctl->cnt[(wave + 1) % 3], f.cap, ctl};
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[(wave + 2) % 3] = 0;
-  for (int i = w0; i < cnt; i += nws) {
-    const int v = cv[i], j = cc[i];
-    int e0, e1;
-    k.range(v, j, &e0, &e1);
-    const int4 pre = k.pre(v, j, lane == 0);
-    for (int base = e0; base < e1; base += 32) {
-      const int e = base + lane;
+  const int per = min(32, max(1, (int)(((int64_t)cnt + nws - 1) / nws)));
+  for (int64_t r0 = 0; r0 < cnt; r0 += (int64_t)nws * per) {
+    const int64_t i = r0 + w0 + (int64_t)lane * nws;  // this lane's item
+    int e0 = 0, d = 0;
+    int4 pre = make_int4(0, 0, 0, 0);
+    if (lane < per && i < cnt) {
+      const int v = cv[i], j = cc[i];
+      int e1 = 0;
+      k.range(v, j, &e0, &e1);
+      d = e1 - e0;
+      pre = k.pre(v, j, true);
+    }
+    int incl = d;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int base = 0; base < total; base += 32) {
+      const int q = base + lane;
+      // it = number of items whose edges end at or before q
+      int it = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(0xffffffffu, incl, it + step - 1) <= q) it += step;
+      const int ie0 = __shfl_sync(0xffffffffu, e0, it);
+      const int ibeg = __shfl_sync(0xffffffffu, incl - d, it);
+      const int4 ip = make_int4(__shfl_sync(0xffffffffu, pre.x, it), __shfl_sync(0xffffffffu, pre.y, it),
+                                __shfl_sync(0xffffffffu, pre.z, it), __shfl_sync(0xffffffffu, pre.w, it));
       bool want = false;
       int w = 0, nch = 0;
-      if (e < e1) want = k.edge(e, pre, wave, &w, &nch);
+      if (q < total) want = k.edge(ie0 + (q - ibeg), ip, wave, &w, &nch);
       push(want, w, want ? nch : 0);
     }
   }
