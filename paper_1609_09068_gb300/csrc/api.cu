@@ -2,6 +2,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -10,7 +11,6 @@
 
 namespace prgb {
 int last_cuda_error();
-long long launch_count();
 pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wave, int32_t max_wave, Arena& tmp,
                        Ctl* ctl);
 
@@ -177,6 +177,7 @@ pr_status pr_partition_info(const pr_partition* part, int32_t* n, int64_t* m, in
 
 void pr_partition_destroy(pr_partition* part) {
   if (!part) return;
+  delete part->plan;
   delete part->keep;
   delete part;
 }
@@ -205,39 +206,51 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t K = part->n_comp;
+  const bool timing = stats && stats->timing;
   Arena tmp(s);
   Ctl* ctl = nullptr;
   int32_t* iters = nullptr;
-  int32_t* replay = nullptr;
-  const double* du = u;
-  double* dR = R;
-  PRGB_TRY(tmp.alloc(&ctl, 1));
-  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
   int32_t* iters64 = nullptr;
-  PRGB_TRY(tmp.alloc(&iters, (size_t)K));
-  if (K > 0) PRGB_CUDA(cudaMemsetAsync(iters, 0, (size_t)K * 4, s));
-  if (mixed) {
-    PRGB_TRY(tmp.alloc(&iters64, (size_t)K));
-    if (K > 0) PRGB_CUDA(cudaMemsetAsync(iters64, 0, (size_t)K * 4, s));
-  }
-  if (o.replay_iters && K > 0) {
-    PRGB_TRY(tmp.alloc(&replay, (size_t)K));
-    PRGB_CUDA(cudaMemcpyAsync(replay, o.replay_iters, (size_t)K * 4, cudaMemcpyHostToDevice, s));
-  }
-  if (o.io_on_host && n > 0) {
-    double *tu = nullptr, *tR = nullptr;
-    PRGB_TRY(tmp.alloc(&tu, (size_t)n));
-    PRGB_TRY(tmp.alloc(&tR, (size_t)n));
-    PRGB_CUDA(cudaMemcpyAsync(tu, u, (size_t)n * 8, cudaMemcpyHostToDevice, s));
-    du = tu;
-    dR = tR;
-  }
   int64_t launches = 0;
-  KernelTiming kt;
-  const bool timing = stats && stats->timing;
-  PRGB_TRY(run_solve(part, c, du, tol, o.norm, o.max_iter, replay, mixed, dR, iters, iters64, tmp, ctl, &launches,
-                     timing ? &kt : nullptr));
-  if (o.io_on_host && n > 0) PRGB_CUDA(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  KernelTiming kt_local;
+  KernelTiming* kt = &kt_local;
+  pr_partition_s* P = const_cast<pr_partition_s*>(part);  // the plan is a cache
+  std::unique_lock<std::mutex> lock(P->plan_mu, std::defer_lock);
+  if (!o.replay_iters) {
+    // the level loop replayed from the partition's cached CUDA graph
+    lock.lock();
+    SolvePlan* pl = nullptr;
+    PRGB_TRY(plan_solve(P, c, u, o.io_on_host != 0, tol, o.norm, o.max_iter, mixed, timing, R, o.io_on_host != 0,
+                        s, &pl, &launches));
+    ctl = pl->ctl;
+    iters = pl->iters;
+    iters64 = mixed ? pl->iters64 : nullptr;
+    kt = &pl->kt;
+  } else {
+    // replayed iteration counts: buffers of its own, launched directly
+    int32_t* replay = nullptr;
+    const double* du = u;
+    double* dR = R;
+    PRGB_TRY(tmp.alloc(&ctl, 1));
+    PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    PRGB_TRY(tmp.alloc(&iters, (size_t)K));
+    if (K > 0) PRGB_CUDA(cudaMemsetAsync(iters, 0, (size_t)K * 4, s));
+    if (K > 0) {
+      PRGB_TRY(tmp.alloc(&replay, (size_t)K));
+      PRGB_CUDA(cudaMemcpyAsync(replay, o.replay_iters, (size_t)K * 4, cudaMemcpyHostToDevice, s));
+    }
+    if (o.io_on_host && n > 0) {
+      double *tu = nullptr, *tR = nullptr;
+      PRGB_TRY(tmp.alloc(&tu, (size_t)n));
+      PRGB_TRY(tmp.alloc(&tR, (size_t)n));
+      PRGB_CUDA(cudaMemcpyAsync(tu, u, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+      du = tu;
+      dR = tR;
+    }
+    PRGB_TRY(run_solve(part, c, du, tol, o.norm, o.max_iter, replay, false, dR, iters, nullptr, tmp, ctl, &launches,
+                       timing ? kt : nullptr));
+    if (o.io_on_host && n > 0) PRGB_CUDA(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  }
   int flags = 0;
   PRGB_TRY(finish_sync(s, ctl, &flags));
   if (stats) {
@@ -267,12 +280,12 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
       if (timing) {
         stats->kernel_ms = 0.0f;
         stats->kernel_bytes = 0;
-        stats->kernel_launches = (int64_t)kt.comps.size();
-        for (size_t i = 0; i < kt.comps.size(); i++) {
+        stats->kernel_launches = (int64_t)kt->comps.size();
+        for (size_t i = 0; i < kt->comps.size(); i++) {
           float ms = 0.0f;
-          PRGB_CUDA(cudaEventElapsedTime(&ms, kt.start[i], kt.stop[i]));
+          PRGB_CUDA(cudaEventElapsedTime(&ms, kt->start[i], kt->stop[i]));
           stats->kernel_ms += ms;
-          const LargeComp& L = kt.comps[i];
+          const LargeComp& L = kt->comps[i];
           const int64_t it = h[L.c];
           // FP32 sweeps move 4 B per edge + 24 B per row (z gather and
           // write, F read/write, row pointer, 1/outdeg in FP32)

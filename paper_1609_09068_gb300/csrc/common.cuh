@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "prgb.h"
@@ -36,6 +37,8 @@ void set_last_cuda_error(cudaError_t e);
   } while (0)
 
 void count_launch();
+long long launch_count();
+void add_launches(long long d);  // kernels launched by a graph replay (or removed: captured, not run)
 #define PRGB_LAUNCH()            \
   do {                           \
     ::prgb::count_launch();      \
@@ -374,6 +377,8 @@ constexpr int kCtaCompMax = 256;     // <= 256 vertices: one CTA
 constexpr int kCluCompMax = 16384;   // <= 16384 vertices: one cluster of 8 CTAs
 constexpr int kNumClasses = 5;       // grid-wide, cluster, CTA, warp, 1-vertex
 
+struct SolvePlan;  // solve.cuh
+
 }  // namespace prgb
 
 // The opaque handles of the C ABI.
@@ -421,4 +426,6 @@ struct pr_partition_s {
   int32_t max_heavy = 0, max_chunks = 0;  // largest slice over the large components
   std::vector<prgb::LevelRange> levels;  // host, processing order
   std::vector<prgb::LargeComp> large;    // host
+  prgb::SolvePlan* plan = nullptr;       // cached solve (graph), built on first use
+  std::mutex plan_mu;                    // one call at a time uses the plan
 };

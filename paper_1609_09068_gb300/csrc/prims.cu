@@ -12,6 +12,7 @@ static thread_local int g_last_cuda_error = 0;
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(long long d) { g_launches.fetch_add(d, std::memory_order_relaxed); }
 void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = static_cast<int>(e); }
 int last_cuda_error() { return g_last_cuda_error; }
 

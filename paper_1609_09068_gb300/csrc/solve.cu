@@ -927,28 +927,6 @@ __global__ void edge_visits_k(int32_t K, const int32_t* c_off, const uint8_t* c_
 
 namespace prgb {
 
-// three non-blocking side streams and the fork / join events of a solve
-struct SideStreams {
-  cudaStream_t st[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t fork = nullptr;
-  cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
-  pr_status create() {
-    for (int q = 0; q < 3; q++) {
-      PRGB_CUDA(cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking));
-      PRGB_CUDA(cudaEventCreateWithFlags(&join[q], cudaEventDisableTiming));
-    }
-    PRGB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    return PR_OK;
-  }
-  ~SideStreams() {
-    for (int q = 0; q < 3; q++) {
-      if (st[q]) cudaStreamDestroy(st[q]);
-      if (join[q]) cudaEventDestroy(join[q]);
-    }
-    if (fork) cudaEventDestroy(fork);
-  }
-};
-
 static unsigned grid_cap(int64_t blocks) {
   int64_t cap = (int64_t)num_sms() * 32;
   return (unsigned)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
@@ -959,18 +937,91 @@ __global__ void to_float_k(int32_t n, const double* __restrict__ x, float* __res
     y[i] = (float)x[i];
 }
 
-pr_status run_solve(const pr_partition_s* P, double c, const double* u, double tol, int norm, int max_iter,
-                    const int32_t* replay, bool mixed, double* R, int32_t* iters_dev, int32_t* iters64_dev,
-                    Arena& tmp, Ctl* ctl, int64_t* launches, KernelTiming* timing) {
-  cudaStream_t s = tmp.stream();
-  const int32_t n = P->g.n;
-  int64_t nl = 0;
-  if (n == 0) {
-    *launches = 0;
-    return PR_OK;
+pr_status SideStreams::create() {
+  for (int q = 0; q < 3; q++) {
+    PRGB_CUDA(cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking));
+    PRGB_CUDA(cudaEventCreateWithFlags(&join[q], cudaEventDisableTiming));
   }
+  PRGB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  return PR_OK;
+}
+
+SideStreams::~SideStreams() {
+  for (int q = 0; q < 3; q++) {
+    if (st[q]) cudaStreamDestroy(st[q]);
+    if (join[q]) cudaEventDestroy(join[q]);
+  }
+  if (fork) cudaEventDestroy(fork);
+}
+
+pr_status KernelTiming::ensure(const pr_partition_s* P) {
+  size_t k = 0;
+  for (const LargeComp& L : P->large) k += L.type == PR_TYPE_SCC;
+  comps.clear();
+  for (const LargeComp& L : P->large)
+    if (L.type == PR_TYPE_SCC) comps.push_back(L);
+  while (start.size() < k) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PRGB_CUDA(cudaEventCreate(&e0));
+    start.push_back(e0);
+    PRGB_CUDA(cudaEventCreate(&e1));
+    stop.push_back(e1);
+  }
+  return PR_OK;
+}
+
+KernelTiming::~KernelTiming() {
+  for (cudaEvent_t e : start) cudaEventDestroy(e);
+  for (cudaEvent_t e : stop) cudaEventDestroy(e);
+}
+
+// Work buffers of a solve (all by permuted position), allocated from `a`;
+// also sets the kernels' shared-memory limits for this partition, so that
+// nothing but launches and memsets is left for the level loop.
+pr_status alloc_solve_bufs(const pr_partition_s* P, bool mixed, Arena& a, SolveBufs* b, int64_t* nl) {
+  cudaStream_t s = a.stream();
+  const int32_t n = P->g.n;
+  PRGB_TRY(a.alloc(&b->R, n));
+  PRGB_TRY(a.alloc(&b->zr, n));
+  PRGB_TRY(a.alloc(&b->W, n));
+  // shared by the level gathers and the grid-wide series (left zeroed after each)
+  PRGB_TRY(alloc_heavy_scratch(&b->hs, std::max(P->max_heavy, P->max_xheavy), std::max(P->max_chunks, P->max_xchunks),
+                               a));
+  if (P->max_large > 0) {
+    PRGB_TRY(a.alloc(&b->zA, P->max_large));
+    PRGB_TRY(a.alloc(&b->zB, P->max_large));
+    PRGB_TRY(a.alloc(&b->part, (size_t)2 * num_sms() * 8));
+  }
+  b->invf = nullptr;
+  if (mixed && n > 0) {
+    PRGB_TRY(a.alloc(&b->invf, n));
+    to_float_k<<<grid_cap((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, P->p_inv, b->invf);
+    PRGB_LAUNCH();
+    ++*nl;
+  }
+  static bool cta_attr = false;
+  static size_t clu_attr[2] = {48 * 1024, 48 * 1024};
+  if (!cta_attr) {
+    PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
+    PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kCtaSmemMixed));
+    cta_attr = true;
+  }
+  int clu_max = 0;
+  for (const LevelRange& r : P->levels) clu_max = std::max(clu_max, r.cta > r.clu ? r.clu_max : 0);
+  const size_t smem = clu_smem(1 << clu_shift(clu_max), mixed);
+  if (clu_max > 0 && smem > clu_attr[mixed]) {
+    PRGB_CUDA(cudaFuncSetAttribute(mixed ? solve_clu_k<true> : solve_clu_k<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    clu_attr[mixed] = smem;
+  }
+  return PR_OK;
+}
+
+SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, double tol, int norm, int max_iter,
+                          const int32_t* replay, const SolveBufs& b, int32_t* iters, int32_t* iters64, Ctl* ctl) {
   SolveArgs a;
-  a.n = n;
+  a.n = P->g.n;
   a.c = c;
   a.tol = tol;
   a.norm = norm;
@@ -989,45 +1040,30 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
   a.sub_ptr = P->sub_ptr;
   a.c_type = P->c_type;
   a.replay = replay;
-  a.iters = iters_dev;
-  a.ctl = ctl;
   a.xlorder = P->xlorder;
-  a.p_invf = nullptr;
-  a.iters64 = iters64_dev;
-  if (mixed) {
-    float* invf = nullptr;
-    PRGB_TRY(tmp.alloc(&invf, n));
-    to_float_k<<<grid_cap((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, P->p_inv, invf);
-    PRGB_LAUNCH();
-    nl++;
-    a.p_invf = invf;
-  }
-  PRGB_TRY(tmp.alloc(&a.R, n));
-  PRGB_TRY(tmp.alloc(&a.zr, n));
-  PRGB_TRY(tmp.alloc(&a.W, n));
-  double *zA = nullptr, *zB = nullptr, *part = nullptr;
-  HeavyScratch hs;  // shared by the level gathers and the grid-wide series (left zeroed after each)
-  PRGB_TRY(alloc_heavy_scratch(&hs, std::max(P->max_heavy, P->max_xheavy), std::max(P->max_chunks, P->max_xchunks),
-                               tmp));
-  if (P->max_large > 0) {
-    PRGB_TRY(tmp.alloc(&zA, P->max_large));
-    PRGB_TRY(tmp.alloc(&zB, P->max_large));
-    PRGB_TRY(tmp.alloc(&part, (size_t)2 * num_sms() * 8));
-  }
-  static bool cta_attr = false;
-  static size_t clu_attr[2] = {48 * 1024, 48 * 1024};
-  // The cluster, CTA and warp kernels of a level are independent: they run on
-  // three side streams, forked after the level's gather and joined before
-  // the next level, so one kernel's tail overlaps the others.
-  SideStreams side;
-  PRGB_TRY(side.create());
-  if (!cta_attr) {
-    PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
-    PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kCtaSmemMixed));
-    cta_attr = true;
-  }
-  size_t li_large = 0;
+  a.p_invf = b.invf;
+  a.iters64 = iters64;
+  a.W = b.W;
+  a.R = b.R;
+  a.zr = b.zr;
+  a.iters = iters;
+  a.ctl = ctl;
+  return a;
+}
+
+// The level loop (Sec. 4.3): per level, the inflow gather and 1-vertex
+// components on s, the grid-wide components on s, then the cluster, CTA and
+// warp classes on the three side streams, joined back into s before the
+// next level.  Only launches, memsets and event records: it can be
+// captured into a CUDA graph.
+pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& b, bool mixed, SideStreams& side,
+                         cudaStream_t s, KernelTiming* timing, int64_t* nl) {
+  Ctl* ctl = a.ctl;
+  double* zA = b.zA;
+  double* zB = b.zB;
+  double* part = b.part;
+  HeavyScratch hs = b.hs;
+  size_t li_large = 0, ti = 0;
   for (size_t li = 0; li < P->levels.size(); li++) {
     const LevelRange& r = P->levels[li];
     {
@@ -1042,7 +1078,7 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       const int64_t work = (int64_t)(r.vend - r.vbeg) + (int64_t)xv.nchunks * 32;
       gather_level_k<<<grid_cap((work + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, r, xv, hs);
       PRGB_LAUNCH();
-      nl++;
+      ++*nl;
     }
     while (li_large < P->large.size() && P->large[li_large].level_idx == (int)li) {
       LargeComp L = P->large[li_large++];
@@ -1060,25 +1096,20 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
         float* F = reinterpret_cast<float*>(zB);
         void* args64[] = {&a, &L, &zA, &zB, &part, &hv, &hs};
         void* args32[] = {&a, &L, &fz, &F, &part, &hv, &hs};
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (timing) {
-          PRGB_CUDA(cudaEventCreate(&e0));
-          timing->start.push_back(e0);
-          PRGB_CUDA(cudaEventCreate(&e1));
-          timing->stop.push_back(e1);
-          timing->comps.push_back(L);
-          PRGB_CUDA(cudaEventRecord(e0, s));
-        }
+        // external records: inside a captured graph they become event-record
+        // nodes, so the events time each replay
+        if (timing) PRGB_CUDA(cudaEventRecordWithFlags(timing->start[ti], s, cudaEventRecordExternal));
         if (mixed)
           PRGB_TRY(launch_coop((const void*)solve_large_scc_mx_k, kBlock, 0, s, args32, 4, nullptr));
         else
           PRGB_TRY(launch_coop((const void*)solve_large_scc_k, kBlock, 0, s, args64, 4, nullptr));
-        if (timing) PRGB_CUDA(cudaEventRecord(e1, s));
+        if (timing) PRGB_CUDA(cudaEventRecordWithFlags(timing->stop[ti], s, cudaEventRecordExternal));
+        ti++;
       } else {
         void* args[] = {&a, &L};
         PRGB_TRY(launch_coop((const void*)solve_large_cac_k, kBlock, 0, s, args, 4, nullptr));
       }
-      nl++;
+      ++*nl;
     }
     PRGB_CUDA(cudaEventRecord(side.fork, s));
     bool joined[3] = {false, false, false};
@@ -1087,17 +1118,12 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       joined[0] = true;
       const int chunk = 1 << clu_shift(r.clu_max);
       const size_t smem = clu_smem(chunk, mixed);
-      if (smem > clu_attr[mixed]) {
-        PRGB_CUDA(cudaFuncSetAttribute(mixed ? solve_clu_k<true> : solve_clu_k<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        clu_attr[mixed] = smem;
-      }
       if (mixed)
         solve_clu_k<true><<<(r.cta - r.clu) * kClu, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
       else
         solve_clu_k<false><<<(r.cta - r.clu) * kClu, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
       PRGB_LAUNCH();
-      nl++;
+      ++*nl;
     }
     if (r.warp > r.cta) {
       PRGB_CUDA(cudaStreamWaitEvent(side.st[1], side.fork, 0));
@@ -1107,7 +1133,7 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       else
         solve_cta_k<false><<<r.warp - r.cta, kCtaThreads, kCtaSmem, side.st[1]>>>(a, r.cta);
       PRGB_LAUNCH();
-      nl++;
+      ++*nl;
     }
     if (r.single > r.warp) {
       const int nw = r.single - r.warp;
@@ -1119,7 +1145,7 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       else
         solve_warp_k<false><<<nb, kWarpBlock, 0, side.st[2]>>>(a, r.warp, r.single);
       PRGB_LAUNCH();
-      nl++;
+      ++*nl;
     }
     for (int q = 0; q < 3; q++) {
       if (!joined[q]) continue;
@@ -1127,9 +1153,147 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
       PRGB_CUDA(cudaStreamWaitEvent(s, side.join[q], 0));
     }
   }
-  scatter_out_k<<<grid_cap((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, P->perm, a.R, R);
+  return PR_OK;
+}
+
+pr_status scatter_out(const pr_partition_s* P, const double* Rp, double* R, cudaStream_t s, int64_t* nl) {
+  const int32_t n = P->g.n;
+  if (n == 0) return PR_OK;
+  scatter_out_k<<<grid_cap((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, P->perm, Rp, R);
   PRGB_LAUNCH();
-  nl++;
+  ++*nl;
+  return PR_OK;
+}
+
+pr_status run_solve(const pr_partition_s* P, double c, const double* u, double tol, int norm, int max_iter,
+                    const int32_t* replay, bool mixed, double* R, int32_t* iters_dev, int32_t* iters64_dev,
+                    Arena& tmp, Ctl* ctl, int64_t* launches, KernelTiming* timing) {
+  cudaStream_t s = tmp.stream();
+  int64_t nl = 0;
+  *launches = 0;
+  if (P->g.n == 0) return PR_OK;
+  SolveBufs b;
+  PRGB_TRY(alloc_solve_bufs(P, mixed, tmp, &b, &nl));
+  const SolveArgs a = make_solve_args(P, c, u, tol, norm, max_iter, replay, b, iters_dev, iters64_dev, ctl);
+  SideStreams side;
+  PRGB_TRY(side.create());
+  if (timing) PRGB_TRY(timing->ensure(P));
+  PRGB_TRY(enqueue_levels(P, a, b, mixed, side, s, timing, &nl));
+  PRGB_TRY(scatter_out(P, b.R, R, s, &nl));
+  *launches = nl;
+  return PR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-partition CUDA graph of the level loop
+// ---------------------------------------------------------------------------
+SolvePlan::~SolvePlan() {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (done) cudaEventDestroy(done);
+  if (cs) cudaStreamDestroy(cs);
+  delete keep;
+}
+
+// (Re)build the graph for these parameters if the cached one differs.
+static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double tol, int norm, int max_iter,
+                              bool mixed, bool timing) {
+  if (pl->exec && pl->c == c && pl->tol == tol && pl->norm == norm && pl->max_iter == max_iter &&
+      pl->mixed == mixed && pl->timing == timing)
+    return PR_OK;
+  const int32_t n = P->g.n;
+  const int32_t K = P->n_comp;
+  if (pl->exec) {
+    cudaGraphExecDestroy(pl->exec);
+    pl->exec = nullptr;
+  }
+  if (pl->graph) {
+    cudaGraphDestroy(pl->graph);
+    pl->graph = nullptr;
+  }
+  if (!pl->keep) {
+    pl->keep = new (std::nothrow) Arena(P->stream);
+    if (!pl->keep) return PR_ENOMEM;
+    PRGB_CUDA(cudaStreamCreateWithFlags(&pl->cs, cudaStreamNonBlocking));
+    PRGB_CUDA(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
+    PRGB_TRY(pl->side.create());
+    PRGB_TRY(pl->keep->alloc(&pl->ctl, 1));
+    PRGB_TRY(pl->keep->alloc(&pl->iters, (size_t)K + 1));
+    PRGB_TRY(pl->keep->alloc(&pl->iters64, (size_t)K + 1));
+    PRGB_TRY(pl->keep->alloc(&pl->u, (size_t)n + 1));
+    PRGB_TRY(pl->keep->alloc(&pl->Rout, (size_t)n + 1));
+    pl->have_mixed_bufs = false;
+    int64_t nl = 0;
+    PRGB_TRY(alloc_solve_bufs(P, false, *pl->keep, &pl->b, &nl));
+    PRGB_CUDA(cudaStreamSynchronize(P->stream));
+  }
+  if (mixed && !pl->have_mixed_bufs) {
+    // a second set only for its FP32 1/outdeg and the mixed kernels' limits
+    int64_t nl = 0;
+    SolveBufs mb;
+    PRGB_TRY(alloc_solve_bufs(P, true, *pl->keep, &mb, &nl));
+    pl->b.invf = mb.invf;
+    pl->have_mixed_bufs = true;
+    PRGB_CUDA(cudaStreamSynchronize(P->stream));
+  }
+  if (timing) PRGB_TRY(pl->kt.ensure(P));
+  const SolveArgs a = make_solve_args(P, c, pl->u, tol, norm, max_iter, nullptr, pl->b, pl->iters,
+                                      mixed ? pl->iters64 : nullptr, pl->ctl);
+  const long long before = launch_count();
+  int64_t nl = 0;
+  PRGB_CUDA(cudaStreamBeginCapture(pl->cs, cudaStreamCaptureModeThreadLocal));
+  pr_status st = PR_OK;
+  if (cudaMemsetAsync(pl->ctl, 0, sizeof(Ctl), pl->cs) != cudaSuccess ||
+      cudaMemsetAsync(pl->iters, 0, ((size_t)K + 1) * 4, pl->cs) != cudaSuccess ||
+      cudaMemsetAsync(pl->iters64, 0, ((size_t)K + 1) * 4, pl->cs) != cudaSuccess)
+    st = PR_ECUDA;
+  if (st == PR_OK) st = enqueue_levels(P, a, pl->b, mixed, pl->side, pl->cs, timing ? &pl->kt : nullptr, &nl);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(pl->cs, &g);
+  add_launches(before - launch_count());  // captured, not launched
+  if (st != PR_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  PRGB_CUDA(ec);
+  pl->graph = g;
+  PRGB_CUDA(cudaGraphInstantiate(&pl->exec, g, 0));
+  pl->nodes = nl;
+  pl->c = c;
+  pl->tol = tol;
+  pl->norm = norm;
+  pl->max_iter = max_iter;
+  pl->mixed = mixed;
+  pl->timing = timing;
+  return PR_OK;
+}
+
+pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_host, double tol, int norm,
+                     int max_iter, bool mixed, bool timing, double* R, bool R_on_host, cudaStream_t s,
+                     SolvePlan** out, int64_t* launches) {
+  if (!P->plan) {
+    P->plan = new (std::nothrow) SolvePlan;
+    if (!P->plan) return PR_ENOMEM;
+  }
+  SolvePlan* pl = P->plan;
+  *out = pl;
+  const int32_t n = P->g.n;
+  PRGB_TRY(plan_prepare(P, pl, c, tol, norm, max_iter, mixed, timing));
+  // the plan's buffers are reused: order this call after the previous one
+  PRGB_CUDA(cudaStreamWaitEvent(s, pl->done, 0));
+  if (n > 0)
+    PRGB_CUDA(cudaMemcpyAsync(pl->u, u, (size_t)n * 8, u_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                              s));
+  PRGB_CUDA(cudaGraphLaunch(pl->exec, s));
+  add_launches(pl->nodes);
+  int64_t nl = pl->nodes;
+  if (R_on_host) {
+    PRGB_TRY(scatter_out(P, pl->b.R, pl->Rout, s, &nl));
+    if (n > 0) PRGB_CUDA(cudaMemcpyAsync(R, pl->Rout, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  } else {
+    PRGB_TRY(scatter_out(P, pl->b.R, R, s, &nl));
+  }
+  PRGB_CUDA(cudaEventRecord(pl->done, s));
   *launches = nl;
   return PR_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "spmv.cuh"
 
 namespace prgb {
 
@@ -35,23 +36,77 @@ struct SolveArgs {
   Ctl* ctl;
 };
 
-// CUDA events around the grid-wide power-series launches (opt-in timing)
+// CUDA events around the grid-wide power-series launches (opt-in timing):
+// one pair per large SCC of the partition, created before any capture
 struct KernelTiming {
   std::vector<cudaEvent_t> start, stop;
   std::vector<LargeComp> comps;
-  ~KernelTiming() {
-    for (cudaEvent_t e : start) cudaEventDestroy(e);
-    for (cudaEvent_t e : stop) cudaEventDestroy(e);
-  }
+  pr_status ensure(const pr_partition_s* P);
+  ~KernelTiming();
 };
 
-// Level-by-level solve of a partition.  u and R are device pointers in the
-// original vertex order; replay (device, [K]) may be null; timing may be null.
+// three non-blocking side streams and the fork / join events of a solve
+struct SideStreams {
+  cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
+  pr_status create();
+  ~SideStreams();
+};
+
+// work buffers of a solve, by permuted position
+struct SolveBufs {
+  double* R = nullptr;
+  double* zr = nullptr;
+  double* W = nullptr;
+  HeavyScratch hs;
+  double* zA = nullptr;
+  double* zB = nullptr;
+  double* part = nullptr;
+  float* invf = nullptr;
+};
+
+// A partition's cached solve: its own buffers and the level loop captured
+// as a CUDA graph for one set of (c, tol, norm, max_iter, precision,
+// timing); rebuilt when they change.  Calls that use it are ordered on the
+// device through `done`.
+struct SolvePlan {
+  Arena* keep = nullptr;
+  SolveBufs b;
+  SideStreams side;
+  KernelTiming kt;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t nodes = 0;  // kernels per replay
+  double c = 0.0, tol = 0.0;
+  int norm = 0, max_iter = 0;
+  bool mixed = false, timing = false, have_mixed_bufs = false;
+  Ctl* ctl = nullptr;
+  int32_t* iters = nullptr;
+  int32_t* iters64 = nullptr;
+  double* u = nullptr;
+  double* Rout = nullptr;
+  ~SolvePlan();
+};
+
+// Level-by-level solve of a partition with buffers of its own (used for
+// replayed iteration counts).  u and R are device pointers in the original
+// vertex order; replay (device, [K]) may be null; timing may be null.
 // mixed: SCC series in FP32 with FP64 residual refinement (iters64 then
 // receives the FP64 sweeps per component; it may be null otherwise).
 pr_status run_solve(const pr_partition_s* P, double c, const double* u, double tol, int norm, int max_iter,
                     const int32_t* replay, bool mixed, double* R, int32_t* iters_dev, int32_t* iters64_dev,
                     Arena& tmp, Ctl* ctl, int64_t* launches, KernelTiming* timing);
+
+// The same through the partition's cached graph: copies u in, replays the
+// graph, scatters R out (host or device pointers); *plan receives the plan,
+// whose ctl / iters / iters64 / kt hold the call's results once the stream
+// has reached them.
+pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_host, double tol, int norm,
+                     int max_iter, bool mixed, bool timing, double* R, bool R_on_host, cudaStream_t s,
+                     SolvePlan** plan, int64_t* launches);
 
 // edges read by the solve; with iters64 (may be null), also the edges read
 // by FP64 residual sweeps

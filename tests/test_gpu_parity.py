@@ -331,3 +331,29 @@ def test_mid_size_sccs_use_clusters(prgb):
     sizes = np.bincount(q.comp[q.type == 1])
     assert np.count_nonzero((sizes > 256) & (sizes <= 16384)) >= 10
     assert_solve_parity(prgb, g, G, P, q)
+
+
+def test_graph_replay_matches_direct_launches(prgb):
+    """pr_solve replays a CUDA graph of the level loop cached in the
+    partition; the same kernels launched directly (replaying the graph's
+    iteration counts) give bit-identical R.  A cached graph is reused, and
+    other parameters rebuild it."""
+    import torch
+    g = gg.web_like(seed=16, n=40_000, n_small=800, layers=10, giant_layer=3)
+    G = prgb.graph(g.rowptr, g.col)
+    P = prgb.partition(G)
+    u = torch.from_numpy(g.u).cuda()
+    R1, st1 = prgb.solve(P, C, u, 1e-10, with_stats=True)
+    R2 = prgb.solve(P, C, u, 1e-10, replay_iters=st1["comp_iters"])
+    assert torch.equal(R1, R2)
+    l0 = prgb.launch_count()
+    R3, st3 = prgb.solve(P, C, u, 1e-10, with_stats=True)
+    assert torch.equal(R1, R3)
+    assert np.array_equal(st1["comp_iters"], st3["comp_iters"])
+    assert prgb.launch_count() - l0 == st3["launches"] + 1  # + the edge-count kernel of the stats
+    R4, st4 = prgb.solve(P, C, u, 1e-7, with_stats=True)
+    assert st4["iters_max"] < st1["iters_max"]
+    assert prgb.residual_l1(G, C, u, R4) <= C * 1e-7 * (1 + 1e-6)
+    Rm = prgb.solve(P, C, u, 1e-10, precision=prgb.PREC_MIXED)
+    assert prgb.residual_l1(G, C, u, Rm) <= 1e-10 * (1 + 1e-6)
+    assert torch.equal(prgb.solve(P, C, u, 1e-10), R1)
