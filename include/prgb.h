@@ -74,6 +74,9 @@ typedef struct pr_graph_s pr_graph;
  * pr_partition_destroy; it refers to its pr_graph, which must outlive it. */
 typedef struct pr_partition_s pr_partition;
 
+/* Opaque learned warm-start model (see pr_mpnn_create). */
+typedef struct pr_mpnn_s pr_mpnn;
+
 /* Component types (Sec. 3 Def. 3.1-3.2; 1-vertex components are CACs). */
 #define PR_TYPE_CAC 0
 #define PR_TYPE_SCC 1
@@ -111,6 +114,14 @@ typedef struct pr_solve_opts {
                                     component instead of the stopping rule
                                     (index = canonical component id); for
                                     pr_global_power, element 0 is used */
+    const struct pr_mpnn_s *warm_start; /* optional (pr_solve only, not with
+                                    replay_iters): the network of
+                                    pr_mpnn_create guesses each SCC's R from
+                                    its vertices' degrees, size and weights W;
+                                    the series then continues from the
+                                    residual of the guess, so the result
+                                    meets the same stopping rule and residual
+                                    bound as a cold start */
 } pr_solve_opts;
 
 typedef struct pr_solve_stats {
@@ -268,6 +279,69 @@ int64_t pr_launch_count(void);
 #define PR_STATIC_MAX_N 1048576
 pr_status pr_residual_l1_static(const pr_csr *g, double c, const double *u, const double *R,
                                 double *out_host, void *stream);
+
+/*
+ * Learned warm start.  The paper starts each SCC's power series from
+ * P_0 = W (Sec. 4.3.2); these calls build, train and evaluate a network that
+ * guesses the SCC's solution instead, so that pr_solve (opts.warm_start)
+ * continues the series from the guess's residual.  The paper has no learned
+ * component; the guess only changes where the series starts, never what it
+ * converges to or when it stops.
+ *
+ * Model, per vertex i of an SCC C (d_i internal in-edges, W_i the
+ * inflow-adjusted weight of Eq. PR:levels, n vertices in the graph):
+ *   x_i  = [log1p(d_i), log1p(outdeg_i), log|C|, log(n W_i + 1e-3), 1, 0, 0, 0]
+ *   h_i  = relu(A1 x_i + B1 mean_{j->i, j in C} x_j + b1)        (64)
+ *   g_i  = relu(A2 h_i + B2 mean_{j->i, j in C} h_j + b2)        (64)
+ *   yhat = v . g_i + b3;  guess R0_i = W_i exp(clamp(yhat, 0, 10)).
+ * Parameters: one float32 vector of pr_mpnn_param_count() = 9409 entries,
+ * A1[64][8], B1[64][8], b1[64], A2[64][64], B2[64][64], b2[64], v[64], b3
+ * (row-major, output index first), rounded to bfloat16 (nearest, ties to
+ * even) for every forward pass; sums in float32.  Training target
+ * y_i = log(R_i / W_i) of a solved R (vertices with W_i = 0 excluded), loss
+ * = mean (yhat_i - y_i)^2 over the SCC vertices, optimiser Adam (0.9, 0.999,
+ * 1e-8) on the float32 weights.
+ */
+int64_t pr_mpnn_param_count(void);
+
+/* New model with seeded weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in))
+ * from splitmix64(seed), zero biases, b3 = 1.  Owned by the caller until
+ * pr_mpnn_destroy.  Errors: PR_EINVAL (out NULL), PR_ENOMEM, PR_ECUDA.
+ * Synchronises the stream. */
+pr_status pr_mpnn_create(uint64_t seed, void *stream, pr_mpnn **out);
+void pr_mpnn_destroy(pr_mpnn *m);
+
+/* Copy the float32 weights out / in (host arrays of exactly
+ * pr_mpnn_param_count() floats, else PR_EINVAL).  Setting them clears the
+ * optimiser state.  Synchronise the model's stream. */
+pr_status pr_mpnn_get_params(const pr_mpnn *m, float *host, int64_t count);
+pr_status pr_mpnn_set_params(pr_mpnn *m, const float *host, int64_t count);
+
+/*
+ * pr_mpnn_predict -- forward pass on a solved graph.
+ *   part : partition of the graph; c : damping factor;
+ *   u, R : [n] float64 DEVICE arrays in the original vertex order: the
+ *          weights and a solution (W is formed from them by Eq. PR:levels).
+ *   yhat : [n] float32 DEVICE output, one entry per vertex in the original
+ *          vertex order (0 outside SCCs); may be NULL when only the loss is
+ *          wanted.
+ *   loss : optional host output, the training loss against R.
+ * Errors: PR_EINVAL, PR_ECUDA.  Synchronises the stream.
+ */
+pr_status pr_mpnn_predict(const pr_mpnn *m, const pr_partition *part, double c, const double *u,
+                          const double *R, float *yhat, double *loss, void *stream);
+
+/* Loss and gradient (float32, host array of pr_mpnn_param_count() floats, or
+ * NULL) of the model on one solved graph, without updating it.  Arguments as
+ * for pr_mpnn_predict.  Synchronises the stream. */
+pr_status pr_mpnn_loss_grad(pr_mpnn *m, const pr_partition *part, double c, const double *u,
+                            const double *R, float *grad_host, double *loss, void *stream);
+
+/* One Adam step (learning rate lr > 0) on the full batch of one solved
+ * graph's SCC vertices; loss (optional) receives the loss before the step.
+ * Synchronises the stream. */
+pr_status pr_mpnn_train_step(pr_mpnn *m, const pr_partition *part, double c, const double *u,
+                             const double *R, float lr, double *loss, void *stream);
 
 /* Human-readable name of a status code (static storage). */
 const char *pr_status_str(pr_status s);

@@ -23,7 +23,7 @@ import numpy as np
 __all__ = [
     "PrError", "Graph", "Partition", "graph", "partition", "solve", "global_power",
     "residual_l1", "load_library", "library_path", "launch_count", "TYPE_CAC", "TYPE_SCC",
-    "NORM_L1", "NORM_LINF", "PREC_FP64", "PREC_MIXED",
+    "NORM_L1", "NORM_LINF", "PREC_FP64", "PREC_MIXED", "Mpnn",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -54,7 +54,7 @@ class _Csr(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("norm", C.c_int32), ("max_iter", C.c_int32), ("precision", C.c_int32),
-                ("io_on_host", C.c_int32), ("replay_iters", C.c_void_p)]
+                ("io_on_host", C.c_int32), ("replay_iters", C.c_void_p), ("warm_start", C.c_void_p)]
 
 
 class _Stats(C.Structure):
@@ -88,6 +88,17 @@ _SIGS = {
     "pr_launch_count": (C.c_int64, []),
     "pr_residual_l1_static": (C.c_int, [C.POINTER(_Csr), C.c_double, C.c_void_p, C.c_void_p,
                                         C.POINTER(C.c_double), C.c_void_p]),
+    "pr_mpnn_param_count": (C.c_int64, []),
+    "pr_mpnn_create": (C.c_int, [C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "pr_mpnn_destroy": (None, [C.c_void_p]),
+    "pr_mpnn_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "pr_mpnn_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "pr_mpnn_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "pr_mpnn_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "pr_mpnn_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                                     C.c_float, C.POINTER(C.c_double), C.c_void_p]),
 }
 
 STATIC_MAX_N = 1 << 20
@@ -237,8 +248,9 @@ def partition(g: Graph):
     return Partition(g)
 
 
-def _opts(norm, max_iter, io_on_host, replay, precision=PREC_FP64):
-    o = _Opts(int(norm), int(max_iter), int(precision), int(io_on_host), None)
+def _opts(norm, max_iter, io_on_host, replay, precision=PREC_FP64, warm=None):
+    o = _Opts(int(norm), int(max_iter), int(precision), int(io_on_host), None,
+              warm.handle if warm is not None else None)
     keep = None
     if replay is not None:
         keep = np.ascontiguousarray(replay, dtype=np.int32)
@@ -259,15 +271,17 @@ def _stats_dict(st):
 
 
 def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iters=None,
-          with_stats=False, allow_noconv=False, timing=False, precision=PREC_FP64):
+          with_stats=False, allow_noconv=False, timing=False, precision=PREC_FP64, warm_start=None):
     """Sec. 4.3 solve on device tensors; returns R (float64, original order).
 
     ``u`` may be a CUDA tensor or a numpy array (host I/O through the C ABI's
     io_on_host path; R is then returned as numpy).  ``precision=PREC_MIXED``
-    runs the SCC series in FP32 with FP64 residual refinement."""
+    runs the SCC series in FP32 with FP64 residual refinement;
+    ``warm_start`` (an ``Mpnn``) starts each SCC's series from the network's
+    guess."""
     lib = load_library()
     on_host = isinstance(u, np.ndarray)
-    o, keep = _opts(norm, max_iter, on_host, replay_iters, precision)
+    o, keep = _opts(norm, max_iter, on_host, replay_iters, precision, warm_start)
     comp_iters = np.zeros(max(part.n_comp, 1), np.int32)
     st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data, int(timing), 0.0, 0, 0, 0, 0)
     if on_host:
@@ -348,3 +362,72 @@ def residual_l1_static(rowptr, col, c, u, R):
                                      Rd.data_ptr() if n else None, C.byref(out), _stream()),
            "pr_residual_l1_static")
     return out.value
+
+
+class Mpnn:
+    """Learned warm start (``pr_mpnn``): a two-layer message-passing network
+    over each SCC's internal in-edges that guesses R_i / W_i; trained with the
+    library's own forward and backward kernels."""
+
+    def __init__(self, seed=0):
+        lib = load_library()
+        self._h = C.c_void_p()
+        _check(lib.pr_mpnn_create(C.c_uint64(int(seed)), _stream(), C.byref(self._h)), "pr_mpnn_create")
+        self.n_params = int(lib.pr_mpnn_param_count())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def get_params(self):
+        out = np.empty(self.n_params, np.float32)
+        _check(load_library().pr_mpnn_get_params(self._h, out.ctypes.data, self.n_params), "pr_mpnn_get_params")
+        return out
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(load_library().pr_mpnn_set_params(self._h, theta.ctypes.data, int(theta.size)),
+               "pr_mpnn_set_params")
+
+    def predict(self, part: Partition, c, u, R):
+        """(yhat float32 CUDA tensor in the original vertex order, loss)."""
+        torch = _torch()
+        ud, Rd = _dev_f64(u), _dev_f64(R)
+        y = torch.zeros(part.n, dtype=torch.float32, device="cuda")
+        loss = C.c_double(0.0)
+        _check(load_library().pr_mpnn_predict(self._h, part.handle, float(c), ud.data_ptr() if part.n else None,
+                                              Rd.data_ptr() if part.n else None,
+                                              y.data_ptr() if part.n else None, C.byref(loss), _stream()),
+               "pr_mpnn_predict")
+        return y, loss.value
+
+    def loss_grad(self, part: Partition, c, u, R):
+        ud, Rd = _dev_f64(u), _dev_f64(R)
+        g = np.empty(self.n_params, np.float32)
+        loss = C.c_double(0.0)
+        _check(load_library().pr_mpnn_loss_grad(self._h, part.handle, float(c), ud.data_ptr() if part.n else None,
+                                                Rd.data_ptr() if part.n else None, g.ctypes.data,
+                                                C.byref(loss), _stream()),
+               "pr_mpnn_loss_grad")
+        return loss.value, g
+
+    def train_step(self, part: Partition, c, u, R, lr=1e-3):
+        ud, Rd = _dev_f64(u), _dev_f64(R)
+        loss = C.c_double(0.0)
+        _check(load_library().pr_mpnn_train_step(self._h, part.handle, float(c),
+                                                 ud.data_ptr() if part.n else None,
+                                                 Rd.data_ptr() if part.n else None, C.c_float(lr),
+                                                 C.byref(loss), _stream()),
+               "pr_mpnn_train_step")
+        return loss.value
+
+    def close(self):
+        if self._h:
+            load_library().pr_mpnn_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

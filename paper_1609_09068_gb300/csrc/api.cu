@@ -193,13 +193,14 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
   if (!part) return PR_EINVAL;
   const int32_t n = part->g.n;
   if (n > 0) PRGB_TRY(check_solve_args(c, u, tol, R));
-  pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr};
+  pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr, nullptr};
   if (opts) o = *opts;
   if (o.max_iter <= 0) o.max_iter = 10000;
   if (o.norm != PR_NORM_L1 && o.norm != PR_NORM_LINF) return PR_EINVAL;
   if (o.precision != PR_PREC_FP64 && o.precision != PR_PREC_MIXED) return PR_EINVAL;
   const bool mixed = o.precision == PR_PREC_MIXED;
   if (mixed && (o.norm != PR_NORM_L1 || o.replay_iters)) return PR_EINVAL;
+  if (o.warm_start && o.replay_iters) return PR_EINVAL;
   if (o.replay_iters) {
     for (int32_t k = 0; k < part->n_comp; k++)
       if (o.replay_iters[k] < 0 || o.replay_iters[k] > 1000000) return PR_EINVAL;
@@ -220,8 +221,8 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
     // the level loop replayed from the partition's cached CUDA graph
     lock.lock();
     SolvePlan* pl = nullptr;
-    PRGB_TRY(plan_solve(P, c, u, o.io_on_host != 0, tol, o.norm, o.max_iter, mixed, timing, R, o.io_on_host != 0,
-                        s, &pl, &launches));
+    PRGB_TRY(plan_solve(P, c, u, o.io_on_host != 0, tol, o.norm, o.max_iter, mixed, timing, o.warm_start, R,
+                        o.io_on_host != 0, s, &pl, &launches));
     ctl = pl->ctl;
     iters = pl->iters;
     iters64 = mixed ? pl->iters64 : nullptr;
@@ -305,11 +306,11 @@ pr_status pr_global_power(const pr_graph* g, double c, const double* u, double t
   if (!g) return PR_EINVAL;
   const int32_t n = g->g.n;
   if (n > 0) PRGB_TRY(check_solve_args(c, u, tol, R));
-  pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr};
+  pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr, nullptr};
   if (opts) o = *opts;
   if (o.max_iter <= 0) o.max_iter = 10000;
   if (o.norm != PR_NORM_L1 && o.norm != PR_NORM_LINF) return PR_EINVAL;
-  if (o.precision != PR_PREC_FP64) return PR_EINVAL;
+  if (o.precision != PR_PREC_FP64 || o.warm_start) return PR_EINVAL;
   int fixed = -1;
   if (o.replay_iters) {
     fixed = o.replay_iters[0];

@@ -416,6 +416,7 @@ struct pr_partition_s {
   int32_t* heavy_chrow = nullptr;
   int32_t* lorder = nullptr;       // [n] positions by (component, internal in-degree class)
   double* p_inv = nullptr;         // [n] 1/outdeg by position
+  int32_t* p_comp = nullptr;       // [n] component of each position
   int32_t* xheavy_rows = nullptr;  // positions with > kHeavy external in-edges
   int32_t* xheavy_choff = nullptr;
   int32_t* xheavy_chrow = nullptr;

@@ -397,6 +397,9 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   P->n_scc_vertices = hs[1];
   P->large.resize(nlarge);
   P->max_large = 0;
+  PRGB_TRY(keep.alloc(&P->p_comp, n));
+  pos_comp_k<<<grid1(n), kBlock, 0, s>>>(n, P->perm, P->comp_id, P->p_comp);
+  PRGB_LAUNCH();
   if (nlarge > 0) {
     LargeComp* dl;
     PRGB_TRY(tmp.alloc(&dl, nlarge));
@@ -410,10 +413,7 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
     // light rows of each component ordered by in-degree class
     PRGB_TRY(build_heavy(P->int_ptr, n, keep, tmp, &P->heavy_rows, &P->heavy_choff, &P->heavy_chrow, &P->nheavy,
                           &P->nchunks));
-    int32_t* pc;
-    PRGB_TRY(tmp.alloc(&pc, n));
-    pos_comp_k<<<grid1(n), kBlock, 0, s>>>(n, P->perm, P->comp_id, pc);
-    PRGB_LAUNCH();
+    int32_t* pc = P->p_comp;
     PRGB_TRY(build_lorder(P->int_ptr, n, pc, K - 1, keep, tmp, &P->lorder));
     std::vector<int32_t> hrows(P->nheavy), hcho(P->nheavy + 1);
     if (P->nheavy > 0) {

@@ -1,0 +1,52 @@
+// mpnn.cuh -- the learned warm start of the SCC power series: a two-layer
+// message-passing network over each SCC's internal in-edges that guesses
+// R_i / W_i (mpnn.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace prgb {
+
+constexpr int kMpF0 = 8;  // input features per vertex
+constexpr int kMpH = 64;  // hidden width
+// parameter vector (float32 masters, bf16 copies for the forward pass):
+// A1[64][8], B1[64][8], b1[64], A2[64][64], B2[64][64], b2[64], v[64], b3
+constexpr int kMpA1 = 0;
+constexpr int kMpB1 = kMpA1 + kMpH * kMpF0;
+constexpr int kMpb1 = kMpB1 + kMpH * kMpF0;
+constexpr int kMpA2 = kMpb1 + kMpH;
+constexpr int kMpB2 = kMpA2 + kMpH * kMpH;
+constexpr int kMpb2 = kMpB2 + kMpH * kMpH;
+constexpr int kMpv = kMpb2 + kMpH;
+constexpr int kMpb3 = kMpv + kMpH;
+constexpr int kMpParams = kMpb3 + 1;
+
+// scratch of one inference pass over rows [r0, r1) of the permuted layout
+struct MpnnInfer {
+  float* X = nullptr;   // [rows][8]
+  float* H1 = nullptr;  // [rows][64]
+};
+
+// one-time kernel attributes of the network's kernels (call before any
+// stream capture that launches them)
+pr_status mpnn_prepare();
+
+// Guess R0 = W * exp(clamp(yhat, 0, 10)) for the SCC rows of [r0, r1)
+// (every internal in-edge of such a row starts inside the range); W and
+// R0 by position.  Launches only (capturable).
+pr_status mpnn_infer(const pr_mpnn_s* M, const pr_partition_s* P, int32_t r0, int32_t r1, const double* W,
+                     double* R0, const MpnnInfer& buf, cudaStream_t s, int64_t* nl);
+
+}  // namespace prgb
+
+// the opaque model of the C ABI
+struct pr_mpnn_s {
+  cudaStream_t stream = nullptr;
+  prgb::Arena* keep = nullptr;
+  float* master = nullptr;  // [kMpParams] float32 weights
+  float* m1 = nullptr;      // Adam moments
+  float* m2 = nullptr;
+  float* grad = nullptr;    // [kMpParams] accumulated gradient
+  uint16_t* w16 = nullptr;  // [kMpParams] bf16 copy used by the forward pass
+  int64_t step = 0;
+};

@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "mpnn.cuh"
 #include "solve.cuh"
 #include "spmv.cuh"
 
@@ -95,7 +96,8 @@ constexpr int kWarpBlock = 64;  // two components per block, spread over many SM
 // component; W is this lane's weight.  Returns the result R of this lane and
 // counts the sweeps in *k (all) and *k64 (FP64 residual sweeps).
 __device__ double warp_series_mixed(const SolveArgs& a, bool act, double W, double inv, const uint8_t* ix, int ib,
-                                    int ie, double* z, float* zf, double tau, int* k, int* k64) {
+                                    int ie, double* z, float* zf, double tau, int* k, int* k64, bool warm,
+                                    double R0) {
   const int lane = threadIdx.x & 31;
   const float cf = (float)a.c;
   const float invf = (float)inv;
@@ -104,10 +106,15 @@ __device__ double warp_series_mixed(const SolveArgs& a, bool act, double W, doub
   const double wsum = group_sum<32>(act ? W : 0.0);
   float thr = (float)fmax(tau, (double)kMixKappa * wsum);
   double R = 0.0;
+  if (warm) {  // start from the guess: straight to its FP64 residual
+    R = act ? R0 : 0.0;
+    F = 0.0f;
+  }
+  bool skip = warm;
   int rounds = 0;
   __syncwarp();
   for (;;) {
-    for (;;) {
+    for (; !skip;) {
       float acc0 = 0.0f, acc1 = 0.0f;
       int e = ib;
       for (; e + 1 < ie; e += 2) {
@@ -129,6 +136,7 @@ __device__ double warp_series_mixed(const SolveArgs& a, bool act, double W, doub
         return R + (double)F;
       }
     }
+    skip = false;
     R += (double)F;
     if (act) z[lane] = R * inv;
     __syncwarp();
@@ -189,11 +197,27 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
     }
   } else if (kMixed) {
     const double tau = a.tol * (double)sz / (double)a.n;
-    R = warp_series_mixed(a, act, W, inv, ix, ib, ie, z, zfsh[wib], tau, &k, &k64);
+    const bool warm = a.R0 != nullptr;
+    R = warp_series_mixed(a, act, W, inv, ix, ib, ie, z, zfsh[wib], tau, &k, &k64, warm, warm && act ? a.R0[p] : 0.0);
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const int fixed = a.replay ? a.replay[c] : -1;
-    if (act) z[lane] = W * inv;
+    if (a.R0) {
+      // warm start: R = R0 + r, the series continues from the residual
+      // r = W + c A^T(R0/outdeg) - R0 (signed)
+      const double r0 = act ? a.R0[p] : 0.0;
+      if (act) z[lane] = r0 * inv;
+      __syncwarp();
+      double acc = 0.0;
+      for (int e = ib; e < ie; e++) acc += z[ix[e]];
+      const double r = act ? W + a.c * acc - r0 : 0.0;
+      __syncwarp();
+      R = r0 + r;
+      if (act) z[lane] = r * inv;
+      k = 1;
+    } else if (act) {
+      z[lane] = W * inv;
+    }
     __syncwarp();
     for (;;) {
       // two partial sums halve the chain of dependent FP64 adds
@@ -216,7 +240,7 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
         if (k >= fixed) break;
         continue;
       }
-      const float pf = (float)pn;
+      const float pf = fabsf((float)pn);  // terms are signed after a warm start
       const float s = a.norm == PR_NORM_L1 ? group_sumf<32>(pf) : group_maxf<32>(pf);
       if (!keep_going32(s, tau, a.norm)) break;
       if (k >= a.max_iter) {
@@ -329,9 +353,14 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
     if (act) zf[i] = (float)(W * inv);
     float thr = (float)fmax(tau, (double)kMixKappa * block_sum(W, red64));  // publishes zf
     double R = 0.0;
+    bool skip = a.R0 != nullptr;  // warm start: straight to the guess's residual
+    if (skip) {
+      R = act ? a.R0[off + i] : 0.0;
+      F = 0.0f;
+    }
     int rounds = 0;
     for (;;) {
-      for (;;) {
+      for (; !skip;) {
         const float pn = act ? cf * row_sumf(i) : 0.0f;
         __syncthreads();  // every row has read zf before it is overwritten
         if (act) {
@@ -347,6 +376,7 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
           break;
         }
       }
+      skip = false;
       R += (double)F;
       if (rounds < 0) break;
       if (act) z[i] = R * inv;
@@ -369,6 +399,22 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const int fixed = a.replay ? a.replay[c] : -1;
+    if (a.R0) {
+      // warm start: R = R0 + r, the series continues from the residual
+      const int i = threadIdx.x;
+      const bool act = i < sz;
+      const double r0 = act ? a.R0[off + i] : 0.0;
+      if (act) z[i] = r0 * iv[i];
+      __syncthreads();
+      const double r = act ? Rs[i] + a.c * row_sum(i) - r0 : 0.0;
+      __syncthreads();
+      if (act) {
+        Rs[i] = r0 + r;
+        z[i] = r * iv[i];
+      }
+      __syncthreads();
+      k = 1;
+    }
     for (;;) {
       double pn[kCtaRows];
       double local = 0.0;
@@ -384,7 +430,7 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
         if (i < sz) {
           Rs[i] += pn[r];
           z[i] = pn[r] * iv[i];
-          local = a.norm == PR_NORM_L1 ? local + pn[r] : fmax(local, pn[r]);
+          local = a.norm == PR_NORM_L1 ? local + fabs(pn[r]) : fmax(local, fabs(pn[r]));
         }
       }
       // the reduction ends with __syncthreads, which also publishes z
@@ -569,12 +615,13 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     float* F = sm.F;
     float* ivf = sm.ivf;
     double wl = 0.0;
+    const bool warm = a.R0 != nullptr;  // start from the guess's residual
     for (int i = threadIdx.x; i < nr; i += blockDim.x) {
       const double W = Rs[i];
-      F[i] = (float)W;
+      F[i] = warm ? 0.0f : (float)W;
       sm.fA[i] = (float)(W * iv[i]);
       ivf[i] = (float)iv[i];
-      Rs[i] = 0.0;
+      Rs[i] = warm ? a.R0[off + r0 + i] : 0.0;
       wl += W;
     }
     const double wb = block_sum(wl, red64);
@@ -584,9 +631,10 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     for (int r = 0; r < kClu; r++) wsum += remD[r][0];
     float thr = (float)fmax(tau, (double)kMixKappa * wsum);
     int zc = 0, dq = 1, rounds = 0;
+    bool skip = warm;
     for (;;) {
       bool stop = false;
-      for (;;) {
+      for (; !skip;) {
         float* const* rem = zc ? remFB : remFA;
         float* nxt = zc ? sm.fA : sm.fB;
         float local = 0.0f;
@@ -610,6 +658,7 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
           break;
         }
       }
+      skip = false;
       for (int i = threadIdx.x; i < nr; i += blockDim.x) {
         const double R = Rs[i] + (double)F[i];
         Rs[i] = R;
@@ -645,6 +694,19 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const int fixed = a.replay ? a.replay[c] : -1;
     const bool is_max = a.norm != PR_NORM_L1;
+    if (a.R0) {
+      // warm start: R = R0 + r; the series continues from r (in zB, k = 1)
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) zA[i] = a.R0[off + r0 + i] * iv[i];
+      cl.sync();
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        const double g0 = a.R0[off + r0 + i];
+        const double r = Rs[i] + a.c * row_sum(remA, i) - g0;
+        Rs[i] = g0 + r;
+        zB[i] = r * iv[i];
+      }
+      cl.sync();
+      k = 1;
+    }
     for (;;) {
       double* const* rem = (k & 1) ? remB : remA;
       double* nxt = (k & 1) ? zA : zB;
@@ -653,7 +715,7 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
         const double pn = a.c * row_sum(rem, i);
         Rs[i] += pn;
         nxt[i] = pn * iv[i];
-        local = is_max ? fmaxf(local, (float)pn) : local + (float)pn;
+        local = is_max ? fmaxf(local, fabsf((float)pn)) : local + fabsf((float)pn);
       }
       const float bs = block_sumf(local, red, is_max);
       if (threadIdx.x == 0) part[k & 1] = bs;
@@ -727,11 +789,30 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
   const int nlight = sz - hv.nheavy;
   const int* lorder = a.lorder + off;
   load_rows(a, off, sz, zA);
+  const bool l1 = a.norm == PR_NORM_L1;
+  int k = 0;
+  if (a.R0) {
+    // warm start: R = R0 + r, the series continues from the residual
+    // r = W + c A^T(R0/outdeg) - R0 (in zB, k = 1)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
+      const int p = off + (int)i;
+      a.R[p] = a.R0[p];
+      zA[i] = a.R0[p] * a.p_inv[p];
+    }
+    if (!grid_sync(a.ctl, 312)) return;
+    auto fin = [&](int row, double acc, bool) -> double {
+      const double r = a.W[row] + a.c * acc - a.R[row];
+      a.R[row] += r;
+      zB[row - off] = r * a.p_inv[row];
+      return fabs(r);
+    };
+    auto val = [&](int e) -> double { return zA[local_or_err(a, a.int_idx[e] - off, sz)]; };
+    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, 0, l1, fin, val);
+    k = 1;
+  }
   if (!grid_sync(a.ctl, 310)) return;
   const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
   const int fixed = a.replay ? a.replay[L.c] : -1;
-  const bool l1 = a.norm == PR_NORM_L1;
-  int k = 0;
   for (;;) {
     const double* cur = (k & 1) ? zB : zA;
     double* nxt = (k & 1) ? zA : zB;
@@ -740,8 +821,8 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
       const double pn = a.c * acc;
       a.R[row] += pn;
       nxt[row - off] = pn * a.p_inv[row];
-      if (!heavy) local = fold2(local, pn, l1);
-      return pn;
+      if (!heavy) local = fold2(local, fabs(pn), l1);
+      return fabs(pn);
     };
     auto val = [&](int e) -> double { return cur[local_or_err(a, a.int_idx[e] - off, sz)]; };
     balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, k & 1, l1, fin, val);
@@ -794,21 +875,23 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_mx_k(SolveArgs a, Larg
   float* const zf0 = fz;
   float* const zf1 = fz + sz;
   double wl = 0.0;
+  const bool warm = a.R0 != nullptr;  // start from the guess's residual
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
     const int p = off + (int)i;
     const double W = a.W[p];
-    F[i] = (float)W;
+    F[i] = warm ? 0.0f : (float)W;
     zf0[i] = (float)(W * a.p_inv[p]);
-    a.R[p] = 0.0;
+    a.R[p] = warm ? a.R0[p] : 0.0;
     wl += W;
   }
   const double wsum = grid_fold(a, part, 0, wl, red, 330);
   if (wsum < 0.0) return;
   float thr = (float)fmax(tau, (double)kMixKappa * wsum);
   int k = 0, k64 = 0, zc = 0, slot = 1, rounds = 0;
+  bool skip = warm;
   for (;;) {
     bool stop = false;
-    for (;;) {
+    for (; !skip;) {
       const float* cur = zc ? zf1 : zf0;
       float* nxt = zc ? zf0 : zf1;
       double local = 0.0;
@@ -834,6 +917,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_mx_k(SolveArgs a, Larg
         break;
       }
     }
+    skip = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz;
          i += (int64_t)gridDim.x * blockDim.x) {
       const int p = off + (int)i;
@@ -1042,6 +1126,7 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
   a.replay = replay;
   a.xlorder = P->xlorder;
   a.p_invf = b.invf;
+  a.R0 = nullptr;
   a.iters64 = iters64;
   a.W = b.W;
   a.R = b.R;
@@ -1057,7 +1142,8 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
 // next level.  Only launches, memsets and event records: it can be
 // captured into a CUDA graph.
 pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& b, bool mixed, SideStreams& side,
-                         cudaStream_t s, KernelTiming* timing, int64_t* nl) {
+                         cudaStream_t s, KernelTiming* timing, int64_t* nl, const pr_mpnn_s* warm = nullptr,
+                         const MpnnInfer* inf = nullptr) {
   Ctl* ctl = a.ctl;
   double* zA = b.zA;
   double* zB = b.zB;
@@ -1080,6 +1166,10 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       PRGB_LAUNCH();
       ++*nl;
     }
+    // learned warm start: the guess R0 of this level's SCC rows, from the
+    // weights W the gather has just formed
+    if (warm && a.R0 && r.vsingle > r.vbeg)
+      PRGB_TRY(mpnn_infer(warm, P, r.vbeg, r.vsingle, a.W, const_cast<double*>(a.R0), *inf, s, nl));
     while (li_large < P->large.size() && P->large[li_large].level_idx == (int)li) {
       LargeComp L = P->large[li_large++];
       PRGB_TRY(reset_ctl(ctl, s));
@@ -1197,9 +1287,9 @@ SolvePlan::~SolvePlan() {
 
 // (Re)build the graph for these parameters if the cached one differs.
 static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double tol, int norm, int max_iter,
-                              bool mixed, bool timing) {
+                              bool mixed, bool timing, const pr_mpnn_s* warm) {
   if (pl->exec && pl->c == c && pl->tol == tol && pl->norm == norm && pl->max_iter == max_iter &&
-      pl->mixed == mixed && pl->timing == timing)
+      pl->mixed == mixed && pl->timing == timing && pl->warm == warm)
     return PR_OK;
   const int32_t n = P->g.n;
   const int32_t K = P->n_comp;
@@ -1236,9 +1326,19 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
     pl->have_mixed_bufs = true;
     PRGB_CUDA(cudaStreamSynchronize(P->stream));
   }
+  if (warm) PRGB_TRY(mpnn_prepare());
+  if (warm && !pl->R0) {
+    // the guess by position and one level's network activations
+    int32_t rows = 0;
+    for (const LevelRange& r : P->levels) rows = std::max(rows, r.vsingle - r.vbeg);
+    PRGB_TRY(pl->keep->alloc(&pl->R0, (size_t)n + 1));
+    PRGB_TRY(pl->keep->alloc(&pl->inf.X, (size_t)rows * kMpF0 + 4));
+    PRGB_TRY(pl->keep->alloc(&pl->inf.H1, (size_t)rows * kMpH + 4));
+  }
   if (timing) PRGB_TRY(pl->kt.ensure(P));
-  const SolveArgs a = make_solve_args(P, c, pl->u, tol, norm, max_iter, nullptr, pl->b, pl->iters,
-                                      mixed ? pl->iters64 : nullptr, pl->ctl);
+  SolveArgs a = make_solve_args(P, c, pl->u, tol, norm, max_iter, nullptr, pl->b, pl->iters,
+                                mixed ? pl->iters64 : nullptr, pl->ctl);
+  if (warm) a.R0 = pl->R0;
   const long long before = launch_count();
   int64_t nl = 0;
   PRGB_CUDA(cudaStreamBeginCapture(pl->cs, cudaStreamCaptureModeThreadLocal));
@@ -1247,7 +1347,8 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
       cudaMemsetAsync(pl->iters, 0, ((size_t)K + 1) * 4, pl->cs) != cudaSuccess ||
       cudaMemsetAsync(pl->iters64, 0, ((size_t)K + 1) * 4, pl->cs) != cudaSuccess)
     st = PR_ECUDA;
-  if (st == PR_OK) st = enqueue_levels(P, a, pl->b, mixed, pl->side, pl->cs, timing ? &pl->kt : nullptr, &nl);
+  if (st == PR_OK)
+    st = enqueue_levels(P, a, pl->b, mixed, pl->side, pl->cs, timing ? &pl->kt : nullptr, &nl, warm, &pl->inf);
   cudaGraph_t g = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(pl->cs, &g);
   add_launches(before - launch_count());  // captured, not launched
@@ -1265,12 +1366,13 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
   pl->max_iter = max_iter;
   pl->mixed = mixed;
   pl->timing = timing;
+  pl->warm = warm;
   return PR_OK;
 }
 
 pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_host, double tol, int norm,
-                     int max_iter, bool mixed, bool timing, double* R, bool R_on_host, cudaStream_t s,
-                     SolvePlan** out, int64_t* launches) {
+                     int max_iter, bool mixed, bool timing, const pr_mpnn_s* warm, double* R, bool R_on_host,
+                     cudaStream_t s, SolvePlan** out, int64_t* launches) {
   if (!P->plan) {
     P->plan = new (std::nothrow) SolvePlan;
     if (!P->plan) return PR_ENOMEM;
@@ -1278,7 +1380,7 @@ pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_hos
   SolvePlan* pl = P->plan;
   *out = pl;
   const int32_t n = P->g.n;
-  PRGB_TRY(plan_prepare(P, pl, c, tol, norm, max_iter, mixed, timing));
+  PRGB_TRY(plan_prepare(P, pl, c, tol, norm, max_iter, mixed, timing, warm));
   // the plan's buffers are reused: order this call after the previous one
   PRGB_CUDA(cudaStreamWaitEvent(s, pl->done, 0));
   if (n > 0)

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "mpnn.cuh"
 #include "spmv.cuh"
 
 namespace prgb {
@@ -28,6 +29,7 @@ struct SolveArgs {
   const int32_t* replay;    // [K] fixed iteration counts, or nullptr
   const int32_t* xlorder;   // [n] positions by (level, external in-degree class)
   const float* p_invf;      // [n] 1/outdeg in FP32 (mixed precision only)
+  const double* R0;         // [n] warm-start guess by position for SCC rows, or nullptr
   int32_t* iters64;         // [K] FP64 residual sweeps per SCC (mixed only)
   double* W;                // [n] inflow-adjusted weights by position
   double* R;                // [n] by position
@@ -88,6 +90,9 @@ struct SolvePlan {
   int32_t* iters64 = nullptr;
   double* u = nullptr;
   double* Rout = nullptr;
+  const pr_mpnn_s* warm = nullptr;  // warm-start model of the cached graph
+  double* R0 = nullptr;             // [n] its guess by position
+  MpnnInfer inf;
   ~SolvePlan();
 };
 
@@ -103,10 +108,11 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
 // The same through the partition's cached graph: copies u in, replays the
 // graph, scatters R out (host or device pointers); *plan receives the plan,
 // whose ctl / iters / iters64 / kt hold the call's results once the stream
-// has reached them.
+// has reached them.  warm (may be null): the network that guesses each
+// SCC's start, evaluated per level inside the graph.
 pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_host, double tol, int norm,
-                     int max_iter, bool mixed, bool timing, double* R, bool R_on_host, cudaStream_t s,
-                     SolvePlan** plan, int64_t* launches);
+                     int max_iter, bool mixed, bool timing, const pr_mpnn_s* warm, double* R, bool R_on_host,
+                     cudaStream_t s, SolvePlan** plan, int64_t* launches);
 
 // edges read by the solve; with iters64 (may be null), also the edges read
 // by FP64 residual sweeps
