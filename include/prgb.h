@@ -122,6 +122,13 @@ typedef struct pr_solve_opts {
                                     residual of the guess, so the result
                                     meets the same stopping rule and residual
                                     bound as a cold start */
+    int32_t lu_threshold;        /* pr_solve only: SCC components of fewer
+                                    than lu_threshold vertices (0 = none, at
+                                    most 129) are solved directly,
+                                    (I - cA_C^T)R_C = W_C by Gaussian
+                                    elimination (Sec. 4.3 item 3: the paper
+                                    suggests fewer than ~100); their
+                                    iteration count is 0 */
 } pr_solve_opts;
 
 typedef struct pr_solve_stats {

@@ -54,7 +54,8 @@ class _Csr(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("norm", C.c_int32), ("max_iter", C.c_int32), ("precision", C.c_int32),
-                ("io_on_host", C.c_int32), ("replay_iters", C.c_void_p), ("warm_start", C.c_void_p)]
+                ("io_on_host", C.c_int32), ("replay_iters", C.c_void_p), ("warm_start", C.c_void_p),
+                ("lu_threshold", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -248,9 +249,9 @@ def partition(g: Graph):
     return Partition(g)
 
 
-def _opts(norm, max_iter, io_on_host, replay, precision=PREC_FP64, warm=None):
+def _opts(norm, max_iter, io_on_host, replay, precision=PREC_FP64, warm=None, lu_threshold=0):
     o = _Opts(int(norm), int(max_iter), int(precision), int(io_on_host), None,
-              warm.handle if warm is not None else None)
+              warm.handle if warm is not None else None, int(lu_threshold))
     keep = None
     if replay is not None:
         keep = np.ascontiguousarray(replay, dtype=np.int32)
@@ -271,17 +272,19 @@ def _stats_dict(st):
 
 
 def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iters=None,
-          with_stats=False, allow_noconv=False, timing=False, precision=PREC_FP64, warm_start=None):
+          with_stats=False, allow_noconv=False, timing=False, precision=PREC_FP64, warm_start=None,
+          lu_threshold=0):
     """Sec. 4.3 solve on device tensors; returns R (float64, original order).
 
     ``u`` may be a CUDA tensor or a numpy array (host I/O through the C ABI's
     io_on_host path; R is then returned as numpy).  ``precision=PREC_MIXED``
     runs the SCC series in FP32 with FP64 residual refinement;
     ``warm_start`` (an ``Mpnn``) starts each SCC's series from the network's
-    guess."""
+    guess; SCCs of fewer than ``lu_threshold`` vertices are solved by dense
+    elimination (Sec. 4.3 item 3)."""
     lib = load_library()
     on_host = isinstance(u, np.ndarray)
-    o, keep = _opts(norm, max_iter, on_host, replay_iters, precision, warm_start)
+    o, keep = _opts(norm, max_iter, on_host, replay_iters, precision, warm_start, lu_threshold)
     comp_iters = np.zeros(max(part.n_comp, 1), np.int32)
     st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data, int(timing), 0.0, 0, 0, 0, 0)
     if on_host:

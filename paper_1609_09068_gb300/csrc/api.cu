@@ -193,7 +193,7 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
   if (!part) return PR_EINVAL;
   const int32_t n = part->g.n;
   if (n > 0) PRGB_TRY(check_solve_args(c, u, tol, R));
-  pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr, nullptr};
+  pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr, nullptr, 0};
   if (opts) o = *opts;
   if (o.max_iter <= 0) o.max_iter = 10000;
   if (o.norm != PR_NORM_L1 && o.norm != PR_NORM_LINF) return PR_EINVAL;
@@ -201,6 +201,7 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
   const bool mixed = o.precision == PR_PREC_MIXED;
   if (mixed && (o.norm != PR_NORM_L1 || o.replay_iters)) return PR_EINVAL;
   if (o.warm_start && o.replay_iters) return PR_EINVAL;
+  if (o.lu_threshold < 0 || o.lu_threshold > 129) return PR_EINVAL;
   if (o.replay_iters) {
     for (int32_t k = 0; k < part->n_comp; k++)
       if (o.replay_iters[k] < 0 || o.replay_iters[k] > 1000000) return PR_EINVAL;
@@ -221,8 +222,8 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
     // the level loop replayed from the partition's cached CUDA graph
     lock.lock();
     SolvePlan* pl = nullptr;
-    PRGB_TRY(plan_solve(P, c, u, o.io_on_host != 0, tol, o.norm, o.max_iter, mixed, timing, o.warm_start, R,
-                        o.io_on_host != 0, s, &pl, &launches));
+    PRGB_TRY(plan_solve(P, c, u, o.io_on_host != 0, tol, o.norm, o.max_iter, mixed, timing, o.warm_start,
+                        o.lu_threshold, R, o.io_on_host != 0, s, &pl, &launches));
     ctl = pl->ctl;
     iters = pl->iters;
     iters64 = mixed ? pl->iters64 : nullptr;
@@ -248,8 +249,8 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
       du = tu;
       dR = tR;
     }
-    PRGB_TRY(run_solve(part, c, du, tol, o.norm, o.max_iter, replay, false, dR, iters, nullptr, tmp, ctl, &launches,
-                       timing ? kt : nullptr));
+    PRGB_TRY(run_solve(part, c, du, tol, o.norm, o.max_iter, replay, false, o.lu_threshold, dR, iters, nullptr, tmp,
+                       ctl, &launches, timing ? kt : nullptr));
     if (o.io_on_host && n > 0) PRGB_CUDA(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
   }
   int flags = 0;
@@ -306,11 +307,11 @@ pr_status pr_global_power(const pr_graph* g, double c, const double* u, double t
   if (!g) return PR_EINVAL;
   const int32_t n = g->g.n;
   if (n > 0) PRGB_TRY(check_solve_args(c, u, tol, R));
-  pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr, nullptr};
+  pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr, nullptr, 0};
   if (opts) o = *opts;
   if (o.max_iter <= 0) o.max_iter = 10000;
   if (o.norm != PR_NORM_L1 && o.norm != PR_NORM_LINF) return PR_EINVAL;
-  if (o.precision != PR_PREC_FP64 || o.warm_start) return PR_EINVAL;
+  if (o.precision != PR_PREC_FP64 || o.warm_start || o.lu_threshold) return PR_EINVAL;
   int fixed = -1;
   if (o.replay_iters) {
     fixed = o.replay_iters[0];

@@ -392,6 +392,8 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   PRGB_CUDA(cudaMemcpyAsync(hs, &ctl->cnt[3], 8, cudaMemcpyDeviceToHost, s));
   P->levels.resize(nlev);
   PRGB_CUDA(cudaMemcpyAsync(P->levels.data(), dlev, sizeof(LevelRange) * nlev, cudaMemcpyDeviceToHost, s));
+  P->h_c_off.resize((size_t)K + 1);
+  PRGB_CUDA(cudaMemcpyAsync(P->h_c_off.data(), P->c_off, ((size_t)K + 1) * 4, cudaMemcpyDeviceToHost, s));
   PRGB_CUDA(cudaStreamSynchronize(s));
   P->n_scc = hs[0];
   P->n_scc_vertices = hs[1];

@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
   double* z = zsh[wib];
   uint8_t* ix = ish[wib];
   const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
+  if (sz < a.lu_threshold && a.c_type[c] == PR_TYPE_SCC) return;  // solved by solve_lu_k (warp-uniform)
   const bool act = lane < sz;
   const int p = off + lane;
   const double inv = act ? a.p_inv[p] : 0.0;
@@ -292,6 +293,7 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
   const int m = a.int_ptr[off + sz] - ib;
   const bool staged = m <= kCtaEdgeCap;
   const bool scc = a.c_type[c] == PR_TYPE_SCC;
+  if (scc && sz < a.lu_threshold) return;  // solved by solve_lu_k (block-uniform)
   for (int i = threadIdx.x; i <= sz; i += blockDim.x) ip[i] = a.int_ptr[off + i] - ib;
   if (staged)
     for (int e = threadIdx.x; e < m; e += blockDim.x) ix[e] = (uint16_t)local_or_err(a, a.int_idx[ib + e] - off, sz);
@@ -746,6 +748,66 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Sec. 4.3 item 3: an SCC of fewer than lu_threshold (<= kLuMax + 1)
+// vertices is solved directly, (I - c A_C^T) R_C = W_C, by Gaussian
+// elimination in shared memory, one CTA per component.  The matrix is
+// column diagonally dominant (each column's off-diagonal entries sum to
+// c * internal outdeg / outdeg <= c < 1) and stays so under elimination, so
+// no pivoting is needed and every pivot is at least 1 - c.
+// ---------------------------------------------------------------------------
+constexpr int kLuMax = 128;
+constexpr int kLuThreads = 256;
+constexpr size_t kLuSmem = ((size_t)kLuMax * kLuMax + 3 * kLuMax) * sizeof(double);
+
+__global__ void __launch_bounds__(kLuThreads) solve_lu_k(SolveArgs a, int32_t cbeg) {
+  extern __shared__ double lm[];
+  const int c = cbeg + (int)blockIdx.x;
+  const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
+  if (a.c_type[c] != PR_TYPE_SCC || sz >= a.lu_threshold || sz > kLuMax) return;  // block-uniform
+  double* M = lm;                      // [sz][sz], row i = equation of vertex i
+  double* b = lm + kLuMax * kLuMax;    // [sz] right-hand side, then the solution
+  double* l = b + kLuMax;              // [sz] multipliers of one step
+  double* iv = l + kLuMax;             // [sz] 1/outdeg
+  for (int t = threadIdx.x; t < sz * sz; t += blockDim.x) M[t] = (t / sz == t % sz) ? 1.0 : 0.0;
+  for (int i = threadIdx.x; i < sz; i += blockDim.x) {
+    b[i] = a.W[off + i];
+    iv[i] = a.p_inv[off + i];
+  }
+  __syncthreads();
+  // row i: -c / outdeg(j) for each internal edge j -> i
+  for (int i = threadIdx.x; i < sz; i += blockDim.x)
+    for (int e = a.int_ptr[off + i]; e < a.int_ptr[off + i + 1]; e++) {
+      const int j = local_or_err(a, a.int_idx[e] - off, sz);
+      M[i * sz + j] -= a.c * a.p_inv[off + j];
+    }
+  __syncthreads();
+  for (int k = 0; k + 1 < sz; k++) {
+    const double ip = 1.0 / M[k * sz + k];
+    for (int i = k + 1 + threadIdx.x; i < sz; i += blockDim.x) l[i] = M[i * sz + k] * ip;
+    __syncthreads();
+    const int w = sz - k - 1;  // rows k+1.., columns k+1..
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      const int i = k + 1 + t / w, j = k + 1 + t % w;
+      M[i * sz + j] -= l[i] * M[k * sz + j];
+    }
+    for (int i = k + 1 + threadIdx.x; i < sz; i += blockDim.x) b[i] -= l[i] * b[k];
+    __syncthreads();
+  }
+  // back substitution, column by column
+  for (int i = sz - 1; i >= 0; i--) {
+    if (threadIdx.x == 0) b[i] = b[i] / M[i * sz + i];
+    __syncthreads();
+    for (int r = threadIdx.x; r < i; r += blockDim.x) b[r] -= M[r * sz + i] * b[i];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < sz; i += blockDim.x) {
+    a.R[off + i] = b[i];
+    a.zr[off + i] = b[i] * iv[i];
+  }
+  if (threadIdx.x == 0) a.iters[c] = 0;
+}
+
+// ---------------------------------------------------------------------------
 // inflow gather of one level (Eq. PR:levels as a pull): for every vertex of
 // the level, W = u + c * sum over external in-edges of R_j / outdeg(j), with
 // the balanced sweep (hubs receive tens of thousands of external edges).
@@ -1086,6 +1148,7 @@ pr_status alloc_solve_bufs(const pr_partition_s* P, bool mixed, Arena& a, SolveB
   static bool cta_attr = false;
   static size_t clu_attr[2] = {48 * 1024, 48 * 1024};
   if (!cta_attr) {
+    PRGB_CUDA(cudaFuncSetAttribute(solve_lu_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmem));
     PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
     PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kCtaSmemMixed));
@@ -1127,6 +1190,7 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
   a.xlorder = P->xlorder;
   a.p_invf = b.invf;
   a.R0 = nullptr;
+  a.lu_threshold = 0;
   a.iters64 = iters64;
   a.W = b.W;
   a.R = b.R;
@@ -1225,6 +1289,23 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       PRGB_LAUNCH();
       ++*nl;
     }
+    if (a.lu_threshold > 0) {
+      // the level's components below the threshold form a suffix of
+      // [cbeg, single) (sizes descend); the kernel skips the CACs among them
+      int lo = std::max(r.cta, r.cbeg), hi = r.single;
+      while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (P->h_c_off[mid + 1] - P->h_c_off[mid] < a.lu_threshold) hi = mid;
+        else lo = mid + 1;
+      }
+      if (r.single > lo) {
+        if (!joined[1]) PRGB_CUDA(cudaStreamWaitEvent(side.st[1], side.fork, 0));
+        joined[1] = true;
+        solve_lu_k<<<r.single - lo, kLuThreads, kLuSmem, side.st[1]>>>(a, lo);
+        PRGB_LAUNCH();
+        ++*nl;
+      }
+    }
     if (r.single > r.warp) {
       const int nw = r.single - r.warp;
       PRGB_CUDA(cudaStreamWaitEvent(side.st[2], side.fork, 0));
@@ -1256,15 +1337,16 @@ pr_status scatter_out(const pr_partition_s* P, const double* Rp, double* R, cuda
 }
 
 pr_status run_solve(const pr_partition_s* P, double c, const double* u, double tol, int norm, int max_iter,
-                    const int32_t* replay, bool mixed, double* R, int32_t* iters_dev, int32_t* iters64_dev,
-                    Arena& tmp, Ctl* ctl, int64_t* launches, KernelTiming* timing) {
+                    const int32_t* replay, bool mixed, int lu_threshold, double* R, int32_t* iters_dev,
+                    int32_t* iters64_dev, Arena& tmp, Ctl* ctl, int64_t* launches, KernelTiming* timing) {
   cudaStream_t s = tmp.stream();
   int64_t nl = 0;
   *launches = 0;
   if (P->g.n == 0) return PR_OK;
   SolveBufs b;
   PRGB_TRY(alloc_solve_bufs(P, mixed, tmp, &b, &nl));
-  const SolveArgs a = make_solve_args(P, c, u, tol, norm, max_iter, replay, b, iters_dev, iters64_dev, ctl);
+  SolveArgs a = make_solve_args(P, c, u, tol, norm, max_iter, replay, b, iters_dev, iters64_dev, ctl);
+  a.lu_threshold = lu_threshold;
   SideStreams side;
   PRGB_TRY(side.create());
   if (timing) PRGB_TRY(timing->ensure(P));
@@ -1278,28 +1360,36 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
 // per-partition CUDA graph of the level loop
 // ---------------------------------------------------------------------------
 SolvePlan::~SolvePlan() {
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
+  for (PlanGraph& e : graphs) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.graph) cudaGraphDestroy(e.graph);
+  }
   if (done) cudaEventDestroy(done);
   if (cs) cudaStreamDestroy(cs);
   delete keep;
 }
 
 // (Re)build the graph for these parameters if the cached one differs.
+// The graphs of the last kPlanGraphs parameter sets are kept (a caller
+// alternating, say, FP64 and mixed solves does not re-capture each time).
 static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double tol, int norm, int max_iter,
-                              bool mixed, bool timing, const pr_mpnn_s* warm) {
-  if (pl->exec && pl->c == c && pl->tol == tol && pl->norm == norm && pl->max_iter == max_iter &&
-      pl->mixed == mixed && pl->timing == timing && pl->warm == warm)
-    return PR_OK;
+                              bool mixed, bool timing, const pr_mpnn_s* warm, int lu, PlanGraph** out) {
+  for (PlanGraph& e : pl->graphs)
+    if (e.c == c && e.tol == tol && e.norm == norm && e.max_iter == max_iter && e.mixed == mixed &&
+        e.timing == timing && e.warm == warm && e.lu == lu) {
+      e.last_use = ++pl->uses;
+      *out = &e;
+      return PR_OK;
+    }
   const int32_t n = P->g.n;
   const int32_t K = P->n_comp;
-  if (pl->exec) {
-    cudaGraphExecDestroy(pl->exec);
-    pl->exec = nullptr;
-  }
-  if (pl->graph) {
-    cudaGraphDestroy(pl->graph);
-    pl->graph = nullptr;
+  if (pl->graphs.size() >= (size_t)kPlanGraphs) {
+    size_t old = 0;
+    for (size_t i = 1; i < pl->graphs.size(); i++)
+      if (pl->graphs[i].last_use < pl->graphs[old].last_use) old = i;
+    if (pl->graphs[old].exec) cudaGraphExecDestroy(pl->graphs[old].exec);
+    if (pl->graphs[old].graph) cudaGraphDestroy(pl->graphs[old].graph);
+    pl->graphs.erase(pl->graphs.begin() + old);
   }
   if (!pl->keep) {
     pl->keep = new (std::nothrow) Arena(P->stream);
@@ -1339,6 +1429,7 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
   SolveArgs a = make_solve_args(P, c, pl->u, tol, norm, max_iter, nullptr, pl->b, pl->iters,
                                 mixed ? pl->iters64 : nullptr, pl->ctl);
   if (warm) a.R0 = pl->R0;
+  a.lu_threshold = lu;
   const long long before = launch_count();
   int64_t nl = 0;
   PRGB_CUDA(cudaStreamBeginCapture(pl->cs, cudaStreamCaptureModeThreadLocal));
@@ -1357,22 +1448,31 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
     return st;
   }
   PRGB_CUDA(ec);
-  pl->graph = g;
-  PRGB_CUDA(cudaGraphInstantiate(&pl->exec, g, 0));
-  pl->nodes = nl;
-  pl->c = c;
-  pl->tol = tol;
-  pl->norm = norm;
-  pl->max_iter = max_iter;
-  pl->mixed = mixed;
-  pl->timing = timing;
-  pl->warm = warm;
+  PlanGraph e;
+  e.graph = g;
+  if (cudaGraphInstantiate(&e.exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    PRGB_CUDA(cudaGetLastError());
+    return PR_ECUDA;
+  }
+  e.nodes = nl;
+  e.c = c;
+  e.tol = tol;
+  e.norm = norm;
+  e.max_iter = max_iter;
+  e.mixed = mixed;
+  e.timing = timing;
+  e.warm = warm;
+  e.lu = lu;
+  e.last_use = ++pl->uses;
+  pl->graphs.push_back(e);
+  *out = &pl->graphs.back();
   return PR_OK;
 }
 
 pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_host, double tol, int norm,
-                     int max_iter, bool mixed, bool timing, const pr_mpnn_s* warm, double* R, bool R_on_host,
-                     cudaStream_t s, SolvePlan** out, int64_t* launches) {
+                     int max_iter, bool mixed, bool timing, const pr_mpnn_s* warm, int lu, double* R,
+                     bool R_on_host, cudaStream_t s, SolvePlan** out, int64_t* launches) {
   if (!P->plan) {
     P->plan = new (std::nothrow) SolvePlan;
     if (!P->plan) return PR_ENOMEM;
@@ -1380,15 +1480,16 @@ pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_hos
   SolvePlan* pl = P->plan;
   *out = pl;
   const int32_t n = P->g.n;
-  PRGB_TRY(plan_prepare(P, pl, c, tol, norm, max_iter, mixed, timing, warm));
+  PlanGraph* ge = nullptr;
+  PRGB_TRY(plan_prepare(P, pl, c, tol, norm, max_iter, mixed, timing, warm, lu, &ge));
   // the plan's buffers are reused: order this call after the previous one
   PRGB_CUDA(cudaStreamWaitEvent(s, pl->done, 0));
   if (n > 0)
     PRGB_CUDA(cudaMemcpyAsync(pl->u, u, (size_t)n * 8, u_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                               s));
-  PRGB_CUDA(cudaGraphLaunch(pl->exec, s));
-  add_launches(pl->nodes);
-  int64_t nl = pl->nodes;
+  PRGB_CUDA(cudaGraphLaunch(ge->exec, s));
+  add_launches(ge->nodes);
+  int64_t nl = ge->nodes;
   if (R_on_host) {
     PRGB_TRY(scatter_out(P, pl->b.R, pl->Rout, s, &nl));
     if (n > 0) PRGB_CUDA(cudaMemcpyAsync(R, pl->Rout, (size_t)n * 8, cudaMemcpyDeviceToHost, s));

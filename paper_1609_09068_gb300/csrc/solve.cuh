@@ -30,6 +30,7 @@ struct SolveArgs {
   const int32_t* xlorder;   // [n] positions by (level, external in-degree class)
   const float* p_invf;      // [n] 1/outdeg in FP32 (mixed precision only)
   const double* R0;         // [n] warm-start guess by position for SCC rows, or nullptr
+  int lu_threshold;         // SCCs with fewer vertices are solved by dense elimination
   int32_t* iters64;         // [K] FP64 residual sweeps per SCC (mixed only)
   double* W;                // [n] inflow-adjusted weights by position
   double* R;                // [n] by position
@@ -68,10 +69,24 @@ struct SolveBufs {
   float* invf = nullptr;
 };
 
+// one captured level loop and the parameters it was captured for
+struct PlanGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t nodes = 0;  // kernels per replay
+  double c = 0.0, tol = 0.0;
+  int norm = 0, max_iter = 0;
+  bool mixed = false, timing = false;
+  const pr_mpnn_s* warm = nullptr;
+  int lu = 0;
+  uint64_t last_use = 0;
+};
+constexpr int kPlanGraphs = 4;
+
 // A partition's cached solve: its own buffers and the level loop captured
-// as a CUDA graph for one set of (c, tol, norm, max_iter, precision,
-// timing); rebuilt when they change.  Calls that use it are ordered on the
-// device through `done`.
+// as CUDA graphs, one per recent set of (c, tol, norm, max_iter, precision,
+// timing, warm start).  Calls that use it are ordered on the device
+// through `done`.
 struct SolvePlan {
   Arena* keep = nullptr;
   SolveBufs b;
@@ -79,19 +94,15 @@ struct SolvePlan {
   KernelTiming kt;
   cudaStream_t cs = nullptr;
   cudaEvent_t done = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int64_t nodes = 0;  // kernels per replay
-  double c = 0.0, tol = 0.0;
-  int norm = 0, max_iter = 0;
-  bool mixed = false, timing = false, have_mixed_bufs = false;
+  std::vector<PlanGraph> graphs;
+  uint64_t uses = 0;
+  bool have_mixed_bufs = false;
   Ctl* ctl = nullptr;
   int32_t* iters = nullptr;
   int32_t* iters64 = nullptr;
   double* u = nullptr;
   double* Rout = nullptr;
-  const pr_mpnn_s* warm = nullptr;  // warm-start model of the cached graph
-  double* R0 = nullptr;             // [n] its guess by position
+  double* R0 = nullptr;             // [n] the warm-start guess by position
   MpnnInfer inf;
   ~SolvePlan();
 };
@@ -101,9 +112,11 @@ struct SolvePlan {
 // vertex order; replay (device, [K]) may be null; timing may be null.
 // mixed: SCC series in FP32 with FP64 residual refinement (iters64 then
 // receives the FP64 sweeps per component; it may be null otherwise).
+// lu_threshold: SCCs of fewer vertices (at most 128) are solved by dense
+// elimination (Sec. 4.3 item 3); 0 turns it off.
 pr_status run_solve(const pr_partition_s* P, double c, const double* u, double tol, int norm, int max_iter,
-                    const int32_t* replay, bool mixed, double* R, int32_t* iters_dev, int32_t* iters64_dev,
-                    Arena& tmp, Ctl* ctl, int64_t* launches, KernelTiming* timing);
+                    const int32_t* replay, bool mixed, int lu_threshold, double* R, int32_t* iters_dev,
+                    int32_t* iters64_dev, Arena& tmp, Ctl* ctl, int64_t* launches, KernelTiming* timing);
 
 // The same through the partition's cached graph: copies u in, replays the
 // graph, scatters R out (host or device pointers); *plan receives the plan,
@@ -111,8 +124,8 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
 // has reached them.  warm (may be null): the network that guesses each
 // SCC's start, evaluated per level inside the graph.
 pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_host, double tol, int norm,
-                     int max_iter, bool mixed, bool timing, const pr_mpnn_s* warm, double* R, bool R_on_host,
-                     cudaStream_t s, SolvePlan** plan, int64_t* launches);
+                     int max_iter, bool mixed, bool timing, const pr_mpnn_s* warm, int lu, double* R,
+                     bool R_on_host, cudaStream_t s, SolvePlan** plan, int64_t* launches);
 
 // edges read by the solve; with iters64 (may be null), also the edges read
 // by FP64 residual sweeps

@@ -55,13 +55,13 @@ def max_rel(a, b):
     return float(np.max(np.abs(a - b) / den)) if a.size else 0.0
 
 
-def assert_solve_parity(prgb, g, G, P, q, tol=1e-10, norm=oracle.NORM_L1):
+def assert_solve_parity(prgb, g, G, P, q, tol=1e-10, norm=oracle.NORM_L1, lu=0):
     import torch
     u = torch.from_numpy(g.u).cuda()
-    R, st = prgb.solve(P, C, u, tol, norm=norm, with_stats=True)
+    R, st = prgb.solve(P, C, u, tol, norm=norm, with_stats=True, lu_threshold=lu)
     R = R.cpu().numpy()
     its = st["comp_iters"]
-    Ro, its_o = oracle.solve_cw(g.rowptr, g.col, q, C, g.u, tol, norm=norm, replay_iters=its)
+    Ro, its_o = oracle.solve_cw(g.rowptr, g.col, q, C, g.u, tol, norm=norm, replay_iters=its, lu_threshold=lu)
     assert np.array_equal(its_o, its)
     assert max_rel(R, Ro) <= RTOL
     if norm == oracle.NORM_L1:
@@ -72,7 +72,7 @@ def assert_solve_parity(prgb, g, G, P, q, tol=1e-10, norm=oracle.NORM_L1):
         assert res <= bound
         assert oracle.residual_l1(g.rowptr, g.col, C, g.u, R) <= bound
     # the GPU's own stopping decisions agree with the oracle's almost everywhere
-    _, its_nat = oracle.solve_cw(g.rowptr, g.col, q, C, g.u, tol, norm=norm)
+    _, its_nat = oracle.solve_cw(g.rowptr, g.col, q, C, g.u, tol, norm=norm, lu_threshold=lu)
     ctype = np.zeros(q.n_comp, np.int64)
     ctype[q.comp] = q.type
     scc = ctype == 1
@@ -357,3 +357,55 @@ def test_graph_replay_matches_direct_launches(prgb):
     Rm = prgb.solve(P, C, u, 1e-10, precision=prgb.PREC_MIXED)
     assert prgb.residual_l1(G, C, u, Rm) <= 1e-10 * (1 + 1e-6)
     assert torch.equal(prgb.solve(P, C, u, 1e-10), R1)
+
+
+@pytest.mark.parametrize("lu", [30, 101, 129])
+def test_small_scc_dense_solve(prgb, lu):
+    """Sec. 4.3 item 3: SCCs below the threshold solved by elimination; the
+    rest by the series.  Parity with the oracle run with the same threshold
+    (iteration counts replayed for the series components)."""
+    g = gg.small_planted(seed=1)
+    G, P, q = assert_partition_equal(prgb, g.rowptr, g.col)
+    R, st = assert_solve_parity(prgb, g, G, P, q, lu=lu)
+    sizes = np.bincount(q.comp, minlength=q.n_comp)
+    ctype = np.zeros(q.n_comp, np.int64)
+    ctype[q.comp] = q.type
+    small = (ctype == 1) & (sizes < lu)
+    assert small.any()
+    assert np.all(st["comp_iters"][small] == 0)
+    assert np.all(st["comp_iters"][(ctype == 1) & ~small] > 0)
+
+
+def test_dense_solve_closed_forms(prgb):
+    import torch
+    # complete digraph K_m: R = u / (1 - c); a cycle with non-uniform u
+    m = 120
+    s, d = np.nonzero(~np.eye(m, dtype=bool))
+    rp, col = gg.csr_from_edges(m, s, d)
+    G = prgb.graph(rp, col)
+    P = prgb.partition(G)
+    u = np.full(m, 1.0 / m)
+    R, st = prgb.solve(P, C, torch.from_numpy(u).cuda(), 1e-10, lu_threshold=129, with_stats=True)
+    np.testing.assert_allclose(R.cpu().numpy(), u / (1 - C), rtol=1e-13)
+    assert st["comp_iters"][0] == 0
+    k = 50
+    rp, col = gg.csr_from_edges(k, np.arange(k), (np.arange(k) + 1) % k)
+    G = prgb.graph(rp, col)
+    P = prgb.partition(G)
+    u = np.random.default_rng(0).random(k)
+    R = prgb.solve(P, C, torch.from_numpy(u).cuda(), 1e-10, lu_threshold=k + 1).cpu().numpy()
+    # R_i = sum_t c^t u_{i-t} / (1 - c^k) on a cycle
+    expect = np.array([sum(C ** t * u[(i - t) % k] for t in range(k)) for i in range(k)]) / (1 - C ** k)
+    np.testing.assert_allclose(R, expect, rtol=1e-12)
+
+
+def test_dense_solve_web_like_and_mixed(prgb):
+    import torch
+    g = gg.web_like(seed=12, n=60_000, n_small=1_200, layers=12, giant_layer=4)
+    G, P, q = assert_partition_equal(prgb, g.rowptr, g.col)
+    assert_solve_parity(prgb, g, G, P, q, lu=100)
+    u = torch.from_numpy(g.u).cuda()
+    Rm = prgb.solve(P, C, u, 1e-10, lu_threshold=100, precision=prgb.PREC_MIXED)
+    assert prgb.residual_l1(G, C, u, Rm) <= 1e-10 * (1 + 1e-6)
+    with pytest.raises(prgb.PrError):
+        prgb.solve(P, C, u, 1e-10, lu_threshold=130)
