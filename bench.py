@@ -47,7 +47,30 @@ WORKLOADS = {
               "u=1/n, c=0.85, L1 tol 1e-10, FP64"),
     "deep": ("deep_dag: n=4,000,000, ~28M edges, 200 forced levels, 200-400 SCCs per level, "
              "CAC chains 1-50, u~U[0,1] normalised, c=0.85, L1 tol 1e-10, FP64"),
+    "large": ("web_like (generated on the GPU): n=50,000,000, ~400M edges, Zipf(2.1) degrees, giant SCC 50%, "
+              "small log-normal SCCs, chains, 12% dangling, 28 layers, u=1/n, c=0.85, L1 tol 1e-10, FP64 "
+              "(mixed precision reported beside it)"),
 }
+
+
+class _DeviceGraph:
+    """A graph generated on the device (the large workload): numpy-like
+    fields for the host copies the end-to-end leg needs."""
+
+    def __init__(self, rowptr, col, u):
+        self.rowptr_d, self.col_d, self.u_d = rowptr, col, u
+        self.n = int(rowptr.numel() - 1)
+        self.nnz = int(col.numel())
+
+    def host(self):
+        return self.rowptr_d.cpu().numpy(), self.col_d.cpu().numpy(), self.u_d.cpu().numpy()
+
+
+def load_workload(name):
+    if name == "large":
+        from graphgen.large import web_like_device
+        return _DeviceGraph(*web_like_device(seed=4, n=50_000_000))
+    return gg.config(name)
 
 
 def parse():
@@ -143,6 +166,11 @@ def oracle_step(g):
 def reference_sample(args):
     """The workload itself when K+W oracle steps fit in ~3 minutes, else the
     same generator at a proportionally smaller n (same shape)."""
+    if args.workload == "large":
+        # the 50M-vertex graph is far beyond a bounded CPU sample: the numpy
+        # web-like generator with the same shape at n = 1,000,000
+        g = gg.web_like(seed=4, n=1_000_000, giant_frac=0.5, n_small=12_000, dangling_frac=0.12)
+        return g, None, "numpy web_like at n=1,000,000 with the large workload's shape (bounded sample)"
     g = gg.config(args.workload)
     t = oracle_step(g)  # also the first warm-up step
     budget = 180.0
@@ -209,11 +237,14 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    g = gg.config(args.workload)
+    g = load_workload(args.workload)
     E = g.nnz
-    rowptr = torch.from_numpy(g.rowptr).cuda()
-    col = torch.from_numpy(g.col).cuda()
-    u = torch.from_numpy(g.u).cuda()
+    if isinstance(g, _DeviceGraph):
+        rowptr, col, u = g.rowptr_d, g.col_d, g.u_d
+    else:
+        rowptr = torch.from_numpy(g.rowptr).cuda()
+        col = torch.from_numpy(g.col).cuda()
+        u = torch.from_numpy(g.u).cuda()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def ev():
@@ -366,9 +397,10 @@ def run_ours(args):
                 "l1_diff_vs_cold": float((Rw - Rc0).abs().sum().item())}
 
     # ---- end to end through the C ABI with host buffers ---------------------
-    rp_h = torch.from_numpy(g.rowptr).pin_memory().numpy()
-    col_h = torch.from_numpy(g.col).pin_memory().numpy()
-    u_h = torch.from_numpy(g.u).pin_memory().numpy()
+    hr, hc, hu_ = g.host() if isinstance(g, _DeviceGraph) else (g.rowptr, g.col, g.u)
+    rp_h = torch.from_numpy(hr).pin_memory().numpy()
+    col_h = torch.from_numpy(hc).pin_memory().numpy()
+    u_h = torch.from_numpy(hu_).pin_memory().numpy()
     e2e_ms = []
     for k in range(args.steps):
         flush.fill_(k & 0xFF)
@@ -382,8 +414,8 @@ def run_ours(args):
         e2e_ms.append(a.elapsed_time(b))
         assert isinstance(Rh, np.ndarray)
     t_e2e = max_over_ranks(float(np.mean(e2e_ms)))
-    h2d = g.rowptr.nbytes + g.col.nbytes + g.u.nbytes
-    d2h = g.u.nbytes
+    h2d = rp_h.nbytes + col_h.nbytes + u_h.nbytes
+    d2h = u_h.nbytes
 
     # ---- roofline of the dominant SpMV kernel --------------------------------
     peaks, peak_kind = measured_peaks()
@@ -400,7 +432,7 @@ def run_ours(args):
 
     # ---- CPU oracle on the host cores ---------------------------------------
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "large":
         import oracle
         oracle.build()
         t_cpu = oracle_step(g)
