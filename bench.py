@@ -66,10 +66,10 @@ class _DeviceGraph:
         return self.rowptr_d.cpu().numpy(), self.col_d.cpu().numpy(), self.u_d.cpu().numpy()
 
 
-def load_workload(name):
+def load_workload(name, large_n=50_000_000):
     if name == "large":
         from graphgen.large import web_like_device
-        return _DeviceGraph(*web_like_device(seed=4, n=50_000_000))
+        return _DeviceGraph(*web_like_device(seed=4, n=large_n))
     return gg.config(name)
 
 
@@ -83,6 +83,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="(per-step times always go to stderr)")
     ap.add_argument("--no-warm-start", action="store_true", help="skip training and timing the learned warm start")
+    ap.add_argument("--large-n", type=int, default=50_000_000, help="vertices of the large workload")
     return ap.parse_args()
 
 
@@ -237,7 +238,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    g = load_workload(args.workload)
+    g = load_workload(args.workload, args.large_n)
     E = g.nnz
     if isinstance(g, _DeviceGraph):
         rowptr, col, u = g.rowptr_d, g.col_d, g.u_d
@@ -445,7 +446,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "n": g.n, "nnz": E, "c": C, "tol": TOL,
+        "config": {"workload": WORKLOADS[args.workload] if args.workload != "large" or args.large_n == 50_000_000
+                   else WORKLOADS["large"].replace("n=50,000,000, ~400M edges", f"n={args.large_n:,}"),
+                   "n": g.n, "nnz": E, "c": C, "tol": TOL,
                    "norm": "L1", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed before each step by a 256 MiB device write outside the timed events"},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
