@@ -241,132 +241,6 @@ static unsigned grid_n(int64_t n) {
   return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-// ---- compaction of the unassigned remainder -----------------------------------
-// The signature rounds only ever follow edges whose endpoints are both
-// unassigned and in the same piece.  A compacted copy of that subgraph
-// (vertices renumbered in ascending original id, so "largest id" means the
-// same before and after) lets each round scan live edges only.
-struct SubGraph {
-  int32_t n = 0;
-  int64_t m = 0;
-  int32_t *optr = nullptr, *oidx = nullptr, *iptr = nullptr, *iidx = nullptr;
-  int32_t* orig = nullptr;  // compact id -> original vertex
-  int32_t *rep = nullptr, *pin = nullptr, *pout = nullptr;  // rep: compact id of the SCC's largest vertex, or -1
-};
-
-__global__ void sub_flag_k(int32_t n, const int32_t* __restrict__ rep, uint8_t* __restrict__ live) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    live[v] = rep[v] < 0;
-}
-
-__global__ void sub_ids_k(int32_t n, const uint8_t* __restrict__ live, const int32_t* __restrict__ nid,
-                          const int32_t* __restrict__ orig_in, const int32_t* __restrict__ pin,
-                          const int32_t* __restrict__ pout, int32_t* __restrict__ orig, int32_t* __restrict__ spin,
-                          int32_t* __restrict__ spout, int32_t* __restrict__ srep) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    if (!live[v]) continue;
-    const int k = nid[v];
-    orig[k] = orig_in ? orig_in[v] : (int32_t)v;
-    spin[k] = pin[v];
-    spout[k] = pout[v];
-    srep[k] = -1;
-  }
-}
-
-// warp per live vertex: its live same-piece neighbours along (ptr, idx);
-// with out != nullptr they are written (order kept) as compact ids
-__global__ void sub_edges_k(int32_t n, const uint8_t* __restrict__ live, const int32_t* __restrict__ nid,
-                            const int32_t* __restrict__ pin, const int32_t* __restrict__ pout,
-                            const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                            int32_t* __restrict__ cnt, const int32_t* __restrict__ optr2, int32_t* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = lanemask_lt();
-  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = w0; v < n; v += nw) {
-    if (!live[v]) continue;  // warp-uniform
-    const int a = pin[v], b = pout[v];
-    int o = out ? optr2[nid[v]] : 0, total = 0;
-    for (int base = ptr[v]; base < ptr[v + 1]; base += 32) {
-      const int e = base + lane;
-      bool keep = false;
-      int x = 0;
-      if (e < ptr[v + 1]) {
-        x = idx[e];
-        const int lx = live[x], px = pin[x], qx = pout[x];
-        keep = lx && px == a && qx == b;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      if (out && keep) out[o + __popc(bal & lt)] = nid[x];
-      o += __popc(bal);
-      total += __popc(bal);
-    }
-    if (!out && lane == 0) cnt[nid[v]] = total;
-  }
-}
-
-// settled vertices of a compacted graph back to original ids
-__global__ void sub_writeback_k(int32_t n, const int32_t* __restrict__ orig, const int32_t* __restrict__ srep,
-                                int32_t* __restrict__ rep) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    if (srep[v] >= 0) rep[orig[v]] = orig[srep[v]];
-}
-
-// Compacted copy of the unassigned vertices of (n, optr, oidx, iptr, iidx)
-// with their (rep, pin, pout); orig_in maps those ids to original vertices
-// (null: they are original).  Synchronises (the sizes are read back).
-static pr_status compact(int32_t n, const int32_t* optr, const int32_t* oidx, const int32_t* iptr,
-                         const int32_t* iidx, const int32_t* rep, const int32_t* pin, const int32_t* pout,
-                         const int32_t* orig_in, SubGraph* out, Arena& tmp) {
-  cudaStream_t s = tmp.stream();
-  uint8_t* live;
-  int32_t* nid;
-  PRGB_TRY(tmp.alloc(&live, (size_t)n + 1));
-  PRGB_TRY(tmp.alloc(&nid, (size_t)n + 1));
-  sub_flag_k<<<grid_n(n), kBlock, 0, s>>>(n, rep, live);
-  PRGB_LAUNCH();
-  PRGB_TRY(scan_u8(live, nid, n, tmp));
-  int32_t nc = 0;
-  PRGB_CUDA(cudaMemcpyAsync(&nc, nid + n, 4, cudaMemcpyDeviceToHost, s));
-  PRGB_CUDA(cudaStreamSynchronize(s));
-  SubGraph g;
-  g.n = nc;
-  PRGB_TRY(tmp.alloc(&g.orig, (size_t)nc + 1));
-  PRGB_TRY(tmp.alloc(&g.rep, (size_t)nc + 1));
-  PRGB_TRY(tmp.alloc(&g.pin, (size_t)nc + 1));
-  PRGB_TRY(tmp.alloc(&g.pout, (size_t)nc + 1));
-  PRGB_TRY(tmp.alloc(&g.optr, (size_t)nc + 1));
-  PRGB_TRY(tmp.alloc(&g.iptr, (size_t)nc + 1));
-  int32_t* cnt;
-  PRGB_TRY(tmp.alloc(&cnt, (size_t)nc + 1));
-  sub_ids_k<<<grid_n(n), kBlock, 0, s>>>(n, live, nid, orig_in, pin, pout, g.orig, g.pin, g.pout, g.rep);
-  PRGB_LAUNCH();
-  const unsigned gw = grid_n((int64_t)n * 32);
-  int64_t mm[2] = {0, 0};
-  for (int dir = 0; dir < 2; dir++) {
-    const int32_t* ptr = dir == 0 ? optr : iptr;
-    const int32_t* idx = dir == 0 ? oidx : iidx;
-    int32_t* sptr = dir == 0 ? g.optr : g.iptr;
-    sub_edges_k<<<gw, kBlock, 0, s>>>(n, live, nid, pin, pout, ptr, idx, cnt, nullptr, nullptr);
-    PRGB_LAUNCH();
-    PRGB_TRY(scan_i32(cnt, sptr, nc, tmp));
-    int32_t m32 = 0;
-    PRGB_CUDA(cudaMemcpyAsync(&m32, sptr + nc, 4, cudaMemcpyDeviceToHost, s));
-    PRGB_CUDA(cudaStreamSynchronize(s));
-    mm[dir] = m32;
-    int32_t* sidx;
-    PRGB_TRY(tmp.alloc(&sidx, (size_t)m32 + 1));
-    sub_edges_k<<<gw, kBlock, 0, s>>>(n, live, nid, pin, pout, ptr, idx, nullptr, sptr, sidx);
-    PRGB_LAUNCH();
-    if (dir == 0) g.oidx = sidx;
-    else g.iidx = sidx;
-  }
-  if (mm[0] != mm[1]) return PR_EINTERNAL;
-  g.m = mm[0];
-  *out = g;
-  return PR_OK;
-}
-
 pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
   cudaStream_t s = tmp.stream();
   const int32_t n = g.n;
@@ -436,51 +310,28 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
       PRGB_LAUNCH();
     }
   }
-  // the remainder, compacted; trimmed again (the giant SCC and the other
-  // piece are gone, so more vertices lose all in- or out-edges), then the
-  // signature rounds; recompacted whenever it has shrunk by half
-  SubGraph sg;
-  PRGB_TRY(compact(n, g.optr, g.oidx, g.iptr, g.iidx, rep, pin, pout, nullptr, &sg, tmp));
-  bool fresh = true;
-  for (int round = 0; round < 20000 && sg.n > 0; round++) {
-    const int32_t nn = sg.n;
-    int cp = cap;
-    if (fresh) {
-      // trim_k reads rep = -1 for all, which a fresh compaction gives
-      void* args[] = {&sg.optr, &sg.oidx, &sg.iptr, &sg.iidx, (void*)&nn, &rem_out, &rem_in, &state, &sg.rep,
-                      &fav, &fac, &fbv, &fbc, &cp, &ctl};
-      PRGB_TRY(reset_ctl(ctl, s));
-      PRGB_TRY(launch_coop((const void*)trim_k, kBlock, 0, s, args, 2, nullptr));
-      fresh = false;
-    }
+  for (int round = 0; round < 20000; round++) {
     for (int dir = 0; dir < 2; dir++) {
       PRGB_TRY(reset_ctl(ctl, s));
-      const int32_t* ptr = dir == 0 ? sg.optr : sg.iptr;
-      const int32_t* idx = dir == 0 ? sg.oidx : sg.iidx;
+      const int32_t* ptr = dir == 0 ? g.optr : g.iptr;
+      const int32_t* idx = dir == 0 ? g.oidx : g.iidx;
       int32_t* sig = dir == 0 ? sin : sout;
-      void* args[] = {&ptr, &idx, (void*)&nn, &sg.rep, &sg.pin, &sg.pout, &sig, &stamp, &fav, &fac, &fbv, &fbc,
-                      &cp, &ctl};
+      int32_t nn = n;
+      int cp = cap;
+      void* args[] = {&ptr, &idx, &nn, &rep, &pin, &pout, &sig, &stamp, &fav, &fac, &fbv, &fbc, &cp, &ctl};
       PRGB_TRY(launch_coop((const void*)propagate_k, kBlock, 0, s, args, 2, nullptr));
     }
     PRGB_CUDA(cudaMemsetAsync(&ctl->cnt[7], 0, sizeof(int), s));
-    assign_k<<<grid_n(nn), kBlock, 0, s>>>(nn, sg.rep, sg.pin, sg.pout, sin, sout, ctl);
+    assign_k<<<grid_n(n), kBlock, 0, s>>>(n, rep, pin, pout, sin, sout, ctl);
     PRGB_LAUNCH();
     int h[2] = {0, 0};
     PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     PRGB_CUDA(cudaMemcpyAsync(&h[1], &ctl->cnt[7], sizeof(int), cudaMemcpyDeviceToHost, s));
     PRGB_CUDA(cudaStreamSynchronize(s));
     if (h[0]) return (pr_status)h[0];
-    if (h[1] == 0 || 2 * (int64_t)h[1] < nn) {
-      sub_writeback_k<<<grid_n(nn), kBlock, 0, s>>>(nn, sg.orig, sg.rep, rep);
-      PRGB_LAUNCH();
-      if (h[1] == 0) return PR_OK;
-      SubGraph next;
-      PRGB_TRY(compact(nn, sg.optr, sg.oidx, sg.iptr, sg.iidx, sg.rep, sg.pin, sg.pout, sg.orig, &next, tmp));
-      sg = next;
-      fresh = true;
-    }
+    if (h[1] == 0) return PR_OK;
   }
-  return sg.n == 0 ? PR_OK : PR_EINTERNAL;
+  return PR_EINTERNAL;
 }
 
 }  // namespace prgb
