@@ -3,12 +3,14 @@
 // The paper finds SCCs with a Tarjan DFS (Sec. 4.1), which is sequential.
 // Here: (1) trim -- repeatedly remove vertices with no remaining in- or
 // out-edge; each is a 1-vertex SCC (it lies on no cycle, Sec. 3 remark on
-// 1-vertex SCCs); (2) signature rounds on what is left: every vertex v gets
-// in(v) = largest id that reaches v and out(v) = largest id reachable from
-// v, both over the "alive" edges.  If in(v) == out(v) = m then m and v reach
-// each other, so v lies in the SCC of m, and m is that SCC's largest id.
-// Edges whose endpoints got different signatures cannot lie inside an SCC;
-// they die and the next round works inside the pieces that remain.  Every
+// 1-vertex SCCs); (2) forward-backward reachability from the best-connected
+// vertex, which takes out the giant SCC; (3) colouring rounds on what is
+// left: every vertex gets colour(v) = largest id that reaches it inside its
+// piece.  A vertex r with colour(r) == r is a root: the vertices of colour r
+// from which r is reachable (a backward search from every root at once,
+// staying inside the root's colour) are exactly r's SCC, and r is its
+// largest id.  Two vertices of one SCC have the same ancestors, hence the
+// same colour, so the colours become the pieces of the next round.  Every
 // round settles at least the SCC of each piece's largest vertex.
 //
 // Result: rep[v] = largest vertex id of v's SCC.
@@ -85,10 +87,11 @@ __global__ void trim_k(const int32_t* __restrict__ optr, const int32_t* __restri
   run_waves(ctl, f, 101, k);
 }
 
-// ---- max-label propagation over alive edges, frontier driven --------------
-// dir 0: along out-edges (sig = largest id reaching v); dir 1: along in-edges.
-// Frontier items are (vertex, chunk of kChunkE edges), so the adjacency of a
-// hub is spread over many warps.
+// ---- max-label propagation inside the pieces, frontier driven ---------------
+// Along out-edges: sig(v) = largest id that reaches v through unsettled
+// vertices of v's piece (pieces: equal (pin, pout)).  Frontier items are
+// (vertex, chunk of kChunkE edges), so the adjacency of a hub is spread over
+// many warps.
 struct PropK {
   const int32_t *ptr, *idx, *rep, *pin, *pout;
   int32_t *sig, *stamp;
@@ -136,6 +139,67 @@ __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __re
   const Frontier f{fav, fac, fbv, fbc, cap};
   PropK k{ptr, idx, rep, pin, pout, sig, stamp};
   run_waves(ctl, f, 111, k);
+}
+
+// ---- backward search from every colour root --------------------------------
+// From each root r (colour(r) == r) along in-edges, entering only unsettled
+// vertices of the same colour: they reach r and r reaches them.
+struct RootBfsK {
+  const int32_t *ptr, *idx, *rep, *color;
+  int32_t* mark;
+  int tag;
+  __device__ void range(int u, int j, int* e0, int* e1) const {
+    *e0 = ptr[u] + j * kChunkE;
+    *e1 = min(ptr[u + 1], *e0 + kChunkE);
+  }
+  __device__ int4 pre(int v, int, bool) const { return make_int4(color[v], 0, 0, 0); }
+  __device__ bool edge(int e, int4 p, int, int* w, int* nch) const {
+    *w = idx[e];
+    const int x = *w;
+    const int rx = rep[x], cx = color[x], mx = vload(&mark[x]);
+    if ((rx >= 0) | (cx != p.x) | (mx == tag) || atomicExch(&mark[x], tag) == tag) return false;
+    *nch = nchunks_of(ptr[x + 1] - ptr[x]);
+    return *nch > 0;
+  }
+};
+
+__global__ void root_bfs_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
+                           const int32_t* __restrict__ rep, const int32_t* __restrict__ color, int32_t* mark,
+                           int tag, int* fav, int* fac, int* fbv, int* fbc, int cap, Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int gw = gwarp(), nw = nwarps();
+  for (int64_t vb = (int64_t)gw * 32; vb < n; vb += (int64_t)nw * 32) {
+    const int64_t v = vb + lane;
+    bool want = false;
+    int nch = 0;
+    if (v < n && rep[v] < 0 && color[v] == (int32_t)v) {
+      mark[v] = tag;
+      nch = nchunks_of(ptr[v + 1] - ptr[v]);
+      want = nch > 0;
+    }
+    warp_push(want, (int)v, nch, fav, fac, &ctl->cnt[0], cap, ctl);
+  }
+  const Frontier f{fav, fac, fbv, fbc, cap};
+  RootBfsK k{ptr, idx, rep, color, mark, tag};
+  run_waves(ctl, f, 131, k);
+}
+
+// settle what the search reached; the colours become the next pieces
+__global__ void assign_color_k(int32_t n, int32_t* rep, int32_t* pin, int32_t* pout, const int32_t* color,
+                               const int32_t* mark, int tag, Ctl* ctl) {
+  int left = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (rep[v] >= 0) continue;
+    if (mark[v] == tag) {
+      rep[v] = color[v];
+    } else {
+      pin[v] = color[v];
+      pout[v] = -1;
+      left++;
+    }
+  }
+  left = __reduce_add_sync(0xffffffffu, left);
+  if ((threadIdx.x & 31) == 0 && left) atomicAdd(&ctl->cnt[7], left);
 }
 
 // ---- FW-BW for the largest SCC ---------------------------------------------
@@ -219,22 +283,6 @@ __global__ void fwbw_assign_k(int32_t n, const int32_t* fw, const int32_t* bw, c
   }
 }
 
-__global__ void assign_k(int32_t n, int32_t* rep, int32_t* pin, int32_t* pout, const int32_t* sin,
-                         const int32_t* sout, Ctl* ctl) {
-  int left = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    if (rep[v] >= 0) continue;
-    if (sin[v] == sout[v]) {
-      rep[v] = sin[v];
-    } else {
-      pin[v] = sin[v];
-      pout[v] = sout[v];
-      left++;
-    }
-  }
-  if (left) atomicAdd(&ctl->cnt[7], left);
-}
-
 static unsigned grid_n(int64_t n) {
   int64_t g = (n + kBlock - 1) / kBlock;
   int64_t cap = (int64_t)num_sms() * 16;
@@ -245,7 +293,7 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
   cudaStream_t s = tmp.stream();
   const int32_t n = g.n;
   if (n == 0) return PR_OK;
-  int32_t *rem_out, *rem_in, *state, *sin, *sout, *pin, *pout, *stamp;
+  int32_t *rem_out, *rem_in, *state, *sin, *pin, *pout, *stamp;
   int *fav, *fac, *fbv, *fbc;
   const int cap = (int)(2 * (int64_t)n + 2 * g.m / kChunkE + 2);
   PRGB_TRY(tmp.alloc(&fav, cap));
@@ -256,7 +304,6 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
   PRGB_TRY(tmp.alloc(&rem_in, n));
   PRGB_TRY(tmp.alloc(&state, n));
   PRGB_TRY(tmp.alloc(&sin, n));
-  PRGB_TRY(tmp.alloc(&sout, n));
   PRGB_TRY(tmp.alloc(&pin, n));
   PRGB_TRY(tmp.alloc(&pout, n));
   PRGB_TRY(tmp.alloc(&stamp, n));
@@ -310,19 +357,29 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
       PRGB_LAUNCH();
     }
   }
+  int32_t* mark;
+  PRGB_TRY(tmp.alloc(&mark, n));
+  PRGB_CUDA(cudaMemsetAsync(mark, 0, (size_t)n * 4, s));
   for (int round = 0; round < 20000; round++) {
-    for (int dir = 0; dir < 2; dir++) {
+    const int32_t nn = n;
+    int cp = cap;
+    int tag = round + 1;
+    {
       PRGB_TRY(reset_ctl(ctl, s));
-      const int32_t* ptr = dir == 0 ? g.optr : g.iptr;
-      const int32_t* idx = dir == 0 ? g.oidx : g.iidx;
-      int32_t* sig = dir == 0 ? sin : sout;
-      int32_t nn = n;
-      int cp = cap;
-      void* args[] = {&ptr, &idx, &nn, &rep, &pin, &pout, &sig, &stamp, &fav, &fac, &fbv, &fbc, &cp, &ctl};
+      const int32_t* ptr = g.optr;
+      const int32_t* idx = g.oidx;
+      void* args[] = {&ptr, &idx, (void*)&nn, &rep, &pin, &pout, &sin, &stamp, &fav, &fac, &fbv, &fbc, &cp, &ctl};
       PRGB_TRY(launch_coop((const void*)propagate_k, kBlock, 0, s, args, 2, nullptr));
     }
+    {
+      PRGB_TRY(reset_ctl(ctl, s));
+      const int32_t* ptr = g.iptr;
+      const int32_t* idx = g.iidx;
+      void* args[] = {&ptr, &idx, (void*)&nn, &rep, &sin, &mark, &tag, &fav, &fac, &fbv, &fbc, &cp, &ctl};
+      PRGB_TRY(launch_coop((const void*)root_bfs_k, kBlock, 0, s, args, 2, nullptr));
+    }
     PRGB_CUDA(cudaMemsetAsync(&ctl->cnt[7], 0, sizeof(int), s));
-    assign_k<<<grid_n(n), kBlock, 0, s>>>(n, rep, pin, pout, sin, sout, ctl);
+    assign_color_k<<<grid_n(n), kBlock, 0, s>>>(n, rep, pin, pout, sin, mark, tag, ctl);
     PRGB_LAUNCH();
     int h[2] = {0, 0};
     PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s));
