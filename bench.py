@@ -92,6 +92,23 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(dist, x, device):
+    """The largest x over the ranks (each rank times its own replica; the job
+    takes as long as the slowest)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(edges_per_rank, world, ms):
+    """Whole-job throughput in GTEPS: every rank solves its own replica of
+    edges_per_rank edges, in ms milliseconds (the max over ranks)."""
+    return world * edges_per_rank / (ms * 1e-3) / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -231,12 +248,8 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_over_ranks_(x):
+        return max_over_ranks(dist, x, "cuda")
 
     g = load_workload(args.workload, args.large_n)
     E = g.nnz
@@ -296,11 +309,11 @@ def run_ours(args):
     clk = clocks.stop()
     phase = np.array([[recs[i][0][j].elapsed_time(recs[i][0][j + 1]) for j in range(4)]
                       for i in range(args.steps)])
-    t_step = max_over_ranks(float(phase.sum(axis=1).mean()))
+    t_step = max_over_ranks_(float(phase.sum(axis=1).mean()))
     stats = [r[1] for r in recs]
     residual = max(r[2] for r in recs)
     P = recs[-1][3]
-    value = world * E / (t_step * 1e-3) / 1e9
+    value = job_value(E, world, t_step)
 
     # ---- global power series on the same GPU --------------------------------
     grecs = []
@@ -310,7 +323,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     gph = np.array([[grecs[i][0][j].elapsed_time(grecs[i][0][j + 1]) for j in range(3)]
                     for i in range(args.steps)])
-    t_global = max_over_ranks(float(gph.sum(axis=1).mean()))
+    t_global = max_over_ranks_(float(gph.sum(axis=1).mean()))
     t_global_solve = float(gph[:, 1].mean())
     g_iters = grecs[-1][3]
     g_res = max(r[2] for r in grecs)
@@ -331,7 +344,7 @@ def run_ours(args):
         b.record()
         mrecs.append((a, b, stm, Rm))
     torch.cuda.synchronize()
-    t_mixed = max_over_ranks(float(np.mean([r[0].elapsed_time(r[1]) for r in mrecs])))
+    t_mixed = max_over_ranks_(float(np.mean([r[0].elapsed_time(r[1]) for r in mrecs])))
     stm, Rm = mrecs[-1][2], mrecs[-1][3]
     m_res = prgb.residual_l1(prgb.graph(rowptr, col), C, u, Rm)
     m_diff = float((Rm - R64).abs().sum().item())
@@ -414,7 +427,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
         assert isinstance(Rh, np.ndarray)
-    t_e2e = max_over_ranks(float(np.mean(e2e_ms)))
+    t_e2e = max_over_ranks_(float(np.mean(e2e_ms)))
     h2d = rp_h.nbytes + col_h.nbytes + u_h.nbytes
     d2h = u_h.nbytes
 
@@ -452,7 +465,7 @@ def run_ours(args):
                    "norm": "L1", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed before each step by a 256 MiB device write outside the timed events"},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
-        "e2e": {"value": world * E / (t_e2e * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_value(E, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},
         "gpu_launches": launches,
         "roofline": roofline,
@@ -465,7 +478,7 @@ def run_ours(args):
                   "traversed_gteps": stats[-1]["edge_visits"] / (ph[2] * 1e-3) / 1e9,
                   "residual_l1": residual},
         "global_power": {"ms_per_step": t_global, "solve_ms": t_global_solve, "iters": g_iters,
-                         "value": world * E / (t_global * 1e-3) / 1e9, "residual_l1": g_res,
+                         "value": job_value(E, world, t_global), "residual_l1": g_res,
                          "kernel_gbs": gk_bytes / (gk_ms * 1e-3) / 1e9 if gk_ms > 0 else None},
         "speedup_vs_global": {"step": t_global / t_step, "solve_only": t_global_solve / float(ph[2])},
         "mixed_precision": mixed,
