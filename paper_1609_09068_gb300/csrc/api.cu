@@ -139,6 +139,12 @@ pr_status pr_partition_create(const pr_graph* g, uint32_t flags, void* stream, p
     if (st == PR_OK) st = build_layout(P, crep, wave, max_wave, tmp, ctl);
     if (st == PR_OK) st = finish_sync(s, ctl, nullptr);
   }
+  if (st == PR_OK) {
+    // the class boundary and grid shape an earlier tuning chose
+    int32_t tc = kCtaCompMax, tb = 4;
+    tuned_defaults(&tc, &tb);
+    if (tc != P->cta_max || tb != P->coop_blocks) retune_levels(P, tc, tb);
+  }
   if (st != PR_OK) {
     delete P->keep;
     delete P;
@@ -300,6 +306,22 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
     }
   }
   return flags ? PR_ENOCONV : PR_OK;
+}
+
+pr_status pr_partition_set_shape(pr_partition* part, int32_t cta_max, int32_t coop_blocks) {
+  if (!part || cta_max < kWarpCompMax || cta_max > kCtaCompMax || coop_blocks < 1 || coop_blocks > 8)
+    return PR_EINVAL;
+  std::lock_guard<std::mutex> lock(part->plan_mu);
+  retune_levels(part, cta_max, coop_blocks);
+  return PR_OK;
+}
+
+pr_status pr_partition_tune(pr_partition* part, double c, const double* u, double tol, void* stream,
+                            int32_t* cta_max, int32_t* coop_blocks, float* best_ms) {
+  if (!part) return PR_EINVAL;
+  if (part->g.n > 0 && (!u || !(c > 0.0 && c < 1.0) || !(tol > 0.0))) return PR_EINVAL;
+  std::lock_guard<std::mutex> lock(part->plan_mu);
+  return tune_partition(part, c, u, tol, (cudaStream_t)stream, cta_max, coop_blocks, best_ms);
 }
 
 pr_status pr_global_power(const pr_graph* g, double c, const double* u, double tol, const pr_solve_opts* opts,

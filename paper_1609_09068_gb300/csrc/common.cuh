@@ -427,6 +427,8 @@ struct pr_partition_s {
   int32_t max_heavy = 0, max_chunks = 0;  // largest slice over the large components
   std::vector<prgb::LevelRange> levels;  // host, processing order
   std::vector<int32_t> h_c_off;          // host copy of c_off [K+1]
+  int32_t cta_max = prgb::kCtaCompMax;   // largest component of the one-CTA class (tunable)
+  int32_t coop_blocks = 4;               // blocks per SM of the grid-wide solve kernels (tunable)
   std::vector<prgb::LargeComp> large;    // host
   prgb::SolvePlan* plan = nullptr;       // cached solve (graph), built on first use
   std::mutex plan_mu;                    // one call at a time uses the plan

@@ -1121,6 +1121,8 @@ KernelTiming::~KernelTiming() {
   for (cudaEvent_t e : stop) cudaEventDestroy(e);
 }
 
+pr_status set_solve_attrs(const pr_partition_s* P, bool mixed);
+
 // Work buffers of a solve (all by permuted position), allocated from `a`;
 // also sets the kernels' shared-memory limits for this partition, so that
 // nothing but launches and memsets is left for the level loop.
@@ -1145,6 +1147,12 @@ pr_status alloc_solve_bufs(const pr_partition_s* P, bool mixed, Arena& a, SolveB
     PRGB_LAUNCH();
     ++*nl;
   }
+  return set_solve_attrs(P, mixed);
+}
+
+// dynamic shared memory limits of the solve kernels for this partition's
+// largest cluster-class component (raised, never lowered)
+pr_status set_solve_attrs(const pr_partition_s* P, bool mixed) {
   static bool cta_attr = false;
   static size_t clu_attr[2] = {48 * 1024, 48 * 1024};
   if (!cta_attr) {
@@ -1254,14 +1262,14 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
         // nodes, so the events time each replay
         if (timing) PRGB_CUDA(cudaEventRecordWithFlags(timing->start[ti], s, cudaEventRecordExternal));
         if (mixed)
-          PRGB_TRY(launch_coop((const void*)solve_large_scc_mx_k, kBlock, 0, s, args32, 4, nullptr));
+          PRGB_TRY(launch_coop((const void*)solve_large_scc_mx_k, kBlock, 0, s, args32, P->coop_blocks, nullptr));
         else
-          PRGB_TRY(launch_coop((const void*)solve_large_scc_k, kBlock, 0, s, args64, 4, nullptr));
+          PRGB_TRY(launch_coop((const void*)solve_large_scc_k, kBlock, 0, s, args64, P->coop_blocks, nullptr));
         if (timing) PRGB_CUDA(cudaEventRecordWithFlags(timing->stop[ti], s, cudaEventRecordExternal));
         ti++;
       } else {
         void* args[] = {&a, &L};
-        PRGB_TRY(launch_coop((const void*)solve_large_cac_k, kBlock, 0, s, args, 4, nullptr));
+        PRGB_TRY(launch_coop((const void*)solve_large_cac_k, kBlock, 0, s, args, P->coop_blocks, nullptr));
       }
       ++*nl;
     }
@@ -1426,6 +1434,7 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
     PRGB_TRY(pl->keep->alloc(&pl->inf.H1, (size_t)rows * kMpH + 4));
   }
   if (timing) PRGB_TRY(pl->kt.ensure(P));
+  PRGB_TRY(set_solve_attrs(P, mixed));
   SolveArgs a = make_solve_args(P, c, pl->u, tol, norm, max_iter, nullptr, pl->b, pl->iters,
                                 mixed ? pl->iters64 : nullptr, pl->ctl);
   if (warm) a.R0 = pl->R0;
@@ -1498,6 +1507,94 @@ pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_hos
   }
   PRGB_CUDA(cudaEventRecord(pl->done, s));
   *launches = nl;
+  return PR_OK;
+}
+
+static int32_t g_tuned_cta = kCtaCompMax;
+static int32_t g_tuned_blocks = 4;
+
+void tuned_defaults(int32_t* cta_max, int32_t* coop_blocks) {
+  *cta_max = g_tuned_cta;
+  *coop_blocks = g_tuned_blocks;
+}
+
+void retune_levels(pr_partition_s* P, int32_t cta_max, int32_t coop_blocks) {
+  P->cta_max = cta_max;
+  P->coop_blocks = coop_blocks;
+  const std::vector<int32_t>& co = P->h_c_off;
+  auto size = [&](int c) { return co[c + 1] - co[c]; };
+  for (LevelRange& r : P->levels) {
+    // sizes descend inside a level: the CTA class starts at the first
+    // component in [clu, warp) with at most cta_max vertices
+    int lo = r.clu, hi = r.warp;
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (size(mid) <= cta_max) hi = mid;
+      else lo = mid + 1;
+    }
+    r.cta = lo;
+    r.clu_max = r.cta > r.clu ? size(r.clu) : 0;
+  }
+  if (P->plan) {
+    for (PlanGraph& e : P->plan->graphs) {
+      if (e.exec) cudaGraphExecDestroy(e.exec);
+      if (e.graph) cudaGraphDestroy(e.graph);
+    }
+    P->plan->graphs.clear();
+  }
+}
+
+pr_status tune_partition(pr_partition_s* P, double c, const double* u, double tol, cudaStream_t s,
+                         int32_t* cta_max, int32_t* coop_blocks, float* best_ms) {
+  const int32_t ctas[3] = {64, 128, kCtaCompMax};
+  const int32_t blocks[2] = {3, 4};
+  float best = -1.0f;
+  int32_t bc = P->cta_max, bb = P->coop_blocks;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PRGB_CUDA(cudaEventCreate(&e0));
+  PRGB_CUDA(cudaEventCreate(&e1));
+  pr_status st = PR_OK;
+  double* R = nullptr;
+  Arena tmp(s);
+  st = tmp.alloc(&R, (size_t)P->g.n + 1);
+  for (int i = 0; i < 3 && st == PR_OK; i++)
+    for (int j = 0; j < 2 && st == PR_OK; j++) {
+      retune_levels(P, ctas[i], blocks[j]);
+      SolvePlan* pl = nullptr;
+      int64_t nl = 0;
+      float t = 1e30f;
+      for (int rep = 0; rep < 3 && st == PR_OK; rep++) {  // the first builds the graph
+        if (cudaEventRecord(e0, s) != cudaSuccess) st = PR_ECUDA;
+        if (st == PR_OK)
+          st = plan_solve(P, c, u, false, tol, PR_NORM_L1, 10000, false, false, nullptr, 0, R, false, s, &pl, &nl);
+        if (st == PR_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+          st = PR_ECUDA;
+        float ms = 0.0f;
+        if (st == PR_OK && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t = std::min(t, ms);
+      }
+      if (st == PR_OK && pl) {
+        int err = 0;
+        if (cudaMemcpyAsync(&err, &pl->ctl->err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+          st = PR_ECUDA;
+        else if (err)
+          st = (pr_status)err;
+      }
+      if (st == PR_OK && (best < 0.0f || t < best)) {
+        best = t;
+        bc = ctas[i];
+        bb = blocks[j];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  retune_levels(P, bc, bb);
+  if (st != PR_OK) return st;
+  g_tuned_cta = bc;
+  g_tuned_blocks = bb;
+  if (cta_max) *cta_max = bc;
+  if (coop_blocks) *coop_blocks = bb;
+  if (best_ms) *best_ms = best;
   return PR_OK;
 }
 

@@ -127,6 +127,17 @@ pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_hos
                      int max_iter, bool mixed, bool timing, const pr_mpnn_s* warm, int lu, double* R,
                      bool R_on_host, cudaStream_t s, SolvePlan** plan, int64_t* launches);
 
+// Autotuner (f-1): move the boundary between the one-CTA and the cluster
+// classes of every level to cta_max (33..kCtaCompMax) and set the grid-wide
+// kernels' blocks per SM; drops the partition's captured graphs.
+void retune_levels(pr_partition_s* P, int32_t cta_max, int32_t coop_blocks);
+// Times the captured solve for each candidate and keeps the fastest; the
+// choice also becomes the default of partitions created later in the process.
+pr_status tune_partition(pr_partition_s* P, double c, const double* u, double tol, cudaStream_t s,
+                         int32_t* cta_max, int32_t* coop_blocks, float* best_ms);
+// the process-wide tuned defaults (kCtaCompMax / 4 until a tuning ran)
+void tuned_defaults(int32_t* cta_max, int32_t* coop_blocks);
+
 // edges read by the solve; with iters64 (may be null), also the edges read
 // by FP64 residual sweeps
 pr_status solve_edge_visits(const pr_partition_s* P, const int32_t* iters_dev, const int32_t* iters64_dev,
