@@ -315,6 +315,8 @@ struct DevGraph {
   int32_t* heavy_chrow = nullptr;
   int32_t nheavy = 0, nchunks = 0;
   int32_t* lorder = nullptr;  // [n] rows ordered by in-degree class (heavy last)
+  int32_t* oheavy = nullptr;  // vertices with more than kHeavy out-edges (ascending)
+  int32_t noheavy = 0;
   double* inv = nullptr;      // [n] 1/outdeg, 0 for dangling vertices
 };
 

@@ -115,13 +115,30 @@ __global__ void sub_tables_k(int32_t n, int32_t K, const uint8_t* subflag, const
   for (int64_t c = gtid(); c < K; c += gstride()) c_sub[c] = subidx[c_off[c]];
 }
 
-// warp per permuted vertex: count internal / external in-edges
-__global__ void edge_count_k(int32_t n, const int32_t* perm, const int32_t* iptr, const int32_t* iidx,
-                             const int32_t* comp_id, int32_t* icnt, int32_t* ecnt) {
+// count internal / external in-edges per permuted vertex: with list ==
+// nullptr a thread per vertex with at most kHeavy in-edges, otherwise a
+// warp per listed vertex (the vertices with more)
+__global__ void edge_count_k(int32_t n, const int32_t* perm, const int32_t* pos, const int32_t* list,
+                             const int32_t* iptr, const int32_t* iidx, const int32_t* comp_id, int32_t* icnt,
+                             int32_t* ecnt) {
+  if (!list) {
+    for (int64_t p = gtid(); p < n; p += gstride()) {
+      const int v = perm[p];
+      const int e0 = iptr[v], e1 = iptr[v + 1];
+      if (e1 - e0 > kHeavy) continue;
+      const int cv = comp_id[v];
+      int in = 0;
+      for (int e = e0; e < e1; e++) in += comp_id[iidx[e]] == cv;
+      icnt[p] = in;
+      ecnt[p] = (e1 - e0) - in;
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const int64_t w0 = gtid() >> 5, nw = gstride() >> 5;
-  for (int64_t p = w0; p < n; p += nw) {
-    const int v = perm[p];
+  for (int64_t i = w0; i < n; i += nw) {
+    const int v = list[i];
+    const int64_t p = pos[v];
     const int cv = comp_id[v];
     int in = 0, ex = 0;
     for (int e = iptr[v] + lane; e < iptr[v + 1]; e += 32) {
@@ -346,8 +363,13 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   PRGB_TRY(build_inv(P->p_outdeg, n, keep, &P->p_inv, s));
   PRGB_TRY(keep.alloc(&P->int_ptr, (size_t)n + 1));
   PRGB_TRY(keep.alloc(&P->ext_ptr, (size_t)n + 1));
-  edge_count_k<<<gridw(n), kBlock, 0, s>>>(n, P->perm, g.iptr, g.iidx, P->comp_id, icnt, ecnt);
+  edge_count_k<<<grid1(n), kBlock, 0, s>>>(n, P->perm, pos, nullptr, g.iptr, g.iidx, P->comp_id, icnt, ecnt);
   PRGB_LAUNCH();
+  if (g.nheavy > 0) {
+    edge_count_k<<<gridw(g.nheavy), kBlock, 0, s>>>(g.nheavy, P->perm, pos, g.heavy_rows, g.iptr, g.iidx,
+                                                    P->comp_id, icnt, ecnt);
+    PRGB_LAUNCH();
+  }
   PRGB_TRY(scan_i32(icnt, P->int_ptr, n, tmp));
   PRGB_TRY(scan_i32(ecnt, P->ext_ptr, n, tmp));
   int32_t mi = 0, me = 0;

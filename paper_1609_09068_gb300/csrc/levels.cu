@@ -16,6 +16,7 @@
 // afterwards with a lock-free union-find (hook the larger root under the
 // smaller), so a CAC's root is its smallest vertex.
 #include "common.cuh"
+#include "spmv.cuh"
 #include "waves.cuh"
 
 namespace prgb {
@@ -43,7 +44,31 @@ __global__ void count_nodes_k(const int32_t* __restrict__ optr, const int32_t* _
       atomicMin(&smin[U], mn);
     }
   }
-  for (int64_t u = gwarp_l(); u < n; u += nwarps_l()) {
+  // external out-edges: a thread per vertex with at most kHeavy out-edges
+  // (the rest: count_nodes_heavy_k)
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int e0 = optr[u], e1 = optr[u + 1];
+    if (e1 - e0 > kHeavy) continue;
+    const int U = rep[u];
+    int ext = 0;
+    for (int e = e0; e < e1; e++) {
+      const int W = rep[oidx[e]];
+      if (W != U) {
+        ext++;
+        atomicAdd(&cin_cnt[W], 1);
+      }
+    }
+    if (ext) atomicAdd(&pending[U], ext);
+  }
+}
+
+// the same for the listed vertices with more than kHeavy out-edges, a warp each
+__global__ void count_nodes_heavy_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx,
+                                    const int32_t* __restrict__ list, int32_t nlist,
+                                    const int32_t* __restrict__ rep, int32_t* pending, int32_t* cin_cnt) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = gwarp_l(); i < nlist; i += nwarps_l()) {
+    const int u = list[i];
     const int U = rep[u];
     int ext = 0;
     for (int e = optr[u] + lane; e < optr[u + 1]; e += 32) {
@@ -58,10 +83,27 @@ __global__ void count_nodes_k(const int32_t* __restrict__ optr, const int32_t* _
   }
 }
 
+// list == nullptr: a thread per vertex with at most kHeavy out-edges;
+// otherwise a warp per listed vertex
 __global__ void fill_cin_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx, int32_t n,
-                           const int32_t* __restrict__ rep, int32_t* cursor, int32_t* cin_src) {
+                           const int32_t* __restrict__ list, const int32_t* __restrict__ rep, int32_t* cursor,
+                           int32_t* cin_src) {
+  if (!list) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+      const int e0 = optr[u], e1 = optr[u + 1];
+      if (e1 - e0 > kHeavy) continue;
+      const int U = rep[u];
+      for (int e = e0; e < e1; e++) {
+        const int W = rep[oidx[e]];
+        if (W != U) cin_src[atomicAdd(&cursor[W], 1)] = U;
+      }
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
-  for (int64_t u = gwarp_l(); u < n; u += nwarps_l()) {
+  for (int64_t i = gwarp_l(); i < n; i += nwarps_l()) {
+    const int u = list[i];
     const int U = rep[u];
     for (int e = optr[u] + lane; e < optr[u + 1]; e += 32) {
       const int W = rep[oidx[e]];
@@ -170,6 +212,7 @@ __device__ __forceinline__ void uf_union(int* par, int a, int b) {
   }
 }
 
+// a warp per vertex: its unions run in parallel lanes
 __global__ void merge_unions_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx, int32_t n,
                                const int32_t* __restrict__ rep, const int32_t* __restrict__ nsize,
                                const int32_t* __restrict__ level_node, const uint8_t* __restrict__ merged,
@@ -248,14 +291,23 @@ pr_status levels_and_merge(const DevGraph& g, const int32_t* rep, int32_t* crep,
   PRGB_CUDA(cudaMemsetAsync(merged, 0, (size_t)n, s));
   count_nodes_k<<<grid_w(n), kBlock, 0, s>>>(g.optr, g.oidx, n, rep, nsize, smin, pending, cin_cnt);
   PRGB_LAUNCH();
+  if (g.noheavy > 0) {
+    count_nodes_heavy_k<<<grid_w(g.noheavy), kBlock, 0, s>>>(g.optr, g.oidx, g.oheavy, g.noheavy, rep, pending,
+                                                             cin_cnt);
+    PRGB_LAUNCH();
+  }
   PRGB_TRY(scan_i32(cin_cnt, cin_ptr, n, tmp));
   int32_t m_ext = 0;
   PRGB_CUDA(cudaMemcpyAsync(&m_ext, cin_ptr + n, 4, cudaMemcpyDeviceToHost, s));
   PRGB_CUDA(cudaStreamSynchronize(s));
   PRGB_TRY(tmp.alloc(&cin_src, (size_t)(m_ext > 0 ? m_ext : 1)));
   PRGB_CUDA(cudaMemcpyAsync(cursor, cin_ptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, s));
-  fill_cin_k<<<grid_w(n), kBlock, 0, s>>>(g.optr, g.oidx, n, rep, cursor, cin_src);
+  fill_cin_k<<<grid_t(n), kBlock, 0, s>>>(g.optr, g.oidx, n, nullptr, rep, cursor, cin_src);
   PRGB_LAUNCH();
+  if (g.noheavy > 0) {
+    fill_cin_k<<<grid_w(g.noheavy), kBlock, 0, s>>>(g.optr, g.oidx, g.noheavy, g.oheavy, rep, cursor, cin_src);
+    PRGB_LAUNCH();
+  }
   // frontier capacity: every node is queued once, in ceil(len/kChunk) items
   const int cap = (int)((int64_t)n + (int64_t)m_ext / kChunk + 1);
   int *fa_node, *fa_chunk, *fb_node, *fb_chunk;
