@@ -367,7 +367,7 @@ pr_status pr_global_power(const pr_graph* g, double c, const double* u, double t
   if (stats) {
     stats->iters_max = iters;
     stats->n_levels = 1;
-    stats->launches = 1;
+    stats->launches = 2;  // c / outdeg, then the series
     stats->edge_visits = (int64_t)iters * g->g.m;
     if (stats->comp_iters) stats->comp_iters[0] = iters;
     if (timing) {

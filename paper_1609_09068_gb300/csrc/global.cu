@@ -1,6 +1,8 @@
 // global.cu -- the baseline method (Sec. 4.3.2: the same power series on the
 // whole graph; Sec. 5.2 method 1) and the residual of the defining system
 // (I - cA^T) R = u (Def. 3.5).
+#include <algorithm>
+
 #include "common.cuh"
 #include "global.cuh"
 #include "spmv.cuh"
@@ -22,7 +24,7 @@ __global__ void __launch_bounds__(kBlock) global_power_k(GlobalArgs a) {
     const double uu = a.u[i];
     if (!(uu >= 0.0) || !isfinite(uu)) set_err(a.ctl, PR_EINVAL, 400);
     a.R[i] = uu;
-    a.zA[i] = uu * a.inv[i];
+    a.zA[i] = uu * a.civ[i];
   }
   if (!grid_sync(a.ctl, 401)) return;
   const bool l1 = a.norm == PR_NORM_L1;
@@ -32,10 +34,12 @@ __global__ void __launch_bounds__(kBlock) global_power_k(GlobalArgs a) {
     const double* cur = (k & 1) ? a.zB : a.zA;
     double* nxt = (k & 1) ? a.zA : a.zB;
     double local = 0.0;
+    // z holds c P / outdeg (civ = c / outdeg): the in-edge sum is the next
+    // term itself
     auto fin = [&](int row, double acc, bool heavy) -> double {
-      const double pn = a.c * acc;
+      const double pn = acc;
       a.R[row] += pn;
-      nxt[row] = pn * a.inv[row];
+      nxt[row] = pn * a.civ[row];
       if (!heavy) local = fold2(local, pn, l1);
       return pn;
     };
@@ -99,6 +103,11 @@ __global__ void __launch_bounds__(kBlock) sum_parts_k(const double* __restrict__
 
 int residual_grid() { return num_sms() * 4; }
 
+__global__ void civ_k(int32_t n, double c, const double* __restrict__ inv, double* __restrict__ civ) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    civ[i] = c * inv[i];
+}
+
 pr_status run_global(const DevGraph& g, double c, const double* u, double tol, int norm, int max_iter, int fixed,
                      double* R, int* iters, Arena& tmp, Ctl* ctl, float* kernel_ms) {
   cudaStream_t s = tmp.stream();
@@ -130,6 +139,12 @@ pr_status run_global(const DevGraph& g, double c, const double* u, double tol, i
   a.hv.hbase = 0;
   a.lorder = g.lorder;
   a.inv = g.inv;
+  double* civ = nullptr;
+  PRGB_TRY(tmp.alloc(&civ, g.n));
+  civ_k<<<(unsigned)std::min<int64_t>(((int64_t)g.n + kBlock - 1) / kBlock, (int64_t)num_sms() * 16), kBlock, 0, s>>>(
+      g.n, c, g.inv, civ);
+  PRGB_LAUNCH();
+  a.civ = civ;
   PRGB_TRY(alloc_heavy_scratch(&a.hs, g.nheavy, g.nchunks, tmp));
   PRGB_TRY(reset_ctl(ctl, s));
   void* args[] = {&a};

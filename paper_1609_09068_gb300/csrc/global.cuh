@@ -13,6 +13,7 @@ struct GlobalArgs {
   const int32_t* outdeg;
   const int32_t* lorder;
   const double* inv;
+  const double* civ;  // c / outdeg
   const double* u;
   double c, tol;
   int norm, max_iter, fixed;

@@ -69,6 +69,19 @@ __device__ __forceinline__ bool keep_going32(float s, double tau, int norm) {
 constexpr float kMixKappa = 8.0f * 5.9604645e-8f;  // 8 * 2^-24
 constexpr int kMixRounds = 6;
 
+// |x| as a float, from the bit pattern of the double: the sign dropped, the
+// exponent rebiased from 1023 to 127 and the mantissa cut to 23 bits
+// (rounding toward zero, relative error below 2^-23); magnitudes under the
+// float range give 0, over it the largest float.  Integer operations only,
+// so the stopping norm costs nothing on the FP64 pipe.
+__device__ __forceinline__ float abs_to_float(double x) {
+  const long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+  const long long f = (b >> 29) - ((long long)(1023 - 127) << 23);
+  if (f <= 0) return 0.0f;
+  if (f >= 0x7f800000LL) return 3.4028235e38f;
+  return __int_as_float((int)f);
+}
+
 // A local index outside [0, sz) would mean a broken layout: record it and
 // read slot 0 instead of touching memory out of bounds.
 __device__ __forceinline__ int local_or_err(const SolveArgs& a, int q, int sz) {
@@ -203,21 +216,23 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const int fixed = a.replay ? a.replay[c] : -1;
+    // z holds c P / outdeg, so that the in-edge sum is the next term itself
+    const double civ = a.c * inv;
     if (a.R0) {
       // warm start: R = R0 + r, the series continues from the residual
       // r = W + c A^T(R0/outdeg) - R0 (signed)
       const double r0 = act ? a.R0[p] : 0.0;
-      if (act) z[lane] = r0 * inv;
+      if (act) z[lane] = r0 * civ;
       __syncwarp();
       double acc = 0.0;
       for (int e = ib; e < ie; e++) acc += z[ix[e]];
-      const double r = act ? W + a.c * acc - r0 : 0.0;
+      const double r = act ? W + acc - r0 : 0.0;
       __syncwarp();
       R = r0 + r;
-      if (act) z[lane] = r * inv;
+      if (act) z[lane] = r * civ;
       k = 1;
     } else if (act) {
-      z[lane] = W * inv;
+      z[lane] = W * civ;
     }
     __syncwarp();
     for (;;) {
@@ -229,10 +244,10 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
         acc1 += z[ix[e + 1]];
       }
       if (e < ie) acc0 += z[ix[e]];
-      const double pn = a.c * (acc0 + acc1);
+      const double pn = acc0 + acc1;
       __syncwarp();
       if (act) {
-        z[lane] = pn * inv;
+        z[lane] = pn * civ;
         R += pn;
       }
       __syncwarp();
@@ -241,7 +256,7 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
         if (k >= fixed) break;
         continue;
       }
-      const float pf = fabsf((float)pn);  // terms are signed after a warm start
+      const float pf = abs_to_float(pn);  // terms are signed after a warm start
       const float s = a.norm == PR_NORM_L1 ? group_sumf<32>(pf) : group_maxf<32>(pf);
       if (!keep_going32(s, tau, a.norm)) break;
       if (k >= a.max_iter) {
@@ -401,42 +416,36 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const int fixed = a.replay ? a.replay[c] : -1;
+    // one row per thread; z holds c P / outdeg, so that the in-edge sum is
+    // the next term itself
+    const int i = threadIdx.x;
+    const bool act = i < sz;
+    const double civ = act ? a.c * iv[i] : 0.0;
     if (a.R0) {
       // warm start: R = R0 + r, the series continues from the residual
-      const int i = threadIdx.x;
-      const bool act = i < sz;
       const double r0 = act ? a.R0[off + i] : 0.0;
-      if (act) z[i] = r0 * iv[i];
+      if (act) z[i] = r0 * civ;
       __syncthreads();
-      const double r = act ? Rs[i] + a.c * row_sum(i) - r0 : 0.0;
+      const double r = act ? Rs[i] + row_sum(i) - r0 : 0.0;
       __syncthreads();
       if (act) {
         Rs[i] = r0 + r;
-        z[i] = r * iv[i];
+        z[i] = r * civ;
       }
-      __syncthreads();
       k = 1;
+    } else if (act) {
+      z[i] = Rs[i] * civ;  // Rs holds W
     }
+    __syncthreads();
     for (;;) {
-      double pn[kCtaRows];
-      double local = 0.0;
-#pragma unroll
-      for (int r = 0; r < kCtaRows; r++) {
-        const int i = threadIdx.x + r * kCtaThreads;
-        pn[r] = i < sz ? a.c * row_sum(i) : 0.0;
-      }
+      const double pn = act ? row_sum(i) : 0.0;
       __syncthreads();  // every row has read z before it is overwritten
-#pragma unroll
-      for (int r = 0; r < kCtaRows; r++) {
-        const int i = threadIdx.x + r * kCtaThreads;
-        if (i < sz) {
-          Rs[i] += pn[r];
-          z[i] = pn[r] * iv[i];
-          local = a.norm == PR_NORM_L1 ? local + fabs(pn[r]) : fmax(local, fabs(pn[r]));
-        }
+      if (act) {
+        Rs[i] += pn;
+        z[i] = pn * civ;
       }
       // the reduction ends with __syncthreads, which also publishes z
-      const float s2 = block_sumf((float)local, red, a.norm != PR_NORM_L1);
+      const float s2 = block_sumf(abs_to_float(pn), red, a.norm != PR_NORM_L1);
       k++;
       if (fixed >= 0) {
         if (k >= fixed) break;
@@ -696,28 +705,34 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const int fixed = a.replay ? a.replay[c] : -1;
     const bool is_max = a.norm != PR_NORM_L1;
+    // iv holds c / outdeg during the series (z = c P / outdeg: the in-edge
+    // sum is the next term itself); 1/outdeg is restored for the result
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) iv[i] *= a.c;
     if (a.R0) {
       // warm start: R = R0 + r; the series continues from r (in zB, k = 1)
       for (int i = threadIdx.x; i < nr; i += blockDim.x) zA[i] = a.R0[off + r0 + i] * iv[i];
       cl.sync();
       for (int i = threadIdx.x; i < nr; i += blockDim.x) {
         const double g0 = a.R0[off + r0 + i];
-        const double r = Rs[i] + a.c * row_sum(remA, i) - g0;
+        const double r = Rs[i] + row_sum(remA, i) - g0;
         Rs[i] = g0 + r;
         zB[i] = r * iv[i];
       }
-      cl.sync();
       k = 1;
+    } else {
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) zA[i] = Rs[i] * iv[i];  // Rs holds W
     }
+    cl.sync();
     for (;;) {
       double* const* rem = (k & 1) ? remB : remA;
       double* nxt = (k & 1) ? zA : zB;
       float local = 0.0f;
       for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-        const double pn = a.c * row_sum(rem, i);
+        const double pn = row_sum(rem, i);
         Rs[i] += pn;
         nxt[i] = pn * iv[i];
-        local = is_max ? fmaxf(local, fabsf((float)pn)) : local + fabsf((float)pn);
+        const float pf = abs_to_float(pn);
+        local = is_max ? fmaxf(local, pf) : local + pf;
       }
       const float bs = block_sumf(local, red, is_max);
       if (threadIdx.x == 0) part[k & 1] = bs;
@@ -735,6 +750,7 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
         break;
       }
     }
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) iv[i] = a.p_inv[off + r0 + i];
   }
   for (int i = threadIdx.x; i < nr; i += blockDim.x) {
     a.R[off + r0 + i] = Rs[i];
@@ -835,12 +851,13 @@ __global__ void __launch_bounds__(kBlock) gather_level_k(SolveArgs a, LevelRange
 constexpr int kG = 8;  // lanes per row
 
 // R[p] = W[p] and z0[p - off] = W/outdeg for the rows of a component
-__device__ __forceinline__ void load_rows(const SolveArgs& a, int off, int sz, double* z0) {
+// R[p] = W[p], and z0[p - off] = W * scale[p] when z0 is given
+__device__ __forceinline__ void load_rows(const SolveArgs& a, int off, int sz, double* z0, const double* scale) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
     const int p = off + (int)i;
     const double W = a.W[p];
     a.R[p] = W;
-    if (z0) z0[i] = W * a.p_inv[p];
+    if (z0) z0[i] = W * scale[p];
   }
 }
 
@@ -850,7 +867,9 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
   const int off = L.off, sz = L.size;
   const int nlight = sz - hv.nheavy;
   const int* lorder = a.lorder + off;
-  load_rows(a, off, sz, zA);
+  // z holds c P / outdeg (a.civ = c / outdeg): the in-edge sum is the next
+  // term itself
+  load_rows(a, off, sz, zA, a.civ);
   const bool l1 = a.norm == PR_NORM_L1;
   int k = 0;
   if (a.R0) {
@@ -859,13 +878,13 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
       const int p = off + (int)i;
       a.R[p] = a.R0[p];
-      zA[i] = a.R0[p] * a.p_inv[p];
+      zA[i] = a.R0[p] * a.civ[p];
     }
     if (!grid_sync(a.ctl, 312)) return;
     auto fin = [&](int row, double acc, bool) -> double {
-      const double r = a.W[row] + a.c * acc - a.R[row];
+      const double r = a.W[row] + acc - a.R[row];
       a.R[row] += r;
-      zB[row - off] = r * a.p_inv[row];
+      zB[row - off] = r * a.civ[row];
       return fabs(r);
     };
     auto val = [&](int e) -> double { return zA[local_or_err(a, a.int_idx[e] - off, sz)]; };
@@ -880,9 +899,9 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
     double* nxt = (k & 1) ? zA : zB;
     double local = 0.0;
     auto fin = [&](int row, double acc, bool heavy) -> double {
-      const double pn = a.c * acc;
+      const double pn = acc;
       a.R[row] += pn;
-      nxt[row - off] = pn * a.p_inv[row];
+      nxt[row - off] = pn * a.civ[row];
       if (!heavy) local = fold2(local, fabs(pn), l1);
       return fabs(pn);
     };
@@ -1021,7 +1040,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_mx_k(SolveArgs a, Larg
 }
 
 __global__ void __launch_bounds__(kBlock) solve_large_cac_k(SolveArgs a, LargeComp L) {
-  load_rows(a, L.off, L.size, nullptr);  // R[p] = W
+  load_rows(a, L.off, L.size, nullptr, nullptr);  // R[p] = W
   if (!grid_sync(a.ctl, 320)) return;
   const int lane = threadIdx.x & (kG - 1);
   const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kG;
@@ -1076,6 +1095,11 @@ namespace prgb {
 static unsigned grid_cap(int64_t blocks) {
   int64_t cap = (int64_t)num_sms() * 32;
   return (unsigned)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+}
+
+__global__ void scale_k(int32_t n, double c, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = c * x[i];
 }
 
 __global__ void to_float_k(int32_t n, const double* __restrict__ x, float* __restrict__ y) {
@@ -1139,6 +1163,7 @@ pr_status alloc_solve_bufs(const pr_partition_s* P, bool mixed, Arena& a, SolveB
     PRGB_TRY(a.alloc(&b->zA, P->max_large));
     PRGB_TRY(a.alloc(&b->zB, P->max_large));
     PRGB_TRY(a.alloc(&b->part, (size_t)2 * num_sms() * 8));
+    PRGB_TRY(a.alloc(&b->civ, (size_t)n + 1));
   }
   b->invf = nullptr;
   if (mixed && n > 0) {
@@ -1197,6 +1222,7 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
   a.replay = replay;
   a.xlorder = P->xlorder;
   a.p_invf = b.invf;
+  a.civ = b.civ;
   a.R0 = nullptr;
   a.lu_threshold = 0;
   a.iters64 = iters64;
@@ -1222,6 +1248,12 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
   double* part = b.part;
   HeavyScratch hs = b.hs;
   size_t li_large = 0, ti = 0;
+  if (b.civ && P->g.n > 0) {
+    // c / outdeg for the grid-wide series of this solve's c
+    scale_k<<<grid_cap((P->g.n + kBlock - 1) / kBlock), kBlock, 0, s>>>(P->g.n, a.c, P->p_inv, b.civ);
+    PRGB_LAUNCH();
+    ++*nl;
+  }
   for (size_t li = 0; li < P->levels.size(); li++) {
     const LevelRange& r = P->levels[li];
     {

@@ -30,6 +30,7 @@ struct SolveArgs {
   const int32_t* xlorder;   // [n] positions by (level, external in-degree class)
   const float* p_invf;      // [n] 1/outdeg in FP32 (mixed precision only)
   const double* R0;         // [n] warm-start guess by position for SCC rows, or nullptr
+  const double* civ;        // [n] c / outdeg by position (grid-wide series), or nullptr
   int lu_threshold;         // SCCs with fewer vertices are solved by dense elimination
   int32_t* iters64;         // [K] FP64 residual sweeps per SCC (mixed only)
   double* W;                // [n] inflow-adjusted weights by position
@@ -67,6 +68,7 @@ struct SolveBufs {
   double* zB = nullptr;
   double* part = nullptr;
   float* invf = nullptr;
+  double* civ = nullptr;  // c / outdeg (when there are grid-wide components)
 };
 
 // one captured level loop and the parameters it was captured for
