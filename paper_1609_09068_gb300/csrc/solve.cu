@@ -236,15 +236,17 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
     }
     __syncwarp();
     for (;;) {
-      // two partial sums halve the chain of dependent FP64 adds
-      double acc0 = 0.0, acc1 = 0.0;
+      // four partial sums: shorter chains of dependent loads and FP64 adds
+      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
       int e = ib;
-      for (; e + 1 < ie; e += 2) {
+      for (; e + 3 < ie; e += 4) {
         acc0 += z[ix[e]];
         acc1 += z[ix[e + 1]];
+        acc2 += z[ix[e + 2]];
+        acc3 += z[ix[e + 3]];
       }
-      if (e < ie) acc0 += z[ix[e]];
-      const double pn = acc0 + acc1;
+      for (; e < ie; e++) acc0 += z[ix[e]];
+      const double pn = (acc0 + acc1) + (acc2 + acc3);
       __syncwarp();
       if (act) {
         z[lane] = pn * civ;
@@ -323,14 +325,21 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
   }
   __syncthreads();
   auto row_sum = [&](int i) -> double {
-    double acc = 0.0;
     const int e0 = ip[i], e1 = ip[i + 1];
     if (staged) {
-#pragma unroll 4
-      for (int e = e0; e < e1; e++) acc += z[ix[e]];
-    } else {
-      for (int e = e0; e < e1; e++) acc += z[local_or_err(a, a.int_idx[ib + e] - off, sz)];
+      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+      int e = e0;
+      for (; e + 3 < e1; e += 4) {
+        acc0 += z[ix[e]];
+        acc1 += z[ix[e + 1]];
+        acc2 += z[ix[e + 2]];
+        acc3 += z[ix[e + 3]];
+      }
+      for (; e < e1; e++) acc0 += z[ix[e]];
+      return (acc0 + acc1) + (acc2 + acc3);
     }
+    double acc = 0.0;
+    for (int e = e0; e < e1; e++) acc += z[local_or_err(a, a.int_idx[ib + e] - off, sz)];
     return acc;
   };
   auto row_sumf = [&](int i) -> float {
@@ -584,16 +593,19 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
   auto row_sum = [&](auto const* rem, int i) {
     using T = typename std::remove_pointer<typename std::remove_const<
         typename std::remove_pointer<decltype(rem)>::type>::type>::type;
-    T acc0 = 0, acc1 = 0;
+    // four independent partial sums: four remote loads in flight at once
+    T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
     const int e0 = ip[i], e1 = ip[i + 1];
     int e = e0;
     if (staged) {
-      for (; e + 1 < e1; e += 2) {
-        const int q0 = ix[e], q1 = ix[e + 1];
+      for (; e + 3 < e1; e += 4) {
+        const int q0 = ix[e], q1 = ix[e + 1], q2 = ix[e + 2], q3 = ix[e + 3];
         acc0 += rem[q0 >> sh][q0 & mask];
         acc1 += rem[q1 >> sh][q1 & mask];
+        acc2 += rem[q2 >> sh][q2 & mask];
+        acc3 += rem[q3 >> sh][q3 & mask];
       }
-      if (e < e1) {
+      for (; e < e1; e++) {
         const int q = ix[e];
         acc0 += rem[q >> sh][q & mask];
       }
@@ -603,7 +615,7 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
         acc0 += rem[q >> sh][q & mask];
       }
     }
-    return acc0 + acc1;
+    return (acc0 + acc1) + (acc2 + acc3);
   };
   int k = 0, k64 = 0;
   if (a.c_type[c] != PR_TYPE_SCC) {
