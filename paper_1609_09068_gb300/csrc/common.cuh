@@ -315,6 +315,7 @@ struct DevGraph {
   int32_t* heavy_chrow = nullptr;
   int32_t nheavy = 0, nchunks = 0;
   int32_t* lorder = nullptr;  // [n] rows ordered by in-degree class (heavy last)
+  int32_t* lpre = nullptr;    // [n+1] row-cost prefix over lorder (see build_lpre), or null
   int32_t* oheavy = nullptr;  // vertices with more than kHeavy out-edges (ascending)
   int32_t noheavy = 0;
   double* inv = nullptr;      // [n] 1/outdeg, 0 for dangling vertices
@@ -324,6 +325,12 @@ struct DevGraph {
 // (group may be null).  Used to give the 32 rows of a warp similar lengths.
 pr_status build_lorder(const int32_t* ptr, int32_t nrows, const int32_t* group, int32_t group_max, Arena& keep,
                        Arena& tmp, int32_t** lorder);
+// Prefix of the row costs (in-degree + kRowCost) in lorder order:
+// lpre[i] = cost of rows lorder[0..i).  Used to give each warp of a sweep
+// an equal share of edges.  Left null when it would not fit in int32.
+constexpr int kRowCost = 8;
+pr_status build_lpre(const int32_t* ptr, const int32_t* lorder, int32_t n, int64_t m, Arena& keep, Arena& tmp,
+                     int32_t** lpre);
 // inv[i] = 1/deg[i] (0 where deg is 0)
 pr_status build_inv(const int32_t* deg, int32_t n, Arena& keep, double** inv, cudaStream_t s);
 
@@ -417,6 +424,7 @@ struct pr_partition_s {
   int32_t* heavy_choff = nullptr;
   int32_t* heavy_chrow = nullptr;
   int32_t* lorder = nullptr;       // [n] positions by (component, internal in-degree class)
+  int32_t* lpre = nullptr;         // [n+1] row-cost prefix over lorder (internal in-degrees), or null
   double* p_inv = nullptr;         // [n] 1/outdeg by position
   int32_t* p_comp = nullptr;       // [n] component of each position
   int32_t* xheavy_rows = nullptr;  // positions with > kHeavy external in-edges

@@ -29,6 +29,8 @@ __global__ void __launch_bounds__(kBlock) global_power_k(GlobalArgs a) {
   if (!grid_sync(a.ctl, 401)) return;
   const bool l1 = a.norm == PR_NORM_L1;
   const int nlight = n - a.hv.nheavy;
+  int lr0 = -1, lr1 = -1;  // this warp's light rows, balanced by cost
+  if (a.lpre) warp_row_range(a.lpre, nlight, &lr0, &lr1);
   int k = 0;
   for (;;) {
     const double* cur = (k & 1) ? a.zB : a.zA;
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(kBlock) global_power_k(GlobalArgs a) {
       return pn;
     };
     auto val = [&](int e) -> double { return cur[a.iidx[e]]; };
-    balanced_sweep(a.iptr, a.lorder, nlight, a.hv, a.hs, k & 1, l1, fin, val);
+    balanced_sweep(a.iptr, a.lorder, nlight, a.hv, a.hs, k & 1, l1, fin, val, lr0, lr1);
     const double bs = l1 ? block_sum(local, red) : block_max(local, red);
     double* slot = a.part + (size_t)(k & 1) * gridDim.x;
     if (threadIdx.x == 0) slot[blockIdx.x] = bs;
@@ -138,6 +140,7 @@ pr_status run_global(const DevGraph& g, double c, const double* u, double tol, i
   a.hv.cbase = 0;
   a.hv.hbase = 0;
   a.lorder = g.lorder;
+  a.lpre = g.lpre;
   a.inv = g.inv;
   double* civ = nullptr;
   PRGB_TRY(tmp.alloc(&civ, g.n));

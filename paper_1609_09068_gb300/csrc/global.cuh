@@ -12,6 +12,7 @@ struct GlobalArgs {
   const int32_t* iidx;
   const int32_t* outdeg;
   const int32_t* lorder;
+  const int32_t* lpre;  // row-cost prefix over lorder, or nullptr
   const double* inv;
   const double* civ;  // c / outdeg
   const double* u;

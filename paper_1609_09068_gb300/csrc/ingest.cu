@@ -127,6 +127,7 @@ pr_status ingest(const pr_csr* csr, DevGraph* g, Arena& keep, Arena& tmp, Ctl* c
   PRGB_TRY(build_heavy(g->iptr, n, keep, tmp, &g->heavy_rows, &g->heavy_choff, &g->heavy_chrow, &g->nheavy,
                         &g->nchunks));
   PRGB_TRY(build_lorder(g->iptr, n, nullptr, 0, keep, tmp, &g->lorder));
+  PRGB_TRY(build_lpre(g->iptr, g->lorder, n, g->m, keep, tmp, &g->lpre));
   {
     // vertices with many out-edges: the partitioner gives them a warp each
     int32_t *choff = nullptr, *chrow = nullptr, nch = 0;

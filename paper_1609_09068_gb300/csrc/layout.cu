@@ -439,6 +439,7 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
                           &P->nchunks));
     int32_t* pc = P->p_comp;
     PRGB_TRY(build_lorder(P->int_ptr, n, pc, K - 1, keep, tmp, &P->lorder));
+    PRGB_TRY(build_lpre(P->int_ptr, P->lorder, n, P->m_int, keep, tmp, &P->lpre));
     std::vector<int32_t> hrows(P->nheavy), hcho(P->nheavy + 1);
     if (P->nheavy > 0) {
       PRGB_CUDA(cudaMemcpyAsync(hrows.data(), P->heavy_rows, (size_t)P->nheavy * 4, cudaMemcpyDeviceToHost, s));

@@ -362,6 +362,27 @@ pr_status build_lorder(const int32_t* ptr, int32_t nrows, const int32_t* group, 
   return radix_sort_pairs(k, reinterpret_cast<uint32_t*>(*lorder), kt, vt, nrows, gbits + 4, tmp);
 }
 
+__global__ void row_cost_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ lorder, int32_t n,
+                           int32_t* __restrict__ cost) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = lorder[i];
+    cost[i] = ptr[r + 1] - ptr[r] + kRowCost;
+  }
+}
+
+pr_status build_lpre(const int32_t* ptr, const int32_t* lorder, int32_t n, int64_t m, Arena& keep, Arena& tmp,
+                     int32_t** lpre) {
+  *lpre = nullptr;
+  if (n == 0 || m + (int64_t)kRowCost * n >= ((int64_t)1 << 31)) return PR_OK;  // ranges off: prefix too large
+  cudaStream_t s = tmp.stream();
+  int32_t* cost;
+  PRGB_TRY(tmp.alloc(&cost, (size_t)n + 1));
+  PRGB_TRY(keep.alloc(lpre, (size_t)n + 1));
+  row_cost_k<<<grid_for(n), kBlock, 0, s>>>(ptr, lorder, n, cost);
+  PRGB_LAUNCH();
+  return scan_i32(cost, *lpre, n, tmp);
+}
+
 __global__ void inv_deg_k(const int32_t* __restrict__ deg, int32_t n, double* inv) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     inv[i] = deg[i] > 0 ? 1.0 / (double)deg[i] : 0.0;

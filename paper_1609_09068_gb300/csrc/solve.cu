@@ -879,6 +879,8 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
   const int off = L.off, sz = L.size;
   const int nlight = sz - hv.nheavy;
   const int* lorder = a.lorder + off;
+  int lr0 = -1, lr1 = -1;  // this warp's light rows, balanced by cost
+  if (a.lpre) warp_row_range(a.lpre + off, nlight, &lr0, &lr1);
   // z holds c P / outdeg (a.civ = c / outdeg): the in-edge sum is the next
   // term itself
   load_rows(a, off, sz, zA, a.civ);
@@ -900,7 +902,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
       return fabs(r);
     };
     auto val = [&](int e) -> double { return zA[local_or_err(a, a.int_idx[e] - off, sz)]; };
-    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, 0, l1, fin, val);
+    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, 0, l1, fin, val, lr0, lr1);
     k = 1;
   }
   if (!grid_sync(a.ctl, 310)) return;
@@ -918,7 +920,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
       return fabs(pn);
     };
     auto val = [&](int e) -> double { return cur[local_or_err(a, a.int_idx[e] - off, sz)]; };
-    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, k & 1, l1, fin, val);
+    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, k & 1, l1, fin, val, lr0, lr1);
     const double bs = l1 ? block_sum(local, red) : block_max(local, red);
     double* slot = part + (size_t)(k & 1) * gridDim.x;
     if (threadIdx.x == 0) slot[blockIdx.x] = bs;
@@ -965,6 +967,8 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_mx_k(SolveArgs a, Larg
   const int* lorder = a.lorder + off;
   const double tau = a.tol * (double)sz / (double)a.n;
   const float cf = (float)a.c;
+  int lr0 = -1, lr1 = -1;  // this warp's light rows, balanced by cost
+  if (a.lpre) warp_row_range(a.lpre + off, nlight, &lr0, &lr1);
   float* const zf0 = fz;
   float* const zf1 = fz + sz;
   double wl = 0.0;
@@ -996,7 +1000,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_mx_k(SolveArgs a, Larg
         return (double)fabsf(pn);
       };
       auto val = [&](int e) -> float { return cur[local_or_err(a, a.int_idx[e] - off, sz)]; };
-      balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, slot & 1, true, fin, val);
+      balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, slot & 1, true, fin, val, lr0, lr1);
       double s = grid_fold(a, part, slot & 1, local, red, 331);
       if (s < 0.0) return;
       if (hv.nheavy > 0) s += __ldcg(&hs.total[slot & 1]);
@@ -1031,7 +1035,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_mx_k(SolveArgs a, Larg
       return fabs(r);
     };
     auto val = [&](int e) -> double { return a.zr[a.int_idx[e]]; };
-    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, slot & 1, true, fin, val);
+    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, slot & 1, true, fin, val, lr0, lr1);
     double rho = grid_fold(a, part, slot & 1, local, red, 333);
     if (rho < 0.0) return;
     if (hv.nheavy > 0) rho += __ldcg(&hs.total[slot & 1]);
@@ -1223,6 +1227,7 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
   a.p_outdeg = P->p_outdeg;
   a.p_inv = P->p_inv;
   a.lorder = P->lorder;
+  a.lpre = P->lpre;
   a.int_ptr = P->int_ptr;
   a.int_idx = P->int_idx;
   a.ext_ptr = P->ext_ptr;

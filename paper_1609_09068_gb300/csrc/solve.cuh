@@ -18,6 +18,7 @@ struct SolveArgs {
   const int32_t* p_outdeg;  // [n] loop-free out-degree by position
   const double* p_inv;      // [n] 1/outdeg by position (0 for dangling)
   const int32_t* lorder;    // [n] positions by (component, in-degree class)
+  const int32_t* lpre;      // [n+1] row-cost prefix over lorder, or nullptr
   const int32_t* int_ptr;
   const int32_t* int_idx;
   const int32_t* ext_ptr;

@@ -85,10 +85,31 @@ __device__ __forceinline__ double fold2(double a, double b, bool l1) { return l1
 // The edge sums are accumulated in the type val returns (double, or float
 // for the FP32 sweeps of the mixed-precision solve); chunk partials and the
 // heavy-row folds are kept in FP64.
+// The warp's share of the light rows when the sweep is balanced by cost:
+// rows [*r0, *r1) of lorder[0, nlight), whose costs (lpre, a prefix over the
+// same rows, lpre[0] its base) add up to about 1/(number of warps) of the
+// total.  Binary searches, once per launch.
+__device__ __forceinline__ void warp_row_range(const int32_t* __restrict__ lpre, int nlight, int* r0, int* r1) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t base = lpre[0], total = (int64_t)lpre[nlight] - base;
+  auto lower = [&](int64_t t) {
+    int lo = 0, hi = nlight;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((int64_t)lpre[mid] - base < t) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo;
+  };
+  *r0 = lower(total * gw / nw);
+  *r1 = lower(total * (gw + 1) / nw);
+}
+
 template <class Fin, class Val>
 __device__ __forceinline__ void balanced_sweep(const int32_t* __restrict__ ptr, const int32_t* __restrict__ lorder,
                                                int nlight, const HeavyRows& hv, const HeavyScratch& hs, int parity,
-                                               bool l1, Fin fin, Val val) {
+                                               bool l1, Fin fin, Val val, int r0 = -1, int r1 = -1) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -158,10 +179,13 @@ __device__ __forceinline__ void balanced_sweep(const int32_t* __restrict__ ptr, 
       hs.total[parity] = ts;
     }
   }
-  // light rows: one per thread
-  for (int64_t base = gw * 32; base < nlight; base += nw * 32) {
+  // light rows: one per thread; with a range, the warp's contiguous share
+  // (rows of similar length, by their class order), else strided groups
+  const bool ranged = r0 >= 0;
+  const int64_t lb = ranged ? r0 : gw * 32, le = ranged ? r1 : nlight, ls = ranged ? 32 : nw * 32;
+  for (int64_t base = lb; base < le; base += ls) {
     const int64_t i = base + lane;
-    if (i < nlight) {
+    if (i < le) {
       const int row = lorder[i];
       const int b = ptr[row], e = ptr[row + 1];
       T acc = 0;
