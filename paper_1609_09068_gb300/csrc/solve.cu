@@ -509,37 +509,45 @@ struct CluSmem {
   uint16_t* ix;
 };
 
-__host__ __device__ __forceinline__ size_t clu_smem(int chunk, bool mixed) {
-  return (size_t)chunk * 4 * sizeof(double) + 2 * sizeof(double) + ((size_t)chunk + 2) * sizeof(int) +
-         2 * sizeof(float) + (mixed ? (size_t)chunk * 4 * sizeof(float) : 0) +
+// z vectors: with push, every rank holds the whole component's z (kClu *
+// chunk entries) and writes its rows into every rank's copy; without, a rank
+// holds its own slice and reads the others' through the cluster window.
+__host__ __device__ __forceinline__ size_t clu_smem(int chunk, bool mixed, bool push) {
+  const size_t zlen = push ? (size_t)chunk * kClu : (size_t)chunk;
+  return (2 * zlen + 2 * (size_t)chunk + 2) * sizeof(double) + ((size_t)chunk + 2) * sizeof(int) +
+         (2 + (mixed ? 2 * zlen + 2 * (size_t)chunk : 0)) * sizeof(float) +
          (size_t)chunk * kCluEdgesPerRow * sizeof(uint16_t);
 }
 
-__device__ __forceinline__ CluSmem clu_carve(double* base, int chunk, bool mixed) {
+__device__ __forceinline__ CluSmem clu_carve(double* base, int chunk, bool mixed, bool push) {
+  const int zlen = push ? chunk * kClu : chunk;
   CluSmem m;
   m.zA = base;
-  m.zB = base + chunk;
-  m.Rs = base + 2 * chunk;
-  m.iv = base + 3 * chunk;
-  m.dpart = base + 4 * chunk;
-  m.ip = reinterpret_cast<int*>(base + 4 * chunk + 2);
+  m.zB = base + zlen;
+  m.Rs = base + 2 * zlen;
+  m.iv = m.Rs + chunk;
+  m.dpart = m.iv + chunk;
+  m.ip = reinterpret_cast<int*>(m.dpart + 2);
   m.part = reinterpret_cast<float*>(m.ip + chunk + 2);
   float* f = m.part + 2;
   m.fA = mixed ? f : nullptr;
-  m.fB = mixed ? f + chunk : nullptr;
-  m.F = mixed ? f + 2 * chunk : nullptr;
-  m.ivf = mixed ? f + 3 * chunk : nullptr;
-  m.ix = reinterpret_cast<uint16_t*>(f + (mixed ? 4 * chunk : 0));
+  m.fB = mixed ? f + zlen : nullptr;
+  m.F = mixed ? f + 2 * zlen : nullptr;
+  m.ivf = mixed ? f + 2 * zlen + chunk : nullptr;
+  m.ix = reinterpret_cast<uint16_t*>(f + (mixed ? 2 * zlen + 2 * chunk : 0));
   return m;
 }
 
-template <bool kMixed>
+// largest component (vertices) a cluster solves in push mode
+constexpr int kCluPushMax = 4096;
+
+template <bool kMixed, bool kPush>
 __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     solve_clu_k(SolveArgs a, int32_t cbeg, int32_t chunk_max) {
   extern __shared__ double cs[];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const CluSmem sm = clu_carve(cs, chunk_max, kMixed);
+  const CluSmem sm = clu_carve(cs, chunk_max, kMixed, kPush);
   double* zA = sm.zA;
   double* zB = sm.zB;
   double* Rs = sm.Rs;
@@ -562,15 +570,32 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
   const int r0 = rank * chunk;
   const int nr = max(0, min(sz, r0 + chunk) - r0);
   if (threadIdx.x < kClu) {
-    remA[threadIdx.x] = cl.map_shared_rank(zA, (int)threadIdx.x);
-    remB[threadIdx.x] = cl.map_shared_rank(zB, (int)threadIdx.x);
-    remP[threadIdx.x] = cl.map_shared_rank(part, (int)threadIdx.x);
-    remD[threadIdx.x] = cl.map_shared_rank(sm.dpart, (int)threadIdx.x);
+    // this rank's own buffers by their plain shared-memory address
+    const int t = (int)threadIdx.x;
+    const bool own = t == rank;
+    remA[t] = own ? zA : cl.map_shared_rank(zA, t);
+    remB[t] = own ? zB : cl.map_shared_rank(zB, t);
+    remP[t] = own ? part : cl.map_shared_rank(part, t);
+    remD[t] = own ? sm.dpart : cl.map_shared_rank(sm.dpart, t);
     if (kMixed) {
-      remFA[threadIdx.x] = cl.map_shared_rank(sm.fA, (int)threadIdx.x);
-      remFB[threadIdx.x] = cl.map_shared_rank(sm.fB, (int)threadIdx.x);
+      remFA[t] = own ? sm.fA : cl.map_shared_rank(sm.fA, t);
+      remFB[t] = own ? sm.fB : cl.map_shared_rank(sm.fB, t);
     }
   }
+  __syncthreads();
+  // with push the staging below already writes other ranks' shared memory:
+  // every block of the cluster must be running first
+  if (kPush) cl.sync();
+  // z of this rank's row i into buffer X: every rank's copy (push) or the
+  // own slice (pull)
+  auto zput = [&](auto* const* remX, int i, auto v) {
+    if (kPush) {
+#pragma unroll
+      for (int rk = 0; rk < kClu; rk++) remX[rk][r0 + i] = v;
+    } else {
+      remX[rank][i] = v;
+    }
+  };
   // stage this rank's rows: local edge offsets and component-local indices
   const int ib = a.int_ptr[off + r0];
   const int m = nr > 0 ? a.int_ptr[off + r0 + nr] - ib : 0;
@@ -585,35 +610,34 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     const double W = a.W[p];
     iv[i] = inv;
     Rs[i] = W;
-    zA[i] = W * inv;
+    zput(remA, i, W * inv);
   }
   cl.sync();
   const int mask = chunk - 1;
-  // sum of z over row i's in-edges, z read from every rank's slice
+  // z of component-local vertex q: from this rank's full copy (push) or
+  // from the owner rank's slice (pull)
+  auto zat = [&](auto const* rem, int q) {
+    if (kPush) return rem[rank][q];
+    return rem[q >> sh][q & mask];
+  };
+  // sum of z over row i's in-edges
   auto row_sum = [&](auto const* rem, int i) {
     using T = typename std::remove_pointer<typename std::remove_const<
         typename std::remove_pointer<decltype(rem)>::type>::type>::type;
-    // four independent partial sums: four remote loads in flight at once
+    // four independent partial sums: four loads in flight at once
     T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
     const int e0 = ip[i], e1 = ip[i + 1];
     int e = e0;
     if (staged) {
       for (; e + 3 < e1; e += 4) {
-        const int q0 = ix[e], q1 = ix[e + 1], q2 = ix[e + 2], q3 = ix[e + 3];
-        acc0 += rem[q0 >> sh][q0 & mask];
-        acc1 += rem[q1 >> sh][q1 & mask];
-        acc2 += rem[q2 >> sh][q2 & mask];
-        acc3 += rem[q3 >> sh][q3 & mask];
+        acc0 += zat(rem, ix[e]);
+        acc1 += zat(rem, ix[e + 1]);
+        acc2 += zat(rem, ix[e + 2]);
+        acc3 += zat(rem, ix[e + 3]);
       }
-      for (; e < e1; e++) {
-        const int q = ix[e];
-        acc0 += rem[q >> sh][q & mask];
-      }
+      for (; e < e1; e++) acc0 += zat(rem, ix[e]);
     } else {
-      for (; e < e1; e++) {
-        const int q = local_or_err(a, a.int_idx[ib + e] - off, sz);
-        acc0 += rem[q >> sh][q & mask];
-      }
+      for (; e < e1; e++) acc0 += zat(rem, local_or_err(a, a.int_idx[ib + e] - off, sz));
     }
     return (acc0 + acc1) + (acc2 + acc3);
   };
@@ -626,7 +650,7 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
       for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const double Rv = Rs[i] + a.c * row_sum(remA, i);
         Rs[i] = Rv;
-        zA[i] = Rv * iv[i];
+        zput(remA, i, Rv * iv[i]);
       }
       cl.sync();
     }
@@ -642,7 +666,7 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     for (int i = threadIdx.x; i < nr; i += blockDim.x) {
       const double W = Rs[i];
       F[i] = warm ? 0.0f : (float)W;
-      sm.fA[i] = (float)(W * iv[i]);
+      zput(remFA, i, (float)(W * iv[i]));
       ivf[i] = (float)iv[i];
       Rs[i] = warm ? a.R0[off + r0 + i] : 0.0;
       wl += W;
@@ -659,12 +683,12 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
       bool stop = false;
       for (; !skip;) {
         float* const* rem = zc ? remFB : remFA;
-        float* nxt = zc ? sm.fA : sm.fB;
+        float* const* nxt = zc ? remFA : remFB;
         float local = 0.0f;
         for (int i = threadIdx.x; i < nr; i += blockDim.x) {
           const float pn = cf * row_sum(rem, i);
           F[i] += pn;
-          nxt[i] = pn * ivf[i];
+          zput(nxt, i, pn * ivf[i]);
           local += fabsf(pn);
         }
         const float bs = block_sumf(local, red, false);
@@ -685,17 +709,17 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
       for (int i = threadIdx.x; i < nr; i += blockDim.x) {
         const double R = Rs[i] + (double)F[i];
         Rs[i] = R;
-        zA[i] = R * iv[i];
+        zput(remA, i, R * iv[i]);
       }
       if (stop) break;
       cl.sync();  // publishes zA
       // FP64 residual; r becomes the start of the next correction pass
-      float* cur = zc ? sm.fB : sm.fA;
+      float* const* cur = zc ? remFB : remFA;
       double rl = 0.0;
       for (int i = threadIdx.x; i < nr; i += blockDim.x) {
         const double r = a.W[off + r0 + i] + a.c * row_sum(remA, i) - Rs[i];
         F[i] = (float)r;
-        cur[i] = (float)(r * iv[i]);
+        zput(cur, i, (float)(r * iv[i]));
         rl += fabs(r);
       }
       const double rb = block_sum(rl, red64);
@@ -722,27 +746,27 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     for (int i = threadIdx.x; i < nr; i += blockDim.x) iv[i] *= a.c;
     if (a.R0) {
       // warm start: R = R0 + r; the series continues from r (in zB, k = 1)
-      for (int i = threadIdx.x; i < nr; i += blockDim.x) zA[i] = a.R0[off + r0 + i] * iv[i];
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) zput(remA, i, a.R0[off + r0 + i] * iv[i]);
       cl.sync();
       for (int i = threadIdx.x; i < nr; i += blockDim.x) {
         const double g0 = a.R0[off + r0 + i];
         const double r = Rs[i] + row_sum(remA, i) - g0;
         Rs[i] = g0 + r;
-        zB[i] = r * iv[i];
+        zput(remB, i, r * iv[i]);
       }
       k = 1;
     } else {
-      for (int i = threadIdx.x; i < nr; i += blockDim.x) zA[i] = Rs[i] * iv[i];  // Rs holds W
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) zput(remA, i, Rs[i] * iv[i]);  // Rs holds W
     }
     cl.sync();
     for (;;) {
       double* const* rem = (k & 1) ? remB : remA;
-      double* nxt = (k & 1) ? zA : zB;
+      double* const* nxt = (k & 1) ? remA : remB;
       float local = 0.0f;
       for (int i = threadIdx.x; i < nr; i += blockDim.x) {
         const double pn = row_sum(rem, i);
         Rs[i] += pn;
-        nxt[i] = pn * iv[i];
+        zput(nxt, i, pn * iv[i]);
         const float pf = abs_to_float(pn);
         local = is_max ? fmaxf(local, pf) : local + pf;
       }
@@ -1195,7 +1219,7 @@ pr_status alloc_solve_bufs(const pr_partition_s* P, bool mixed, Arena& a, SolveB
 // largest cluster-class component (raised, never lowered)
 pr_status set_solve_attrs(const pr_partition_s* P, bool mixed) {
   static bool cta_attr = false;
-  static size_t clu_attr[2] = {48 * 1024, 48 * 1024};
+  static size_t clu_attr[4] = {48 * 1024, 48 * 1024, 48 * 1024, 48 * 1024};
   if (!cta_attr) {
     PRGB_CUDA(cudaFuncSetAttribute(solve_lu_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmem));
     PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
@@ -1203,13 +1227,23 @@ pr_status set_solve_attrs(const pr_partition_s* P, bool mixed) {
                                    (int)kCtaSmemMixed));
     cta_attr = true;
   }
-  int clu_max = 0;
-  for (const LevelRange& r : P->levels) clu_max = std::max(clu_max, r.cta > r.clu ? r.clu_max : 0);
-  const size_t smem = clu_smem(1 << clu_shift(clu_max), mixed);
-  if (clu_max > 0 && smem > clu_attr[mixed]) {
-    PRGB_CUDA(cudaFuncSetAttribute(mixed ? solve_clu_k<true> : solve_clu_k<false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    clu_attr[mixed] = smem;
+  // the largest cluster-class component of any level, with and without push
+  int clu_max = 0, push_max = 0;
+  for (const LevelRange& r : P->levels) {
+    const int m = r.cta > r.clu ? r.clu_max : 0;
+    clu_max = std::max(clu_max, m);
+    if (m <= kCluPushMax) push_max = std::max(push_max, m);
+  }
+  for (int push = 0; push < 2; push++) {
+    const int m = push ? push_max : clu_max;
+    const size_t smem = clu_smem(1 << clu_shift(m), mixed, push != 0);
+    const int slot = (mixed ? 2 : 0) + push;
+    if (m > 0 && smem > clu_attr[slot]) {
+      const void* f = mixed ? (push ? (const void*)solve_clu_k<true, true> : (const void*)solve_clu_k<true, false>)
+                            : (push ? (const void*)solve_clu_k<false, true> : (const void*)solve_clu_k<false, false>);
+      PRGB_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      clu_attr[slot] = smem;
+    }
   }
   return PR_OK;
 }
@@ -1328,11 +1362,13 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       PRGB_CUDA(cudaStreamWaitEvent(side.st[0], side.fork, 0));
       joined[0] = true;
       const int chunk = 1 << clu_shift(r.clu_max);
-      const size_t smem = clu_smem(chunk, mixed);
-      if (mixed)
-        solve_clu_k<true><<<(r.cta - r.clu) * kClu, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
-      else
-        solve_clu_k<false><<<(r.cta - r.clu) * kClu, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
+      const bool push = r.clu_max <= kCluPushMax;
+      const size_t smem = clu_smem(chunk, mixed, push);
+      const unsigned nb = (unsigned)(r.cta - r.clu) * kClu;
+      if (mixed && push) solve_clu_k<true, true><<<nb, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
+      else if (mixed) solve_clu_k<true, false><<<nb, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
+      else if (push) solve_clu_k<false, true><<<nb, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
+      else solve_clu_k<false, false><<<nb, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
       PRGB_LAUNCH();
       ++*nl;
     }
