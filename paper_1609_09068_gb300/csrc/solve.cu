@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t 
 constexpr int kCtaThreads = 256;
 constexpr int kCtaEdgeCap = 8192;
 constexpr int kCtaRows = kCtaCompMax / kCtaThreads;
-constexpr size_t kCtaSmem = (size_t)kCtaCompMax * (3 * sizeof(double) + sizeof(int)) + sizeof(int) +
+constexpr size_t kCtaSmem = (size_t)kCtaCompMax * (4 * sizeof(double) + sizeof(int)) + sizeof(int) +
                             (size_t)kCtaEdgeCap * sizeof(uint16_t);
 constexpr size_t kCtaSmemMixed = kCtaSmem + (size_t)kCtaCompMax * sizeof(float);
 static_assert(kCtaRows == 1, "the mixed-precision CTA series keeps one row per thread");
@@ -299,11 +299,13 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
   double* Rs = sm;
   double* z = sm + kCtaCompMax;
   double* iv = sm + 2 * kCtaCompMax;
-  int* ip = reinterpret_cast<int*>(sm + 3 * kCtaCompMax);  // [sz+1] local edge offsets
+  double* z1 = sm + 3 * kCtaCompMax;  // second z buffer of the FP64 series
+  int* ip = reinterpret_cast<int*>(sm + 4 * kCtaCompMax);  // [sz+1] local edge offsets
   uint16_t* ix = reinterpret_cast<uint16_t*>(ip + kCtaCompMax + 1);
   float* zf = reinterpret_cast<float*>(ix + kCtaEdgeCap);  // [kCtaCompMax], mixed precision only
   __shared__ float red[kCtaThreads / 32];
   __shared__ double red64[kCtaThreads / 32];
+  __shared__ float red2[2][kCtaThreads / 32];  // warp partials of the norm, by sweep parity
   const int c = cbeg + (int)blockIdx.x;
   const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
   const int ib = a.int_ptr[off];
@@ -324,24 +326,25 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
     z[i] = W * inv;
   }
   __syncthreads();
-  auto row_sum = [&](int i) -> double {
+  auto row_sum_of = [&](const double* zb, int i) -> double {
     const int e0 = ip[i], e1 = ip[i + 1];
     if (staged) {
       double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
       int e = e0;
       for (; e + 3 < e1; e += 4) {
-        acc0 += z[ix[e]];
-        acc1 += z[ix[e + 1]];
-        acc2 += z[ix[e + 2]];
-        acc3 += z[ix[e + 3]];
+        acc0 += zb[ix[e]];
+        acc1 += zb[ix[e + 1]];
+        acc2 += zb[ix[e + 2]];
+        acc3 += zb[ix[e + 3]];
       }
-      for (; e < e1; e++) acc0 += z[ix[e]];
+      for (; e < e1; e++) acc0 += zb[ix[e]];
       return (acc0 + acc1) + (acc2 + acc3);
     }
     double acc = 0.0;
-    for (int e = e0; e < e1; e++) acc += z[local_or_err(a, a.int_idx[ib + e] - off, sz)];
+    for (int e = e0; e < e1; e++) acc += zb[local_or_err(a, a.int_idx[ib + e] - off, sz)];
     return acc;
   };
+  auto row_sum = [&](int i) -> double { return row_sum_of(z, i); };
   auto row_sumf = [&](int i) -> float {
     float acc = 0.0f;
     const int e0 = ip[i], e1 = ip[i + 1];
@@ -446,15 +449,27 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
       z[i] = Rs[i] * civ;  // Rs holds W
     }
     __syncthreads();
+    // z double-buffered and the norm from warp partials: one barrier a sweep
+    const bool is_max = a.norm != PR_NORM_L1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double* zc = z;
+    double* zn = z1;
     for (;;) {
-      const double pn = act ? row_sum(i) : 0.0;
-      __syncthreads();  // every row has read z before it is overwritten
+      const double pn = act ? row_sum_of(zc, i) : 0.0;
       if (act) {
         Rs[i] += pn;
-        z[i] = pn * civ;
+        zn[i] = pn * civ;
       }
-      // the reduction ends with __syncthreads, which also publishes z
-      const float s2 = block_sumf(abs_to_float(pn), red, a.norm != PR_NORM_L1);
+      float pf = abs_to_float(pn);
+      pf = is_max ? group_maxf<32>(pf) : group_sumf<32>(pf);
+      if (lane == 0) red2[k & 1][wib] = pf;
+      __syncthreads();  // publishes zn and the partials
+      float s2 = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kCtaThreads / 32; w++) s2 = is_max ? fmaxf(s2, red2[k & 1][w]) : s2 + red2[k & 1][w];
+      double* t = zc;
+      zc = zn;
+      zn = t;
       k++;
       if (fixed >= 0) {
         if (k >= fixed) break;
@@ -559,10 +574,14 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
   __shared__ double red64[kCluThreads / 32];
   __shared__ double* remA[kClu];
   __shared__ double* remB[kClu];
-  __shared__ float* remP[kClu];
   __shared__ double* remD[kClu];
   __shared__ float* remFA[kClu];
   __shared__ float* remFB[kClu];
+  // every warp's norm partial of a sweep, gathered in every rank: slot
+  // (parity, rank * 8 + warp)
+  constexpr int kCluWarps = kCluThreads / 32;
+  __shared__ float pw[2 * kClu * kCluWarps];
+  __shared__ float* remPW[kClu];
   const int c = cbeg + (int)(blockIdx.x / kClu);
   const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
   const int sh = clu_shift(sz);
@@ -575,8 +594,8 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     const bool own = t == rank;
     remA[t] = own ? zA : cl.map_shared_rank(zA, t);
     remB[t] = own ? zB : cl.map_shared_rank(zB, t);
-    remP[t] = own ? part : cl.map_shared_rank(part, t);
     remD[t] = own ? sm.dpart : cl.map_shared_rank(sm.dpart, t);
+    remPW[t] = own ? pw : cl.map_shared_rank(pw, t);
     if (kMixed) {
       remFA[t] = own ? sm.fA : cl.map_shared_rank(sm.fA, t);
       remFB[t] = own ? sm.fB : cl.map_shared_rank(sm.fB, t);
@@ -586,6 +605,24 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
   // with push the staging below already writes other ranks' shared memory:
   // every block of the cluster must be running first
   if (kPush) cl.sync();
+  // The norm of a sweep: each warp reduces its rows' terms and stores the
+  // result into every rank's pw; after the cluster barrier every thread
+  // folds the same kClu * 8 values in the same order.
+  auto norm_put = [&](float local, int parity, bool is_max) {
+    const float w = is_max ? group_maxf<32>(local) : group_sumf<32>(local);
+    if ((threadIdx.x & 31) == 0) {
+      const int slot = parity * kClu * kCluWarps + rank * kCluWarps + (int)(threadIdx.x >> 5);
+#pragma unroll
+      for (int rk = 0; rk < kClu; rk++) remPW[rk][slot] = w;
+    }
+  };
+  auto norm_get = [&](int parity, bool is_max) {
+    float s = 0.0f;
+    const float* b = pw + parity * kClu * kCluWarps;
+#pragma unroll 8
+    for (int j = 0; j < kClu * kCluWarps; j++) s = is_max ? fmaxf(s, b[j]) : s + b[j];
+    return s;
+  };
   // z of this rank's row i into buffer X: every rank's copy (push) or the
   // own slice (pull)
   auto zput = [&](auto* const* remX, int i, auto v) {
@@ -691,11 +728,9 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
           zput(nxt, i, pn * ivf[i]);
           local += fabsf(pn);
         }
-        const float bs = block_sumf(local, red, false);
-        if (threadIdx.x == 0) part[k & 1] = bs;
-        cl.sync();  // publishes nxt and the rank partials
-        float s2 = 0.0f;
-        for (int r = 0; r < kClu; r++) s2 += remP[r][k & 1];
+        norm_put(local, k & 1, false);
+        cl.sync();  // publishes nxt and the partials
+        const float s2 = norm_get(k & 1, false);
         k++;
         zc ^= 1;
         if (s2 <= thr) break;
@@ -770,11 +805,9 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
         const float pf = abs_to_float(pn);
         local = is_max ? fmaxf(local, pf) : local + pf;
       }
-      const float bs = block_sumf(local, red, is_max);
-      if (threadIdx.x == 0) part[k & 1] = bs;
-      cl.sync();  // publishes nxt and the rank partials
-      float s2 = 0.0f;
-      for (int r = 0; r < kClu; r++) s2 = is_max ? fmaxf(s2, remP[r][k & 1]) : s2 + remP[r][k & 1];
+      norm_put(local, k & 1, is_max);
+      cl.sync();  // publishes nxt and the partials
+      const float s2 = norm_get(k & 1, is_max);
       k++;
       if (fixed >= 0) {
         if (k >= fixed) break;
