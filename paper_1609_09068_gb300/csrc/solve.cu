@@ -345,15 +345,22 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
     return acc;
   };
   auto row_sum = [&](int i) -> double { return row_sum_of(z, i); };
-  auto row_sumf = [&](int i) -> float {
-    float acc = 0.0f;
+  auto row_sumf = [&](const float* zb, int i) -> float {
     const int e0 = ip[i], e1 = ip[i + 1];
     if (staged) {
-#pragma unroll 4
-      for (int e = e0; e < e1; e++) acc += zf[ix[e]];
-    } else {
-      for (int e = e0; e < e1; e++) acc += zf[local_or_err(a, a.int_idx[ib + e] - off, sz)];
+      float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
+      int e = e0;
+      for (; e + 3 < e1; e += 4) {
+        acc0 += zb[ix[e]];
+        acc1 += zb[ix[e + 1]];
+        acc2 += zb[ix[e + 2]];
+        acc3 += zb[ix[e + 3]];
+      }
+      for (; e < e1; e++) acc0 += zb[ix[e]];
+      return (acc0 + acc1) + (acc2 + acc3);
     }
+    float acc = 0.0f;
+    for (int e = e0; e < e1; e++) acc += zb[local_or_err(a, a.int_idx[ib + e] - off, sz)];
     return acc;
   };
   int k = 0, k64 = 0;
@@ -388,15 +395,27 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
       F = 0.0f;
     }
     int rounds = 0;
+    // the FP32 z double-buffered (the second buffer in the FP64 one's
+    // space) and the norm from warp partials: one barrier a sweep
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float* fc = zf;
+    float* fn = reinterpret_cast<float*>(z1);
     for (;;) {
       for (; !skip;) {
-        const float pn = act ? cf * row_sumf(i) : 0.0f;
-        __syncthreads();  // every row has read zf before it is overwritten
+        const float pn = act ? cf * row_sumf(fc, i) : 0.0f;
         if (act) {
-          zf[i] = pn * invf;
+          fn[i] = pn * invf;
           F += pn;
         }
-        const float s2 = block_sumf(fabsf(pn), red, false);  // publishes zf
+        const float pf = group_sumf<32>(fabsf(pn));
+        if (lane == 0) red2[k & 1][wib] = pf;
+        __syncthreads();  // publishes fn and the partials
+        float s2 = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kCtaThreads / 32; w++) s2 += red2[k & 1][w];
+        float* t = fc;
+        fc = fn;
+        fn = t;
         k++;
         if (s2 <= thr) break;
         if (k >= a.max_iter) {
@@ -420,7 +439,7 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
         break;
       }
       F = (float)r;
-      if (act) zf[i] = (float)(r * inv);
+      if (act) fc[i] = (float)(r * inv);  // the buffer the next FP32 sweep reads
       thr = fmaxf(0.5f * (float)tau, kMixKappa * (float)rho);
       __syncthreads();
     }
