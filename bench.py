@@ -38,6 +38,10 @@ UNIT = "GTEPS"
 C = 0.85
 TOL = 1e-10
 FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one launch of the grid-wide SCC kernel, from
+# an ncu capture of the current kernel on that workload (the summary under
+# profiles/ gives the command); None where no capture was taken
+TRAFFIC_BYTES = {"web": 28_122_368 + 1_624_320}
 
 WORKLOADS = {
     "web": ("web_like: n=1,000,000, mean out-degree 8, Zipf(2.1) degrees, giant SCC 40%, "
@@ -441,7 +445,7 @@ def run_ours(args):
     achieved = k_bytes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
     peak = float(peaks.get("hbm_gbs", 6800.0))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": TRAFFIC_BYTES.get(args.workload),
                 "kernel": "solve_large_scc_k (grid-wide SCC power series)",
                 "peak_kind": f"{peak_kind} copy bandwidth", "kernel_ms_per_step": k_ms,
                 "algorithmic_bytes_per_step": k_bytes,
