@@ -215,22 +215,24 @@ pr_status pr_partition_info(const pr_partition *part, int32_t *n, int64_t *m, in
  *   - the size boundary between the one-CTA class and the 8-CTA cluster
  *     class (64, 128 or 256 vertices), and
  *   - the blocks per SM of the grid-wide power-series kernels (3 or 4),
+ *   - then, for the best of those, whether the grid-wide sweeps share their
+ *     short rows among warps by cost (in-degree + 8) or in strided groups,
  * keeps the fastest for this partition and makes it the default of
  * partitions created later in the process.  Results of pr_solve do not
  * depend on the choice beyond rounding order.
  *   u      : [n] float64 DEVICE weights for the timed solves.
- *   cta_max, coop_blocks, best_ms : optional host outputs (the choice and
- *            its solve time).
+ *   cta_max, coop_blocks, balance, best_ms : optional host outputs (the
+ *            choice and its solve time).
  * Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA and the errors of pr_solve.
- * Synchronises the stream; about eighteen solves' worth of time.
+ * Synchronises the stream; about twenty-one solves' worth of time.
  */
 pr_status pr_partition_tune(pr_partition *part, double c, const double *u, double tol, void *stream,
-                            int32_t *cta_max, int32_t *coop_blocks, float *best_ms);
+                            int32_t *cta_max, int32_t *coop_blocks, int32_t *balance, float *best_ms);
 
-/* Set the tuner's two parameters by hand for this partition: cta_max in
- * [32, 256], coop_blocks in [1, 8] (fewer if the kernels do not fit).
- * Errors: PR_EINVAL. */
-pr_status pr_partition_set_shape(pr_partition *part, int32_t cta_max, int32_t coop_blocks);
+/* Set the tuner's parameters by hand for this partition: cta_max in
+ * [32, 256], coop_blocks in [1, 8] (fewer if the kernels do not fit),
+ * balance 0 or 1.  Errors: PR_EINVAL. */
+pr_status pr_partition_set_shape(pr_partition *part, int32_t cta_max, int32_t coop_blocks, int32_t balance);
 
 /* Release the partition's device memory (asynchronously, on the stream it
  * was created on, which must still exist). NULL is accepted. */

@@ -90,8 +90,9 @@ _SIGS = {
     "pr_residual_l1_static": (C.c_int, [C.POINTER(_Csr), C.c_double, C.c_void_p, C.c_void_p,
                                         C.POINTER(C.c_double), C.c_void_p]),
     "pr_partition_tune": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.c_void_p,
-                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
-    "pr_partition_set_shape": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_float)]),
+    "pr_partition_set_shape": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "pr_mpnn_param_count": (C.c_int64, []),
     "pr_mpnn_create": (C.c_int, [C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
     "pr_mpnn_destroy": (None, [C.c_void_p]),
@@ -234,17 +235,17 @@ class Partition:
 
     def tune(self, c, u, tol):
         """Autotune the solve's launch shapes on this partition (see
-        pr_partition_tune); returns {"cta_max", "coop_blocks", "best_ms"}."""
+        pr_partition_tune); returns {"cta_max", "coop_blocks", "balance", "best_ms"}."""
         ud = _dev_f64(u)
-        a, b, t = C.c_int32(), C.c_int32(), C.c_float()
+        a, b, bl, t = C.c_int32(), C.c_int32(), C.c_int32(), C.c_float()
         _check(load_library().pr_partition_tune(self._h, float(c), ud.data_ptr() if self.n else None, float(tol),
-                                                _stream(), C.byref(a), C.byref(b), C.byref(t)),
+                                                _stream(), C.byref(a), C.byref(b), C.byref(bl), C.byref(t)),
                "pr_partition_tune")
-        return {"cta_max": a.value, "coop_blocks": b.value, "best_ms": t.value}
+        return {"cta_max": a.value, "coop_blocks": b.value, "balance": bl.value, "best_ms": t.value}
 
-    def set_shape(self, cta_max, coop_blocks):
+    def set_shape(self, cta_max, coop_blocks, balance=1):
         """Set the tuner's parameters by hand (pr_partition_set_shape)."""
-        _check(load_library().pr_partition_set_shape(self._h, int(cta_max), int(coop_blocks)),
+        _check(load_library().pr_partition_set_shape(self._h, int(cta_max), int(coop_blocks), int(balance)),
                "pr_partition_set_shape")
 
     def close(self):

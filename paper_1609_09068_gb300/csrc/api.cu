@@ -141,9 +141,9 @@ pr_status pr_partition_create(const pr_graph* g, uint32_t flags, void* stream, p
   }
   if (st == PR_OK) {
     // the class boundary and grid shape an earlier tuning chose
-    int32_t tc = kCtaCompMax, tb = 4;
-    tuned_defaults(&tc, &tb);
-    if (tc != P->cta_max || tb != P->coop_blocks) retune_levels(P, tc, tb);
+    int32_t tc = kCtaCompMax, tb = 4, tl = 1;
+    tuned_defaults(&tc, &tb, &tl);
+    if (tc != P->cta_max || tb != P->coop_blocks || tl != P->balance) retune_levels(P, tc, tb, tl);
   }
   if (st != PR_OK) {
     delete P->keep;
@@ -308,20 +308,21 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
   return flags ? PR_ENOCONV : PR_OK;
 }
 
-pr_status pr_partition_set_shape(pr_partition* part, int32_t cta_max, int32_t coop_blocks) {
-  if (!part || cta_max < kWarpCompMax || cta_max > kCtaCompMax || coop_blocks < 1 || coop_blocks > 8)
+pr_status pr_partition_set_shape(pr_partition* part, int32_t cta_max, int32_t coop_blocks, int32_t balance) {
+  if (!part || cta_max < kWarpCompMax || cta_max > kCtaCompMax || coop_blocks < 1 || coop_blocks > 8 ||
+      (balance != 0 && balance != 1))
     return PR_EINVAL;
   std::lock_guard<std::mutex> lock(part->plan_mu);
-  retune_levels(part, cta_max, coop_blocks);
+  retune_levels(part, cta_max, coop_blocks, balance);
   return PR_OK;
 }
 
 pr_status pr_partition_tune(pr_partition* part, double c, const double* u, double tol, void* stream,
-                            int32_t* cta_max, int32_t* coop_blocks, float* best_ms) {
+                            int32_t* cta_max, int32_t* coop_blocks, int32_t* balance, float* best_ms) {
   if (!part) return PR_EINVAL;
   if (part->g.n > 0 && (!u || !(c > 0.0 && c < 1.0) || !(tol > 0.0))) return PR_EINVAL;
   std::lock_guard<std::mutex> lock(part->plan_mu);
-  return tune_partition(part, c, u, tol, (cudaStream_t)stream, cta_max, coop_blocks, best_ms);
+  return tune_partition(part, c, u, tol, (cudaStream_t)stream, cta_max, coop_blocks, balance, best_ms);
 }
 
 pr_status pr_global_power(const pr_graph* g, double c, const double* u, double tol, const pr_solve_opts* opts,

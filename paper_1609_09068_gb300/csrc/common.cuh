@@ -439,6 +439,7 @@ struct pr_partition_s {
   std::vector<int32_t> h_c_off;          // host copy of c_off [K+1]
   int32_t cta_max = prgb::kCtaCompMax;   // largest component of the one-CTA class (tunable)
   int32_t coop_blocks = 4;               // blocks per SM of the grid-wide solve kernels (tunable)
+  int32_t balance = 1;                   // grid-wide sweeps share light rows by cost (tunable)
   std::vector<prgb::LargeComp> large;    // host
   prgb::SolvePlan* plan = nullptr;       // cached solve (graph), built on first use
   std::mutex plan_mu;                    // one call at a time uses the plan

@@ -1313,7 +1313,7 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
   a.p_outdeg = P->p_outdeg;
   a.p_inv = P->p_inv;
   a.lorder = P->lorder;
-  a.lpre = P->lpre;
+  a.lpre = P->balance ? P->lpre : nullptr;
   a.int_ptr = P->int_ptr;
   a.int_idx = P->int_idx;
   a.ext_ptr = P->ext_ptr;
@@ -1649,15 +1649,18 @@ pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_hos
 
 static int32_t g_tuned_cta = kCtaCompMax;
 static int32_t g_tuned_blocks = 4;
+static int32_t g_tuned_balance = 1;
 
-void tuned_defaults(int32_t* cta_max, int32_t* coop_blocks) {
+void tuned_defaults(int32_t* cta_max, int32_t* coop_blocks, int32_t* balance) {
   *cta_max = g_tuned_cta;
   *coop_blocks = g_tuned_blocks;
+  *balance = g_tuned_balance;
 }
 
-void retune_levels(pr_partition_s* P, int32_t cta_max, int32_t coop_blocks) {
+void retune_levels(pr_partition_s* P, int32_t cta_max, int32_t coop_blocks, int32_t balance) {
   P->cta_max = cta_max;
   P->coop_blocks = coop_blocks;
+  P->balance = balance;
   const std::vector<int32_t>& co = P->h_c_off;
   auto size = [&](int c) { return co[c + 1] - co[c]; };
   for (LevelRange& r : P->levels) {
@@ -1682,11 +1685,17 @@ void retune_levels(pr_partition_s* P, int32_t cta_max, int32_t coop_blocks) {
 }
 
 pr_status tune_partition(pr_partition_s* P, double c, const double* u, double tol, cudaStream_t s,
-                         int32_t* cta_max, int32_t* coop_blocks, float* best_ms) {
-  const int32_t ctas[3] = {64, 128, kCtaCompMax};
-  const int32_t blocks[2] = {3, 4};
+                         int32_t* cta_max, int32_t* coop_blocks, int32_t* balance, float* best_ms) {
+  // the class boundary x grid shape with cost-balanced sweeps, then the best
+  // of those without balancing
+  struct Cand {
+    int32_t cta, blocks, bal;
+  };
+  std::vector<Cand> cands;
+  for (int32_t cm : {64, 128, kCtaCompMax})
+    for (int32_t b : {3, 4}) cands.push_back({cm, b, 1});
   float best = -1.0f;
-  int32_t bc = P->cta_max, bb = P->coop_blocks;
+  Cand bc{P->cta_max, P->coop_blocks, P->balance};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   PRGB_CUDA(cudaEventCreate(&e0));
   PRGB_CUDA(cudaEventCreate(&e1));
@@ -1694,43 +1703,45 @@ pr_status tune_partition(pr_partition_s* P, double c, const double* u, double to
   double* R = nullptr;
   Arena tmp(s);
   st = tmp.alloc(&R, (size_t)P->g.n + 1);
-  for (int i = 0; i < 3 && st == PR_OK; i++)
-    for (int j = 0; j < 2 && st == PR_OK; j++) {
-      retune_levels(P, ctas[i], blocks[j]);
-      SolvePlan* pl = nullptr;
-      int64_t nl = 0;
-      float t = 1e30f;
-      for (int rep = 0; rep < 3 && st == PR_OK; rep++) {  // the first builds the graph
-        if (cudaEventRecord(e0, s) != cudaSuccess) st = PR_ECUDA;
-        if (st == PR_OK)
-          st = plan_solve(P, c, u, false, tol, PR_NORM_L1, 10000, false, false, nullptr, 0, R, false, s, &pl, &nl);
-        if (st == PR_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
-          st = PR_ECUDA;
-        float ms = 0.0f;
-        if (st == PR_OK && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t = std::min(t, ms);
-      }
-      if (st == PR_OK && pl) {
-        int err = 0;
-        if (cudaMemcpyAsync(&err, &pl->ctl->err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-          st = PR_ECUDA;
-        else if (err)
-          st = (pr_status)err;
-      }
-      if (st == PR_OK && (best < 0.0f || t < best)) {
-        best = t;
-        bc = ctas[i];
-        bb = blocks[j];
-      }
+  for (size_t ci = 0; ci <= cands.size() && st == PR_OK; ci++) {
+    // the last round tries the best so far without balancing
+    const Cand cd = ci < cands.size() ? cands[ci] : Cand{bc.cta, bc.blocks, 0};
+    retune_levels(P, cd.cta, cd.blocks, cd.bal);
+    SolvePlan* pl = nullptr;
+    int64_t nl = 0;
+    float t = 1e30f;
+    for (int rep = 0; rep < 3 && st == PR_OK; rep++) {  // the first builds the graph
+      if (cudaEventRecord(e0, s) != cudaSuccess) st = PR_ECUDA;
+      if (st == PR_OK)
+        st = plan_solve(P, c, u, false, tol, PR_NORM_L1, 10000, false, false, nullptr, 0, R, false, s, &pl, &nl);
+      if (st == PR_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        st = PR_ECUDA;
+      float ms = 0.0f;
+      if (st == PR_OK && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t = std::min(t, ms);
     }
+    if (st == PR_OK && pl) {
+      int err = 0;
+      if (cudaMemcpyAsync(&err, &pl->ctl->err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        st = PR_ECUDA;
+      else if (err)
+        st = (pr_status)err;
+    }
+    if (st == PR_OK && (best < 0.0f || t < best)) {
+      best = t;
+      bc = cd;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  retune_levels(P, bc, bb);
+  retune_levels(P, bc.cta, bc.blocks, bc.bal);
   if (st != PR_OK) return st;
-  g_tuned_cta = bc;
-  g_tuned_blocks = bb;
-  if (cta_max) *cta_max = bc;
-  if (coop_blocks) *coop_blocks = bb;
+  g_tuned_cta = bc.cta;
+  g_tuned_blocks = bc.blocks;
+  g_tuned_balance = bc.bal;
+  if (cta_max) *cta_max = bc.cta;
+  if (coop_blocks) *coop_blocks = bc.blocks;
+  if (balance) *balance = bc.bal;
   if (best_ms) *best_ms = best;
   return PR_OK;
 }

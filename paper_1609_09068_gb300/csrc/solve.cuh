@@ -133,13 +133,15 @@ pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_hos
 // Autotuner (f-1): move the boundary between the one-CTA and the cluster
 // classes of every level to cta_max (33..kCtaCompMax) and set the grid-wide
 // kernels' blocks per SM; drops the partition's captured graphs.
-void retune_levels(pr_partition_s* P, int32_t cta_max, int32_t coop_blocks);
+// balance: 1 = the grid-wide sweeps share their light rows among warps by
+// cost, 0 = in strided groups.
+void retune_levels(pr_partition_s* P, int32_t cta_max, int32_t coop_blocks, int32_t balance);
 // Times the captured solve for each candidate and keeps the fastest; the
 // choice also becomes the default of partitions created later in the process.
 pr_status tune_partition(pr_partition_s* P, double c, const double* u, double tol, cudaStream_t s,
-                         int32_t* cta_max, int32_t* coop_blocks, float* best_ms);
-// the process-wide tuned defaults (kCtaCompMax / 4 until a tuning ran)
-void tuned_defaults(int32_t* cta_max, int32_t* coop_blocks);
+                         int32_t* cta_max, int32_t* coop_blocks, int32_t* balance, float* best_ms);
+// the process-wide tuned defaults (kCtaCompMax / 4 / 1 until a tuning ran)
+void tuned_defaults(int32_t* cta_max, int32_t* coop_blocks, int32_t* balance);
 
 // edges read by the solve; with iters64 (may be null), also the edges read
 // by FP64 residual sweeps

@@ -411,18 +411,18 @@ def test_dense_solve_web_like_and_mixed(prgb):
         prgb.solve(P, C, u, 1e-10, lu_threshold=130)
 
 
-@pytest.mark.parametrize("cta_max,blocks", [(64, 3), (128, 4), (256, 2)])
-def test_launch_shapes_keep_parity(prgb, cta_max, blocks):
+@pytest.mark.parametrize("cta_max,blocks,balance", [(64, 3, 1), (128, 4, 0), (256, 2, 1)])
+def test_launch_shapes_keep_parity(prgb, cta_max, blocks, balance):
     """The autotuner's parameters change which kernel class solves a
     component and the grid of the grid-wide kernels, never the result."""
     g = gg.small_planted(seed=33, n=40_000, n_scc=20, scc_vertices=30_000, n_dangling=4_000, layers=6,
                          target_edges=200_000)
     G, P, q = assert_partition_equal(prgb, g.rowptr, g.col)
-    P.set_shape(cta_max, blocks)
+    P.set_shape(cta_max, blocks, balance)
     assert_solve_parity(prgb, g, G, P, q)
     g2 = gg.web_like(seed=12, n=60_000, n_small=1_200, layers=12, giant_layer=4)
     G2, P2, q2 = assert_partition_equal(prgb, g2.rowptr, g2.col)
-    P2.set_shape(cta_max, blocks)
+    P2.set_shape(cta_max, blocks, balance)
     assert_solve_parity(prgb, g2, G2, P2, q2)
 
 
@@ -431,7 +431,7 @@ def test_autotuner(prgb):
     g = gg.web_like(seed=12, n=60_000, n_small=1_200, layers=12, giant_layer=4)
     G, P, q = assert_partition_equal(prgb, g.rowptr, g.col)
     choice = P.tune(C, torch.from_numpy(g.u).cuda(), 1e-10)
-    assert choice["cta_max"] in (64, 128, 256) and choice["coop_blocks"] in (3, 4)
+    assert choice["cta_max"] in (64, 128, 256) and choice["coop_blocks"] in (3, 4) and choice["balance"] in (0, 1)
     assert choice["best_ms"] > 0
     assert_solve_parity(prgb, g, G, P, q)
     # partitions created afterwards start from the tuned shape
