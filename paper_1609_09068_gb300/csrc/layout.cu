@@ -4,11 +4,13 @@
 //   size descending (Sec. 4.2), ties by smallest vertex ascending.  Two
 //   stable radix sorts (size, then level) over the component list, which is
 //   built in ascending smallest-vertex order.
-// * Permutation: vertices ordered by (component id, wave descending, vertex
-//   id).  Each component is a contiguous range; inside a CAC the wave order
-//   is a topological order (an edge v -> w inside a CAC has wave(v) >
-//   wave(w)), so runs of equal wave ("sub-levels") can be solved one after
-//   the other in a single pass, as the CAC BFS of Sec. 4.3.1 does.
+// * Permutation: vertices ordered by (component id, wave descending,
+//   out-degree descending, vertex id).  Each component is a contiguous
+//   range; inside a CAC the wave order is a topological order (an edge
+//   v -> w inside a CAC has wave(v) > wave(w)), so runs of equal wave
+//   ("sub-levels") can be solved one after the other in a single pass, as
+//   the CAC BFS of Sec. 4.3.1 does.  The out-degree key puts the entries of
+//   z that the sweeps gather most often next to each other.
 // * Per permuted vertex: internal in-edges (same component) and external
 //   in-edges (from components of higher levels), both as permuted source
 //   positions in CSC order; these are the edge lists "within each component"
@@ -75,11 +77,19 @@ __global__ void comp_of_rep_k(int32_t K, const uint32_t* vals, int32_t* comp_of_
   for (int64_t k = gtid(); k < K; k += gstride()) comp_of_rep[vals[k]] = (int32_t)k;
 }
 
+// Order key of a vertex inside its component: wave descending (a CAC's
+// sub-levels in topological order; one wave for all members of an SCC), then
+// out-degree descending in the low dbits bits.  z_j is gathered once per
+// out-edge of j, so the second key packs the most-gathered entries of every
+// component into a few cache lines.
 __global__ void vertex_comp_k(int32_t n, const int32_t* crep, const int32_t* comp_of_rep, const int32_t* wave,
-                              int32_t maxw, int32_t* comp_id, uint32_t* keys, uint32_t* vals) {
+                              int32_t maxw, const int32_t* __restrict__ outdeg, int dbits, int32_t* comp_id,
+                              uint32_t* keys, uint32_t* vals) {
+  const uint32_t dmax = (1u << dbits) - 1u;
   for (int64_t v = gtid(); v < n; v += gstride()) {
     comp_id[v] = comp_of_rep[crep[v]];
-    keys[v] = (uint32_t)(maxw - wave[v]);  // wave descending
+    const uint32_t d = min((uint32_t)outdeg[v], dmax);
+    keys[v] = ((uint32_t)(maxw - wave[v]) << dbits) | (dmax - d);
     vals[v] = (uint32_t)v;
   }
 }
@@ -323,9 +333,14 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   PRGB_TRY(tmp.alloc(&vv, n));
   PRGB_TRY(tmp.alloc(&vkt, n));
   PRGB_TRY(tmp.alloc(&vvt, n));
-  vertex_comp_k<<<grid1(n), kBlock, 0, s>>>(n, crep, comp_of_rep, wave, max_wave, P->comp_id, vk, vv);
+  // the out-degree key fills the wave key's last 8-bit radix pass (at least
+  // 8 bits while the wave key leaves room)
+  const int wbits = bits_for((uint32_t)max_wave);
+  const int vbits = std::min(32, (wbits + 8 + 7) / 8 * 8);
+  vertex_comp_k<<<grid1(n), kBlock, 0, s>>>(n, crep, comp_of_rep, wave, max_wave, g.outdeg, vbits - wbits,
+                                            P->comp_id, vk, vv);
   PRGB_LAUNCH();
-  PRGB_TRY(radix_sort_pairs(vk, vv, vkt, vvt, n, bits_for((uint32_t)max_wave), tmp));
+  PRGB_TRY(radix_sort_pairs(vk, vv, vkt, vvt, n, vbits, tmp));
   comp_keys_k<<<grid1(n), kBlock, 0, s>>>(n, vv, P->comp_id, vk);
   PRGB_LAUNCH();
   PRGB_TRY(radix_sort_pairs(vk, vv, vkt, vvt, n, bits_for((uint32_t)(K - 1)), tmp));
