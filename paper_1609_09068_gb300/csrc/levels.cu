@@ -21,7 +21,7 @@
 
 namespace prgb {
 
-constexpr int kChunk = 256;  // in-edge entries per work item
+constexpr int kChunk = 32;  // in-edge entries per work item: one 32-lane pass of a warp
 
 __device__ __forceinline__ int gwarp_l() { return (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
 __device__ __forceinline__ int nwarps_l() { return (int)(((int64_t)gridDim.x * blockDim.x) >> 5); }

@@ -22,7 +22,7 @@ namespace prgb {
 __device__ __forceinline__ int gwarp() { return (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
 __device__ __forceinline__ int nwarps() { return (int)(((int64_t)gridDim.x * blockDim.x) >> 5); }
 
-constexpr int kChunkE = 256;  // edges per frontier item
+constexpr int kChunkE = 32;  // edges per frontier item: one 32-lane pass of a warp
 
 __device__ __forceinline__ int nchunks_of(int d) { return (d + kChunkE - 1) / kChunkE; }
 
