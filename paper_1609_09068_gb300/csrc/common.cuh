@@ -49,16 +49,19 @@ void add_launches(long long d);  // kernels launched by a graph replay (or remov
 // device control block: error word and grid-barrier state.  One per call
 // site that needs it, zeroed before each persistent launch.
 // ---------------------------------------------------------------------------
+// The words that different blocks hammer at the same time sit on separate
+// 128-byte lines, so barrier arrivals, barrier polls and frontier pushes do
+// not queue behind each other at one L2 slice.
 struct Ctl {
-  int err;               // pr_status written by kernels (first error wins)
+  alignas(128) int err;  // pr_status written by kernels (first error wins)
   int where;             // diagnostic: which wait expired
-  unsigned int bar_count;
-  unsigned int bar_gen;
-  int cnt[8];            // frontier counters (rotating)
-  int flags[8];          // misc flags (e.g. not-converged)
-  double dsum[4];
+  alignas(128) unsigned int bar_count;  // grid barrier arrivals
+  alignas(128) unsigned int bar_gen;    // grid barrier releases (polled)
   int bwave[2];          // wave barriers: next wave and its frontier size,
   int bcnt[2];           //   published by the last block to arrive
+  alignas(128) int cnt[8];  // frontier counters (rotating)
+  alignas(128) int flags[8];  // misc flags (e.g. not-converged)
+  double dsum[4];
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -81,6 +84,7 @@ __device__ __forceinline__ void set_err(Ctl* ctl, int code, int where) {
 // when any block has recorded an error, so that callers can return early.
 // The Ctl block must have bar_count == 0 when the kernel starts.
 __device__ __forceinline__ bool grid_sync(Ctl* ctl, int where) {
+  __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int nb = gridDim.x;
@@ -93,8 +97,11 @@ __device__ __forceinline__ bool grid_sync(Ctl* ctl, int where) {
       atomicAdd(&ctl->bar_gen, 1u);
     } else {
       const unsigned long long t0 = globaltimer_ns();
-      while (vloadu(&ctl->bar_gen) == gen) {
-        if (vload(&ctl->err) != 0) break;
+      for (;;) {
+        // both words in flight together: one round trip per poll
+        const unsigned int g = vloadu(&ctl->bar_gen);
+        const int e = vload(&ctl->err);
+        if (g != gen || e != 0) break;
         __nanosleep(32);
         if (globaltimer_ns() - t0 > kWaitNs) {
           set_err(ctl, PR_ETIMEOUT, where);
@@ -103,9 +110,10 @@ __device__ __forceinline__ bool grid_sync(Ctl* ctl, int where) {
       }
     }
     __threadfence();
+    ok = vload(&ctl->err) == 0;  // one read per block, not per thread
   }
   __syncthreads();
-  return vload(&ctl->err) == 0;
+  return ok != 0;
 }
 
 // ---------------------------------------------------------------------------

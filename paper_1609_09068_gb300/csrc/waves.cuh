@@ -108,7 +108,7 @@ struct WaveState {
 };
 
 __device__ __forceinline__ bool wave_barrier(Ctl* ctl, int where, int next, WaveState* out) {
-  __shared__ int sh[2];
+  __shared__ int sh[3];
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int gen = vloadu(&ctl->bar_gen);
@@ -124,8 +124,11 @@ __device__ __forceinline__ bool wave_barrier(Ctl* ctl, int where, int next, Wave
       atomicAdd(&ctl->bar_gen, 1u);
     } else {
       const unsigned long long t0 = globaltimer_ns();
-      while (vloadu(&ctl->bar_gen) == gen) {
-        if (vload(&ctl->err) != 0) break;
+      for (;;) {
+        // both words in flight together: one round trip per poll
+        const unsigned int g = vloadu(&ctl->bar_gen);
+        const int e = vload(&ctl->err);
+        if (g != gen || e != 0) break;
         __nanosleep(32);
         if (globaltimer_ns() - t0 > kWaitNs) {
           set_err(ctl, PR_ETIMEOUT, where);
@@ -134,13 +137,15 @@ __device__ __forceinline__ bool wave_barrier(Ctl* ctl, int where, int next, Wave
       }
     }
     __threadfence();
+    // the three reads in one round trip, one per block
     sh[0] = vload(&ctl->bwave[gen & 1]);
     sh[1] = vload(&ctl->bcnt[gen & 1]);
+    sh[2] = vload(&ctl->err);
   }
   __syncthreads();
   out->wave = sh[0];
   out->cnt = sh[1];
-  return vload(&ctl->err) == 0;
+  return sh[2] == 0;
 }
 
 // Runs waves until the frontier is empty.  The caller has filled the first
