@@ -15,7 +15,7 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
                        Ctl* ctl);
 
 // keep freed stream-ordered memory cached in the device's default pool so
-// repeated calls do not return it to the driver
+// repeated calls do not return it to the CUDA driver
 static void tune_pool() {
   static bool done[64] = {false};
   int dev = 0;

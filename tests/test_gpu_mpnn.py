@@ -157,7 +157,7 @@ def check_warm(prgb, g, M, tol=1e-10, precision=0):
 
 def test_warm_start_bounds_with_untrained_network(prgb):
     """Whatever the network guesses, the solve meets the cold start's bounds
-    (the plain series from the guess's residual is the judge)."""
+    (the plain series from the guess's residual decides)."""
     M = prgb.Mpnn(seed=11)
     for g in [small_graph(23), gg.web_like(seed=12, n=60_000, n_small=1_200, layers=12, giant_layer=4)]:
         check_warm(prgb, g, M)
