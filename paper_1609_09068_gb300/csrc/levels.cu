@@ -45,20 +45,31 @@ __global__ void count_nodes_k(const int32_t* __restrict__ optr, const int32_t* _
     }
   }
   // external out-edges: a thread per vertex with at most kHeavy out-edges
-  // (the rest: count_nodes_heavy_k)
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
-    const int e0 = optr[u], e1 = optr[u + 1];
-    if (e1 - e0 > kHeavy) continue;
-    const int U = rep[u];
+  // (the rest: count_nodes_heavy_k).  Lanes that update the same node add
+  // their counts in one atomic: the giant SCC's node alone is the target of
+  // about a tenth of all external edges and the source of a quarter, and
+  // one atomic per edge would queue them all at one address.
+  for (int64_t ub = (int64_t)gwarp_l() * 32; ub < n; ub += (int64_t)nwarps_l() * 32) {
+    const int64_t u = ub + lane;
+    int e0 = 0, e1 = 0, U = -1;
+    if (u < n) {
+      e0 = optr[u];
+      e1 = optr[u + 1];
+      if (e1 - e0 > kHeavy) e1 = e0;
+      else U = rep[u];
+    }
     int ext = 0;
     for (int e = e0; e < e1; e++) {
       const int W = rep[oidx[e]];
-      if (W != U) {
-        ext++;
-        atomicAdd(&cin_cnt[W], 1);
-      }
+      const bool x = W != U;
+      ext += x;
+      const unsigned am = __activemask();
+      const unsigned same = __match_any_sync(am, x ? W : -1);
+      if (x && lane == __ffs(same) - 1) atomicAdd(&cin_cnt[W], __popc(same));
     }
-    if (ext) atomicAdd(&pending[U], ext);
+    const unsigned same = __match_any_sync(0xffffffffu, ext ? U : -1);
+    const int tot = __reduce_add_sync(same, ext);
+    if (ext && lane == __ffs(same) - 1) atomicAdd(&pending[U], tot);
   }
 }
 
@@ -73,10 +84,11 @@ __global__ void count_nodes_heavy_k(const int32_t* __restrict__ optr, const int3
     int ext = 0;
     for (int e = optr[u] + lane; e < optr[u + 1]; e += 32) {
       const int W = rep[oidx[e]];
-      if (W != U) {
-        ext++;
-        atomicAdd(&cin_cnt[W], 1);
-      }
+      const bool x = W != U;
+      ext += x;
+      const unsigned am = __activemask();
+      const unsigned same = __match_any_sync(am, x ? W : -1);
+      if (x && lane == __ffs(same) - 1) atomicAdd(&cin_cnt[W], __popc(same));
     }
     ext = __reduce_add_sync(0xffffffffu, ext);
     if (lane == 0 && ext) atomicAdd(&pending[U], ext);
@@ -88,6 +100,17 @@ __global__ void count_nodes_heavy_k(const int32_t* __restrict__ optr, const int3
 __global__ void fill_cin_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx, int32_t n,
                            const int32_t* __restrict__ list, const int32_t* __restrict__ rep, int32_t* cursor,
                            int32_t* cin_src) {
+  const int lane = threadIdx.x & 31;
+  // lanes appending to the same node's list take their slots with one atomic
+  auto append = [&](bool x, int W, int U) {
+    const unsigned am = __activemask();
+    const unsigned same = __match_any_sync(am, x ? W : -1);
+    const int leader = __ffs(same) - 1;
+    int base = 0;
+    if (x && lane == leader) base = atomicAdd(&cursor[W], __popc(same));
+    base = __shfl_sync(same, base, leader);
+    if (x) cin_src[base + __popc(same & lanemask_lt())] = U;
+  };
   if (!list) {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
          u += (int64_t)gridDim.x * blockDim.x) {
@@ -96,18 +119,17 @@ __global__ void fill_cin_k(const int32_t* __restrict__ optr, const int32_t* __re
       const int U = rep[u];
       for (int e = e0; e < e1; e++) {
         const int W = rep[oidx[e]];
-        if (W != U) cin_src[atomicAdd(&cursor[W], 1)] = U;
+        append(W != U, W, U);
       }
     }
     return;
   }
-  const int lane = threadIdx.x & 31;
   for (int64_t i = gwarp_l(); i < n; i += nwarps_l()) {
     const int u = list[i];
     const int U = rep[u];
     for (int e = optr[u] + lane; e < optr[u + 1]; e += 32) {
       const int W = rep[oidx[e]];
-      if (W != U) cin_src[atomicAdd(&cursor[W], 1)] = U;
+      append(W != U, W, U);
     }
   }
 }
@@ -155,11 +177,22 @@ struct KahnK {
   __device__ int4 pre(int X, int, bool) const {
     return make_int4(2 * level_node[X] + (nsize[X] >= 2 ? 1 : 0), 0, 0, 0);
   }
+  // Lanes whose edges leave the same node U fold their keys and their
+  // decrements into one atomicMax and one decrement by the group's size,
+  // issued by the group's first lane; it finalizes U when the count reaches
+  // zero (a node like the giant SCC has hundreds of thousands of successors,
+  // and one pair of atomics per edge would queue at its two words).
   __device__ bool edge(int e, int4 p, int wave, int* w, int* nch) const {
+    const int lane = threadIdx.x & 31;
     const int U = cin_src[e];
     *w = U;
-    atomicMax(&key[U], p.x);
-    if (atomic_add_acq_rel(&pending[U], -1) != 1) return false;
+    const unsigned am = __activemask();
+    const unsigned same = __match_any_sync(am, U);
+    const int kmax = __reduce_max_sync(same, p.x);
+    const int cnt = __popc(same);
+    if (lane != __ffs(same) - 1) return false;
+    atomicMax(&key[U], kmax);
+    if (atomic_add_acq_rel(&pending[U], -cnt) != cnt) return false;
     *nch = finalize_node(U, wave + 1, nsize, key, level_node, wave_node, merged, cin_ptr);
     return *nch > 0;
   }
