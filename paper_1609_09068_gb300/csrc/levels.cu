@@ -84,11 +84,10 @@ __global__ void count_nodes_heavy_k(const int32_t* __restrict__ optr, const int3
     int ext = 0;
     for (int e = optr[u] + lane; e < optr[u + 1]; e += 32) {
       const int W = rep[oidx[e]];
-      const bool x = W != U;
-      ext += x;
-      const unsigned am = __activemask();
-      const unsigned same = __match_any_sync(am, x ? W : -1);
-      if (x && lane == __ffs(same) - 1) atomicAdd(&cin_cnt[W], __popc(same));
+      if (W != U) {
+        ext++;
+        atomicAdd(&cin_cnt[W], 1);
+      }
     }
     ext = __reduce_add_sync(0xffffffffu, ext);
     if (lane == 0 && ext) atomicAdd(&pending[U], ext);
