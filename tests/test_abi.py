@@ -63,3 +63,19 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(prgb, "_LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         prgb.load_library()
+
+
+def test_newer_entry_points_reject_null_arguments_on_host(lib):
+    from oracle import mpnn as ref
+    assert lib.pr_mpnn_param_count() == ref.N_PARAMS == 9409
+    assert lib.pr_mpnn_create(C.c_uint64(1), None, None) == 1
+    buf = (C.c_float * ref.N_PARAMS)()
+    assert lib.pr_mpnn_get_params(None, buf, ref.N_PARAMS) == 1
+    assert lib.pr_mpnn_set_params(None, buf, ref.N_PARAMS) == 1
+    assert lib.pr_mpnn_predict(None, None, 0.85, None, None, None, None, None) == 1
+    assert lib.pr_mpnn_loss_grad(None, None, 0.85, None, None, None, None, None) == 1
+    assert lib.pr_mpnn_train_step(None, None, 0.85, None, None, C.c_float(1e-3), None, None) == 1
+    lib.pr_mpnn_destroy(None)
+    assert lib.pr_partition_set_shape(None, 256, 4, 1) == 1
+    assert lib.pr_partition_tune(None, 0.85, None, 1e-10, None, None, None, None, None) == 1
+    assert lib.pr_launch_count() >= 0
