@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--breakdown", action="store_true", help="(per-step times always go to stderr)")
     ap.add_argument("--no-warm-start", action="store_true", help="skip training and timing the learned warm start")
     ap.add_argument("--large-n", type=int, default=50_000_000, help="vertices of the large workload")
+    ap.add_argument("--cpu-parallel-worker", action="store_true",
+                    help="internal: time the multi-core CPU baseline and print one JSON line")
     return ap.parse_args()
 
 
@@ -230,6 +232,55 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def cpu_parallel_worker(args):
+    """The multi-core CPU baseline on the host cores: the partition from the
+    oracle (single thread, timed apart), then the componentwise step and the
+    global power series parallelised with OpenMP (cpu_parallel/), one
+    warm-up and the median of three timed runs each."""
+    import cpu_parallel as cp
+    import oracle
+    oracle.build()
+    g = gg.config(args.workload)
+    t0 = time.perf_counter()
+    q = oracle.partition(g.rowptr, g.col)
+    t_part = time.perf_counter() - t0
+    plan = cp.Plan(g.rowptr, g.col, q.comp, q.type, q.level)
+    cores = cp.max_threads()
+
+    def timed(fn):
+        fn()
+        ts, out = [], None
+        for _ in range(3):
+            t = time.perf_counter()
+            out = fn()
+            ts.append(time.perf_counter() - t)
+        return float(np.median(ts)) * 1e3, out
+
+    cw_ms, (R, cw_it) = timed(lambda: plan.solve_cw(C, g.u, TOL, threads=cores))
+    gl_ms, (Rg, gl_it) = timed(lambda: plan.solve_global(C, g.u, TOL, threads=cores))
+    print(json.dumps({
+        "cores": cores, "kind": "OpenMP componentwise step and global power series (cpu_parallel/)",
+        "partition_ms": t_part * 1e3, "partition_kind": "oracle Tarjan DFS, single thread",
+        "cw_solve_ms": cw_ms, "cw_iters_max": cw_it,
+        "cw_residual_l1": oracle.residual_l1(g.rowptr, g.col, C, g.u, R),
+        "global_solve_ms": gl_ms, "global_iters": gl_it,
+        "global_residual_l1": oracle.residual_l1(g.rowptr, g.col, C, g.u, Rg)}), flush=True)
+    return 0
+
+
+def cpu_parallel_leg(args):
+    """Runs cpu_parallel_worker in a child process (a failure there costs this
+    field only); returns its JSON object or {"unavailable": reason}."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-parallel-worker", "--workload", args.workload]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=240)
+        if r.returncode != 0:
+            return {"unavailable": f"worker exited {r.returncode}: {r.stderr.strip()[-300:]}"}
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.TimeoutExpired, OSError, ValueError, IndexError) as e:
+        return {"unavailable": f"{type(e).__name__}: {str(e)[:300]}"}
 
 
 def run_ours(args):
@@ -460,6 +511,13 @@ def run_ours(args):
         cpu = {"value": E / t_cpu / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "one full step of the same workload: oracle partition (Tarjan DFS) + "
                          f"componentwise solve, single thread, {t_cpu:.1f} s"}
+    # ---- multi-core CPU baseline (OpenMP) on the host cores ------------------
+    cpu_par = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "large":
+        cpu_par = cpu_parallel_leg(args)
+        if "cw_solve_ms" in cpu_par:
+            cpu_par["gpu_speedup"] = {"cw_solve": cpu_par["cw_solve_ms"] / float(np.mean(phase[:, 2])),
+                                      "global_solve": cpu_par["global_solve_ms"] / t_global_solve}
 
     ph = phase.mean(axis=0)
     line = {
@@ -477,6 +535,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "cpu_parallel": cpu_par,
         "breakdown_ms": {"graph_prepare": float(ph[0]), "partition": float(ph[1]),
                          "solve": float(ph[2]), "residual_check": float(ph[3])},
         "solve": {"iters_max": max(s["iters_max"] for s in stats), "levels": P.n_levels,
@@ -504,6 +563,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.cpu_parallel_worker:
+        return cpu_parallel_worker(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
