@@ -234,6 +234,36 @@ def run_reference(args):
     return 0
 
 
+def sweep_stats(comp, ctype, rowptr, col, comp_iters, g_iters):
+    """Power-series sweeps per SCC: min / median / max over the SCCs and the
+    mean over SCC-internal edges (each edge weighted by its SCC's sweeps),
+    next to the global series' sweeps -- the comparison of Sec. 5.2 (sweeps
+    per SCC edge, componentwise against the whole graph as one component).
+    comp, ctype: per-vertex component id and type (torch, any device);
+    rowptr, col: the CSR on the same device; comp_iters: numpy, by
+    component id."""
+    import torch
+    n = comp.numel()
+    n_comp = len(comp_iters)
+    dev = comp.device
+    comp = comp.long()
+    deg = (rowptr[1:] - rowptr[:-1]).long()
+    src = torch.repeat_interleave(torch.arange(n, device=dev), deg)
+    dst = col.long()
+    cs = comp[src]
+    internal = (cs == comp[dst]) & (src != dst)
+    m_c = torch.bincount(cs[internal], minlength=n_comp).double()
+    is_scc = torch.zeros(n_comp, dtype=torch.bool, device=dev)
+    is_scc[comp[ctype == 1]] = True
+    it = torch.as_tensor(np.asarray(comp_iters), device=dev).double()
+    its, ms = it[is_scc], m_c[is_scc]
+    if its.numel() == 0:
+        return {"scc_components": 0, "global_sweeps": int(g_iters)}
+    return {"scc_components": int(its.numel()), "min": int(its.min()), "median": float(its.median()),
+            "max": int(its.max()), "edge_weighted_mean": float((its * ms).sum() / ms.sum()),
+            "scc_internal_edges": int(ms.sum()), "global_sweeps": int(g_iters)}
+
+
 def cpu_parallel_worker(args):
     """The multi-core CPU baseline on the host cores: the partition from the
     oracle (single thread, timed apart), then the componentwise step and the
@@ -387,6 +417,14 @@ def run_ours(args):
     g_res = max(r[2] for r in grecs)
     gk_ms = float(np.mean([r[1]["kernel_ms"] for r in grecs]))
     gk_bytes = float(np.mean([r[1]["kernel_bytes"] for r in grecs]))
+
+    # sweeps per SCC against the global series' (outside the timed regions)
+    try:
+        comp_d, type_d, _ = P.query()
+        sweeps = sweep_stats(comp_d, type_d, rowptr, col, stats[-1]["comp_iters"], g_iters)
+        del comp_d, type_d
+    except Exception as e:  # a report field only: never lose the bench line
+        sweeps = {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
 
     # ---- mixed precision (FP32 SCC series + FP64 residual refinement) ------
     # the solve alone, on the partition of the timed steps, against the FP64
@@ -542,6 +580,8 @@ def run_ours(args):
                   "components": P.n_comp, "scc_components": P.n_scc,
                   "edge_visits": stats[-1]["edge_visits"],
                   "traversed_gteps": stats[-1]["edge_visits"] / (ph[2] * 1e-3) / 1e9,
+                  "equivalent_gteps": E * g_iters / (ph[2] * 1e-3) / 1e9,
+                  "sweeps": sweeps,
                   "residual_l1": residual},
         "global_power": {"ms_per_step": t_global, "solve_ms": t_global_solve, "iters": g_iters,
                          "value": job_value(E, world, t_global), "residual_l1": g_res,
