@@ -179,12 +179,17 @@ class Clocks:
         return out
 
 
-def oracle_step(g):
+def oracle_step_result(g):
+    """One oracle step (partition + componentwise solve): (seconds, R)."""
     import oracle
     t0 = time.perf_counter()
     q = oracle.partition(g.rowptr, g.col)
-    oracle.solve_cw(g.rowptr, g.col, q, C, g.u, TOL)
-    return time.perf_counter() - t0
+    R, _ = oracle.solve_cw(g.rowptr, g.col, q, C, g.u, TOL)
+    return time.perf_counter() - t0, R
+
+
+def oracle_step(g):
+    return oracle_step_result(g)[0]
 
 
 def reference_sample(args):
@@ -542,13 +547,24 @@ def run_ours(args):
 
     # ---- CPU oracle on the host cores ---------------------------------------
     cpu = None
+    vs_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "large":
         import oracle
         oracle.build()
-        t_cpu = oracle_step(g)
+        t_cpu, R_oracle = oracle_step_result(g)
         cpu = {"value": E / t_cpu / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "one full step of the same workload: oracle partition (Tarjan DFS) + "
                          f"componentwise solve, single thread, {t_cpu:.1f} s"}
+        # the GPU's FP64 result against the oracle's on the full workload;
+        # each side stops by its own rule (no replayed sweep counts), so the
+        # bound is 2 tol / (1 - c) in L1
+        try:
+            R_gpu = R64.double().cpu().numpy()
+            vs_oracle = {"l1_diff": float(np.abs(R_gpu - R_oracle).sum()),
+                         "max_rel": float(np.max(np.abs(R_gpu - R_oracle) / np.abs(R_oracle).clip(1e-300))),
+                         "l1_bound": 2 * TOL / (1 - C)}
+        except Exception as e:  # a report field only: never lose the bench line
+            vs_oracle = {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
     # ---- multi-core CPU baseline (OpenMP) on the host cores ------------------
     cpu_par = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "large":
@@ -582,7 +598,7 @@ def run_ours(args):
                   "traversed_gteps": stats[-1]["edge_visits"] / (ph[2] * 1e-3) / 1e9,
                   "equivalent_gteps": E * g_iters / (ph[2] * 1e-3) / 1e9,
                   "sweeps": sweeps,
-                  "residual_l1": residual},
+                  "residual_l1": residual, "vs_oracle": vs_oracle},
         "global_power": {"ms_per_step": t_global, "solve_ms": t_global_solve, "iters": g_iters,
                          "value": job_value(E, world, t_global), "residual_l1": g_res,
                          "kernel_gbs": gk_bytes / (gk_ms * 1e-3) / 1e9 if gk_ms > 0 else None},
