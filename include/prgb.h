@@ -382,6 +382,14 @@ const char *pr_status_str(pr_status s);
 /* The cudaError_t of the most recent PR_ECUDA in this thread (0 if none). */
 int pr_last_cuda_error(void);
 
+/* The most recent non-OK status that a call of this library returned in
+ * this thread -- a failed argument check, an allocation, a CUDA call, or a
+ * device-side check or bounded wait (PR_EINTERNAL, PR_ETIMEOUT) -- and
+ * PR_OK if none failed since the last read.  Reading clears it.  Every
+ * call also returns its own status; this is for callers that check
+ * after a batch of calls. */
+pr_status pr_last_device_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,7 @@ _SIGS = {
     "pr_status_str": (C.c_char_p, [C.c_int]),
     "pr_last_cuda_error": (C.c_int, []),
     "pr_launch_count": (C.c_int64, []),
+    "pr_last_device_error": (C.c_int, []),
     "pr_residual_l1_static": (C.c_int, [C.POINTER(_Csr), C.c_double, C.c_void_p, C.c_void_p,
                                         C.POINTER(C.c_double), C.c_void_p]),
     "pr_partition_tune": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.c_void_p,

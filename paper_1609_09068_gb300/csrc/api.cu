@@ -58,9 +58,11 @@ const char* pr_status_str(pr_status s) {
 
 int pr_last_cuda_error(void) { return prgb::last_cuda_error(); }
 
+pr_status pr_last_device_error(void) { return prgb::take_last_status(); }
+
 int64_t pr_launch_count(void) { return (int64_t)prgb::launch_count(); }
 
-pr_status pr_graph_create(const pr_csr* csr, void* stream, pr_graph** out) {
+static pr_status pr_graph_create_body(const pr_csr* csr, void* stream, pr_graph** out) {
   if (!out) return PR_EINVAL;
   *out = nullptr;
   if (!csr || csr->n < 0 || csr->nnz < 0 || csr->nnz >= ((int64_t)1 << 31)) return PR_EINVAL;
@@ -98,13 +100,17 @@ pr_status pr_graph_create(const pr_csr* csr, void* stream, pr_graph** out) {
   return PR_OK;
 }
 
+pr_status pr_graph_create(const pr_csr* csr, void* stream, pr_graph** out) {
+  return prgb::note_status(pr_graph_create_body(csr, stream, out));
+}
+
 void pr_graph_destroy(pr_graph* g) {
   if (!g) return;
   delete g->keep;
   delete g;
 }
 
-pr_status pr_partition_create(const pr_graph* g, uint32_t flags, void* stream, pr_partition** out) {
+static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, void* stream, pr_partition** out) {
   if (!out) return PR_EINVAL;
   *out = nullptr;
   if (!g || flags != 0) return PR_EINVAL;
@@ -154,7 +160,11 @@ pr_status pr_partition_create(const pr_graph* g, uint32_t flags, void* stream, p
   return PR_OK;
 }
 
-pr_status pr_partition_query(const pr_partition* part, int32_t* comp_id, uint8_t* type, int32_t* level,
+pr_status pr_partition_create(const pr_graph* g, uint32_t flags, void* stream, pr_partition** out) {
+  return prgb::note_status(pr_partition_create_body(g, flags, stream, out));
+}
+
+static pr_status pr_partition_query_body(const pr_partition* part, int32_t* comp_id, uint8_t* type, int32_t* level,
                              int32_t* n_comp, int32_t* n_levels, void* stream) {
   if (!part) return PR_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -169,7 +179,12 @@ pr_status pr_partition_query(const pr_partition* part, int32_t* comp_id, uint8_t
   return PR_OK;
 }
 
-pr_status pr_partition_info(const pr_partition* part, int32_t* n, int64_t* m, int32_t* n_comp, int32_t* n_levels,
+pr_status pr_partition_query(const pr_partition* part, int32_t* comp_id, uint8_t* type, int32_t* level,
+                             int32_t* n_comp, int32_t* n_levels, void* stream) {
+  return prgb::note_status(pr_partition_query_body(part, comp_id, type, level, n_comp, n_levels, stream));
+}
+
+static pr_status pr_partition_info_body(const pr_partition* part, int32_t* n, int64_t* m, int32_t* n_comp, int32_t* n_levels,
                             int32_t* n_scc, int32_t* n_scc_vertices) {
   if (!part) return PR_EINVAL;
   if (n) *n = part->g.n;
@@ -179,6 +194,11 @@ pr_status pr_partition_info(const pr_partition* part, int32_t* n, int64_t* m, in
   if (n_scc) *n_scc = part->n_scc;
   if (n_scc_vertices) *n_scc_vertices = part->n_scc_vertices;
   return PR_OK;
+}
+
+pr_status pr_partition_info(const pr_partition* part, int32_t* n, int64_t* m, int32_t* n_comp, int32_t* n_levels,
+                            int32_t* n_scc, int32_t* n_scc_vertices) {
+  return prgb::note_status(pr_partition_info_body(part, n, m, n_comp, n_levels, n_scc, n_scc_vertices));
 }
 
 void pr_partition_destroy(pr_partition* part) {
@@ -194,7 +214,7 @@ static pr_status check_solve_args(double c, const double* u, double tol, const d
   return PR_OK;
 }
 
-pr_status pr_solve(const pr_partition* part, double c, const double* u, double tol, const pr_solve_opts* opts,
+static pr_status pr_solve_body(const pr_partition* part, double c, const double* u, double tol, const pr_solve_opts* opts,
                    double* R, pr_solve_stats* stats, void* stream) {
   if (!part) return PR_EINVAL;
   const int32_t n = part->g.n;
@@ -308,7 +328,12 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
   return flags ? PR_ENOCONV : PR_OK;
 }
 
-pr_status pr_partition_set_shape(pr_partition* part, int32_t cta_max, int32_t coop_blocks, int32_t balance) {
+pr_status pr_solve(const pr_partition* part, double c, const double* u, double tol, const pr_solve_opts* opts,
+                   double* R, pr_solve_stats* stats, void* stream) {
+  return prgb::note_status(pr_solve_body(part, c, u, tol, opts, R, stats, stream));
+}
+
+static pr_status pr_partition_set_shape_body(pr_partition* part, int32_t cta_max, int32_t coop_blocks, int32_t balance) {
   if (!part || cta_max < kWarpCompMax || cta_max > kCtaCompMax || coop_blocks < 1 || coop_blocks > 8 ||
       (balance != 0 && balance != 1))
     return PR_EINVAL;
@@ -317,7 +342,11 @@ pr_status pr_partition_set_shape(pr_partition* part, int32_t cta_max, int32_t co
   return PR_OK;
 }
 
-pr_status pr_partition_tune(pr_partition* part, double c, const double* u, double tol, void* stream,
+pr_status pr_partition_set_shape(pr_partition* part, int32_t cta_max, int32_t coop_blocks, int32_t balance) {
+  return prgb::note_status(pr_partition_set_shape_body(part, cta_max, coop_blocks, balance));
+}
+
+static pr_status pr_partition_tune_body(pr_partition* part, double c, const double* u, double tol, void* stream,
                             int32_t* cta_max, int32_t* coop_blocks, int32_t* balance, float* best_ms) {
   if (!part) return PR_EINVAL;
   if (part->g.n > 0 && (!u || !(c > 0.0 && c < 1.0) || !(tol > 0.0))) return PR_EINVAL;
@@ -325,7 +354,12 @@ pr_status pr_partition_tune(pr_partition* part, double c, const double* u, doubl
   return tune_partition(part, c, u, tol, (cudaStream_t)stream, cta_max, coop_blocks, balance, best_ms);
 }
 
-pr_status pr_global_power(const pr_graph* g, double c, const double* u, double tol, const pr_solve_opts* opts,
+pr_status pr_partition_tune(pr_partition* part, double c, const double* u, double tol, void* stream,
+                            int32_t* cta_max, int32_t* coop_blocks, int32_t* balance, float* best_ms) {
+  return prgb::note_status(pr_partition_tune_body(part, c, u, tol, stream, cta_max, coop_blocks, balance, best_ms));
+}
+
+static pr_status pr_global_power_body(const pr_graph* g, double c, const double* u, double tol, const pr_solve_opts* opts,
                           double* R, pr_solve_stats* stats, void* stream) {
   if (!g) return PR_EINVAL;
   const int32_t n = g->g.n;
@@ -380,7 +414,12 @@ pr_status pr_global_power(const pr_graph* g, double c, const double* u, double t
   return st;
 }
 
-pr_status pr_residual_l1(const pr_graph* g, double c, const double* u, const double* R, double* out_host,
+pr_status pr_global_power(const pr_graph* g, double c, const double* u, double tol, const pr_solve_opts* opts,
+                          double* R, pr_solve_stats* stats, void* stream) {
+  return prgb::note_status(pr_global_power_body(g, c, u, tol, opts, R, stats, stream));
+}
+
+static pr_status pr_residual_l1_body(const pr_graph* g, double c, const double* u, const double* R, double* out_host,
                          void* stream) {
   if (!g || !out_host) return PR_EINVAL;
   if (g->g.n > 0 && (!u || !R)) return PR_EINVAL;
@@ -394,6 +433,11 @@ pr_status pr_residual_l1(const pr_graph* g, double c, const double* u, const dou
   PRGB_CUDA(cudaMemcpyAsync(out_host, out, 8, cudaMemcpyDeviceToHost, s));
   PRGB_CUDA(cudaStreamSynchronize(s));
   return PR_OK;
+}
+
+pr_status pr_residual_l1(const pr_graph* g, double c, const double* u, const double* R, double* out_host,
+                         void* stream) {
+  return prgb::note_status(pr_residual_l1_body(g, c, u, R, out_host, stream));
 }
 
 }  // extern "C"

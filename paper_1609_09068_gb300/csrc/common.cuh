@@ -20,6 +20,10 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded device waits: 
 // status plumbing
 // ---------------------------------------------------------------------------
 void set_last_cuda_error(cudaError_t e);
+// records a non-OK status of a public call (read and cleared by
+// pr_last_device_error); returns s
+pr_status note_status(pr_status s);
+pr_status take_last_status();
 
 #define PRGB_TRY(expr)                                   \
   do {                                                   \

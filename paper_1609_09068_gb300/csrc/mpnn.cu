@@ -547,7 +547,7 @@ extern "C" {
 
 int64_t pr_mpnn_param_count(void) { return kMpParams; }
 
-pr_status pr_mpnn_create(uint64_t seed, void* stream, pr_mpnn** out) {
+static pr_status pr_mpnn_create_body(uint64_t seed, void* stream, pr_mpnn** out) {
   if (!out) return PR_EINVAL;
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
@@ -602,20 +602,28 @@ pr_status pr_mpnn_create(uint64_t seed, void* stream, pr_mpnn** out) {
   return PR_OK;
 }
 
+pr_status pr_mpnn_create(uint64_t seed, void* stream, pr_mpnn** out) {
+  return prgb::note_status(pr_mpnn_create_body(seed, stream, out));
+}
+
 void pr_mpnn_destroy(pr_mpnn* M) {
   if (!M) return;
   delete M->keep;
   delete M;
 }
 
-pr_status pr_mpnn_get_params(const pr_mpnn* M, float* host, int64_t count) {
+static pr_status pr_mpnn_get_params_body(const pr_mpnn* M, float* host, int64_t count) {
   if (!M || !host || count != kMpParams) return PR_EINVAL;
   PRGB_CUDA(cudaMemcpyAsync(host, M->master, kMpParams * 4, cudaMemcpyDeviceToHost, M->stream));
   PRGB_CUDA(cudaStreamSynchronize(M->stream));
   return PR_OK;
 }
 
-pr_status pr_mpnn_set_params(pr_mpnn* M, const float* host, int64_t count) {
+pr_status pr_mpnn_get_params(const pr_mpnn* M, float* host, int64_t count) {
+  return prgb::note_status(pr_mpnn_get_params_body(M, host, count));
+}
+
+static pr_status pr_mpnn_set_params_body(pr_mpnn* M, const float* host, int64_t count) {
   if (!M || !host || count != kMpParams) return PR_EINVAL;
   cudaStream_t s = M->stream;
   PRGB_CUDA(cudaMemcpyAsync(M->master, host, kMpParams * 4, cudaMemcpyHostToDevice, s));
@@ -629,6 +637,10 @@ pr_status pr_mpnn_set_params(pr_mpnn* M, const float* host, int64_t count) {
   return PR_OK;
 }
 
+pr_status pr_mpnn_set_params(pr_mpnn* M, const float* host, int64_t count) {
+  return prgb::note_status(pr_mpnn_set_params_body(M, host, count));
+}
+
 static pr_status mp_check(const pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R) {
   if (!M || !part) return PR_EINVAL;
   if (!(c > 0.0 && c < 1.0)) return PR_EINVAL;
@@ -636,7 +648,7 @@ static pr_status mp_check(const pr_mpnn* M, const pr_partition* part, double c, 
   return PR_OK;
 }
 
-pr_status pr_mpnn_predict(const pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
+static pr_status pr_mpnn_predict_body(const pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
                           float* yhat, double* loss, void* stream) {
   PRGB_TRY(mp_check(M, part, c, u, R));
   cudaStream_t s = (cudaStream_t)stream;
@@ -656,7 +668,12 @@ pr_status pr_mpnn_predict(const pr_mpnn* M, const pr_partition* part, double c, 
   return PR_OK;
 }
 
-pr_status pr_mpnn_loss_grad(pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
+pr_status pr_mpnn_predict(const pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
+                          float* yhat, double* loss, void* stream) {
+  return prgb::note_status(pr_mpnn_predict_body(M, part, c, u, R, yhat, loss, stream));
+}
+
+static pr_status pr_mpnn_loss_grad_body(pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
                             float* grad_host, double* loss, void* stream) {
   PRGB_TRY(mp_check(M, part, c, u, R));
   cudaStream_t s = (cudaStream_t)stream;
@@ -674,7 +691,12 @@ pr_status pr_mpnn_loss_grad(pr_mpnn* M, const pr_partition* part, double c, cons
   return PR_OK;
 }
 
-pr_status pr_mpnn_train_step(pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
+pr_status pr_mpnn_loss_grad(pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
+                            float* grad_host, double* loss, void* stream) {
+  return prgb::note_status(pr_mpnn_loss_grad_body(M, part, c, u, R, grad_host, loss, stream));
+}
+
+static pr_status pr_mpnn_train_step_body(pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
                              float lr, double* loss, void* stream) {
   PRGB_TRY(mp_check(M, part, c, u, R));
   if (!(lr > 0.0f)) return PR_EINVAL;
@@ -693,6 +715,11 @@ pr_status pr_mpnn_train_step(pr_mpnn* M, const pr_partition* part, double c, con
   // later solves on other streams see the new weights
   PRGB_CUDA(cudaStreamSynchronize(s));
   return PR_OK;
+}
+
+pr_status pr_mpnn_train_step(pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
+                             float lr, double* loss, void* stream) {
+  return prgb::note_status(pr_mpnn_train_step_body(M, part, c, u, R, lr, loss, stream));
 }
 
 }  // extern "C"

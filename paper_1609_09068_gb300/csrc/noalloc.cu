@@ -111,7 +111,7 @@ __global__ void static_final_k(int nparts, double* part) {
 
 using namespace prgb;
 
-extern "C" pr_status pr_residual_l1_static(const pr_csr* g, double c, const double* u, const double* R,
+static pr_status pr_residual_l1_static_body(const pr_csr* g, double c, const double* u, const double* R,
                                            double* out_host, void* stream) {
   if (!g || !out_host || g->on_host) return PR_EINVAL;
   if (g->n < 0 || g->n > PR_STATIC_MAX_N || g->nnz < 0 || g->nnz >= ((int64_t)1 << 31)) return PR_EINVAL;
@@ -137,4 +137,9 @@ extern "C" pr_status pr_residual_l1_static(const pr_csr* g, double c, const doub
   PRGB_CUDA(cudaMemcpyAsync(&err, sc.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   PRGB_CUDA(cudaStreamSynchronize(s));
   return err ? PR_EINVAL : PR_OK;
+}
+
+extern "C" pr_status pr_residual_l1_static(const pr_csr* g, double c, const double* u, const double* R,
+                                           double* out_host, void* stream) {
+  return prgb::note_status(pr_residual_l1_static_body(g, c, u, R, out_host, stream));
 }

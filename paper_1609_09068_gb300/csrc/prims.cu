@@ -14,6 +14,19 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void add_launches(long long d) { g_launches.fetch_add(d, std::memory_order_relaxed); }
 void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = static_cast<int>(e); }
+
+static thread_local int g_last_status = 0;
+
+pr_status note_status(pr_status s) {
+  if (s != PR_OK) g_last_status = static_cast<int>(s);
+  return s;
+}
+
+pr_status take_last_status() {
+  const int s = g_last_status;
+  g_last_status = 0;
+  return static_cast<pr_status>(s);
+}
 int last_cuda_error() { return g_last_cuda_error; }
 
 int num_sms() {

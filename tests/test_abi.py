@@ -79,3 +79,16 @@ def test_newer_entry_points_reject_null_arguments_on_host(lib):
     assert lib.pr_partition_set_shape(None, 256, 4, 1) == 1
     assert lib.pr_partition_tune(None, 0.85, None, 1e-10, None, None, None, None, None) == 1
     assert lib.pr_launch_count() >= 0
+
+
+def test_last_device_error_records_and_clears(lib):
+    lib.pr_last_device_error()  # start clean
+    assert lib.pr_last_device_error() == 0
+    out = C.c_void_p()
+    assert lib.pr_graph_create(None, None, C.byref(out)) == 1
+    assert lib.pr_mpnn_param_count() > 0  # a call that cannot fail leaves it alone
+    assert lib.pr_last_device_error() == 1
+    assert lib.pr_last_device_error() == 0  # reading cleared it
+    assert lib.pr_partition_set_shape(None, 256, 4, 1) == 1
+    assert lib.pr_solve(None, 0.85, None, 1e-10, None, None, None, None) == 1
+    assert lib.pr_last_device_error() == 1
