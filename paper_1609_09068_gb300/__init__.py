@@ -265,7 +265,13 @@ def graph(rowptr, col, on_host=False):
     return Graph(rowptr, col, on_host=on_host)
 
 
-def partition(g: Graph):
+def partition(g, col=None, on_host=False):
+    """``partition(graph)``, or ``partition(rowptr, col)`` for a CSR (the
+    graph is prepared on the way and kept alive by the partition)."""
+    if col is not None:
+        g = Graph(g, col, on_host=on_host)
+    elif not isinstance(g, Graph):
+        raise TypeError("partition() takes a Graph, or rowptr and col")
     return Partition(g)
 
 

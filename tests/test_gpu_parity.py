@@ -265,6 +265,16 @@ def test_host_io_matches_device(prgb):
     assert k == kd and np.array_equal(Rg, Rgd.cpu().numpy())
 
 
+def test_partition_from_csr(prgb):
+    """partition(rowptr, col) prepares the graph itself: same result."""
+    import torch
+    g = gg.small_planted(seed=5)
+    P1 = prgb.partition(g.rowptr, g.col)
+    P2 = prgb.partition(prgb.graph(g.rowptr, g.col))
+    for a, b in zip(P1.query(), P2.query()):
+        assert torch.equal(a, b)
+
+
 def test_deterministic(prgb):
     import torch
     g = gg.web_like(seed=15, n=30_000, n_small=600, layers=8, giant_layer=3)
