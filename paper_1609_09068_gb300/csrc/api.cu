@@ -184,8 +184,8 @@ pr_status pr_partition_query(const pr_partition* part, int32_t* comp_id, uint8_t
   return prgb::note_status(pr_partition_query_body(part, comp_id, type, level, n_comp, n_levels, stream));
 }
 
-static pr_status pr_partition_info_body(const pr_partition* part, int32_t* n, int64_t* m, int32_t* n_comp, int32_t* n_levels,
-                            int32_t* n_scc, int32_t* n_scc_vertices) {
+static pr_status pr_partition_info_body(const pr_partition* part, int32_t* n, int64_t* m, int32_t* n_comp,
+                                        int32_t* n_levels, int32_t* n_scc, int32_t* n_scc_vertices) {
   if (!part) return PR_EINVAL;
   if (n) *n = part->g.n;
   if (m) *m = part->g.m;
@@ -214,8 +214,8 @@ static pr_status check_solve_args(double c, const double* u, double tol, const d
   return PR_OK;
 }
 
-static pr_status pr_solve_body(const pr_partition* part, double c, const double* u, double tol, const pr_solve_opts* opts,
-                   double* R, pr_solve_stats* stats, void* stream) {
+static pr_status pr_solve_body(const pr_partition* part, double c, const double* u, double tol,
+                               const pr_solve_opts* opts, double* R, pr_solve_stats* stats, void* stream) {
   if (!part) return PR_EINVAL;
   const int32_t n = part->g.n;
   if (n > 0) PRGB_TRY(check_solve_args(c, u, tol, R));
@@ -333,7 +333,8 @@ pr_status pr_solve(const pr_partition* part, double c, const double* u, double t
   return prgb::note_status(pr_solve_body(part, c, u, tol, opts, R, stats, stream));
 }
 
-static pr_status pr_partition_set_shape_body(pr_partition* part, int32_t cta_max, int32_t coop_blocks, int32_t balance) {
+static pr_status pr_partition_set_shape_body(pr_partition* part, int32_t cta_max, int32_t coop_blocks,
+                                             int32_t balance) {
   if (!part || cta_max < kWarpCompMax || cta_max > kCtaCompMax || coop_blocks < 1 || coop_blocks > 8 ||
       (balance != 0 && balance != 1))
     return PR_EINVAL;
@@ -359,8 +360,8 @@ pr_status pr_partition_tune(pr_partition* part, double c, const double* u, doubl
   return prgb::note_status(pr_partition_tune_body(part, c, u, tol, stream, cta_max, coop_blocks, balance, best_ms));
 }
 
-static pr_status pr_global_power_body(const pr_graph* g, double c, const double* u, double tol, const pr_solve_opts* opts,
-                          double* R, pr_solve_stats* stats, void* stream) {
+static pr_status pr_global_power_body(const pr_graph* g, double c, const double* u, double tol,
+                                      const pr_solve_opts* opts, double* R, pr_solve_stats* stats, void* stream) {
   if (!g) return PR_EINVAL;
   const int32_t n = g->g.n;
   if (n > 0) PRGB_TRY(check_solve_args(c, u, tol, R));

@@ -648,8 +648,8 @@ static pr_status mp_check(const pr_mpnn* M, const pr_partition* part, double c, 
   return PR_OK;
 }
 
-static pr_status pr_mpnn_predict_body(const pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
-                          float* yhat, double* loss, void* stream) {
+static pr_status pr_mpnn_predict_body(const pr_mpnn* M, const pr_partition* part, double c, const double* u,
+                                      const double* R, float* yhat, double* loss, void* stream) {
   PRGB_TRY(mp_check(M, part, c, u, R));
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t n = part->g.n;
@@ -673,8 +673,8 @@ pr_status pr_mpnn_predict(const pr_mpnn* M, const pr_partition* part, double c, 
   return prgb::note_status(pr_mpnn_predict_body(M, part, c, u, R, yhat, loss, stream));
 }
 
-static pr_status pr_mpnn_loss_grad_body(pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
-                            float* grad_host, double* loss, void* stream) {
+static pr_status pr_mpnn_loss_grad_body(pr_mpnn* M, const pr_partition* part, double c, const double* u,
+                                        const double* R, float* grad_host, double* loss, void* stream) {
   PRGB_TRY(mp_check(M, part, c, u, R));
   cudaStream_t s = (cudaStream_t)stream;
   Arena tmp(s);
@@ -696,8 +696,8 @@ pr_status pr_mpnn_loss_grad(pr_mpnn* M, const pr_partition* part, double c, cons
   return prgb::note_status(pr_mpnn_loss_grad_body(M, part, c, u, R, grad_host, loss, stream));
 }
 
-static pr_status pr_mpnn_train_step_body(pr_mpnn* M, const pr_partition* part, double c, const double* u, const double* R,
-                             float lr, double* loss, void* stream) {
+static pr_status pr_mpnn_train_step_body(pr_mpnn* M, const pr_partition* part, double c, const double* u,
+                                         const double* R, float lr, double* loss, void* stream) {
   PRGB_TRY(mp_check(M, part, c, u, R));
   if (!(lr > 0.0f)) return PR_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
