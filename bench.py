@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--breakdown", action="store_true", help="(per-step times always go to stderr)")
     ap.add_argument("--no-warm-start", action="store_true", help="skip training and timing the learned warm start")
     ap.add_argument("--large-n", type=int, default=50_000_000, help="vertices of the large workload")
+    ap.add_argument("--no-blocks", action="store_true",
+                    help="skip the deep_dag and 50M-vertex blocks of the default web_like run")
     ap.add_argument("--cpu-parallel-worker", action="store_true",
                     help="internal: time the multi-core CPU baseline and print one JSON line")
     return ap.parse_args()
@@ -230,7 +232,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "n": g.n, "nnz": g.nnz, "sample": sample},
+        "config": {"workload": WORKLOADS[args.workload], "n": g.n, "nnz": g.nnz, "c": C, "tol": TOL,
+                   "norm": "L1", "parallelism": "single", "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{sample}: oracle partition + componentwise solve, single thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -318,65 +321,63 @@ def cpu_parallel_leg(args):
         return {"unavailable": f"{type(e).__name__}: {str(e)[:300]}"}
 
 
-def run_ours(args):
+def diff_fields(R_gpu, R_ref):
+    """L1 difference and largest relative difference of two solutions."""
+    d = np.abs(np.asarray(R_gpu) - np.asarray(R_ref))
+    return {"l1_diff": float(d.sum()),
+            "max_rel": float(np.max(d / np.abs(np.asarray(R_ref)).clip(1e-300))) if d.size else 0.0}
+
+
+def replay_for(q, gpu_comp, gpu_iters, ids=None):
+    """The GPU's sweep count of each SCC, indexed by the oracle's component
+    ids: through one member vertex of each component (ids maps the vertices
+    of a slice back to the whole graph).  CACs and dummies get 0."""
+    K = q.n_comp
+    member = np.zeros(K, np.int64)
+    member[q.comp] = np.arange(q.comp.shape[0])
+    ctype = np.zeros(K, np.uint8)
+    ctype[q.comp] = q.type
+    scc = ctype == 1
+    orig = member if ids is None else ids[np.minimum(member, ids.shape[0] - 1)]
+    return np.where(scc, np.asarray(gpu_iters)[np.asarray(gpu_comp)[orig]], 0).astype(np.int32)
+
+
+def oracle_vs(rowptr, col, u, tol, R_gpu, gpu_comp, gpu_iters, ids=None, tol_scale=1.0):
+    """The oracle (partition + componentwise FP64 solve, single thread) on a
+    CSR, against the GPU's FP64 result on the same vertices: once with each
+    side stopping by its own rule (the difference is then bounded by
+    2 tol / (1 - c) in L1), once with the GPU's sweep counts replayed, where
+    both compute the same truncated series and the difference is rounding
+    (bound 1e-12 relative per entry).  On a slice (ids given) tol is scaled
+    so that every component keeps its budget tol |C| / n of the whole graph."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    q = oracle.partition(rowptr, col)
+    t_part = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    R_own, _ = oracle.solve_cw(rowptr, col, q, C, u, tol * tol_scale)
+    t_solve = time.perf_counter() - t0
+    R_rep, _ = oracle.solve_cw(rowptr, col, q, C, u, tol * tol_scale,
+                               replay_iters=replay_for(q, gpu_comp, gpu_iters, ids))
+    k = R_gpu.shape[0]
+    own = diff_fields(R_gpu, R_own[:k])
+    rep = diff_fields(R_gpu, R_rep[:k])
+    return {"own_rule": dict(own, l1_bound=2 * TOL / (1 - C)),
+            "replayed_sweeps": dict(rep, max_rel_bound=1e-12),
+            "oracle_partition_s": t_part, "oracle_solve_s": t_solve}, R_own[:k]
+
+
+def make_steps(prgb, rowptr, col, u):
+    """One componentwise step (graph, partition, solve, residual) and one
+    global step (graph, series, residual), each bracketed by CUDA events on
+    the current stream."""
     import torch
-
-    import paper_1609_09068_gb300 as prgb
-    from paper_1609_09068_gb300 import _build
-
-    rank, local, world = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if not _build.up_to_date():
-        _build.build()
-    prgb.load_library()
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks_(x):
-        return max_over_ranks(dist, x, "cuda")
-
-    g = load_workload(args.workload, args.large_n)
-    E = g.nnz
-    if isinstance(g, _DeviceGraph):
-        rowptr, col, u = g.rowptr_d, g.col_d, g.u_d
-    else:
-        rowptr = torch.from_numpy(g.rowptr).cuda()
-        col = torch.from_numpy(g.col).cuda()
-        u = torch.from_numpy(g.u).cuda()
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    def cw_step():
-        e = [ev() for _ in range(5)]
-        e[0].record()
-        G = prgb.graph(rowptr, col)
-        e[1].record()
-        P = prgb.partition(G)
-        e[2].record()
-        R, st = prgb.solve(P, C, u, TOL, with_stats=True, timing=True)
-        e[3].record()
-        res = prgb.residual_l1(G, C, u, R)
-        e[4].record()
-        return e, st, res, P
-
-    def global_step():
-        e = [ev() for _ in range(4)]
-        e[0].record()
-        G = prgb.graph(rowptr, col)
-        e[1].record()
-        R, k, st = prgb.global_power(G, C, u, TOL, with_stats=True, timing=True)
-        e[2].record()
-        res = prgb.residual_l1(G, C, u, R)
-        e[3].record()
-        return e, st, res, k
+    cw_step, global_step = make_steps(prgb, rowptr, col, u)
 
     # one-time autotuning of the solve's launch shapes (pr_partition_tune);
     # partitions built in the timed steps start from its choice
@@ -546,23 +547,21 @@ def run_ours(args):
                 "launches_per_step": float(np.mean([s["kernel_launches"] for s in stats]))}
 
     # ---- CPU oracle on the host cores ---------------------------------------
+    # one full oracle step (partition + componentwise solve, single thread)
+    # timed, and the GPU's FP64 result compared with it: each side stopping by
+    # its own rule (L1 bound 2 tol / (1 - c)) and with the GPU's sweep counts
+    # replayed (rounding only: 1e-12 per entry)
     cpu = None
     vs_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "large":
-        import oracle
-        oracle.build()
-        t_cpu, R_oracle = oracle_step_result(g)
-        cpu = {"value": E / t_cpu / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one full step of the same workload: oracle partition (Tarjan DFS) + "
-                         f"componentwise solve, single thread, {t_cpu:.1f} s"}
-        # the GPU's FP64 result against the oracle's on the full workload;
-        # each side stops by its own rule (no replayed sweep counts), so the
-        # bound is 2 tol / (1 - c) in L1
         try:
-            R_gpu = R64.double().cpu().numpy()
-            vs_oracle = {"l1_diff": float(np.abs(R_gpu - R_oracle).sum()),
-                         "max_rel": float(np.max(np.abs(R_gpu - R_oracle) / np.abs(R_oracle).clip(1e-300))),
-                         "l1_bound": 2 * TOL / (1 - C)}
+            comp_h, _, _ = P.query()
+            vs_oracle, _ = oracle_vs(g.rowptr, g.col, g.u, TOL, R64.double().cpu().numpy(), comp_h.cpu().numpy(),
+                                     np.asarray(stats[-1]["comp_iters"]))
+            t_cpu = vs_oracle["oracle_partition_s"] + vs_oracle["oracle_solve_s"]
+            cpu = {"value": E / t_cpu / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "one full step of the same workload: oracle partition (Tarjan DFS) + "
+                             f"componentwise solve, single thread, {t_cpu:.1f} s"}
         except Exception as e:  # a report field only: never lose the bench line
             vs_oracle = {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
     # ---- multi-core CPU baseline (OpenMP) on the host cores ------------------
@@ -607,6 +606,24 @@ def run_ours(args):
         "mixed_precision": mixed,
         "learned_warm_start": warm,
     }
+    # ---- the other configurations, each timed the same way ------------------
+    # deep_dag (n = 4M, 200 levels) and the 50M-vertex web-like graph (FP64
+    # and mixed precision), after the headline's timed regions
+    if world == 1 and args.workload == "web" and not args.no_blocks:
+        del recs, grecs, mrecs
+        for name, key in (("deep", "deep_dag"), ("large", "large")):
+            try:
+                blk, kept = config_block(prgb, name, args, flush, local)
+                if not args.no_cpu_baseline:
+                    try:
+                        blk["vs_oracle"] = block_vs_oracle(name, kept)
+                    except Exception as e:  # a report field only
+                        blk["vs_oracle"] = {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
+                del kept
+            except Exception as e:  # a report block only: never lose the bench line
+                blk = {"unavailable": f"{type(e).__name__}: {str(e)[:300]}"}
+            line[key] = blk
+            torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(line), flush=True)
         print(json.dumps({"phase_ms_per_step": np.round(phase, 3).tolist(),

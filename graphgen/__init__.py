@@ -37,7 +37,7 @@ import numpy as np
 
 __all__ = [
     "Graph", "csr_from_edges", "small_planted", "web_like", "deep_dag",
-    "random_digraph", "uniform_u", "random_u", "config",
+    "random_digraph", "uniform_u", "random_u", "config", "closed_slice",
 ]
 
 
@@ -64,8 +64,11 @@ def csr_from_edges(n, src, dst, dedupe=True):
     """Sorted-row CSR from edge arrays (self-loops kept if present)."""
     src = np.asarray(src, dtype=np.int64)
     dst = np.asarray(dst, dtype=np.int64)
-    key = src * np.int64(n) + dst
-    key = np.unique(key) if dedupe else np.sort(key)
+    key = np.sort(src * np.int64(n) + dst)
+    if dedupe and key.shape[0] > 1:
+        # sorted, then adjacent duplicates dropped: the same array as
+        # np.unique, which on recent numpy hashes first and is far slower
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     s = key // n
     d = key - s * n
     counts = np.bincount(s, minlength=n).astype(np.int64)
@@ -421,6 +424,39 @@ def deep_dag(seed=3, n=4_000_000, levels=200, scc_per_level=(200, 400),
     rowptr, col = csr_from_edges(n, src, dst)
     planted = {"levels": levels, "n_scc": int(len(scc_units))}
     return Graph(n, rowptr, col, random_u(n, rng), f"deep_dag(seed={seed}, n={n})", planted)
+
+
+def closed_slice(rowptr, col, u, keep):
+    """The sub-CSR induced by the vertices with ``keep`` set, every edge that
+    leaves the set redirected to a dangling dummy vertex: the k-th leaving
+    edge of a row goes to dummy ns + k (ns = kept vertices), so each kept
+    vertex keeps its out-degree and rows stay simple.  When the kept set is
+    closed under predecessors (every in-neighbour of a kept vertex is kept),
+    the system (I - c A^T) R = u restricted to it is unchanged: each equation
+    involves only in-neighbours and their out-degrees.  Dummies get u = 0.
+    Returns (rowptr, col, u, kept_ids): the kept vertices are renumbered
+    0..ns-1 in ascending original id, listed in kept_ids."""
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    n = rowptr.shape[0] - 1
+    ids = np.nonzero(np.asarray(keep, dtype=bool))[0]
+    ns = ids.shape[0]
+    newid = np.full(n, -1, np.int64)
+    newid[ids] = np.arange(ns)
+    cnt = rowptr[ids + 1] - rowptr[ids]
+    first = np.cumsum(cnt) - cnt
+    e = np.arange(int(cnt.sum()), dtype=np.int64) - np.repeat(first, cnt) + np.repeat(rowptr[ids], cnt)
+    src = np.repeat(np.arange(ns, dtype=np.int64), cnt)
+    dst = newid[col[e]]
+    leave = dst < 0
+    # rank of each leaving edge within its row
+    lc = np.cumsum(leave) - leave
+    rank = lc - np.repeat(lc[first] if ns else lc[:0], cnt)
+    dst[leave] = ns + rank[leave]
+    n_dummy = int(rank[leave].max()) + 1 if leave.any() else 0
+    rp, cl = csr_from_edges(ns + n_dummy, src, dst)
+    us = np.concatenate([np.asarray(u, dtype=np.float64)[ids], np.zeros(n_dummy)])
+    return rp, cl, us, ids
 
 
 def random_digraph(n, p, seed, loops=False):

@@ -8,7 +8,8 @@ internal edges), chains (acyclic) and dangling vertices -- with Zipf(2.1)
 out-degrees; edges leaving a unit go to a later layer at a geometric layer
 distance, to targets drawn with Zipf(2.1) in-weights.  Vertex ids are
 shuffled.  The graph stays on the device: (rowptr, col) int32 CUDA tensors,
-rows sorted, no duplicates, no self-loops; u = 1/n.
+rows sorted, no duplicates, no self-loops; u = 1/n.  With ``with_layers``
+the planted layer of each vertex comes back too.
 
 The draws come from torch's CUDA generator, so the graph depends on the
 torch version as well as the seed.
@@ -27,7 +28,7 @@ def _zipf(torch, gen, a, size, cap, device):
 
 def web_like_device(seed=4, n=50_000_000, mean_deg=8.0, giant_frac=0.5, small_frac=0.012,
                     dangling_frac=0.12, layers=28, giant_layer=9, zipf_a=2.1, small_median=6.0,
-                    small_sigma=1.5, small_max=2_000, device="cuda"):
+                    small_sigma=1.5, small_max=2_000, device="cuda", with_layers=False):
     import torch
 
     gen = torch.Generator(device=device)
@@ -142,4 +143,11 @@ def web_like_device(seed=4, n=50_000_000, mean_deg=8.0, giant_frac=0.5, small_fr
     rowptr = torch.zeros(n + 1, device=device, dtype=torch.int32)
     rowptr[1:] = torch.cumsum(counts, 0).to(torch.int32)
     u = torch.full((n,), 1.0 / n, device=device, dtype=torch.float64)
+    if with_layers:
+        # the planted layer of every vertex (after the id shuffle): edges only
+        # stay inside a unit or go to a later layer, so the vertices of the
+        # first L layers are closed under predecessors for every L
+        vlayer = torch.empty(n, device=device, dtype=torch.int8)
+        vlayer[perm] = pl.to(torch.int8)
+        return rowptr, col, u, vlayer
     return rowptr, col, u

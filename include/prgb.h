@@ -307,7 +307,9 @@ int64_t pr_launch_count(void);
  * in-flow is accumulated with atomic adds, so the last bits can differ from
  * pr_residual_l1 and from call to call.
  * Errors: PR_EINVAL for n > PR_STATIC_MAX_N, on_host = 1, NULL pointers, or a
- * row or column index out of range; PR_ECUDA.  Synchronises the stream.
+ * malformed CSR as pr_graph_create defines it (rowptr[0] != 0,
+ * rowptr[n] != nnz, a decreasing rowptr, a column out of range, unsorted or
+ * duplicate columns in a row); PR_ECUDA.  Synchronises the stream.
  */
 #define PR_STATIC_MAX_N 1048576
 pr_status pr_residual_l1_static(const pr_csr *g, double c, const double *u, const double *R,

@@ -144,6 +144,23 @@ def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _length(x):
+    """Number of elements of a 1-D tensor, array or sequence (no copy to the
+    device); raises ValueError for anything that is not one-dimensional."""
+    shape = tuple(x.shape) if hasattr(x, "shape") else (len(x),)
+    if len(shape) != 1:
+        raise ValueError(f"expected a 1-D vector, got shape {shape}")
+    return int(shape[0])
+
+
+def _need_len(x, n, what):
+    """Reject a vector whose length is not n before any pointer reaches the
+    C ABI: the kernels and host copies read exactly n entries."""
+    k = _length(x)
+    if k != n:
+        raise ValueError(f"{what} has {k} entries, expected {n}")
+
+
 def _dev_i32(x):
     torch = _torch()
     t = torch.as_tensor(x)
@@ -237,6 +254,7 @@ class Partition:
     def tune(self, c, u, tol):
         """Autotune the solve's launch shapes on this partition (see
         pr_partition_tune); returns {"cta_max", "coop_blocks", "balance", "best_ms"}."""
+        _need_len(u, self.n, "u")
         ud = _dev_f64(u)
         a, b, bl, t = C.c_int32(), C.c_int32(), C.c_int32(), C.c_float()
         _check(load_library().pr_partition_tune(self._h, float(c), ud.data_ptr() if self.n else None, float(tol),
@@ -308,6 +326,9 @@ def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
     ``warm_start`` (an ``Mpnn``) starts each SCC's series from the network's
     guess; SCCs of fewer than ``lu_threshold`` vertices are solved by dense
     elimination (Sec. 4.3 item 3)."""
+    _need_len(u, part.n, "u")
+    if replay_iters is not None:
+        _need_len(replay_iters, part.n_comp, "replay_iters")
     lib = load_library()
     on_host = isinstance(u, np.ndarray)
     o, keep = _opts(norm, max_iter, on_host, replay_iters, precision, warm_start, lu_threshold)
@@ -337,6 +358,7 @@ def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
 def global_power(g: Graph, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iters=None,
                  with_stats=False, allow_noconv=False, timing=False):
     """Baseline power series on the whole graph; returns (R, iterations)."""
+    _need_len(u, g.n, "u")
     lib = load_library()
     on_host = isinstance(u, np.ndarray)
     rep = None if replay_iters is None else [int(replay_iters)]
@@ -365,6 +387,8 @@ def global_power(g: Graph, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
 
 def residual_l1(g: Graph, c, u, R):
     """|| u + c A^T (R/outdeg) - R ||_1 in FP64 on the device."""
+    _need_len(u, g.n, "u")
+    _need_len(R, g.n, "R")
     lib = load_library()
     ud = _dev_f64(u)
     Rd = _dev_f64(R)
@@ -379,6 +403,11 @@ def residual_l1_static(rowptr, col, c, u, R):
     """The L1 residual through pr_residual_l1_static, which allocates no device
     memory (for callers that cannot allocate); all arguments on the device,
     n <= STATIC_MAX_N."""
+    n = _length(rowptr) - 1
+    if n < 0:
+        raise ValueError("rowptr needs at least one entry")
+    _need_len(u, n, "u")
+    _need_len(R, n, "R")
     lib = load_library()
     rp = _dev_i32(rowptr)
     cl = _dev_i32(col)
@@ -420,6 +449,8 @@ class Mpnn:
 
     def predict(self, part: Partition, c, u, R):
         """(yhat float32 CUDA tensor in the original vertex order, loss)."""
+        _need_len(u, part.n, "u")
+        _need_len(R, part.n, "R")
         torch = _torch()
         ud, Rd = _dev_f64(u), _dev_f64(R)
         y = torch.zeros(part.n, dtype=torch.float32, device="cuda")
@@ -431,6 +462,8 @@ class Mpnn:
         return y, loss.value
 
     def loss_grad(self, part: Partition, c, u, R):
+        _need_len(u, part.n, "u")
+        _need_len(R, part.n, "R")
         ud, Rd = _dev_f64(u), _dev_f64(R)
         g = np.empty(self.n_params, np.float32)
         loss = C.c_double(0.0)
@@ -441,6 +474,8 @@ class Mpnn:
         return loss.value, g
 
     def train_step(self, part: Partition, c, u, R, lr=1e-3):
+        _need_len(u, part.n, "u")
+        _need_len(R, part.n, "R")
         ud, Rd = _dev_f64(u), _dev_f64(R)
         loss = C.c_double(0.0)
         _check(load_library().pr_mpnn_train_step(self._h, part.handle, float(c),

@@ -18,6 +18,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -554,6 +555,8 @@ static pr_status pr_mpnn_create_body(uint64_t seed, void* stream, pr_mpnn** out)
   pr_mpnn_s* M = new (std::nothrow) pr_mpnn_s;
   if (!M) return PR_ENOMEM;
   M->stream = s;
+  static std::atomic<uint64_t> next_uid{1};
+  M->uid = next_uid.fetch_add(1, std::memory_order_relaxed);
   M->keep = new (std::nothrow) Arena(s);
   if (!M->keep) {
     delete M;

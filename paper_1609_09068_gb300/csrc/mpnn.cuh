@@ -49,4 +49,8 @@ struct pr_mpnn_s {
   float* grad = nullptr;    // [kMpParams] accumulated gradient
   uint16_t* w16 = nullptr;  // [kMpParams] bf16 copy used by the forward pass
   int64_t step = 0;
+  // process-unique id (never reused): a captured solve that runs this
+  // network is matched by it, not by the handle's address, which a later
+  // model may receive once this one is destroyed
+  uint64_t uid = 0;
 };

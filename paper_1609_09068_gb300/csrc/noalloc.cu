@@ -60,7 +60,8 @@ __global__ void static_clear_k(int32_t n, double* acc, int* err) {
 }
 
 // one warp per row i: push c * R_i / outdeg(i) to every out-neighbour j != i
-// (self-loops are ignored); malformed rows are flagged and skipped
+// (self-loops are ignored); malformed rows (bad offsets, columns out of
+// range, unsorted or repeated) are flagged and skipped
 __global__ void static_push_k(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t n,
                               int64_t nnz, double c, const double* __restrict__ R, double* acc, int* err) {
   const int lane = threadIdx.x & 31;
@@ -68,7 +69,15 @@ __global__ void static_push_k(const int32_t* __restrict__ rowptr, const int32_t*
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w0; i < n; i += nw) {
     const int64_t s = rowptr[i], e = rowptr[i + 1];
-    if (s < 0 || e < s || e > nnz) {
+    if (s < 0 || e < s || e > nnz || (i == 0 && s != 0) || (i == n - 1 && e != nnz)) {
+      if (lane == 0) atomicExch(err, 1);
+      continue;
+    }
+    // the graph model is a simple digraph with sorted rows, as pr_graph_create
+    // requires: a repeated or out-of-order column is rejected, not counted
+    bool bad = false;
+    for (int64_t k = s + 1 + lane; k < e; k += 32) bad |= col[k - 1] >= col[k];
+    if (__any_sync(0xffffffffu, bad)) {
       if (lane == 0) atomicExch(err, 1);
       continue;
     }

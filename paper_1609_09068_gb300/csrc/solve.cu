@@ -1521,7 +1521,7 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
                               bool mixed, bool timing, const pr_mpnn_s* warm, int lu, PlanGraph** out) {
   for (PlanGraph& e : pl->graphs)
     if (e.c == c && e.tol == tol && e.norm == norm && e.max_iter == max_iter && e.mixed == mixed &&
-        e.timing == timing && e.warm == warm && e.lu == lu) {
+        e.timing == timing && e.warm_uid == (warm ? warm->uid : 0) && e.lu == lu) {
       e.last_use = ++pl->uses;
       *out = &e;
       return PR_OK;
@@ -1608,7 +1608,7 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
   e.max_iter = max_iter;
   e.mixed = mixed;
   e.timing = timing;
-  e.warm = warm;
+  e.warm_uid = warm ? warm->uid : 0;
   e.lu = lu;
   e.last_use = ++pl->uses;
   pl->graphs.push_back(e);

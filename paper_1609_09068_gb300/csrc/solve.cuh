@@ -80,7 +80,7 @@ struct PlanGraph {
   double c = 0.0, tol = 0.0;
   int norm = 0, max_iter = 0;
   bool mixed = false, timing = false;
-  const pr_mpnn_s* warm = nullptr;
+  uint64_t warm_uid = 0;  // the warm-start network's id (0: none)
   int lu = 0;
   uint64_t last_use = 0;
 };

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -88,3 +89,90 @@ def test_static_residual_rejects_oversized_input(prgb):
     out = C.c_double(0.0)
     assert lib.pr_residual_l1_static(C.byref(csr), CC, u.data_ptr(), u.data_ptr(), C.byref(out),
                                      prgb._stream()) == 1
+
+
+def test_static_residual_matches_oracle(prgb):
+    """Against the CPU oracle's residual of the same vectors (its own
+    definition of u + c A^T (R/outdeg) - R, summed in FP64 on the host)."""
+    import torch
+    g = gg.small_planted(seed=7)
+    rowptr = torch.from_numpy(g.rowptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    u = torch.from_numpy(g.u).cuda()
+    P = prgb.partition(prgb.graph(rowptr, col))
+    rng = np.random.default_rng(11)
+    for R in (prgb.solve(P, CC, u, 1e-10), torch.from_numpy(rng.random(g.n) / g.n).cuda()):
+        r_static = prgb.residual_l1_static(rowptr, col, CC, u, R)
+        r_oracle = oracle.residual_l1(g.rowptr, g.col, CC, g.u, R.cpu().numpy())
+        floor = 8 * 2.2e-16 * (float(u.sum()) + 2 * float(R.sum()))
+        assert abs(r_static - r_oracle) <= 1e-12 * abs(r_oracle) + floor
+
+
+def _driver():
+    """libcuda through ctypes: the device's free memory and the high-water mark
+    of its default stream-ordered pool (the pool cudaMallocAsync draws from)."""
+    cu = C.CDLL("libcuda.so.1")
+    dev = C.c_int(0)
+    assert cu.cuCtxGetDevice(C.byref(dev)) == 0
+    pool = C.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(C.byref(pool), dev) == 0
+    used_high = 8  # CU_MEMPOOL_ATTR_USED_MEM_HIGH
+
+    def reset_high():
+        zero = C.c_uint64(0)
+        assert cu.cuMemPoolSetAttribute(pool, used_high, C.byref(zero)) == 0
+
+    def high():
+        v = C.c_uint64(0)
+        assert cu.cuMemPoolGetAttribute(pool, used_high, C.byref(v)) == 0
+        return v.value
+
+    def free_bytes():
+        f, t = C.c_size_t(0), C.c_size_t(0)
+        assert cu.cuMemGetInfo_v2(C.byref(f), C.byref(t)) == 0
+        return f.value
+
+    return reset_high, high, free_bytes
+
+
+def test_static_residual_allocates_nothing(prgb):
+    """Across a call (after the first, which looks up the scratch address):
+    the default pool's high-water mark does not rise above what was in use
+    before, device free memory does not move, and torch's allocator is not
+    touched."""
+    import torch
+    g = gg.web_like(seed=23, n=100_000, n_small=2_000, layers=10, giant_layer=3)
+    rowptr = torch.from_numpy(g.rowptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    u = torch.from_numpy(g.u).cuda()
+    R = u * 3.0
+    prgb.residual_l1_static(rowptr, col, CC, u, R)  # set-up call
+    torch.cuda.synchronize()
+    reset_high, high, free_bytes = _driver()
+    reset_high()
+    h0, f0 = high(), free_bytes()
+    t0 = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    for _ in range(2):
+        prgb.residual_l1_static(rowptr, col, CC, u, R)
+    torch.cuda.synchronize()
+    assert high() == h0
+    assert free_bytes() == f0
+    assert torch.cuda.max_memory_allocated() == t0
+
+
+def test_static_residual_rejects_unsorted_rows(prgb):
+    """A repeated or out-of-order column is a malformed CSR, as for
+    pr_graph_create (every index stays in range, so the check reads in
+    bounds)."""
+    import torch
+    n = 4
+    for rp, cl in (([0, 2, 3, 4, 5], [1, 1, 2, 3, 0]),    # duplicate 0 -> 1
+                   ([0, 2, 3, 4, 5], [2, 1, 2, 3, 0])):   # unsorted row 0
+        rowptr = torch.tensor(rp, dtype=torch.int32, device="cuda")
+        col = torch.tensor(cl, dtype=torch.int32, device="cuda")
+        u = torch.full((n,), 0.25, dtype=torch.float64, device="cuda")
+        rc, _ = _static_via_abi(prgb, rowptr, col, u, u)
+        assert rc == 1
+        with pytest.raises(prgb.PrError):
+            prgb.graph(rowptr, col)
