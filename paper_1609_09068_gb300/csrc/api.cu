@@ -150,6 +150,7 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
     int32_t tc = kCtaCompMax, tb = 4, tl = 1;
     tuned_defaults(&tc, &tb, &tl);
     if (tc != P->cta_max || tb != P->coop_blocks || tl != P->balance) retune_levels(P, tc, tb, tl);
+    else split_fx_ranges(P);
   }
   if (st != PR_OK) {
     delete P->keep;

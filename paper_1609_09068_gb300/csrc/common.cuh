@@ -387,6 +387,11 @@ struct LargeComp {
 struct LevelRange {
   int32_t cbeg, clu, cta, warp, single, cend;
   int32_t clu_max;              // vertices of the largest cluster-class component
+  // FP64 solves split the cluster class: [clu, big) stays on clusters,
+  // [big, cta) (at most kFxMax vertices) goes to one 1024-thread CTA each;
+  // big_max is the largest component of [big, cta) (host-side, set by
+  // split_fx_ranges)
+  int32_t big, big_max;
   int32_t vbeg, vsingle, vend;  // permuted vertex range of the level / its singletons
   // rows of the level with more than kHeavy external in-edges: a slice of
   // the partition's external heavy-row list, and its chunk range

@@ -5,12 +5,16 @@
 //   stable radix sorts (size, then level) over the component list, which is
 //   built in ascending smallest-vertex order.
 // * Permutation: vertices ordered by (component id, wave descending,
-//   out-degree descending, vertex id).  Each component is a contiguous
-//   range; inside a CAC the wave order is a topological order (an edge
-//   v -> w inside a CAC has wave(v) > wave(w)), so runs of equal wave
-//   ("sub-levels") can be solved one after the other in a single pass, as
-//   the CAC BFS of Sec. 4.3.1 does.  The out-degree key puts the entries of
-//   z that the sweeps gather most often next to each other.
+//   internal in-degree ascending, out-degree descending, vertex id).  Each
+//   component is a contiguous range; inside a CAC the wave order is a
+//   topological order (an edge v -> w inside a CAC has wave(v) > wave(w)),
+//   so runs of equal wave ("sub-levels") can be solved one after the other
+//   in a single pass, as the CAC BFS of Sec. 4.3.1 does.  Rows of similar
+//   in-degree side by side give the 32 lanes of a warp rows of similar
+//   length, and make the in-degree-class order of the grid-wide sweeps the
+//   position order itself (their per-row reads and writes coalesce); among
+//   equal in-degrees the out-degree key puts the entries of z that the sweeps
+//   gather most often next to each other.
 // * Per permuted vertex: internal in-edges (same component) and external
 //   in-edges (from components of higher levels), both as permuted source
 //   positions in CSC order; these are the edge lists "within each component"
@@ -77,19 +81,46 @@ __global__ void comp_of_rep_k(int32_t K, const uint32_t* vals, int32_t* comp_of_
   for (int64_t k = gtid(); k < K; k += gstride()) comp_of_rep[vals[k]] = (int32_t)k;
 }
 
+// in-edges from the same final component, per vertex: with list ==
+// nullptr a thread per vertex with at most kHeavy in-edges, otherwise a warp
+// per listed vertex (the vertices with more)
+__global__ void int_indeg_k(int32_t n, const int32_t* list, const int32_t* __restrict__ iptr,
+                            const int32_t* __restrict__ iidx, const int32_t* __restrict__ crep, int32_t* icnt_v) {
+  if (!list) {
+    for (int64_t v = gtid(); v < n; v += gstride()) {
+      const int e0 = iptr[v], e1 = iptr[v + 1];
+      if (e1 - e0 > kHeavy) continue;
+      const int r = crep[v];
+      int in = 0;
+      for (int e = e0; e < e1; e++) in += crep[iidx[e]] == r;
+      icnt_v[v] = in;
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = gtid() >> 5; i < n; i += gstride() >> 5) {
+    const int v = list[i];
+    const int r = crep[v];
+    int in = 0;
+    for (int e = iptr[v] + lane; e < iptr[v + 1]; e += 32) in += crep[iidx[e]] == r;
+    in = __reduce_add_sync(0xffffffffu, in);
+    if (lane == 0) icnt_v[v] = in;
+  }
+}
+
 // Order key of a vertex inside its component: wave descending (a CAC's
-// sub-levels in topological order; one wave for all members of an SCC), then
-// out-degree descending in the low dbits bits.  z_j is gathered once per
-// out-edge of j, so the second key packs the most-gathered entries of every
-// component into a few cache lines.
+// sub-levels in topological order; one wave for all members of an SCC),
+// then internal in-degree ascending (ibits, capped), then out-degree
+// descending (obits, capped).
 __global__ void vertex_comp_k(int32_t n, const int32_t* crep, const int32_t* comp_of_rep, const int32_t* wave,
-                              int32_t maxw, const int32_t* __restrict__ outdeg, int dbits, int32_t* comp_id,
-                              uint32_t* keys, uint32_t* vals) {
-  const uint32_t dmax = (1u << dbits) - 1u;
+                              int32_t maxw, const int32_t* __restrict__ outdeg, const int32_t* __restrict__ icnt_v,
+                              int ibits, int obits, int32_t* comp_id, uint32_t* keys, uint32_t* vals) {
+  const uint32_t imax = (1u << ibits) - 1u, omax = (1u << obits) - 1u;
   for (int64_t v = gtid(); v < n; v += gstride()) {
     comp_id[v] = comp_of_rep[crep[v]];
-    const uint32_t d = min((uint32_t)outdeg[v], dmax);
-    keys[v] = ((uint32_t)(maxw - wave[v]) << dbits) | (dmax - d);
+    const uint32_t d = min((uint32_t)outdeg[v], omax);
+    const uint32_t in = min((uint32_t)icnt_v[v], imax);
+    keys[v] = ((((uint32_t)(maxw - wave[v]) << ibits) | in) << obits) | (omax - d);
     vals[v] = (uint32_t)v;
   }
 }
@@ -125,41 +156,14 @@ __global__ void sub_tables_k(int32_t n, int32_t K, const uint8_t* subflag, const
   for (int64_t c = gtid(); c < K; c += gstride()) c_sub[c] = subidx[c_off[c]];
 }
 
-// count internal / external in-edges per permuted vertex: with list ==
-// nullptr a thread per vertex with at most kHeavy in-edges, otherwise a
-// warp per listed vertex (the vertices with more)
-__global__ void edge_count_k(int32_t n, const int32_t* perm, const int32_t* pos, const int32_t* list,
-                             const int32_t* iptr, const int32_t* iidx, const int32_t* comp_id, int32_t* icnt,
-                             int32_t* ecnt) {
-  if (!list) {
-    for (int64_t p = gtid(); p < n; p += gstride()) {
-      const int v = perm[p];
-      const int e0 = iptr[v], e1 = iptr[v + 1];
-      if (e1 - e0 > kHeavy) continue;
-      const int cv = comp_id[v];
-      int in = 0;
-      for (int e = e0; e < e1; e++) in += comp_id[iidx[e]] == cv;
-      icnt[p] = in;
-      ecnt[p] = (e1 - e0) - in;
-    }
-    return;
-  }
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = gtid() >> 5, nw = gstride() >> 5;
-  for (int64_t i = w0; i < n; i += nw) {
-    const int v = list[i];
-    const int64_t p = pos[v];
-    const int cv = comp_id[v];
-    int in = 0, ex = 0;
-    for (int e = iptr[v] + lane; e < iptr[v + 1]; e += 32) {
-      if (comp_id[iidx[e]] == cv) in++; else ex++;
-    }
-    in = __reduce_add_sync(0xffffffffu, in);
-    ex = __reduce_add_sync(0xffffffffu, ex);
-    if (lane == 0) {
-      icnt[p] = in;
-      ecnt[p] = ex;
-    }
+// internal / external in-edge counts by position
+__global__ void edge_count_k(int32_t n, const int32_t* perm, const int32_t* __restrict__ iptr,
+                             const int32_t* __restrict__ icnt_v, int32_t* icnt, int32_t* ecnt) {
+  for (int64_t p = gtid(); p < n; p += gstride()) {
+    const int v = perm[p];
+    const int in = icnt_v[v];
+    icnt[p] = in;
+    ecnt[p] = (iptr[v + 1] - iptr[v]) - in;
   }
 }
 
@@ -335,9 +339,23 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   PRGB_TRY(tmp.alloc(&vvt, n));
   // the out-degree key fills the wave key's last 8-bit radix pass (at least
   // 8 bits while the wave key leaves room)
+  // internal in-degrees (from the final components) for the order key and
+  // the internal / external split below
+  int32_t* icnt_v;
+  PRGB_TRY(tmp.alloc(&icnt_v, n));
+  int_indeg_k<<<grid1(n), kBlock, 0, s>>>(n, nullptr, g.iptr, g.iidx, crep, icnt_v);
+  PRGB_LAUNCH();
+  if (g.nheavy > 0) {
+    int_indeg_k<<<gridw(g.nheavy), kBlock, 0, s>>>(g.nheavy, g.heavy_rows, g.iptr, g.iidx, crep, icnt_v);
+    PRGB_LAUNCH();
+  }
+  // the secondary keys fill the radix passes the wave key leaves: up to 8
+  // bits of in-degree and 4 of out-degree
   const int wbits = bits_for((uint32_t)max_wave);
-  const int vbits = std::min(32, (wbits + 8 + 7) / 8 * 8);
-  vertex_comp_k<<<grid1(n), kBlock, 0, s>>>(n, crep, comp_of_rep, wave, max_wave, g.outdeg, vbits - wbits,
+  const int vbits = std::min(32, (wbits + 12 + 7) / 8 * 8);
+  const int ibits = std::min(8, vbits - wbits);
+  const int obits = std::min(4, vbits - wbits - ibits);
+  vertex_comp_k<<<grid1(n), kBlock, 0, s>>>(n, crep, comp_of_rep, wave, max_wave, g.outdeg, icnt_v, ibits, obits,
                                             P->comp_id, vk, vv);
   PRGB_LAUNCH();
   PRGB_TRY(radix_sort_pairs(vk, vv, vkt, vvt, n, vbits, tmp));
@@ -378,13 +396,8 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   PRGB_TRY(build_inv(P->p_outdeg, n, keep, &P->p_inv, s));
   PRGB_TRY(keep.alloc(&P->int_ptr, (size_t)n + 1));
   PRGB_TRY(keep.alloc(&P->ext_ptr, (size_t)n + 1));
-  edge_count_k<<<grid1(n), kBlock, 0, s>>>(n, P->perm, pos, nullptr, g.iptr, g.iidx, P->comp_id, icnt, ecnt);
+  edge_count_k<<<grid1(n), kBlock, 0, s>>>(n, P->perm, g.iptr, icnt_v, icnt, ecnt);
   PRGB_LAUNCH();
-  if (g.nheavy > 0) {
-    edge_count_k<<<gridw(g.nheavy), kBlock, 0, s>>>(g.nheavy, P->perm, pos, g.heavy_rows, g.iptr, g.iidx,
-                                                    P->comp_id, icnt, ecnt);
-    PRGB_LAUNCH();
-  }
   PRGB_TRY(scan_i32(icnt, P->int_ptr, n, tmp));
   PRGB_TRY(scan_i32(ecnt, P->ext_ptr, n, tmp));
   int32_t mi = 0, me = 0;

@@ -353,7 +353,7 @@ pr_status levels_and_merge(const DevGraph& g, const int32_t* rep, int32_t* crep,
     int cp = cap;
     void* args[] = {&nn, &rep, &nsize, &pending, &key, &level_node, &wave_node, &merged, &cin_ptr, &cin_src,
                     &fa_node, &fa_chunk, &fb_node, &fb_chunk, &cp, &ctl};
-    PRGB_TRY(launch_coop((const void*)kahn_k, kBlock, 0, s, args, 2, nullptr));
+    PRGB_TRY(launch_coop((const void*)kahn_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
   }
   iota_i32_k<<<grid_t(n), kBlock, 0, s>>>(par, n);
   PRGB_LAUNCH();

@@ -316,7 +316,7 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
     int cp = cap;
     void* args[] = {&gg.optr, &gg.oidx, &gg.iptr, &gg.iidx, &nn, &rem_out, &rem_in, &state, &rep,
                     &fav, &fac, &fbv, &fbc, &cp, &ctl};
-    PRGB_TRY(launch_coop((const void*)trim_k, kBlock, 0, s, args, 2, nullptr));
+    PRGB_TRY(launch_coop((const void*)trim_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
   }
   // FW-BW from the best-connected unassigned vertex takes out the giant SCC
   {
@@ -349,7 +349,7 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
         const int32_t* need = dir == 0 ? nullptr : fw;
         int tag_need = 1;
         void* args[] = {&ptr, &idx, &nn, &pv, &rep, &mark, &tag, &need, &tag_need, &fav, &fac, &fbv, &fbc, &cp, &ctl};
-        PRGB_TRY(launch_coop((const void*)reach_k, kBlock, 0, s, args, 2, nullptr));
+        PRGB_TRY(launch_coop((const void*)reach_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
       }
       fwbw_max_k<<<grid_n(n), kBlock, 0, s>>>(n, fw, bw, bmax);
       PRGB_LAUNCH();
@@ -369,14 +369,14 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
       const int32_t* ptr = g.optr;
       const int32_t* idx = g.oidx;
       void* args[] = {&ptr, &idx, (void*)&nn, &rep, &pin, &pout, &sin, &stamp, &fav, &fac, &fbv, &fbc, &cp, &ctl};
-      PRGB_TRY(launch_coop((const void*)propagate_k, kBlock, 0, s, args, 2, nullptr));
+      PRGB_TRY(launch_coop((const void*)propagate_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
     }
     {
       PRGB_TRY(reset_ctl(ctl, s));
       const int32_t* ptr = g.iptr;
       const int32_t* idx = g.iidx;
       void* args[] = {&ptr, &idx, (void*)&nn, &rep, &sin, &mark, &tag, &fav, &fac, &fbv, &fbc, &cp, &ctl};
-      PRGB_TRY(launch_coop((const void*)root_bfs_k, kBlock, 0, s, args, 2, nullptr));
+      PRGB_TRY(launch_coop((const void*)root_bfs_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
     }
     PRGB_CUDA(cudaMemsetAsync(&ctl->cnt[7], 0, sizeof(int), s));
     assign_color_k<<<grid_n(n), kBlock, 0, s>>>(n, rep, pin, pout, sin, mark, tag, ctl);

@@ -35,21 +35,6 @@ namespace prgb {
 // z = x / outdeg as x * (1/outdeg): the reciprocal is precomputed once per
 // vertex, because FP64 division is expensive on this part.
 
-__device__ __forceinline__ bool keep_going(double s, double tau, int norm) {
-  return norm == PR_NORM_LINF ? (s >= tau) : (s > tau);
-}
-
-// The warp and CTA kernels reduce the stopping norm in FP32: FP64 shuffles
-// and adds cost more than the rows themselves on this part.  The FP32 sum
-// of n non-negative terms is within n * 2^-24 of the FP64 one, so a relative
-// margin of 1e-4 on the test keeps the FP64 norm at or below the threshold
-// whenever the series stops (it may run one iteration longer than an exact
-// test would).
-constexpr double kNormMargin = 1.0 + 1e-4;
-__device__ __forceinline__ bool keep_going32(float s, double tau, int norm) {
-  const double sd = (double)s * kNormMargin;
-  return norm == PR_NORM_LINF ? (sd >= tau) : (sd > tau);
-}
 
 // Mixed precision (the SCC series only; the gather, CACs and 1-vertex
 // components stay FP64).  Per SCC C with budget tau = tol*|C|/n:
@@ -69,33 +54,6 @@ __device__ __forceinline__ bool keep_going32(float s, double tau, int norm) {
 constexpr float kMixKappa = 8.0f * 5.9604645e-8f;  // 8 * 2^-24
 constexpr int kMixRounds = 6;
 
-// |x| as a float, from the bit pattern of the double: the sign dropped, the
-// exponent rebiased from 1023 to 127 and the mantissa cut to 23 bits
-// (rounding toward zero, relative error below 2^-23); magnitudes under the
-// float range give 0, over it the largest float.  Integer operations only,
-// so the stopping norm costs nothing on the FP64 pipe.
-__device__ __forceinline__ float abs_to_float(double x) {
-  const long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
-  const long long f = (b >> 29) - ((long long)(1023 - 127) << 23);
-  if (f <= 0) return 0.0f;
-  if (f >= 0x7f800000LL) return 3.4028235e38f;
-  return __int_as_float((int)f);
-}
-
-// A local index outside [0, sz) would mean a broken layout: record it and
-// read slot 0 instead of touching memory out of bounds.
-__device__ __forceinline__ int local_or_err(const SolveArgs& a, int q, int sz) {
-  if ((unsigned)q >= (unsigned)sz) {
-    set_err(a.ctl, PR_EINTERNAL, 301);
-    return 0;
-  }
-  return q;
-}
-
-__device__ __forceinline__ double check_u(const SolveArgs& a, double uu) {
-  if (!(uu >= 0.0) || !isfinite(uu)) set_err(a.ctl, PR_EINVAL, 300);
-  return uu;
-}
 
 // ---------------------------------------------------------------------------
 // one warp per component of 2..32 vertices, one vertex per lane.  The
@@ -1200,7 +1158,7 @@ __global__ void to_float_k(int32_t n, const double* __restrict__ x, float* __res
 }
 
 pr_status SideStreams::create() {
-  for (int q = 0; q < 3; q++) {
+  for (int q = 0; q < kSideStreams; q++) {
     PRGB_CUDA(cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking));
     PRGB_CUDA(cudaEventCreateWithFlags(&join[q], cudaEventDisableTiming));
   }
@@ -1209,7 +1167,7 @@ pr_status SideStreams::create() {
 }
 
 SideStreams::~SideStreams() {
-  for (int q = 0; q < 3; q++) {
+  for (int q = 0; q < kSideStreams; q++) {
     if (st[q]) cudaStreamDestroy(st[q]);
     if (join[q]) cudaEventDestroy(join[q]);
   }
@@ -1273,6 +1231,7 @@ pr_status set_solve_attrs(const pr_partition_s* P, bool mixed) {
   static bool cta_attr = false;
   static size_t clu_attr[4] = {48 * 1024, 48 * 1024, 48 * 1024, 48 * 1024};
   if (!cta_attr) {
+    PRGB_TRY(set_fx_attrs());
     PRGB_CUDA(cudaFuncSetAttribute(solve_lu_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmem));
     PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
     PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1409,14 +1368,17 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       ++*nl;
     }
     PRGB_CUDA(cudaEventRecord(side.fork, s));
-    bool joined[3] = {false, false, false};
-    if (r.cta > r.clu) {
+    bool joined[kSideStreams] = {false, false, false, false};
+    // FP64 solves give the components of at most kFxMax vertices of the
+    // cluster class, and the whole CTA class, to the fixed-point kernels
+    const int32_t clu_end = mixed ? r.cta : r.big;
+    if (clu_end > r.clu) {
       PRGB_CUDA(cudaStreamWaitEvent(side.st[0], side.fork, 0));
       joined[0] = true;
       const int chunk = 1 << clu_shift(r.clu_max);
       const bool push = r.clu_max <= kCluPushMax;
       const size_t smem = clu_smem(chunk, mixed, push);
-      const unsigned nb = (unsigned)(r.cta - r.clu) * kClu;
+      const unsigned nb = (unsigned)(clu_end - r.clu) * kClu;
       if (mixed && push) solve_clu_k<true, true><<<nb, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
       else if (mixed) solve_clu_k<true, false><<<nb, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
       else if (push) solve_clu_k<false, true><<<nb, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
@@ -1424,14 +1386,21 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       PRGB_LAUNCH();
       ++*nl;
     }
+    if (!mixed && r.cta > r.big) {
+      PRGB_CUDA(cudaStreamWaitEvent(side.st[3], side.fork, 0));
+      joined[3] = true;
+      PRGB_TRY(launch_fx(a, r.big, r.cta, r.big_max, true, side.st[3]));
+      ++*nl;
+    }
     if (r.warp > r.cta) {
       PRGB_CUDA(cudaStreamWaitEvent(side.st[1], side.fork, 0));
       joined[1] = true;
-      if (mixed)
+      if (mixed) {
         solve_cta_k<true><<<r.warp - r.cta, kCtaThreads, kCtaSmemMixed, side.st[1]>>>(a, r.cta);
-      else
-        solve_cta_k<false><<<r.warp - r.cta, kCtaThreads, kCtaSmem, side.st[1]>>>(a, r.cta);
-      PRGB_LAUNCH();
+        PRGB_LAUNCH();
+      } else {
+        PRGB_TRY(launch_fx(a, r.cta, r.warp, P->h_c_off[r.cta + 1] - P->h_c_off[r.cta], false, side.st[1]));
+      }
       ++*nl;
     }
     if (a.lu_threshold > 0) {
@@ -1463,7 +1432,7 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       PRGB_LAUNCH();
       ++*nl;
     }
-    for (int q = 0; q < 3; q++) {
+    for (int q = 0; q < kSideStreams; q++) {
       if (!joined[q]) continue;
       PRGB_CUDA(cudaEventRecord(side.join[q], side.st[q]));
       PRGB_CUDA(cudaStreamWaitEvent(s, side.join[q], 0));
@@ -1657,6 +1626,23 @@ void tuned_defaults(int32_t* cta_max, int32_t* coop_blocks, int32_t* balance) {
   *balance = g_tuned_balance;
 }
 
+void split_fx_ranges(pr_partition_s* P) {
+  const std::vector<int32_t>& co = P->h_c_off;
+  auto size = [&](int c) { return co[c + 1] - co[c]; };
+  for (LevelRange& r : P->levels) {
+    // sizes descend: [big, cta) are the cluster-class components of at most
+    // kFxMax vertices
+    int lo = r.clu, hi = r.cta;
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (size(mid) <= kFxMax) hi = mid;
+      else lo = mid + 1;
+    }
+    r.big = lo;
+    r.big_max = r.cta > r.big ? size(r.big) : 0;
+  }
+}
+
 void retune_levels(pr_partition_s* P, int32_t cta_max, int32_t coop_blocks, int32_t balance) {
   P->cta_max = cta_max;
   P->coop_blocks = coop_blocks;
@@ -1675,6 +1661,7 @@ void retune_levels(pr_partition_s* P, int32_t cta_max, int32_t coop_blocks, int3
     r.cta = lo;
     r.clu_max = r.cta > r.clu ? size(r.clu) : 0;
   }
+  split_fx_ranges(P);
   if (P->plan) {
     for (PlanGraph& e : P->plan->graphs) {
       if (e.exec) cudaGraphExecDestroy(e.exec);

@@ -41,6 +41,53 @@ struct SolveArgs {
   Ctl* ctl;
 };
 
+// ---------------------------------------------------------------------------
+// device helpers shared by the solve kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool keep_going(double s, double tau, int norm) {
+  return norm == PR_NORM_LINF ? (s >= tau) : (s > tau);
+}
+
+// The warp and CTA kernels reduce the stopping norm in FP32: FP64 shuffles
+// and adds cost more than the rows themselves on this part.  The FP32 sum
+// of n non-negative terms is within n * 2^-24 of the FP64 one, so a relative
+// margin of 1e-4 on the test keeps the FP64 norm at or below the threshold
+// whenever the series stops (it may run one iteration longer than an exact
+// test would).
+constexpr double kNormMargin = 1.0 + 1e-4;
+__device__ __forceinline__ bool keep_going32(float s, double tau, int norm) {
+  const double sd = (double)s * kNormMargin;
+  return norm == PR_NORM_LINF ? (sd >= tau) : (sd > tau);
+}
+
+// |x| as a float, from the bit pattern of the double: the sign dropped, the
+// exponent rebiased from 1023 to 127 and the mantissa cut to 23 bits
+// (rounding toward zero, relative error below 2^-23); magnitudes under the
+// float range give 0, over it the largest float.  Integer operations only,
+// so the stopping norm costs nothing on the FP64 pipe.
+__device__ __forceinline__ float abs_to_float(double x) {
+  const long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+  const long long f = (b >> 29) - ((long long)(1023 - 127) << 23);
+  if (f <= 0) return 0.0f;
+  if (f >= 0x7f800000LL) return 3.4028235e38f;
+  return __int_as_float((int)f);
+}
+
+// A local index outside [0, sz) would mean a broken layout: record it and
+// read slot 0 instead of touching memory out of bounds.
+__device__ __forceinline__ int local_or_err(const SolveArgs& a, int q, int sz) {
+  if ((unsigned)q >= (unsigned)sz) {
+    set_err(a.ctl, PR_EINTERNAL, 301);
+    return 0;
+  }
+  return q;
+}
+
+__device__ __forceinline__ double check_u(const SolveArgs& a, double uu) {
+  if (!(uu >= 0.0) || !isfinite(uu)) set_err(a.ctl, PR_EINVAL, 300);
+  return uu;
+}
+
 // CUDA events around the grid-wide power-series launches (opt-in timing):
 // one pair per large SCC of the partition, created before any capture
 struct KernelTiming {
@@ -50,11 +97,12 @@ struct KernelTiming {
   ~KernelTiming();
 };
 
-// three non-blocking side streams and the fork / join events of a solve
+// four non-blocking side streams and the fork / join events of a solve
+constexpr int kSideStreams = 4;
 struct SideStreams {
-  cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t st[kSideStreams] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t fork = nullptr;
-  cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t join[kSideStreams] = {nullptr, nullptr, nullptr, nullptr};
   pr_status create();
   ~SideStreams();
 };
@@ -109,6 +157,19 @@ struct SolvePlan {
   MpnnInfer inf;
   ~SolvePlan();
 };
+
+// The fixed-point series of solve_fx.cu (FP64 mode): SCCs of 33..kFxMax
+// vertices, one CTA per component -- kFxBigThreads threads for components
+// above kCtaCompMax vertices, kFxThreads up to it.
+constexpr int kFxMax = 1024;  // above it the 8-CTA clusters are faster (measured)
+constexpr int kFxBigThreads = 1024;
+constexpr int kFxThreads = 256;
+pr_status set_fx_attrs();
+// components [cbeg, cend) of one level, the largest of max_size vertices;
+// big selects the 1024-thread kernel
+pr_status launch_fx(const SolveArgs& a, int32_t cbeg, int32_t cend, int32_t max_size, bool big, cudaStream_t s);
+// host: every level's split of its cluster class at kFxMax (big, big_max)
+void split_fx_ranges(pr_partition_s* P);
 
 // Level-by-level solve of a partition with buffers of its own (used for
 // replayed iteration counts).  u and R are device pointers in the original

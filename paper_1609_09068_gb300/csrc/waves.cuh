@@ -15,6 +15,8 @@
 
 namespace prgb {
 
+constexpr int kWaveBlock = 256;      // threads per block of the wave kernels
+constexpr int kWavePerSm = 2;        // their co-resident blocks per SM
 constexpr int kSmallFrontier = 64;
 constexpr int kLocalWaves = 4096;
 
