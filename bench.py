@@ -117,6 +117,24 @@ def job_value(edges_per_rank, world, ms):
     return world * edges_per_rank / (ms * 1e-3) / 1e9
 
 
+def measured_l2_gbs(reps=40):
+    """L2 read bandwidth measured live: a 64 MiB float64 vector, resident in
+    L2 after a warm-up, summed reps times by the device reduction, bytes over
+    CUDA-event time.  The denominator of the roofline when the dominant
+    kernel's working set stays in L2 (no device constant gives it)."""
+    import torch
+    x = torch.ones(8 << 20, dtype=torch.float64, device="cuda")
+    for _ in range(5):
+        x.sum()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        x.sum()
+    b.record()
+    torch.cuda.synchronize()
+    return x.numel() * 8 * reps / (a.elapsed_time(b) * 1e-3) / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -738,16 +756,26 @@ def run_ours(args):
     d2h = u_h.nbytes
 
     # ---- roofline of the dominant SpMV kernel --------------------------------
+    # The grid-wide power series (the largest share of the solve).  On the
+    # web-like graph (n = 1M) its sweep's working set stays in the 126 MB L2
+    # (ncu: ~30 MB of DRAM traffic per launch against ~2 GB of algorithmic
+    # bytes), so the bound reported is L2 bandwidth, measured live; the
+    # fraction of HBM is kept beside it.  The 50M-vertex block reports HBM.
     peaks, peak_kind = measured_peaks()
     k_ms = float(np.mean([s["kernel_ms"] for s in stats]))
     k_bytes = float(np.mean([s["kernel_bytes"] for s in stats]))
     achieved = k_bytes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    l2 = measured_l2_gbs()
+    in_l2 = args.workload in ("web", "small")
+    peak = l2 if in_l2 else hbm
+    roofline = {"bound": "l2" if in_l2 else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_BYTES.get(args.workload),
                 "kernel": "solve_large_scc_k (grid-wide SCC power series)",
-                "peak_kind": f"{peak_kind} copy bandwidth", "kernel_ms_per_step": k_ms,
-                "algorithmic_bytes_per_step": k_bytes,
+                "peak_kind": ("L2 read bandwidth measured live (64 MiB resident vector, device reduction)"
+                              if in_l2 else f"{peak_kind} copy bandwidth"),
+                "hbm_peak": hbm, "hbm_frac": achieved / hbm, "hbm_peak_kind": f"{peak_kind} copy bandwidth",
+                "kernel_ms_per_step": k_ms, "algorithmic_bytes_per_step": k_bytes,
                 "launches_per_step": float(np.mean([s["kernel_launches"] for s in stats]))}
 
     # ---- CPU oracle on the host cores ---------------------------------------

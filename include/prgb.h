@@ -11,7 +11,10 @@
  * (SCC/CAC partition with levels, Sec. 3 Theorem 3.1 and Sec. 4.1), an
  * intermediate layout step (Sec. 4.2) and the level-by-level PageRank step
  * (Sec. 4.3).  pr_partition_create performs the first two, pr_solve the
- * third.  pr_global_power is the paper's baseline (the power series on the
+ * third.  Calls that read the graph take a prepared pr_graph handle made
+ * once from the caller's CSR by pr_graph_create (validation, loop removal
+ * and the in-adjacency are done once and shared by the partition, the
+ * global series and the residual) rather than the CSR itself.  pr_global_power is the paper's baseline (the power series on the
  * whole graph, Sec. 4.3.2) and pr_residual_l1 evaluates the residual of the
  * defining system.
  *
@@ -30,8 +33,9 @@
  *     synchronise that stream before returning.
  *   - Every call returns a pr_status.  PR_ECUDA means a CUDA runtime call
  *     failed (pr_last_cuda_error gives its code); PR_ETIMEOUT means a
- *     device-side wait reached its time limit (about two seconds) and the
- *     kernel returned early; the CUDA context stays usable after both.
+ *     device-side wait reached its time limit (two seconds unless
+ *     pr_set_wait_limit says otherwise) and the kernel returned early; the
+ *     CUDA context stays usable after both.
  *   - The library allocates device memory with cudaMallocAsync on the
  *     caller's stream and releases it the same way.
  */
@@ -145,7 +149,8 @@ typedef struct pr_solve_stats {
     int64_t kernel_bytes; /* out (timing = 1): their algorithmic bytes: per
                              sweep 4 B per edge + 40 B per row (index, z
                              gather, R read/write, z write, row pointer and
-                             out-degree), plus the inflow gather */
+                             out-degree), plus 56 B per row once per launch
+                             (the start and the end of the series) */
     int64_t kernel_launches; /* out (timing = 1): number of such launches */
     int32_t fp64_sweeps_max; /* PR_PREC_MIXED: the most FP64 residual sweeps
                                 of any SCC (included in iters_max and
@@ -167,6 +172,22 @@ typedef struct pr_solve_stats {
  * PR_ECUDA.  Synchronises the stream.
  */
 pr_status pr_graph_create(const pr_csr *csr, void *stream, pr_graph **out);
+
+/* Flags of pr_graph_create_ex. */
+#define PR_CANONICALIZE 1u /* sort every row's columns and drop repeated ones
+                              (one edge per ordered pair: the simple graph of
+                              Sec. 3) instead of rejecting the CSR */
+
+/*
+ * pr_graph_create_ex -- pr_graph_create with flags: 0 behaves exactly like
+ * pr_graph_create; PR_CANONICALIZE accepts rows with unsorted or repeated
+ * columns and builds the graph of the distinct edges (on the device: two
+ * stable radix sorts of the edges by column and by row, then a compaction).
+ * Row offsets and column ranges must still be valid.
+ * Errors: PR_EINVAL for an unknown flag, invalid offsets or a column out of
+ * range; otherwise those of pr_graph_create.  Synchronises the stream.
+ */
+pr_status pr_graph_create_ex(const pr_csr *csr, uint32_t flags, void *stream, pr_graph **out);
 
 /* Release a graph (asynchronously, on the stream it was created on, which
  * must still exist).  Partitions built on it must be destroyed first.  NULL is
@@ -287,6 +308,17 @@ pr_status pr_residual_l1(const pr_graph *g, double c, const double *u, const dou
 /* Number of kernels this library has launched in this process so far (all
  * entry points, all threads).  Lets a caller count the kernels of a region. */
 int64_t pr_launch_count(void);
+
+/*
+ * pr_set_wait_limit -- the time limit of every bounded device-side wait (the
+ * grid barriers of the persistent kernels), in microseconds, for the calls
+ * that start after it (a solve's cached graph is rebuilt for a new limit);
+ * 0 restores the default of two seconds.  When a wait reaches the limit the
+ * kernel records PR_ETIMEOUT and returns, and the call returns PR_ETIMEOUT;
+ * the CUDA context stays usable.  The paper has no counterpart: this is the
+ * library's failure detection.  Process-wide; always returns PR_OK.
+ */
+pr_status pr_set_wait_limit(uint32_t microseconds);
 
 /*
  * pr_residual_l1_static -- the same L1 residual as pr_residual_l1, for

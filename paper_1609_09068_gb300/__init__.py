@@ -23,7 +23,7 @@ import numpy as np
 __all__ = [
     "PrError", "Graph", "Partition", "graph", "partition", "solve", "global_power",
     "residual_l1", "load_library", "library_path", "launch_count", "TYPE_CAC", "TYPE_SCC",
-    "NORM_L1", "NORM_LINF", "PREC_FP64", "PREC_MIXED", "Mpnn",
+    "NORM_L1", "NORM_LINF", "PREC_FP64", "PREC_MIXED", "Mpnn", "set_wait_limit", "CANONICALIZE",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -41,10 +41,15 @@ _STATUS = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOMEM", 3: "PR_ECUDA", 4: "PR_ENO
 
 
 class PrError(RuntimeError):
-    def __init__(self, code, where):
+    """A non-OK pr_status; for PR_ECUDA, cuda_error is the cudaError_t the
+    library recorded (pr_last_cuda_error)."""
+
+    def __init__(self, code, where, cuda_error=0):
         self.code = code
         self.name = _STATUS.get(code, str(code))
-        super().__init__(f"{where}: {self.name}")
+        self.cuda_error = cuda_error
+        extra = f" (cudaError {cuda_error})" if cuda_error else ""
+        super().__init__(f"{where}: {self.name}{extra}")
 
 
 class _Csr(C.Structure):
@@ -70,6 +75,7 @@ _lib = None
 # name -> (restype, argtypes), mirroring include/prgb.h
 _SIGS = {
     "pr_graph_create": (C.c_int, [C.POINTER(_Csr), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "pr_graph_create_ex": (C.c_int, [C.POINTER(_Csr), C.c_uint32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "pr_graph_destroy": (None, [C.c_void_p]),
     "pr_partition_create": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "pr_partition_query": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -87,6 +93,7 @@ _SIGS = {
     "pr_status_str": (C.c_char_p, [C.c_int]),
     "pr_last_cuda_error": (C.c_int, []),
     "pr_launch_count": (C.c_int64, []),
+    "pr_set_wait_limit": (C.c_int, [C.c_uint32]),
     "pr_last_device_error": (C.c_int, []),
     "pr_residual_l1_static": (C.c_int, [C.POINTER(_Csr), C.c_double, C.c_void_p, C.c_void_p,
                                         C.POINTER(C.c_double), C.c_void_p]),
@@ -131,7 +138,7 @@ def load_library():
 
 def _check(rc, where):
     if rc != 0:
-        raise PrError(rc, where)
+        raise PrError(rc, where, int(_lib.pr_last_cuda_error()) if rc == 3 and _lib is not None else 0)
 
 
 def _torch():
@@ -181,10 +188,15 @@ def _dev_f64(x):
     return t.contiguous()
 
 
-class Graph:
-    """Prepared graph (``pr_graph``): validated CSR, loop-free, with CSC."""
+CANONICALIZE = 1
 
-    def __init__(self, rowptr, col, on_host=False):
+
+class Graph:
+    """Prepared graph (``pr_graph``): validated CSR, loop-free, with CSC.
+    ``canonicalize=True`` sorts the rows and drops repeated columns instead
+    of rejecting them (PR_CANONICALIZE)."""
+
+    def __init__(self, rowptr, col, on_host=False, canonicalize=False):
         lib = load_library()
         self._h = C.c_void_p()
         if on_host:
@@ -198,7 +210,7 @@ class Graph:
             keep = (rp, cl)
             csr = _Csr(rp.shape[0] - 1, cl.shape[0], rp.data_ptr(), cl.data_ptr() if cl.numel() else None, 0)
         self.n = int(csr.n)
-        rc = lib.pr_graph_create(C.byref(csr), _stream(), C.byref(self._h))
+        rc = lib.pr_graph_create_ex(C.byref(csr), CANONICALIZE if canonicalize else 0, _stream(), C.byref(self._h))
         del keep
         _check(rc, "pr_graph_create")
 
@@ -279,8 +291,8 @@ class Partition:
             pass
 
 
-def graph(rowptr, col, on_host=False):
-    return Graph(rowptr, col, on_host=on_host)
+def graph(rowptr, col, on_host=False, canonicalize=False):
+    return Graph(rowptr, col, on_host=on_host, canonicalize=canonicalize)
 
 
 def partition(g, col=None, on_host=False):
@@ -306,6 +318,12 @@ def _opts(norm, max_iter, io_on_host, replay, precision=PREC_FP64, warm=None, lu
 def launch_count():
     """Kernels launched by the library in this process so far."""
     return int(load_library().pr_launch_count())
+
+
+def set_wait_limit(microseconds):
+    """Time limit of the bounded device-side waits for later calls
+    (pr_set_wait_limit); 0 restores the default of two seconds."""
+    _check(load_library().pr_set_wait_limit(int(microseconds)), "pr_set_wait_limit")
 
 
 def _stats_dict(st):

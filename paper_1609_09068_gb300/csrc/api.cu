@@ -11,6 +11,7 @@
 
 namespace prgb {
 int last_cuda_error();
+void set_wait_limit_us(unsigned int us);
 pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wave, int32_t max_wave, Arena& tmp,
                        Ctl* ctl);
 
@@ -62,9 +63,15 @@ pr_status pr_last_device_error(void) { return prgb::take_last_status(); }
 
 int64_t pr_launch_count(void) { return (int64_t)prgb::launch_count(); }
 
-static pr_status pr_graph_create_body(const pr_csr* csr, void* stream, pr_graph** out) {
+pr_status pr_set_wait_limit(uint32_t microseconds) {
+  prgb::set_wait_limit_us(microseconds);
+  return PR_OK;
+}
+
+static pr_status pr_graph_create_body(const pr_csr* csr, uint32_t flags, void* stream, pr_graph** out) {
   if (!out) return PR_EINVAL;
   *out = nullptr;
+  if (flags & ~(uint32_t)PR_CANONICALIZE) return PR_EINVAL;
   if (!csr || csr->n < 0 || csr->nnz < 0 || csr->nnz >= ((int64_t)1 << 31)) return PR_EINVAL;
   if (csr->n > 0 && (!csr->rowptr || (csr->nnz > 0 && !csr->col))) return PR_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -83,8 +90,8 @@ static pr_status pr_graph_create_body(const pr_csr* csr, void* stream, pr_graph*
     Ctl* ctl = nullptr;
     st = tmp.alloc(&ctl, 1);
     if (st == PR_OK) {
-      cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
-      st = ingest(csr, &G->g, *G->keep, tmp, ctl);
+      st = init_ctl(ctl, s);
+      if (st == PR_OK) st = ingest(csr, flags, &G->g, *G->keep, tmp, ctl);
     }
     if (st == PR_OK) {
       int e = 0;
@@ -101,7 +108,11 @@ static pr_status pr_graph_create_body(const pr_csr* csr, void* stream, pr_graph*
 }
 
 pr_status pr_graph_create(const pr_csr* csr, void* stream, pr_graph** out) {
-  return prgb::note_status(pr_graph_create_body(csr, stream, out));
+  return prgb::note_status(pr_graph_create_body(csr, 0, stream, out));
+}
+
+pr_status pr_graph_create_ex(const pr_csr* csr, uint32_t flags, void* stream, pr_graph** out) {
+  return prgb::note_status(pr_graph_create_body(csr, flags, stream, out));
 }
 
 void pr_graph_destroy(pr_graph* g) {
@@ -139,7 +150,7 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
     if (st == PR_OK) st = tmp.alloc(&rep, (size_t)n);
     if (st == PR_OK) st = tmp.alloc(&crep, (size_t)n);
     if (st == PR_OK) st = tmp.alloc(&wave, (size_t)n);
-    if (st == PR_OK && cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess) st = PR_ECUDA;
+    if (st == PR_OK) st = init_ctl(ctl, s);
     if (st == PR_OK) st = scc_detect(P->g, rep, tmp, ctl);
     if (st == PR_OK) st = levels_and_merge(P->g, rep, crep, P->level, P->type, wave, &max_wave, tmp, ctl);
     if (st == PR_OK) st = build_layout(P, crep, wave, max_wave, tmp, ctl);
@@ -223,6 +234,7 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
   pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr, nullptr, 0};
   if (opts) o = *opts;
   if (o.max_iter <= 0) o.max_iter = 10000;
+  if (fault_hit(kFaultNoconv)) o.max_iter = 1;
   if (o.norm != PR_NORM_L1 && o.norm != PR_NORM_LINF) return PR_EINVAL;
   if (o.precision != PR_PREC_FP64 && o.precision != PR_PREC_MIXED) return PR_EINVAL;
   const bool mixed = o.precision == PR_PREC_MIXED;
@@ -261,7 +273,7 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
     const double* du = u;
     double* dR = R;
     PRGB_TRY(tmp.alloc(&ctl, 1));
-    PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    PRGB_TRY(init_ctl(ctl, s));
     PRGB_TRY(tmp.alloc(&iters, (size_t)K));
     if (K > 0) PRGB_CUDA(cudaMemsetAsync(iters, 0, (size_t)K * 4, s));
     if (K > 0) {
@@ -272,13 +284,13 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
       double *tu = nullptr, *tR = nullptr;
       PRGB_TRY(tmp.alloc(&tu, (size_t)n));
       PRGB_TRY(tmp.alloc(&tR, (size_t)n));
-      PRGB_CUDA(cudaMemcpyAsync(tu, u, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+      PRGB_COPY(cudaMemcpyAsync(tu, u, (size_t)n * 8, cudaMemcpyHostToDevice, s));
       du = tu;
       dR = tR;
     }
     PRGB_TRY(run_solve(part, c, du, tol, o.norm, o.max_iter, replay, false, o.lu_threshold, dR, iters, nullptr, tmp,
                        ctl, &launches, timing ? kt : nullptr));
-    if (o.io_on_host && n > 0) PRGB_CUDA(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    if (o.io_on_host && n > 0) PRGB_COPY(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
   }
   int flags = 0;
   PRGB_TRY(finish_sync(s, ctl, &flags));
@@ -317,11 +329,13 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
           const LargeComp& L = kt->comps[i];
           const int64_t it = h[L.c];
           // FP32 sweeps move 4 B per edge + 24 B per row (z gather and
-          // write, F read/write, row pointer, 1/outdeg in FP32)
+          // write, F read/write, row pointer, 1/outdeg in FP32); once per
+          // launch 56 B per row: the start (W, c/outdeg read, R and z
+          // written) and the end (R, 1/outdeg read, R/outdeg written)
           const int64_t it64 = mixed ? h64[L.c] : it;
           stats->kernel_bytes += it64 * (4 * (int64_t)L.m_int + 40 * (int64_t)L.size) +
                                  (it - it64) * (4 * (int64_t)L.m_int + 24 * (int64_t)L.size) +
-                                 52 * (int64_t)L.size + 12 * (int64_t)L.m_ext;
+                                 56 * (int64_t)L.size;
         }
       }
     }
@@ -369,6 +383,7 @@ static pr_status pr_global_power_body(const pr_graph* g, double c, const double*
   pr_solve_opts o = {PR_NORM_L1, 10000, PR_PREC_FP64, 0, nullptr, nullptr, 0};
   if (opts) o = *opts;
   if (o.max_iter <= 0) o.max_iter = 10000;
+  if (fault_hit(kFaultNoconv)) o.max_iter = 1;
   if (o.norm != PR_NORM_L1 && o.norm != PR_NORM_LINF) return PR_EINVAL;
   if (o.precision != PR_PREC_FP64 || o.warm_start || o.lu_threshold) return PR_EINVAL;
   int fixed = -1;
@@ -380,14 +395,14 @@ static pr_status pr_global_power_body(const pr_graph* g, double c, const double*
   Arena tmp(s);
   Ctl* ctl = nullptr;
   PRGB_TRY(tmp.alloc(&ctl, 1));
-  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  PRGB_TRY(init_ctl(ctl, s));
   const double* du = u;
   double* dR = R;
   if (o.io_on_host && n > 0) {
     double *tu = nullptr, *tR = nullptr;
     PRGB_TRY(tmp.alloc(&tu, (size_t)n));
     PRGB_TRY(tmp.alloc(&tR, (size_t)n));
-    PRGB_CUDA(cudaMemcpyAsync(tu, u, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    PRGB_COPY(cudaMemcpyAsync(tu, u, (size_t)n * 8, cudaMemcpyHostToDevice, s));
     du = tu;
     dR = tR;
   }
@@ -398,7 +413,7 @@ static pr_status pr_global_power_body(const pr_graph* g, double c, const double*
                             timing ? &kms : nullptr);
   if (st != PR_OK && st != PR_ENOCONV) return st;
   if (o.io_on_host && n > 0) {
-    PRGB_CUDA(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    PRGB_COPY(cudaMemcpyAsync(R, dR, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
     PRGB_CUDA(cudaStreamSynchronize(s));
   }
   if (stats) {

@@ -40,13 +40,32 @@ pr_status take_last_status();
     }                                                    \
   } while (0)
 
+// Host-side fault injection for tests of the failure paths (no GPU fault
+// is involved): PRGB_FAULT=alloc[:N], launch[:N] or copy[:N] makes the N-th
+// device allocation, kernel launch or host<->device copy (N = 1 by default,
+// counted from the moment the variable took its current value) report
+// failure -- PR_ENOMEM, PR_ECUDA, PR_ECUDA.  An allocation, a copy or a
+// cooperative launch is then not made; an ordinary kernel launch is reported
+// failed right after it is enqueued, as a launch error would be (the call's
+// buffers are released in stream order behind it).  PRGB_FAULT=noconv caps
+// the series at one sweep (PR_ENOCONV).
+enum FaultKind { kFaultAlloc = 0, kFaultLaunch = 1, kFaultCopy = 2, kFaultNoconv = 3 };
+bool fault_hit(FaultKind k);
+
 void count_launch();
 long long launch_count();
 void add_launches(long long d);  // kernels launched by a graph replay (or removed: captured, not run)
-#define PRGB_LAUNCH()            \
-  do {                           \
-    ::prgb::count_launch();      \
-    PRGB_CUDA(cudaGetLastError()); \
+#define PRGB_LAUNCH()                                               \
+  do {                                                              \
+    if (::prgb::fault_hit(::prgb::kFaultLaunch)) return PR_ECUDA;   \
+    ::prgb::count_launch();                                         \
+    PRGB_CUDA(cudaGetLastError());                                  \
+  } while (0)
+// a host<->device copy of the caller's data
+#define PRGB_COPY(expr)                                             \
+  do {                                                              \
+    if (::prgb::fault_hit(::prgb::kFaultCopy)) return PR_ECUDA;     \
+    PRGB_CUDA(expr);                                                \
   } while (0)
 
 // ---------------------------------------------------------------------------
@@ -59,6 +78,7 @@ void add_launches(long long d);  // kernels launched by a graph replay (or remov
 struct Ctl {
   alignas(128) int err;  // pr_status written by kernels (first error wins)
   int where;             // diagnostic: which wait expired
+  unsigned int wait_us;  // limit of each bounded wait in microseconds (0: kWaitNs)
   alignas(128) unsigned int bar_count;  // grid barrier arrivals
   alignas(128) unsigned int bar_gen;    // grid barrier releases (polled)
   int bwave[2];          // wave barriers: next wave and its frontier size,
@@ -79,12 +99,18 @@ __device__ __forceinline__ unsigned int vloadu(const unsigned int* p) {
   return *(volatile const unsigned int*)p;
 }
 
+// the time a bounded wait may take before it gives up
+__device__ __forceinline__ unsigned long long wait_limit_ns(const Ctl* ctl) {
+  const unsigned int us = *(volatile const unsigned int*)&ctl->wait_us;
+  return us ? (unsigned long long)us * 1000ull : kWaitNs;
+}
+
 __device__ __forceinline__ void set_err(Ctl* ctl, int code, int where) {
   if (atomicCAS(&ctl->err, 0, code) == 0) ctl->where = where;
 }
 
 // Grid-wide barrier for cooperative launches, with a bounded wait: after
-// kWaitNs the waiting block records PR_ETIMEOUT and leaves.  Returns false
+// wait_limit_ns the waiting block records PR_ETIMEOUT and leaves.  Returns false
 // when any block has recorded an error, so that callers can return early.
 // The Ctl block must have bar_count == 0 when the kernel starts.
 __device__ __forceinline__ bool grid_sync(Ctl* ctl, int where) {
@@ -100,14 +126,14 @@ __device__ __forceinline__ bool grid_sync(Ctl* ctl, int where) {
       __threadfence();
       atomicAdd(&ctl->bar_gen, 1u);
     } else {
-      const unsigned long long t0 = globaltimer_ns();
+      const unsigned long long t0 = globaltimer_ns(), lim = wait_limit_ns(ctl);
       for (;;) {
         // both words in flight together: one round trip per poll
         const unsigned int g = vloadu(&ctl->bar_gen);
         const int e = vload(&ctl->err);
         if (g != gen || e != 0) break;
         __nanosleep(32);
-        if (globaltimer_ns() - t0 > kWaitNs) {
+        if (globaltimer_ns() - t0 > lim) {
           set_err(ctl, PR_ETIMEOUT, where);
           break;
         }
@@ -260,6 +286,10 @@ class Arena {
   pr_status alloc(T** out, size_t count) {
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
+    if (fault_hit(kFaultAlloc)) {
+      *out = nullptr;
+      return PR_ENOMEM;
+    }
     void* p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, bytes, s_);
     if (e != cudaSuccess) {
@@ -281,6 +311,12 @@ class Arena {
   cudaStream_t s_;
   std::vector<void*> bufs_;
 };
+
+// Zero a control block and set the wait limit of this process
+// (pr_set_wait_limit) in it; only launches and memsets, so it can be captured.
+pr_status init_ctl(Ctl* ctl, cudaStream_t s);
+// the limit of pr_set_wait_limit in microseconds (0: the default kWaitNs)
+unsigned int wait_limit_us();
 
 // zero the barrier counter and the frontier counters (not the error word)
 // before a persistent launch
@@ -355,7 +391,7 @@ pr_status build_heavy(const int32_t* ptr, int32_t nrows, Arena& keep, Arena& tmp
 
 // ingest.cu: validate the CSR, drop loops, build out- and in-adjacency.
 // Buffers of g are allocated from `keep`; scratch from `tmp`.
-pr_status ingest(const pr_csr* csr, DevGraph* g, Arena& keep, Arena& tmp, Ctl* ctl);
+pr_status ingest(const pr_csr* csr, uint32_t flags, DevGraph* g, Arena& keep, Arena& tmp, Ctl* ctl);
 
 // scc.cu: rep[v] = representative (largest vertex id) of v's SCC.
 pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl);
@@ -379,6 +415,10 @@ struct LargeComp {
   int32_t m_ext;               // external in-edges
   int32_t heavy_begin, heavy_end;  // slice of the partition's heavy-row list
   int32_t chunk_begin, chunk_end;  // its chunk range
+  // SCCs: the light rows [off, off + nlight) (the heavy ones follow) as
+  // 32-row slices [sell_begin, sell_end) of the partition's SELL layout;
+  // sell_end == sell_begin when the component has none
+  int32_t nlight, sell_begin, sell_end;
 };
 
 // per level (in processing order): component ranges by class
@@ -452,6 +492,15 @@ struct pr_partition_s {
   int32_t* xlorder = nullptr;      // [n] positions by (level, external in-degree class)
   int32_t nheavy = 0, nchunks = 0;
   int32_t max_heavy = 0, max_chunks = 0;  // largest slice over the large components
+  // light rows of the grid-wide SCCs in SELL-32 form: slice s holds 32
+  // consecutive rows, its k-th in-edges side by side at
+  // sell_idx[sell_ptr[s] + 32 k + lane] (component-local sources; short rows
+  // padded with the component's size, a slot that holds 0); sell_cpre is a
+  // prefix of the slices' costs (width + 2) for balanced shares
+  int32_t* sell_ptr = nullptr;
+  int32_t* sell_idx = nullptr;
+  int32_t* sell_cpre = nullptr;
+  int32_t nsell = 0;
   std::vector<prgb::LevelRange> levels;  // host, processing order
   std::vector<int32_t> h_c_off;          // host copy of c_off [K+1]
   int32_t cta_max = prgb::kCtaCompMax;   // largest component of the one-CTA class (tunable)

@@ -79,4 +79,64 @@ __device__ __forceinline__ double from_fx(fx128 v, int F) {
   return __longlong_as_double((long long)bits);
 }
 
+// A positive double below 1 (c/outdeg) as M 2^-sh with M normalised to
+// 64 bits (top bit set), so sh >= 64; zero gives M = 0.
+struct FxMul {
+  unsigned long long M;
+  int sh;
+};
+__device__ __forceinline__ FxMul fx_mul_of(double x) {
+  FxMul r{0ULL, 64};
+  if (!(x > 0.0)) return r;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((b >> 52) & 0x7ff);
+  unsigned long long m = b & 0xfffffffffffffULL;
+  if (e) m |= 1ULL << 52;
+  else e = 1;
+  const int lz = __clzll((long long)m);
+  r.M = m << lz;
+  r.sh = 1075 - e + lz;  // x = m 2^(e - 1075) = M 2^-(1075 - e + lz)
+  return r;
+}
+
+// round(v M 2^-sh) (half away from zero), the exact product of a
+// fixed-point value and the double that f describes, rounded once: 64-bit
+// multiplies on the integer pipes, no floating point.  |result| < |v|.
+__device__ __forceinline__ fx128 fx_scale(fx128 v, FxMul f) {
+  const bool neg = v < 0;
+  const ufx128 a = neg ? (ufx128)(-v) : (ufx128)v;  // below 2^127
+  const ufx128 t0 = (ufx128)(unsigned long long)a * f.M;
+  const ufx128 t1 = (ufx128)(unsigned long long)(a >> 64) * f.M;  // below 2^127
+  // the product is hi 2^64 + w0
+  const ufx128 mid = (t0 >> 64) + (ufx128)(unsigned long long)t1;
+  const ufx128 hi = ((t1 >> 64) << 64) + mid;
+  const unsigned long long w0 = (unsigned long long)t0;
+  const int r = f.sh - 64;
+  ufx128 q;
+  if (r == 0) {
+    q = hi + (w0 >> 63);
+  } else if (r <= 127) {
+    const ufx128 h = hi >> (r - 1);  // the rounding bit is h's lowest
+    q = (h >> 1) + (h & 1);
+  } else {
+    q = 0;
+  }
+  return neg ? -(fx128)q : (fx128)q;
+}
+
+// |v| 2^-F as a float, rounded toward zero (relative error below 2^-23);
+// magnitudes under the normal float range give 0.  Integer operations only.
+__device__ __forceinline__ float fx_abs_float(fx128 v, int F) {
+  if (v == 0) return 0.0f;
+  const ufx128 a = v < 0 ? (ufx128)(-v) : (ufx128)v;
+  const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  const int e = (127 - lz) - F;  // |v| 2^-F in [2^e, 2^(e+1))
+  if (e < -126) return 0.0f;
+  if (e > 127) return 3.4028235e38f;
+  const unsigned long long top = (unsigned long long)((a << lz) >> 64);  // leading one at bit 63
+  const unsigned mant = (unsigned)(top >> 40) & 0x7fffffu;
+  return __int_as_float(((e + 127) << 23) | (int)mant);
+}
+
 }  // namespace prgb

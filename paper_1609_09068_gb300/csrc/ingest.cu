@@ -61,6 +61,97 @@ __global__ void strip_loops_k(const int32_t* __restrict__ rowptr, const int32_t*
   }
 }
 
+// ---- PR_CANONICALIZE: sort every row and drop repeated columns -------------
+// row offsets and column range are checked as in validate_rows_k (those are
+// not fixable); each edge is tagged with its row
+__global__ void edge_rows_k(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t n,
+                            int64_t nnz, uint32_t* __restrict__ ecol, uint32_t* __restrict__ erow, Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const int64_t s = rowptr[i], e = rowptr[i + 1];
+    bool bad = (s > e) || (s < 0) || (e > nnz) || (i == 0 && s != 0) || (i == n - 1 && e != nnz);
+    if (!bad) {
+      for (int64_t k = s + lane; k < e; k += 32) {
+        const int32_t c = col[k];
+        if (c < 0 || c >= n) bad = true;
+        ecol[k] = (uint32_t)c;
+        erow[k] = (uint32_t)i;
+      }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (bad && lane == 0) set_err(ctl, PR_EINVAL, 2);
+  }
+}
+
+// after the sort by (row, col): keep the first of each run of equal pairs
+__global__ void dedup_flags_k(int64_t nnz, const uint32_t* __restrict__ erow, const uint32_t* __restrict__ ecol,
+                              uint8_t* keepf, int32_t* rcnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool k = i == 0 || erow[i] != erow[i - 1] || ecol[i] != ecol[i - 1];
+    keepf[i] = k;
+    if (k) atomicAdd(&rcnt[erow[i]], 1);
+  }
+}
+
+__global__ void dedup_compact_k(int64_t nnz, const uint32_t* __restrict__ ecol, const uint8_t* __restrict__ keepf,
+                                const int32_t* __restrict__ kidx, int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
+    if (keepf[i]) out[kidx[i]] = (int32_t)ecol[i];
+}
+
+static unsigned grid_rows(int64_t n);
+
+// rowptr / col (device) -> a CSR with sorted, duplicate-free rows in tmp
+static pr_status canonicalize(const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz, Arena& tmp,
+                              Ctl* ctl, int32_t** rp_out, int32_t** col_out, int64_t* nnz_out) {
+  cudaStream_t s = tmp.stream();
+  uint32_t *ecol, *erow, *kt, *vt;
+  const size_t m1 = (size_t)(nnz > 0 ? nnz : 1);
+  PRGB_TRY(tmp.alloc(&ecol, m1));
+  PRGB_TRY(tmp.alloc(&erow, m1));
+  PRGB_TRY(tmp.alloc(&kt, m1));
+  PRGB_TRY(tmp.alloc(&vt, m1));
+  if (n > 0) {
+    edge_rows_k<<<grid_rows(n), kBlock, 0, s>>>(rowptr, col, n, nnz, ecol, erow, ctl);
+    PRGB_LAUNCH();
+  }
+  int err = 0;
+  PRGB_CUDA(cudaMemcpyAsync(&err, &ctl->err, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  if (err) return (pr_status)err;
+  const int bits = bits_for((uint32_t)(n > 0 ? n - 1 : 0));
+  // stable sorts: by column, then by row -> ordered by (row, column)
+  PRGB_TRY(radix_sort_pairs(ecol, erow, kt, vt, nnz, bits, tmp));
+  PRGB_TRY(radix_sort_pairs(erow, ecol, kt, vt, nnz, bits, tmp));
+  uint8_t* keepf;
+  int32_t *rcnt, *kidx, *rp, *cl;
+  PRGB_TRY(tmp.alloc(&keepf, m1));
+  PRGB_TRY(tmp.alloc(&rcnt, (size_t)n + 1));
+  PRGB_TRY(tmp.alloc(&kidx, m1 + 1));
+  PRGB_TRY(tmp.alloc(&rp, (size_t)n + 1));
+  PRGB_CUDA(cudaMemsetAsync(rcnt, 0, ((size_t)n + 1) * 4, s));
+  if (nnz > 0) {
+    dedup_flags_k<<<grid_rows((nnz + 7) / 8), kBlock, 0, s>>>(nnz, erow, ecol, keepf, rcnt);
+    PRGB_LAUNCH();
+  }
+  PRGB_TRY(scan_u8(keepf, kidx, nnz, tmp));
+  PRGB_TRY(scan_i32(rcnt, rp, n, tmp));
+  int32_t kept = 0;
+  PRGB_CUDA(cudaMemcpyAsync(&kept, kidx + nnz, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  PRGB_TRY(tmp.alloc(&cl, (size_t)(kept > 0 ? kept : 1)));
+  if (nnz > 0) {
+    dedup_compact_k<<<grid_rows((nnz + 7) / 8), kBlock, 0, s>>>(nnz, ecol, keepf, kidx, cl);
+    PRGB_LAUNCH();
+  }
+  *rp_out = rp;
+  *col_out = cl;
+  *nnz_out = kept;
+  return PR_OK;
+}
+
 static unsigned grid_rows(int64_t n) {
   int64_t warps_per_block = kBlock / 32;
   int64_t g = (n + warps_per_block - 1) / warps_per_block;
@@ -70,10 +161,10 @@ static unsigned grid_rows(int64_t n) {
   return (unsigned)g;
 }
 
-pr_status ingest(const pr_csr* csr, DevGraph* g, Arena& keep, Arena& tmp, Ctl* ctl) {
+pr_status ingest(const pr_csr* csr, uint32_t flags, DevGraph* g, Arena& keep, Arena& tmp, Ctl* ctl) {
   cudaStream_t s = tmp.stream();
   const int32_t n = csr->n;
-  const int64_t nnz = csr->nnz;
+  int64_t nnz = csr->nnz;
   g->n = n;
   const int32_t* rowptr = csr->rowptr;
   const int32_t* col = csr->col;
@@ -81,10 +172,16 @@ pr_status ingest(const pr_csr* csr, DevGraph* g, Arena& keep, Arena& tmp, Ctl* c
     int32_t *drp = nullptr, *dcol = nullptr;
     PRGB_TRY(tmp.alloc(&drp, (size_t)n + 1));
     PRGB_TRY(tmp.alloc(&dcol, (size_t)(nnz > 0 ? nnz : 1)));
-    PRGB_CUDA(cudaMemcpyAsync(drp, rowptr, ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, s));
-    if (nnz > 0) PRGB_CUDA(cudaMemcpyAsync(dcol, col, (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+    PRGB_COPY(cudaMemcpyAsync(drp, rowptr, ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, s));
+    if (nnz > 0) PRGB_COPY(cudaMemcpyAsync(dcol, col, (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
     rowptr = drp;
     col = dcol;
+  }
+  if (flags & PR_CANONICALIZE) {
+    int32_t *crp = nullptr, *ccol = nullptr;
+    PRGB_TRY(canonicalize(rowptr, col, n, nnz, tmp, ctl, &crp, &ccol, &nnz));
+    rowptr = crp;
+    col = ccol;
   }
   PRGB_TRY(keep.alloc(&g->outdeg, (size_t)n + 1));
   PRGB_TRY(keep.alloc(&g->optr, (size_t)n + 1));

@@ -289,6 +289,100 @@ __global__ void scc_count_k(int32_t K, const uint8_t* c_type, const int32_t* c_o
   }
 }
 
+// ---- SELL-32 form of the light rows of the grid-wide SCCs -----------------
+// Members are ordered by internal in-degree ascending, so a component's
+// light rows are [off, off + nlight) and its heavy rows the rest; a slice's
+// width is the in-degree of its last row.
+__global__ void sell_width_k(const int32_t* __restrict__ int_ptr, int32_t off, int32_t nlight, int32_t nsl,
+                             int32_t* w32, int32_t* cost) {
+  for (int64_t sl = gtid(); sl < nsl; sl += gstride()) {
+    const int last = off + (int)min((int64_t)nlight - 1, sl * 32 + 31);
+    const int w = int_ptr[last + 1] - int_ptr[last];
+    w32[sl] = 32 * w;
+    cost[sl] = w + 2;
+  }
+}
+
+// Every entry of every slice is written, including the lanes of the last
+// slice that lie past the component's light rows (their loads happen too;
+// they read the zero slot).  Each entry is a component-local index in
+// [0, pad] (pad = size: the zero slot); an internal edge from outside the
+// component would mean a broken layout and is recorded instead of stored.
+__global__ void sell_fill_k(const int32_t* __restrict__ int_ptr, const int32_t* __restrict__ int_idx, int32_t off,
+                            int32_t nlight, int32_t pad, const int32_t* __restrict__ sptr, int32_t* sell_idx,
+                            Ctl* ctl) {
+  const int64_t lanes = ((int64_t)nlight + 31) / 32 * 32;
+  for (int64_t i = gtid(); i < lanes; i += gstride()) {
+    const int r = off + (int)i;
+    const int sl = (int)(i >> 5), lane = (int)(i & 31);
+    const int b = sptr[sl] + lane, w = (sptr[sl + 1] - sptr[sl]) >> 5;
+    const bool row = i < nlight;
+    const int e0 = row ? int_ptr[r] : 0, d = row ? int_ptr[r + 1] - e0 : 0;
+    for (int k = 0; k < w; k++) {
+      int q = pad;
+      if (k < d) {
+        q = int_idx[e0 + k] - off;
+        if ((unsigned)q >= (unsigned)pad) {
+          set_err(ctl, PR_EINTERNAL, 230);
+          q = pad;
+        }
+      }
+      sell_idx[b + 32 * k] = q;
+    }
+  }
+}
+
+pr_status build_sell(pr_partition_s* P, const std::vector<int32_t>& hrows, Arena& tmp, Ctl* ctl) {
+  cudaStream_t s = tmp.stream();
+  Arena& keep = *P->keep;
+  // slices per SCC whose heavy rows are exactly its last rows
+  int32_t nsl_all = 0;
+  for (LargeComp& L : P->large) {
+    L.nlight = L.size - (L.heavy_end - L.heavy_begin);
+    L.sell_begin = L.sell_end = nsl_all;
+    bool tail = L.type == PR_TYPE_SCC && L.nlight > 0;
+    for (int32_t h = L.heavy_begin; tail && h < L.heavy_end; h++)
+      tail = hrows[h] == L.off + L.nlight + (h - L.heavy_begin);
+    if (!tail) continue;
+    L.sell_end = nsl_all + (L.nlight + 31) / 32;
+    nsl_all = L.sell_end;
+  }
+  // a light row has at most kHeavy in-edges, so the padded slices fit int32
+  // offsets whenever 32 * kHeavy * slices does; larger graphs keep the CSC
+  // sweep
+  if (nsl_all == 0 || (int64_t)32 * kHeavy * nsl_all >= ((int64_t)1 << 31)) {
+    for (LargeComp& L : P->large) L.sell_begin = L.sell_end = 0;
+    return PR_OK;
+  }
+  P->nsell = nsl_all;
+  int32_t *w32, *cost;
+  PRGB_TRY(tmp.alloc(&w32, (size_t)nsl_all + 1));
+  PRGB_TRY(tmp.alloc(&cost, (size_t)nsl_all + 1));
+  PRGB_TRY(keep.alloc(&P->sell_ptr, (size_t)nsl_all + 1));
+  PRGB_TRY(keep.alloc(&P->sell_cpre, (size_t)nsl_all + 1));
+  for (const LargeComp& L : P->large) {
+    if (L.sell_end == L.sell_begin) continue;
+    sell_width_k<<<grid1(L.sell_end - L.sell_begin), kBlock, 0, s>>>(P->int_ptr, L.off, L.nlight,
+                                                                     L.sell_end - L.sell_begin, w32 + L.sell_begin,
+                                                                     cost + L.sell_begin);
+    PRGB_LAUNCH();
+  }
+  PRGB_TRY(scan_i32(w32, P->sell_ptr, nsl_all, tmp));
+  PRGB_TRY(scan_i32(cost, P->sell_cpre, nsl_all, tmp));
+  int32_t total = 0;
+  PRGB_CUDA(cudaMemcpyAsync(&total, P->sell_ptr + nsl_all, 4, cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  PRGB_TRY(keep.alloc(&P->sell_idx, (size_t)(total > 0 ? total : 1)));
+  for (const LargeComp& L : P->large) {
+    if (L.sell_end == L.sell_begin) continue;
+    sell_fill_k<<<grid1((int64_t)(L.sell_end - L.sell_begin) * 32), kBlock, 0, s>>>(P->int_ptr, P->int_idx, L.off,
+                                                                                   L.nlight, L.size,
+                                                    P->sell_ptr + L.sell_begin, P->sell_idx, ctl);
+    PRGB_LAUNCH();
+  }
+  return PR_OK;
+}
+
 pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wave, int32_t max_wave, Arena& tmp,
                        Ctl* ctl) {
   cudaStream_t s = tmp.stream();
@@ -305,7 +399,7 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   PRGB_TRY(tmp.alloc(&isrep, n));
   PRGB_TRY(tmp.alloc(&ridx, (size_t)n + 1));
   PRGB_CUDA(cudaMemsetAsync(csize, 0, (size_t)n * 4, s));
-  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  PRGB_TRY(init_ctl(ctl, s));
   csize_k<<<grid1(n), kBlock, 0, s>>>(n, crep, P->level, csize, isrep, ctl);
   PRGB_LAUNCH();
   PRGB_TRY(scan_u8(isrep, ridx, n, tmp));
@@ -482,6 +576,7 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
       P->max_heavy = std::max(P->max_heavy, L.heavy_end - L.heavy_begin);
       P->max_chunks = std::max(P->max_chunks, L.chunk_end - L.chunk_begin);
     }
+    PRGB_TRY(build_sell(P, hrows, tmp, ctl));
   }
   // rows with many external in-edges (the inflow gather of Eq. PR:levels)
   // and the light rows of each level ordered by external in-degree class

@@ -347,7 +347,7 @@ pr_status levels_and_merge(const DevGraph& g, const int32_t* rep, int32_t* crep,
   PRGB_TRY(tmp.alloc(&fa_chunk, cap));
   PRGB_TRY(tmp.alloc(&fb_node, cap));
   PRGB_TRY(tmp.alloc(&fb_chunk, cap));
-  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  PRGB_TRY(init_ctl(ctl, s));
   {
     int32_t nn = n;
     int cp = cap;

@@ -661,7 +661,7 @@ static pr_status pr_mpnn_predict_body(const pr_mpnn* M, const pr_partition* part
   float* yp = nullptr;
   PRGB_TRY(tmp.alloc(&ctl, 1));
   PRGB_TRY(tmp.alloc(&yp, (size_t)n + 1));
-  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  PRGB_TRY(init_ctl(ctl, s));
   PRGB_TRY(mp_pass(const_cast<pr_mpnn*>(M), part, c, u, R, false, yp, loss, tmp, ctl));
   if (yhat && n > 0) {
     mp_unperm_k<<<mp_grid(n, kBlock), kBlock, 0, s>>>(n, part->perm, yp, yhat);
@@ -683,7 +683,7 @@ static pr_status pr_mpnn_loss_grad_body(pr_mpnn* M, const pr_partition* part, do
   Arena tmp(s);
   Ctl* ctl = nullptr;
   PRGB_TRY(tmp.alloc(&ctl, 1));
-  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  PRGB_TRY(init_ctl(ctl, s));
   PRGB_CUDA(cudaMemsetAsync(M->grad, 0, kMpParams * 4, s));
   PRGB_TRY(mp_pass(M, part, c, u, R, true, nullptr, loss, tmp, ctl));
   if (grad_host) {
@@ -707,7 +707,7 @@ static pr_status pr_mpnn_train_step_body(pr_mpnn* M, const pr_partition* part, d
   Arena tmp(s);
   Ctl* ctl = nullptr;
   PRGB_TRY(tmp.alloc(&ctl, 1));
-  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  PRGB_TRY(init_ctl(ctl, s));
   PRGB_CUDA(cudaMemsetAsync(M->grad, 0, kMpParams * 4, s));
   PRGB_TRY(mp_pass(M, part, c, u, R, true, nullptr, loss, tmp, ctl));
   M->step++;

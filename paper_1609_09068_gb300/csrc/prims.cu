@@ -1,7 +1,12 @@
 // prims.cu -- scan, stable radix sort and launch helpers used by the
 // partitioner and the layout step (Sec. 4.2 notes that sorting by level and
 // size can be done without comparisons; a radix sort is that kind of sort).
+#include <stdlib.h>
+#include <string.h>
+
 #include <atomic>
+#include <mutex>
+#include <string>
 
 #include "common.cuh"
 #include "spmv.cuh"
@@ -29,6 +34,52 @@ pr_status take_last_status() {
 }
 int last_cuda_error() { return g_last_cuda_error; }
 
+// PRGB_FAULT: the spec as last seen, and the events counted since
+static std::mutex g_fault_mu;
+static std::string g_fault_spec;
+static long long g_fault_seen[4] = {0, 0, 0, 0};
+
+bool fault_hit(FaultKind k) {
+  const char* env = getenv("PRGB_FAULT");
+  if (!env || !*env) {
+    if (!g_fault_spec.empty()) {
+      std::lock_guard<std::mutex> lock(g_fault_mu);
+      g_fault_spec.clear();
+    }
+    return false;
+  }
+  std::lock_guard<std::mutex> lock(g_fault_mu);
+  if (g_fault_spec != env) {
+    g_fault_spec = env;
+    for (long long& c : g_fault_seen) c = 0;
+  }
+  static const char* const names[4] = {"alloc", "launch", "copy", "noconv"};
+  const size_t len = strlen(names[k]);
+  if (g_fault_spec.compare(0, len, names[k]) != 0 ||
+      (g_fault_spec.size() > len && g_fault_spec[len] != ':'))
+    return false;
+  if (k == kFaultNoconv) return true;
+  long long nth = 1;
+  if (g_fault_spec.size() > len + 1) nth = atoll(g_fault_spec.c_str() + len + 1);
+  return ++g_fault_seen[k] == (nth > 0 ? nth : 1);
+}
+
+static std::atomic<unsigned int> g_wait_us{0};
+unsigned int wait_limit_us() { return g_wait_us.load(std::memory_order_relaxed); }
+void set_wait_limit_us(unsigned int us) { g_wait_us.store(us, std::memory_order_relaxed); }
+
+__global__ void set_wait_k(Ctl* ctl, unsigned int us) { ctl->wait_us = us; }
+
+pr_status init_ctl(Ctl* ctl, cudaStream_t s) {
+  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  const unsigned int us = wait_limit_us();
+  if (us) {
+    set_wait_k<<<1, 1, 0, s>>>(ctl, us);
+    PRGB_LAUNCH();
+  }
+  return PR_OK;
+}
+
 int num_sms() {
   static int cached[64] = {0};
   int dev = 0;
@@ -50,6 +101,7 @@ pr_status launch_coop(const void* kernel, int block, size_t smem, cudaStream_t s
   if (max_per_sm > 0 && per_sm > max_per_sm) per_sm = max_per_sm;
   const int grid = per_sm * num_sms();
   if (grid_out) *grid_out = grid;
+  if (fault_hit(kFaultLaunch)) return PR_ECUDA;
   PRGB_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(block), args, smem, s));
   count_launch();
   return PR_OK;

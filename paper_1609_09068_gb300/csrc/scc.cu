@@ -309,7 +309,7 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
   PRGB_TRY(tmp.alloc(&stamp, n));
   PRGB_CUDA(cudaMemsetAsync(pin, 0xff, (size_t)n * 4, s));
   PRGB_CUDA(cudaMemsetAsync(pout, 0xff, (size_t)n * 4, s));
-  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  PRGB_TRY(init_ctl(ctl, s));
   {
     DevGraph gg = g;
     int32_t nn = n;

@@ -27,6 +27,7 @@
 #include "mpnn.cuh"
 #include "solve.cuh"
 #include "spmv.cuh"
+#include "warp_solve.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -36,203 +37,17 @@ namespace prgb {
 // vertex, because FP64 division is expensive on this part.
 
 
-// Mixed precision (the SCC series only; the gather, CACs and 1-vertex
-// components stay FP64).  Per SCC C with budget tau = tol*|C|/n:
-//   1. the series P_0 = W, P_{k+1} = c A^T P_k, F = sum P_k in FP32 values
-//      and FP32 accumulation, until the FP32 norm of P falls to
-//      max(tau, kMixKappa * ||W||_1): below that FP32 rounding of F
-//      dominates what further terms would add;
-//   2. R += F in FP64 and the FP64 residual r = W + c A^T (R/outdeg) - R,
-//      its L1 norm rho; done when rho <= tau;
-//   3. otherwise solve (I - c A^T) D = r by the same series in FP32 from
-//      P_0 = r (signed), until the FP32 norm of P falls to
-//      max(tau/2, kMixKappa * rho); F = D, back to 2.
-// Each FP32 pass gains about six digits, so one or two rounds of 2-3 meet
-// any budget above ~1e-13 ||R||_1; after kMixRounds residuals above tau the
-// component is reported as not converged (PR_ENOCONV).  The final per-SCC
-// residual check is FP64, so the L1 residual budget holds as in FP64 mode.
-constexpr float kMixKappa = 8.0f * 5.9604645e-8f;  // 8 * 2^-24
-constexpr int kMixRounds = 6;
-
-
-// ---------------------------------------------------------------------------
-// one warp per component of 2..32 vertices, one vertex per lane.  The
-// component's internal in-edges (at most 32*31) are staged in shared memory
-// as 8-bit local indices, so each series iteration reads shared memory only.
-// ---------------------------------------------------------------------------
-constexpr int kWarpEdges = kWarpCompMax * (kWarpCompMax - 1);
 constexpr int kWarpBlock = 64;  // two components per block, spread over many SMs
-
-// FP32 series with FP64 residual refinement (see kMixKappa) for one warp's
-// component; W is this lane's weight.  Returns the result R of this lane and
-// counts the sweeps in *k (all) and *k64 (FP64 residual sweeps).
-__device__ double warp_series_mixed(const SolveArgs& a, bool act, double W, double inv, const uint8_t* ix, int ib,
-                                    int ie, double* z, float* zf, double tau, int* k, int* k64, bool warm,
-                                    double R0) {
-  const int lane = threadIdx.x & 31;
-  const float cf = (float)a.c;
-  const float invf = (float)inv;
-  float F = act ? (float)W : 0.0f;
-  if (act) zf[lane] = (float)(W * inv);
-  const double wsum = group_sum<32>(act ? W : 0.0);
-  float thr = (float)fmax(tau, (double)kMixKappa * wsum);
-  double R = 0.0;
-  if (warm) {  // start from the guess: straight to its FP64 residual
-    R = act ? R0 : 0.0;
-    F = 0.0f;
-  }
-  bool skip = warm;
-  int rounds = 0;
-  __syncwarp();
-  for (;;) {
-    for (; !skip;) {
-      float acc0 = 0.0f, acc1 = 0.0f;
-      int e = ib;
-      for (; e + 1 < ie; e += 2) {
-        acc0 += zf[ix[e]];
-        acc1 += zf[ix[e + 1]];
-      }
-      if (e < ie) acc0 += zf[ix[e]];
-      const float pn = cf * (acc0 + acc1);
-      __syncwarp();
-      if (act) {
-        zf[lane] = pn * invf;
-        F += pn;
-      }
-      __syncwarp();
-      ++*k;
-      if (group_sumf<32>(fabsf(pn)) <= thr) break;
-      if (*k >= a.max_iter) {
-        if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
-        return R + (double)F;
-      }
-    }
-    skip = false;
-    R += (double)F;
-    if (act) z[lane] = R * inv;
-    __syncwarp();
-    double acc = 0.0;
-    for (int e = ib; e < ie; e++) acc += z[ix[e]];
-    const double r = act ? W + a.c * acc - R : 0.0;
-    ++*k;
-    ++*k64;
-    const double rho = group_sum<32>(fabs(r));
-    if (rho <= tau) break;
-    if (++rounds >= kMixRounds || *k >= a.max_iter) {
-      if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
-      break;
-    }
-    F = (float)r;
-    __syncwarp();  // every lane has read z before the next residual rewrites it
-    if (act) zf[lane] = (float)(r * inv);
-    thr = fmaxf(0.5f * (float)tau, kMixKappa * (float)rho);
-    __syncwarp();
-  }
-  return R;
-}
 
 template <bool kMixed>
 __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t cbeg, int32_t cend) {
   __shared__ double zsh[kWarpBlock / 32][32];
   __shared__ float zfsh[kWarpBlock / 32][32];
   __shared__ uint8_t ish[kWarpBlock / 32][kWarpEdges];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int wib = threadIdx.x >> 5;
   const int c = cbeg + (int)blockIdx.x * (kWarpBlock / 32) + wib;
   if (c >= cend) return;  // warp-uniform
-  double* z = zsh[wib];
-  uint8_t* ix = ish[wib];
-  const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
-  if (sz < a.lu_threshold && a.c_type[c] == PR_TYPE_SCC) return;  // solved by solve_lu_k (warp-uniform)
-  const bool act = lane < sz;
-  const int p = off + lane;
-  const double inv = act ? a.p_inv[p] : 0.0;
-  const int ib0 = a.int_ptr[off];
-  const int m = a.int_ptr[off + sz] - ib0;
-  for (int e = lane; e < m && e < kWarpEdges; e += 32) ix[e] = (uint8_t)local_or_err(a, a.int_idx[ib0 + e] - off, sz);
-  if (m > kWarpEdges) set_err(a.ctl, PR_EINTERNAL, 302);
-  const double W = act ? a.W[p] : 0.0;
-  const int ib = act ? a.int_ptr[p] - ib0 : 0, ie = act ? min(a.int_ptr[p + 1] - ib0, kWarpEdges) : 0;
-  __syncwarp();
-  double R = W;
-  int k = 0, k64 = 0;
-  if (a.c_type[c] == PR_TYPE_CAC) {
-    const int sb = a.c_sub[c], se = a.c_sub[c + 1];
-    for (int s = sb; s < se; s++) {
-      const int lo = a.sub_ptr[s], hi = a.sub_ptr[s + 1];
-      if (act && p >= lo && p < hi) {
-        double acc = 0.0;
-        for (int e = ib; e < ie; e++) acc += z[ix[e]];
-        R = W + a.c * acc;
-        z[lane] = R * inv;
-      }
-      __syncwarp();
-    }
-  } else if (kMixed) {
-    const double tau = a.tol * (double)sz / (double)a.n;
-    const bool warm = a.R0 != nullptr;
-    R = warp_series_mixed(a, act, W, inv, ix, ib, ie, z, zfsh[wib], tau, &k, &k64, warm, warm && act ? a.R0[p] : 0.0);
-  } else {
-    const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
-    const int fixed = a.replay ? a.replay[c] : -1;
-    // z holds c P / outdeg, so that the in-edge sum is the next term itself
-    const double civ = a.c * inv;
-    if (a.R0) {
-      // warm start: R = R0 + r, the series continues from the residual
-      // r = W + c A^T(R0/outdeg) - R0 (signed)
-      const double r0 = act ? a.R0[p] : 0.0;
-      if (act) z[lane] = r0 * civ;
-      __syncwarp();
-      double acc = 0.0;
-      for (int e = ib; e < ie; e++) acc += z[ix[e]];
-      const double r = act ? W + acc - r0 : 0.0;
-      __syncwarp();
-      R = r0 + r;
-      if (act) z[lane] = r * civ;
-      k = 1;
-    } else if (act) {
-      z[lane] = W * civ;
-    }
-    __syncwarp();
-    for (;;) {
-      // four partial sums: shorter chains of dependent loads and FP64 adds
-      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-      int e = ib;
-      for (; e + 3 < ie; e += 4) {
-        acc0 += z[ix[e]];
-        acc1 += z[ix[e + 1]];
-        acc2 += z[ix[e + 2]];
-        acc3 += z[ix[e + 3]];
-      }
-      for (; e < ie; e++) acc0 += z[ix[e]];
-      const double pn = (acc0 + acc1) + (acc2 + acc3);
-      __syncwarp();
-      if (act) {
-        z[lane] = pn * civ;
-        R += pn;
-      }
-      __syncwarp();
-      k++;
-      if (fixed >= 0) {
-        if (k >= fixed) break;
-        continue;
-      }
-      const float pf = abs_to_float(pn);  // terms are signed after a warm start
-      const float s = a.norm == PR_NORM_L1 ? group_sumf<32>(pf) : group_maxf<32>(pf);
-      if (!keep_going32(s, tau, a.norm)) break;
-      if (k >= a.max_iter) {
-        if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
-        break;
-      }
-    }
-  }
-  if (act) {
-    a.R[p] = R;
-    a.zr[p] = R * inv;
-  }
-  if (lane == 0) {
-    a.iters[c] = k;
-    if (kMixed) a.iters64[c] = k64;
-  }
+  warp_component<kMixed>(a, c, zsh[wib], zfsh[wib], ish[wib]);
 }
 
 // ---------------------------------------------------------------------------
@@ -939,6 +754,15 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
     balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, 0, l1, fin, val, lr0, lr1);
     k = 1;
   }
+  // light rows in SELL-32 slices when the layout has them: this warp's
+  // share of the component's slices, balanced by cost
+  const bool sell = L.sell_end > L.sell_begin;
+  int ls0 = 0, ls1 = 0;
+  if (sell) warp_slice_range(a.sell_cpre + L.sell_begin, L.sell_end - L.sell_begin, &ls0, &ls1);
+  if (sell && blockIdx.x == 0 && threadIdx.x == 0) {
+    zA[sz] = 0.0;  // the slot padded entries read
+    zB[sz] = 0.0;
+  }
   if (!grid_sync(a.ctl, 310)) return;
   const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
   const int fixed = a.replay ? a.replay[L.c] : -1;
@@ -954,7 +778,13 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeCo
       return fabs(pn);
     };
     auto val = [&](int e) -> double { return cur[local_or_err(a, a.int_idx[e] - off, sz)]; };
-    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, k & 1, l1, fin, val, lr0, lr1);
+    if (sell) {
+      balanced_sweep(a.int_ptr, lorder, 0, hv, hs, k & 1, l1, fin, val, 0, 0);  // heavy rows only
+      auto sval = [&](int q) -> double { return cur[q]; };  // q <= sz by construction of the slices
+      sell_rows(a.sell_ptr + L.sell_begin, a.sell_idx, ls0, ls1, off, L.nlight, sval, fin);
+    } else {
+      balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, k & 1, l1, fin, val, lr0, lr1);
+    }
     const double bs = l1 ? block_sum(local, red) : block_max(local, red);
     double* slot = part + (size_t)(k & 1) * gridDim.x;
     if (threadIdx.x == 0) slot[blockIdx.x] = bs;
@@ -1003,8 +833,17 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_mx_k(SolveArgs a, Larg
   const float cf = (float)a.c;
   int lr0 = -1, lr1 = -1;  // this warp's light rows, balanced by cost
   if (a.lpre) warp_row_range(a.lpre + off, nlight, &lr0, &lr1);
+  // the two FP32 z vectors, each with one more slot: the zero that padded
+  // SELL entries read
   float* const zf0 = fz;
-  float* const zf1 = fz + sz;
+  float* const zf1 = fz + sz + 1;
+  const bool sell = L.sell_end > L.sell_begin;
+  int ls0 = 0, ls1 = 0;
+  if (sell) warp_slice_range(a.sell_cpre + L.sell_begin, L.sell_end - L.sell_begin, &ls0, &ls1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    zf0[sz] = 0.0f;
+    zf1[sz] = 0.0f;
+  }
   double wl = 0.0;
   const bool warm = a.R0 != nullptr;  // start from the guess's residual
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1034,7 +873,13 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_mx_k(SolveArgs a, Larg
         return (double)fabsf(pn);
       };
       auto val = [&](int e) -> float { return cur[local_or_err(a, a.int_idx[e] - off, sz)]; };
-      balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, slot & 1, true, fin, val, lr0, lr1);
+      if (sell) {
+        balanced_sweep(a.int_ptr, lorder, 0, hv, hs, slot & 1, true, fin, val, 0, 0);  // heavy rows only
+        auto sval = [&](int q) -> float { return cur[q]; };  // q <= sz by construction of the slices
+        sell_rows(a.sell_ptr + L.sell_begin, a.sell_idx, ls0, ls1, off, L.nlight, sval, fin);
+      } else {
+        balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, slot & 1, true, fin, val, lr0, lr1);
+      }
       double s = grid_fold(a, part, slot & 1, local, red, 331);
       if (s < 0.0) return;
       if (hv.nheavy > 0) s += __ldcg(&hs.total[slot & 1]);
@@ -1206,12 +1051,14 @@ pr_status alloc_solve_bufs(const pr_partition_s* P, bool mixed, Arena& a, SolveB
   PRGB_TRY(a.alloc(&b->R, n));
   PRGB_TRY(a.alloc(&b->zr, n));
   PRGB_TRY(a.alloc(&b->W, n));
+  PRGB_TRY(a.alloc(&b->lvl_ctr, 4 * P->levels.size() + 4));
   // shared by the level gathers and the grid-wide series (left zeroed after each)
   PRGB_TRY(alloc_heavy_scratch(&b->hs, std::max(P->max_heavy, P->max_xheavy), std::max(P->max_chunks, P->max_xchunks),
                                a));
   if (P->max_large > 0) {
-    PRGB_TRY(a.alloc(&b->zA, P->max_large));
-    PRGB_TRY(a.alloc(&b->zB, P->max_large));
+    // one slot more: the zero that padded SELL entries read
+    PRGB_TRY(a.alloc(&b->zA, (size_t)P->max_large + 1));
+    PRGB_TRY(a.alloc(&b->zB, (size_t)P->max_large + 1));
     PRGB_TRY(a.alloc(&b->part, (size_t)2 * num_sms() * 8));
     PRGB_TRY(a.alloc(&b->civ, (size_t)n + 1));
   }
@@ -1233,7 +1080,6 @@ pr_status set_solve_attrs(const pr_partition_s* P, bool mixed) {
   if (!cta_attr) {
     PRGB_TRY(set_fx_attrs());
     PRGB_CUDA(cudaFuncSetAttribute(solve_lu_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmem));
-    PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmem));
     PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kCtaSmemMixed));
     cta_attr = true;
@@ -1285,6 +1131,9 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
   a.xlorder = P->xlorder;
   a.p_invf = b.invf;
   a.civ = b.civ;
+  a.sell_ptr = P->sell_ptr;
+  a.sell_idx = P->sell_idx;
+  a.sell_cpre = P->sell_cpre;
   a.R0 = nullptr;
   a.lu_threshold = 0;
   a.iters64 = iters64;
@@ -1310,6 +1159,7 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
   double* part = b.part;
   HeavyScratch hs = b.hs;
   size_t li_large = 0, ti = 0;
+  if (!mixed) PRGB_CUDA(cudaMemsetAsync(b.lvl_ctr, 0, (4 * P->levels.size() + 4) * sizeof(int32_t), s));
   if (b.civ && P->g.n > 0) {
     // c / outdeg for the grid-wide series of this solve's c
     scale_k<<<grid_cap((P->g.n + kBlock - 1) / kBlock), kBlock, 0, s>>>(P->g.n, a.c, P->p_inv, b.civ);
@@ -1386,21 +1236,11 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       PRGB_LAUNCH();
       ++*nl;
     }
-    if (!mixed && r.cta > r.big) {
-      PRGB_CUDA(cudaStreamWaitEvent(side.st[3], side.fork, 0));
-      joined[3] = true;
-      PRGB_TRY(launch_fx(a, r.big, r.cta, r.big_max, true, side.st[3]));
-      ++*nl;
-    }
-    if (r.warp > r.cta) {
+    if (mixed && r.warp > r.cta) {
       PRGB_CUDA(cudaStreamWaitEvent(side.st[1], side.fork, 0));
       joined[1] = true;
-      if (mixed) {
-        solve_cta_k<true><<<r.warp - r.cta, kCtaThreads, kCtaSmemMixed, side.st[1]>>>(a, r.cta);
-        PRGB_LAUNCH();
-      } else {
-        PRGB_TRY(launch_fx(a, r.cta, r.warp, P->h_c_off[r.cta + 1] - P->h_c_off[r.cta], false, side.st[1]));
-      }
+      solve_cta_k<true><<<r.warp - r.cta, kCtaThreads, kCtaSmemMixed, side.st[1]>>>(a, r.cta);
+      PRGB_LAUNCH();
       ++*nl;
     }
     if (a.lu_threshold > 0) {
@@ -1420,16 +1260,18 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
         ++*nl;
       }
     }
-    if (r.single > r.warp) {
+    if (mixed && r.single > r.warp) {
       const int nw = r.single - r.warp;
       PRGB_CUDA(cudaStreamWaitEvent(side.st[2], side.fork, 0));
       joined[2] = true;
       const unsigned nb = (nw + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
-      if (mixed)
-        solve_warp_k<true><<<nb, kWarpBlock, 0, side.st[2]>>>(a, r.warp, r.single);
-      else
-        solve_warp_k<false><<<nb, kWarpBlock, 0, side.st[2]>>>(a, r.warp, r.single);
+      solve_warp_k<true><<<nb, kWarpBlock, 0, side.st[2]>>>(a, r.warp, r.single);
       PRGB_LAUNCH();
+      ++*nl;
+    }
+    if (!mixed && r.single > r.big) {
+      // every component of at most kFxMax vertices: one persistent launch
+      PRGB_TRY(launch_level(a, r, b.lvl_ctr + 4 * li, s));
       ++*nl;
     }
     for (int q = 0; q < kSideStreams; q++) {
@@ -1490,7 +1332,7 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
                               bool mixed, bool timing, const pr_mpnn_s* warm, int lu, PlanGraph** out) {
   for (PlanGraph& e : pl->graphs)
     if (e.c == c && e.tol == tol && e.norm == norm && e.max_iter == max_iter && e.mixed == mixed &&
-        e.timing == timing && e.warm_uid == (warm ? warm->uid : 0) && e.lu == lu) {
+        e.timing == timing && e.warm_uid == (warm ? warm->uid : 0) && e.lu == lu && e.wait_us == wait_limit_us()) {
       e.last_use = ++pl->uses;
       *out = &e;
       return PR_OK;
@@ -1549,10 +1391,11 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
   int64_t nl = 0;
   PRGB_CUDA(cudaStreamBeginCapture(pl->cs, cudaStreamCaptureModeThreadLocal));
   pr_status st = PR_OK;
-  if (cudaMemsetAsync(pl->ctl, 0, sizeof(Ctl), pl->cs) != cudaSuccess ||
+  if (init_ctl(pl->ctl, pl->cs) != PR_OK ||
       cudaMemsetAsync(pl->iters, 0, ((size_t)K + 1) * 4, pl->cs) != cudaSuccess ||
       cudaMemsetAsync(pl->iters64, 0, ((size_t)K + 1) * 4, pl->cs) != cudaSuccess)
     st = PR_ECUDA;
+  if (st == PR_OK && wait_limit_us()) nl++;  // the kernel that sets the wait limit
   if (st == PR_OK)
     st = enqueue_levels(P, a, pl->b, mixed, pl->side, pl->cs, timing ? &pl->kt : nullptr, &nl, warm, &pl->inf);
   cudaGraph_t g = nullptr;
@@ -1579,6 +1422,7 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
   e.timing = timing;
   e.warm_uid = warm ? warm->uid : 0;
   e.lu = lu;
+  e.wait_us = wait_limit_us();
   e.last_use = ++pl->uses;
   pl->graphs.push_back(e);
   *out = &pl->graphs.back();
@@ -1600,14 +1444,14 @@ pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_hos
   // the plan's buffers are reused: order this call after the previous one
   PRGB_CUDA(cudaStreamWaitEvent(s, pl->done, 0));
   if (n > 0)
-    PRGB_CUDA(cudaMemcpyAsync(pl->u, u, (size_t)n * 8, u_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+    PRGB_COPY(cudaMemcpyAsync(pl->u, u, (size_t)n * 8, u_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                               s));
   PRGB_CUDA(cudaGraphLaunch(ge->exec, s));
   add_launches(ge->nodes);
   int64_t nl = ge->nodes;
   if (R_on_host) {
     PRGB_TRY(scatter_out(P, pl->b.R, pl->Rout, s, &nl));
-    if (n > 0) PRGB_CUDA(cudaMemcpyAsync(R, pl->Rout, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    if (n > 0) PRGB_COPY(cudaMemcpyAsync(R, pl->Rout, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
   } else {
     PRGB_TRY(scatter_out(P, pl->b.R, R, s, &nl));
   }

@@ -32,6 +32,9 @@ struct SolveArgs {
   const float* p_invf;      // [n] 1/outdeg in FP32 (mixed precision only)
   const double* R0;         // [n] warm-start guess by position for SCC rows, or nullptr
   const double* civ;        // [n] c / outdeg by position (grid-wide series), or nullptr
+  const int32_t* sell_ptr;  // SELL-32 slices of the grid-wide SCCs' light rows (see pr_partition_s)
+  const int32_t* sell_idx;
+  const int32_t* sell_cpre;
   int lu_threshold;         // SCCs with fewer vertices are solved by dense elimination
   int32_t* iters64;         // [K] FP64 residual sweeps per SCC (mixed only)
   double* W;                // [n] inflow-adjusted weights by position
@@ -118,6 +121,7 @@ struct SolveBufs {
   double* part = nullptr;
   float* invf = nullptr;
   double* civ = nullptr;  // c / outdeg (when there are grid-wide components)
+  int32_t* lvl_ctr = nullptr;  // [4 * levels] claim counters of the level kernels
 };
 
 // one captured level loop and the parameters it was captured for
@@ -130,6 +134,7 @@ struct PlanGraph {
   bool mixed = false, timing = false;
   uint64_t warm_uid = 0;  // the warm-start network's id (0: none)
   int lu = 0;
+  unsigned int wait_us = 0;  // the wait limit captured in the graph
   uint64_t last_use = 0;
 };
 constexpr int kPlanGraphs = 4;
@@ -158,16 +163,15 @@ struct SolvePlan {
   ~SolvePlan();
 };
 
-// The fixed-point series of solve_fx.cu (FP64 mode): SCCs of 33..kFxMax
-// vertices, one CTA per component -- kFxBigThreads threads for components
-// above kCtaCompMax vertices, kFxThreads up to it.
+// FP64 solves: every component of a level with at most kFxMax vertices
+// (SCCs by the fixed-point series, CACs and the warp class as elsewhere) in
+// one persistent launch of solve_fx.cu (solve_level_k); larger ones keep the
+// cluster and grid-wide kernels.
 constexpr int kFxMax = 1024;  // above it the 8-CTA clusters are faster (measured)
-constexpr int kFxBigThreads = 1024;
-constexpr int kFxThreads = 256;
 pr_status set_fx_attrs();
-// components [cbeg, cend) of one level, the largest of max_size vertices;
-// big selects the 1024-thread kernel
-pr_status launch_fx(const SolveArgs& a, int32_t cbeg, int32_t cend, int32_t max_size, bool big, cudaStream_t s);
+// the level's components [big, single) in one launch on s; ctr: three claim
+// counters of this level, zero when the launch starts
+pr_status launch_level(const SolveArgs& a, const LevelRange& r, int32_t* ctr, cudaStream_t s);
 // host: every level's split of its cluster class at kFxMax (big, big_max)
 void split_fx_ranges(pr_partition_s* P);
 

@@ -196,4 +196,37 @@ __device__ __forceinline__ void balanced_sweep(const int32_t* __restrict__ ptr, 
   }
 }
 
+// The warp's share of slices [0, nsl) when each slice costs cpre[s+1] -
+// cpre[s] (cpre[0] is the base of the component's part of the prefix).
+__device__ __forceinline__ void warp_slice_range(const int32_t* __restrict__ cpre, int nsl, int* s0, int* s1) {
+  warp_row_range(cpre, nsl, s0, s1);
+}
+
+// Light rows in SELL-32 form (one warp per 32-row slice, the k-th in-edges
+// of the slice's rows side by side): slice s covers rows r0 + 32 s + lane,
+// the first nrows of them exist.  The index loads of a warp are one
+// contiguous 128-byte line and its per-row reads and writes (fin) are
+// consecutive; padding entries point at a z slot that holds 0.
+template <class Fin, class Val>
+__device__ __forceinline__ void sell_rows(const int32_t* __restrict__ sptr, const int32_t* __restrict__ sidx, int s0,
+                                          int s1, int r0, int nrows, Val val, Fin fin) {
+  const int lane = threadIdx.x & 31;
+  using T = decltype(val(0));
+  for (int s = s0; s < s1; s++) {
+    const int b = sptr[s], w = (sptr[s + 1] - b) >> 5;
+    const int32_t* p = sidx + b + lane;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int k = 0;
+    for (; k + 3 < w; k += 4) {
+      a0 += val(p[32 * k]);
+      a1 += val(p[32 * (k + 1)]);
+      a2 += val(p[32 * (k + 2)]);
+      a3 += val(p[32 * (k + 3)]);
+    }
+    for (; k < w; k++) a0 += val(p[32 * k]);
+    const int i = 32 * s + lane;
+    if (i < nrows) fin(r0 + i, (a0 + a1) + (a2 + a3), false);
+  }
+}
+
 }  // namespace prgb

@@ -1,0 +1,204 @@
+// warp_solve.cuh -- one warp per component of 2..32 vertices (Sec. 4.3:
+// CACs in one topological pass, SCCs by the power series of Sec. 4.3.2),
+// shared by the warp-class kernel and the persistent level kernel.
+#pragma once
+
+#include "common.cuh"
+#include "solve.cuh"
+
+namespace prgb {
+
+// Mixed precision (the SCC series only; the gather, CACs and 1-vertex
+// components stay FP64).  Per SCC C with budget tau = tol*|C|/n:
+//   1. the series P_0 = W, P_{k+1} = c A^T P_k, F = sum P_k in FP32 values
+//      and FP32 accumulation, until the FP32 norm of P falls to
+//      max(tau, kMixKappa * ||W||_1): below that FP32 rounding of F
+//      dominates what further terms would add;
+//   2. R += F in FP64 and the FP64 residual r = W + c A^T (R/outdeg) - R,
+//      its L1 norm rho; done when rho <= tau;
+//   3. otherwise solve (I - c A^T) D = r by the same series in FP32 from
+//      P_0 = r (signed), until the FP32 norm of P falls to
+//      max(tau/2, kMixKappa * rho); F = D, back to 2.
+// Each FP32 pass gains about six digits, so one or two rounds of 2-3 meet
+// any budget above ~1e-13 ||R||_1; after kMixRounds residuals above tau the
+// component is reported as not converged (PR_ENOCONV).  The final per-SCC
+// residual check is FP64, so the L1 residual budget holds as in FP64 mode.
+constexpr float kMixKappa = 8.0f * 5.9604645e-8f;  // 8 * 2^-24
+constexpr int kMixRounds = 6;
+
+
+// ---------------------------------------------------------------------------
+// one warp per component of 2..32 vertices, one vertex per lane.  The
+// component's internal in-edges (at most 32*31) are staged in shared memory
+// as 8-bit local indices, so each series iteration reads shared memory only.
+// ---------------------------------------------------------------------------
+constexpr int kWarpEdges = kWarpCompMax * (kWarpCompMax - 1);
+
+// FP32 series with FP64 residual refinement (see kMixKappa) for one warp's
+// component; W is this lane's weight.  Returns the result R of this lane and
+// counts the sweeps in *k (all) and *k64 (FP64 residual sweeps).
+static __device__ double warp_series_mixed(const SolveArgs& a, bool act, double W, double inv, const uint8_t* ix, int ib,
+                                    int ie, double* z, float* zf, double tau, int* k, int* k64, bool warm,
+                                    double R0) {
+  const int lane = threadIdx.x & 31;
+  const float cf = (float)a.c;
+  const float invf = (float)inv;
+  float F = act ? (float)W : 0.0f;
+  if (act) zf[lane] = (float)(W * inv);
+  const double wsum = group_sum<32>(act ? W : 0.0);
+  float thr = (float)fmax(tau, (double)kMixKappa * wsum);
+  double R = 0.0;
+  if (warm) {  // start from the guess: straight to its FP64 residual
+    R = act ? R0 : 0.0;
+    F = 0.0f;
+  }
+  bool skip = warm;
+  int rounds = 0;
+  __syncwarp();
+  for (;;) {
+    for (; !skip;) {
+      float acc0 = 0.0f, acc1 = 0.0f;
+      int e = ib;
+      for (; e + 1 < ie; e += 2) {
+        acc0 += zf[ix[e]];
+        acc1 += zf[ix[e + 1]];
+      }
+      if (e < ie) acc0 += zf[ix[e]];
+      const float pn = cf * (acc0 + acc1);
+      __syncwarp();
+      if (act) {
+        zf[lane] = pn * invf;
+        F += pn;
+      }
+      __syncwarp();
+      ++*k;
+      if (group_sumf<32>(fabsf(pn)) <= thr) break;
+      if (*k >= a.max_iter) {
+        if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
+        return R + (double)F;
+      }
+    }
+    skip = false;
+    R += (double)F;
+    if (act) z[lane] = R * inv;
+    __syncwarp();
+    double acc = 0.0;
+    for (int e = ib; e < ie; e++) acc += z[ix[e]];
+    const double r = act ? W + a.c * acc - R : 0.0;
+    ++*k;
+    ++*k64;
+    const double rho = group_sum<32>(fabs(r));
+    if (rho <= tau) break;
+    if (++rounds >= kMixRounds || *k >= a.max_iter) {
+      if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
+      break;
+    }
+    F = (float)r;
+    __syncwarp();  // every lane has read z before the next residual rewrites it
+    if (act) zf[lane] = (float)(r * inv);
+    thr = fmaxf(0.5f * (float)tau, kMixKappa * (float)rho);
+    __syncwarp();
+  }
+  return R;
+}
+
+// One warp solves component c: z (32 doubles), zf (32 floats, mixed
+// precision only) and ix (kWarpEdges bytes) are the warp's own shared memory.
+template <bool kMixed>
+__device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, uint8_t* ix) {
+  const int lane = threadIdx.x & 31;
+  const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
+  if (sz < a.lu_threshold && a.c_type[c] == PR_TYPE_SCC) return;  // solved by solve_lu_k (warp-uniform)
+  const bool act = lane < sz;
+  const int p = off + lane;
+  const double inv = act ? a.p_inv[p] : 0.0;
+  const int ib0 = a.int_ptr[off];
+  const int m = a.int_ptr[off + sz] - ib0;
+  for (int e = lane; e < m && e < kWarpEdges; e += 32) ix[e] = (uint8_t)local_or_err(a, a.int_idx[ib0 + e] - off, sz);
+  if (m > kWarpEdges) set_err(a.ctl, PR_EINTERNAL, 302);
+  const double W = act ? a.W[p] : 0.0;
+  const int ib = act ? a.int_ptr[p] - ib0 : 0, ie = act ? min(a.int_ptr[p + 1] - ib0, kWarpEdges) : 0;
+  __syncwarp();
+  double R = W;
+  int k = 0, k64 = 0;
+  if (a.c_type[c] == PR_TYPE_CAC) {
+    const int sb = a.c_sub[c], se = a.c_sub[c + 1];
+    for (int s = sb; s < se; s++) {
+      const int lo = a.sub_ptr[s], hi = a.sub_ptr[s + 1];
+      if (act && p >= lo && p < hi) {
+        double acc = 0.0;
+        for (int e = ib; e < ie; e++) acc += z[ix[e]];
+        R = W + a.c * acc;
+        z[lane] = R * inv;
+      }
+      __syncwarp();
+    }
+  } else if (kMixed) {
+    const double tau = a.tol * (double)sz / (double)a.n;
+    const bool warm = a.R0 != nullptr;
+    R = warp_series_mixed(a, act, W, inv, ix, ib, ie, z, zf, tau, &k, &k64, warm, warm && act ? a.R0[p] : 0.0);
+  } else {
+    const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
+    const int fixed = a.replay ? a.replay[c] : -1;
+    // z holds c P / outdeg, so that the in-edge sum is the next term itself
+    const double civ = a.c * inv;
+    if (a.R0) {
+      // warm start: R = R0 + r, the series continues from the residual
+      // r = W + c A^T(R0/outdeg) - R0 (signed)
+      const double r0 = act ? a.R0[p] : 0.0;
+      if (act) z[lane] = r0 * civ;
+      __syncwarp();
+      double acc = 0.0;
+      for (int e = ib; e < ie; e++) acc += z[ix[e]];
+      const double r = act ? W + acc - r0 : 0.0;
+      __syncwarp();
+      R = r0 + r;
+      if (act) z[lane] = r * civ;
+      k = 1;
+    } else if (act) {
+      z[lane] = W * civ;
+    }
+    __syncwarp();
+    for (;;) {
+      // four partial sums: shorter chains of dependent loads and FP64 adds
+      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+      int e = ib;
+      for (; e + 3 < ie; e += 4) {
+        acc0 += z[ix[e]];
+        acc1 += z[ix[e + 1]];
+        acc2 += z[ix[e + 2]];
+        acc3 += z[ix[e + 3]];
+      }
+      for (; e < ie; e++) acc0 += z[ix[e]];
+      const double pn = (acc0 + acc1) + (acc2 + acc3);
+      __syncwarp();
+      if (act) {
+        z[lane] = pn * civ;
+        R += pn;
+      }
+      __syncwarp();
+      k++;
+      if (fixed >= 0) {
+        if (k >= fixed) break;
+        continue;
+      }
+      const float pf = abs_to_float(pn);  // terms are signed after a warm start
+      const float s = a.norm == PR_NORM_L1 ? group_sumf<32>(pf) : group_maxf<32>(pf);
+      if (!keep_going32(s, tau, a.norm)) break;
+      if (k >= a.max_iter) {
+        if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
+        break;
+      }
+    }
+  }
+  if (act) {
+    a.R[p] = R;
+    a.zr[p] = R * inv;
+  }
+  if (lane == 0) {
+    a.iters[c] = k;
+    if (kMixed) a.iters64[c] = k64;
+  }
+}
+
+}  // namespace prgb

@@ -125,14 +125,14 @@ __device__ __forceinline__ bool wave_barrier(Ctl* ctl, int where, int next, Wave
       __threadfence();
       atomicAdd(&ctl->bar_gen, 1u);
     } else {
-      const unsigned long long t0 = globaltimer_ns();
+      const unsigned long long t0 = globaltimer_ns(), lim = wait_limit_ns(ctl);
       for (;;) {
         // both words in flight together: one round trip per poll
         const unsigned int g = vloadu(&ctl->bar_gen);
         const int e = vload(&ctl->err);
         if (g != gen || e != 0) break;
         __nanosleep(32);
-        if (globaltimer_ns() - t0 > kWaitNs) {
+        if (globaltimer_ns() - t0 > lim) {
           set_err(ctl, PR_ETIMEOUT, where);
           break;
         }
