@@ -81,8 +81,6 @@ struct Ctl {
   unsigned int wait_us;  // limit of each bounded wait in microseconds (0: kWaitNs)
   alignas(128) unsigned int bar_count;  // grid barrier arrivals
   alignas(128) unsigned int bar_gen;    // grid barrier releases (polled)
-  int bwave[2];          // wave barriers: next wave and its frontier size,
-  int bcnt[2];           //   published by the last block to arrive
   alignas(128) int cnt[8];  // frontier counters (rotating)
   alignas(128) int flags[8];  // misc flags (e.g. not-converged)
   double dsum[4];
@@ -109,37 +107,59 @@ __device__ __forceinline__ void set_err(Ctl* ctl, int code, int where) {
   if (atomicCAS(&ctl->err, 0, code) == 0) ctl->where = where;
 }
 
-// Grid-wide barrier for cooperative launches, with a bounded wait: after
-// wait_limit_ns the waiting block records PR_ETIMEOUT and leaves.  Returns false
-// when any block has recorded an error, so that callers can return early.
-// The Ctl block must have bar_count == 0 when the kernel starts.
+// Arrival at the grid barrier: one fetch-add with acquire-release ordering
+// at device scope (the block's earlier writes are visible to every block that
+// sees the arrival, and this block sees theirs).
+__device__ __forceinline__ unsigned int arrive_acq_rel(unsigned int* p) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0 of a block arrives at the grid barrier and waits for the others,
+// with a bounded wait.  The last block to arrive resets the count and
+// releases the generation word, which the others poll with acquire loads;
+// the count is thus 0 after every barrier (and must be when the kernel
+// starts).  After wait_limit_ns a waiting block records PR_ETIMEOUT and
+// leaves.
+__device__ __forceinline__ void grid_arrive_wait(Ctl* ctl, int where) {
+  // the generation cannot move before this block arrives, and it is at
+  // least the one this block saw released at its previous barrier
+  const unsigned int gen = ld_acquire_u32(&ctl->bar_gen);
+  if (arrive_acq_rel(&ctl->bar_count) == gridDim.x - 1) {
+    // the reset is ordered before the release of the generation, which
+    // every block sees before it arrives again
+    asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&ctl->bar_count) : "memory");
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_gen) : "memory");
+    return;
+  }
+  const unsigned long long t0 = globaltimer_ns(), lim = wait_limit_ns(ctl);
+  for (;;) {
+    // both words in flight together: one round trip per poll
+    const unsigned int g = ld_acquire_u32(&ctl->bar_gen);
+    const int e = vload(&ctl->err);
+    if (g != gen || e != 0) return;
+    __nanosleep(32);
+    if (globaltimer_ns() - t0 > lim) {
+      set_err(ctl, PR_ETIMEOUT, where);
+      return;
+    }
+  }
+}
+
+// Grid-wide barrier for cooperative launches.  Returns false when any block
+// has recorded an error, so that callers can return early.
 __device__ __forceinline__ bool grid_sync(Ctl* ctl, int where) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int nb = gridDim.x;
-    const unsigned int gen = vloadu(&ctl->bar_gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
-    if (arrived == nb - 1) {
-      atomicExch(&ctl->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
-    } else {
-      const unsigned long long t0 = globaltimer_ns(), lim = wait_limit_ns(ctl);
-      for (;;) {
-        // both words in flight together: one round trip per poll
-        const unsigned int g = vloadu(&ctl->bar_gen);
-        const int e = vload(&ctl->err);
-        if (g != gen || e != 0) break;
-        __nanosleep(32);
-        if (globaltimer_ns() - t0 > lim) {
-          set_err(ctl, PR_ETIMEOUT, where);
-          break;
-        }
-      }
-    }
-    __threadfence();
+    grid_arrive_wait(ctl, where);
     ok = vload(&ctl->err) == 0;  // one read per block, not per thread
   }
   __syncthreads();
@@ -365,7 +385,9 @@ struct DevGraph {
   int32_t* lorder = nullptr;  // [n] rows ordered by in-degree class (heavy last)
   int32_t* lpre = nullptr;    // [n+1] row-cost prefix over lorder (see build_lpre), or null
   int32_t* oheavy = nullptr;  // vertices with more than kHeavy out-edges (ascending)
-  int32_t noheavy = 0;
+  int32_t* ochoff = nullptr;  // their kChunkH-edge chunks: first chunk per listed vertex
+  int32_t* ochrow = nullptr;  // per chunk, its index in oheavy
+  int32_t noheavy = 0, nochunks = 0;
   double* inv = nullptr;      // [n] 1/outdeg, 0 for dangling vertices
 };
 
@@ -383,7 +405,7 @@ pr_status build_lpre(const int32_t* ptr, const int32_t* lorder, int32_t n, int64
 pr_status build_inv(const int32_t* deg, int32_t n, Arena& keep, double** inv, cudaStream_t s);
 
 // List the rows r in [0, nrows) of ptr with ptr[r+1]-ptr[r] > kHeavy
-// (ascending), their chunk offsets (exclusive prefix of ceil(deg/kHeavy))
+// (ascending), their chunk offsets (exclusive prefix of ceil(deg/kChunkH))
 // and, per chunk, its heavy-row index; reads the two counts back
 // (synchronises).
 pr_status build_heavy(const int32_t* ptr, int32_t nrows, Arena& keep, Arena& tmp, int32_t** rows,

@@ -225,11 +225,8 @@ pr_status ingest(const pr_csr* csr, uint32_t flags, DevGraph* g, Arena& keep, Ar
                         &g->nchunks));
   PRGB_TRY(build_lorder(g->iptr, n, nullptr, 0, keep, tmp, &g->lorder));
   PRGB_TRY(build_lpre(g->iptr, g->lorder, n, g->m, keep, tmp, &g->lpre));
-  {
-    // vertices with many out-edges: the partitioner gives them a warp each
-    int32_t *choff = nullptr, *chrow = nullptr, nch = 0;
-    PRGB_TRY(build_heavy(g->optr, n, keep, tmp, &g->oheavy, &choff, &chrow, &g->noheavy, &nch));
-  }
+  // vertices with many out-edges: the partitioner spreads their chunks over warps
+  PRGB_TRY(build_heavy(g->optr, n, keep, tmp, &g->oheavy, &g->ochoff, &g->ochrow, &g->noheavy, &g->nochunks));
   PRGB_TRY(build_inv(g->outdeg, n, keep, &g->inv, s));
   return PR_OK;
 }

@@ -81,30 +81,40 @@ __global__ void comp_of_rep_k(int32_t K, const uint32_t* vals, int32_t* comp_of_
   for (int64_t k = gtid(); k < K; k += gstride()) comp_of_rep[vals[k]] = (int32_t)k;
 }
 
-// in-edges from the same final component, per vertex: with list ==
-// nullptr a thread per vertex with at most kHeavy in-edges, otherwise a warp
-// per listed vertex (the vertices with more)
-__global__ void int_indeg_k(int32_t n, const int32_t* list, const int32_t* __restrict__ iptr,
-                            const int32_t* __restrict__ iidx, const int32_t* __restrict__ crep, int32_t* icnt_v) {
-  if (!list) {
-    for (int64_t v = gtid(); v < n; v += gstride()) {
-      const int e0 = iptr[v], e1 = iptr[v + 1];
-      if (e1 - e0 > kHeavy) continue;
-      const int r = crep[v];
-      int in = 0;
-      for (int e = e0; e < e1; e++) in += crep[iidx[e]] == r;
-      icnt_v[v] = in;
-    }
-    return;
-  }
-  const int lane = threadIdx.x & 31;
-  for (int64_t i = gtid() >> 5; i < n; i += gstride() >> 5) {
-    const int v = list[i];
-    const int r = crep[v];
+// in-edges from the same final component, per vertex: a thread per vertex
+// with at most kHeavy in-edges (the others start at zero)
+__global__ void int_indeg_k(int32_t n, const int32_t* __restrict__ iptr, const int32_t* __restrict__ iidx,
+                            const int32_t* __restrict__ crep, int32_t* icnt_v) {
+  for (int64_t v = gtid(); v < n; v += gstride()) {
+    const int e0 = iptr[v], e1 = iptr[v + 1];
     int in = 0;
-    for (int e = iptr[v] + lane; e < iptr[v + 1]; e += 32) in += crep[iidx[e]] == r;
+    if (e1 - e0 <= kHeavy) {
+      const int r = crep[v];
+      for (int e = e0; e < e1; e++) in += crep[iidx[e]] == r;
+    }
+    icnt_v[v] = in;
+  }
+}
+
+// the vertices with more: a warp per chunk of kChunkH in-edges, which also
+// keeps its own count (chunk_in) for the order-preserving split below
+__global__ void int_indeg_heavy_k(int32_t nchunks, const int32_t* __restrict__ rows,
+                                  const int32_t* __restrict__ choff, const int32_t* __restrict__ chrow,
+                                  const int32_t* __restrict__ iptr, const int32_t* __restrict__ iidx,
+                                  const int32_t* __restrict__ crep, int32_t* icnt_v, int32_t* chunk_in) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t c = gtid() >> 5; c < nchunks; c += gstride() >> 5) {
+    const int h = chrow[c];
+    const int v = rows[h];
+    const int r = crep[v];
+    const int e0 = iptr[v] + ((int)c - choff[h]) * kChunkH, e1 = min(iptr[v + 1], e0 + kChunkH);
+    int in = 0;
+    for (int e = e0 + lane; e < e1; e += 32) in += crep[iidx[e]] == r;
     in = __reduce_add_sync(0xffffffffu, in);
-    if (lane == 0) icnt_v[v] = in;
+    if (lane == 0) {
+      chunk_in[c] = in;
+      atomicAdd(&icnt_v[v], in);
+    }
   }
 }
 
@@ -167,31 +177,60 @@ __global__ void edge_count_k(int32_t n, const int32_t* perm, const int32_t* __re
   }
 }
 
-// warp per permuted vertex: order-preserving split of the in-edges
+// Order-preserving split of in-edges [b, e_end) of v into internal ones
+// (written from int_idx + oi) and external ones (from ext_idx + oe), as
+// positions; the warp's 32 lanes take 32 edges at a time.
+__device__ __forceinline__ void split_edges(int b, int e_end, int cv, int oi, int oe, const int32_t* pos,
+                                            const int32_t* iidx, const int32_t* comp_id, int32_t* int_idx,
+                                            int32_t* ext_idx) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  for (int base = b; base < e_end; base += 32) {
+    const int e = base + lane;
+    const bool ok = e < e_end;
+    int u = ok ? iidx[e] : 0;
+    const bool in = ok && comp_id[u] == cv;
+    const bool ex = ok && !in;
+    const unsigned bi = __ballot_sync(0xffffffffu, in);
+    const unsigned be = __ballot_sync(0xffffffffu, ex);
+    if (in) int_idx[oi + __popc(bi & lt)] = pos[u];
+    if (ex) ext_idx[oe + __popc(be & lt)] = pos[u];
+    oi += __popc(bi);
+    oe += __popc(be);
+  }
+}
+
+// a warp per permuted vertex with at most kHeavy in-edges
 __global__ void edge_fill_k(int32_t n, const int32_t* perm, const int32_t* pos, const int32_t* iptr,
                             const int32_t* iidx, const int32_t* comp_id, const int32_t* int_ptr,
                             const int32_t* ext_ptr, int32_t* int_idx, int32_t* ext_idx) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = lanemask_lt();
   const int64_t w0 = gtid() >> 5, nw = gstride() >> 5;
   for (int64_t p = w0; p < n; p += nw) {
     const int v = perm[p];
-    const int cv = comp_id[v];
-    int oi = int_ptr[p], oe = ext_ptr[p];
     const int b = iptr[v], e_end = iptr[v + 1];
-    for (int base = b; base < e_end; base += 32) {
-      const int e = base + lane;
-      const bool ok = e < e_end;
-      int u = ok ? iidx[e] : 0;
-      const bool in = ok && comp_id[u] == cv;
-      const bool ex = ok && !in;
-      const unsigned bi = __ballot_sync(0xffffffffu, in);
-      const unsigned be = __ballot_sync(0xffffffffu, ex);
-      if (in) int_idx[oi + __popc(bi & lt)] = pos[u];
-      if (ex) ext_idx[oe + __popc(be & lt)] = pos[u];
-      oi += __popc(bi);
-      oe += __popc(be);
-    }
+    if (e_end - b > kHeavy) continue;
+    split_edges(b, e_end, comp_id[v], int_ptr[p], ext_ptr[p], pos, iidx, comp_id, int_idx, ext_idx);
+  }
+}
+
+// the others, a warp per chunk of kChunkH in-edges: chunk_pre (exclusive
+// prefix of the chunks' internal counts) places each chunk's edges after
+// those of the vertex's earlier chunks
+__global__ void edge_fill_heavy_k(int32_t nchunks, const int32_t* __restrict__ rows,
+                                  const int32_t* __restrict__ choff, const int32_t* __restrict__ chrow,
+                                  const int32_t* __restrict__ chunk_pre, const int32_t* pos, const int32_t* iptr,
+                                  const int32_t* iidx, const int32_t* comp_id, const int32_t* int_ptr,
+                                  const int32_t* ext_ptr, int32_t* int_idx, int32_t* ext_idx) {
+  for (int64_t c = gtid() >> 5; c < nchunks; c += gstride() >> 5) {
+    const int h = chrow[c];
+    const int v = rows[h];
+    const int c0 = choff[h];
+    const int p = pos[v];
+    const int in_before = chunk_pre[c] - chunk_pre[c0];
+    const int e_before = ((int)c - c0) * kChunkH;
+    const int b = iptr[v] + e_before, e_end = min(iptr[v + 1], b + kChunkH);
+    split_edges(b, e_end, comp_id[v], int_ptr[p] + in_before, ext_ptr[p] + e_before - in_before, pos, iidx,
+                comp_id, int_idx, ext_idx);
   }
 }
 
@@ -437,12 +476,17 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   // the internal / external split below
   int32_t* icnt_v;
   PRGB_TRY(tmp.alloc(&icnt_v, n));
-  int_indeg_k<<<grid1(n), kBlock, 0, s>>>(n, nullptr, g.iptr, g.iidx, crep, icnt_v);
+  int32_t *chunk_in = nullptr, *chunk_pre = nullptr;
+  PRGB_TRY(tmp.alloc(&chunk_in, (size_t)g.nchunks + 1));
+  PRGB_TRY(tmp.alloc(&chunk_pre, (size_t)g.nchunks + 1));
+  int_indeg_k<<<grid1(n), kBlock, 0, s>>>(n, g.iptr, g.iidx, crep, icnt_v);
   PRGB_LAUNCH();
-  if (g.nheavy > 0) {
-    int_indeg_k<<<gridw(g.nheavy), kBlock, 0, s>>>(g.nheavy, g.heavy_rows, g.iptr, g.iidx, crep, icnt_v);
+  if (g.nchunks > 0) {
+    int_indeg_heavy_k<<<gridw(g.nchunks), kBlock, 0, s>>>(g.nchunks, g.heavy_rows, g.heavy_choff, g.heavy_chrow,
+                                                          g.iptr, g.iidx, crep, icnt_v, chunk_in);
     PRGB_LAUNCH();
   }
+  PRGB_TRY(scan_i32(chunk_in, chunk_pre, g.nchunks, tmp));
   // the secondary keys fill the radix passes the wave key leaves: up to 8
   // bits of in-degree and 4 of out-degree
   const int wbits = bits_for((uint32_t)max_wave);
@@ -505,6 +549,12 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
   edge_fill_k<<<gridw(n), kBlock, 0, s>>>(n, P->perm, pos, g.iptr, g.iidx, P->comp_id, P->int_ptr, P->ext_ptr,
                                           P->int_idx, P->ext_idx);
   PRGB_LAUNCH();
+  if (g.nchunks > 0) {
+    edge_fill_heavy_k<<<gridw(g.nchunks), kBlock, 0, s>>>(g.nchunks, g.heavy_rows, g.heavy_choff, g.heavy_chrow,
+                                                          chunk_pre, pos, g.iptr, g.iidx, P->comp_id, P->int_ptr,
+                                                          P->ext_ptr, P->int_idx, P->ext_idx);
+    PRGB_LAUNCH();
+  }
   // level ranges and size classes
   int32_t *lvl_cbeg, *cls;
   LevelRange* dlev;

@@ -73,16 +73,30 @@ __global__ void count_nodes_k(const int32_t* __restrict__ optr, const int32_t* _
   }
 }
 
-// the same for the listed vertices with more than kHeavy out-edges, a warp each
+// Edges [*e0, *e1) of chunk c of the out-heavy vertices (kChunkH edges
+// each, the last one of a vertex shorter); returns the vertex.
+__device__ __forceinline__ int out_chunk(const int32_t* optr, const int32_t* list, const int32_t* choff,
+                                         const int32_t* chrow, int c, int* e0, int* e1) {
+  const int h = chrow[c];
+  const int u = list[h];
+  *e0 = optr[u] + (c - choff[h]) * kChunkH;
+  *e1 = min(optr[u + 1], *e0 + kChunkH);
+  return u;
+}
+
+// the same for the vertices with more than kHeavy out-edges, a warp per
+// chunk of kChunkH out-edges (a hub's edges spread over many warps)
 __global__ void count_nodes_heavy_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx,
-                                    const int32_t* __restrict__ list, int32_t nlist,
+                                    const int32_t* __restrict__ list, const int32_t* __restrict__ choff,
+                                    const int32_t* __restrict__ chrow, int32_t nchunks,
                                     const int32_t* __restrict__ rep, int32_t* pending, int32_t* cin_cnt) {
   const int lane = threadIdx.x & 31;
-  for (int64_t i = gwarp_l(); i < nlist; i += nwarps_l()) {
-    const int u = list[i];
+  for (int64_t c = gwarp_l(); c < nchunks; c += nwarps_l()) {
+    int e0, e1;
+    const int u = out_chunk(optr, list, choff, chrow, (int)c, &e0, &e1);
     const int U = rep[u];
     int ext = 0;
-    for (int e = optr[u] + lane; e < optr[u + 1]; e += 32) {
+    for (int e = e0 + lane; e < e1; e += 32) {
       const int W = rep[oidx[e]];
       if (W != U) {
         ext++;
@@ -95,9 +109,10 @@ __global__ void count_nodes_heavy_k(const int32_t* __restrict__ optr, const int3
 }
 
 // list == nullptr: a thread per vertex with at most kHeavy out-edges;
-// otherwise a warp per listed vertex
+// otherwise a warp per chunk of the listed vertices' out-edges (n chunks)
 __global__ void fill_cin_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx, int32_t n,
-                           const int32_t* __restrict__ list, const int32_t* __restrict__ rep, int32_t* cursor,
+                           const int32_t* __restrict__ list, const int32_t* __restrict__ choff,
+                           const int32_t* __restrict__ chrow, const int32_t* __restrict__ rep, int32_t* cursor,
                            int32_t* cin_src) {
   const int lane = threadIdx.x & 31;
   // lanes appending to the same node's list take their slots with one atomic
@@ -123,10 +138,11 @@ __global__ void fill_cin_k(const int32_t* __restrict__ optr, const int32_t* __re
     }
     return;
   }
-  for (int64_t i = gwarp_l(); i < n; i += nwarps_l()) {
-    const int u = list[i];
+  for (int64_t c = gwarp_l(); c < n; c += nwarps_l()) {
+    int e0, e1;
+    const int u = out_chunk(optr, list, choff, chrow, (int)c, &e0, &e1);
     const int U = rep[u];
-    for (int e = optr[u] + lane; e < optr[u + 1]; e += 32) {
+    for (int e = e0 + lane; e < e1; e += 32) {
       const int W = rep[oidx[e]];
       append(W != U, W, U);
     }
@@ -244,20 +260,50 @@ __device__ __forceinline__ void uf_union(int* par, int a, int b) {
   }
 }
 
-// a warp per vertex: its unions run in parallel lanes
+__device__ __forceinline__ bool merges(int v, const int32_t* rep, const int32_t* nsize, const uint8_t* merged) {
+  return merged[v] && rep[v] == v && nsize[v] == 1;
+}
+
+// unions of v with the 1-vertex components of its level among the targets
+// of out-edges [e0, e1), in parallel lanes
+__device__ __forceinline__ void merge_range(int v, int e0, int e1, const int32_t* oidx, const int32_t* rep,
+                                            const int32_t* nsize, const int32_t* level_node, int* par) {
+  const int lv = level_node[v];
+  for (int e = e0 + (threadIdx.x & 31); e < e1; e += 32) {
+    const int w = oidx[e];
+    const int W = rep[w];
+    if (nsize[W] == 1 && level_node[W] == lv) uf_union(par, v, w);
+  }
+}
+
+// a thread per vertex finds the merging ones with at most kHeavy out-edges;
+// the warp then takes each in turn
 __global__ void merge_unions_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx, int32_t n,
                                const int32_t* __restrict__ rep, const int32_t* __restrict__ nsize,
                                const int32_t* __restrict__ level_node, const uint8_t* __restrict__ merged,
                                int* par) {
   const int lane = threadIdx.x & 31;
-  for (int64_t v = gwarp_l(); v < n; v += nwarps_l()) {
-    if (!merged[v] || rep[v] != (int32_t)v || nsize[v] != 1) continue;
-    const int lv = level_node[v];
-    for (int e = optr[v] + lane; e < optr[v + 1]; e += 32) {
-      const int w = oidx[e];
-      const int W = rep[w];
-      if (nsize[W] == 1 && level_node[W] == lv) uf_union(par, (int)v, w);
+  for (int64_t vb = (int64_t)gwarp_l() * 32; vb < n; vb += (int64_t)nwarps_l() * 32) {
+    const int64_t vl = vb + lane;
+    const bool mine = vl < n && optr[vl + 1] - optr[vl] <= kHeavy && merges((int)vl, rep, nsize, merged);
+    for (unsigned todo = __ballot_sync(0xffffffffu, mine); todo; todo &= todo - 1) {
+      const int v = (int)vb + __ffs(todo) - 1;
+      merge_range(v, optr[v], optr[v + 1], oidx, rep, nsize, level_node, par);
     }
+  }
+}
+
+// the merging vertices with more out-edges: a warp per chunk of kChunkH
+__global__ void merge_unions_heavy_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx,
+                                     const int32_t* __restrict__ list, const int32_t* __restrict__ choff,
+                                     const int32_t* __restrict__ chrow, int32_t nchunks,
+                                     const int32_t* __restrict__ rep, const int32_t* __restrict__ nsize,
+                                     const int32_t* __restrict__ level_node, const uint8_t* __restrict__ merged,
+                                     int* par) {
+  for (int64_t c = gwarp_l(); c < nchunks; c += nwarps_l()) {
+    int e0, e1;
+    const int u = out_chunk(optr, list, choff, chrow, (int)c, &e0, &e1);
+    if (merges(u, rep, nsize, merged)) merge_range(u, e0, e1, oidx, rep, nsize, level_node, par);
   }
 }
 
@@ -323,9 +369,9 @@ pr_status levels_and_merge(const DevGraph& g, const int32_t* rep, int32_t* crep,
   PRGB_CUDA(cudaMemsetAsync(merged, 0, (size_t)n, s));
   count_nodes_k<<<grid_w(n), kBlock, 0, s>>>(g.optr, g.oidx, n, rep, nsize, smin, pending, cin_cnt);
   PRGB_LAUNCH();
-  if (g.noheavy > 0) {
-    count_nodes_heavy_k<<<grid_w(g.noheavy), kBlock, 0, s>>>(g.optr, g.oidx, g.oheavy, g.noheavy, rep, pending,
-                                                             cin_cnt);
+  if (g.nochunks > 0) {
+    count_nodes_heavy_k<<<grid_w(g.nochunks), kBlock, 0, s>>>(g.optr, g.oidx, g.oheavy, g.ochoff, g.ochrow,
+                                                              g.nochunks, rep, pending, cin_cnt);
     PRGB_LAUNCH();
   }
   PRGB_TRY(scan_i32(cin_cnt, cin_ptr, n, tmp));
@@ -334,10 +380,11 @@ pr_status levels_and_merge(const DevGraph& g, const int32_t* rep, int32_t* crep,
   PRGB_CUDA(cudaStreamSynchronize(s));
   PRGB_TRY(tmp.alloc(&cin_src, (size_t)(m_ext > 0 ? m_ext : 1)));
   PRGB_CUDA(cudaMemcpyAsync(cursor, cin_ptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, s));
-  fill_cin_k<<<grid_t(n), kBlock, 0, s>>>(g.optr, g.oidx, n, nullptr, rep, cursor, cin_src);
+  fill_cin_k<<<grid_t(n), kBlock, 0, s>>>(g.optr, g.oidx, n, nullptr, nullptr, nullptr, rep, cursor, cin_src);
   PRGB_LAUNCH();
-  if (g.noheavy > 0) {
-    fill_cin_k<<<grid_w(g.noheavy), kBlock, 0, s>>>(g.optr, g.oidx, g.noheavy, g.oheavy, rep, cursor, cin_src);
+  if (g.nochunks > 0) {
+    fill_cin_k<<<grid_w(g.nochunks), kBlock, 0, s>>>(g.optr, g.oidx, g.nochunks, g.oheavy, g.ochoff, g.ochrow, rep,
+                                                     cursor, cin_src);
     PRGB_LAUNCH();
   }
   // frontier capacity: every node is queued once, in ceil(len/kChunk) items
@@ -357,8 +404,13 @@ pr_status levels_and_merge(const DevGraph& g, const int32_t* rep, int32_t* crep,
   }
   iota_i32_k<<<grid_t(n), kBlock, 0, s>>>(par, n);
   PRGB_LAUNCH();
-  merge_unions_k<<<grid_w(n), kBlock, 0, s>>>(g.optr, g.oidx, n, rep, nsize, level_node, merged, par);
+  merge_unions_k<<<grid_t(n), kBlock, 0, s>>>(g.optr, g.oidx, n, rep, nsize, level_node, merged, par);
   PRGB_LAUNCH();
+  if (g.nochunks > 0) {
+    merge_unions_heavy_k<<<grid_w(g.nochunks), kBlock, 0, s>>>(g.optr, g.oidx, g.oheavy, g.ochoff, g.ochrow,
+                                                               g.nochunks, rep, nsize, level_node, merged, par);
+    PRGB_LAUNCH();
+  }
   PRGB_CUDA(cudaMemsetAsync(&ctl->cnt[6], 0, sizeof(int), s));
   finish_vertices_k<<<grid_t(n), kBlock, 0, s>>>(n, rep, nsize, smin, level_node, wave_node, par, crep, level,
                                                  type, wave, ctl);

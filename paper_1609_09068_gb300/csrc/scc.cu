@@ -89,24 +89,27 @@ __global__ void trim_k(const int32_t* __restrict__ optr, const int32_t* __restri
 
 // ---- max-label propagation inside the pieces, frontier driven ---------------
 // Along out-edges: sig(v) = largest id that reaches v through unsettled
-// vertices of v's piece (pieces: equal (pin, pout)).  Frontier items are
-// (vertex, chunk of kChunkE edges), so the adjacency of a hub is spread over
-// many warps.
+// vertices of v's piece (piece: pin, the colour of the round before, -2 / -1
+// for the giant's forward set / the rest in the first round, kSettled once
+// the vertex's SCC is known).  Frontier items are (vertex, chunk of kChunkE
+// edges), so the adjacency of a hub is spread over many warps.
+constexpr int32_t kSettled = INT32_MIN;
+
 struct PropK {
-  const int32_t *ptr, *idx, *rep, *pin, *pout;
+  const int32_t *ptr, *idx, *pin;
   int32_t *sig, *stamp;
   __device__ void range(int u, int j, int* e0, int* e1) const {
     *e0 = ptr[u] + j * kChunkE;
     *e1 = min(ptr[u + 1], *e0 + kChunkE);
   }
-  __device__ int4 pre(int u, int, bool) const { return make_int4(vload(&sig[u]), pin[u], pout[u], 0); }
+  __device__ int4 pre(int u, int, bool) const { return make_int4(vload(&sig[u]), pin[u], 0, 0); }
   __device__ bool edge(int e, int4 p, int wave, int* w, int* nch) const {
     *w = idx[e];
     const int x = *w;
-    // four independent loads in flight at once (a short-circuit test would
-    // serialise them)
-    const int rx = rep[x], px = pin[x], qx = pout[x], sx = vload(&sig[x]);
-    if ((rx >= 0) | (px != p.y) | (qx != p.z) | (sx >= p.x)) return false;
+    // both loads in flight at once (a short-circuit test would serialise
+    // them); a settled target's piece is kSettled, never a live one's
+    const int px = pin[x], sx = vload(&sig[x]);
+    if ((px != p.y) | (sx >= p.x)) return false;
     const int old = atomicMax(&sig[x], p.x);
     if (old < p.x && atomicExch(&stamp[x], wave) != wave) {
       *nch = nchunks_of(ptr[x + 1] - ptr[x]);
@@ -117,9 +120,8 @@ struct PropK {
 };
 
 __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
-                            const int32_t* __restrict__ rep, const int32_t* __restrict__ pin,
-                            const int32_t* __restrict__ pout, int32_t* sig, int32_t* stamp, int* fav, int* fac,
-                            int* fbv, int* fbc, int cap, Ctl* ctl) {
+                            const int32_t* __restrict__ rep, const int32_t* __restrict__ pin, int32_t* sig,
+                            int32_t* stamp, int* fav, int* fac, int* fbv, int* fbc, int cap, Ctl* ctl) {
   const int lane = threadIdx.x & 31;
   const int gw = gwarp(), nw = nwarps();
   for (int64_t vb = (int64_t)gw * 32; vb < n; vb += (int64_t)nw * 32) {
@@ -128,8 +130,10 @@ __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __re
     int nch = 0;
     if (v < n) {
       stamp[v] = -1;
-      if (rep[v] < 0) {
-        sig[v] = (int32_t)v;
+      // a settled vertex's colour is -1: it matches no root in root_bfs_k
+      const bool live = rep[v] < 0;
+      sig[v] = live ? (int32_t)v : -1;
+      if (live) {
         nch = nchunks_of(ptr[v + 1] - ptr[v]);
         want = nch > 0;
       }
@@ -137,15 +141,16 @@ __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __re
     warp_push(want, (int)v, nch, fav, fac, &ctl->cnt[0], cap, ctl);
   }
   const Frontier f{fav, fac, fbv, fbc, cap};
-  PropK k{ptr, idx, rep, pin, pout, sig, stamp};
+  PropK k{ptr, idx, pin, sig, stamp};
   run_waves(ctl, f, 111, k);
 }
 
 // ---- backward search from every colour root --------------------------------
 // From each root r (colour(r) == r) along in-edges, entering only unsettled
-// vertices of the same colour: they reach r and r reaches them.
+// vertices of the same colour (a settled vertex's colour is -1): they reach r
+// and r reaches them.
 struct RootBfsK {
-  const int32_t *ptr, *idx, *rep, *color;
+  const int32_t *ptr, *idx, *color;
   int32_t* mark;
   int tag;
   __device__ void range(int u, int j, int* e0, int* e1) const {
@@ -156,8 +161,8 @@ struct RootBfsK {
   __device__ bool edge(int e, int4 p, int, int* w, int* nch) const {
     *w = idx[e];
     const int x = *w;
-    const int rx = rep[x], cx = color[x], mx = vload(&mark[x]);
-    if ((rx >= 0) | (cx != p.x) | (mx == tag) || atomicExch(&mark[x], tag) == tag) return false;
+    const int cx = color[x], mx = vload(&mark[x]);
+    if ((cx != p.x) | (mx == tag) || atomicExch(&mark[x], tag) == tag) return false;
     *nch = nchunks_of(ptr[x + 1] - ptr[x]);
     return *nch > 0;
   }
@@ -180,21 +185,21 @@ __global__ void root_bfs_k(const int32_t* __restrict__ ptr, const int32_t* __res
     warp_push(want, (int)v, nch, fav, fac, &ctl->cnt[0], cap, ctl);
   }
   const Frontier f{fav, fac, fbv, fbc, cap};
-  RootBfsK k{ptr, idx, rep, color, mark, tag};
+  RootBfsK k{ptr, idx, color, mark, tag};
   run_waves(ctl, f, 131, k);
 }
 
 // settle what the search reached; the colours become the next pieces
-__global__ void assign_color_k(int32_t n, int32_t* rep, int32_t* pin, int32_t* pout, const int32_t* color,
-                               const int32_t* mark, int tag, Ctl* ctl) {
+__global__ void assign_color_k(int32_t n, int32_t* rep, int32_t* pin, const int32_t* color, const int32_t* mark,
+                               int tag, Ctl* ctl) {
   int left = 0;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     if (rep[v] >= 0) continue;
     if (mark[v] == tag) {
       rep[v] = color[v];
+      pin[v] = kSettled;
     } else {
       pin[v] = color[v];
-      pout[v] = -1;
       left++;
     }
   }
@@ -273,13 +278,20 @@ __global__ void fwbw_max_k(int32_t n, const int32_t* fw, const int32_t* bw, int*
   if ((threadIdx.x & 31) == 0 && loc >= 0) atomicMax(best, loc);
 }
 
+// also gives every vertex settled so far (trimmed or in the giant) the
+// piece kSettled
 __global__ void fwbw_assign_k(int32_t n, const int32_t* fw, const int32_t* bw, const int* best, int32_t* rep,
                               int32_t* pin) {
   const int r = *best;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    if (rep[v] >= 0) continue;
-    if (fw[v] == 1 && bw[v] == 2) rep[v] = r;
-    else pin[v] = fw[v] == 1 ? -2 : -1;
+    if (rep[v] >= 0) {
+      pin[v] = kSettled;
+    } else if (fw[v] == 1 && bw[v] == 2) {
+      rep[v] = r;
+      pin[v] = kSettled;
+    } else {
+      pin[v] = fw[v] == 1 ? -2 : -1;
+    }
   }
 }
 
@@ -293,7 +305,7 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
   cudaStream_t s = tmp.stream();
   const int32_t n = g.n;
   if (n == 0) return PR_OK;
-  int32_t *rem_out, *rem_in, *state, *sin, *pin, *pout, *stamp;
+  int32_t *rem_out, *rem_in, *state, *sin, *pin, *stamp;
   int *fav, *fac, *fbv, *fbc;
   const int cap = (int)(2 * (int64_t)n + 2 * g.m / kChunkE + 2);
   PRGB_TRY(tmp.alloc(&fav, cap));
@@ -305,10 +317,8 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
   PRGB_TRY(tmp.alloc(&state, n));
   PRGB_TRY(tmp.alloc(&sin, n));
   PRGB_TRY(tmp.alloc(&pin, n));
-  PRGB_TRY(tmp.alloc(&pout, n));
   PRGB_TRY(tmp.alloc(&stamp, n));
   PRGB_CUDA(cudaMemsetAsync(pin, 0xff, (size_t)n * 4, s));
-  PRGB_CUDA(cudaMemsetAsync(pout, 0xff, (size_t)n * 4, s));
   PRGB_TRY(init_ctl(ctl, s));
   {
     DevGraph gg = g;
@@ -368,7 +378,7 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
       PRGB_TRY(reset_ctl(ctl, s));
       const int32_t* ptr = g.optr;
       const int32_t* idx = g.oidx;
-      void* args[] = {&ptr, &idx, (void*)&nn, &rep, &pin, &pout, &sin, &stamp, &fav, &fac, &fbv, &fbc, &cp, &ctl};
+      void* args[] = {&ptr, &idx, (void*)&nn, &rep, &pin, &sin, &stamp, &fav, &fac, &fbv, &fbc, &cp, &ctl};
       PRGB_TRY(launch_coop((const void*)propagate_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
     }
     {
@@ -379,7 +389,7 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
       PRGB_TRY(launch_coop((const void*)root_bfs_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
     }
     PRGB_CUDA(cudaMemsetAsync(&ctl->cnt[7], 0, sizeof(int), s));
-    assign_color_k<<<grid_n(n), kBlock, 0, s>>>(n, rep, pin, pout, sin, mark, tag, ctl);
+    assign_color_k<<<grid_n(n), kBlock, 0, s>>>(n, rep, pin, sin, mark, tag, ctl);
     PRGB_LAUNCH();
     int h[2] = {0, 0};
     PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -16,7 +16,7 @@
 namespace prgb {
 
 constexpr int kWaveBlock = 256;      // threads per block of the wave kernels
-constexpr int kWavePerSm = 2;        // their co-resident blocks per SM
+constexpr int kWavePerSm = 4;        // their co-resident blocks per SM (2 and 8: slower)
 constexpr int kSmallFrontier = 64;
 constexpr int kLocalWaves = 4096;
 
@@ -99,11 +99,11 @@ __device__ __forceinline__ void one_wave(Ctl* ctl, const Frontier& f, int wave, 
   }
 }
 
-// Grid barrier that also publishes the next wave and its frontier size.
-// The last block to arrive reads them (next >= 0: the wave all blocks agree
-// on; next < 0: the wave block 0 left in flags[7]) into a slot chosen by the
-// barrier's generation, so no block ever reads a counter that another block
-// may already be changing.  Bounded like grid_sync.
+// Grid barrier of the wave kernels (grid_arrive_wait), after which each
+// block reads the next wave (next, or the wave block 0 left in flags[7] when
+// next < 0) and its frontier size: the three frontier counters rotate, so the
+// one read here is not written again before every block has passed the next
+// barrier.
 struct WaveState {
   int wave;
   int cnt;
@@ -113,35 +113,10 @@ __device__ __forceinline__ bool wave_barrier(Ctl* ctl, int where, int next, Wave
   __shared__ int sh[3];
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int gen = vloadu(&ctl->bar_gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
-      const int w = next >= 0 ? next : vload(&ctl->flags[7]);
-      ctl->bwave[gen & 1] = w;
-      ctl->bcnt[gen & 1] = atomicAdd(&ctl->cnt[w % 3], 0);
-      __threadfence();
-      atomicExch(&ctl->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
-    } else {
-      const unsigned long long t0 = globaltimer_ns(), lim = wait_limit_ns(ctl);
-      for (;;) {
-        // both words in flight together: one round trip per poll
-        const unsigned int g = vloadu(&ctl->bar_gen);
-        const int e = vload(&ctl->err);
-        if (g != gen || e != 0) break;
-        __nanosleep(32);
-        if (globaltimer_ns() - t0 > lim) {
-          set_err(ctl, PR_ETIMEOUT, where);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    // the three reads in one round trip, one per block
-    sh[0] = vload(&ctl->bwave[gen & 1]);
-    sh[1] = vload(&ctl->bcnt[gen & 1]);
+    grid_arrive_wait(ctl, where);
+    const int w = next >= 0 ? next : vload(&ctl->flags[7]);
+    sh[0] = w;
+    sh[1] = vload(&ctl->cnt[w % 3]);
     sh[2] = vload(&ctl->err);
   }
   __syncthreads();
