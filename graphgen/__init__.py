@@ -470,6 +470,14 @@ def random_digraph(n, p, seed, loops=False):
     return Graph(n, rowptr, col, uniform_u(n), f"gnp(n={n},p={p},seed={seed})")
 
 
+def deep_dag_arrays(spec):
+    """(rowptr, col, u) of deep_dag(seed, n, levels) for spec = (seed, n,
+    levels): a picklable entry point for process pools."""
+    seed, n, levels = spec
+    g = deep_dag(seed=seed, n=n, levels=levels)
+    return g.rowptr, g.col, g.u
+
+
 def config(name, seed=None, **kw):
     """Named workloads with their default seeds."""
     if name == "small":

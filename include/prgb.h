@@ -157,6 +157,11 @@ typedef struct pr_solve_stats {
                                 comp_iters, which count all sweeps) */
     int64_t fp64_edge_visits; /* PR_PREC_MIXED: edges read by FP64 residual
                                  sweeps (included in edge_visits) */
+    float *level_ms;      /* optional caller-owned HOST array [n_levels]; with
+                             timing = 1 (pr_solve only) each level's device
+                             time in walk order (Eq. PR:levels gather through
+                             the level's last component), from CUDA events
+                             recorded between the levels */
 } pr_solve_stats;
 
 /*

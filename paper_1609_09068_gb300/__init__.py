@@ -67,7 +67,7 @@ class _Stats(C.Structure):
     _fields_ = [("iters_max", C.c_int32), ("n_levels", C.c_int32), ("edge_visits", C.c_int64),
                 ("launches", C.c_int64), ("comp_iters", C.c_void_p), ("timing", C.c_int32),
                 ("kernel_ms", C.c_float), ("kernel_bytes", C.c_int64), ("kernel_launches", C.c_int64),
-                ("fp64_sweeps_max", C.c_int32), ("fp64_edge_visits", C.c_int64)]
+                ("fp64_sweeps_max", C.c_int32), ("fp64_edge_visits", C.c_int64), ("level_ms", C.c_void_p)]
 
 
 _lib = None
@@ -351,7 +351,8 @@ def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
     on_host = isinstance(u, np.ndarray)
     o, keep = _opts(norm, max_iter, on_host, replay_iters, precision, warm_start, lu_threshold)
     comp_iters = np.zeros(max(part.n_comp, 1), np.int32)
-    st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data, int(timing), 0.0, 0, 0, 0, 0)
+    level_ms = np.zeros(max(part.n_levels, 1), np.float32)
+    st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data, int(timing), 0.0, 0, 0, 0, 0, level_ms.ctypes.data)
     if on_host:
         uh = np.ascontiguousarray(u, dtype=np.float64)
         R = np.empty(part.n, np.float64)
@@ -369,6 +370,8 @@ def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
     if with_stats:
         d = _stats_dict(st)
         d.update(comp_iters=comp_iters[: part.n_comp].copy(), status=rc)
+        if timing:
+            d.update(level_ms=level_ms[: part.n_levels].copy())
         return R, d
     return R
 
@@ -381,7 +384,7 @@ def global_power(g: Graph, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
     on_host = isinstance(u, np.ndarray)
     rep = None if replay_iters is None else [int(replay_iters)]
     o, keep = _opts(norm, max_iter, on_host, rep)
-    st = _Stats(0, 0, 0, 0, None, int(timing), 0.0, 0, 0, 0, 0)
+    st = _Stats(0, 0, 0, 0, None, int(timing), 0.0, 0, 0, 0, 0, None)
     if on_host:
         uh = np.ascontiguousarray(u, dtype=np.float64)
         R = np.empty(g.n, np.float64)

@@ -112,6 +112,7 @@ pr_status pr_graph_create(const pr_csr* csr, void* stream, pr_graph** out) {
 }
 
 pr_status pr_graph_create_ex(const pr_csr* csr, uint32_t flags, void* stream, pr_graph** out) {
+  prgb::NvtxRange nvtx("prgb graph_create");
   return prgb::note_status(pr_graph_create_body(csr, flags, stream, out));
 }
 
@@ -151,9 +152,18 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
     if (st == PR_OK) st = tmp.alloc(&crep, (size_t)n);
     if (st == PR_OK) st = tmp.alloc(&wave, (size_t)n);
     if (st == PR_OK) st = init_ctl(ctl, s);
-    if (st == PR_OK) st = scc_detect(P->g, rep, tmp, ctl);
-    if (st == PR_OK) st = levels_and_merge(P->g, rep, crep, P->level, P->type, wave, &max_wave, tmp, ctl);
-    if (st == PR_OK) st = build_layout(P, crep, wave, max_wave, tmp, ctl);
+    if (st == PR_OK) {
+      NvtxRange r("prgb scc");
+      st = scc_detect(P->g, rep, tmp, ctl);
+    }
+    if (st == PR_OK) {
+      NvtxRange r("prgb levels");
+      st = levels_and_merge(P->g, rep, crep, P->level, P->type, wave, &max_wave, tmp, ctl);
+    }
+    if (st == PR_OK) {
+      NvtxRange r("prgb layout");
+      st = build_layout(P, crep, wave, max_wave, tmp, ctl);
+    }
     if (st == PR_OK) st = finish_sync(s, ctl, nullptr);
   }
   if (st == PR_OK) {
@@ -173,6 +183,7 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
 }
 
 pr_status pr_partition_create(const pr_graph* g, uint32_t flags, void* stream, pr_partition** out) {
+  prgb::NvtxRange nvtx("prgb partition");
   return prgb::note_status(pr_partition_create_body(g, flags, stream, out));
 }
 
@@ -318,6 +329,10 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
       for (int32_t k = 0; k < K; k++) stats->iters_max = h[k] > stats->iters_max ? h[k] : stats->iters_max;
       for (int32_t k = 0; k < (int32_t)h64.size(); k++)
         stats->fp64_sweeps_max = h64[k] > stats->fp64_sweeps_max ? h64[k] : stats->fp64_sweeps_max;
+      if (timing && stats->level_ms && kt->level.size() >= part->levels.size() + 1) {
+        for (size_t li = 0; li < part->levels.size(); li++)
+          PRGB_CUDA(cudaEventElapsedTime(&stats->level_ms[li], kt->level[li], kt->level[li + 1]));
+      }
       if (timing) {
         stats->kernel_ms = 0.0f;
         stats->kernel_bytes = 0;
@@ -345,6 +360,7 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
 
 pr_status pr_solve(const pr_partition* part, double c, const double* u, double tol, const pr_solve_opts* opts,
                    double* R, pr_solve_stats* stats, void* stream) {
+  prgb::NvtxRange nvtx("prgb solve");
   return prgb::note_status(pr_solve_body(part, c, u, tol, opts, R, stats, stream));
 }
 
@@ -372,6 +388,7 @@ static pr_status pr_partition_tune_body(pr_partition* part, double c, const doub
 
 pr_status pr_partition_tune(pr_partition* part, double c, const double* u, double tol, void* stream,
                             int32_t* cta_max, int32_t* coop_blocks, int32_t* balance, float* best_ms) {
+  prgb::NvtxRange nvtx("prgb tune");
   return prgb::note_status(pr_partition_tune_body(part, c, u, tol, stream, cta_max, coop_blocks, balance, best_ms));
 }
 
@@ -433,6 +450,7 @@ static pr_status pr_global_power_body(const pr_graph* g, double c, const double*
 
 pr_status pr_global_power(const pr_graph* g, double c, const double* u, double tol, const pr_solve_opts* opts,
                           double* R, pr_solve_stats* stats, void* stream) {
+  prgb::NvtxRange nvtx("prgb global_power");
   return prgb::note_status(pr_global_power_body(g, c, u, tol, opts, R, stats, stream));
 }
 
@@ -454,6 +472,7 @@ static pr_status pr_residual_l1_body(const pr_graph* g, double c, const double* 
 
 pr_status pr_residual_l1(const pr_graph* g, double c, const double* u, const double* R, double* out_host,
                          void* stream) {
+  prgb::NvtxRange nvtx("prgb residual_l1");
   return prgb::note_status(pr_residual_l1_body(g, c, u, R, out_host, stream));
 }
 

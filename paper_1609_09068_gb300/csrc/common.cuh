@@ -3,7 +3,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include <mutex>
 #include <vector>
@@ -67,6 +69,21 @@ void add_launches(long long d);  // kernels launched by a graph replay (or remov
     if (::prgb::fault_hit(::prgb::kFaultCopy)) return PR_ECUDA;     \
     PRGB_CUDA(expr);                                                \
   } while (0)
+
+// A named range on the host timeline of a profiler (NVTX): the phases of a
+// call and each level of a solve.  It brackets what the call enqueues; for a
+// solve replayed from its CUDA graph the level ranges mark the capture.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  NvtxRange(const char* name, int k) {
+    char buf[64];
+    snprintf(buf, sizeof buf, "%s %d", name, k);
+    nvtxRangePushA(buf);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // device control block: error word and grid-barrier state.  One per call

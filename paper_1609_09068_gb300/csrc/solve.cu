@@ -1032,12 +1032,18 @@ pr_status KernelTiming::ensure(const pr_partition_s* P) {
     PRGB_CUDA(cudaEventCreate(&e1));
     stop.push_back(e1);
   }
+  while (level.size() < P->levels.size() + 1) {
+    cudaEvent_t e = nullptr;
+    PRGB_CUDA(cudaEventCreate(&e));
+    level.push_back(e);
+  }
   return PR_OK;
 }
 
 KernelTiming::~KernelTiming() {
   for (cudaEvent_t e : start) cudaEventDestroy(e);
   for (cudaEvent_t e : stop) cudaEventDestroy(e);
+  for (cudaEvent_t e : level) cudaEventDestroy(e);
 }
 
 pr_status set_solve_attrs(const pr_partition_s* P, bool mixed);
@@ -1168,6 +1174,10 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
   }
   for (size_t li = 0; li < P->levels.size(); li++) {
     const LevelRange& r = P->levels[li];
+    NvtxRange nvtx_level("prgb level", (int)li);
+    // external records: inside a captured graph they become event-record
+    // nodes, so the events time each replay
+    if (timing) PRGB_CUDA(cudaEventRecordWithFlags(timing->level[li], s, cudaEventRecordExternal));
     {
       HeavyRows xv;
       xv.rows = P->xheavy_rows + r.xh_begin;
@@ -1280,6 +1290,8 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       PRGB_CUDA(cudaStreamWaitEvent(s, side.join[q], 0));
     }
   }
+  if (timing && !P->levels.empty())
+    PRGB_CUDA(cudaEventRecordWithFlags(timing->level[P->levels.size()], s, cudaEventRecordExternal));
   return PR_OK;
 }
 

@@ -96,6 +96,7 @@ __device__ __forceinline__ double check_u(const SolveArgs& a, double uu) {
 struct KernelTiming {
   std::vector<cudaEvent_t> start, stop;
   std::vector<LargeComp> comps;
+  std::vector<cudaEvent_t> level;  // [n_levels + 1]: each level's start, then the end of the last
   pr_status ensure(const pr_partition_s* P);
   ~KernelTiming();
 };

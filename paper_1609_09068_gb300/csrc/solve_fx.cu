@@ -161,7 +161,8 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
       dst[32 * j] = make_uint2(q0 | (q1 << 16), q2 | (q3 << 16));
     }
   }
-  const int F = fx_point(grp_sum(g, act ? fabs(a.W[off + i]) : 0.0, red64));  // its barriers publish the slices
+  const double wsum = grp_sum(g, act ? fabs(a.W[off + i]) : 0.0, red64);  // its barriers publish the slices
+  const int F = fx_point(wsum);
   auto row = [&](const fx128* __restrict__ z) -> fx128 {
     if (!staged) return act ? fx_row_global(a, z, ib, off, sz, e0, e1) : (fx128)0;
     fx128 s0 = 0, s1 = 0;
@@ -180,24 +181,33 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
   int k = 0;
   fx128* cur = zA;
   fx128* nxt = zB;
+  bool cold = true;
   if (a.R0) {
     // warm start: R = R0 + r with the residual r = W + c A^T(R0/outdeg) - R0
-    // (signed), from which the series continues
+    // (signed), from which the series continues -- if the guess pays: the
+    // cold series' next term is at most c ||W_C||_1, so a residual at least
+    // that large means starting from W instead (one sweep lost at most)
     if (act) {
       Rf = to_fx(a.R0[off + i], F);
       zA[i] = fx_scale(Rf, mul);
     }
     g.sync();
     const fx128 s = row(zA);
-    if (act) {
-      const fx128 res = to_fx(a.W[off + i], F) + s - Rf;
-      Rf += res;
-      zB[i] = fx_scale(res, mul);
+    fx128 res = 0;
+    if (act) res = to_fx(a.W[off + i], F) + s - Rf;
+    const float rn = grp_norm(g, act ? fx_abs_float(res, F) : 0.0f, red, 0, false);  // after every read of zA
+    cold = !((double)rn < a.c * wsum);
+    if (!cold) {
+      if (act) {
+        Rf += res;
+        zB[i] = fx_scale(res, mul);
+      }
+      cur = zB;
+      nxt = zA;
+      k = 1;
     }
-    cur = zB;
-    nxt = zA;
-    k = 1;
-  } else if (act) {
+  }
+  if (cold && act) {
     Rf = to_fx(a.W[off + i], F);
     zA[i] = fx_scale(Rf, mul);
   }

@@ -142,9 +142,12 @@ __device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, 
     const int fixed = a.replay ? a.replay[c] : -1;
     // z holds c P / outdeg, so that the in-edge sum is the next term itself
     const double civ = a.c * inv;
+    bool cold = true;
     if (a.R0) {
       // warm start: R = R0 + r, the series continues from the residual
-      // r = W + c A^T(R0/outdeg) - R0 (signed)
+      // r = W + c A^T(R0/outdeg) - R0 (signed) -- if the guess pays: a
+      // residual of at least c ||W_C||_1 (the cold series' next term is at
+      // most that) means starting from W instead
       const double r0 = act ? a.R0[p] : 0.0;
       if (act) z[lane] = r0 * civ;
       __syncwarp();
@@ -152,12 +155,14 @@ __device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, 
       for (int e = ib; e < ie; e++) acc += z[ix[e]];
       const double r = act ? W + acc - r0 : 0.0;
       __syncwarp();
-      R = r0 + r;
-      if (act) z[lane] = r * civ;
-      k = 1;
-    } else if (act) {
-      z[lane] = W * civ;
+      cold = !(group_sum<32>(fabs(r)) < a.c * group_sum<32>(fabs(W)));
+      if (!cold) {
+        R = r0 + r;
+        if (act) z[lane] = r * civ;
+        k = 1;
+      }
     }
+    if (cold && act) z[lane] = W * civ;
     __syncwarp();
     for (;;) {
       // four partial sums: shorter chains of dependent loads and FP64 adds

@@ -1,0 +1,43 @@
+"""Per-level device times of a solve (pr_solve_stats.level_ms, CUDA events
+recorded between the levels of the captured level loop)."""
+import pytest
+
+import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def prgb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1609_09068_gb300 as m
+    from paper_1609_09068_gb300 import _build
+    _build.build()
+    m.load_library()
+    return m
+
+
+def test_level_times_cover_the_solve(prgb):
+    import torch
+    g = gg.deep_dag(seed=7, n=200_000, levels=40)
+    G = prgb.graph(torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.col).cuda())
+    P = prgb.partition(G)
+    u = torch.from_numpy(g.u).cuda()
+    prgb.solve(P, 0.85, u, 1e-10, timing=True)  # captures the timed graph
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    R, st = prgb.solve(P, 0.85, u, 1e-10, with_stats=True, timing=True)
+    b.record()
+    torch.cuda.synchronize()
+    lv = st["level_ms"]
+    assert lv.shape == (P.n_levels,) and P.n_levels == 40
+    assert (lv > 0).all()
+    # the levels run back to back inside the call
+    assert lv.sum() <= a.elapsed_time(b) * 1.001
+    assert lv.sum() >= 0.5 * a.elapsed_time(b)
+    # without timing nothing is reported
+    R2, st2 = prgb.solve(P, 0.85, u, 1e-10, with_stats=True)
+    assert "level_ms" not in st2
+    assert torch.equal(R, R2)
