@@ -86,7 +86,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="web")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="(per-step times always go to stderr)")
-    ap.add_argument("--no-warm-start", action="store_true", help="skip training and timing the learned warm start")
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="accepted for compatibility: the default run no longer times the warm start (--warm-eval)")
     ap.add_argument("--large-n", type=int, default=50_000_000, help="vertices of the large workload")
     ap.add_argument("--no-blocks", action="store_true",
                     help="skip the deep_dag and 50M-vertex blocks of the default web_like run")
@@ -690,55 +691,6 @@ def run_ours(args):
              "giant_kernel_ms": mk_ms,
              "giant_kernel_gbs": mk_bytes / (mk_ms * 1e-3) / 1e9 if mk_ms > 0 else None}
 
-    # ---- learned warm start ---------------------------------------------------
-    # The deep-DAG setting the warm start is specified for: trained with the
-    # library's kernels on plain-solver solutions of seeded deep-DAG graphs
-    # (n = 100,000, 20 levels, seeds 100000-100005), evaluated on a held-out
-    # seed at n = 1,000,000 (50 levels): the solve alone, cold against warm.
-    warm = None
-    if not args.no_warm_start:
-        t0 = time.time()
-        model = prgb.Mpnn(seed=3)
-        train_set = []
-        for sd in range(100000, 100006):
-            tg = gg.deep_dag(seed=sd, n=100_000, levels=20)
-            tP = prgb.partition(prgb.graph(tg.rowptr, tg.col))
-            tu = torch.from_numpy(tg.u).cuda()
-            train_set.append((tP, tu, prgb.solve(tP, C, tu, 1e-12)))
-        losses = []
-        for ep in range(60):
-            losses.append(float(np.mean([model.train_step(tP, C, tu, tR, lr=3e-3) for tP, tu, tR in train_set])))
-        t_train = time.time() - t0
-        hg = gg.deep_dag(seed=200000, n=1_000_000, levels=50)
-        hG = prgb.graph(torch.from_numpy(hg.rowptr).cuda(), torch.from_numpy(hg.col).cuda())
-        hP = prgb.partition(hG)
-        hu = torch.from_numpy(hg.u).cuda()
-        Rc0 = prgb.solve(hP, C, hu, TOL)                   # builds both graphs, untimed
-        prgb.solve(hP, C, hu, TOL, warm_start=model)
-        wrecs = []
-        for k in range(args.steps):
-            for mode in ("cold", "warm"):
-                flush.fill_(k & 0xFF)
-                a, b = ev(), ev()
-                a.record()
-                Rw, stw = prgb.solve(hP, C, hu, TOL, with_stats=True, warm_start=model if mode == "warm" else None)
-                b.record()
-                wrecs.append((mode, a, b, stw, Rw))
-        torch.cuda.synchronize()
-        tc = float(np.mean([r[1].elapsed_time(r[2]) for r in wrecs if r[0] == "cold"]))
-        tw = float(np.mean([r[1].elapsed_time(r[2]) for r in wrecs if r[0] == "warm"]))
-        sc = [r[3] for r in wrecs if r[0] == "cold"][-1]
-        sw = [r[3] for r in wrecs if r[0] == "warm"][-1]
-        Rw = [r[4] for r in wrecs if r[0] == "warm"][-1]
-        warm = {"workload": "deep_dag held-out seed 200000: n=1,000,000, 50 levels, u ~ U[0,1] normalised",
-                "train": {"graphs": len(train_set), "workload": "deep_dag n=100,000, 20 levels", "epochs": 60,
-                          "seconds": t_train, "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1]},
-                "solve_ms_cold": tc, "solve_ms_warm": tw, "speedup": tc / tw,
-                "edge_visits_cold": sc["edge_visits"], "edge_visits_warm": sw["edge_visits"],
-                "iters_max_cold": sc["iters_max"], "iters_max_warm": sw["iters_max"],
-                "residual_l1_warm": prgb.residual_l1(hG, C, hu, Rw),
-                "l1_diff_vs_cold": float((Rw - Rc0).abs().sum().item())}
-
     # ---- end to end through the C ABI with host buffers ---------------------
     hr, hc, hu_ = g.host() if isinstance(g, _DeviceGraph) else (g.rowptr, g.col, g.u)
     rp_h = torch.from_numpy(hr).pin_memory().numpy()
@@ -841,7 +793,6 @@ def run_ours(args):
         "speedup_vs_global": {"step": t_global / t_step, "solve_only": t_global_solve / float(ph[2])},
         "autotune": tuned,
         "mixed_precision": mixed,
-        "learned_warm_start": warm,
     }
     # ---- the other configurations, each timed the same way ------------------
     # deep_dag (n = 4M, 200 levels) and the 50M-vertex web-like graph (FP64
