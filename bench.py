@@ -880,14 +880,26 @@ def warm_eval(args):
                     ts.append(a.elapsed_time(b))
                 rec[mode] = {"solve_ms": statistics.median(ts), "iters_max": st["iters_max"],
                              "edge_visits": st["edge_visits"], "residual_l1": prgb.residual_l1(G, C, ud, R)}
+            # the guess is computed once per partition and model version;
+            # re-setting the weights forces it, so this solve pays for it
+            model.set_params(model.get_params())
+            a, b = ev(), ev()
+            a.record()
+            prgb.solve(P, C, ud, TOL, warm_start=model)
+            b.record()
+            torch.cuda.synchronize()
+            rec["warm"]["solve_ms_with_guess"] = a.elapsed_time(b)
             rec["speedup"] = rec["cold"]["solve_ms"] / rec["warm"]["solve_ms"]
+            rec["speedup_with_guess"] = rec["cold"]["solve_ms"] / rec["warm"]["solve_ms_with_guess"]
             seeds.append(rec)
             P.close()
             G.close()
     sp = [r["speedup"] for r in seeds]
+    spg = [r["speedup_with_guess"] for r in seeds]
     line = {
         "metric": "learned warm start: solve time to L1 residual 1e-10, cold / warm (deep_dag, 1 GB300)",
-        "value": statistics.mean(sp) if sp else None, "unit": "x (cold ms / warm ms)", "higher_is_better": True,
+        "value": statistics.mean(spg) if spg else None, "unit": "x (cold ms / warm ms incl. the guess)",
+        "higher_is_better": True, "speedup_guess_cached": statistics.mean(sp) if sp else None,
         "data": "synthetic", "dtype": "f64",
         "config": {"workload": "deep_dag warm start: train %d graphs n=100,000 (5 levels of 20,000), held-out %d "
                                "graphs n=4,000,000 (200 levels), c=0.85, L1 tol 1e-10, FP64" %
@@ -899,6 +911,8 @@ def warm_eval(args):
                      "speedup_max": max(sp) if sp else None,
                      "solve_ms_cold_mean": statistics.mean(r["cold"]["solve_ms"] for r in seeds),
                      "solve_ms_warm_mean": statistics.mean(r["warm"]["solve_ms"] for r in seeds),
+                     "solve_ms_warm_with_guess_mean": statistics.mean(r["warm"]["solve_ms_with_guess"]
+                                                                      for r in seeds),
                      "iters_max_cold_mean": statistics.mean(r["cold"]["iters_max"] for r in seeds),
                      "iters_max_warm_mean": statistics.mean(r["warm"]["iters_max"] for r in seeds),
                      "edge_visits_ratio_mean": statistics.mean(r["warm"]["edge_visits"] / r["cold"]["edge_visits"]

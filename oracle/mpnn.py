@@ -9,16 +9,25 @@ the definition of the guess the GPU computes: a two-layer message-passing
 network over the SCC's internal in-edges, evaluated here in float64 with the
 same bf16-rounded weights.
 
-Per SCC vertex i of component C (internal in-degree d_i >= 1):
-  x_i  = [log1p(d_i), log1p(outdeg_i), log|C|, log(n W_i + 1e-3), 1, 0, 0, 0]
+The solution is R_C = W_C + M_C W_C with M_C = (I - c A_C^T)^-1 - I >= 0, so
+R_i - W_i is about b_i mean_C(W) when W does not vary much inside C, b_i
+being the amplification of row i (the row sum of M_C, weighted by W).  The
+network guesses b_i from the structure alone, so that it can run once per
+graph before the level loop, and the solver forms the guess from the W of
+the level when it gets there (and a guess depends on the graph and the
+network only, so it serves every solve of the partition).  Per SCC vertex i
+of component C (internal in-degree d_i >= 1, internal out-degree o_i,
+external in-degree e_i):
+  x_i  = [log1p(d_i), log1p(outdeg_i), log|C|, o_i / outdeg_i, log1p(e_i),
+          log1p(outdeg_i - o_i), 1, 0]
   m_i  = mean of x_j over the internal in-edges j -> i
   h_i  = relu(A1 x_i + B1 m_i + b1)                       (64)
   m'_i = mean of h_j over the internal in-edges j -> i
   g_i  = relu(A2 h_i + B2 m'_i + b2)                      (64)
   yhat = v . g_i + b3
-target y_i = log(R_i / W_i) for the solved R (vertices with W_i = 0 are
-left out); loss = mean (yhat_i - y_i)^2.  The guess is
-R0_i = W_i exp(clamp(yhat_i, 0, 10)).
+target y_i = log(max((R_i - W_i) / mean_C(W), 1e-6)) for the solved R
+(components with mean_C(W) = 0 are left out); loss = mean (yhat_i - y_i)^2.
+The guess is R0_i = W_i + exp(clamp(yhat_i, -14, 9)) mean_C(W).
 
 Parameters, one float32 vector: A1[64][8], B1[64][8], b1[64], A2[64][64],
 B2[64][64], b2[64], v[64], b3[1] (row-major, output index first).
@@ -32,7 +41,8 @@ H = 64
 SHAPES = [("A1", (H, F0)), ("B1", (H, F0)), ("b1", (H,)), ("A2", (H, H)), ("B2", (H, H)), ("b2", (H,)),
           ("v", (H,)), ("b3", (1,))]
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
-YHAT_MAX = 10.0
+YHAT_MIN, YHAT_MAX = -14.0, 9.0
+B_FLOOR = 1e-6
 
 
 def unpack(theta):
@@ -63,7 +73,8 @@ def features(rowptr, col, part, c, u, R):
     Returns (rows, X, in_ptr, in_src, y, mask): rows are the SCC vertices in
     ascending id; in_ptr/in_src list, per row, the row indices of its
     internal in-neighbours (same component, self-loops dropped); W is formed
-    from R as in Eq. (PR:levels)."""
+    from R as in Eq. (PR:levels) (for the target only: the inputs do not
+    depend on R)."""
     rowptr = np.asarray(rowptr, np.int64)
     col = np.asarray(col, np.int64)
     n = rowptr.shape[0] - 1
@@ -88,18 +99,37 @@ def features(rowptr, col, part, c, u, R):
     order = np.lexsort((src[inte], dst[inte]))
     e_src, e_dst = src[inte][order], dst[inte][order]
     din = np.bincount(ridx[e_dst], minlength=rows.size)
+    dout = np.bincount(ridx[e_src], minlength=rows.size)
+    ein = np.bincount(dst[ext], minlength=n)
     in_ptr = np.concatenate([[0], np.cumsum(din)])
     in_src = ridx[e_src]
     X = np.zeros((rows.size, F0))
     X[:, 0] = np.log1p(din)
     X[:, 1] = np.log1p(outdeg[rows])
     X[:, 2] = np.log(size[comp[rows]])
-    X[:, 3] = np.log(n * W[rows] + 1e-3)
-    X[:, 4] = 1.0
-    Wr = W[rows]
-    mask = Wr > 0
-    y = np.where(mask, np.log(np.where(mask, R[rows], 1.0) / np.where(mask, Wr, 1.0)), 0.0)
+    X[:, 3] = dout / np.maximum(outdeg[rows], 1)
+    X[:, 4] = np.log1p(ein[rows])
+    X[:, 5] = np.log1p(outdeg[rows] - dout)
+    X[:, 6] = 1.0
+    cmean = component_means(comp, part.n_comp, W)
+    mw = cmean[comp[rows]]
+    mask = mw > 0
+    b = np.where(mask, (R[rows] - W[rows]) / np.where(mask, mw, 1.0), 1.0)
+    y = np.where(mask, np.log(np.maximum(b, B_FLOOR)), 0.0)
     return rows, X, in_ptr, in_src, y, mask
+
+
+def component_means(comp, n_comp, W):
+    """mean_C(W) per component C."""
+    comp = np.asarray(comp, np.int64)
+    s = np.zeros(n_comp)
+    np.add.at(s, comp, W)
+    return s / np.maximum(np.bincount(comp, minlength=n_comp), 1)
+
+
+def guess(yhat, W_rows, mean_rows):
+    """R0 of the SCC rows from the network's yhat and the level's W."""
+    return W_rows + np.exp(np.clip(yhat, YHAT_MIN, YHAT_MAX)) * mean_rows
 
 
 def _mean_in(in_ptr, in_src, Hm):

@@ -20,8 +20,9 @@ typedef unsigned __int128 ufx128;
 
 // Binary point for a component whose weights sum (L1) to wsum: every value
 // the series forms is at most 2^17 * wsum in magnitude (terms and partial
-// sums of a cold start are at most wsum; a warm start's residual at most
-// about 2 e^10 wsum), so F = 110 - (exponent of wsum) leaves them below 2^127.
+// sums of a cold start are at most wsum / (1 - c); a warm start's guess is
+// at most (1 + e^9) wsum, its residual about twice that), so
+// F = 110 - (exponent of wsum) leaves them below 2^127.
 // The quantum is then 2^-110 wsum.  Clamped so that every conversion below
 // stays in the normal double range.
 __device__ __forceinline__ int fx_point(double wsum) {

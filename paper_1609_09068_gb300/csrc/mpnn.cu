@@ -3,17 +3,25 @@
 // The paper starts every SCC's power series from P_0 = W (Sec. 4.3.2).  A
 // guess R0 close to the solution shortens the series: continuing from the
 // residual r = W + cA^T(R0/outdeg) - R0 needs log(||r||/tau)/log(1/c)
-// sweeps instead of log(||W||/tau)/log(1/c).  The guess comes from a small
-// network over the SCC's internal in-edges (per SCC vertex i, d_i internal
-// in-edges, component C, inflow-adjusted weight W_i):
-//   x_i  = [log1p(d_i), log1p(outdeg_i), log|C|, log(n W_i + 1e-3), 1, 0, 0, 0]
+// sweeps instead of log(||W||/tau)/log(1/c).  The solution of an SCC is
+// R_C = W_C + M_C W_C with M_C = (I - c A_C^T)^-1 - I >= 0, so R_i - W_i is
+// about b_i mean_C(W), b_i being row i's amplification.  A small network
+// over the SCC's internal in-edges guesses b_i from the structure alone
+// (per SCC vertex i of component C: internal in-degree d_i, internal
+// out-degree o_i, external in-degree e_i):
+//   x_i  = [log1p(d_i), log1p(outdeg_i), log|C|, o_i/outdeg_i, log1p(e_i),
+//           log1p(outdeg_i - o_i), 1, 0]
 //   h_i  = relu(A1 x_i + B1 mean_{j->i} x_j + b1)           (64)
 //   g_i  = relu(A2 h_i + B2 mean_{j->i} h_j + b2)           (64)
-//   yhat = v . g_i + b3,   R0_i = W_i exp(clamp(yhat, 0, 10))
-// trained on y_i = log(R_i / W_i) of solved graphs with the mean squared
-// error.  Weights are kept in float32 for the optimiser (Adam) and rounded
-// to bfloat16 for the forward pass; sums are float32.  The forward pass is
-// a gather of neighbour features (memory bound) followed by a 64 x 128
+//   yhat = v . g_i + b3
+// trained on y_i = log(max((R_i - W_i)/mean_C(W), 1e-6)) of solved graphs
+// with the mean squared error.  The guess is
+//   R0_i = W_i + exp(clamp(yhat_i, -14, 9)) mean_C(W),
+// formed by the solver from the level's W when the level is reached, so the
+// network runs once per partition and model (its inputs are structural).
+// Weights are kept in float32 for the optimiser (Adam) and rounded to
+// bfloat16 for the forward pass; sums are float32.  The forward pass is a
+// gather of neighbour features (memory bound) followed by a 64 x 128
 // matrix-vector product per vertex on the FP32 pipes.
 #include <math.h>
 #include <string.h>
@@ -54,6 +62,7 @@ struct MpLayout {
   int32_t r0, r1;
   const int32_t* int_ptr;
   const int32_t* int_idx;
+  const int32_t* ext_ptr;
   const int32_t* p_outdeg;
   const int32_t* p_comp;
   const int32_t* c_off;
@@ -66,6 +75,7 @@ static MpLayout mp_layout(const pr_partition_s* P, int32_t r0, int32_t r1) {
   L.r1 = r1;
   L.int_ptr = P->int_ptr;
   L.int_idx = P->int_idx;
+  L.ext_ptr = P->ext_ptr;
   L.p_outdeg = P->p_outdeg;
   L.p_comp = P->p_comp;
   L.c_off = P->c_off;
@@ -84,22 +94,42 @@ __device__ __forceinline__ int mp_row(const MpLayout& L, int q, Ctl* ctl) {
 }
 
 // ---- features ---------------------------------------------------------------
-__global__ void mp_feat_k(MpLayout L, const double* __restrict__ W, double nn, float* __restrict__ X) {
+// internal out-degree of the SCC rows of the range: a warp per row adds one
+// to the source of each internal in-edge (dout zeroed by the caller)
+__global__ void mp_dout_k(MpLayout L, int32_t* __restrict__ dout, Ctl* ctl) {
+  const int rows = L.r1 - L.r0;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w0; i < rows; i += nw) {
+    const int p = L.r0 + (int)i;
+    if (!mp_is_scc(L.p_comp, L.c_type, p)) continue;  // warp-uniform
+    for (int e = L.int_ptr[p] + lane; e < L.int_ptr[p + 1]; e += 32) {
+      const int j = mp_row(L, L.int_idx[e], ctl);
+      if (j >= 0) atomicAdd(&dout[j], 1);
+    }
+  }
+}
+
+__global__ void mp_feat_k(MpLayout L, const int32_t* __restrict__ dout, float* __restrict__ X) {
   const int rows = L.r1 - L.r0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
     const int p = L.r0 + i;
     float x[kMpF0] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (mp_is_scc(L.p_comp, L.c_type, p)) {
       const int c = L.p_comp[p];
+      const int od = L.p_outdeg[p], o = dout[i];
       x[0] = log1pf((float)(L.int_ptr[p + 1] - L.int_ptr[p]));
-      x[1] = log1pf((float)L.p_outdeg[p]);
+      x[1] = log1pf((float)od);
       x[2] = logf((float)(L.c_off[c + 1] - L.c_off[c]));
-      x[3] = logf((float)(nn * W[p]) + 1e-3f);
-      x[4] = 1.0f;
+      x[3] = (float)o / (float)max(od, 1);
+      x[4] = log1pf((float)(L.ext_ptr[p + 1] - L.ext_ptr[p]));
+      x[5] = log1pf((float)(od - o));
+      x[6] = 1.0f;
     }
-    float4* o = reinterpret_cast<float4*>(X + (size_t)i * kMpF0);
-    o[0] = make_float4(x[0], x[1], x[2], x[3]);
-    o[1] = make_float4(x[4], x[5], x[6], x[7]);
+    float4* out = reinterpret_cast<float4*>(X + (size_t)i * kMpF0);
+    out[0] = make_float4(x[0], x[1], x[2], x[3]);
+    out[1] = make_float4(x[4], x[5], x[6], x[7]);
   }
 }
 
@@ -155,9 +185,7 @@ constexpr size_t kMpL2Smem = (size_t)(2 * kMpH * kMpH + 2 * kMpH + (kBlock / 32)
 
 __global__ void __launch_bounds__(kBlock) mp_l2_k(MpLayout L, const float* __restrict__ H1,
                                                   const uint16_t* __restrict__ w16, float* __restrict__ yhat,
-                                                  float* __restrict__ G, float* __restrict__ M2,
-                                                  const double* __restrict__ W, double* __restrict__ R0,
-                                                  Ctl* ctl) {
+                                                  float* __restrict__ G, float* __restrict__ M2, Ctl* ctl) {
   extern __shared__ float sm[];
   float* A2t = sm;                    // [k][o]
   float* B2t = sm + kMpH * kMpH;      // [k][o]
@@ -219,15 +247,7 @@ __global__ void __launch_bounds__(kBlock) mp_l2_k(MpLayout L, const float* __res
     }
     if (G) *reinterpret_cast<float2*>(G + (size_t)i * kMpH + 2 * lane) = g2;
     if (M2) *reinterpret_cast<float2*>(M2 + (size_t)i * kMpH + 2 * lane) = m2;
-    if (lane == 0) {
-      if (yhat) yhat[i] = y;
-      if (R0 && scc) {
-        const double w = W[p];
-        double r0 = w * exp((double)fminf(fmaxf(y, 0.0f), 10.0f));
-        if (!isfinite(r0)) r0 = w;
-        R0[p] = r0;
-      }
-    }
+    if (lane == 0 && yhat) yhat[i] = y;
   }
 }
 
@@ -253,16 +273,35 @@ __global__ void mp_w_k(int32_t n, const int32_t* __restrict__ perm, const double
   }
 }
 
-// r_i = yhat_i - y_i on the SCC rows with W > 0 (0 elsewhere), its squared
+// mean_C(W) of every SCC (a warp per component, a fixed-order sum)
+__global__ void mp_cmean_k(int32_t K, const int32_t* __restrict__ c_off, const uint8_t* __restrict__ c_type,
+                           const double* __restrict__ W, double* __restrict__ cmean) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = w0; c < K; c += nw) {
+    if (c_type[c] != PR_TYPE_SCC) continue;  // warp-uniform
+    const int o0 = c_off[c], o1 = c_off[c + 1];
+    double s = 0.0;
+    for (int p = o0 + lane; p < o1; p += 32) s += W[p];
+    s = group_sum<32>(s);
+    if (lane == 0) cmean[c] = s / (double)(o1 - o0);
+  }
+}
+
+// r_i = yhat_i - y_i on the rows of the SCCs with mean_C(W) > 0 (0
+// elsewhere), y_i = log(max((R_i - W_i) / mean_C(W), 1e-6)); its squared
 // sum and the row count
 __global__ void mp_resid_k(int32_t n, const int32_t* __restrict__ p_comp, const uint8_t* __restrict__ c_type,
-                           const double* __restrict__ W, const double* __restrict__ Rp,
-                           const float* __restrict__ yhat, float* __restrict__ r, double* __restrict__ acc) {
+                           const double* __restrict__ W, const double* __restrict__ cmean,
+                           const double* __restrict__ Rp, const float* __restrict__ yhat, float* __restrict__ r,
+                           double* __restrict__ acc) {
   double s = 0.0, cnt = 0.0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     float d = 0.0f;
-    if (mp_is_scc(p_comp, c_type, (int)p) && W[p] > 0.0) {
-      const float y = logf((float)(Rp[p] / W[p]));
+    const int c = p_comp[p];
+    if (c_type[c] == PR_TYPE_SCC && cmean[c] > 0.0) {
+      const float y = logf((float)fmax((Rp[p] - W[p]) / cmean[c], 1e-6));
       d = yhat[p] - y;
       s += (double)d * d;
       cnt += 1.0;
@@ -442,20 +481,57 @@ pr_status mpnn_prepare() {
   return PR_OK;
 }
 
-pr_status mpnn_infer(const pr_mpnn_s* M, const pr_partition_s* P, int32_t r0, int32_t r1, const double* W,
-                     double* R0, const MpnnInfer& buf, cudaStream_t s, int64_t* nl) {
-  if (r1 <= r0) return PR_OK;
+pr_status mpnn_guess(const pr_mpnn_s* M, const pr_partition_s* P, float* yhat, const MpnnInfer& buf, Ctl* ctl,
+                     cudaStream_t s) {
+  const int32_t n = P->g.n;
+  if (n == 0) return PR_OK;
   PRGB_TRY(mpnn_prepare());
-  const MpLayout L = mp_layout(P, r0, r1);
-  const int rows = r1 - r0;
-  mp_feat_k<<<mp_grid(rows, kBlock), kBlock, 0, s>>>(L, W, (double)P->g.n, buf.X);
+  const MpLayout L = mp_layout(P, 0, n);
+  const unsigned gn = mp_grid(n, kBlock), gw = mp_grid(n, kBlock / 32);
+  PRGB_CUDA(cudaMemsetAsync(buf.dout, 0, (size_t)n * 4, s));
+  mp_dout_k<<<gw, kBlock, 0, s>>>(L, buf.dout, ctl);
   PRGB_LAUNCH();
-  mp_l1_k<<<mp_grid(rows, kBlock), kBlock, 0, s>>>(L, buf.X, M->w16, buf.H1, nullptr, nullptr);
+  mp_feat_k<<<gn, kBlock, 0, s>>>(L, buf.dout, buf.X);
   PRGB_LAUNCH();
-  mp_l2_k<<<mp_grid(rows, kBlock / 32), kBlock, kMpL2Smem, s>>>(L, buf.H1, M->w16, nullptr, nullptr, nullptr, W,
-                                                                 R0, nullptr);
+  mp_l1_k<<<gn, kBlock, 0, s>>>(L, buf.X, M->w16, buf.H1, nullptr, ctl);
   PRGB_LAUNCH();
-  *nl += 3;
+  mp_l2_k<<<gw, kBlock, kMpL2Smem, s>>>(L, buf.H1, M->w16, yhat, nullptr, nullptr, ctl);
+  PRGB_LAUNCH();
+  return PR_OK;
+}
+
+// R0 = W + exp(clamp(yhat)) mean_C(W) over the rows of SCC c, a CTA per
+// component (fixed-order block sum); components above kMpMeanMax vertices
+// get R0 = W (the cold start: the guess is not worth a grid-wide sum)
+constexpr int kMpMeanMax = 16384;
+__global__ void mp_level_r0_k(int32_t c0, const int32_t* __restrict__ c_off, const uint8_t* __restrict__ c_type,
+                              const double* __restrict__ W, const float* __restrict__ yhat,
+                              double* __restrict__ R0) {
+  __shared__ double red[kBlock / 32];
+  const int c = c0 + (int)blockIdx.x;
+  if (c_type[c] != PR_TYPE_SCC) return;  // block-uniform
+  const int o0 = c_off[c], o1 = c_off[c + 1], sz = o1 - o0;
+  if (sz > kMpMeanMax) {
+    for (int p = o0 + threadIdx.x; p < o1; p += blockDim.x) R0[p] = W[p];
+    return;
+  }
+  double s = 0.0;
+  for (int p = o0 + threadIdx.x; p < o1; p += blockDim.x) s += W[p];
+  s = group_sum<32>(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  s = group_sum<32>((threadIdx.x & 31) < kBlock / 32 ? red[threadIdx.x & 31] : 0.0);
+  const double mean = s / (double)sz;
+  for (int p = o0 + threadIdx.x; p < o1; p += blockDim.x)
+    R0[p] = W[p] + exp((double)fminf(fmaxf(yhat[p], kMpYMin), kMpYMax)) * mean;
+}
+
+pr_status mpnn_level_r0(const pr_partition_s* P, int32_t c0, int32_t c1, const double* W, const float* yhat,
+                        double* R0, cudaStream_t s, int64_t* nl) {
+  if (c1 <= c0) return PR_OK;
+  mp_level_r0_k<<<(unsigned)(c1 - c0), kBlock, 0, s>>>(c0, P->c_off, P->c_type, W, yhat, R0);
+  PRGB_LAUNCH();
+  ++*nl;
   return PR_OK;
 }
 
@@ -466,10 +542,13 @@ static pr_status mp_pass(pr_mpnn_s* M, const pr_partition_s* P, double c, const 
   cudaStream_t s = tmp.stream();
   const int32_t n = P->g.n;
   PRGB_TRY(mpnn_prepare());
-  double *Rp, *W, *acc;
+  double *Rp, *W, *acc, *cmean;
   float *X, *H1, *G, *M1 = nullptr, *M2 = nullptr, *yh, *dy;
+  int32_t* dout;
   PRGB_TRY(tmp.alloc(&Rp, n));
   PRGB_TRY(tmp.alloc(&W, n));
+  PRGB_TRY(tmp.alloc(&cmean, (size_t)P->n_comp + 1));
+  PRGB_TRY(tmp.alloc(&dout, (size_t)n + 1));
   PRGB_TRY(tmp.alloc(&acc, 2));
   PRGB_TRY(tmp.alloc(&X, (size_t)n * kMpF0));
   PRGB_TRY(tmp.alloc(&H1, (size_t)n * kMpH));
@@ -487,13 +566,19 @@ static pr_status mp_pass(pr_mpnn_s* M, const pr_partition_s* P, double c, const 
   PRGB_LAUNCH();
   mp_w_k<<<gn, kBlock, 0, s>>>(n, P->perm, u, Rp, P->ext_ptr, P->ext_idx, P->p_inv, c, W);
   PRGB_LAUNCH();
-  mp_feat_k<<<gn, kBlock, 0, s>>>(L, W, (double)n, X);
+  PRGB_CUDA(cudaMemsetAsync(cmean, 0, ((size_t)P->n_comp + 1) * 8, s));
+  mp_cmean_k<<<mp_grid(P->n_comp, kBlock / 32), kBlock, 0, s>>>(P->n_comp, P->c_off, P->c_type, W, cmean);
+  PRGB_LAUNCH();
+  PRGB_CUDA(cudaMemsetAsync(dout, 0, ((size_t)n + 1) * 4, s));
+  mp_dout_k<<<gw, kBlock, 0, s>>>(L, dout, ctl);
+  PRGB_LAUNCH();
+  mp_feat_k<<<gn, kBlock, 0, s>>>(L, dout, X);
   PRGB_LAUNCH();
   mp_l1_k<<<gn, kBlock, 0, s>>>(L, X, M->w16, H1, M1, ctl);
   PRGB_LAUNCH();
-  mp_l2_k<<<gw, kBlock, kMpL2Smem, s>>>(L, H1, M->w16, yh, G, M2, nullptr, nullptr, ctl);
+  mp_l2_k<<<gw, kBlock, kMpL2Smem, s>>>(L, H1, M->w16, yh, G, M2, ctl);
   PRGB_LAUNCH();
-  mp_resid_k<<<gn, kBlock, 0, s>>>(n, P->p_comp, P->c_type, W, Rp, yh, dy, acc);
+  mp_resid_k<<<gn, kBlock, 0, s>>>(n, P->p_comp, P->c_type, W, cmean, Rp, yh, dy, acc);
   PRGB_LAUNCH();
   if (yhat_pos) PRGB_CUDA(cudaMemcpyAsync(yhat_pos, yh, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
   if (grad) {
@@ -634,6 +719,7 @@ static pr_status pr_mpnn_set_params_body(pr_mpnn* M, const float* host, int64_t 
   PRGB_CUDA(cudaMemsetAsync(M->m2, 0, kMpParams * 4, s));
   PRGB_CUDA(cudaMemsetAsync(M->grad, 0, kMpParams * 4, s));
   M->step = 0;
+  M->version++;
   mp_to_bf16_k<<<mp_grid(kMpParams, kBlock), kBlock, 0, s>>>(kMpParams, M->master, M->w16);
   PRGB_LAUNCH();
   PRGB_CUDA(cudaStreamSynchronize(s));
@@ -711,6 +797,7 @@ static pr_status pr_mpnn_train_step_body(pr_mpnn* M, const pr_partition* part, d
   PRGB_CUDA(cudaMemsetAsync(M->grad, 0, kMpParams * 4, s));
   PRGB_TRY(mp_pass(M, part, c, u, R, true, nullptr, loss, tmp, ctl));
   M->step++;
+  M->version++;
   const float c1 = 1.0f - powf(0.9f, (float)M->step), c2 = 1.0f - powf(0.999f, (float)M->step);
   mp_adam_k<<<mp_grid(kMpParams, kBlock), kBlock, 0, s>>>(kMpParams, M->master, M->grad, M->m1, M->m2, M->w16, lr,
                                                           c1, c2);

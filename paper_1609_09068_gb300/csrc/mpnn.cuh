@@ -1,6 +1,6 @@
 // mpnn.cuh -- the learned warm start of the SCC power series: a two-layer
 // message-passing network over each SCC's internal in-edges that guesses
-// R_i / W_i (mpnn.cu).
+// each row's amplification (R_i - W_i) / mean_C(W) (mpnn.cu).
 #pragma once
 
 #include "common.cuh"
@@ -21,21 +21,31 @@ constexpr int kMpv = kMpb2 + kMpH;
 constexpr int kMpb3 = kMpv + kMpH;
 constexpr int kMpParams = kMpb3 + 1;
 
-// scratch of one inference pass over rows [r0, r1) of the permuted layout
+// the guess's clamp: R0 = W + exp(clamp(yhat, kMpYMin, kMpYMax)) mean_C(W)
+constexpr float kMpYMin = -14.0f;
+constexpr float kMpYMax = 9.0f;
+
+// scratch of one inference pass over every row of the permuted layout
 struct MpnnInfer {
-  float* X = nullptr;   // [rows][8]
-  float* H1 = nullptr;  // [rows][64]
+  float* X = nullptr;      // [n][8]
+  float* H1 = nullptr;     // [n][64]
+  int32_t* dout = nullptr; // [n] internal out-degree
 };
 
 // one-time kernel attributes of the network's kernels (call before any
 // stream capture that launches them)
 pr_status mpnn_prepare();
 
-// Guess R0 = W * exp(clamp(yhat, 0, 10)) for the SCC rows of [r0, r1)
-// (every internal in-edge of such a row starts inside the range); W and
-// R0 by position.  Launches only (capturable).
-pr_status mpnn_infer(const pr_mpnn_s* M, const pr_partition_s* P, int32_t r0, int32_t r1, const double* W,
-                     double* R0, const MpnnInfer& buf, cudaStream_t s, int64_t* nl);
+// yhat by position for every SCC row (0 elsewhere): the network's guess of
+// log of the row's amplification, from the structure only.  Launches only.
+pr_status mpnn_guess(const pr_mpnn_s* M, const pr_partition_s* P, float* yhat, const MpnnInfer& buf, Ctl* ctl,
+                     cudaStream_t s);
+
+// R0 of the SCC rows of components [c0, c1) from the level's W and yhat
+// (a CTA per component; R0 = W above 16,384 vertices).  One launch
+// (capturable).
+pr_status mpnn_level_r0(const pr_partition_s* P, int32_t c0, int32_t c1, const double* W, const float* yhat,
+                        double* R0, cudaStream_t s, int64_t* nl);
 
 }  // namespace prgb
 
@@ -53,4 +63,5 @@ struct pr_mpnn_s {
   // network is matched by it, not by the handle's address, which a later
   // model may receive once this one is destroyed
   uint64_t uid = 0;
+  uint64_t version = 0;  // bumped by every change of the weights
 };

@@ -1141,6 +1141,7 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
   a.sell_idx = P->sell_idx;
   a.sell_cpre = P->sell_cpre;
   a.R0 = nullptr;
+  a.yhat = nullptr;
   a.lu_threshold = 0;
   a.iters64 = iters64;
   a.W = b.W;
@@ -1157,8 +1158,7 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
 // next level.  Only launches, memsets and event records: it can be
 // captured into a CUDA graph.
 pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& b, bool mixed, SideStreams& side,
-                         cudaStream_t s, KernelTiming* timing, int64_t* nl, const pr_mpnn_s* warm = nullptr,
-                         const MpnnInfer* inf = nullptr) {
+                         cudaStream_t s, KernelTiming* timing, int64_t* nl, const float* yhat = nullptr) {
   Ctl* ctl = a.ctl;
   double* zA = b.zA;
   double* zB = b.zB;
@@ -1192,10 +1192,13 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       PRGB_LAUNCH();
       ++*nl;
     }
-    // learned warm start: the guess R0 of this level's SCC rows, from the
-    // weights W the gather has just formed
-    if (warm && a.R0 && r.vsingle > r.vbeg)
-      PRGB_TRY(mpnn_infer(warm, P, r.vbeg, r.vsingle, a.W, const_cast<double*>(a.R0), *inf, s, nl));
+    // learned warm start: the guess R0 of the level's SCCs that the level
+    // kernel does not take (all of them in mixed precision), from the
+    // weights W the gather has just formed; the level kernel forms its own
+    if (yhat && a.R0) {
+      const int32_t c1 = mixed ? r.single : r.big;
+      PRGB_TRY(mpnn_level_r0(P, r.cbeg, c1, a.W, yhat, const_cast<double*>(a.R0), s, nl));
+    }
     while (li_large < P->large.size() && P->large[li_large].level_idx == (int)li) {
       LargeComp L = P->large[li_large++];
       PRGB_TRY(reset_ctl(ctl, s));
@@ -1386,18 +1389,22 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
   }
   if (warm) PRGB_TRY(mpnn_prepare());
   if (warm && !pl->R0) {
-    // the guess by position and one level's network activations
-    int32_t rows = 0;
-    for (const LevelRange& r : P->levels) rows = std::max(rows, r.vsingle - r.vbeg);
+    // the guess by position, the network's output and its activations
     PRGB_TRY(pl->keep->alloc(&pl->R0, (size_t)n + 1));
-    PRGB_TRY(pl->keep->alloc(&pl->inf.X, (size_t)rows * kMpF0 + 4));
-    PRGB_TRY(pl->keep->alloc(&pl->inf.H1, (size_t)rows * kMpH + 4));
+    PRGB_TRY(pl->keep->alloc(&pl->yhat, (size_t)n + 1));
+    PRGB_TRY(pl->keep->alloc(&pl->inf.X, (size_t)n * kMpF0 + 4));
+    PRGB_TRY(pl->keep->alloc(&pl->inf.H1, (size_t)n * kMpH + 4));
+    PRGB_TRY(pl->keep->alloc(&pl->inf.dout, (size_t)n + 1));
+    pl->yhat_uid = 0;
   }
   if (timing) PRGB_TRY(pl->kt.ensure(P));
   PRGB_TRY(set_solve_attrs(P, mixed));
   SolveArgs a = make_solve_args(P, c, pl->u, tol, norm, max_iter, nullptr, pl->b, pl->iters,
                                 mixed ? pl->iters64 : nullptr, pl->ctl);
-  if (warm) a.R0 = pl->R0;
+  if (warm) {
+    a.R0 = pl->R0;
+    a.yhat = mixed ? nullptr : pl->yhat;
+  }
   a.lu_threshold = lu;
   const long long before = launch_count();
   int64_t nl = 0;
@@ -1409,7 +1416,8 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
     st = PR_ECUDA;
   if (st == PR_OK && wait_limit_us()) nl++;  // the kernel that sets the wait limit
   if (st == PR_OK)
-    st = enqueue_levels(P, a, pl->b, mixed, pl->side, pl->cs, timing ? &pl->kt : nullptr, &nl, warm, &pl->inf);
+    st = enqueue_levels(P, a, pl->b, mixed, pl->side, pl->cs, timing ? &pl->kt : nullptr, &nl,
+                        warm ? pl->yhat : nullptr);
   cudaGraph_t g = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(pl->cs, &g);
   add_launches(before - launch_count());  // captured, not launched
@@ -1458,9 +1466,19 @@ pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_hos
   if (n > 0)
     PRGB_COPY(cudaMemcpyAsync(pl->u, u, (size_t)n * 8, u_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                               s));
+  int64_t nguess = 0;
+  if (warm && (pl->yhat_uid != warm->uid || pl->yhat_ver != warm->version)) {
+    // the network's output depends on the graph and the weights only: once
+    // per partition and model version, before the captured level loop
+    const long long before = launch_count();
+    PRGB_TRY(mpnn_guess(warm, P, pl->yhat, pl->inf, nullptr, s));
+    nguess = launch_count() - before;
+    pl->yhat_uid = warm->uid;
+    pl->yhat_ver = warm->version;
+  }
   PRGB_CUDA(cudaGraphLaunch(ge->exec, s));
   add_launches(ge->nodes);
-  int64_t nl = ge->nodes;
+  int64_t nl = ge->nodes + nguess;
   if (R_on_host) {
     PRGB_TRY(scatter_out(P, pl->b.R, pl->Rout, s, &nl));
     if (n > 0) PRGB_COPY(cudaMemcpyAsync(R, pl->Rout, (size_t)n * 8, cudaMemcpyDeviceToHost, s));

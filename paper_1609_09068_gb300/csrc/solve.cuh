@@ -31,6 +31,8 @@ struct SolveArgs {
   const int32_t* xlorder;   // [n] positions by (level, external in-degree class)
   const float* p_invf;      // [n] 1/outdeg in FP32 (mixed precision only)
   const double* R0;         // [n] warm-start guess by position for SCC rows, or nullptr
+  const float* yhat;        // [n] the network's log-amplification by position: the level kernel forms its
+                            //   own guess from it (FP64 warm start), or nullptr
   const double* civ;        // [n] c / outdeg by position (grid-wide series), or nullptr
   const int32_t* sell_ptr;  // SELL-32 slices of the grid-wide SCCs' light rows (see pr_partition_s)
   const int32_t* sell_idx;
@@ -159,7 +161,9 @@ struct SolvePlan {
   int32_t* iters64 = nullptr;
   double* u = nullptr;
   double* Rout = nullptr;
-  double* R0 = nullptr;             // [n] the warm-start guess by position
+  double* R0 = nullptr;             // [n] the warm-start guess by position (classes outside the level kernel)
+  float* yhat = nullptr;            // [n] the network's output for this partition, by position
+  uint64_t yhat_uid = 0, yhat_ver = 0;  // the model (and its weights' version) yhat was computed with
   MpnnInfer inf;
   ~SolvePlan();
 };

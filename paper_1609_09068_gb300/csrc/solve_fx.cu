@@ -34,6 +34,7 @@
 
 #include "common.cuh"
 #include "fx128.cuh"
+#include "mpnn.cuh"
 #include "solve.cuh"
 #include "warp_solve.cuh"
 
@@ -182,13 +183,15 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
   fx128* cur = zA;
   fx128* nxt = zB;
   bool cold = true;
-  if (a.R0) {
-    // warm start: R = R0 + r with the residual r = W + c A^T(R0/outdeg) - R0
-    // (signed), from which the series continues -- if the guess pays: the
-    // cold series' next term is at most c ||W_C||_1, so a residual at least
-    // that large means starting from W instead (one sweep lost at most)
+  if (a.yhat) {
+    // warm start from the network's guess R0 = W + exp(clamp(yhat)) mean_C(W):
+    // R = R0 + r with the residual r = W + c A^T(R0/outdeg) - R0 (signed),
+    // from which the series continues -- if the guess pays: the cold
+    // series' next term is at most c ||W_C||_1, so a residual at least that
+    // large means starting from W instead (one sweep lost at most)
     if (act) {
-      Rf = to_fx(a.R0[off + i], F);
+      const float y = fminf(fmaxf(a.yhat[off + i], kMpYMin), kMpYMax);
+      Rf = to_fx(a.W[off + i] + exp((double)y) * (wsum / (double)sz), F);
       zA[i] = fx_scale(Rf, mul);
     }
     g.sync();

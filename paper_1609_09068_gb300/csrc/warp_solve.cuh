@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "mpnn.cuh"
 #include "solve.cuh"
 
 namespace prgb {
@@ -143,12 +144,14 @@ __device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, 
     // z holds c P / outdeg, so that the in-edge sum is the next term itself
     const double civ = a.c * inv;
     bool cold = true;
-    if (a.R0) {
-      // warm start: R = R0 + r, the series continues from the residual
+    if (a.yhat) {
+      // warm start from the network's guess R0 = W + exp(clamp(yhat))
+      // mean_C(W): R = R0 + r, the series continues from the residual
       // r = W + c A^T(R0/outdeg) - R0 (signed) -- if the guess pays: a
       // residual of at least c ||W_C||_1 (the cold series' next term is at
       // most that) means starting from W instead
-      const double r0 = act ? a.R0[p] : 0.0;
+      const double mean = group_sum<32>(W) / (double)sz;
+      const double r0 = act ? W + exp((double)fminf(fmaxf(a.yhat[p], kMpYMin), kMpYMax)) * mean : 0.0;
       if (act) z[lane] = r0 * civ;
       __syncwarp();
       double acc = 0.0;

@@ -92,12 +92,39 @@ def test_features_on_a_cycle():
     R = u / (1 - C)
     rows, X, ip, isrc, y, mask = mpnn.features(rp, col, q, C, u, R)
     assert np.array_equal(rows, np.arange(k))
-    expect = np.array([np.log(2), np.log(2), np.log(k), np.log(1 + 1e-3), 1, 0, 0, 0])
+    # in-degree 1, out-degree 1, |C| = k, every out-edge internal, no
+    # external in- or out-edge
+    expect = np.array([np.log(2), np.log(2), np.log(k), 1.0, 0.0, 0.0, 1, 0])
     assert np.allclose(X, expect[None, :])
-    assert np.allclose(y, np.log(1 / (1 - C)))
+    # R = u / (1 - c) and W = u: the amplification is c / (1 - c)
+    assert np.allclose(y, np.log(C / (1 - C)))
     assert mask.all()
+    # ... and the guess built from it is the solution itself
+    assert np.allclose(mpnn.guess(y, u, np.full(k, u.mean())), R)
     # every vertex's in-neighbour is its predecessor on the cycle
     assert np.array_equal(isrc, (np.arange(k) - 1) % k)
+
+
+def test_target_amplification_sums_to_the_internal_mass():
+    """sum_i b_i mean_C(W) = sum_i (R_i - W_i) = ||R_C||_1 - ||W_C||_1 per
+    component, and the external in-degree and internal out-degree features
+    count what they say (a 2-cycle fed by a source, with a leaving edge)."""
+    # 0 -> 1, 1 -> 2, 2 -> 1, 2 -> 3: SCC {1, 2}; 0 and 3 are 1-vertex components
+    rp, col = gg.csr_from_edges(4, [0, 1, 2, 2], [1, 2, 1, 3])
+    q = oracle.partition(rp, col)
+    u = np.array([0.4, 0.1, 0.3, 0.2])
+    R, _ = oracle.solve_cw(rp, col, q, C, u, 1e-15)
+    rows, X, ip, isrc, y, mask = mpnn.features(rp, col, q, C, u, R)
+    assert np.array_equal(rows, [1, 2])
+    assert np.allclose(X[:, 3], [1.0, 0.5])           # 1 -> 2 internal; 2 -> 1 of 2 out-edges
+    assert np.allclose(X[:, 4], np.log1p([1.0, 0.0]))  # 0 -> 1 enters from outside
+    assert np.allclose(X[:, 5], np.log1p([0.0, 1.0]))  # 2 -> 3 leaves
+    W = u[rows].copy()
+    W[0] += C * R[0]                                   # inflow of vertex 1 from vertex 0
+    mw = W.mean()
+    b = np.exp(y)
+    assert np.isclose((b * mw).sum(), (R[rows] - W).sum())
+    assert np.allclose(mpnn.guess(y, W, np.full(2, mw)), R[rows])
 
 
 def test_bf16_rounding_cases():
