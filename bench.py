@@ -41,7 +41,7 @@ FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the grid-wide SCC kernel, from
 # an ncu capture of the current kernel on that workload (the summary under
 # profiles/ gives the command); None where no capture was taken
-TRAFFIC_BYTES = {"web": 28_271_616 + 1_505_024}
+TRAFFIC_BYTES = {"web": 23_848_704 + 1_018_368}
 
 WORKLOADS = {
     "web": ("web_like: n=1,000,000, mean out-degree 8, Zipf(2.1) degrees, giant SCC 40%, "
@@ -96,6 +96,10 @@ def parse():
                          "evaluate on 20 held-out graphs of n=4,000,000 against cold start (one JSON line)")
     ap.add_argument("--warm-train", type=int, default=1000, help="training graphs of --warm-eval")
     ap.add_argument("--warm-held", type=int, default=20, help="held-out graphs of --warm-eval")
+    ap.add_argument("--profile-solves", type=int, default=0,
+                    help="for profilers: prepare and partition the workload, run this many FP64 solves, exit")
+    ap.add_argument("--shape", default=None,
+                    help="cta_max,coop_blocks,balance of --profile-solves (default: the autotuner's choice)")
     ap.add_argument("--cpu-parallel-worker", action="store_true",
                     help="internal: time the multi-core CPU baseline and print one JSON line")
     return ap.parse_args()
@@ -924,8 +928,42 @@ def warm_eval(args):
     return 0
 
 
+def profile_solves(args):
+    """A short run for profilers: graph, partition, the launch shape, then
+    --profile-solves FP64 solves (one launch of the grid-wide SCC kernel per
+    large SCC and one level-kernel launch per level each); one line out."""
+    import torch
+    import paper_1609_09068_gb300 as prgb
+    prgb.load_library()
+    g = load_workload(args.workload, args.large_n)
+    if isinstance(g, _DeviceGraph):
+        rp, cl, u = g.rowptr_d, g.col_d, g.u_d
+    else:
+        rp, cl, u = (torch.from_numpy(x).cuda() for x in (g.rowptr, g.col, g.u))
+    G = prgb.graph(rp, cl)
+    P = prgb.partition(G)
+    if args.shape:
+        cm, cb, bl = (int(x) for x in args.shape.split(","))
+        P.set_shape(cm, cb, bl)
+        shape = {"cta_max": cm, "coop_blocks": cb, "balance": bl}
+    else:
+        shape = P.tune(C, u, TOL)
+    for _ in range(args.profile_solves):
+        R = prgb.solve(P, C, u, TOL)
+    # one more, timed (it comes after the launches a profiler captures with -s/-c)
+    R, st = prgb.solve(P, C, u, TOL, with_stats=True, timing=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.workload, "solves": args.profile_solves, "shape": shape,
+                      "levels": P.n_levels, "residual_l1": prgb.residual_l1(G, C, u, R),
+                      "grid_scc_kernel": {"launches": st["kernel_launches"], "ms": st["kernel_ms"],
+                                          "algorithmic_bytes": st["kernel_bytes"]}}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_solves > 0:
+        return profile_solves(args)
     if args.cpu_parallel_worker:
         return cpu_parallel_worker(args)
     if args.warm_eval:
