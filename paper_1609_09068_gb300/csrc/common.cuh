@@ -428,6 +428,10 @@ pr_status build_inv(const int32_t* deg, int32_t n, Arena& keep, double** inv, cu
 pr_status build_heavy(const int32_t* ptr, int32_t nrows, Arena& keep, Arena& tmp, int32_t** rows,
                       int32_t** choff, int32_t** chrow, int32_t* nheavy, int32_t* nchunks);
 
+// fx_sched.cu: the conflict-free slices of the fixed-point series (after
+// the layout).
+pr_status build_fx_sched(pr_partition_s* P, Arena& tmp, Ctl* ctl);
+
 // ingest.cu: validate the CSR, drop loops, build out- and in-adjacency.
 // Buffers of g are allocated from `keep`; scratch from `tmp`.
 pr_status ingest(const pr_csr* csr, uint32_t flags, DevGraph* g, Arena& keep, Arena& tmp, Ctl* ctl);
@@ -540,6 +544,14 @@ struct pr_partition_s {
   int32_t* sell_idx = nullptr;
   int32_t* sell_cpre = nullptr;
   int32_t nsell = 0;
+  // conflict-free slices of the SCCs of the fixed-point level kernel
+  // (fx_sched.cu): per component the word offset of its slices in fxs_words
+  // (-1: none, the kernel builds them), the index of its first warp in
+  // fxs_wcnt; per warp its words a lane.  Null when no component has one.
+  int32_t* fxs_ptr = nullptr;
+  int32_t* fxs_wbase = nullptr;
+  uint8_t* fxs_wcnt = nullptr;
+  uint2* fxs_words = nullptr;
   std::vector<prgb::LevelRange> levels;  // host, processing order
   std::vector<int32_t> h_c_off;          // host copy of c_off [K+1]
   int32_t cta_max = prgb::kCtaCompMax;   // largest component of the one-CTA class (tunable)

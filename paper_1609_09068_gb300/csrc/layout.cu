@@ -628,6 +628,7 @@ pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wa
     }
     PRGB_TRY(build_sell(P, hrows, tmp, ctl));
   }
+  PRGB_TRY(build_fx_sched(P, tmp, ctl));
   // rows with many external in-edges (the inflow gather of Eq. PR:levels)
   // and the light rows of each level ordered by external in-degree class
   {

@@ -1140,6 +1140,10 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
   a.sell_ptr = P->sell_ptr;
   a.sell_idx = P->sell_idx;
   a.sell_cpre = P->sell_cpre;
+  a.fxs_ptr = P->fxs_ptr;
+  a.fxs_wbase = P->fxs_wbase;
+  a.fxs_wcnt = P->fxs_wcnt;
+  a.fxs_words = P->fxs_words;
   a.R0 = nullptr;
   a.yhat = nullptr;
   a.lu_threshold = 0;

@@ -34,6 +34,10 @@ struct SolveArgs {
   const float* yhat;        // [n] the network's log-amplification by position: the level kernel forms its
                             //   own guess from it (FP64 warm start), or nullptr
   const double* civ;        // [n] c / outdeg by position (grid-wide series), or nullptr
+  const int32_t* fxs_ptr;   // conflict-free slices of the fixed-point series (see pr_partition_s), or nullptr
+  const int32_t* fxs_wbase;
+  const uint8_t* fxs_wcnt;
+  const uint2* fxs_words;
   const int32_t* sell_ptr;  // SELL-32 slices of the grid-wide SCCs' light rows (see pr_partition_s)
   const int32_t* sell_idx;
   const int32_t* sell_cpre;

@@ -54,11 +54,12 @@ struct Grp {
 
 // Shared memory of one group (its part of the CTA's, `bytes` long): the
 // scratch (reduction partials and the per-warp slice widths), the z pair of
-// cap + 1 entries each (entry cap ... sz is the zero that padded slice
-// entries read), then the staged in-edges.
+// cap + kFxZeros entries each (entries sz .. sz + 7 are the zeros that
+// padded slice entries read, one per bank group), then the staged in-edges.
 constexpr int kFxScratch = 768;
+constexpr int kFxZeros = 8;
 __host__ __device__ constexpr size_t fx_group_fixed(int cap) {
-  return kFxScratch + (size_t)2 * (cap + 1) * sizeof(fx128);
+  return kFxScratch + (size_t)2 * (cap + kFxZeros) * sizeof(fx128);
 }
 
 // deterministic sum over the group (fixed tree)
@@ -106,10 +107,13 @@ __device__ __forceinline__ float grp_norm(const Grp<T>& g, float part, float* re
 // The in-edges are staged as one slice per warp (SELL-32, Sec. 4.3.2's
 // sweep is a gather over them): lane l of warp w holds its row's local
 // source indices, 16 bits each, four to an 8-byte word, word j at
-// slice_w + 32 j + l; every row of the warp is padded to the warp's longest
-// (rounded up to 4) with index sz, whose z entry is zero.  The layout order
-// puts rows of similar in-degree next to each other, so the padding is
-// small, and each word load is one coalesced access for the warp.
+// slice_w + 32 j + l, and each word load is one coalesced access for the
+// warp.  Where the partition holds the component's conflict-free slices
+// (fx_sched.cu: every column's eight lanes of a phase read distinct bank
+// groups of z), they are copied in; otherwise they are built here from the
+// CSR, every row of the warp padded to the warp's longest (rounded up to 4)
+// with index sz, whose z entry is zero (the layout order puts rows of
+// similar in-degree next to each other, so the padding is small).
 //
 // Per sweep and row: the exact fixed-point sum of z over the in-edges (the
 // next term p), R += p, z' = p c/outdeg as the exact product rounded once to
@@ -123,8 +127,8 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
   double* red64 = reinterpret_cast<double*>(base + 256);       // [kNW]
   int* wcnt = reinterpret_cast<int*>(base + 512);              // [kNW] words per lane of each slice
   fx128* zA = reinterpret_cast<fx128*>(base + kFxScratch);
-  fx128* zB = zA + cap + 1;
-  unsigned char* tail = reinterpret_cast<unsigned char*>(zB + cap + 1);
+  fx128* zB = zA + cap + kFxZeros;
+  unsigned char* tail = reinterpret_cast<unsigned char*>(zB + cap + kFxZeros);
   const size_t room = bytes - (size_t)(tail - base);
   const int i = g.tid, lane = i & 31, wib = i >> 5;
   const bool act = i < sz;
@@ -133,11 +137,14 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
   const int fixed = a.replay ? a.replay[c] : -1;
   const FxMul mul = fx_mul_of(act ? a.c * a.p_inv[off + i] : 0.0);
   const int e0 = act ? a.int_ptr[off + i] - ib : 0, e1 = act ? a.int_ptr[off + i + 1] - ib : 0;
-  const int words = (__reduce_max_sync(0xffffffffu, (unsigned)(e1 - e0)) + 3) >> 2;
+  const bool pre = a.fxs_ptr != nullptr && a.fxs_ptr[c] >= 0;
+  int words;
+  if (pre) words = wib < (sz + 31) / 32 ? (int)a.fxs_wcnt[a.fxs_wbase[c] + wib] : 0;
+  else words = (int)((__reduce_max_sync(0xffffffffu, (unsigned)(e1 - e0)) + 3) >> 2);
   if (lane == 0) wcnt[wib] = words;
-  if (i == 0) {
-    zA[sz] = 0;
-    zB[sz] = 0;
+  if (i < kFxZeros) {
+    zA[sz + i] = 0;
+    zB[sz + i] = 0;
   }
   g.sync();
   int slice = 0, total = 0;  // this warp's first word, all slices' words
@@ -146,26 +153,39 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
     slice += w < wib ? u : 0;
     total += u;
   }
-  // the slices, built from a staged copy of the CSR at the end of the space
-  const bool staged = (size_t)total * 8 + (size_t)m * 2 <= room;
-  const uint2* ell = reinterpret_cast<const uint2*>(tail) + slice + lane;
-  if (staged) {
-    uint16_t* csr = reinterpret_cast<uint16_t*>(base + bytes) - m;
-    for (int e = i; e < m; e += T) csr[e] = (uint16_t)local_or_err(a, a.int_idx[ib + e] - off, sz);
-    g.sync();
-    uint2* dst = reinterpret_cast<uint2*>(tail) + slice + lane;
-    const unsigned pad = (unsigned)sz;
-    for (int j = 0; j < words; j++) {
-      const int e = e0 + 4 * j;
-      const unsigned q0 = e < e1 ? csr[e] : pad, q1 = e + 1 < e1 ? csr[e + 1] : pad;
-      const unsigned q2 = e + 2 < e1 ? csr[e + 2] : pad, q3 = e + 3 < e1 ? csr[e + 3] : pad;
-      dst[32 * j] = make_uint2(q0 | (q1 << 16), q2 | (q3 << 16));
+  // sliced: the rows read slices (else each row reads its CSR from global)
+  bool sliced;
+  const uint2* ell;
+  if (pre) {
+    // the partition's slices: copied in when they fit, else read in place
+    const uint2* src = a.fxs_words + a.fxs_ptr[c];
+    const bool fits = (size_t)total * 8 <= room;
+    if (fits)
+      for (int t = i; t < total; t += T) reinterpret_cast<uint2*>(tail)[t] = src[t];
+    ell = (fits ? reinterpret_cast<const uint2*>(tail) : src) + slice + lane;
+    sliced = true;
+  } else {
+    // the slices, built from a staged copy of the CSR at the end of the space
+    sliced = (size_t)total * 8 + (size_t)m * 2 <= room;
+    ell = reinterpret_cast<const uint2*>(tail) + slice + lane;
+    if (sliced) {
+      uint16_t* csr = reinterpret_cast<uint16_t*>(base + bytes) - m;
+      for (int e = i; e < m; e += T) csr[e] = (uint16_t)local_or_err(a, a.int_idx[ib + e] - off, sz);
+      g.sync();
+      uint2* dst = reinterpret_cast<uint2*>(tail) + slice + lane;
+      const unsigned pad = (unsigned)sz;
+      for (int j = 0; j < words; j++) {
+        const int e = e0 + 4 * j;
+        const unsigned q0 = e < e1 ? csr[e] : pad, q1 = e + 1 < e1 ? csr[e + 1] : pad;
+        const unsigned q2 = e + 2 < e1 ? csr[e + 2] : pad, q3 = e + 3 < e1 ? csr[e + 3] : pad;
+        dst[32 * j] = make_uint2(q0 | (q1 << 16), q2 | (q3 << 16));
+      }
     }
   }
   const double wsum = grp_sum(g, act ? fabs(a.W[off + i]) : 0.0, red64);  // its barriers publish the slices
   const int F = fx_point(wsum);
   auto row = [&](const fx128* __restrict__ z) -> fx128 {
-    if (!staged) return act ? fx_row_global(a, z, ib, off, sz, e0, e1) : (fx128)0;
+    if (!sliced) return act ? fx_row_global(a, z, ib, off, sz, e0, e1) : (fx128)0;
     fx128 s0 = 0, s1 = 0;
 #pragma unroll 1
     for (int j = 0; j < words; j++) {
