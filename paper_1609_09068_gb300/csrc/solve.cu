@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
     if (act) Rs[i] = R;
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
+    const float thr = stop_thr32(tau);
     const int fixed = a.replay ? a.replay[c] : -1;
     // one row per thread; z holds c P / outdeg, so that the in-edge sum is
     // the next term itself
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t 
         if (k >= fixed) break;
         continue;
       }
-      if (!keep_going32(s2, tau, a.norm)) break;
+      if (!keep_going32(s2, thr, a.norm)) break;
       if (k >= a.max_iter) {
         if (threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
         break;
@@ -566,6 +567,7 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
     }
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
+    const float thr = stop_thr32(tau);
     const int fixed = a.replay ? a.replay[c] : -1;
     const bool is_max = a.norm != PR_NORM_L1;
     // iv holds c / outdeg during the series (z = c P / outdeg: the in-edge
@@ -605,7 +607,7 @@ __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads)
         if (k >= fixed) break;
         continue;
       }
-      if (!keep_going32(s2, tau, a.norm)) break;
+      if (!keep_going32(s2, thr, a.norm)) break;
       if (k >= a.max_iter) {
         if (rank == 0 && threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
         break;

@@ -63,10 +63,15 @@ __device__ __forceinline__ bool keep_going(double s, double tau, int norm) {
 // margin of 1e-4 on the test keeps the FP64 norm at or below the threshold
 // whenever the series stops (it may run one iteration longer than an exact
 // test would).
+// The test runs in FP32 against thr = tau / margin rounded down to a float
+// (stop_thr32, once per component), so stopping still implies
+// s * margin <= tau, and a sweep pays no FP64 instruction for it (GB300's
+// FP64 pipe takes ~76 cycles to issue one warp instruction per
+// sub-partition).
 constexpr double kNormMargin = 1.0 + 1e-4;
-__device__ __forceinline__ bool keep_going32(float s, double tau, int norm) {
-  const double sd = (double)s * kNormMargin;
-  return norm == PR_NORM_LINF ? (sd >= tau) : (sd > tau);
+__device__ __forceinline__ float stop_thr32(double tau) { return __double2float_rd(tau / kNormMargin); }
+__device__ __forceinline__ bool keep_going32(float s, float thr, int norm) {
+  return norm == PR_NORM_LINF ? (s >= thr) : (s > thr);
 }
 
 // |x| as a float, from the bit pattern of the double: the sign dropped, the

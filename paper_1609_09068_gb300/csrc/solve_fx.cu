@@ -134,6 +134,7 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
   const bool act = i < sz;
   const bool l1 = a.norm == PR_NORM_L1;
   const double tau = l1 ? a.tol * (double)sz / (double)a.n : a.tol;
+  const float thr = stop_thr32(tau);
   const int fixed = a.replay ? a.replay[c] : -1;
   const FxMul mul = fx_mul_of(act ? a.c * a.p_inv[off + i] : 0.0);
   const int e0 = act ? a.int_ptr[off + i] - ib : 0, e1 = act ? a.int_ptr[off + i + 1] - ib : 0;
@@ -252,7 +253,7 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
       if (k >= fixed) break;
       continue;
     }
-    if (!keep_going32(s2, tau, a.norm)) break;
+    if (!keep_going32(s2, thr, a.norm)) break;
     if (k >= a.max_iter) {
       if (g.tid == 0) atomicOr(&a.ctl->flags[0], 1);
       break;

@@ -140,6 +140,7 @@ __device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, 
     R = warp_series_mixed(a, act, W, inv, ix, ib, ie, z, zf, tau, &k, &k64, warm, warm && act ? a.R0[p] : 0.0);
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
+    const float thr = stop_thr32(tau);
     const int fixed = a.replay ? a.replay[c] : -1;
     // z holds c P / outdeg, so that the in-edge sum is the next term itself
     const double civ = a.c * inv;
@@ -192,7 +193,7 @@ __device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, 
       }
       const float pf = abs_to_float(pn);  // terms are signed after a warm start
       const float s = a.norm == PR_NORM_L1 ? group_sumf<32>(pf) : group_maxf<32>(pf);
-      if (!keep_going32(s, tau, a.norm)) break;
+      if (!keep_going32(s, thr, a.norm)) break;
       if (k >= a.max_iter) {
         if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
         break;
