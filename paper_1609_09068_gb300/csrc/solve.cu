@@ -41,13 +41,12 @@ constexpr int kWarpBlock = 64;  // two components per block, spread over many SM
 
 template <bool kMixed>
 __global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t cbeg, int32_t cend) {
-  __shared__ double zsh[kWarpBlock / 32][32];
-  __shared__ float zfsh[kWarpBlock / 32][32];
+  __shared__ __align__(16) unsigned char zsh[kWarpBlock / 32][kWarpZBytes];
   __shared__ uint8_t ish[kWarpBlock / 32][kWarpEdges];
   const int wib = threadIdx.x >> 5;
   const int c = cbeg + (int)blockIdx.x * (kWarpBlock / 32) + wib;
   if (c >= cend) return;  // warp-uniform
-  warp_component<kMixed>(a, c, zsh[wib], zfsh[wib], ish[wib]);
+  warp_component<kMixed>(a, c, zsh[wib], ish[wib]);
 }
 
 // ---------------------------------------------------------------------------

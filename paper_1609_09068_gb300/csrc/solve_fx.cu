@@ -212,7 +212,7 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
     // large means starting from W instead (one sweep lost at most)
     if (act) {
       const float y = fminf(fmaxf(a.yhat[off + i], kMpYMin), kMpYMax);
-      Rf = to_fx(a.W[off + i] + exp((double)y) * (wsum / (double)sz), F);
+      Rf = to_fx(a.W[off + i] + (double)expf(y) * (wsum / (double)sz), F);
       zA[i] = fx_scale(Rf, mul);
     }
     g.sync();
@@ -328,7 +328,8 @@ constexpr int kLevelThreads = 1024;
 constexpr int kQuarter = 256;
 constexpr size_t kLevelSmem = 200 * 1024;  // one CTA per SM
 constexpr size_t kQuarterBytes = kLevelSmem / 4;
-constexpr size_t kWarpBytes = 32 * sizeof(double) + 32 * sizeof(float) + kWarpEdges;
+constexpr size_t kWarpBytes = kWarpZBytes + kWarpEdges;
+static_assert(kWarpBytes % 16 == 0, "every warp's z space stays 16-byte aligned");
 static_assert(kLevelThreads / kQuarter == 4, "four quarters per CTA");
 static_assert(kCtaCompMax <= kQuarter, "a quarter holds one row per thread");
 
@@ -387,9 +388,7 @@ __global__ void __launch_bounds__(kLevelThreads, 1) solve_level_k(SolveArgs a, L
     nfree += G - lo;
   }
   unsigned char* wb = qbase + (size_t)wq * kWarpBytes;
-  double* z = reinterpret_cast<double*>(wb);
-  float* zf = reinterpret_cast<float*>(z + 32);
-  uint8_t* ix = reinterpret_cast<uint8_t*>(zf + 32);
+  uint8_t* ix = wb + kWarpZBytes;
   for (bool first = rank >= 0;; first = false) {
     int i = 0;
     const int d = (wq - q + kQuarter / 32) % (kQuarter / 32);
@@ -397,7 +396,7 @@ __global__ void __launch_bounds__(kLevelThreads, 1) solve_level_k(SolveArgs a, L
     i = __shfl_sync(0xffffffffu, i, 0);
     const int c = w.small0 + i;
     if (c >= w.small1) break;
-    warp_component<false>(a, c, z, zf, ix);
+    warp_component<false>(a, c, wb, ix);
     __syncwarp();
   }
 }

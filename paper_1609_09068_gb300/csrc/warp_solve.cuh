@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "fx128.cuh"
 #include "mpnn.cuh"
 #include "solve.cuh"
 
@@ -34,6 +35,9 @@ constexpr int kMixRounds = 6;
 // as 8-bit local indices, so each series iteration reads shared memory only.
 // ---------------------------------------------------------------------------
 constexpr int kWarpEdges = kWarpCompMax * (kWarpCompMax - 1);
+// the warp's z space: 32 fixed-point entries (FP64 mode), or 32 doubles and
+// 32 floats (mixed precision); 16-byte aligned
+constexpr int kWarpZBytes = 32 * 16;
 
 // FP32 series with FP64 residual refinement (see kMixKappa) for one warp's
 // component; W is this lane's weight.  Returns the result R of this lane and
@@ -103,13 +107,43 @@ static __device__ double warp_series_mixed(const SolveArgs& a, bool act, double 
   return R;
 }
 
-// One warp solves component c: z (32 doubles), zf (32 floats, mixed
-// precision only) and ix (kWarpEdges bytes) are the warp's own shared memory.
+// Warm start of a warp's fixed-point series from the network's guess
+// R0 = W + exp(clamp(yhat)) mean_C(W): R = R0 + r, the series continuing from
+// the residual r = W + c A^T(R0/outdeg) - R0 (signed), written to zx as
+// r c/outdeg with *Rf = R0 + r -- if the guess pays: a residual of at least
+// c ||W_C||_1 (the cold series' next term is at most that) returns false,
+// the caller then starts from W (*Rf = W is left as it was).  Run once per
+// component, outside the sweep loop's registers.
+static __device__ __noinline__ bool warp_fx_warm(const SolveArgs& a, int p, bool act, double W, double mean, int F,
+                                                 FxMul mul, const uint8_t* ix, int ib, int ie, fx128* zx, fx128* Rf) {
+  const int lane = threadIdx.x & 31;
+  const fx128 r0 =
+      act ? to_fx(W + (double)expf(fminf(fmaxf(a.yhat[p], kMpYMin), kMpYMax)) * mean, F) : (fx128)0;
+  if (act) zx[lane] = fx_scale(r0, mul);
+  __syncwarp();
+  fx128 acc = 0;
+  for (int e = ib; e < ie; e++) acc += zx[ix[e]];
+  const fx128 res = act ? *Rf + acc - r0 : (fx128)0;
+  __syncwarp();
+  const double wsum = mean * (double)__popc(__ballot_sync(0xffffffffu, act));
+  if (!((double)group_sumf<32>(fx_abs_float(res, F)) < a.c * wsum)) return false;
+  *Rf = r0 + res;
+  if (act) zx[lane] = fx_scale(res, mul);
+  return true;
+}
+
+// One warp solves component c in its own shared memory: zbuf (kWarpZBytes,
+// 16-byte aligned) and ix (kWarpEdges bytes).  FP64 mode runs the SCC
+// series in exact 128-bit fixed point (fx128.cuh, as for the larger
+// components): a row's in-edge sum and R are exact integer sums, z' = P
+// c/outdeg the exact product rounded once, and a sweep has no floating-point
+// arithmetic.  CACs take one FP64 pass over their sub-levels.
 template <bool kMixed>
-__device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, uint8_t* ix) {
+__device__ void warp_component(const SolveArgs& a, int c, unsigned char* zbuf, uint8_t* ix) {
   const int lane = threadIdx.x & 31;
   const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
   if (sz < a.lu_threshold && a.c_type[c] == PR_TYPE_SCC) return;  // solved by solve_lu_k (warp-uniform)
+  double* z = reinterpret_cast<double*>(zbuf);
   const bool act = lane < sz;
   const int p = off + lane;
   const double inv = act ? a.p_inv[p] : 0.0;
@@ -134,7 +168,8 @@ __device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, 
       }
       __syncwarp();
     }
-  } else if (kMixed) {
+  } else if constexpr (kMixed) {
+    float* zf = reinterpret_cast<float*>(zbuf + 32 * sizeof(double));
     const double tau = a.tol * (double)sz / (double)a.n;
     const bool warm = a.R0 != nullptr;
     R = warp_series_mixed(a, act, W, inv, ix, ib, ie, z, zf, tau, &k, &k64, warm, warm && act ? a.R0[p] : 0.0);
@@ -142,48 +177,31 @@ __device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, 
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const float thr = stop_thr32(tau);
     const int fixed = a.replay ? a.replay[c] : -1;
-    // z holds c P / outdeg, so that the in-edge sum is the next term itself
-    const double civ = a.c * inv;
-    bool cold = true;
-    if (a.yhat) {
-      // warm start from the network's guess R0 = W + exp(clamp(yhat))
-      // mean_C(W): R = R0 + r, the series continues from the residual
-      // r = W + c A^T(R0/outdeg) - R0 (signed) -- if the guess pays: a
-      // residual of at least c ||W_C||_1 (the cold series' next term is at
-      // most that) means starting from W instead
-      const double mean = group_sum<32>(W) / (double)sz;
-      const double r0 = act ? W + exp((double)fminf(fmaxf(a.yhat[p], kMpYMin), kMpYMax)) * mean : 0.0;
-      if (act) z[lane] = r0 * civ;
-      __syncwarp();
-      double acc = 0.0;
-      for (int e = ib; e < ie; e++) acc += z[ix[e]];
-      const double r = act ? W + acc - r0 : 0.0;
-      __syncwarp();
-      cold = !(group_sum<32>(fabs(r)) < a.c * group_sum<32>(fabs(W)));
-      if (!cold) {
-        R = r0 + r;
-        if (act) z[lane] = r * civ;
-        k = 1;
-      }
-    }
-    if (cold && act) z[lane] = W * civ;
+    // z holds c P / outdeg in fixed point, so that the in-edge sum is the
+    // next term itself
+    fx128* zx = reinterpret_cast<fx128*>(zbuf);
+    const double wsum = group_sum<32>(W);  // W >= 0
+    const int F = fx_point(wsum);
+    const FxMul mul = fx_mul_of(a.c * inv);
+    fx128 Rf = act ? to_fx(W, F) : (fx128)0;
+    const bool cold = !(a.yhat && warp_fx_warm(a, p, act, W, wsum / (double)sz, F, mul, ix, ib, ie, zx, &Rf));
+    if (cold && act) zx[lane] = fx_scale(Rf, mul);
+    if (!cold) k = 1;
     __syncwarp();
     for (;;) {
-      // four partial sums: shorter chains of dependent loads and FP64 adds
-      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+      // two carry chains of exact adds
+      fx128 s0 = 0, s1 = 0;
       int e = ib;
-      for (; e + 3 < ie; e += 4) {
-        acc0 += z[ix[e]];
-        acc1 += z[ix[e + 1]];
-        acc2 += z[ix[e + 2]];
-        acc3 += z[ix[e + 3]];
+      for (; e + 1 < ie; e += 2) {
+        s0 += zx[ix[e]];
+        s1 += zx[ix[e + 1]];
       }
-      for (; e < ie; e++) acc0 += z[ix[e]];
-      const double pn = (acc0 + acc1) + (acc2 + acc3);
+      if (e < ie) s0 += zx[ix[e]];
+      const fx128 pn = s0 + s1;  // the next term, exact
       __syncwarp();
       if (act) {
-        z[lane] = pn * civ;
-        R += pn;
+        zx[lane] = fx_scale(pn, mul);
+        Rf += pn;
       }
       __syncwarp();
       k++;
@@ -191,7 +209,7 @@ __device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, 
         if (k >= fixed) break;
         continue;
       }
-      const float pf = abs_to_float(pn);  // terms are signed after a warm start
+      const float pf = fx_abs_float(pn, F);  // terms are signed after a warm start
       const float s = a.norm == PR_NORM_L1 ? group_sumf<32>(pf) : group_maxf<32>(pf);
       if (!keep_going32(s, thr, a.norm)) break;
       if (k >= a.max_iter) {
@@ -199,6 +217,7 @@ __device__ void warp_component(const SolveArgs& a, int c, double* z, float* zf, 
         break;
       }
     }
+    R = act ? from_fx(Rf, F) : 0.0;
   }
   if (act) {
     a.R[p] = R;
