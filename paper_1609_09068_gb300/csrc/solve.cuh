@@ -74,6 +74,24 @@ __device__ __forceinline__ bool keep_going32(float s, float thr, int norm) {
   return norm == PR_NORM_LINF ? (s >= thr) : (s > thr);
 }
 
+// The same test on integers, so that a warp reduces the norm with one
+// redux.sync instead of a chain of shuffles: each lane's |term| becomes
+// q = ceil(|term| * 2^20 / thr), capped at 2^21 (a lane at twice the
+// threshold keeps the series going on its own).  Rounding up makes the sum
+// of q an upper bound of the scaled FP32 norm, so stopping still implies
+// norm <= thr; it may add one sweep when the norm ends within 2^-10 of
+// thr.  At most 1,024 lanes of 2^21 sum below 2^32.
+constexpr float kNormQOne = 1048576.0f;  // 2^20: thr in q units
+constexpr float kNormQMax = 2097152.0f;  // 2^21
+__device__ __forceinline__ float norm_q_scale(float thr) { return thr > 0.0f ? kNormQOne / thr : 0.0f; }
+__device__ __forceinline__ unsigned norm_q(float pf, float scale) {
+  if (!(pf > 0.0f)) return 0u;
+  return scale > 0.0f ? __float2uint_ru(fminf(__fmul_ru(pf, scale), kNormQMax)) : (unsigned)kNormQMax;
+}
+__device__ __forceinline__ bool keep_going_q(unsigned s, int norm) {
+  return norm == PR_NORM_LINF ? (s >= (unsigned)kNormQOne) : (s > (unsigned)kNormQOne);
+}
+
 // |x| as a float, from the bit pattern of the double: the sign dropped, the
 // exponent rebiased from 1023 to 127 and the mantissa cut to 23 bits
 // (rounding toward zero, relative error below 2^-23); magnitudes under the

@@ -102,6 +102,20 @@ __device__ __forceinline__ float grp_norm(const Grp<T>& g, float part, float* re
   return is_max ? group_maxf<32>(t) : group_sumf<32>(t);
 }
 
+// the same over the integer norm (norm_q): one redux.sync a warp, one
+// barrier, one redux.sync over the warps' partials
+template <int T>
+__device__ __forceinline__ unsigned grp_norm_q(const Grp<T>& g, unsigned q, unsigned* red, int parity,
+                                               bool is_max) {
+  constexpr int kNW = T / 32;
+  const int lane = g.tid & 31, wib = g.tid >> 5;
+  q = is_max ? __reduce_max_sync(0xffffffffu, q) : __reduce_add_sync(0xffffffffu, q);
+  if (lane == 0) red[parity * kNW + wib] = q;
+  g.sync();
+  const unsigned t = lane < kNW ? red[parity * kNW + lane] : 0u;
+  return is_max ? __reduce_max_sync(0xffffffffu, t) : __reduce_add_sync(0xffffffffu, t);
+}
+
 // The series of SCC c, one row per thread (sz <= T).
 //
 // The in-edges are staged as one slice per warp (SELL-32, Sec. 4.3.2's
@@ -236,15 +250,16 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
     zA[i] = fx_scale(Rf, mul);
   }
   g.sync();
+  const float qscale = norm_q_scale(thr);
   for (;;) {
     const fx128 p = row(cur);  // the next term, exact
-    float part = 0.0f;
+    unsigned q = 0u;
     if (act) {
       Rf += p;
       nxt[i] = fx_scale(p, mul);
-      part = fx_abs_float(p, F);
+      q = norm_q(fx_abs_float(p, F), qscale);
     }
-    const float s2 = grp_norm(g, part, red, k & 1, !l1);  // also publishes nxt
+    const unsigned s2 = grp_norm_q(g, q, reinterpret_cast<unsigned*>(red), k & 1, !l1);  // also publishes nxt
     fx128* t = cur;
     cur = nxt;
     nxt = t;
@@ -253,7 +268,7 @@ __device__ void fx_series(const SolveArgs& a, const Grp<T>& g, int c, int off, i
       if (k >= fixed) break;
       continue;
     }
-    if (!keep_going32(s2, thr, a.norm)) break;
+    if (!keep_going_q(s2, a.norm)) break;
     if (k >= a.max_iter) {
       if (g.tid == 0) atomicOr(&a.ctl->flags[0], 1);
       break;

@@ -187,6 +187,7 @@ __device__ void warp_component(const SolveArgs& a, int c, unsigned char* zbuf, u
     const bool cold = !(a.yhat && warp_fx_warm(a, p, act, W, wsum / (double)sz, F, mul, ix, ib, ie, zx, &Rf));
     if (cold && act) zx[lane] = fx_scale(Rf, mul);
     if (!cold) k = 1;
+    const float qscale = norm_q_scale(thr);
     __syncwarp();
     for (;;) {
       // two carry chains of exact adds
@@ -209,9 +210,9 @@ __device__ void warp_component(const SolveArgs& a, int c, unsigned char* zbuf, u
         if (k >= fixed) break;
         continue;
       }
-      const float pf = fx_abs_float(pn, F);  // terms are signed after a warm start
-      const float s = a.norm == PR_NORM_L1 ? group_sumf<32>(pf) : group_maxf<32>(pf);
-      if (!keep_going32(s, thr, a.norm)) break;
+      const unsigned q = norm_q(fx_abs_float(pn, F), qscale);  // terms are signed after a warm start
+      const unsigned s = a.norm == PR_NORM_L1 ? __reduce_add_sync(0xffffffffu, q) : __reduce_max_sync(0xffffffffu, q);
+      if (!keep_going_q(s, a.norm)) break;
       if (k >= a.max_iter) {
         if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
         break;
