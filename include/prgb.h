@@ -90,22 +90,28 @@ typedef struct pr_mpnn_s pr_mpnn;
 #define PR_NORM_LINF 1 /* the paper's rule: iterate while max(P) >= tol */
 
 /* Arithmetic of the solve. */
-#define PR_PREC_FP64 0  /* FP64 throughout */
-#define PR_PREC_MIXED 1 /* pr_solve only, with PR_NORM_L1 and no replay: each
-                           SCC series runs in FP32 (values, z = P/outdeg and
-                           accumulation), then an FP64 residual
-                           r = W + cA^T(R/outdeg) - R of the component is
-                           formed; while ||r||_1 > tol*|C|/n the correction
-                           (I - cA^T)D = r is summed by the same FP32 series
-                           and R += D in FP64.  The inflow gather, CACs and
-                           1-vertex components stay FP64.  Every SCC ends
-                           with an FP64 residual within its budget, so the
-                           L1 residual of R is at most tol (plus FP64
-                           rounding of the gather) as in FP64 mode; R differs
-                           from the FP64 result by at most 2*tol/(1-c) in L1.
-                           PR_ENOCONV when six corrections do not meet the
-                           budget (tol below ~1e-13 ||R||_1) or max_iter
-                           sweeps are reached. */
+#define PR_PREC_FP64 0  /* FP64, except that the series of SCCs of at most
+                           1,024 vertices is summed exactly in 128-bit fixed
+                           point (each row's sum and R exact, each term
+                           rounded once to a quantum of about 2^-110
+                           ||W_C||_1), which is at least as accurate */
+#define PR_PREC_MIXED 1 /* pr_solve only, with PR_NORM_L1 and no replay: the
+                           series of each SCC above 1,024 vertices runs in
+                           FP32 (values, z = P/outdeg and accumulation), then
+                           an FP64 residual r = W + cA^T(R/outdeg) - R of the
+                           component is formed; while ||r||_1 > tol*|C|/n
+                           the correction (I - cA^T)D = r is summed by the
+                           same FP32 series and R += D in FP64.  Smaller SCCs
+                           run the exact fixed-point series as in
+                           PR_PREC_FP64; the inflow gather, CACs and 1-vertex
+                           components stay FP64.  Every SCC ends with a
+                           residual within its budget, so the L1 residual of
+                           R is at most tol (plus FP64 rounding of the
+                           gather) as in FP64 mode; R differs from the FP64
+                           result by at most 2*tol/(1-c) in L1.  PR_ENOCONV
+                           when six corrections do not meet the budget (tol
+                           below ~1e-13 ||R||_1) or max_iter sweeps are
+                           reached. */
 
 typedef struct pr_solve_opts {
     int32_t norm;                /* PR_NORM_L1 (default) or PR_NORM_LINF */

@@ -37,254 +37,6 @@ namespace prgb {
 // vertex, because FP64 division is expensive on this part.
 
 
-constexpr int kWarpBlock = 64;  // two components per block, spread over many SMs
-
-template <bool kMixed>
-__global__ void __launch_bounds__(kWarpBlock) solve_warp_k(SolveArgs a, int32_t cbeg, int32_t cend) {
-  __shared__ __align__(16) unsigned char zsh[kWarpBlock / 32][kWarpZBytes];
-  __shared__ uint8_t ish[kWarpBlock / 32][kWarpEdges];
-  const int wib = threadIdx.x >> 5;
-  const int c = cbeg + (int)blockIdx.x * (kWarpBlock / 32) + wib;
-  if (c >= cend) return;  // warp-uniform
-  warp_component<kMixed>(a, c, zsh[wib], ish[wib]);
-}
-
-// ---------------------------------------------------------------------------
-// one CTA of 256 threads per component of 33..kCtaCompMax vertices, one row
-// per thread.  The component's internal in-edges are staged in
-// shared memory as 16-bit local indices with local row offsets, next to R
-// and the double-buffered z, so the series runs from shared memory only.  A
-// component with more internal edges than the staging area reads its
-// indices from global memory instead.
-// ---------------------------------------------------------------------------
-constexpr int kCtaThreads = 256;
-constexpr int kCtaEdgeCap = 8192;
-constexpr int kCtaRows = kCtaCompMax / kCtaThreads;
-constexpr size_t kCtaSmem = (size_t)kCtaCompMax * (4 * sizeof(double) + sizeof(int)) + sizeof(int) +
-                            (size_t)kCtaEdgeCap * sizeof(uint16_t);
-constexpr size_t kCtaSmemMixed = kCtaSmem + (size_t)kCtaCompMax * sizeof(float);
-static_assert(kCtaRows == 1, "the mixed-precision CTA series keeps one row per thread");
-
-template <bool kMixed>
-__global__ void __launch_bounds__(kCtaThreads) solve_cta_k(SolveArgs a, int32_t cbeg) {
-  extern __shared__ double sm[];
-  double* Rs = sm;
-  double* z = sm + kCtaCompMax;
-  double* iv = sm + 2 * kCtaCompMax;
-  double* z1 = sm + 3 * kCtaCompMax;  // second z buffer of the FP64 series
-  int* ip = reinterpret_cast<int*>(sm + 4 * kCtaCompMax);  // [sz+1] local edge offsets
-  uint16_t* ix = reinterpret_cast<uint16_t*>(ip + kCtaCompMax + 1);
-  float* zf = reinterpret_cast<float*>(ix + kCtaEdgeCap);  // [kCtaCompMax], mixed precision only
-  __shared__ float red[kCtaThreads / 32];
-  __shared__ double red64[kCtaThreads / 32];
-  __shared__ float red2[2][kCtaThreads / 32];  // warp partials of the norm, by sweep parity
-  const int c = cbeg + (int)blockIdx.x;
-  const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
-  const int ib = a.int_ptr[off];
-  const int m = a.int_ptr[off + sz] - ib;
-  const bool staged = m <= kCtaEdgeCap;
-  const bool scc = a.c_type[c] == PR_TYPE_SCC;
-  if (scc && sz < a.lu_threshold) return;  // solved by solve_lu_k (block-uniform)
-  for (int i = threadIdx.x; i <= sz; i += blockDim.x) ip[i] = a.int_ptr[off + i] - ib;
-  if (staged)
-    for (int e = threadIdx.x; e < m; e += blockDim.x) ix[e] = (uint16_t)local_or_err(a, a.int_idx[ib + e] - off, sz);
-  // inflow-adjusted weights from the level's gather
-  for (int i = threadIdx.x; i < sz; i += blockDim.x) {
-    const int p = off + i;
-    const double inv = a.p_inv[p];
-    const double W = a.W[p];
-    iv[i] = inv;
-    Rs[i] = W;
-    z[i] = W * inv;
-  }
-  __syncthreads();
-  auto row_sum_of = [&](const double* zb, int i) -> double {
-    const int e0 = ip[i], e1 = ip[i + 1];
-    if (staged) {
-      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-      int e = e0;
-      for (; e + 3 < e1; e += 4) {
-        acc0 += zb[ix[e]];
-        acc1 += zb[ix[e + 1]];
-        acc2 += zb[ix[e + 2]];
-        acc3 += zb[ix[e + 3]];
-      }
-      for (; e < e1; e++) acc0 += zb[ix[e]];
-      return (acc0 + acc1) + (acc2 + acc3);
-    }
-    double acc = 0.0;
-    for (int e = e0; e < e1; e++) acc += zb[local_or_err(a, a.int_idx[ib + e] - off, sz)];
-    return acc;
-  };
-  auto row_sum = [&](int i) -> double { return row_sum_of(z, i); };
-  auto row_sumf = [&](const float* zb, int i) -> float {
-    const int e0 = ip[i], e1 = ip[i + 1];
-    if (staged) {
-      float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
-      int e = e0;
-      for (; e + 3 < e1; e += 4) {
-        acc0 += zb[ix[e]];
-        acc1 += zb[ix[e + 1]];
-        acc2 += zb[ix[e + 2]];
-        acc3 += zb[ix[e + 3]];
-      }
-      for (; e < e1; e++) acc0 += zb[ix[e]];
-      return (acc0 + acc1) + (acc2 + acc3);
-    }
-    float acc = 0.0f;
-    for (int e = e0; e < e1; e++) acc += zb[local_or_err(a, a.int_idx[ib + e] - off, sz)];
-    return acc;
-  };
-  int k = 0, k64 = 0;
-  if (!scc) {
-    // CAC: one pass, sub-level by sub-level (topological order)
-    const int sb = a.c_sub[c], se = a.c_sub[c + 1];
-    for (int s2 = sb; s2 < se; s2++) {
-      const int lo = a.sub_ptr[s2] - off, hi = a.sub_ptr[s2 + 1] - off;
-      for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const double Rv = Rs[i] + a.c * row_sum(i);
-        Rs[i] = Rv;
-        z[i] = Rv * iv[i];
-      }
-      __syncthreads();
-    }
-  } else if (kMixed) {
-    // FP32 series with FP64 residual refinement (see kMixKappa); row i of
-    // thread i
-    const int i = threadIdx.x;
-    const bool act = i < sz;
-    const double tau = a.tol * (double)sz / (double)a.n;
-    const float cf = (float)a.c;
-    const double W = act ? Rs[i] : 0.0, inv = act ? iv[i] : 0.0;
-    const float invf = (float)inv;
-    float F = act ? (float)W : 0.0f;
-    if (act) zf[i] = (float)(W * inv);
-    float thr = (float)fmax(tau, (double)kMixKappa * block_sum(W, red64));  // publishes zf
-    double R = 0.0;
-    bool skip = a.R0 != nullptr;  // warm start: straight to the guess's residual
-    if (skip) {
-      R = act ? a.R0[off + i] : 0.0;
-      F = 0.0f;
-    }
-    int rounds = 0;
-    // the FP32 z double-buffered (the second buffer in the FP64 one's
-    // space) and the norm from warp partials: one barrier a sweep
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float* fc = zf;
-    float* fn = reinterpret_cast<float*>(z1);
-    for (;;) {
-      for (; !skip;) {
-        const float pn = act ? cf * row_sumf(fc, i) : 0.0f;
-        if (act) {
-          fn[i] = pn * invf;
-          F += pn;
-        }
-        const float pf = group_sumf<32>(fabsf(pn));
-        if (lane == 0) red2[k & 1][wib] = pf;
-        __syncthreads();  // publishes fn and the partials
-        float s2 = 0.0f;
-#pragma unroll
-        for (int w = 0; w < kCtaThreads / 32; w++) s2 += red2[k & 1][w];
-        float* t = fc;
-        fc = fn;
-        fn = t;
-        k++;
-        if (s2 <= thr) break;
-        if (k >= a.max_iter) {
-          if (threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
-          rounds = -1;
-          break;
-        }
-      }
-      skip = false;
-      R += (double)F;
-      if (rounds < 0) break;
-      if (act) z[i] = R * inv;
-      __syncthreads();
-      const double r = act ? W + a.c * row_sum(i) - R : 0.0;
-      const double rho = block_sum(fabs(r), red64);  // also orders the z reads before later writes
-      k++;
-      k64++;
-      if (rho <= tau) break;
-      if (++rounds >= kMixRounds || k >= a.max_iter) {
-        if (threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
-        break;
-      }
-      F = (float)r;
-      if (act) fc[i] = (float)(r * inv);  // the buffer the next FP32 sweep reads
-      thr = fmaxf(0.5f * (float)tau, kMixKappa * (float)rho);
-      __syncthreads();
-    }
-    if (act) Rs[i] = R;
-  } else {
-    const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
-    const float thr = stop_thr32(tau);
-    const int fixed = a.replay ? a.replay[c] : -1;
-    // one row per thread; z holds c P / outdeg, so that the in-edge sum is
-    // the next term itself
-    const int i = threadIdx.x;
-    const bool act = i < sz;
-    const double civ = act ? a.c * iv[i] : 0.0;
-    if (a.R0) {
-      // warm start: R = R0 + r, the series continues from the residual
-      const double r0 = act ? a.R0[off + i] : 0.0;
-      if (act) z[i] = r0 * civ;
-      __syncthreads();
-      const double r = act ? Rs[i] + row_sum(i) - r0 : 0.0;
-      __syncthreads();
-      if (act) {
-        Rs[i] = r0 + r;
-        z[i] = r * civ;
-      }
-      k = 1;
-    } else if (act) {
-      z[i] = Rs[i] * civ;  // Rs holds W
-    }
-    __syncthreads();
-    // z double-buffered and the norm from warp partials: one barrier a sweep
-    const bool is_max = a.norm != PR_NORM_L1;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    double* zc = z;
-    double* zn = z1;
-    for (;;) {
-      const double pn = act ? row_sum_of(zc, i) : 0.0;
-      if (act) {
-        Rs[i] += pn;
-        zn[i] = pn * civ;
-      }
-      float pf = abs_to_float(pn);
-      pf = is_max ? group_maxf<32>(pf) : group_sumf<32>(pf);
-      if (lane == 0) red2[k & 1][wib] = pf;
-      __syncthreads();  // publishes zn and the partials
-      float s2 = 0.0f;
-#pragma unroll
-      for (int w = 0; w < kCtaThreads / 32; w++) s2 = is_max ? fmaxf(s2, red2[k & 1][w]) : s2 + red2[k & 1][w];
-      double* t = zc;
-      zc = zn;
-      zn = t;
-      k++;
-      if (fixed >= 0) {
-        if (k >= fixed) break;
-        continue;
-      }
-      if (!keep_going32(s2, thr, a.norm)) break;
-      if (k >= a.max_iter) {
-        if (threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
-        break;
-      }
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < sz; i += blockDim.x) {
-    a.R[off + i] = Rs[i];
-    a.zr[off + i] = Rs[i] * iv[i];
-  }
-  if (threadIdx.x == 0) {
-    a.iters[c] = k;
-    if (kMixed && scc) a.iters64[c] = k64;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // one cluster of kClu CTAs (on kClu SMs) per component of
 // kCtaCompMax+1..kCluCompMax vertices.  Rank r owns the component-local rows
@@ -1087,8 +839,6 @@ pr_status set_solve_attrs(const pr_partition_s* P, bool mixed) {
   if (!cta_attr) {
     PRGB_TRY(set_fx_attrs());
     PRGB_CUDA(cudaFuncSetAttribute(solve_lu_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmem));
-    PRGB_CUDA(cudaFuncSetAttribute(solve_cta_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kCtaSmemMixed));
     cta_attr = true;
   }
   // the largest cluster-class component of any level, with and without push
@@ -1170,7 +920,7 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
   double* part = b.part;
   HeavyScratch hs = b.hs;
   size_t li_large = 0, ti = 0;
-  if (!mixed) PRGB_CUDA(cudaMemsetAsync(b.lvl_ctr, 0, (4 * P->levels.size() + 4) * sizeof(int32_t), s));
+  PRGB_CUDA(cudaMemsetAsync(b.lvl_ctr, 0, (4 * P->levels.size() + 4) * sizeof(int32_t), s));
   if (b.civ && P->g.n > 0) {
     // c / outdeg for the grid-wide series of this solve's c
     scale_k<<<grid_cap((P->g.n + kBlock - 1) / kBlock), kBlock, 0, s>>>(P->g.n, a.c, P->p_inv, b.civ);
@@ -1201,8 +951,7 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
     // kernel does not take (all of them in mixed precision), from the
     // weights W the gather has just formed; the level kernel forms its own
     if (yhat && a.R0) {
-      const int32_t c1 = mixed ? r.single : r.big;
-      PRGB_TRY(mpnn_level_r0(P, r.cbeg, c1, a.W, yhat, const_cast<double*>(a.R0), s, nl));
+      PRGB_TRY(mpnn_level_r0(P, r.cbeg, r.big, a.W, yhat, const_cast<double*>(a.R0), s, nl));
     }
     while (li_large < P->large.size() && P->large[li_large].level_idx == (int)li) {
       LargeComp L = P->large[li_large++];
@@ -1237,9 +986,9 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
     }
     PRGB_CUDA(cudaEventRecord(side.fork, s));
     bool joined[kSideStreams] = {false, false, false, false};
-    // FP64 solves give the components of at most kFxMax vertices of the
-    // cluster class, and the whole CTA class, to the fixed-point kernels
-    const int32_t clu_end = mixed ? r.cta : r.big;
+    // the cluster class keeps the components above kFxMax vertices; the
+    // smaller ones go to the level kernel below
+    const int32_t clu_end = r.big;
     if (clu_end > r.clu) {
       PRGB_CUDA(cudaStreamWaitEvent(side.st[0], side.fork, 0));
       joined[0] = true;
@@ -1251,13 +1000,6 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       else if (mixed) solve_clu_k<true, false><<<nb, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
       else if (push) solve_clu_k<false, true><<<nb, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
       else solve_clu_k<false, false><<<nb, kCluThreads, smem, side.st[0]>>>(a, r.clu, chunk);
-      PRGB_LAUNCH();
-      ++*nl;
-    }
-    if (mixed && r.warp > r.cta) {
-      PRGB_CUDA(cudaStreamWaitEvent(side.st[1], side.fork, 0));
-      joined[1] = true;
-      solve_cta_k<true><<<r.warp - r.cta, kCtaThreads, kCtaSmemMixed, side.st[1]>>>(a, r.cta);
       PRGB_LAUNCH();
       ++*nl;
     }
@@ -1278,16 +1020,7 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
         ++*nl;
       }
     }
-    if (mixed && r.single > r.warp) {
-      const int nw = r.single - r.warp;
-      PRGB_CUDA(cudaStreamWaitEvent(side.st[2], side.fork, 0));
-      joined[2] = true;
-      const unsigned nb = (nw + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
-      solve_warp_k<true><<<nb, kWarpBlock, 0, side.st[2]>>>(a, r.warp, r.single);
-      PRGB_LAUNCH();
-      ++*nl;
-    }
-    if (!mixed && r.single > r.big) {
+    if (r.single > r.big) {
       // every component of at most kFxMax vertices: one persistent launch
       PRGB_TRY(launch_level(a, r, b.lvl_ctr + 4 * li, s));
       ++*nl;
@@ -1408,7 +1141,7 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
                                 mixed ? pl->iters64 : nullptr, pl->ctl);
   if (warm) {
     a.R0 = pl->R0;
-    a.yhat = mixed ? nullptr : pl->yhat;
+    a.yhat = pl->yhat;
   }
   a.lu_threshold = lu;
   const long long before = launch_count();

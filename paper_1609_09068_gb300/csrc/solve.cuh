@@ -195,10 +195,10 @@ struct SolvePlan {
   ~SolvePlan();
 };
 
-// FP64 solves: every component of a level with at most kFxMax vertices
-// (SCCs by the fixed-point series, CACs and the warp class as elsewhere) in
-// one persistent launch of solve_fx.cu (solve_level_k); larger ones keep the
-// cluster and grid-wide kernels.
+// Every component of a level with at most kFxMax vertices (SCCs by the
+// exact fixed-point series, CACs by one FP64 pass) in one persistent launch
+// of solve_fx.cu (solve_level_k), in FP64 and mixed precision alike; larger
+// ones keep the cluster and grid-wide kernels.
 constexpr int kFxMax = 1024;  // above it the 8-CTA clusters are faster (measured)
 pr_status set_fx_attrs();
 // the level's components [big, single) in one launch on s; ctr: three claim

@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kLevelThreads, 1) solve_level_k(SolveArgs a, L
     i = __shfl_sync(0xffffffffu, i, 0);
     const int c = w.small0 + i;
     if (c >= w.small1) break;
-    warp_component<false>(a, c, wb, ix);
+    warp_component(a, c, wb, ix);
     __syncwarp();
   }
 }

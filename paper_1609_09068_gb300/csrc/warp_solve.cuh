@@ -1,6 +1,6 @@
 // warp_solve.cuh -- one warp per component of 2..32 vertices (Sec. 4.3:
 // CACs in one topological pass, SCCs by the power series of Sec. 4.3.2),
-// shared by the warp-class kernel and the persistent level kernel.
+// the warp items of the persistent level kernel.
 #pragma once
 
 #include "common.cuh"
@@ -10,8 +10,10 @@
 
 namespace prgb {
 
-// Mixed precision (the SCC series only; the gather, CACs and 1-vertex
-// components stay FP64).  Per SCC C with budget tau = tol*|C|/n:
+// Mixed precision (the SCC series of the cluster and grid-wide classes; the
+// gather, CACs and 1-vertex components stay FP64, and the components of at
+// most 1,024 vertices run the exact fixed-point series of the level kernel
+// in either mode).  Per SCC C with budget tau = tol*|C|/n:
 //   1. the series P_0 = W, P_{k+1} = c A^T P_k, F = sum P_k in FP32 values
 //      and FP32 accumulation, until the FP32 norm of P falls to
 //      max(tau, kMixKappa * ||W||_1): below that FP32 rounding of F
@@ -35,77 +37,9 @@ constexpr int kMixRounds = 6;
 // as 8-bit local indices, so each series iteration reads shared memory only.
 // ---------------------------------------------------------------------------
 constexpr int kWarpEdges = kWarpCompMax * (kWarpCompMax - 1);
-// the warp's z space: 32 fixed-point entries (FP64 mode), or 32 doubles and
-// 32 floats (mixed precision); 16-byte aligned
+// the warp's z space: 32 fixed-point entries (an SCC's series) or 32 doubles
+// (a CAC's pass); 16-byte aligned
 constexpr int kWarpZBytes = 32 * 16;
-
-// FP32 series with FP64 residual refinement (see kMixKappa) for one warp's
-// component; W is this lane's weight.  Returns the result R of this lane and
-// counts the sweeps in *k (all) and *k64 (FP64 residual sweeps).
-static __device__ double warp_series_mixed(const SolveArgs& a, bool act, double W, double inv, const uint8_t* ix, int ib,
-                                    int ie, double* z, float* zf, double tau, int* k, int* k64, bool warm,
-                                    double R0) {
-  const int lane = threadIdx.x & 31;
-  const float cf = (float)a.c;
-  const float invf = (float)inv;
-  float F = act ? (float)W : 0.0f;
-  if (act) zf[lane] = (float)(W * inv);
-  const double wsum = group_sum<32>(act ? W : 0.0);
-  float thr = (float)fmax(tau, (double)kMixKappa * wsum);
-  double R = 0.0;
-  if (warm) {  // start from the guess: straight to its FP64 residual
-    R = act ? R0 : 0.0;
-    F = 0.0f;
-  }
-  bool skip = warm;
-  int rounds = 0;
-  __syncwarp();
-  for (;;) {
-    for (; !skip;) {
-      float acc0 = 0.0f, acc1 = 0.0f;
-      int e = ib;
-      for (; e + 1 < ie; e += 2) {
-        acc0 += zf[ix[e]];
-        acc1 += zf[ix[e + 1]];
-      }
-      if (e < ie) acc0 += zf[ix[e]];
-      const float pn = cf * (acc0 + acc1);
-      __syncwarp();
-      if (act) {
-        zf[lane] = pn * invf;
-        F += pn;
-      }
-      __syncwarp();
-      ++*k;
-      if (group_sumf<32>(fabsf(pn)) <= thr) break;
-      if (*k >= a.max_iter) {
-        if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
-        return R + (double)F;
-      }
-    }
-    skip = false;
-    R += (double)F;
-    if (act) z[lane] = R * inv;
-    __syncwarp();
-    double acc = 0.0;
-    for (int e = ib; e < ie; e++) acc += z[ix[e]];
-    const double r = act ? W + a.c * acc - R : 0.0;
-    ++*k;
-    ++*k64;
-    const double rho = group_sum<32>(fabs(r));
-    if (rho <= tau) break;
-    if (++rounds >= kMixRounds || *k >= a.max_iter) {
-      if (lane == 0) atomicOr(&a.ctl->flags[0], 1);
-      break;
-    }
-    F = (float)r;
-    __syncwarp();  // every lane has read z before the next residual rewrites it
-    if (act) zf[lane] = (float)(r * inv);
-    thr = fmaxf(0.5f * (float)tau, kMixKappa * (float)rho);
-    __syncwarp();
-  }
-  return R;
-}
 
 // Warm start of a warp's fixed-point series from the network's guess
 // R0 = W + exp(clamp(yhat)) mean_C(W): R = R0 + r, the series continuing from
@@ -138,8 +72,7 @@ static __device__ __noinline__ bool warp_fx_warm(const SolveArgs& a, int p, bool
 // components): a row's in-edge sum and R are exact integer sums, z' = P
 // c/outdeg the exact product rounded once, and a sweep has no floating-point
 // arithmetic.  CACs take one FP64 pass over their sub-levels.
-template <bool kMixed>
-__device__ void warp_component(const SolveArgs& a, int c, unsigned char* zbuf, uint8_t* ix) {
+static __device__ void warp_component(const SolveArgs& a, int c, unsigned char* zbuf, uint8_t* ix) {
   const int lane = threadIdx.x & 31;
   const int off = a.c_off[c], sz = a.c_off[c + 1] - off;
   if (sz < a.lu_threshold && a.c_type[c] == PR_TYPE_SCC) return;  // solved by solve_lu_k (warp-uniform)
@@ -155,7 +88,7 @@ __device__ void warp_component(const SolveArgs& a, int c, unsigned char* zbuf, u
   const int ib = act ? a.int_ptr[p] - ib0 : 0, ie = act ? min(a.int_ptr[p + 1] - ib0, kWarpEdges) : 0;
   __syncwarp();
   double R = W;
-  int k = 0, k64 = 0;
+  int k = 0;
   if (a.c_type[c] == PR_TYPE_CAC) {
     const int sb = a.c_sub[c], se = a.c_sub[c + 1];
     for (int s = sb; s < se; s++) {
@@ -168,11 +101,6 @@ __device__ void warp_component(const SolveArgs& a, int c, unsigned char* zbuf, u
       }
       __syncwarp();
     }
-  } else if constexpr (kMixed) {
-    float* zf = reinterpret_cast<float*>(zbuf + 32 * sizeof(double));
-    const double tau = a.tol * (double)sz / (double)a.n;
-    const bool warm = a.R0 != nullptr;
-    R = warp_series_mixed(a, act, W, inv, ix, ib, ie, z, zf, tau, &k, &k64, warm, warm && act ? a.R0[p] : 0.0);
   } else {
     const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
     const float thr = stop_thr32(tau);
@@ -224,10 +152,7 @@ __device__ void warp_component(const SolveArgs& a, int c, unsigned char* zbuf, u
     a.R[p] = R;
     a.zr[p] = R * inv;
   }
-  if (lane == 0) {
-    a.iters[c] = k;
-    if (kMixed) a.iters64[c] = k64;
-  }
+  if (lane == 0) a.iters[c] = k;
 }
 
 }  // namespace prgb

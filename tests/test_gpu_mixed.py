@@ -1,5 +1,6 @@
-"""Mixed precision (FP32 SCC series with FP64 residual refinement) against the
-FP64 oracle.
+"""Mixed precision (FP32 SCC series with FP64 residual refinement for the
+SCCs above 1,024 vertices; the smaller ones run the exact fixed-point series
+as in FP64 mode) against the FP64 oracle.
 
 The FP32 iterates differ from the FP64 ones, so there is no element-wise
 1e-12 comparison.  What pins the result instead (the solution of
@@ -56,9 +57,16 @@ def check_mixed(prgb, g, tol=1e-10, max_rel_bound=1e-6):
     assert np.abs(R - Ro).sum() <= 2 * tol / (1 - C) + 2 * floor64(g.u, R) / (1 - C)
     rel = float(np.max(np.abs(R - Ro) / np.maximum(np.abs(Ro), 1e-300)))
     assert rel <= max_rel_bound
-    if P.n_scc:
+    sizes = np.bincount(q.comp, minlength=q.n_comp)
+    ctype = np.zeros(q.n_comp, np.int64)
+    ctype[q.comp] = q.type
+    if np.any((ctype == 1) & (sizes > 1024)):
+        # FP32 series refined by FP64 residual sweeps
         assert st["fp64_sweeps_max"] >= 1
         assert 0 < st["fp64_edge_visits"] < st["edge_visits"]
+    else:
+        # every SCC in the exact fixed-point series: no FP64 sweep
+        assert st["fp64_sweeps_max"] == 0 and st["fp64_edge_visits"] == 0
     return R, st, rel
 
 
@@ -91,9 +99,11 @@ def test_random_with_loops_mixed_tight_tol(prgb):
 
 def test_loose_tol_needs_one_residual(prgb):
     """With a budget far above the FP32 rounding of the sum (tol*|C|/n
-    against ~1e-5 |R_C|), the first FP32 pass meets it and one FP64 residual
-    confirms it."""
-    _, st, _ = check_mixed(prgb, gg.small_planted(seed=5), tol=1e-3, max_rel_bound=0.05)
+    against ~1e-5 |R_C|), the first FP32 pass of each cluster-class SCC meets
+    it and one FP64 residual confirms it."""
+    g = gg.small_planted(seed=33, n=40_000, n_scc=20, scc_vertices=30_000, n_dangling=4_000, layers=6,
+                         target_edges=200_000)
+    _, st, _ = check_mixed(prgb, g, tol=1e-3, max_rel_bound=0.05)
     assert st["fp64_sweeps_max"] == 1
 
 
