@@ -128,21 +128,30 @@ def job_value(edges_per_rank, world, ms):
 
 
 def measured_l2_gbs(reps=40):
-    """L2 read bandwidth measured live: a 64 MiB float64 vector, resident in
-    L2 after a warm-up, summed reps times by the device reduction, bytes over
-    CUDA-event time.  The denominator of the roofline when the dominant
-    kernel's working set stays in L2 (no device constant gives it)."""
+    """L2 bandwidth measured live on 64 MiB resident in L2 after a warm-up,
+    bytes over CUDA-event time, the larger of: an FP32 sum of a 64 MiB
+    vector (reads; FP32 adds run at full rate, so the loads bound it -- an
+    FP64 sum would be bound by GB300's slow FP64 pipe instead) and a copy
+    between two 32 MiB buffers (read + write bytes).  The denominator of the
+    roofline when the dominant kernel's working set stays in L2 (no device
+    constant gives it)."""
     import torch
-    x = torch.ones(8 << 20, dtype=torch.float64, device="cuda")
-    for _ in range(5):
-        x.sum()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(reps):
-        x.sum()
-    b.record()
-    torch.cuda.synchronize()
-    return x.numel() * 8 * reps / (a.elapsed_time(b) * 1e-3) / 1e9
+    x = torch.ones(16 << 20, dtype=torch.float32, device="cuda")
+    src = torch.ones(4 << 20, dtype=torch.float64, device="cuda")
+    dst = torch.empty_like(src)
+
+    def rate(fn, nbytes):
+        for _ in range(5):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return nbytes * reps / (a.elapsed_time(b) * 1e-3) / 1e9
+
+    return max(rate(x.sum, x.numel() * 4), rate(lambda: dst.copy_(src), 2 * src.numel() * 8))
 
 
 def measured_peaks():
@@ -432,6 +441,17 @@ def make_steps(prgb, rowptr, col, u):
     return cw_step, global_step
 
 
+def partition_phases(prgb, rowptr, col, flush):
+    """One extra partition (outside the timed regions, L2 flushed before it)
+    with PR_PARTITION_TIMING: its phase times and wave counts."""
+    try:
+        flush.fill_(7)
+        G = prgb.graph(rowptr, col)
+        return prgb.partition(G, timing=True).timing()
+    except Exception as e:  # a report field only: never lose the bench line
+        return {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
+
+
 def elapsed(recs, nphase):
     return np.array([[r[0][j].elapsed_time(r[0][j + 1]) for j in range(nphase)] for r in recs])
 
@@ -486,6 +506,7 @@ def config_block(prgb, name, args, flush, local):
     comp_d, type_d, _ = P.query()
     g_iters = grecs[-1][3]
     sweeps = sweep_stats(comp_d, type_d, rowptr, col, st["comp_iters"], g_iters)
+    part_phases = partition_phases(prgb, rowptr, col, flush)
     R64 = prgb.solve(P, C, u, TOL)
     prgb.solve(P, C, u, TOL, timing=True, precision=prgb.PREC_MIXED)  # builds its graph, untimed
     mts = []
@@ -517,6 +538,7 @@ def config_block(prgb, name, args, flush, local):
         "value": E / (t_step * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": t_step,
         "breakdown_ms": {"graph_prepare": float(ph[:, 0].mean()), "partition": float(ph[:, 1].mean()),
                          "solve": t_solve, "residual_check": float(ph[:, 3].mean())},
+        "partition_phases": part_phases,
         "global_power": {"ms_per_step": t_global, "solve_ms": t_global_solve, "iters": g_iters,
                          "value": E / (t_global * 1e-3) / 1e9},
         "speedup_vs_global": {"step": t_global / t_step, "solve_only": t_global_solve / t_solve},
@@ -656,6 +678,8 @@ def run_ours(args):
     gk_ms = float(np.mean([r[1]["kernel_ms"] for r in grecs]))
     gk_bytes = float(np.mean([r[1]["kernel_bytes"] for r in grecs]))
 
+    part_phases = partition_phases(prgb, rowptr, col, flush)
+
     # sweeps per SCC against the global series' (outside the timed regions)
     try:
         comp_d, type_d, _ = P.query()
@@ -733,7 +757,7 @@ def run_ours(args):
     roofline = {"bound": "l2" if in_l2 else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_BYTES.get(args.workload),
                 "kernel": "solve_large_scc_k (grid-wide SCC power series)",
-                "peak_kind": ("L2 read bandwidth measured live (64 MiB resident vector, device reduction)"
+                "peak_kind": ("L2 bandwidth measured live (64 MiB resident: FP32 sum or 32 MiB copy, the larger)"
                               if in_l2 else f"{peak_kind} copy bandwidth"),
                 "hbm_peak": hbm, "hbm_frac": achieved / hbm, "hbm_peak_kind": f"{peak_kind} copy bandwidth",
                 "kernel_ms_per_step": k_ms, "algorithmic_bytes_per_step": k_bytes,
@@ -784,6 +808,7 @@ def run_ours(args):
         "cpu_parallel": cpu_par,
         "breakdown_ms": {"graph_prepare": float(ph[0]), "partition": float(ph[1]),
                          "solve": float(ph[2]), "residual_check": float(ph[3])},
+        "partition_phases": part_phases,
         "solve": {"iters_max": max(s["iters_max"] for s in stats), "levels": P.n_levels,
                   "components": P.n_comp, "scc_components": P.n_scc,
                   "edge_visits": stats[-1]["edge_visits"],

@@ -205,21 +205,52 @@ pr_status pr_graph_create_ex(const pr_csr *csr, uint32_t flags, void *stream, pr
  * accepted. */
 void pr_graph_destroy(pr_graph *g);
 
+/* Flags of pr_partition_create. */
+#define PR_PARTITION_TIMING 1u /* record CUDA events between the phases, for
+                                  pr_partition_timing_get */
+
+/* Phase times of a partition built with PR_PARTITION_TIMING: device time
+ * between CUDA events recorded on its stream (host gaps between launches
+ * included), and what the frontier-wave kernels ran. */
+typedef struct pr_partition_timing {
+    float trim_ms;    /* peeling of vertices with no in- or out-edge (Sec. 3
+                         remark on 1-vertex SCCs) */
+    float giant_ms;   /* forward-backward search for the largest SCC */
+    float colour_ms;  /* colouring rounds for the other SCCs (Def. 3.1) */
+    float levels_ms;  /* levels and CAC merges (Def. 3.3, Theorem 3.1) */
+    float layout_ms;  /* canonical ids and the solve's layout */
+    float total_ms;   /* the whole call up to its final synchronisation */
+    int32_t colour_rounds;
+    /* waves per kernel, [k][0] run by the whole grid (one grid barrier each)
+       and [k][1] by one block alone (small frontiers); k = 0 trim,
+       1 colour propagation, 2 forward-backward reachability, 3 backward
+       search from the colour roots, 4 Kahn level order */
+    int32_t waves[5][2];
+} pr_partition_timing;
+
 /*
  * pr_partition_create -- component finding and intermediate step
  * (Sec. 4.1-4.2).
  *   g      : a prepared graph; it must outlive the partition.
- *   flags  : reserved, pass 0.
+ *   flags  : 0 or PR_PARTITION_TIMING.
  *   stream : CUDA stream.
  *   out    : receives a new partition handle on PR_OK (NULL otherwise).
  * The partition is the unique SCC/CAC partition of Theorem 3.1 with
  * 0-based levels (Def. 3.3).  Component ids are canonical: sorted by level
  * descending, size descending, smallest vertex id ascending.
- * Errors: PR_EINVAL for a NULL graph or output, or flags != 0; PR_ENOMEM,
- * PR_ECUDA, PR_ETIMEOUT, PR_EINTERNAL.  Synchronises the stream (component
- * counts are read back).
+ * Errors: PR_EINVAL for a NULL graph or output, or an unknown flag;
+ * PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT, PR_EINTERNAL.  Synchronises the stream
+ * (component counts are read back).
  */
 pr_status pr_partition_create(const pr_graph *g, uint32_t flags, void *stream, pr_partition **out);
+
+/*
+ * pr_partition_timing_get -- the phase times and wave counts of a partition
+ * created with PR_PARTITION_TIMING, copied to *out (host).
+ * Errors: PR_EINVAL for NULL arguments or a partition created without the
+ * flag.
+ */
+pr_status pr_partition_timing_get(const pr_partition *part, pr_partition_timing *out);
 
 /*
  * pr_partition_query -- copy the partition out, one entry per vertex in the

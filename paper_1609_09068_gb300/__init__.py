@@ -24,6 +24,7 @@ __all__ = [
     "PrError", "Graph", "Partition", "graph", "partition", "solve", "global_power",
     "residual_l1", "load_library", "library_path", "launch_count", "TYPE_CAC", "TYPE_SCC",
     "NORM_L1", "NORM_LINF", "PREC_FP64", "PREC_MIXED", "Mpnn", "set_wait_limit", "CANONICALIZE",
+    "PARTITION_TIMING",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -70,6 +71,12 @@ class _Stats(C.Structure):
                 ("fp64_sweeps_max", C.c_int32), ("fp64_edge_visits", C.c_int64), ("level_ms", C.c_void_p)]
 
 
+class _PartTiming(C.Structure):
+    _fields_ = [("trim_ms", C.c_float), ("giant_ms", C.c_float), ("colour_ms", C.c_float),
+                ("levels_ms", C.c_float), ("layout_ms", C.c_float), ("total_ms", C.c_float),
+                ("colour_rounds", C.c_int32), ("waves", (C.c_int32 * 2) * 5)]
+
+
 _lib = None
 
 # name -> (restype, argtypes), mirroring include/prgb.h
@@ -84,6 +91,7 @@ _SIGS = {
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pr_partition_destroy": (None, [C.c_void_p]),
+    "pr_partition_timing_get": (C.c_int, [C.c_void_p, C.POINTER(_PartTiming)]),
     "pr_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.POINTER(_Opts),
                            C.c_void_p, C.POINTER(_Stats), C.c_void_p]),
     "pr_global_power": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.POINTER(_Opts),
@@ -189,6 +197,7 @@ def _dev_f64(x):
 
 
 CANONICALIZE = 1
+PARTITION_TIMING = 1
 
 
 class Graph:
@@ -233,11 +242,12 @@ class Graph:
 class Partition:
     """SCC/CAC partition with levels and the solver layout (``pr_partition``)."""
 
-    def __init__(self, g: Graph):
+    def __init__(self, g: Graph, timing=False):
         lib = load_library()
         self.graph = g  # the partition refers to the graph's buffers
         self._h = C.c_void_p()
-        _check(lib.pr_partition_create(g.handle, 0, _stream(), C.byref(self._h)), "pr_partition_create")
+        _check(lib.pr_partition_create(g.handle, PARTITION_TIMING if timing else 0, _stream(),
+                                       C.byref(self._h)), "pr_partition_create")
         n, m, nc, nl, ns, nsv = (C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32(),
                                  C.c_int32())
         _check(lib.pr_partition_info(self._h, C.byref(n), C.byref(m), C.byref(nc), C.byref(nl),
@@ -262,6 +272,17 @@ class Partition:
                                                  C.byref(nc), C.byref(nl), _stream()),
                "pr_partition_query")
         return comp, typ, lev
+
+    def timing(self):
+        """Phase times (ms) and wave counts of a partition built with
+        ``timing=True`` (pr_partition_timing_get)."""
+        t = _PartTiming()
+        _check(load_library().pr_partition_timing_get(self._h, C.byref(t)), "pr_partition_timing_get")
+        kinds = ("trim", "propagate", "reach", "root_bfs", "kahn")
+        return {"trim_ms": t.trim_ms, "giant_ms": t.giant_ms, "colour_ms": t.colour_ms,
+                "levels_ms": t.levels_ms, "layout_ms": t.layout_ms, "total_ms": t.total_ms,
+                "colour_rounds": t.colour_rounds,
+                "waves": {k: {"grid": t.waves[i][0], "block": t.waves[i][1]} for i, k in enumerate(kinds)}}
 
     def tune(self, c, u, tol):
         """Autotune the solve's launch shapes on this partition (see
@@ -295,14 +316,16 @@ def graph(rowptr, col, on_host=False, canonicalize=False):
     return Graph(rowptr, col, on_host=on_host, canonicalize=canonicalize)
 
 
-def partition(g, col=None, on_host=False):
+def partition(g, col=None, on_host=False, timing=False):
     """``partition(graph)``, or ``partition(rowptr, col)`` for a CSR (the
-    graph is prepared on the way and kept alive by the partition)."""
+    graph is prepared on the way and kept alive by the partition).
+    ``timing=True`` records the phase times (PR_PARTITION_TIMING), read by
+    ``Partition.timing()``."""
     if col is not None:
         g = Graph(g, col, on_host=on_host)
     elif not isinstance(g, Graph):
         raise TypeError("partition() takes a Graph, or rowptr and col")
-    return Partition(g)
+    return Partition(g, timing=timing)
 
 
 def _opts(norm, max_iter, io_on_host, replay, precision=PREC_FP64, warm=None, lu_threshold=0):

@@ -29,6 +29,43 @@ static void tune_pool() {
   done[dev] = true;
 }
 
+// CUDA events between the phases of a partition (PR_PARTITION_TIMING); a
+// no-op when off
+struct PhaseEvents {
+  bool on;
+  cudaEvent_t e[7] = {};
+  explicit PhaseEvents(bool want) : on(want) {}
+  ~PhaseEvents() {
+    for (cudaEvent_t x : e)
+      if (x) cudaEventDestroy(x);
+  }
+  pr_status start(cudaStream_t s) {
+    if (!on) return PR_OK;
+    for (cudaEvent_t& x : e) {
+      PRGB_CUDA(cudaEventCreate(&x));
+      PRGB_CUDA(cudaEventRecord(x, s));
+    }
+    return PR_OK;
+  }
+  pr_status mark(int i, cudaStream_t s) {
+    if (on) PRGB_CUDA(cudaEventRecord(e[i], s));
+    return PR_OK;
+  }
+  // after the stream has synchronised: trim, giant, colouring, levels,
+  // layout, total
+  pr_status read(float* ms) {
+    PRGB_CUDA(cudaEventSynchronize(e[6]));
+    for (int i = 0; i < 5; i++) PRGB_CUDA(cudaEventElapsedTime(&ms[i], e[i], e[i + 1]));
+    PRGB_CUDA(cudaEventElapsedTime(&ms[5], e[0], e[6]));
+    return PR_OK;
+  }
+};
+
+static pr_status copy_waves(int32_t (*dst)[2], const Ctl* ctl) {
+  PRGB_CUDA(cudaMemcpy(dst, ctl->waves, 5 * 2 * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return PR_OK;
+}
+
 static pr_status finish_sync(cudaStream_t s, Ctl* ctl, int* flags_out) {
   int h[2] = {0, 0};
   PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, 4, cudaMemcpyDeviceToHost, s));
@@ -125,7 +162,7 @@ void pr_graph_destroy(pr_graph* g) {
 static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, void* stream, pr_partition** out) {
   if (!out) return PR_EINVAL;
   *out = nullptr;
-  if (!g || flags != 0) return PR_EINVAL;
+  if (!g || (flags & ~PR_PARTITION_TIMING) != 0) return PR_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   tune_pool();
   pr_partition_s* P = new (std::nothrow) pr_partition_s;
@@ -152,19 +189,33 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
     if (st == PR_OK) st = tmp.alloc(&crep, (size_t)n);
     if (st == PR_OK) st = tmp.alloc(&wave, (size_t)n);
     if (st == PR_OK) st = init_ctl(ctl, s);
+    // phase events: 0 start, 1 trim, 2 giant, 3 colouring, 4 levels,
+    // 5 layout, 6 end; all recorded at the start, so a phase that does not
+    // run reads 0 ms
+    PhaseEvents ev(flags & PR_PARTITION_TIMING);
+    if (st == PR_OK) st = ev.start(s);
     if (st == PR_OK) {
       NvtxRange r("prgb scc");
-      st = scc_detect(P->g, rep, tmp, ctl);
+      st = scc_detect(P->g, rep, tmp, ctl, ev.on ? ev.e + 1 : nullptr, &P->colour_rounds);
     }
+    if (st == PR_OK) st = ev.mark(3, s);
     if (st == PR_OK) {
       NvtxRange r("prgb levels");
       st = levels_and_merge(P->g, rep, crep, P->level, P->type, wave, &max_wave, tmp, ctl);
     }
+    if (st == PR_OK) st = ev.mark(4, s);
     if (st == PR_OK) {
       NvtxRange r("prgb layout");
       st = build_layout(P, crep, wave, max_wave, tmp, ctl);
     }
+    if (st == PR_OK) st = ev.mark(5, s);
     if (st == PR_OK) st = finish_sync(s, ctl, nullptr);
+    if (st == PR_OK) st = ev.mark(6, s);
+    if (st == PR_OK && ev.on) {
+      P->timed = true;
+      st = ev.read(P->phase_ms);
+      if (st == PR_OK) st = copy_waves(P->waves, ctl);
+    }
   }
   if (st == PR_OK) {
     // the class boundary and grid shape an earlier tuning chose
@@ -185,6 +236,20 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
 pr_status pr_partition_create(const pr_graph* g, uint32_t flags, void* stream, pr_partition** out) {
   prgb::NvtxRange nvtx("prgb partition");
   return prgb::note_status(pr_partition_create_body(g, flags, stream, out));
+}
+
+pr_status pr_partition_timing_get(const pr_partition* part, pr_partition_timing* out) {
+  if (!part || !out || !part->timed) return PR_EINVAL;
+  out->trim_ms = part->phase_ms[0];
+  out->giant_ms = part->phase_ms[1];
+  out->colour_ms = part->phase_ms[2];
+  out->levels_ms = part->phase_ms[3];
+  out->layout_ms = part->phase_ms[4];
+  out->total_ms = part->phase_ms[5];
+  out->colour_rounds = part->colour_rounds;
+  for (int k = 0; k < 5; k++)
+    for (int j = 0; j < 2; j++) out->waves[k][j] = part->waves[k][j];
+  return PR_OK;
 }
 
 static pr_status pr_partition_query_body(const pr_partition* part, int32_t* comp_id, uint8_t* type, int32_t* level,

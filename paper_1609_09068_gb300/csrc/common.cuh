@@ -101,6 +101,10 @@ struct Ctl {
   alignas(128) int cnt[8];  // frontier counters (rotating)
   alignas(128) int flags[8];  // misc flags (e.g. not-converged)
   double dsum[4];
+  // waves run by the partitioner's wave kernels, per WaveKind: [0] by the
+  // whole grid (a grid barrier each), [1] by block 0 alone; counted by
+  // block 0's thread 0, zeroed by init_ctl only
+  alignas(128) int waves[8][2];
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -437,7 +441,10 @@ pr_status build_fx_sched(pr_partition_s* P, Arena& tmp, Ctl* ctl);
 pr_status ingest(const pr_csr* csr, uint32_t flags, DevGraph* g, Arena& keep, Arena& tmp, Ctl* ctl);
 
 // scc.cu: rep[v] = representative (largest vertex id) of v's SCC.
-pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl);
+// ev (may be null): events recorded after the trim and after the giant SCC's
+// forward-backward search; *rounds (may be null): colouring rounds run
+pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl, cudaEvent_t* ev = nullptr,
+                     int32_t* rounds = nullptr);
 
 // levels.cu: levels, merge flags and CAC grouping (Theorem 3.1 restated
 // per condensation node).  Outputs per vertex: crep (smallest vertex of the
@@ -552,6 +559,11 @@ struct pr_partition_s {
   int32_t* fxs_wbase = nullptr;
   uint8_t* fxs_wcnt = nullptr;
   uint2* fxs_words = nullptr;
+  // PR_PARTITION_TIMING: phase times (pr_partition_timing order) and counts
+  bool timed = false;
+  float phase_ms[6] = {0, 0, 0, 0, 0, 0};
+  int32_t colour_rounds = 0;
+  int32_t waves[5][2] = {};
   std::vector<prgb::LevelRange> levels;  // host, processing order
   std::vector<int32_t> h_c_off;          // host copy of c_off [K+1]
   int32_t cta_max = prgb::kCtaCompMax;   // largest component of the one-CTA class (tunable)

@@ -228,7 +228,7 @@ __global__ void kahn_k(int32_t n, const int32_t* __restrict__ rep, const int32_t
   }
   const Frontier f{fa_node, fa_chunk, fb_node, fb_chunk, cap};
   KahnK k{nsize, pending, key, level_node, wave_node, merged, cin_ptr, cin_src};
-  run_waves(ctl, f, 211, k);
+  run_waves(ctl, f, 211, kWaveKahn, k);
 }
 
 // lock-free union-find with parent[x] <= x (roots are the smallest ids)

@@ -84,7 +84,7 @@ __global__ void trim_k(const int32_t* __restrict__ optr, const int32_t* __restri
   }
   const Frontier f{fav, fac, fbv, fbc, cap};
   TrimK k{optr, oidx, iptr, iidx, rem_out, rem_in, state, rep};
-  run_waves(ctl, f, 101, k);
+  run_waves(ctl, f, 101, kWaveTrim, k);
 }
 
 // ---- max-label propagation inside the pieces, frontier driven ---------------
@@ -142,7 +142,7 @@ __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __re
   }
   const Frontier f{fav, fac, fbv, fbc, cap};
   PropK k{ptr, idx, pin, sig, stamp};
-  run_waves(ctl, f, 111, k);
+  run_waves(ctl, f, 111, kWaveProp, k);
 }
 
 // ---- backward search from every colour root --------------------------------
@@ -186,7 +186,7 @@ __global__ void root_bfs_k(const int32_t* __restrict__ ptr, const int32_t* __res
   }
   const Frontier f{fav, fac, fbv, fbc, cap};
   RootBfsK k{ptr, idx, color, mark, tag};
-  run_waves(ctl, f, 131, k);
+  run_waves(ctl, f, 131, kWaveRoot, k);
 }
 
 // settle what the search reached; the colours become the next pieces
@@ -265,7 +265,7 @@ __global__ void reach_k(const int32_t* __restrict__ ptr, const int32_t* __restri
   }
   const Frontier f{fav, fac, fbv, fbc, cap};
   ReachK k{ptr, idx, rep, mark, tag, need, tag_need};
-  run_waves(ctl, f, 121, k);
+  run_waves(ctl, f, 121, kWaveReach, k);
 }
 
 // the SCC of the pivot is F and B: find its largest id, then assign it and
@@ -301,7 +301,7 @@ static unsigned grid_n(int64_t n) {
   return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
+pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl, cudaEvent_t* ev, int32_t* rounds) {
   cudaStream_t s = tmp.stream();
   const int32_t n = g.n;
   if (n == 0) return PR_OK;
@@ -328,6 +328,7 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
                     &fav, &fac, &fbv, &fbc, &cp, &ctl};
     PRGB_TRY(launch_coop((const void*)trim_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
   }
+  if (ev) PRGB_CUDA(cudaEventRecord(ev[0], s));
   // FW-BW from the best-connected unassigned vertex takes out the giant SCC
   {
     unsigned long long* best;
@@ -367,6 +368,7 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
       PRGB_LAUNCH();
     }
   }
+  if (ev) PRGB_CUDA(cudaEventRecord(ev[1], s));
   int32_t* mark;
   PRGB_TRY(tmp.alloc(&mark, n));
   PRGB_CUDA(cudaMemsetAsync(mark, 0, (size_t)n * 4, s));
@@ -395,6 +397,7 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl) {
     PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     PRGB_CUDA(cudaMemcpyAsync(&h[1], &ctl->cnt[7], sizeof(int), cudaMemcpyDeviceToHost, s));
     PRGB_CUDA(cudaStreamSynchronize(s));
+    if (rounds) *rounds = round + 1;
     if (h[0]) return (pr_status)h[0];
     if (h[1] == 0) return PR_OK;
   }

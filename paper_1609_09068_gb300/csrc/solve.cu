@@ -912,6 +912,17 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
 // warp classes on the three side streams, joined back into s before the
 // next level.  Only launches, memsets and event records: it can be
 // captured into a CUDA graph.
+// A timing event: inside a stream capture an external record, which becomes
+// an event-record node so that the event times each replay; a plain record
+// otherwise.
+static cudaError_t record_timing(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t q = cudaStreamIsCapturing(s, &cs);
+  if (q != cudaSuccess) return q;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(e, s);
+}
+
 pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& b, bool mixed, SideStreams& side,
                          cudaStream_t s, KernelTiming* timing, int64_t* nl, const float* yhat = nullptr) {
   Ctl* ctl = a.ctl;
@@ -932,7 +943,7 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
     NvtxRange nvtx_level("prgb level", (int)li);
     // external records: inside a captured graph they become event-record
     // nodes, so the events time each replay
-    if (timing) PRGB_CUDA(cudaEventRecordWithFlags(timing->level[li], s, cudaEventRecordExternal));
+    if (timing) PRGB_CUDA(record_timing(timing->level[li], s));
     {
       HeavyRows xv;
       xv.rows = P->xheavy_rows + r.xh_begin;
@@ -971,12 +982,12 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
         void* args32[] = {&a, &L, &fz, &F, &part, &hv, &hs};
         // external records: inside a captured graph they become event-record
         // nodes, so the events time each replay
-        if (timing) PRGB_CUDA(cudaEventRecordWithFlags(timing->start[ti], s, cudaEventRecordExternal));
+        if (timing) PRGB_CUDA(record_timing(timing->start[ti], s));
         if (mixed)
           PRGB_TRY(launch_coop((const void*)solve_large_scc_mx_k, kBlock, 0, s, args32, P->coop_blocks, nullptr));
         else
           PRGB_TRY(launch_coop((const void*)solve_large_scc_k, kBlock, 0, s, args64, P->coop_blocks, nullptr));
-        if (timing) PRGB_CUDA(cudaEventRecordWithFlags(timing->stop[ti], s, cudaEventRecordExternal));
+        if (timing) PRGB_CUDA(record_timing(timing->stop[ti], s));
         ti++;
       } else {
         void* args[] = {&a, &L};
@@ -1032,7 +1043,7 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
     }
   }
   if (timing && !P->levels.empty())
-    PRGB_CUDA(cudaEventRecordWithFlags(timing->level[P->levels.size()], s, cudaEventRecordExternal));
+    PRGB_CUDA(record_timing(timing->level[P->levels.size()], s));
   return PR_OK;
 }
 
@@ -1078,34 +1089,32 @@ SolvePlan::~SolvePlan() {
   delete keep;
 }
 
-// (Re)build the graph for these parameters if the cached one differs.
-// The graphs of the last kPlanGraphs parameter sets are kept (a caller
-// alternating, say, FP64 and mixed solves does not re-capture each time).
-static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double tol, int norm, int max_iter,
-                              bool mixed, bool timing, const pr_mpnn_s* warm, int lu, PlanGraph** out) {
+// The cached graph for these parameters, or null.  The graphs of the last
+// kPlanGraphs parameter sets are kept (a caller alternating, say, FP64 and
+// mixed solves does not re-capture each time).
+static PlanGraph* plan_find(SolvePlan* pl, double c, double tol, int norm, int max_iter, bool mixed, bool timing,
+                            const pr_mpnn_s* warm, int lu) {
   for (PlanGraph& e : pl->graphs)
     if (e.c == c && e.tol == tol && e.norm == norm && e.max_iter == max_iter && e.mixed == mixed &&
         e.timing == timing && e.warm_uid == (warm ? warm->uid : 0) && e.lu == lu && e.wait_us == wait_limit_us()) {
       e.last_use = ++pl->uses;
-      *out = &e;
-      return PR_OK;
+      return &e;
     }
+  return nullptr;
+}
+
+// The plan's buffers and streams, allocated on first use (and the mixed,
+// warm-start and timing extras when first asked for).
+static pr_status plan_setup(pr_partition_s* P, SolvePlan* pl, bool mixed, bool timing, const pr_mpnn_s* warm) {
   const int32_t n = P->g.n;
   const int32_t K = P->n_comp;
-  if (pl->graphs.size() >= (size_t)kPlanGraphs) {
-    size_t old = 0;
-    for (size_t i = 1; i < pl->graphs.size(); i++)
-      if (pl->graphs[i].last_use < pl->graphs[old].last_use) old = i;
-    if (pl->graphs[old].exec) cudaGraphExecDestroy(pl->graphs[old].exec);
-    if (pl->graphs[old].graph) cudaGraphDestroy(pl->graphs[old].graph);
-    pl->graphs.erase(pl->graphs.begin() + old);
-  }
   if (!pl->keep) {
     pl->keep = new (std::nothrow) Arena(P->stream);
     if (!pl->keep) return PR_ENOMEM;
     PRGB_CUDA(cudaStreamCreateWithFlags(&pl->cs, cudaStreamNonBlocking));
     PRGB_CUDA(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
     PRGB_TRY(pl->side.create());
+    PRGB_TRY(pl->cap_side.create());
     PRGB_TRY(pl->keep->alloc(&pl->ctl, 1));
     PRGB_TRY(pl->keep->alloc(&pl->iters, (size_t)K + 1));
     PRGB_TRY(pl->keep->alloc(&pl->iters64, (size_t)K + 1));
@@ -1136,7 +1145,11 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
     pl->yhat_uid = 0;
   }
   if (timing) PRGB_TRY(pl->kt.ensure(P));
-  PRGB_TRY(set_solve_attrs(P, mixed));
+  return set_solve_attrs(P, mixed);
+}
+
+static SolveArgs plan_args(pr_partition_s* P, SolvePlan* pl, double c, double tol, int norm, int max_iter,
+                           bool mixed, const pr_mpnn_s* warm, int lu) {
   SolveArgs a = make_solve_args(P, c, pl->u, tol, norm, max_iter, nullptr, pl->b, pl->iters,
                                 mixed ? pl->iters64 : nullptr, pl->ctl);
   if (warm) {
@@ -1144,17 +1157,39 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
     a.yhat = pl->yhat;
   }
   a.lu_threshold = lu;
+  return a;
+}
+
+// The start of every solve of the plan: its control word and counters.
+static pr_status plan_head(SolvePlan* pl, int32_t K, cudaStream_t s, int64_t* nl) {
+  PRGB_TRY(init_ctl(pl->ctl, s));
+  PRGB_CUDA(cudaMemsetAsync(pl->iters, 0, ((size_t)K + 1) * 4, s));
+  PRGB_CUDA(cudaMemsetAsync(pl->iters64, 0, ((size_t)K + 1) * 4, s));
+  if (wait_limit_us()) ++*nl;  // the kernel that sets the wait limit
+  return PR_OK;
+}
+
+// Capture the level loop for these parameters into a CUDA graph (on the
+// plan's own capture stream and side streams, so that it can run while the
+// device still executes work the call enqueued on the others) and cache it,
+// evicting the least recently used graph beyond kPlanGraphs.
+static pr_status plan_capture(pr_partition_s* P, SolvePlan* pl, double c, double tol, int norm, int max_iter,
+                              bool mixed, bool timing, const pr_mpnn_s* warm, int lu) {
+  if (pl->graphs.size() >= (size_t)kPlanGraphs) {
+    size_t old = 0;
+    for (size_t i = 1; i < pl->graphs.size(); i++)
+      if (pl->graphs[i].last_use < pl->graphs[old].last_use) old = i;
+    if (pl->graphs[old].exec) cudaGraphExecDestroy(pl->graphs[old].exec);
+    if (pl->graphs[old].graph) cudaGraphDestroy(pl->graphs[old].graph);
+    pl->graphs.erase(pl->graphs.begin() + old);
+  }
+  const SolveArgs a = plan_args(P, pl, c, tol, norm, max_iter, mixed, warm, lu);
   const long long before = launch_count();
   int64_t nl = 0;
   PRGB_CUDA(cudaStreamBeginCapture(pl->cs, cudaStreamCaptureModeThreadLocal));
-  pr_status st = PR_OK;
-  if (init_ctl(pl->ctl, pl->cs) != PR_OK ||
-      cudaMemsetAsync(pl->iters, 0, ((size_t)K + 1) * 4, pl->cs) != cudaSuccess ||
-      cudaMemsetAsync(pl->iters64, 0, ((size_t)K + 1) * 4, pl->cs) != cudaSuccess)
-    st = PR_ECUDA;
-  if (st == PR_OK && wait_limit_us()) nl++;  // the kernel that sets the wait limit
+  pr_status st = plan_head(pl, P->n_comp, pl->cs, &nl);
   if (st == PR_OK)
-    st = enqueue_levels(P, a, pl->b, mixed, pl->side, pl->cs, timing ? &pl->kt : nullptr, &nl,
+    st = enqueue_levels(P, a, pl->b, mixed, pl->cap_side, pl->cs, timing ? &pl->kt : nullptr, &nl,
                         warm ? pl->yhat : nullptr);
   cudaGraph_t g = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(pl->cs, &g);
@@ -1183,7 +1218,6 @@ static pr_status plan_prepare(pr_partition_s* P, SolvePlan* pl, double c, double
   e.wait_us = wait_limit_us();
   e.last_use = ++pl->uses;
   pl->graphs.push_back(e);
-  *out = &pl->graphs.back();
   return PR_OK;
 }
 
@@ -1197,26 +1231,36 @@ pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_hos
   SolvePlan* pl = P->plan;
   *out = pl;
   const int32_t n = P->g.n;
-  PlanGraph* ge = nullptr;
-  PRGB_TRY(plan_prepare(P, pl, c, tol, norm, max_iter, mixed, timing, warm, lu, &ge));
+  PRGB_TRY(plan_setup(P, pl, mixed, timing, warm));
+  PlanGraph* ge = plan_find(pl, c, tol, norm, max_iter, mixed, timing, warm, lu);
   // the plan's buffers are reused: order this call after the previous one
   PRGB_CUDA(cudaStreamWaitEvent(s, pl->done, 0));
   if (n > 0)
     PRGB_COPY(cudaMemcpyAsync(pl->u, u, (size_t)n * 8, u_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                               s));
-  int64_t nguess = 0;
+  int64_t nl = 0;
   if (warm && (pl->yhat_uid != warm->uid || pl->yhat_ver != warm->version)) {
     // the network's output depends on the graph and the weights only: once
-    // per partition and model version, before the captured level loop
+    // per partition and model version, before the level loop
     const long long before = launch_count();
     PRGB_TRY(mpnn_guess(warm, P, pl->yhat, pl->inf, nullptr, s));
-    nguess = launch_count() - before;
+    nl += launch_count() - before;
     pl->yhat_uid = warm->uid;
     pl->yhat_ver = warm->version;
   }
-  PRGB_CUDA(cudaGraphLaunch(ge->exec, s));
-  add_launches(ge->nodes);
-  int64_t nl = ge->nodes + nguess;
+  if (ge) {
+    PRGB_CUDA(cudaGraphLaunch(ge->exec, s));
+    add_launches(ge->nodes);
+    nl += ge->nodes;
+  } else {
+    // first solve with these parameters: the level loop launched directly
+    // (the device starts at once), then captured for the next calls while
+    // the device runs this one
+    const SolveArgs a = plan_args(P, pl, c, tol, norm, max_iter, mixed, warm, lu);
+    PRGB_TRY(plan_head(pl, P->n_comp, s, &nl));
+    PRGB_TRY(enqueue_levels(P, a, pl->b, mixed, pl->side, s, timing ? &pl->kt : nullptr, &nl,
+                            warm ? pl->yhat : nullptr));
+  }
   if (R_on_host) {
     PRGB_TRY(scatter_out(P, pl->b.R, pl->Rout, s, &nl));
     if (n > 0) PRGB_COPY(cudaMemcpyAsync(R, pl->Rout, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
@@ -1225,6 +1269,7 @@ pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_hos
   }
   PRGB_CUDA(cudaEventRecord(pl->done, s));
   *launches = nl;
+  if (!ge) PRGB_TRY(plan_capture(P, pl, c, tol, norm, max_iter, mixed, timing, warm, lu));
   return PR_OK;
 }
 
@@ -1309,7 +1354,7 @@ pr_status tune_partition(pr_partition_s* P, double c, const double* u, double to
     SolvePlan* pl = nullptr;
     int64_t nl = 0;
     float t = 1e30f;
-    for (int rep = 0; rep < 3 && st == PR_OK; rep++) {  // the first builds the graph
+    for (int rep = 0; rep < 3 && st == PR_OK; rep++) {  // the first runs directly and captures the graph
       if (cudaEventRecord(e0, s) != cudaSuccess) st = PR_ECUDA;
       if (st == PR_OK)
         st = plan_solve(P, c, u, false, tol, PR_NORM_L1, 10000, false, false, nullptr, 0, R, false, s, &pl, &nl);

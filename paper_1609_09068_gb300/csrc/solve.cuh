@@ -176,7 +176,8 @@ constexpr int kPlanGraphs = 4;
 struct SolvePlan {
   Arena* keep = nullptr;
   SolveBufs b;
-  SideStreams side;
+  SideStreams side;      // the directly launched solves
+  SideStreams cap_side;  // the captures
   KernelTiming kt;
   cudaStream_t cs = nullptr;
   cudaEvent_t done = nullptr;

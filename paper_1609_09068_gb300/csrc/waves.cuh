@@ -20,6 +20,9 @@ constexpr int kWavePerSm = 4;        // their co-resident blocks per SM (2 and 8
 constexpr int kSmallFrontier = 64;
 constexpr int kLocalWaves = 4096;
 
+// which kernel runs the waves (the slot of Ctl::waves)
+enum WaveKind { kWaveTrim = 0, kWaveProp = 1, kWaveReach = 2, kWaveRoot = 3, kWaveKahn = 4 };
+
 struct Frontier {
   int* av;
   int* ac;
@@ -129,7 +132,7 @@ __device__ __forceinline__ bool wave_barrier(Ctl* ctl, int where, int next, Wave
 // frontier (wave 0) into (av, ac), counting it in ctl->cnt[0]; this starts
 // with the barrier that publishes it.  Returns false when a barrier failed.
 template <class K>
-__device__ bool run_waves(Ctl* ctl, const Frontier& f, int where, const K& item) {
+__device__ bool run_waves(Ctl* ctl, const Frontier& f, int where, WaveKind kind, const K& item) {
   const int gw = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
   const int lw0 = threadIdx.x >> 5, lnw = blockDim.x >> 5;
@@ -138,6 +141,7 @@ __device__ bool run_waves(Ctl* ctl, const Frontier& f, int where, const K& item)
   for (;;) {
     if (st.cnt == 0) return true;
     if (st.cnt >= kSmallFrontier) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->waves[kind][0]++;
       one_wave(ctl, f, st.wave, st.cnt, gw, nw, item);
       if (!wave_barrier(ctl, where, st.wave + 1, &st)) return false;
       continue;
@@ -156,6 +160,7 @@ __device__ bool run_waves(Ctl* ctl, const Frontier& f, int where, const K& item)
         if (c == 0 || c >= kSmallFrontier) break;
       }
       if (threadIdx.x == 0) {
+        ctl->waves[kind][1] += wave - st.wave;
         ctl->flags[7] = wave;
         __threadfence();
       }

@@ -41,3 +41,33 @@ def test_level_times_cover_the_solve(prgb):
     R2, st2 = prgb.solve(P, 0.85, u, 1e-10, with_stats=True)
     assert "level_ms" not in st2
     assert torch.equal(R, R2)
+
+
+def test_partition_phase_times(prgb):
+    """PR_PARTITION_TIMING: phase times between CUDA events that add up to
+    the call, wave counts of the frontier kernels, and the same partition as
+    without the flag."""
+    import torch
+    g = gg.web_like(seed=12, n=60_000, n_small=1_200, layers=12, giant_layer=4)
+    G = prgb.graph(torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.col).cuda())
+    P0 = prgb.partition(G)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    P1 = prgb.partition(G, timing=True)
+    b.record()
+    torch.cuda.synchronize()
+    t = P1.timing()
+    phases = [t[k] for k in ("trim_ms", "giant_ms", "colour_ms", "levels_ms", "layout_ms")]
+    assert all(x >= 0 for x in phases) and t["total_ms"] > 0
+    assert sum(phases) <= t["total_ms"] * 1.001 + 1e-3
+    assert t["total_ms"] <= a.elapsed_time(b) * 1.001 + 1e-3
+    assert t["colour_rounds"] >= 1
+    w = t["waves"]
+    assert w["trim"]["grid"] + w["trim"]["block"] >= 1
+    assert w["reach"]["grid"] + w["reach"]["block"] >= 1  # the giant's forward-backward search
+    assert w["kahn"]["grid"] + w["kahn"]["block"] >= 1
+    for x, y in zip(P0.query(), P1.query()):
+        assert torch.equal(x, y)
+    with pytest.raises(prgb.PrError) as e:
+        P0.timing()
+    assert e.value.code == 1
