@@ -189,6 +189,7 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
     if (st == PR_OK) st = tmp.alloc(&crep, (size_t)n);
     if (st == PR_OK) st = tmp.alloc(&wave, (size_t)n);
     if (st == PR_OK) st = init_ctl(ctl, s);
+    if (st == PR_OK && cudaMemsetAsync(ctl->waves, 0, sizeof(ctl->waves), s) != cudaSuccess) st = PR_ECUDA;
     // phase events: 0 start, 1 trim, 2 giant, 3 colouring, 4 levels,
     // 5 layout, 6 end; all recorded at the start, so a phase that does not
     // run reads 0 ms

@@ -103,7 +103,8 @@ struct Ctl {
   double dsum[4];
   // waves run by the partitioner's wave kernels, per WaveKind: [0] by the
   // whole grid (a grid barrier each), [1] by block 0 alone; counted by
-  // block 0's thread 0, zeroed by init_ctl only
+  // block 0's thread 0.  init_ctl leaves them alone (they add up over the
+  // phases of a partition): the partition zeroes them once.
   alignas(128) int waves[8][2];
 };
 

@@ -8,27 +8,57 @@
 namespace prgb {
 
 // one warp per row: range and order checks, loop detection, loop-free degree
+// Rows of at most kLaneRow entries are checked one per lane (a warp takes 32
+// consecutive rows, whose entries are contiguous); longer rows are walked by
+// the whole warp, one after the other.
+constexpr int kLaneRow = 32;
+
 __global__ void validate_rows_k(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                 int32_t n, int64_t nnz, int32_t* __restrict__ outdeg,
                                 uint8_t* __restrict__ has_loop, Ctl* ctl) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp; i < n; i += nwarps) {
-    const int64_t s = rowptr[i], e = rowptr[i + 1];
-    bool bad = (s > e) || (s < 0) || (e > nnz) || (i == 0 && s != 0) || (i == n - 1 && e != nnz);
+  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    int64_t s = 0, e = 0;
+    bool bad = false, longrow = false;
     int loop = 0;
-    if (!bad) {
-      for (int64_t k = s + lane; k < e; k += 32) {
-        const int32_t c = col[k];
-        if (c < 0 || c >= n) bad = true;
-        if (k > s && col[k - 1] >= c) bad = true;
-        if (c == (int32_t)i) loop = 1;
+    if (i < n) {
+      s = rowptr[i];
+      e = rowptr[i + 1];
+      bad = (s > e) || (s < 0) || (e > nnz) || (i == 0 && s != 0) || (i == n - 1 && e != nnz);
+      longrow = !bad && e - s > kLaneRow;
+      if (!bad && !longrow) {
+        int32_t prev = -1;
+        for (int64_t k = s; k < e; k++) {
+          const int32_t c = col[k];
+          if (c < 0 || c >= n || c <= prev) bad = true;  // in range, strictly ascending
+          if (c == (int32_t)i) loop = 1;
+          prev = c;
+        }
       }
     }
-    bad = __any_sync(0xffffffffu, bad);
-    loop = __any_sync(0xffffffffu, loop);
-    if (lane == 0) {
+    for (unsigned todo = __ballot_sync(0xffffffffu, longrow); todo; todo &= todo - 1) {
+      const int src = __ffs(todo) - 1;
+      const int64_t rs = __shfl_sync(0xffffffffu, s, src), re = __shfl_sync(0xffffffffu, e, src);
+      const int32_t r = (int32_t)(base + src);
+      bool b = false;
+      int lp = 0;
+      for (int64_t k = rs + lane; k < re; k += 32) {
+        const int32_t c = col[k];
+        if (c < 0 || c >= n) b = true;
+        if (k > rs && col[k - 1] >= c) b = true;
+        if (c == r) lp = 1;
+      }
+      b = __any_sync(0xffffffffu, b);
+      lp = __any_sync(0xffffffffu, lp);
+      if (lane == src) {
+        bad = b;
+        loop = lp;
+      }
+    }
+    if (i < n) {
       if (bad) set_err(ctl, PR_EINVAL, 1);
       outdeg[i] = bad ? 0 : (int32_t)(e - s) - loop;
       has_loop[i] = (uint8_t)loop;
@@ -36,28 +66,57 @@ __global__ void validate_rows_k(const int32_t* __restrict__ rowptr, const int32_
   }
 }
 
-// copy non-loop entries; also records the source row of every kept edge
+// copy the non-loop entries and record the source row of every kept edge
+// (rows split between lanes and warps as in validate_rows_k)
+__device__ __forceinline__ void strip_one(int64_t k, int64_t s, int64_t o, bool lp, int32_t i,
+                                          const int32_t* __restrict__ col, int32_t* __restrict__ oidx,
+                                          uint32_t* __restrict__ key_dst, uint32_t* __restrict__ val_src) {
+  const int32_t c = col[k];
+  if (c == i) return;
+  const int64_t pos = o + (k - s) - ((lp && c > i) ? 1 : 0);
+  oidx[pos] = c;
+  key_dst[pos] = (uint32_t)c;
+  val_src[pos] = (uint32_t)i;
+}
+
 __global__ void strip_loops_k(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                               int32_t n, const uint8_t* __restrict__ has_loop,
                               const int32_t* __restrict__ optr, int32_t* __restrict__ oidx,
-                              uint32_t* __restrict__ key_dst, uint32_t* __restrict__ val_src,
-                              int32_t* __restrict__ indeg) {
+                              uint32_t* __restrict__ key_dst, uint32_t* __restrict__ val_src) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp; i < n; i += nwarps) {
-    const int64_t s = rowptr[i], e = rowptr[i + 1];
-    const int64_t o = optr[i];
-    const bool lp = has_loop[i] != 0;
-    for (int64_t k = s + lane; k < e; k += 32) {
-      const int32_t c = col[k];
-      if (c == (int32_t)i) continue;
-      const int64_t pos = o + (k - s) - ((lp && c > (int32_t)i) ? 1 : 0);
-      oidx[pos] = c;
-      key_dst[pos] = (uint32_t)c;
-      val_src[pos] = (uint32_t)i;
-      atomicAdd(&indeg[c], 1);
+  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    int64_t s = 0, e = 0, o = 0;
+    bool lp = false;
+    if (i < n) {
+      s = rowptr[i];
+      e = rowptr[i + 1];
+      o = optr[i];
+      lp = has_loop[i] != 0;
     }
+    const bool longrow = e - s > kLaneRow;
+    if (i < n && !longrow)
+      for (int64_t k = s; k < e; k++) strip_one(k, s, o, lp, (int32_t)i, col, oidx, key_dst, val_src);
+    for (unsigned todo = __ballot_sync(0xffffffffu, longrow); todo; todo &= todo - 1) {
+      const int src = __ffs(todo) - 1;
+      const int64_t rs = __shfl_sync(0xffffffffu, s, src), re = __shfl_sync(0xffffffffu, e, src);
+      const int64_t ro = __shfl_sync(0xffffffffu, o, src);
+      const bool rl = __shfl_sync(0xffffffffu, (int)lp, src) != 0;
+      for (int64_t k = rs + lane; k < re; k += 32)
+        strip_one(k, rs, ro, rl, (int32_t)(base + src), col, oidx, key_dst, val_src);
+    }
+  }
+}
+
+// Column offsets from the edges' targets sorted ascending: iptr[x] = the
+// number of edges whose target is below x, for x in [0, n].
+__global__ void col_ptr_k(int64_t m, const uint32_t* __restrict__ tgt, int32_t n, int32_t* __restrict__ iptr) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = i == 0 ? 0 : (int64_t)tgt[i - 1] + 1;  // first column whose offset is i
+    const int64_t hi = i == m ? (int64_t)n : (int64_t)tgt[i];  // last such column
+    for (int64_t x = lo; x <= hi; x++) iptr[x] = (int32_t)i;
   }
 }
 
@@ -205,22 +264,21 @@ pr_status ingest(const pr_csr* csr, uint32_t flags, DevGraph* g, Arena& keep, Ar
   PRGB_TRY(keep.alloc(&g->oidx, (size_t)(m > 0 ? m : 1)));
   PRGB_TRY(keep.alloc(&g->iidx, (size_t)(m > 0 ? m : 1)));
   uint32_t *kd = nullptr, *vs = nullptr, *kt = nullptr, *vt = nullptr;
-  int32_t* indeg = nullptr;
   PRGB_TRY(tmp.alloc(&kd, (size_t)(m > 0 ? m : 1)));
   PRGB_TRY(tmp.alloc(&vs, (size_t)(m > 0 ? m : 1)));
   PRGB_TRY(tmp.alloc(&kt, (size_t)(m > 0 ? m : 1)));
   PRGB_TRY(tmp.alloc(&vt, (size_t)(m > 0 ? m : 1)));
-  PRGB_TRY(tmp.alloc(&indeg, (size_t)n + 1));
-  PRGB_CUDA(cudaMemsetAsync(indeg, 0, ((size_t)n + 1) * 4, s));
   if (n > 0) {
-    strip_loops_k<<<grid_rows(n), kBlock, 0, s>>>(rowptr, col, n, has_loop, g->optr, g->oidx, kd, vs, indeg);
+    strip_loops_k<<<grid_rows(n), kBlock, 0, s>>>(rowptr, col, n, has_loop, g->optr, g->oidx, kd, vs);
     PRGB_LAUNCH();
   }
-  PRGB_TRY(scan_i32(indeg, g->iptr, n, tmp));
   // CSR order is (source asc, target asc); a stable sort by target gives
-  // each column's sources in ascending order.
+  // each column's sources in ascending order, and the sorted targets the
+  // column offsets.
   PRGB_TRY(radix_sort_pairs(kd, vs, kt, vt, m, bits_for((uint32_t)(n > 0 ? n - 1 : 0)), tmp));
   if (m > 0) PRGB_CUDA(cudaMemcpyAsync(g->iidx, vs, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
+  col_ptr_k<<<grid_rows((m + 1 + 7) / 8), kBlock, 0, s>>>(m, kd, n, g->iptr);
+  PRGB_LAUNCH();
   PRGB_TRY(build_heavy(g->iptr, n, keep, tmp, &g->heavy_rows, &g->heavy_choff, &g->heavy_chrow, &g->nheavy,
                         &g->nchunks));
   PRGB_TRY(build_lorder(g->iptr, n, nullptr, 0, keep, tmp, &g->lorder));

@@ -8,6 +8,8 @@
 #include <mutex>
 #include <string>
 
+#include <stddef.h>
+
 #include "common.cuh"
 #include "spmv.cuh"
 
@@ -71,7 +73,8 @@ void set_wait_limit_us(unsigned int us) { g_wait_us.store(us, std::memory_order_
 __global__ void set_wait_k(Ctl* ctl, unsigned int us) { ctl->wait_us = us; }
 
 pr_status init_ctl(Ctl* ctl, cudaStream_t s) {
-  PRGB_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+  // the wave counters are left alone: they add up over a whole partition
+  PRGB_CUDA(cudaMemsetAsync(ctl, 0, offsetof(Ctl, waves), s));
   const unsigned int us = wait_limit_us();
   if (us) {
     set_wait_k<<<1, 1, 0, s>>>(ctl, us);
