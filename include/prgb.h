@@ -90,20 +90,25 @@ typedef struct pr_mpnn_s pr_mpnn;
 #define PR_NORM_LINF 1 /* the paper's rule: iterate while max(P) >= tol */
 
 /* Arithmetic of the solve. */
-#define PR_PREC_FP64 0  /* FP64, except that the series of SCCs of at most
-                           1,024 vertices is summed exactly in 128-bit fixed
-                           point (each row's sum and R exact, each term
-                           rounded once to a quantum of about 2^-110
-                           ||W_C||_1), which is at least as accurate */
+#define PR_PREC_FP64 0  /* FP64, except that the series of the SCCs of at
+                           most 1,024 vertices and of the SCCs above 16,384
+                           vertices (the grid-wide ones) is summed exactly in
+                           128-bit fixed point (each row's sum and R exact,
+                           each term rounded once to a quantum of about
+                           2^-110 ||W_C||_1, 2^-110 |C| max W_C for the
+                           grid-wide ones), which is at least as accurate */
 #define PR_PREC_MIXED 1 /* pr_solve only, with PR_NORM_L1 and no replay: the
-                           series of each SCC above 1,024 vertices runs in
-                           FP32 (values, z = P/outdeg and accumulation), then
-                           an FP64 residual r = W + cA^T(R/outdeg) - R of the
-                           component is formed; while ||r||_1 > tol*|C|/n
-                           the correction (I - cA^T)D = r is summed by the
-                           same FP32 series and R += D in FP64.  Smaller SCCs
-                           run the exact fixed-point series as in
-                           PR_PREC_FP64; the inflow gather, CACs and 1-vertex
+                           series of each SCC of 1,025-16,384 vertices, and
+                           of each larger one whose fixed-point sweep would
+                           not fit in half the L2 cache (48 B per vertex),
+                           runs in FP32 (values, z = P/outdeg and
+                           accumulation), then an FP64 residual
+                           r = W + cA^T(R/outdeg) - R of the component is
+                           formed; while ||r||_1 > tol*|C|/n the correction
+                           (I - cA^T)D = r is summed by the same FP32 series
+                           and R += D in FP64.  The other SCCs run the exact
+                           fixed-point series as in PR_PREC_FP64 (faster
+                           there); the inflow gather, CACs and 1-vertex
                            components stay FP64.  Every SCC ends with a
                            residual within its budget, so the L1 residual of
                            R is at most tol (plus FP64 rounding of the
@@ -152,11 +157,15 @@ typedef struct pr_solve_stats {
     int32_t timing;       /* in: 1 = time the grid-wide power-series kernels
                              with CUDA events on the call's stream */
     float kernel_ms;      /* out (timing = 1): their summed device time */
-    int64_t kernel_bytes; /* out (timing = 1): their algorithmic bytes: per
-                             sweep 4 B per edge + 40 B per row (index, z
-                             gather, R read/write, z write, row pointer and
-                             out-degree), plus 56 B per row once per launch
-                             (the start and the end of the series) */
+    int64_t kernel_bytes; /* out (timing = 1): their algorithmic bytes.
+                             FP64 mode (16-byte fixed-point values): per
+                             sweep 4 B per edge (index) + 72 B per row (z
+                             gather and write, R read and write, c/outdeg),
+                             plus 88 B per row once per launch (the start
+                             and the end of the series).  Mixed precision:
+                             per FP64 sweep 4 B per edge + 40 B per row, per
+                             FP32 sweep 4 B per edge + 24 B per row, plus 56 B
+                             per row per launch */
     int64_t kernel_launches; /* out (timing = 1): number of such launches */
     int32_t fp64_sweeps_max; /* PR_PREC_MIXED: the most FP64 residual sweeps
                                 of any SCC (included in iters_max and

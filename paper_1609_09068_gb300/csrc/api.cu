@@ -409,11 +409,22 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
           stats->kernel_ms += ms;
           const LargeComp& L = kt->comps[i];
           const int64_t it = h[L.c];
-          // FP32 sweeps move 4 B per edge + 24 B per row (z gather and
-          // write, F read/write, row pointer, 1/outdeg in FP32); once per
-          // launch 56 B per row: the start (W, c/outdeg read, R and z
-          // written) and the end (R, 1/outdeg read, R/outdeg written)
-          const int64_t it64 = mixed ? h64[L.c] : it;
+          if (!mixed) {
+            // the fixed-point series (16-byte values): per sweep 4 B per
+            // edge + 72 B per row (z gather and write, R read and write,
+            // c/outdeg); once per launch 88 B per row: the start (W and
+            // c/outdeg read, R and z written) and the end (R and 1/outdeg
+            // read, R and R/outdeg written)
+            stats->kernel_bytes += it * (4 * (int64_t)L.m_int + 72 * (int64_t)L.size) + 88 * (int64_t)L.size;
+            continue;
+          }
+          // mixed precision: FP64 sweeps move 4 B per edge + 40 B per row (z
+          // gather and write, R read and write, c/outdeg), FP32 sweeps 4 B
+          // per edge + 24 B per row (z gather and write, F read/write, row
+          // pointer, 1/outdeg in FP32); once per launch 56 B per row: the
+          // start (W, c/outdeg read, R and z written) and the end (R,
+          // 1/outdeg read, R/outdeg written)
+          const int64_t it64 = h64[L.c];
           stats->kernel_bytes += it64 * (4 * (int64_t)L.m_int + 40 * (int64_t)L.size) +
                                  (it - it64) * (4 * (int64_t)L.m_int + 24 * (int64_t)L.size) +
                                  56 * (int64_t)L.size;

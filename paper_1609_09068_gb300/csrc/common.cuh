@@ -370,6 +370,8 @@ inline pr_status reset_ctl(Ctl* ctl, cudaStream_t s) {
 
 // number of SMs of the current device (cached per device)
 int num_sms();
+// L2 cache size of the current device in bytes (cached per device)
+int64_t l2_bytes();
 
 // cooperative launch with as many co-resident blocks as fit (capped per SM)
 pr_status launch_coop(const void* kernel, int block, size_t smem, cudaStream_t s, void** args,

@@ -96,6 +96,19 @@ int num_sms() {
   return cached[dev];
 }
 
+int64_t l2_bytes() {
+  static int64_t cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev);
+    cached[dev] = v > 0 ? v : 1;
+  }
+  return cached[dev];
+}
+
 pr_status launch_coop(const void* kernel, int block, size_t smem, cudaStream_t s, void** args,
                       int max_per_sm, int* grid_out) {
   int per_sm = 0;

@@ -820,6 +820,16 @@ pr_status alloc_solve_bufs(const pr_partition_s* P, bool mixed, Arena& a, SolveB
     PRGB_TRY(a.alloc(&b->zB, (size_t)P->max_large + 1));
     PRGB_TRY(a.alloc(&b->part, (size_t)2 * num_sms() * 8));
     PRGB_TRY(a.alloc(&b->civ, (size_t)n + 1));
+    {
+      GiantFxBufs& g = b->gfx;
+      PRGB_TRY(a.alloc(&g.zA, (size_t)P->max_large + 1));
+      PRGB_TRY(a.alloc(&g.zB, (size_t)P->max_large + 1));
+      PRGB_TRY(a.alloc(&g.R, (size_t)P->max_large + 1));
+      PRGB_TRY(a.alloc(&g.part, (size_t)P->max_chunks + 1));
+      PRGB_TRY(a.alloc(&g.cnt, (size_t)P->max_heavy + 1));
+      PRGB_TRY(a.alloc(&g.acc, 4));
+      PRGB_CUDA(cudaMemsetAsync(g.cnt, 0, ((size_t)P->max_heavy + 1) * 4, s));
+    }
   }
   b->invf = nullptr;
   if (mixed && n > 0) {
@@ -983,10 +993,21 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
         // external records: inside a captured graph they become event-record
         // nodes, so the events time each replay
         if (timing) PRGB_CUDA(record_timing(timing->start[ti], s));
-        if (mixed)
+        // Mixed precision keeps its FP32 series for an SCC whose sweep
+        // does not fit in L2 (there the 4-byte values move a quarter of the
+        // fixed-point bytes); one that fits runs the exact fixed-point
+        // series, which is faster there than the FP32 one
+        const bool fx_fits = (int64_t)L.size * kGiantFxRowBytes <= l2_bytes() / 2;
+        if (mixed && !(fx_fits && b.gfx.acc)) {
           PRGB_TRY(launch_coop((const void*)solve_large_scc_mx_k, kBlock, 0, s, args32, P->coop_blocks, nullptr));
-        else
+        } else if (b.gfx.acc) {
+          GiantFxBufs gfx = b.gfx;
+          void* argsfx[] = {&a, &L, &gfx, &hv};
+          PRGB_CUDA(cudaMemsetAsync(gfx.acc, 0, 4 * sizeof(unsigned long long), s));
+          PRGB_TRY(launch_coop((const void*)solve_large_scc_fx_k, kBlock, 0, s, argsfx, P->coop_blocks, nullptr));
+        } else {
           PRGB_TRY(launch_coop((const void*)solve_large_scc_k, kBlock, 0, s, args64, P->coop_blocks, nullptr));
+        }
         if (timing) PRGB_CUDA(record_timing(timing->stop[ti], s));
         ti++;
       } else {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "fx128.cuh"
 #include "mpnn.cuh"
 #include "spmv.cuh"
 
@@ -140,6 +141,17 @@ struct SideStreams {
   ~SideStreams();
 };
 
+// scratch of the grid-wide fixed-point series (giant_fx.cu), sized for the
+// partition's largest grid-wide SCC
+struct GiantFxBufs {
+  fx128* zA = nullptr;   // [max_large + 1] z = P c/outdeg, two sweeps alternating
+  fx128* zB = nullptr;
+  fx128* R = nullptr;    // [max_large] the running sum
+  fx128* part = nullptr; // [max_chunks] heavy-row chunk partials
+  int32_t* cnt = nullptr;  // [max_heavy] chunk arrivals, zero between launches
+  unsigned long long* acc = nullptr;  // [4] norm slots of sweeps k % 3, then max W's bits; zeroed per launch
+};
+
 // work buffers of a solve, by permuted position
 struct SolveBufs {
   double* R = nullptr;
@@ -152,6 +164,7 @@ struct SolveBufs {
   float* invf = nullptr;
   double* civ = nullptr;  // c / outdeg (when there are grid-wide components)
   int32_t* lvl_ctr = nullptr;  // [4 * levels] claim counters of the level kernels
+  GiantFxBufs gfx;             // FP64 mode's grid-wide SCC series (when there are grid-wide SCCs)
 };
 
 // one captured level loop and the parameters it was captured for
@@ -195,6 +208,12 @@ struct SolvePlan {
   MpnnInfer inf;
   ~SolvePlan();
 };
+
+// The exact fixed-point series of one grid-wide SCC (giant_fx.cu); a
+// cooperative launch of kBlock-thread blocks.  g.acc must be zero at launch.
+// Its sweep touches about kGiantFxRowBytes per row (z twice, R, z gathered).
+constexpr int64_t kGiantFxRowBytes = 48;
+__global__ void solve_large_scc_fx_k(SolveArgs a, LargeComp L, GiantFxBufs g, HeavyRows hv);
 
 // Every component of a level with at most kFxMax vertices (SCCs by the
 // exact fixed-point series, CACs by one FP64 pass) in one persistent launch
