@@ -464,8 +464,8 @@ __global__ void __launch_bounds__(kBlock) gather_level_k(SolveArgs a, LevelRange
 // ---------------------------------------------------------------------------
 constexpr int kG = 8;  // lanes per row
 
-// R[p] = W[p] and z0[p - off] = W/outdeg for the rows of a component
-// R[p] = W[p], and z0[p - off] = W * scale[p] when z0 is given
+// R[p] = W[p], and z0[p - off] = W * scale[p] when z0 is given, for the
+// rows of a component
 __device__ __forceinline__ void load_rows(const SolveArgs& a, int off, int sz, double* z0, const double* scale) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
     const int p = off + (int)i;
@@ -473,93 +473,6 @@ __device__ __forceinline__ void load_rows(const SolveArgs& a, int off, int sz, d
     a.R[p] = W;
     if (z0) z0[i] = W * scale[p];
   }
-}
-
-__global__ void __launch_bounds__(kBlock) solve_large_scc_k(SolveArgs a, LargeComp L, double* zA, double* zB,
-                                                            double* part, HeavyRows hv, HeavyScratch hs) {
-  __shared__ double red[kBlock / 32];
-  const int off = L.off, sz = L.size;
-  const int nlight = sz - hv.nheavy;
-  const int* lorder = a.lorder + off;
-  int lr0 = -1, lr1 = -1;  // this warp's light rows, balanced by cost
-  if (a.lpre) warp_row_range(a.lpre + off, nlight, &lr0, &lr1);
-  // z holds c P / outdeg (a.civ = c / outdeg): the in-edge sum is the next
-  // term itself
-  load_rows(a, off, sz, zA, a.civ);
-  const bool l1 = a.norm == PR_NORM_L1;
-  int k = 0;
-  if (a.R0) {
-    // warm start: R = R0 + r, the series continues from the residual
-    // r = W + c A^T(R0/outdeg) - R0 (in zB, k = 1)
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
-      const int p = off + (int)i;
-      a.R[p] = a.R0[p];
-      zA[i] = a.R0[p] * a.civ[p];
-    }
-    if (!grid_sync(a.ctl, 312)) return;
-    auto fin = [&](int row, double acc, bool) -> double {
-      const double r = a.W[row] + acc - a.R[row];
-      a.R[row] += r;
-      zB[row - off] = r * a.civ[row];
-      return fabs(r);
-    };
-    auto val = [&](int e) -> double { return zA[local_or_err(a, a.int_idx[e] - off, sz)]; };
-    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, 0, l1, fin, val, lr0, lr1);
-    k = 1;
-  }
-  // light rows in SELL-32 slices when the layout has them: this warp's
-  // share of the component's slices, balanced by cost
-  const bool sell = L.sell_end > L.sell_begin;
-  int ls0 = 0, ls1 = 0;
-  if (sell) warp_slice_range(a.sell_cpre + L.sell_begin, L.sell_end - L.sell_begin, &ls0, &ls1);
-  if (sell && blockIdx.x == 0 && threadIdx.x == 0) {
-    zA[sz] = 0.0;  // the slot padded entries read
-    zB[sz] = 0.0;
-  }
-  if (!grid_sync(a.ctl, 310)) return;
-  const double tau = a.norm == PR_NORM_L1 ? a.tol * (double)sz / (double)a.n : a.tol;
-  const int fixed = a.replay ? a.replay[L.c] : -1;
-  for (;;) {
-    const double* cur = (k & 1) ? zB : zA;
-    double* nxt = (k & 1) ? zA : zB;
-    double local = 0.0;
-    auto fin = [&](int row, double acc, bool heavy) -> double {
-      const double pn = acc;
-      a.R[row] += pn;
-      nxt[row - off] = pn * a.civ[row];
-      if (!heavy) local = fold2(local, fabs(pn), l1);
-      return fabs(pn);
-    };
-    auto val = [&](int e) -> double { return cur[local_or_err(a, a.int_idx[e] - off, sz)]; };
-    if (sell) {
-      balanced_sweep(a.int_ptr, lorder, 0, hv, hs, k & 1, l1, fin, val, 0, 0);  // heavy rows only
-      auto sval = [&](int q) -> double { return cur[q]; };  // q <= sz by construction of the slices
-      sell_rows(a.sell_ptr + L.sell_begin, a.sell_idx, ls0, ls1, off, L.nlight, sval, fin);
-    } else {
-      balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, k & 1, l1, fin, val, lr0, lr1);
-    }
-    const double bs = l1 ? block_sum(local, red) : block_max(local, red);
-    double* slot = part + (size_t)(k & 1) * gridDim.x;
-    if (threadIdx.x == 0) slot[blockIdx.x] = bs;
-    if (!grid_sync(a.ctl, 311)) return;
-    double t = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t = fold2(t, __ldcg(&slot[b]), l1);
-    double s = l1 ? block_sum(t, red) : block_max(t, red);
-    if (hv.nheavy > 0) s = fold2(s, __ldcg(&hs.total[k & 1]), l1);
-    k++;
-    if (fixed >= 0) {
-      if (k >= fixed) break;
-      continue;
-    }
-    if (!keep_going(s, tau, a.norm)) break;
-    if (k >= a.max_iter) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
-      break;
-    }
-  }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x)
-    a.zr[off + i] = a.R[off + i] * a.p_inv[off + i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.iters[L.c] = k;
 }
 
 // The grid-wide series in mixed precision (see kMixKappa).  Buffers: fz
@@ -988,7 +901,6 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
         hv.hbase = L.heavy_begin;
         float* fz = reinterpret_cast<float*>(zA);
         float* F = reinterpret_cast<float*>(zB);
-        void* args64[] = {&a, &L, &zA, &zB, &part, &hv, &hs};
         void* args32[] = {&a, &L, &fz, &F, &part, &hv, &hs};
         // external records: inside a captured graph they become event-record
         // nodes, so the events time each replay
@@ -998,15 +910,13 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
         // fixed-point bytes); one that fits runs the exact fixed-point
         // series, which is faster there than the FP32 one
         const bool fx_fits = (int64_t)L.size * kGiantFxRowBytes <= l2_bytes() / 2;
-        if (mixed && !(fx_fits && b.gfx.acc)) {
+        if (mixed && !fx_fits) {
           PRGB_TRY(launch_coop((const void*)solve_large_scc_mx_k, kBlock, 0, s, args32, P->coop_blocks, nullptr));
-        } else if (b.gfx.acc) {
+        } else {
           GiantFxBufs gfx = b.gfx;
           void* argsfx[] = {&a, &L, &gfx, &hv};
           PRGB_CUDA(cudaMemsetAsync(gfx.acc, 0, 4 * sizeof(unsigned long long), s));
           PRGB_TRY(launch_coop((const void*)solve_large_scc_fx_k, kBlock, 0, s, argsfx, P->coop_blocks, nullptr));
-        } else {
-          PRGB_TRY(launch_coop((const void*)solve_large_scc_k, kBlock, 0, s, args64, P->coop_blocks, nullptr));
         }
         if (timing) PRGB_CUDA(record_timing(timing->stop[ti], s));
         ti++;
