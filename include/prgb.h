@@ -155,15 +155,18 @@ typedef struct pr_solve_stats {
                              filled with per-component iteration counts when
                              non-NULL (0 for CACs and 1-vertex components) */
     int32_t timing;       /* in: 1 = time the grid-wide power-series kernels
-                             with CUDA events on the call's stream */
+                             with CUDA events on the call's stream; 2 = also
+                             record an event between the levels (level_ms;
+                             a few microseconds a level) */
     float kernel_ms;      /* out (timing = 1): their summed device time */
     int64_t kernel_bytes; /* out (timing = 1): their algorithmic bytes.
-                             FP64 mode (16-byte fixed-point values): per
+                             The fixed-point series (FP64 mode; mixed
+                             precision where it runs it): per
                              sweep 4 B per edge (index) + 72 B per row (z
                              gather and write, R read and write, c/outdeg),
                              plus 88 B per row once per launch (the start
-                             and the end of the series).  Mixed precision:
-                             per FP64 sweep 4 B per edge + 40 B per row, per
+                             and the end of the series).  The FP32 series
+                             of mixed precision: per FP64 sweep 4 B per edge + 40 B per row, per
                              FP32 sweep 4 B per edge + 24 B per row, plus 56 B
                              per row per launch */
     int64_t kernel_launches; /* out (timing = 1): number of such launches */
@@ -173,10 +176,14 @@ typedef struct pr_solve_stats {
     int64_t fp64_edge_visits; /* PR_PREC_MIXED: edges read by FP64 residual
                                  sweeps (included in edge_visits) */
     float *level_ms;      /* optional caller-owned HOST array [n_levels]; with
-                             timing = 1 (pr_solve only) each level's device
+                             timing = 2 (pr_solve only) each level's device
                              time in walk order (Eq. PR:levels gather through
                              the level's last component), from CUDA events
                              recorded between the levels */
+    int32_t counts_off;   /* in: 1 = leave iters_max, edge_visits, fp64_* and
+                             comp_iters unset: the call then reads back only
+                             what timing needs (the grid-wide components'
+                             sweep counts) */
 } pr_solve_stats;
 
 /*

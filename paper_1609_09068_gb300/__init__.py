@@ -68,7 +68,8 @@ class _Stats(C.Structure):
     _fields_ = [("iters_max", C.c_int32), ("n_levels", C.c_int32), ("edge_visits", C.c_int64),
                 ("launches", C.c_int64), ("comp_iters", C.c_void_p), ("timing", C.c_int32),
                 ("kernel_ms", C.c_float), ("kernel_bytes", C.c_int64), ("kernel_launches", C.c_int64),
-                ("fp64_sweeps_max", C.c_int32), ("fp64_edge_visits", C.c_int64), ("level_ms", C.c_void_p)]
+                ("fp64_sweeps_max", C.c_int32), ("fp64_edge_visits", C.c_int64), ("level_ms", C.c_void_p),
+                ("counts_off", C.c_int32)]
 
 
 class _PartTiming(C.Structure):
@@ -358,7 +359,7 @@ def _stats_dict(st):
 
 def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iters=None,
           with_stats=False, allow_noconv=False, timing=False, precision=PREC_FP64, warm_start=None,
-          lu_threshold=0):
+          lu_threshold=0, level_times=False, counts=True):
     """Sec. 4.3 solve on device tensors; returns R (float64, original order).
 
     ``u`` may be a CUDA tensor or a numpy array (host I/O through the C ABI's
@@ -366,7 +367,11 @@ def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
     runs the SCC series in FP32 with FP64 residual refinement;
     ``warm_start`` (an ``Mpnn``) starts each SCC's series from the network's
     guess; SCCs of fewer than ``lu_threshold`` vertices are solved by dense
-    elimination (Sec. 4.3 item 3)."""
+    elimination (Sec. 4.3 item 3).  ``timing`` times the grid-wide series
+    kernels (stats ``kernel_ms``); ``level_times`` also records an event
+    between the levels (stats ``level_ms``; the events cost a few
+    microseconds a level).  ``counts=False`` skips the per-component sweep
+    counts and edge visits (read back and summed on the host otherwise)."""
     _need_len(u, part.n, "u")
     if replay_iters is not None:
         _need_len(replay_iters, part.n_comp, "replay_iters")
@@ -375,7 +380,9 @@ def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
     o, keep = _opts(norm, max_iter, on_host, replay_iters, precision, warm_start, lu_threshold)
     comp_iters = np.zeros(max(part.n_comp, 1), np.int32)
     level_ms = np.zeros(max(part.n_levels, 1), np.float32)
-    st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data, int(timing), 0.0, 0, 0, 0, 0, level_ms.ctypes.data)
+    tmode = 2 if level_times else (1 if timing else 0)
+    st = _Stats(0, 0, 0, 0, comp_iters.ctypes.data if counts else None, tmode, 0.0, 0, 0, 0, 0,
+                level_ms.ctypes.data, 0 if counts else 1)
     if on_host:
         uh = np.ascontiguousarray(u, dtype=np.float64)
         R = np.empty(part.n, np.float64)
@@ -392,8 +399,10 @@ def solve(part: Partition, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
     del keep
     if with_stats:
         d = _stats_dict(st)
-        d.update(comp_iters=comp_iters[: part.n_comp].copy(), status=rc)
-        if timing:
+        d.update(status=rc)
+        if counts:
+            d.update(comp_iters=comp_iters[: part.n_comp].copy())
+        if level_times:
             d.update(level_ms=level_ms[: part.n_levels].copy())
         return R, d
     return R
@@ -407,7 +416,7 @@ def global_power(g: Graph, c, u, tol, norm=NORM_L1, max_iter=10_000, replay_iter
     on_host = isinstance(u, np.ndarray)
     rep = None if replay_iters is None else [int(replay_iters)]
     o, keep = _opts(norm, max_iter, on_host, rep)
-    st = _Stats(0, 0, 0, 0, None, int(timing), 0.0, 0, 0, 0, 0, None)
+    st = _Stats(0, 0, 0, 0, None, int(timing), 0.0, 0, 0, 0, 0, None, 0)
     if on_host:
         uh = np.ascontiguousarray(u, dtype=np.float64)
         R = np.empty(g.n, np.float64)

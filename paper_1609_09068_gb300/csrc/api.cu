@@ -2,6 +2,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
 #include <new>
 
@@ -325,12 +326,14 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t K = part->n_comp;
   const bool timing = stats && stats->timing;
+  const bool level_events = timing && stats->timing >= 2;
   Arena tmp(s);
   Ctl* ctl = nullptr;
   int32_t* iters = nullptr;
   int32_t* iters64 = nullptr;
   int64_t launches = 0;
   KernelTiming kt_local;
+  kt_local.levels = level_events;
   KernelTiming* kt = &kt_local;
   pr_partition_s* P = const_cast<pr_partition_s*>(part);  // the plan is a cache
   std::unique_lock<std::mutex> lock(P->plan_mu, std::defer_lock);
@@ -338,7 +341,8 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
     // the level loop replayed from the partition's cached CUDA graph
     lock.lock();
     SolvePlan* pl = nullptr;
-    PRGB_TRY(plan_solve(P, c, u, o.io_on_host != 0, tol, o.norm, o.max_iter, mixed, timing, o.warm_start,
+    PRGB_TRY(plan_solve(P, c, u, o.io_on_host != 0, tol, o.norm, o.max_iter, mixed,
+                        timing ? (level_events ? 2 : 1) : 0, o.warm_start,
                         o.lu_threshold, R, o.io_on_host != 0, s, &pl, &launches));
     ctl = pl->ctl;
     iters = pl->iters;
@@ -379,23 +383,37 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
     stats->fp64_sweeps_max = 0;
     stats->fp64_edge_visits = 0;
     if (K > 0) {
+      // per-component sweep counts: all of them, or (counts_off) only the
+      // timed grid-wide components' for the byte count
+      const bool counts = !stats->counts_off;
+      std::map<int32_t, int32_t> hl, hl64;
       int32_t* h = stats->comp_iters;
       std::vector<int32_t> local, h64;
-      if (!h) {
-        local.resize(K);
-        h = local.data();
+      if (counts) {
+        if (!h) {
+          local.resize(K);
+          h = local.data();
+        }
+        PRGB_CUDA(cudaMemcpyAsync(h, iters, (size_t)K * 4, cudaMemcpyDeviceToHost, s));
+        if (mixed) {
+          h64.resize(K);
+          PRGB_CUDA(cudaMemcpyAsync(h64.data(), iters64, (size_t)K * 4, cudaMemcpyDeviceToHost, s));
+        }
+        PRGB_TRY(solve_edge_visits(part, iters, iters64, &stats->edge_visits, &stats->fp64_edge_visits,
+                                   tmp));  // synchronises
+        for (int32_t k = 0; k < K; k++) stats->iters_max = h[k] > stats->iters_max ? h[k] : stats->iters_max;
+        for (int32_t k = 0; k < (int32_t)h64.size(); k++)
+          stats->fp64_sweeps_max = h64[k] > stats->fp64_sweeps_max ? h64[k] : stats->fp64_sweeps_max;
+      } else if (timing) {
+        for (const LargeComp& L : kt->comps) {
+          PRGB_CUDA(cudaMemcpyAsync(&hl[L.c], iters + L.c, 4, cudaMemcpyDeviceToHost, s));
+          if (mixed) PRGB_CUDA(cudaMemcpyAsync(&hl64[L.c], iters64 + L.c, 4, cudaMemcpyDeviceToHost, s));
+        }
+        PRGB_CUDA(cudaStreamSynchronize(s));
       }
-      PRGB_CUDA(cudaMemcpyAsync(h, iters, (size_t)K * 4, cudaMemcpyDeviceToHost, s));
-      if (mixed) {
-        h64.resize(K);
-        PRGB_CUDA(cudaMemcpyAsync(h64.data(), iters64, (size_t)K * 4, cudaMemcpyDeviceToHost, s));
-      }
-      PRGB_TRY(solve_edge_visits(part, iters, iters64, &stats->edge_visits, &stats->fp64_edge_visits,
-                                 tmp));  // synchronises
-      for (int32_t k = 0; k < K; k++) stats->iters_max = h[k] > stats->iters_max ? h[k] : stats->iters_max;
-      for (int32_t k = 0; k < (int32_t)h64.size(); k++)
-        stats->fp64_sweeps_max = h64[k] > stats->fp64_sweeps_max ? h64[k] : stats->fp64_sweeps_max;
-      if (timing && stats->level_ms && kt->level.size() >= part->levels.size() + 1) {
+      auto sweeps = [&](int32_t c) -> int64_t { return counts ? h[c] : hl[c]; };
+      auto sweeps64 = [&](int32_t c) -> int64_t { return counts ? h64[c] : hl64[c]; };
+      if (level_events && stats->level_ms && kt->level.size() >= part->levels.size() + 1) {
         for (size_t li = 0; li < part->levels.size(); li++)
           PRGB_CUDA(cudaEventElapsedTime(&stats->level_ms[li], kt->level[li], kt->level[li + 1]));
       }
@@ -408,8 +426,8 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
           PRGB_CUDA(cudaEventElapsedTime(&ms, kt->start[i], kt->stop[i]));
           stats->kernel_ms += ms;
           const LargeComp& L = kt->comps[i];
-          const int64_t it = h[L.c];
-          if (!mixed) {
+          const int64_t it = sweeps(L.c);
+          if (giant_runs_fx(L, mixed)) {
             // the fixed-point series (16-byte values): per sweep 4 B per
             // edge + 72 B per row (z gather and write, R read and write,
             // c/outdeg); once per launch 88 B per row: the start (W and
@@ -424,7 +442,7 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
           // pointer, 1/outdeg in FP32); once per launch 56 B per row: the
           // start (W, c/outdeg read, R and z written) and the end (R,
           // 1/outdeg read, R/outdeg written)
-          const int64_t it64 = h64[L.c];
+          const int64_t it64 = sweeps64(L.c);
           stats->kernel_bytes += it64 * (4 * (int64_t)L.m_int + 40 * (int64_t)L.size) +
                                  (it - it64) * (4 * (int64_t)L.m_int + 24 * (int64_t)L.size) +
                                  56 * (int64_t)L.size;

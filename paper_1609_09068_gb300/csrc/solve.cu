@@ -835,6 +835,10 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
 // warp classes on the three side streams, joined back into s before the
 // next level.  Only launches, memsets and event records: it can be
 // captured into a CUDA graph.
+bool giant_runs_fx(const LargeComp& L, bool mixed) {
+  return !mixed || (int64_t)L.size * kGiantFxRowBytes <= l2_bytes() / 2;
+}
+
 // A timing event: inside a stream capture an external record, which becomes
 // an event-record node so that the event times each replay; a plain record
 // otherwise.
@@ -866,7 +870,7 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
     NvtxRange nvtx_level("prgb level", (int)li);
     // external records: inside a captured graph they become event-record
     // nodes, so the events time each replay
-    if (timing) PRGB_CUDA(record_timing(timing->level[li], s));
+    if (timing && timing->levels) PRGB_CUDA(record_timing(timing->level[li], s));
     {
       HeavyRows xv;
       xv.rows = P->xheavy_rows + r.xh_begin;
@@ -905,12 +909,7 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
         // external records: inside a captured graph they become event-record
         // nodes, so the events time each replay
         if (timing) PRGB_CUDA(record_timing(timing->start[ti], s));
-        // Mixed precision keeps its FP32 series for an SCC whose sweep
-        // does not fit in L2 (there the 4-byte values move a quarter of the
-        // fixed-point bytes); one that fits runs the exact fixed-point
-        // series, which is faster there than the FP32 one
-        const bool fx_fits = (int64_t)L.size * kGiantFxRowBytes <= l2_bytes() / 2;
-        if (mixed && !fx_fits) {
+        if (!giant_runs_fx(L, mixed)) {
           PRGB_TRY(launch_coop((const void*)solve_large_scc_mx_k, kBlock, 0, s, args32, P->coop_blocks, nullptr));
         } else {
           GiantFxBufs gfx = b.gfx;
@@ -973,7 +972,7 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
       PRGB_CUDA(cudaStreamWaitEvent(s, side.join[q], 0));
     }
   }
-  if (timing && !P->levels.empty())
+  if (timing && timing->levels && !P->levels.empty())
     PRGB_CUDA(record_timing(timing->level[P->levels.size()], s));
   return PR_OK;
 }
@@ -1023,7 +1022,7 @@ SolvePlan::~SolvePlan() {
 // The cached graph for these parameters, or null.  The graphs of the last
 // kPlanGraphs parameter sets are kept (a caller alternating, say, FP64 and
 // mixed solves does not re-capture each time).
-static PlanGraph* plan_find(SolvePlan* pl, double c, double tol, int norm, int max_iter, bool mixed, bool timing,
+static PlanGraph* plan_find(SolvePlan* pl, double c, double tol, int norm, int max_iter, bool mixed, int timing,
                             const pr_mpnn_s* warm, int lu) {
   for (PlanGraph& e : pl->graphs)
     if (e.c == c && e.tol == tol && e.norm == norm && e.max_iter == max_iter && e.mixed == mixed &&
@@ -1036,7 +1035,7 @@ static PlanGraph* plan_find(SolvePlan* pl, double c, double tol, int norm, int m
 
 // The plan's buffers and streams, allocated on first use (and the mixed,
 // warm-start and timing extras when first asked for).
-static pr_status plan_setup(pr_partition_s* P, SolvePlan* pl, bool mixed, bool timing, const pr_mpnn_s* warm) {
+static pr_status plan_setup(pr_partition_s* P, SolvePlan* pl, bool mixed, int timing, const pr_mpnn_s* warm) {
   const int32_t n = P->g.n;
   const int32_t K = P->n_comp;
   if (!pl->keep) {
@@ -1076,6 +1075,7 @@ static pr_status plan_setup(pr_partition_s* P, SolvePlan* pl, bool mixed, bool t
     pl->yhat_uid = 0;
   }
   if (timing) PRGB_TRY(pl->kt.ensure(P));
+  pl->kt.levels = timing >= 2;
   return set_solve_attrs(P, mixed);
 }
 
@@ -1105,7 +1105,7 @@ static pr_status plan_head(SolvePlan* pl, int32_t K, cudaStream_t s, int64_t* nl
 // device still executes work the call enqueued on the others) and cache it,
 // evicting the least recently used graph beyond kPlanGraphs.
 static pr_status plan_capture(pr_partition_s* P, SolvePlan* pl, double c, double tol, int norm, int max_iter,
-                              bool mixed, bool timing, const pr_mpnn_s* warm, int lu) {
+                              bool mixed, int timing, const pr_mpnn_s* warm, int lu) {
   if (pl->graphs.size() >= (size_t)kPlanGraphs) {
     size_t old = 0;
     for (size_t i = 1; i < pl->graphs.size(); i++)
@@ -1153,7 +1153,7 @@ static pr_status plan_capture(pr_partition_s* P, SolvePlan* pl, double c, double
 }
 
 pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_host, double tol, int norm,
-                     int max_iter, bool mixed, bool timing, const pr_mpnn_s* warm, int lu, double* R,
+                     int max_iter, bool mixed, int timing, const pr_mpnn_s* warm, int lu, double* R,
                      bool R_on_host, cudaStream_t s, SolvePlan** out, int64_t* launches) {
   if (!P->plan) {
     P->plan = new (std::nothrow) SolvePlan;

@@ -127,6 +127,7 @@ struct KernelTiming {
   std::vector<cudaEvent_t> start, stop;
   std::vector<LargeComp> comps;
   std::vector<cudaEvent_t> level;  // [n_levels + 1]: each level's start, then the end of the last
+  bool levels = false;             // record the level events too (they cost a few microseconds a level)
   pr_status ensure(const pr_partition_s* P);
   ~KernelTiming();
 };
@@ -174,7 +175,8 @@ struct PlanGraph {
   int64_t nodes = 0;  // kernels per replay
   double c = 0.0, tol = 0.0;
   int norm = 0, max_iter = 0;
-  bool mixed = false, timing = false;
+  bool mixed = false;
+  int timing = 0;  // 0 none, 1 the grid-wide kernels, 2 also the levels
   uint64_t warm_uid = 0;  // the warm-start network's id (0: none)
   int lu = 0;
   unsigned int wait_us = 0;  // the wait limit captured in the graph
@@ -213,6 +215,10 @@ struct SolvePlan {
 // cooperative launch of kBlock-thread blocks.  g.acc must be zero at launch.
 // Its sweep touches about kGiantFxRowBytes per row (z twice, R, z gathered).
 constexpr int64_t kGiantFxRowBytes = 48;
+// Whether grid-wide SCC L runs the fixed-point series: always in FP64 mode;
+// in mixed precision when its sweep fits in half the L2 (there it is faster
+// than the FP32 series, which moves a quarter of the bytes elsewhere)
+bool giant_runs_fx(const LargeComp& L, bool mixed);
 __global__ void solve_large_scc_fx_k(SolveArgs a, LargeComp L, GiantFxBufs g, HeavyRows hv);
 
 // Every component of a level with at most kFxMax vertices (SCCs by the
@@ -244,7 +250,7 @@ pr_status run_solve(const pr_partition_s* P, double c, const double* u, double t
 // has reached them.  warm (may be null): the network that guesses each
 // SCC's start, evaluated per level inside the graph.
 pr_status plan_solve(pr_partition_s* P, double c, const double* u, bool u_on_host, double tol, int norm,
-                     int max_iter, bool mixed, bool timing, const pr_mpnn_s* warm, int lu, double* R,
+                     int max_iter, bool mixed, int timing, const pr_mpnn_s* warm, int lu, double* R,
                      bool R_on_host, cudaStream_t s, SolvePlan** plan, int64_t* launches);
 
 // Autotuner (f-1): move the boundary between the one-CTA and the cluster

@@ -25,10 +25,10 @@ def test_level_times_cover_the_solve(prgb):
     G = prgb.graph(torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.col).cuda())
     P = prgb.partition(G)
     u = torch.from_numpy(g.u).cuda()
-    prgb.solve(P, 0.85, u, 1e-10, timing=True)  # captures the timed graph
+    prgb.solve(P, 0.85, u, 1e-10, level_times=True)  # captures the timed graph
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    R, st = prgb.solve(P, 0.85, u, 1e-10, with_stats=True, timing=True)
+    R, st = prgb.solve(P, 0.85, u, 1e-10, with_stats=True, level_times=True)
     b.record()
     torch.cuda.synchronize()
     lv = st["level_ms"]
@@ -37,10 +37,13 @@ def test_level_times_cover_the_solve(prgb):
     # the levels run back to back inside the call
     assert lv.sum() <= a.elapsed_time(b) * 1.001
     assert lv.sum() >= 0.5 * a.elapsed_time(b)
-    # without timing nothing is reported
+    # without level timing nothing is reported
     R2, st2 = prgb.solve(P, 0.85, u, 1e-10, with_stats=True)
     assert "level_ms" not in st2
     assert torch.equal(R, R2)
+    R3, st3 = prgb.solve(P, 0.85, u, 1e-10, with_stats=True, timing=True)
+    assert "level_ms" not in st3 and st3["kernel_ms"] >= 0
+    assert torch.equal(R, R3)
 
 
 def test_partition_phase_times(prgb):
