@@ -41,7 +41,7 @@ FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the grid-wide SCC kernel, from
 # an ncu capture of the current kernel on that workload (the summary under
 # profiles/ gives the command); None where no capture was taken
-TRAFFIC_BYTES = {"web": 23_820_032 + 1_577_472, "large": 839_220_000_000 + 63_590_000_000}
+TRAFFIC_BYTES = {"web": 23_820_032 + 1_577_472}
 
 WORKLOADS = {
     "web": ("web_like: n=1,000,000, mean out-degree 8, Zipf(2.1) degrees, giant SCC 40%, "
@@ -550,7 +550,8 @@ def config_block(prgb, name, args, flush, local):
         ach = k_bytes / (k_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": TRAFFIC_BYTES.get(name),
-                "kernel": "solve_large_scc_fx_k (grid-wide SCC power series, fixed point)",
+                "kernel": ("solve_large_scc_fxd_k (grid-wide SCC power series, fixed point, z gathered as FP64)"
+                           if name == "large" else "solve_large_scc_fx_k (grid-wide SCC power series, fixed point)"),
                 "peak_kind": f"{peak_kind} copy bandwidth", "kernel_ms_per_step": k_ms,
                 "algorithmic_bytes_per_step": k_bytes}
     out = {

@@ -90,33 +90,33 @@ typedef struct pr_mpnn_s pr_mpnn;
 #define PR_NORM_LINF 1 /* the paper's rule: iterate while max(P) >= tol */
 
 /* Arithmetic of the solve. */
-#define PR_PREC_FP64 0  /* FP64, except that the series of the SCCs of at
-                           most 1,024 vertices and of the SCCs above 16,384
-                           vertices (the grid-wide ones) is summed exactly in
-                           128-bit fixed point (each row's sum and R exact,
-                           each term rounded once to a quantum of about
-                           2^-110 ||W_C||_1, 2^-110 |C| max W_C for the
-                           grid-wide ones), which is at least as accurate */
+#define PR_PREC_FP64 0  /* FP64, except that the SCC series of every
+                           component outside the cluster class (SCCs of at
+                           most 1,024 or more than 16,384 vertices) is summed
+                           exactly in 128-bit fixed point (each row's sum and
+                           R exact, each term rounded once: to a quantum of
+                           about 2^-110 ||W_C||_1, or 2^-110 |C| max W_C for
+                           the grid-wide ones, whose z may be gathered as the
+                           nearest FP64 values), which is at least as
+                           accurate */
 #define PR_PREC_MIXED 1 /* pr_solve only, with PR_NORM_L1 and no replay: the
-                           series of each SCC of 1,025-16,384 vertices, and
-                           of each larger one whose fixed-point sweep would
-                           not fit in half the L2 cache (48 B per vertex),
-                           runs in FP32 (values, z = P/outdeg and
-                           accumulation), then an FP64 residual
-                           r = W + cA^T(R/outdeg) - R of the component is
-                           formed; while ||r||_1 > tol*|C|/n the correction
-                           (I - cA^T)D = r is summed by the same FP32 series
-                           and R += D in FP64.  The other SCCs run the exact
-                           fixed-point series as in PR_PREC_FP64 (faster
-                           there); the inflow gather, CACs and 1-vertex
-                           components stay FP64.  Every SCC ends with a
-                           residual within its budget, so the L1 residual of
-                           R is at most tol (plus FP64 rounding of the
-                           gather) as in FP64 mode; R differs from the FP64
-                           result by at most 2*tol/(1-c) in L1.  PR_ENOCONV
-                           when six corrections do not meet the budget (tol
-                           below ~1e-13 ||R||_1) or max_iter sweeps are
-                           reached. */
+                           series of each SCC of the cluster class
+                           (1,025-16,384 vertices) runs in FP32 (values,
+                           z = P/outdeg and accumulation), then an FP64
+                           residual r = W + cA^T(R/outdeg) - R of the
+                           component is formed; while ||r||_1 > tol*|C|/n
+                           the correction (I - cA^T)D = r is summed by the
+                           same FP32 series and R += D in FP64.  The other
+                           SCCs run the exact fixed-point series as in
+                           PR_PREC_FP64 (faster there on this GPU); the
+                           inflow gather, CACs and 1-vertex components stay
+                           FP64.  Every SCC ends with a residual within its
+                           budget, so the L1 residual of R is at most tol
+                           (plus FP64 rounding of the gather) as in FP64
+                           mode; R differs from the FP64 result by at most
+                           2*tol/(1-c) in L1.  PR_ENOCONV when six
+                           corrections do not meet the budget (tol below
+                           ~1e-13 ||R||_1) or max_iter sweeps are reached. */
 
 typedef struct pr_solve_opts {
     int32_t norm;                /* PR_NORM_L1 (default) or PR_NORM_LINF */
@@ -159,16 +159,14 @@ typedef struct pr_solve_stats {
                              record an event between the levels (level_ms;
                              a few microseconds a level) */
     float kernel_ms;      /* out (timing = 1): their summed device time */
-    int64_t kernel_bytes; /* out (timing = 1): their algorithmic bytes.
-                             The fixed-point series (FP64 mode; mixed
-                             precision where it runs it): per
-                             sweep 4 B per edge (index) + 72 B per row (z
-                             gather and write, R read and write, c/outdeg),
-                             plus 88 B per row once per launch (the start
-                             and the end of the series).  The FP32 series
-                             of mixed precision: per FP64 sweep 4 B per edge + 40 B per row, per
-                             FP32 sweep 4 B per edge + 24 B per row, plus 56 B
-                             per row per launch */
+    int64_t kernel_bytes; /* out (timing = 1): their algorithmic bytes
+                             (the exact fixed-point series): per sweep 4 B
+                             per edge (index) + 72 B per row (z gather and
+                             write, R read and write, c/outdeg), plus 88 B
+                             per row once per launch (the start and the end
+                             of the series); 56 B and 80 B when z is
+                             gathered as FP64 values (an SCC whose sweep does
+                             not fit in half the L2) */
     int64_t kernel_launches; /* out (timing = 1): number of such launches */
     int32_t fp64_sweeps_max; /* PR_PREC_MIXED: the most FP64 residual sweeps
                                 of any SCC (included in iters_max and

@@ -386,7 +386,7 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
       // per-component sweep counts: all of them, or (counts_off) only the
       // timed grid-wide components' for the byte count
       const bool counts = !stats->counts_off;
-      std::map<int32_t, int32_t> hl, hl64;
+      std::map<int32_t, int32_t> hl;
       int32_t* h = stats->comp_iters;
       std::vector<int32_t> local, h64;
       if (counts) {
@@ -405,14 +405,11 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
         for (int32_t k = 0; k < (int32_t)h64.size(); k++)
           stats->fp64_sweeps_max = h64[k] > stats->fp64_sweeps_max ? h64[k] : stats->fp64_sweeps_max;
       } else if (timing) {
-        for (const LargeComp& L : kt->comps) {
+        for (const LargeComp& L : kt->comps)
           PRGB_CUDA(cudaMemcpyAsync(&hl[L.c], iters + L.c, 4, cudaMemcpyDeviceToHost, s));
-          if (mixed) PRGB_CUDA(cudaMemcpyAsync(&hl64[L.c], iters64 + L.c, 4, cudaMemcpyDeviceToHost, s));
-        }
         PRGB_CUDA(cudaStreamSynchronize(s));
       }
       auto sweeps = [&](int32_t c) -> int64_t { return counts ? h[c] : hl[c]; };
-      auto sweeps64 = [&](int32_t c) -> int64_t { return counts ? h64[c] : hl64[c]; };
       if (level_events && stats->level_ms && kt->level.size() >= part->levels.size() + 1) {
         for (size_t li = 0; li < part->levels.size(); li++)
           PRGB_CUDA(cudaEventElapsedTime(&stats->level_ms[li], kt->level[li], kt->level[li + 1]));
@@ -427,25 +424,14 @@ static pr_status pr_solve_body(const pr_partition* part, double c, const double*
           stats->kernel_ms += ms;
           const LargeComp& L = kt->comps[i];
           const int64_t it = sweeps(L.c);
-          if (giant_runs_fx(L, mixed)) {
-            // the fixed-point series (16-byte values): per sweep 4 B per
-            // edge + 72 B per row (z gather and write, R read and write,
-            // c/outdeg); once per launch 88 B per row: the start (W and
-            // c/outdeg read, R and z written) and the end (R and 1/outdeg
-            // read, R and R/outdeg written)
-            stats->kernel_bytes += it * (4 * (int64_t)L.m_int + 72 * (int64_t)L.size) + 88 * (int64_t)L.size;
-            continue;
-          }
-          // mixed precision: FP64 sweeps move 4 B per edge + 40 B per row (z
-          // gather and write, R read and write, c/outdeg), FP32 sweeps 4 B
-          // per edge + 24 B per row (z gather and write, F read/write, row
-          // pointer, 1/outdeg in FP32); once per launch 56 B per row: the
-          // start (W, c/outdeg read, R and z written) and the end (R,
-          // 1/outdeg read, R/outdeg written)
-          const int64_t it64 = sweeps64(L.c);
-          stats->kernel_bytes += it64 * (4 * (int64_t)L.m_int + 40 * (int64_t)L.size) +
-                                 (it - it64) * (4 * (int64_t)L.m_int + 24 * (int64_t)L.size) +
-                                 56 * (int64_t)L.size;
+          // the fixed-point series: per sweep 4 B per edge + per row the z
+          // gather and write (16 B each, or 8 B when z is gathered as FP64
+          // values), R read and write (16 B each) and c/outdeg (8 B); once
+          // per launch: the start (W and c/outdeg read, R and z written) and
+          // the end (R and 1/outdeg read, R and R/outdeg written)
+          const int64_t zb = giant_fits_l2(L) ? 16 : 8;
+          stats->kernel_bytes += it * (4 * (int64_t)L.m_int + (2 * zb + 40) * (int64_t)L.size) +
+                                 (72 + zb) * (int64_t)L.size;
         }
       }
     }

@@ -64,9 +64,28 @@ __device__ __forceinline__ fx128 ld_cg_fx(const fx128* p) {
   return (fx128)((hi << 64) | lo);
 }
 
-__global__ void __launch_bounds__(kBlock) solve_large_scc_fx_k(SolveArgs a, LargeComp L, GiantFxBufs g,
-                                                               HeavyRows hv) {
+// The gathered vector z = P c/outdeg: 16-byte fixed-point words (ZT =
+// fx128) when the sweep fits in L2, else FP64 values (ZT = double, half the
+// bytes of every gather that misses L2), each the fixed-point product
+// rounded to the nearest double and decoded exactly into the row's
+// fixed-point sum.
+template <class ZT>
+__device__ __forceinline__ fx128 z_load(const ZT* z, int q, int F) {
+  if constexpr (sizeof(ZT) == 16) return z[q];
+  else return to_fx(z[q], F);
+}
+template <class ZT>
+__device__ __forceinline__ ZT z_value(fx128 p, FxMul mul, int F) {
+  if constexpr (sizeof(ZT) == 16) return fx_scale(p, mul);
+  else return from_fx(fx_scale(p, mul), F);
+}
+
+template <class ZT>
+__device__ __forceinline__ void giant_fx_body(const SolveArgs& a, const LargeComp& L, const GiantFxBufs& g,
+                                              const HeavyRows& hv) {
   __shared__ unsigned long long sh_acc, sh_val;
+  ZT* const zA = reinterpret_cast<ZT*>(g.zA);
+  ZT* const zB = reinterpret_cast<ZT*>(g.zB);
   const int lane = threadIdx.x & 31;
   const int off = L.off, sz = L.size;
   const int nlight = sz - hv.nheavy;
@@ -94,11 +113,11 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_fx_k(SolveArgs a, Larg
     const int p = off + (int)i;
     const fx128 R = to_fx(warm0 ? a.R0[p] : a.W[p], F);
     g.R[i] = R;
-    g.zA[i] = fx_scale(R, fx_mul_of(a.civ[p]));
+    zA[i] = z_value<ZT>(R, fx_mul_of(a.civ[p]), F);
   }
   if (tid == 0) {
-    g.zA[sz] = 0;
-    g.zB[sz] = 0;
+    zA[sz] = 0;
+    zB[sz] = 0;
   }
   const bool sell = L.sell_end > L.sell_begin;
   int ls0 = 0, ls1 = 0, lr0 = -1, lr1 = -1;
@@ -115,8 +134,8 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_fx_k(SolveArgs a, Larg
     // the first sweep of a warm start forms the residual
     // r = W + c A^T(R0/outdeg) - R0 (signed) and continues from it
     const bool warm = warm0 && k == 0;
-    const fx128* cur = (k & 1) ? g.zB : g.zA;
-    fx128* nxt = (k & 1) ? g.zA : g.zB;
+    const ZT* cur = (k & 1) ? zB : zA;
+    ZT* nxt = (k & 1) ? zA : zB;
     unsigned long long local = 0;
     if (threadIdx.x == 0) {
       sh_acc = 0;
@@ -129,7 +148,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_fx_k(SolveArgs a, Larg
       fx128 R = g.R[i];
       const fx128 pn = warm ? to_fx(a.W[row], F) + acc - R : acc;
       g.R[i] = R + pn;
-      nxt[i] = fx_scale(pn, fx_mul_of(a.civ[row]));
+      nxt[i] = z_value<ZT>(pn, fx_mul_of(a.civ[row]), F);
       return gnorm_q(fx_abs_float(pn, F), qs);
     };
     // heavy rows: a warp per chunk of kChunkH edges; the warp that brings a
@@ -145,7 +164,7 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_fx_k(SolveArgs a, Larg
 #pragma unroll
       for (int kk = 0; kk < kChunkH / 32; kk++) {
         const int e = e0 + kk * 32 + lane;
-        if (e < e1) acc += cur[local_or_err(a, a.int_idx[e] - off, sz)];
+        if (e < e1) acc += z_load(cur, local_or_err(a, a.int_idx[e] - off, sz), F);
       }
       acc = warp_sum_fx(acc);
       const int nch = hv.choff[h + 1] - hv.choff[h];
@@ -183,12 +202,12 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_fx_k(SolveArgs a, Larg
         fx128 a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         int kk = 0;
         for (; kk + 3 < w; kk += 4) {
-          a0 += cur[pp[32 * kk]];
-          a1 += cur[pp[32 * (kk + 1)]];
-          a2 += cur[pp[32 * (kk + 2)]];
-          a3 += cur[pp[32 * (kk + 3)]];
+          a0 += z_load(cur, pp[32 * kk], F);
+          a1 += z_load(cur, pp[32 * (kk + 1)], F);
+          a2 += z_load(cur, pp[32 * (kk + 2)], F);
+          a3 += z_load(cur, pp[32 * (kk + 3)], F);
         }
-        for (; kk < w; kk++) a0 += cur[pp[32 * kk]];
+        for (; kk < w; kk++) a0 += z_load(cur, pp[32 * kk], F);
         const int i = 32 * s + lane;
         if (i < L.nlight) {
           const unsigned long long q = fin(off + i, (a0 + a1) + (a2 + a3));
@@ -203,7 +222,8 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_fx_k(SolveArgs a, Larg
         if (i < le) {
           const int row = lorder[i];
           fx128 acc = 0;
-          for (int e = a.int_ptr[row]; e < a.int_ptr[row + 1]; e++) acc += cur[local_or_err(a, a.int_idx[e] - off, sz)];
+          for (int e = a.int_ptr[row]; e < a.int_ptr[row + 1]; e++)
+            acc += z_load(cur, local_or_err(a, a.int_idx[e] - off, sz), F);
           const unsigned long long q = fin(row, acc);
           local = l1 ? local + q : (q > local ? q : local);
         }
@@ -243,6 +263,16 @@ __global__ void __launch_bounds__(kBlock) solve_large_scc_fx_k(SolveArgs a, Larg
     a.zr[p] = R * a.p_inv[p];
   }
   if (tid == 0) a.iters[L.c] = k;
+}
+
+__global__ void __launch_bounds__(kBlock) solve_large_scc_fx_k(SolveArgs a, LargeComp L, GiantFxBufs g,
+                                                               HeavyRows hv) {
+  giant_fx_body<fx128>(a, L, g, hv);
+}
+
+__global__ void __launch_bounds__(kBlock) solve_large_scc_fxd_k(SolveArgs a, LargeComp L, GiantFxBufs g,
+                                                                HeavyRows hv) {
+  giant_fx_body<double>(a, L, g, hv);
 }
 
 }  // namespace prgb

@@ -475,131 +475,6 @@ __device__ __forceinline__ void load_rows(const SolveArgs& a, int off, int sz, d
   }
 }
 
-// The grid-wide series in mixed precision (see kMixKappa).  Buffers: fz
-// holds the FP32 z pair (2 * size floats), F the FP32 sum of the current
-// pass; a.R the FP64 result so far and a.zr its R/outdeg for the residual.
-__device__ __forceinline__ double grid_fold(const SolveArgs& a, double* part, int slot, double local,
-                                            double* red, int where) {
-  const double bs = block_sum(local, red);
-  double* sl = part + (size_t)slot * gridDim.x;
-  if (threadIdx.x == 0) sl[blockIdx.x] = bs;
-  if (!grid_sync(a.ctl, where)) return -1.0;
-  double t = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&sl[b]);
-  return block_sum(t, red);
-}
-
-__global__ void __launch_bounds__(kBlock) solve_large_scc_mx_k(SolveArgs a, LargeComp L, float* fz, float* F,
-                                                               double* part, HeavyRows hv, HeavyScratch hs) {
-  __shared__ double red[kBlock / 32];
-  const int off = L.off, sz = L.size;
-  const int nlight = sz - hv.nheavy;
-  const int* lorder = a.lorder + off;
-  const double tau = a.tol * (double)sz / (double)a.n;
-  const float cf = (float)a.c;
-  int lr0 = -1, lr1 = -1;  // this warp's light rows, balanced by cost
-  if (a.lpre) warp_row_range(a.lpre + off, nlight, &lr0, &lr1);
-  // the two FP32 z vectors, each with one more slot: the zero that padded
-  // SELL entries read
-  float* const zf0 = fz;
-  float* const zf1 = fz + sz + 1;
-  const bool sell = L.sell_end > L.sell_begin;
-  int ls0 = 0, ls1 = 0;
-  if (sell) warp_slice_range(a.sell_cpre + L.sell_begin, L.sell_end - L.sell_begin, &ls0, &ls1);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    zf0[sz] = 0.0f;
-    zf1[sz] = 0.0f;
-  }
-  double wl = 0.0;
-  const bool warm = a.R0 != nullptr;  // start from the guess's residual
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
-    const int p = off + (int)i;
-    const double W = a.W[p];
-    F[i] = warm ? 0.0f : (float)W;
-    zf0[i] = (float)(W * a.p_inv[p]);
-    a.R[p] = warm ? a.R0[p] : 0.0;
-    wl += W;
-  }
-  const double wsum = grid_fold(a, part, 0, wl, red, 330);
-  if (wsum < 0.0) return;
-  float thr = (float)fmax(tau, (double)kMixKappa * wsum);
-  int k = 0, k64 = 0, zc = 0, slot = 1, rounds = 0;
-  bool skip = warm;
-  for (;;) {
-    bool stop = false;
-    for (; !skip;) {
-      const float* cur = zc ? zf1 : zf0;
-      float* nxt = zc ? zf0 : zf1;
-      double local = 0.0;
-      auto fin = [&](int row, float acc, bool heavy) -> double {
-        const float pn = cf * acc;
-        F[row - off] += pn;
-        nxt[row - off] = pn * a.p_invf[row];
-        if (!heavy) local += (double)fabsf(pn);
-        return (double)fabsf(pn);
-      };
-      auto val = [&](int e) -> float { return cur[local_or_err(a, a.int_idx[e] - off, sz)]; };
-      if (sell) {
-        balanced_sweep(a.int_ptr, lorder, 0, hv, hs, slot & 1, true, fin, val, 0, 0);  // heavy rows only
-        auto sval = [&](int q) -> float { return cur[q]; };  // q <= sz by construction of the slices
-        sell_rows(a.sell_ptr + L.sell_begin, a.sell_idx, ls0, ls1, off, L.nlight, sval, fin);
-      } else {
-        balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, slot & 1, true, fin, val, lr0, lr1);
-      }
-      double s = grid_fold(a, part, slot & 1, local, red, 331);
-      if (s < 0.0) return;
-      if (hv.nheavy > 0) s += __ldcg(&hs.total[slot & 1]);
-      slot++;
-      k++;
-      zc ^= 1;
-      if (s <= (double)thr) break;
-      if (k >= a.max_iter) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
-        stop = true;
-        break;
-      }
-    }
-    skip = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sz;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      const int p = off + (int)i;
-      const double R = a.R[p] + (double)F[i];
-      a.R[p] = R;
-      a.zr[p] = R * a.p_inv[p];
-    }
-    if (stop) break;
-    if (!grid_sync(a.ctl, 332)) return;
-    // FP64 residual; r starts the next correction pass
-    float* cur = zc ? zf1 : zf0;
-    double local = 0.0;
-    auto fin = [&](int row, double acc, bool heavy) -> double {
-      const double r = a.W[row] + a.c * acc - a.R[row];
-      F[row - off] = (float)r;
-      cur[row - off] = (float)(r * a.p_inv[row]);
-      if (!heavy) local += fabs(r);
-      return fabs(r);
-    };
-    auto val = [&](int e) -> double { return a.zr[a.int_idx[e]]; };
-    balanced_sweep(a.int_ptr, lorder, nlight, hv, hs, slot & 1, true, fin, val, lr0, lr1);
-    double rho = grid_fold(a, part, slot & 1, local, red, 333);
-    if (rho < 0.0) return;
-    if (hv.nheavy > 0) rho += __ldcg(&hs.total[slot & 1]);
-    slot++;
-    k++;
-    k64++;
-    if (rho <= tau) break;
-    if (++rounds >= kMixRounds || k >= a.max_iter) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->flags[0], 1);
-      break;
-    }
-    thr = fmaxf(0.5f * (float)tau, kMixKappa * (float)rho);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.iters[L.c] = k;
-    a.iters64[L.c] = k64;
-  }
-}
-
 __global__ void __launch_bounds__(kBlock) solve_large_cac_k(SolveArgs a, LargeComp L) {
   load_rows(a, L.off, L.size, nullptr, nullptr);  // R[p] = W
   if (!grid_sync(a.ctl, 320)) return;
@@ -663,11 +538,6 @@ __global__ void scale_k(int32_t n, double c, const double* __restrict__ x, doubl
     y[i] = c * x[i];
 }
 
-__global__ void to_float_k(int32_t n, const double* __restrict__ x, float* __restrict__ y) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = (float)x[i];
-}
-
 pr_status SideStreams::create() {
   for (int q = 0; q < kSideStreams; q++) {
     PRGB_CUDA(cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking));
@@ -728,12 +598,9 @@ pr_status alloc_solve_bufs(const pr_partition_s* P, bool mixed, Arena& a, SolveB
   PRGB_TRY(alloc_heavy_scratch(&b->hs, std::max(P->max_heavy, P->max_xheavy), std::max(P->max_chunks, P->max_xchunks),
                                a));
   if (P->max_large > 0) {
-    // one slot more: the zero that padded SELL entries read
-    PRGB_TRY(a.alloc(&b->zA, (size_t)P->max_large + 1));
-    PRGB_TRY(a.alloc(&b->zB, (size_t)P->max_large + 1));
-    PRGB_TRY(a.alloc(&b->part, (size_t)2 * num_sms() * 8));
     PRGB_TRY(a.alloc(&b->civ, (size_t)n + 1));
     {
+      // one z slot more: the zero that padded SELL entries read
       GiantFxBufs& g = b->gfx;
       PRGB_TRY(a.alloc(&g.zA, (size_t)P->max_large + 1));
       PRGB_TRY(a.alloc(&g.zB, (size_t)P->max_large + 1));
@@ -743,13 +610,6 @@ pr_status alloc_solve_bufs(const pr_partition_s* P, bool mixed, Arena& a, SolveB
       PRGB_TRY(a.alloc(&g.acc, 4));
       PRGB_CUDA(cudaMemsetAsync(g.cnt, 0, ((size_t)P->max_heavy + 1) * 4, s));
     }
-  }
-  b->invf = nullptr;
-  if (mixed && n > 0) {
-    PRGB_TRY(a.alloc(&b->invf, n));
-    to_float_k<<<grid_cap((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, P->p_inv, b->invf);
-    PRGB_LAUNCH();
-    ++*nl;
   }
   return set_solve_attrs(P, mixed);
 }
@@ -809,7 +669,6 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
   a.c_type = P->c_type;
   a.replay = replay;
   a.xlorder = P->xlorder;
-  a.p_invf = b.invf;
   a.civ = b.civ;
   a.sell_ptr = P->sell_ptr;
   a.sell_idx = P->sell_idx;
@@ -835,9 +694,7 @@ SolveArgs make_solve_args(const pr_partition_s* P, double c, const double* u, do
 // warp classes on the three side streams, joined back into s before the
 // next level.  Only launches, memsets and event records: it can be
 // captured into a CUDA graph.
-bool giant_runs_fx(const LargeComp& L, bool mixed) {
-  return !mixed || (int64_t)L.size * kGiantFxRowBytes <= l2_bytes() / 2;
-}
+bool giant_fits_l2(const LargeComp& L) { return (int64_t)L.size * kGiantFxRowBytes <= l2_bytes() / 2; }
 
 // A timing event: inside a stream capture an external record, which becomes
 // an event-record node so that the event times each replay; a plain record
@@ -853,9 +710,6 @@ static cudaError_t record_timing(cudaEvent_t e, cudaStream_t s) {
 pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& b, bool mixed, SideStreams& side,
                          cudaStream_t s, KernelTiming* timing, int64_t* nl, const float* yhat = nullptr) {
   Ctl* ctl = a.ctl;
-  double* zA = b.zA;
-  double* zB = b.zB;
-  double* part = b.part;
   HeavyScratch hs = b.hs;
   size_t li_large = 0, ti = 0;
   PRGB_CUDA(cudaMemsetAsync(b.lvl_ctr, 0, (4 * P->levels.size() + 4) * sizeof(int32_t), s));
@@ -903,20 +757,18 @@ pr_status enqueue_levels(const pr_partition_s* P, SolveArgs a, const SolveBufs& 
         hv.nchunks = L.chunk_end - L.chunk_begin;
         hv.cbase = L.chunk_begin;
         hv.hbase = L.heavy_begin;
-        float* fz = reinterpret_cast<float*>(zA);
-        float* F = reinterpret_cast<float*>(zB);
-        void* args32[] = {&a, &L, &fz, &F, &part, &hv, &hs};
         // external records: inside a captured graph they become event-record
         // nodes, so the events time each replay
         if (timing) PRGB_CUDA(record_timing(timing->start[ti], s));
-        if (!giant_runs_fx(L, mixed)) {
-          PRGB_TRY(launch_coop((const void*)solve_large_scc_mx_k, kBlock, 0, s, args32, P->coop_blocks, nullptr));
-        } else {
-          GiantFxBufs gfx = b.gfx;
-          void* argsfx[] = {&a, &L, &gfx, &hv};
-          PRGB_CUDA(cudaMemsetAsync(gfx.acc, 0, 4 * sizeof(unsigned long long), s));
-          PRGB_TRY(launch_coop((const void*)solve_large_scc_fx_k, kBlock, 0, s, argsfx, P->coop_blocks, nullptr));
-        }
+        // the exact fixed-point series in both precision modes: on GB300 it
+        // beat the FP32 series with FP64 refinement at every size measured
+        // (web_like's 400k-vertex giant 1.9 against 3.0 ms, the 50M graph's
+        // 25M-vertex one 243 against 261 ms per solve)
+        GiantFxBufs gfx = b.gfx;
+        void* argsfx[] = {&a, &L, &gfx, &hv};
+        PRGB_CUDA(cudaMemsetAsync(gfx.acc, 0, 4 * sizeof(unsigned long long), s));
+        const void* kfx = giant_fits_l2(L) ? (const void*)solve_large_scc_fx_k : (const void*)solve_large_scc_fxd_k;
+        PRGB_TRY(launch_coop(kfx, kBlock, 0, s, argsfx, P->coop_blocks, nullptr));
         if (timing) PRGB_CUDA(record_timing(timing->stop[ti], s));
         ti++;
       } else {
@@ -1050,18 +902,8 @@ static pr_status plan_setup(pr_partition_s* P, SolvePlan* pl, bool mixed, int ti
     PRGB_TRY(pl->keep->alloc(&pl->iters64, (size_t)K + 1));
     PRGB_TRY(pl->keep->alloc(&pl->u, (size_t)n + 1));
     PRGB_TRY(pl->keep->alloc(&pl->Rout, (size_t)n + 1));
-    pl->have_mixed_bufs = false;
     int64_t nl = 0;
     PRGB_TRY(alloc_solve_bufs(P, false, *pl->keep, &pl->b, &nl));
-    PRGB_CUDA(cudaStreamSynchronize(P->stream));
-  }
-  if (mixed && !pl->have_mixed_bufs) {
-    // a second set only for its FP32 1/outdeg and the mixed kernels' limits
-    int64_t nl = 0;
-    SolveBufs mb;
-    PRGB_TRY(alloc_solve_bufs(P, true, *pl->keep, &mb, &nl));
-    pl->b.invf = mb.invf;
-    pl->have_mixed_bufs = true;
     PRGB_CUDA(cudaStreamSynchronize(P->stream));
   }
   if (warm) PRGB_TRY(mpnn_prepare());

@@ -30,7 +30,6 @@ struct SolveArgs {
   const uint8_t* c_type;
   const int32_t* replay;    // [K] fixed iteration counts, or nullptr
   const int32_t* xlorder;   // [n] positions by (level, external in-degree class)
-  const float* p_invf;      // [n] 1/outdeg in FP32 (mixed precision only)
   const double* R0;         // [n] warm-start guess by position for SCC rows, or nullptr
   const float* yhat;        // [n] the network's log-amplification by position: the level kernel forms its
                             //   own guess from it (FP64 warm start), or nullptr
@@ -159,10 +158,6 @@ struct SolveBufs {
   double* zr = nullptr;
   double* W = nullptr;
   HeavyScratch hs;
-  double* zA = nullptr;
-  double* zB = nullptr;
-  double* part = nullptr;
-  float* invf = nullptr;
   double* civ = nullptr;  // c / outdeg (when there are grid-wide components)
   int32_t* lvl_ctr = nullptr;  // [4 * levels] claim counters of the level kernels
   GiantFxBufs gfx;             // FP64 mode's grid-wide SCC series (when there are grid-wide SCCs)
@@ -198,7 +193,6 @@ struct SolvePlan {
   cudaEvent_t done = nullptr;
   std::vector<PlanGraph> graphs;
   uint64_t uses = 0;
-  bool have_mixed_bufs = false;
   Ctl* ctl = nullptr;
   int32_t* iters = nullptr;
   int32_t* iters64 = nullptr;
@@ -215,11 +209,13 @@ struct SolvePlan {
 // cooperative launch of kBlock-thread blocks.  g.acc must be zero at launch.
 // Its sweep touches about kGiantFxRowBytes per row (z twice, R, z gathered).
 constexpr int64_t kGiantFxRowBytes = 48;
-// Whether grid-wide SCC L runs the fixed-point series: always in FP64 mode;
-// in mixed precision when its sweep fits in half the L2 (there it is faster
-// than the FP32 series, which moves a quarter of the bytes elsewhere)
-bool giant_runs_fx(const LargeComp& L, bool mixed);
+// Whether its fixed-point sweep fits in half the L2 (else z is gathered as
+// FP64 values)
+bool giant_fits_l2(const LargeComp& L);
 __global__ void solve_large_scc_fx_k(SolveArgs a, LargeComp L, GiantFxBufs g, HeavyRows hv);
+// the same with z gathered as FP64 values (for an SCC whose 16-byte sweep
+// does not fit in L2)
+__global__ void solve_large_scc_fxd_k(SolveArgs a, LargeComp L, GiantFxBufs g, HeavyRows hv);
 
 // Every component of a level with at most kFxMax vertices (SCCs by the
 // exact fixed-point series, CACs by one FP64 pass) in one persistent launch

@@ -10,9 +10,8 @@
 
 namespace prgb {
 
-// Mixed precision (the SCC series of the cluster class, and of grid-wide
-// SCCs whose fixed-point sweep would not fit in half the L2; the gather,
-// CACs and 1-vertex components stay FP64, and the other SCCs run the exact
+// Mixed precision (the SCC series of the cluster class; the gather, CACs
+// and 1-vertex components stay FP64, and the other SCCs run the exact
 // fixed-point series in either mode).  Per SCC C with budget
 // tau = tol*|C|/n:
 //   1. the series P_0 = W, P_{k+1} = c A^T P_k, F = sum P_k in FP32 values

@@ -1,7 +1,6 @@
 """Mixed precision (FP32 SCC series with FP64 residual refinement for the
-SCCs of the cluster class, 1,025-16,384 vertices, and for grid-wide SCCs whose
-sweep does not fit in half the L2; the others run the exact fixed-point
-series as in FP64 mode) against the FP64 oracle.
+SCCs of the cluster class, 1,025-16,384 vertices; the others run the exact
+fixed-point series as in FP64 mode) against the FP64 oracle.
 
 The FP32 iterates differ from the FP64 ones, so there is no element-wise
 1e-12 comparison.  What pins the result instead (the solution of
@@ -61,9 +60,7 @@ def check_mixed(prgb, g, tol=1e-10, max_rel_bound=1e-6):
     sizes = np.bincount(q.comp, minlength=q.n_comp)
     ctype = np.zeros(q.n_comp, np.int64)
     ctype[q.comp] = q.type
-    l2 = torch.cuda.get_device_properties(0).L2_cache_size
-    scc = ctype == 1
-    fp32 = (scc & (sizes > 1024) & (sizes <= 16384)) | (scc & (sizes > 16384) & (sizes * 48 > l2 // 2))
+    fp32 = (ctype == 1) & (sizes > 1024) & (sizes <= 16384)
     if np.any(fp32):
         # FP32 series refined by FP64 residual sweeps
         assert st["fp64_sweeps_max"] >= 1
