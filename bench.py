@@ -41,7 +41,7 @@ FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one launch of the grid-wide SCC kernel, from
 # an ncu capture of the current kernel on that workload (the summary under
 # profiles/ gives the command); None where no capture was taken
-TRAFFIC_BYTES = {"web": 23_820_032 + 1_577_472}
+TRAFFIC_BYTES = {"web": 23_820_032 + 1_577_472, "large": 572_180_000_000 + 47_880_000_000}
 
 WORKLOADS = {
     "web": ("web_like: n=1,000,000, mean out-degree 8, Zipf(2.1) degrees, giant SCC 40%, "
