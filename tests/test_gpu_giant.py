@@ -74,3 +74,34 @@ def test_grid_wide_without_slices(prgb):
     assert prgb.residual_l1(G, C, u, R) <= C * tol * (1 + 1e-6) + floor
     Rg, _ = prgb.global_power(G, C, u, tol)
     assert float((R - Rg).abs().sum().item()) <= 4 * tol / (1 - C) + 2 * floor / (1 - C)
+
+
+def test_grid_wide_fp64_gathers(prgb):
+    """A giant SCC whose fixed-point sweep does not fit in half the L2 (48 B
+    per vertex) but still has SELL slices: z is gathered as FP64 values and
+    decoded into the exact sums.  Against the oracle with the GPU's sweep
+    counts replayed (1e-12 per entry); by its own rule against the residual
+    bound and the global power series."""
+    import torch
+    rng = np.random.default_rng(17)
+    n, d = 1_600_000, 3
+    src = np.repeat(np.arange(n), d)
+    dst = rng.integers(0, n, d * n)
+    rp, col = gg.csr_from_edges(n, src, dst)
+    G = prgb.graph(rp, col)
+    P = prgb.partition(G)
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    assert P.n_scc_vertices * 48 > l2 // 2  # the giant gathers FP64 values
+    q = oracle.partition(rp, col)
+    u = np.full(n, 1.0 / n)
+    ud = torch.from_numpy(u).cuda()
+    tol = 1e-10
+    R, st = prgb.solve(P, C, ud, tol, with_stats=True)
+    R = R.cpu().numpy()
+    its = st["comp_iters"]
+    Ro, _ = oracle.solve_cw(rp, col, q, C, u, tol, replay_iters=its)
+    assert np.max(np.abs(R - Ro) / np.maximum(np.abs(Ro), 1e-300)) <= RTOL
+    floor = 8 * 2.2e-16 * (1.0 + 2 * R.sum())
+    assert prgb.residual_l1(G, C, ud, torch.from_numpy(R).cuda()) <= C * tol * (1 + 1e-6) + floor
+    Rg, _ = prgb.global_power(G, C, ud, tol)
+    assert float(np.abs(R - Rg.cpu().numpy()).sum()) <= 4 * tol / (1 - C) + 2 * floor / (1 - C)
