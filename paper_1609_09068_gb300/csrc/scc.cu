@@ -119,9 +119,10 @@ struct PropK {
   }
 };
 
-__global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
-                            const int32_t* __restrict__ rep, const int32_t* __restrict__ pin, int32_t* sig,
-                            int32_t* stamp, int* fav, int* fac, int* fbv, int* fbc, int cap, Ctl* ctl) {
+// first frontier of a propagation: every live vertex with out-edges, its
+// own id as its label
+__device__ __forceinline__ void prop_init(const int32_t* __restrict__ ptr, int32_t n, const int32_t* __restrict__ rep,
+                                          int32_t* sig, int32_t* stamp, int* fav, int* fac, int cap, Ctl* ctl) {
   const int lane = threadIdx.x & 31;
   const int gw = gwarp(), nw = nwarps();
   for (int64_t vb = (int64_t)gw * 32; vb < n; vb += (int64_t)nw * 32) {
@@ -130,7 +131,7 @@ __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __re
     int nch = 0;
     if (v < n) {
       stamp[v] = -1;
-      // a settled vertex's colour is -1: it matches no root in root_bfs_k
+      // a settled vertex's colour is -1: it matches no root in the search
       const bool live = rep[v] < 0;
       sig[v] = live ? (int32_t)v : -1;
       if (live) {
@@ -140,9 +141,6 @@ __global__ void propagate_k(const int32_t* __restrict__ ptr, const int32_t* __re
     }
     warp_push(want, (int)v, nch, fav, fac, &ctl->cnt[0], cap, ctl);
   }
-  const Frontier f{fav, fac, fbv, fbc, cap};
-  PropK k{ptr, idx, pin, sig, stamp};
-  run_waves(ctl, f, 111, kWaveProp, k);
 }
 
 // ---- backward search from every colour root --------------------------------
@@ -168,9 +166,10 @@ struct RootBfsK {
   }
 };
 
-__global__ void root_bfs_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
-                           const int32_t* __restrict__ rep, const int32_t* __restrict__ color, int32_t* mark,
-                           int tag, int* fav, int* fac, int* fbv, int* fbc, int cap, Ctl* ctl) {
+// first frontier of the backward search: the roots (colour(r) == r)
+__device__ __forceinline__ void root_init(const int32_t* __restrict__ ptr, int32_t n, const int32_t* __restrict__ rep,
+                                          const int32_t* __restrict__ color, int32_t* mark, int tag, int* fav,
+                                          int* fac, int cap, Ctl* ctl) {
   const int lane = threadIdx.x & 31;
   const int gw = gwarp(), nw = nwarps();
   for (int64_t vb = (int64_t)gw * 32; vb < n; vb += (int64_t)nw * 32) {
@@ -184,14 +183,13 @@ __global__ void root_bfs_k(const int32_t* __restrict__ ptr, const int32_t* __res
     }
     warp_push(want, (int)v, nch, fav, fac, &ctl->cnt[0], cap, ctl);
   }
-  const Frontier f{fav, fac, fbv, fbc, cap};
-  RootBfsK k{ptr, idx, color, mark, tag};
-  run_waves(ctl, f, 131, kWaveRoot, k);
 }
 
-// settle what the search reached; the colours become the next pieces
-__global__ void assign_color_k(int32_t n, int32_t* rep, int32_t* pin, const int32_t* color, const int32_t* mark,
-                               int tag, Ctl* ctl) {
+// settle what the search reached (its colour's largest id is the SCC's
+// representative); the colours become the next pieces; the vertices left
+// are counted into *left
+__device__ __forceinline__ void assign_color(int32_t n, int32_t* rep, int32_t* pin, const int32_t* color,
+                                             const int32_t* mark, int tag, int* left_ctr) {
   int left = 0;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     if (rep[v] >= 0) continue;
@@ -204,7 +202,51 @@ __global__ void assign_color_k(int32_t n, int32_t* rep, int32_t* pin, const int3
     }
   }
   left = __reduce_add_sync(0xffffffffu, left);
-  if ((threadIdx.x & 31) == 0 && left) atomicAdd(&ctl->cnt[7], left);
+  if ((threadIdx.x & 31) == 0 && left) atomicAdd(left_ctr, left);
+}
+
+// Between two phases of the fused colouring kernel: every block has left
+// the previous phase's waves before block 0 clears the frontier counters
+// (and the vertex counter of the next round), and the next phase pushes
+// only after that.
+__device__ __forceinline__ bool phase_reset(Ctl* ctl, int where, int next_left) {
+  if (!grid_sync(ctl, where)) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->cnt[0] = 0;
+    ctl->cnt[1] = 0;
+    ctl->cnt[2] = 0;
+    if (next_left >= 0) ctl->cnt[next_left] = 0;
+  }
+  return grid_sync(ctl, where + 1);
+}
+
+// All colouring rounds in one cooperative launch: per round the forward
+// label propagation, the backward search from the roots and the settling
+// pass, separated by grid barriers instead of host round trips.  Round r
+// counts the vertices still unsettled into cnt[6 + (r & 1)] (the other slot
+// is cleared for the next round after every block has read it); the
+// number of rounds run goes to cnt[5].
+__global__ void colour_k(const int32_t* __restrict__ optr, const int32_t* __restrict__ oidx,
+                         const int32_t* __restrict__ iptr, const int32_t* __restrict__ iidx, int32_t n, int32_t* rep,
+                         int32_t* pin, int32_t* sig, int32_t* stamp, int32_t* mark, int* fav, int* fac, int* fbv,
+                         int* fbc, int cap, Ctl* ctl) {
+  const Frontier f{fav, fac, fbv, fbc, cap};
+  for (int round = 0; round < 20000; round++) {
+    const int tag = round + 1;
+    const int slot = 6 + (round & 1);
+    prop_init(optr, n, rep, sig, stamp, fav, fac, cap, ctl);
+    if (!run_waves(ctl, f, 111, kWaveProp, PropK{optr, oidx, pin, sig, stamp})) return;
+    if (!phase_reset(ctl, 141, 6 + ((round + 1) & 1))) return;
+    root_init(iptr, n, rep, sig, mark, tag, fav, fac, cap, ctl);
+    if (!run_waves(ctl, f, 131, kWaveRoot, RootBfsK{iptr, iidx, sig, mark, tag})) return;
+    assign_color(n, rep, pin, sig, mark, tag, &ctl->cnt[slot]);
+    if (!phase_reset(ctl, 151, -1)) return;
+    if (vload(&ctl->cnt[slot]) == 0) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[5] = round + 1;
+      return;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) set_err(ctl, PR_EINTERNAL, 160);
 }
 
 // ---- FW-BW for the largest SCC ---------------------------------------------
@@ -372,36 +414,21 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl, cuda
   int32_t* mark;
   PRGB_TRY(tmp.alloc(&mark, n));
   PRGB_CUDA(cudaMemsetAsync(mark, 0, (size_t)n * 4, s));
-  for (int round = 0; round < 20000; round++) {
-    const int32_t nn = n;
+  {
+    PRGB_TRY(reset_ctl(ctl, s));
+    int32_t nn = n;
     int cp = cap;
-    int tag = round + 1;
-    {
-      PRGB_TRY(reset_ctl(ctl, s));
-      const int32_t* ptr = g.optr;
-      const int32_t* idx = g.oidx;
-      void* args[] = {&ptr, &idx, (void*)&nn, &rep, &pin, &sin, &stamp, &fav, &fac, &fbv, &fbc, &cp, &ctl};
-      PRGB_TRY(launch_coop((const void*)propagate_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
-    }
-    {
-      PRGB_TRY(reset_ctl(ctl, s));
-      const int32_t* ptr = g.iptr;
-      const int32_t* idx = g.iidx;
-      void* args[] = {&ptr, &idx, (void*)&nn, &rep, &sin, &mark, &tag, &fav, &fac, &fbv, &fbc, &cp, &ctl};
-      PRGB_TRY(launch_coop((const void*)root_bfs_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
-    }
-    PRGB_CUDA(cudaMemsetAsync(&ctl->cnt[7], 0, sizeof(int), s));
-    assign_color_k<<<grid_n(n), kBlock, 0, s>>>(n, rep, pin, sin, mark, tag, ctl);
-    PRGB_LAUNCH();
-    int h[2] = {0, 0};
-    PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PRGB_CUDA(cudaMemcpyAsync(&h[1], &ctl->cnt[7], sizeof(int), cudaMemcpyDeviceToHost, s));
-    PRGB_CUDA(cudaStreamSynchronize(s));
-    if (rounds) *rounds = round + 1;
-    if (h[0]) return (pr_status)h[0];
-    if (h[1] == 0) return PR_OK;
+    DevGraph gg = g;
+    void* args[] = {&gg.optr, &gg.oidx, &gg.iptr, &gg.iidx, &nn, &rep, &pin, &sin, &stamp, &mark,
+                    &fav, &fac, &fbv, &fbc, &cp, &ctl};
+    PRGB_TRY(launch_coop((const void*)colour_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
   }
-  return PR_EINTERNAL;
+  int h[2] = {0, 0};
+  PRGB_CUDA(cudaMemcpyAsync(&h[0], &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaMemcpyAsync(&h[1], &ctl->cnt[5], sizeof(int), cudaMemcpyDeviceToHost, s));
+  PRGB_CUDA(cudaStreamSynchronize(s));
+  if (rounds) *rounds = h[1];
+  return (pr_status)h[0];
 }
 
 }  // namespace prgb
