@@ -375,9 +375,9 @@ pr_status levels_and_merge(const DevGraph& g, const int32_t* rep, int32_t* crep,
     PRGB_LAUNCH();
   }
   PRGB_TRY(scan_i32(cin_cnt, cin_ptr, n, tmp));
-  int32_t m_ext = 0;
-  PRGB_CUDA(cudaMemcpyAsync(&m_ext, cin_ptr + n, 4, cudaMemcpyDeviceToHost, s));
-  PRGB_CUDA(cudaStreamSynchronize(s));
+  // the condensation's edges number at most the graph's: sized by that
+  // bound, the lists need no round trip for their exact count
+  const int64_t m_ext = g.m;
   PRGB_TRY(tmp.alloc(&cin_src, (size_t)(m_ext > 0 ? m_ext : 1)));
   PRGB_CUDA(cudaMemcpyAsync(cursor, cin_ptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToDevice, s));
   fill_cin_k<<<grid_t(n), kBlock, 0, s>>>(g.optr, g.oidx, n, nullptr, nullptr, nullptr, rep, cursor, cin_src);

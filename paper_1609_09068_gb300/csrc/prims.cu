@@ -404,13 +404,14 @@ pr_status build_heavy(const int32_t* ptr, int32_t nrows, Arena& keep, Arena& tmp
     heavy_fill_k<<<grid_for(nrows), kBlock, 0, s>>>(nrows, flag, hidx, cho_all, *rows, *choff);
     PRGB_LAUNCH();
   }
+  // a copy from pageable host memory has read its source when the call
+  // returns, so h may go out of scope without a synchronisation
   PRGB_CUDA(cudaMemcpyAsync(*choff + h[0], &h[1], 4, cudaMemcpyHostToDevice, s));
   PRGB_TRY(keep.alloc(chrow, (size_t)h[1] + 1));
   if (h[0] > 0) {
     heavy_chrow_k<<<grid_for(h[0]), kBlock, 0, s>>>(h[0], *choff, *chrow);
     PRGB_LAUNCH();
   }
-  PRGB_CUDA(cudaStreamSynchronize(s));
   return PR_OK;
 }
 

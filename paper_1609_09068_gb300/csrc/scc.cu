@@ -295,12 +295,16 @@ struct ReachK {
 // vertex reached along (ptr, idx); when need is set, only vertices with
 // need[v] == tag_need are entered (the backward pass stays inside the
 // forward set).
-__global__ void reach_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n, int pivot,
+__global__ void reach_k(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
+                        const unsigned long long* __restrict__ best,
                         const int32_t* __restrict__ rep, int32_t* mark, int tag, const int32_t* __restrict__ need,
                         int tag_need, int* fav, int* fac, int* fbv, int* fbc, int cap, Ctl* ctl) {
   const int lane = threadIdx.x & 31;
   const int gw = gwarp(), nw = nwarps();
-  if (gw == 0) {
+  // the pivot (pivot_k's key: its low word; none when the key is 0)
+  const unsigned long long key = *best;
+  const int pivot = (int)(uint32_t)(key & 0xffffffffu);
+  if (gw == 0 && key != 0 && pivot < n) {
     const int nch = nchunks_of(ptr[pivot + 1] - ptr[pivot]);
     if (lane == 0) mark[pivot] = tag;
     warp_push(lane == 0 && nch > 0, pivot, nch, fav, fac, &ctl->cnt[0], cap, ctl);
@@ -386,11 +390,9 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl, cuda
     PRGB_CUDA(cudaMemsetAsync(bw, 0, (size_t)n * 4, s));
     pivot_k<<<grid_n(n), kBlock, 0, s>>>(g.optr, g.iptr, n, rep, best);
     PRGB_LAUNCH();
-    unsigned long long hb = 0;
-    PRGB_CUDA(cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, s));
-    PRGB_CUDA(cudaStreamSynchronize(s));
-    if (hb != 0) {
-      int pv = (int)(uint32_t)(hb & 0xffffffffu);
+    // the searches read the pivot on the device (none: they visit nothing
+    // and every vertex keeps its piece), so no round trip is needed
+    {
       int32_t nn = n;
       int cp = cap;
       for (int dir = 0; dir < 2; dir++) {
@@ -401,7 +403,8 @@ pr_status scc_detect(const DevGraph& g, int32_t* rep, Arena& tmp, Ctl* ctl, cuda
         int tag = dir == 0 ? 1 : 2;
         const int32_t* need = dir == 0 ? nullptr : fw;
         int tag_need = 1;
-        void* args[] = {&ptr, &idx, &nn, &pv, &rep, &mark, &tag, &need, &tag_need, &fav, &fac, &fbv, &fbc, &cp, &ctl};
+        void* args[] = {&ptr, &idx, &nn, &best, &rep, &mark, &tag, &need, &tag_need, &fav, &fac, &fbv, &fbc, &cp,
+                        &ctl};
         PRGB_TRY(launch_coop((const void*)reach_k, kWaveBlock, 0, s, args, kWavePerSm, nullptr));
       }
       fwbw_max_k<<<grid_n(n), kBlock, 0, s>>>(n, fw, bw, bmax);
