@@ -23,6 +23,9 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 #include "mpnn.cuh"
 #include "solve.cuh"
@@ -538,21 +541,71 @@ __global__ void scale_k(int32_t n, double c, const double* __restrict__ x, doubl
     y[i] = c * x[i];
 }
 
-pr_status SideStreams::create() {
-  for (int q = 0; q < kSideStreams; q++) {
-    PRGB_CUDA(cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking));
-    PRGB_CUDA(cudaEventCreateWithFlags(&join[q], cudaEventDisableTiming));
+// Process-wide pools of non-blocking streams and timing-free events, per
+// device: a partition's first solve and every replayed-count solve would
+// otherwise create (and later destroy) about ten of each.  Never freed (it
+// must outlive the handles' last use at process exit).
+namespace {
+struct HandlePool {
+  std::mutex mu;
+  std::vector<cudaStream_t> streams[64];
+  std::vector<cudaEvent_t> events[64];
+};
+HandlePool& handle_pool() {
+  static HandlePool* p = new HandlePool;
+  return *p;
+}
+int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d >= 0 && d < 64 ? d : 0;
+}
+}  // namespace
+
+cudaError_t pool_stream(int dev, cudaStream_t* out) {
+  HandlePool& p = handle_pool();
+  {
+    std::lock_guard<std::mutex> lock(p.mu);
+    if (!p.streams[dev].empty()) {
+      *out = p.streams[dev].back();
+      p.streams[dev].pop_back();
+      return cudaSuccess;
+    }
   }
-  PRGB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  return cudaStreamCreateWithFlags(out, cudaStreamNonBlocking);
+}
+cudaError_t pool_event(int dev, cudaEvent_t* out) {
+  HandlePool& p = handle_pool();
+  {
+    std::lock_guard<std::mutex> lock(p.mu);
+    if (!p.events[dev].empty()) {
+      *out = p.events[dev].back();
+      p.events[dev].pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaEventCreateWithFlags(out, cudaEventDisableTiming);
+}
+void pool_release(int dev, cudaStream_t st, cudaEvent_t ev) {
+  HandlePool& p = handle_pool();
+  std::lock_guard<std::mutex> lock(p.mu);
+  if (st) p.streams[dev].push_back(st);
+  if (ev) p.events[dev].push_back(ev);
+}
+
+pr_status SideStreams::create() {
+  dev = current_device();
+  for (int q = 0; q < kSideStreams; q++) {
+    PRGB_CUDA(pool_stream(dev, &st[q]));
+    PRGB_CUDA(pool_event(dev, &join[q]));
+  }
+  PRGB_CUDA(pool_event(dev, &fork));
   return PR_OK;
 }
 
 SideStreams::~SideStreams() {
-  for (int q = 0; q < kSideStreams; q++) {
-    if (st[q]) cudaStreamDestroy(st[q]);
-    if (join[q]) cudaEventDestroy(join[q]);
-  }
-  if (fork) cudaEventDestroy(fork);
+  for (int q = 0; q < kSideStreams; q++) pool_release(dev, st[q], join[q]);
+  pool_release(dev, nullptr, fork);
 }
 
 pr_status KernelTiming::ensure(const pr_partition_s* P) {
@@ -568,7 +621,7 @@ pr_status KernelTiming::ensure(const pr_partition_s* P) {
     PRGB_CUDA(cudaEventCreate(&e1));
     stop.push_back(e1);
   }
-  while (level.size() < P->levels.size() + 1) {
+  while (levels && level.size() < P->levels.size() + 1) {
     cudaEvent_t e = nullptr;
     PRGB_CUDA(cudaEventCreate(&e));
     level.push_back(e);
@@ -866,8 +919,7 @@ SolvePlan::~SolvePlan() {
     if (e.exec) cudaGraphExecDestroy(e.exec);
     if (e.graph) cudaGraphDestroy(e.graph);
   }
-  if (done) cudaEventDestroy(done);
-  if (cs) cudaStreamDestroy(cs);
+  pool_release(dev, cs, done);
   delete keep;
 }
 
@@ -893,8 +945,9 @@ static pr_status plan_setup(pr_partition_s* P, SolvePlan* pl, bool mixed, int ti
   if (!pl->keep) {
     pl->keep = new (std::nothrow) Arena(P->stream);
     if (!pl->keep) return PR_ENOMEM;
-    PRGB_CUDA(cudaStreamCreateWithFlags(&pl->cs, cudaStreamNonBlocking));
-    PRGB_CUDA(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
+    pl->dev = current_device();
+    PRGB_CUDA(pool_stream(pl->dev, &pl->cs));
+    PRGB_CUDA(pool_event(pl->dev, &pl->done));
     PRGB_TRY(pl->side.create());
     PRGB_TRY(pl->cap_side.create());
     PRGB_TRY(pl->keep->alloc(&pl->ctl, 1));
@@ -916,8 +969,8 @@ static pr_status plan_setup(pr_partition_s* P, SolvePlan* pl, bool mixed, int ti
     PRGB_TRY(pl->keep->alloc(&pl->inf.dout, (size_t)n + 1));
     pl->yhat_uid = 0;
   }
-  if (timing) PRGB_TRY(pl->kt.ensure(P));
   pl->kt.levels = timing >= 2;
+  if (timing) PRGB_TRY(pl->kt.ensure(P));
   return set_solve_attrs(P, mixed);
 }
 

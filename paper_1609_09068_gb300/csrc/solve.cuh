@@ -126,7 +126,8 @@ struct KernelTiming {
   std::vector<cudaEvent_t> start, stop;
   std::vector<LargeComp> comps;
   std::vector<cudaEvent_t> level;  // [n_levels + 1]: each level's start, then the end of the last
-  bool levels = false;             // record the level events too (they cost a few microseconds a level)
+  bool levels = false;             // record the level events too (they cost a few microseconds a level);
+                                   // ensure() creates them only then
   pr_status ensure(const pr_partition_s* P);
   ~KernelTiming();
 };
@@ -137,6 +138,7 @@ struct SideStreams {
   cudaStream_t st[kSideStreams] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kSideStreams] = {nullptr, nullptr, nullptr, nullptr};
+  int dev = 0;  // the device of the pooled handles
   pr_status create();
   ~SideStreams();
 };
@@ -191,6 +193,7 @@ struct SolvePlan {
   KernelTiming kt;
   cudaStream_t cs = nullptr;
   cudaEvent_t done = nullptr;
+  int dev = 0;  // the device of the pooled cs and done
   std::vector<PlanGraph> graphs;
   uint64_t uses = 0;
   Ctl* ctl = nullptr;
