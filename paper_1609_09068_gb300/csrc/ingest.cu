@@ -7,105 +7,87 @@
 
 namespace prgb {
 
-// one warp per row: range and order checks, loop detection, loop-free degree
-// Rows of at most kLaneRow entries are checked one per lane (a warp takes 32
-// consecutive rows, whose entries are contiguous); longer rows are walked by
-// the whole warp, one after the other.
-constexpr int kLaneRow = 32;
+// The checks and the copy walk the entries, not the rows: a warp takes 1,024
+// consecutive entries (lane l the entries base + l + 32 k), so every load of
+// col and every store of the copy is one coalesced access whatever the row
+// lengths, and a hub row is spread over many warps.  Each lane finds the row
+// of its first entry by a binary search of rowptr and then steps forward.
+constexpr int kWarpEntries = 1024;
 
-__global__ void validate_rows_k(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                int32_t n, int64_t nnz, int32_t* __restrict__ outdeg,
-                                uint8_t* __restrict__ has_loop, Ctl* ctl) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
-    const int64_t i = base + lane;
-    int64_t s = 0, e = 0;
-    bool bad = false, longrow = false;
-    int loop = 0;
-    if (i < n) {
-      s = rowptr[i];
-      e = rowptr[i + 1];
-      bad = (s > e) || (s < 0) || (e > nnz) || (i == 0 && s != 0) || (i == n - 1 && e != nnz);
-      longrow = !bad && e - s > kLaneRow;
-      if (!bad && !longrow) {
-        int32_t prev = -1;
-        for (int64_t k = s; k < e; k++) {
-          const int32_t c = col[k];
-          if (c < 0 || c >= n || c <= prev) bad = true;  // in range, strictly ascending
-          if (c == (int32_t)i) loop = 1;
-          prev = c;
-        }
-      }
-    }
-    for (unsigned todo = __ballot_sync(0xffffffffu, longrow); todo; todo &= todo - 1) {
-      const int src = __ffs(todo) - 1;
-      const int64_t rs = __shfl_sync(0xffffffffu, s, src), re = __shfl_sync(0xffffffffu, e, src);
-      const int32_t r = (int32_t)(base + src);
-      bool b = false;
-      int lp = 0;
-      for (int64_t k = rs + lane; k < re; k += 32) {
-        const int32_t c = col[k];
-        if (c < 0 || c >= n) b = true;
-        if (k > rs && col[k - 1] >= c) b = true;
-        if (c == r) lp = 1;
-      }
-      b = __any_sync(0xffffffffu, b);
-      lp = __any_sync(0xffffffffu, lp);
-      if (lane == src) {
-        bad = b;
-        loop = lp;
-      }
-    }
-    if (i < n) {
-      if (bad) set_err(ctl, PR_EINVAL, 1);
-      outdeg[i] = bad ? 0 : (int32_t)(e - s) - loop;
-      has_loop[i] = (uint8_t)loop;
-    }
+// the row of entry e: rowptr[r] <= e < rowptr[r + 1] (rowptr checked first)
+__device__ __forceinline__ int row_of(const int32_t* __restrict__ rowptr, int32_t n, int64_t e) {
+  int lo = 0, hi = n;  // the answer is in [lo, hi)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if ((int64_t)rowptr[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// the offsets: non-decreasing, starting at 0 and ending at nnz
+__global__ void validate_ptr_k(const int32_t* __restrict__ rowptr, int32_t n, int64_t nnz, uint8_t* has_loop,
+                               Ctl* ctl) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = rowptr[i], e = rowptr[i + 1];
+    if ((s > e) || (s < 0) || (e > nnz) || (i == 0 && s != 0) || (i == n - 1 && e != nnz)) set_err(ctl, PR_EINVAL, 1);
+    has_loop[i] = 0;
   }
 }
 
-// copy the non-loop entries and record the source row of every kept edge
-// (rows split between lanes and warps as in validate_rows_k)
-__device__ __forceinline__ void strip_one(int64_t k, int64_t s, int64_t o, bool lp, int32_t i,
-                                          const int32_t* __restrict__ col, int32_t* __restrict__ oidx,
-                                          uint32_t* __restrict__ key_dst, uint32_t* __restrict__ val_src) {
-  const int32_t c = col[k];
-  if (c == i) return;
-  const int64_t pos = o + (k - s) - ((lp && c > i) ? 1 : 0);
-  oidx[pos] = c;
-  key_dst[pos] = (uint32_t)c;
-  val_src[pos] = (uint32_t)i;
+// the entries: in range, strictly ascending within a row; a self-loop marks
+// its row (at most one per row in a valid row)
+__global__ void validate_cols_k(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t n,
+                                int64_t nnz, uint8_t* has_loop, Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  if (vload(&ctl->err)) return;  // bad offsets: the rows are not searchable
+  for (int64_t base = gw * kWarpEntries; base < nnz; base += nw * kWarpEntries) {
+    int64_t e = base + lane;
+    if (e >= nnz) continue;
+    int r = row_of(rowptr, n, e);
+    bool bad = false;
+    for (int k = 0; k < kWarpEntries / 32 && e < nnz; k++, e += 32) {
+      while (r < n - 1 && (int64_t)rowptr[r + 1] <= e) r++;
+      const int32_t c = col[e];
+      if (c < 0 || c >= n) bad = true;
+      if (e > rowptr[r] && col[e - 1] >= c) bad = true;
+      if (c == r) has_loop[r] = 1;
+    }
+    if (bad) set_err(ctl, PR_EINVAL, 1);
+  }
 }
 
-__global__ void strip_loops_k(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                              int32_t n, const uint8_t* __restrict__ has_loop,
+// loop-free out-degree of every row
+__global__ void outdeg_k(const int32_t* __restrict__ rowptr, int32_t n, const uint8_t* __restrict__ has_loop,
+                         int32_t* __restrict__ outdeg) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    outdeg[i] = rowptr[i + 1] - rowptr[i] - (int32_t)has_loop[i];
+}
+
+// copy the non-loop entries and record the source row of every kept edge:
+// entry e of row r goes to optr[r] + (e - rowptr[r]), one less when it
+// follows the row's self-loop
+__global__ void strip_loops_k(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t n,
+                              int64_t nnz, const uint8_t* __restrict__ has_loop,
                               const int32_t* __restrict__ optr, int32_t* __restrict__ oidx,
                               uint32_t* __restrict__ key_dst, uint32_t* __restrict__ val_src) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
-    const int64_t i = base + lane;
-    int64_t s = 0, e = 0, o = 0;
-    bool lp = false;
-    if (i < n) {
-      s = rowptr[i];
-      e = rowptr[i + 1];
-      o = optr[i];
-      lp = has_loop[i] != 0;
-    }
-    const bool longrow = e - s > kLaneRow;
-    if (i < n && !longrow)
-      for (int64_t k = s; k < e; k++) strip_one(k, s, o, lp, (int32_t)i, col, oidx, key_dst, val_src);
-    for (unsigned todo = __ballot_sync(0xffffffffu, longrow); todo; todo &= todo - 1) {
-      const int src = __ffs(todo) - 1;
-      const int64_t rs = __shfl_sync(0xffffffffu, s, src), re = __shfl_sync(0xffffffffu, e, src);
-      const int64_t ro = __shfl_sync(0xffffffffu, o, src);
-      const bool rl = __shfl_sync(0xffffffffu, (int)lp, src) != 0;
-      for (int64_t k = rs + lane; k < re; k += 32)
-        strip_one(k, rs, ro, rl, (int32_t)(base + src), col, oidx, key_dst, val_src);
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gw * kWarpEntries; base < nnz; base += nw * kWarpEntries) {
+    int64_t e = base + lane;
+    if (e >= nnz) continue;
+    int r = row_of(rowptr, n, e);
+    for (int k = 0; k < kWarpEntries / 32 && e < nnz; k++, e += 32) {
+      while (r < n - 1 && (int64_t)rowptr[r + 1] <= e) r++;
+      const int32_t c = col[e];
+      if (c == r) continue;
+      const int64_t pos = optr[r] + (e - rowptr[r]) - ((has_loop[r] && c > r) ? 1 : 0);
+      oidx[pos] = c;
+      key_dst[pos] = (uint32_t)c;
+      val_src[pos] = (uint32_t)r;
     }
   }
 }
@@ -248,7 +230,12 @@ pr_status ingest(const pr_csr* csr, uint32_t flags, DevGraph* g, Arena& keep, Ar
   uint8_t* has_loop = nullptr;
   PRGB_TRY(tmp.alloc(&has_loop, (size_t)n + 1));
   if (n > 0) {
-    validate_rows_k<<<grid_rows(n), kBlock, 0, s>>>(rowptr, col, n, nnz, g->outdeg, has_loop, ctl);
+    validate_ptr_k<<<grid_rows((n + 7) / 8), kBlock, 0, s>>>(rowptr, n, nnz, has_loop, ctl);
+    PRGB_LAUNCH();
+    validate_cols_k<<<grid_rows((nnz + kWarpEntries - 1) / kWarpEntries), kBlock, 0, s>>>(rowptr, col, n, nnz,
+                                                                                          has_loop, ctl);
+    PRGB_LAUNCH();
+    outdeg_k<<<grid_rows((n + 7) / 8), kBlock, 0, s>>>(rowptr, n, has_loop, g->outdeg);
     PRGB_LAUNCH();
   }
   PRGB_TRY(scan_i32(g->outdeg, g->optr, n, tmp));
@@ -269,7 +256,8 @@ pr_status ingest(const pr_csr* csr, uint32_t flags, DevGraph* g, Arena& keep, Ar
   PRGB_TRY(tmp.alloc(&kt, (size_t)(m > 0 ? m : 1)));
   PRGB_TRY(tmp.alloc(&vt, (size_t)(m > 0 ? m : 1)));
   if (n > 0) {
-    strip_loops_k<<<grid_rows(n), kBlock, 0, s>>>(rowptr, col, n, has_loop, g->optr, g->oidx, kd, vs);
+    strip_loops_k<<<grid_rows((nnz + kWarpEntries - 1) / kWarpEntries), kBlock, 0, s>>>(rowptr, col, n, nnz, has_loop,
+                                                                                        g->optr, g->oidx, kd, vs);
     PRGB_LAUNCH();
   }
   // CSR order is (source asc, target asc); a stable sort by target gives
