@@ -135,10 +135,22 @@ int bits_for(uint32_t max_value) {
 // ---------------------------------------------------------------------------
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kBlock * kScanItems;  // 4096
+constexpr int64_t kScanFold = 2048;             // tiles up to which blocks fold the prefix themselves
+
+// sum of v over the block (every thread gets it), on the integer pipes
+__device__ __forceinline__ int32_t block_sum_i32(int32_t v, int32_t* sh) {
+  v = (int32_t)__reduce_add_sync(0xffffffffu, (unsigned)v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  const int32_t t = (threadIdx.x & 31) < (int)(blockDim.x >> 5) ? sh[threadIdx.x & 31] : 0;
+  const int32_t r = (int32_t)__reduce_add_sync(0xffffffffu, (unsigned)t);
+  __syncthreads();  // sh may be reused
+  return r;
+}
 
 template <typename T>
 __global__ void scan_reduce_k(const T* __restrict__ in, int64_t n, int32_t* __restrict__ tile_sums) {
-  __shared__ double sh[kBlock / 32];
+  __shared__ int32_t sh[kBlock / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   int32_t s = 0;
 #pragma unroll
@@ -146,9 +158,8 @@ __global__ void scan_reduce_k(const T* __restrict__ in, int64_t n, int32_t* __re
     int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
     if (i < n) s += (int32_t)in[i];
   }
-  // integer reduce through the double helper is exact for |s| < 2^53
-  double t = block_sum((double)s, sh);
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = (int32_t)t;
+  const int32_t t = block_sum_i32(s, sh);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = t;
 }
 
 // single block: exclusive scan of tile sums in place
@@ -174,10 +185,22 @@ __global__ void scan_tiles_k(int32_t* __restrict__ sums, int64_t ntiles) {
   }
 }
 
+// tile_off: the exclusive prefix of the tile sums, or (fold) the tile sums
+// themselves, whose prefix this block adds up first (few tiles: it saves
+// the single-block scan launch between the two passes)
 template <typename T>
-__global__ void scan_tile_k(const T* __restrict__ in, int64_t n, const int32_t* __restrict__ tile_off,
+__global__ void scan_tile_k(const T* __restrict__ in, int64_t n, const int32_t* __restrict__ tile_off, bool fold,
                             int32_t* __restrict__ out) {
   __shared__ int32_t sh[kBlock];
+  __shared__ int32_t shr[kBlock / 32];
+  int32_t toff;
+  if (fold) {
+    int32_t a = 0;
+    for (int64_t t = threadIdx.x; t < (int64_t)blockIdx.x; t += blockDim.x) a += tile_off[t];
+    toff = block_sum_i32(a, shr);
+  } else {
+    toff = tile_off[blockIdx.x];
+  }
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int32_t v[kScanItems];
   int32_t s = 0;
@@ -195,7 +218,7 @@ __global__ void scan_tile_k(const T* __restrict__ in, int64_t n, const int32_t* 
     sh[threadIdx.x] += t;
     __syncthreads();
   }
-  int32_t run = tile_off[blockIdx.x] + sh[threadIdx.x] - s;
+  int32_t run = toff + sh[threadIdx.x] - s;
 #pragma unroll
   for (int k = 0; k < kScanItems; k++) {
     int64_t i = base + k;
@@ -217,9 +240,13 @@ static pr_status scan_impl(const T* in, int32_t* out, int64_t n, Arena& a) {
   PRGB_TRY(a.alloc(&sums, (size_t)ntiles));
   scan_reduce_k<T><<<(unsigned)ntiles, kBlock, 0, s>>>(in, n, sums);
   PRGB_LAUNCH();
-  scan_tiles_k<<<1, kBlock, 0, s>>>(sums, ntiles);
-  PRGB_LAUNCH();
-  scan_tile_k<T><<<(unsigned)ntiles, kBlock, 0, s>>>(in, n, sums, out);
+  // up to kScanFold tiles each block adds its predecessors' sums itself
+  const bool fold = ntiles <= kScanFold;
+  if (!fold) {
+    scan_tiles_k<<<1, kBlock, 0, s>>>(sums, ntiles);
+    PRGB_LAUNCH();
+  }
+  scan_tile_k<T><<<(unsigned)ntiles, kBlock, 0, s>>>(in, n, sums, fold, out);
   PRGB_LAUNCH();
   return PR_OK;
 }
