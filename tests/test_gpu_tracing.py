@@ -74,3 +74,20 @@ def test_partition_phase_times(prgb):
     with pytest.raises(prgb.PrError) as e:
         P0.timing()
     assert e.value.code == 1
+
+
+def test_counts_off_reads_back_only_timing(prgb):
+    """counts_off: the solve reports its kernel times (and the grid-wide
+    components' bytes) without the per-component counts, and R is the same."""
+    import torch
+    g = gg.web_like(seed=12, n=60_000, n_small=1_200, layers=12, giant_layer=4)
+    G = prgb.graph(torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.col).cuda())
+    P = prgb.partition(G)
+    u = torch.from_numpy(g.u).cuda()
+    R1, s1 = prgb.solve(P, 0.85, u, 1e-10, with_stats=True, timing=True)
+    R2, s2 = prgb.solve(P, 0.85, u, 1e-10, with_stats=True, timing=True, counts=False)
+    assert torch.equal(R1, R2)
+    assert "comp_iters" in s1 and "comp_iters" not in s2
+    assert s2["iters_max"] == 0 and s2["edge_visits"] == 0
+    assert s1["kernel_launches"] == s2["kernel_launches"] >= 1
+    assert s2["kernel_bytes"] == s1["kernel_bytes"] > 0 and s2["kernel_ms"] > 0
