@@ -140,6 +140,8 @@ def test_static_residual_allocates_nothing(prgb):
     the default pool's high-water mark does not rise above what was in use
     before, device free memory does not move, and torch's allocator is not
     touched."""
+    import gc
+
     import torch
     g = gg.web_like(seed=23, n=100_000, n_small=2_000, layers=10, giant_layer=3)
     rowptr = torch.from_numpy(g.rowptr).cuda()
@@ -147,15 +149,22 @@ def test_static_residual_allocates_nothing(prgb):
     u = torch.from_numpy(g.u).cuda()
     R = u * 3.0
     prgb.residual_l1_static(rowptr, col, CC, u, R)  # set-up call
+    # objects left by earlier tests are collected now, not inside the window
+    # (their destructors release memory through the library and torch)
+    gc.collect()
     torch.cuda.synchronize()
     reset_high, high, free_bytes = _driver()
     reset_high()
     h0, f0 = high(), free_bytes()
     t0 = torch.cuda.memory_allocated()
     torch.cuda.reset_peak_memory_stats()
-    for _ in range(2):
-        prgb.residual_l1_static(rowptr, col, CC, u, R)
-    torch.cuda.synchronize()
+    gc.disable()
+    try:
+        for _ in range(2):
+            prgb.residual_l1_static(rowptr, col, CC, u, R)
+        torch.cuda.synchronize()
+    finally:
+        gc.enable()
     assert high() == h0
     assert free_bytes() == f0
     assert torch.cuda.max_memory_allocated() == t0
