@@ -9,7 +9,8 @@
 // z' = P c/outdeg is the exact product rounded once (fx_scale), and R is an
 // exact running sum; a sweep issues no floating-point instruction but the
 // stopping norm's FP32 conversion.  The results equal the real-number
-// series up to one rounding of each z and of the final R.
+// series up to one rounding of each z (and, where z is gathered as FP64
+// values, its rounding to the nearest double) and of the final R.
 //
 // The stopping norm is reduced on integers too: each row contributes
 // q = ceil(|P_i| 2^32 / thr) (thr = tau / (1 + 1e-4) rounded down to FP32
