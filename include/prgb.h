@@ -259,6 +259,49 @@ typedef struct pr_partition_timing {
 pr_status pr_partition_create(const pr_graph *g, uint32_t flags, void *stream, pr_partition **out);
 
 /*
+ * pr_partition_save -- write a partition to a host file, so that the same
+ * graph can be partitioned again (pr_partition_load) without the component
+ * search and level assignment of Sec. 4.1.
+ *   part   : the partition (from pr_partition_create or pr_partition_load).
+ *   path   : host file path, created or truncated.
+ *   stream : CUDA stream; synchronised.
+ * Format (little endian): a 64-byte header -- magic "PRGBPART", format
+ * version 1 (uint32), header size 64 (uint32), n and the loop-free edge
+ * count (int64 each), a 64-bit digest of the graph's loop-free edge set, a
+ * 64-bit digest of the arrays below, the component count, level count and
+ * largest sub-level wave (int32 each), 4 bytes of zero -- then for every
+ * vertex in the graph's vertex order its component id, its level (Def. 3.3),
+ * its sub-level wave (int32 arrays of n entries each; a wave orders the
+ * vertices of a CAC topologically) and its type PR_TYPE_* (uint8 array):
+ * 13 bytes per vertex.  The digests detect a different graph and accidental
+ * damage, not deliberate tampering: a loaded file is trusted.
+ * Errors: PR_EINVAL for NULL arguments or a file that cannot be written (a
+ * partly written file is removed); PR_ENOMEM, PR_ECUDA.
+ */
+pr_status pr_partition_save(const pr_partition *part, const char *path, void *stream);
+
+/*
+ * pr_partition_load -- the partition of g read from a file that
+ * pr_partition_save wrote for the same graph (same n, same loop-free edge
+ * set): the layout of Sec. 4.2 is rebuilt from it on the device.  The
+ * result equals pr_partition_create(g): the same component ids, types and
+ * levels, and solves with the same results.
+ *   g      : a prepared graph; it must outlive the partition.
+ *   path   : host file path.
+ *   flags  : 0.
+ *   stream : CUDA stream; synchronised.
+ *   out    : receives a new partition handle on PR_OK (NULL otherwise).
+ * Errors: PR_EINVAL for NULL arguments, a nonzero flag, or a file that
+ * cannot be read, is not a partition file of format version 1, was written
+ * for a graph with another n, edge count or edge set, is truncated or
+ * longer than its header says, holds a value out of range or fails its
+ * digest, or whose component ids the rebuilt layout does not reproduce;
+ * PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT, PR_EINTERNAL.
+ */
+pr_status pr_partition_load(const pr_graph *g, const char *path, uint32_t flags, void *stream,
+                            pr_partition **out);
+
+/*
  * pr_partition_timing_get -- the phase times and wave counts of a partition
  * created with PR_PARTITION_TIMING, copied to *out (host).
  * Errors: PR_EINVAL for NULL arguments or a partition created without the

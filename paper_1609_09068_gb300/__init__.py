@@ -24,7 +24,7 @@ __all__ = [
     "PrError", "Graph", "Partition", "graph", "partition", "solve", "global_power",
     "residual_l1", "load_library", "library_path", "launch_count", "TYPE_CAC", "TYPE_SCC",
     "NORM_L1", "NORM_LINF", "PREC_FP64", "PREC_MIXED", "Mpnn", "set_wait_limit", "CANONICALIZE",
-    "PARTITION_TIMING",
+    "PARTITION_TIMING", "load_partition",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -93,6 +93,8 @@ _SIGS = {
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pr_partition_destroy": (None, [C.c_void_p]),
     "pr_partition_timing_get": (C.c_int, [C.c_void_p, C.POINTER(_PartTiming)]),
+    "pr_partition_save": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p]),
+    "pr_partition_load": (C.c_int, [C.c_void_p, C.c_char_p, C.c_uint32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "pr_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.POINTER(_Opts),
                            C.c_void_p, C.POINTER(_Stats), C.c_void_p]),
     "pr_global_power": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.POINTER(_Opts),
@@ -243,12 +245,16 @@ class Graph:
 class Partition:
     """SCC/CAC partition with levels and the solver layout (``pr_partition``)."""
 
-    def __init__(self, g: Graph, timing=False):
+    def __init__(self, g: Graph, timing=False, path=None):
         lib = load_library()
         self.graph = g  # the partition refers to the graph's buffers
         self._h = C.c_void_p()
-        _check(lib.pr_partition_create(g.handle, PARTITION_TIMING if timing else 0, _stream(),
-                                       C.byref(self._h)), "pr_partition_create")
+        if path is None:
+            _check(lib.pr_partition_create(g.handle, PARTITION_TIMING if timing else 0, _stream(),
+                                           C.byref(self._h)), "pr_partition_create")
+        else:
+            _check(lib.pr_partition_load(g.handle, os.fsencode(path), 0, _stream(), C.byref(self._h)),
+                   "pr_partition_load")
         n, m, nc, nl, ns, nsv = (C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32(),
                                  C.c_int32())
         _check(lib.pr_partition_info(self._h, C.byref(n), C.byref(m), C.byref(nc), C.byref(nl),
@@ -284,6 +290,11 @@ class Partition:
                 "levels_ms": t.levels_ms, "layout_ms": t.layout_ms, "total_ms": t.total_ms,
                 "colour_rounds": t.colour_rounds,
                 "waves": {k: {"grid": t.waves[i][0], "block": t.waves[i][1]} for i, k in enumerate(kinds)}}
+
+    def save(self, path):
+        """Write the partition to a file (pr_partition_save); ``load_partition``
+        reads it back for the same graph."""
+        _check(load_library().pr_partition_save(self._h, os.fsencode(path), _stream()), "pr_partition_save")
 
     def tune(self, c, u, tol):
         """Autotune the solve's launch shapes on this partition (see
@@ -327,6 +338,15 @@ def partition(g, col=None, on_host=False, timing=False):
     elif not isinstance(g, Graph):
         raise TypeError("partition() takes a Graph, or rowptr and col")
     return Partition(g, timing=timing)
+
+
+def load_partition(g, path):
+    """The partition of graph ``g`` saved by ``Partition.save`` (pr_partition_load):
+    the same components, levels and solves as ``partition(g)``, without the
+    component search."""
+    if not isinstance(g, Graph):
+        raise TypeError("load_partition() takes a Graph")
+    return Partition(g, path=path)
 
 
 def _opts(norm, max_iter, io_on_host, replay, precision=PREC_FP64, warm=None, lu_threshold=0):

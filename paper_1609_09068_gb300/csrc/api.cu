@@ -1,6 +1,10 @@
 // api.cu -- the extern "C" entry points declared in include/prgb.h.
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
 
 #include <map>
 #include <mutex>
@@ -15,6 +19,12 @@ int last_cuda_error();
 void set_wait_limit_us(unsigned int us);
 pr_status build_layout(pr_partition_s* P, const int32_t* crep, const int32_t* wave, int32_t max_wave, Arena& tmp,
                        Ctl* ctl);
+pr_status graph_digest(const DevGraph& g, Arena& tmp, uint64_t* out);
+pr_status partition_digest(int32_t n, const int32_t* comp, const uint8_t* type, const int32_t* level,
+                           const int32_t* wave, int32_t n_comp, int32_t n_levels, int32_t max_wave, bool check,
+                           Arena& tmp, Ctl* ctl, uint64_t* out);
+pr_status smallest_members(int32_t n, int32_t n_comp, const int32_t* comp, int32_t* crep, Arena& tmp);
+pr_status check_same_ids(int32_t n, const int32_t* a, const int32_t* b, Ctl* ctl, cudaStream_t s);
 
 // keep freed stream-ordered memory cached in the device's default pool so
 // repeated calls do not return it to the CUDA driver
@@ -74,6 +84,65 @@ static pr_status finish_sync(cudaStream_t s, Ctl* ctl, int* flags_out) {
   PRGB_CUDA(cudaStreamSynchronize(s));
   if (flags_out) *flags_out = h[1];
   return (pr_status)h[0];
+}
+
+// The header of a partition file (pr_partition_save); host byte order,
+// which is little endian on every host this library builds for.
+struct PartFileHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t header_bytes;
+  int64_t n;
+  int64_t m;
+  uint64_t graph_digest;
+  uint64_t part_digest;
+  int32_t n_comp;
+  int32_t n_levels;
+  int32_t max_wave;
+  int32_t zero;
+};
+static_assert(sizeof(PartFileHeader) == 64, "the partition file header is 64 bytes");
+static const char kPartMagic[8] = {'P', 'R', 'G', 'B', 'P', 'A', 'R', 'T'};
+constexpr uint32_t kPartVersion = 1;
+
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() {
+    if (f) fclose(f);
+  }
+};
+
+// a host staging buffer of at most 64 MiB for the copies between a file and
+// device arrays of `bytes` bytes
+struct IoBuf {
+  char* p = nullptr;
+  size_t size = 0;
+  explicit IoBuf(size_t bytes) {
+    size = std::min(bytes, (size_t)64 << 20);
+    if (size < 16) size = 16;
+    p = new (std::nothrow) char[size];
+  }
+  ~IoBuf() { delete[] p; }
+};
+
+static pr_status write_dev(FILE* f, const void* d, size_t bytes, IoBuf& b, cudaStream_t s) {
+  for (size_t o = 0; o < bytes; o += b.size) {
+    const size_t k = std::min(b.size, bytes - o);
+    PRGB_CUDA(cudaMemcpyAsync(b.p, (const char*)d + o, k, cudaMemcpyDeviceToHost, s));
+    PRGB_CUDA(cudaStreamSynchronize(s));
+    if (fwrite(b.p, 1, k, f) != k) return PR_EINVAL;
+  }
+  return PR_OK;
+}
+
+static pr_status read_dev(FILE* f, void* d, size_t bytes, IoBuf& b, cudaStream_t s) {
+  for (size_t o = 0; o < bytes; o += b.size) {
+    const size_t k = std::min(b.size, bytes - o);
+    if (fread(b.p, 1, k, f) != k) return PR_EINVAL;
+    PRGB_CUDA(cudaMemcpyAsync((char*)d + o, b.p, k, cudaMemcpyHostToDevice, s));
+    PRGB_CUDA(cudaStreamSynchronize(s));
+  }
+  return PR_OK;
 }
 
 }  // namespace prgb
@@ -160,6 +229,24 @@ void pr_graph_destroy(pr_graph* g) {
   delete g;
 }
 
+// The end of creating or loading a partition: the class boundary and grid
+// shape an earlier tuning chose, or the partition released on failure.
+static pr_status finish_partition(pr_partition_s* P, pr_status st, pr_partition** out) {
+  if (st == PR_OK) {
+    int32_t tc = kCtaCompMax, tb = 4, tl = 1;
+    tuned_defaults(&tc, &tb, &tl);
+    if (tc != P->cta_max || tb != P->coop_blocks || tl != P->balance) retune_levels(P, tc, tb, tl);
+    else split_fx_ranges(P);
+  }
+  if (st != PR_OK) {
+    delete P->keep;
+    delete P;
+    return st;
+  }
+  *out = P;
+  return PR_OK;
+}
+
 static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, void* stream, pr_partition** out) {
   if (!out) return PR_EINVAL;
   *out = nullptr;
@@ -180,7 +267,7 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
   {
     Arena tmp(s);
     Ctl* ctl = nullptr;
-    int32_t *rep = nullptr, *crep = nullptr, *wave = nullptr;
+    int32_t *rep = nullptr, *crep = nullptr;
     int32_t max_wave = 0;
     if (st == PR_OK) st = tmp.alloc(&ctl, 1);
     if (st == PR_OK) st = P->keep->alloc(&P->comp_id, (size_t)n);
@@ -188,7 +275,8 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
     if (st == PR_OK) st = P->keep->alloc(&P->level, (size_t)n);
     if (st == PR_OK) st = tmp.alloc(&rep, (size_t)n);
     if (st == PR_OK) st = tmp.alloc(&crep, (size_t)n);
-    if (st == PR_OK) st = tmp.alloc(&wave, (size_t)n);
+    if (st == PR_OK) st = P->keep->alloc(&P->wave, (size_t)n);
+    int32_t* wave = P->wave;
     if (st == PR_OK) st = init_ctl(ctl, s);
     if (st == PR_OK && cudaMemsetAsync(ctl->waves, 0, sizeof(ctl->waves), s) != cudaSuccess) st = PR_ECUDA;
     // phase events: 0 start, 1 trim, 2 giant, 3 colouring, 4 levels,
@@ -206,6 +294,7 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
       st = levels_and_merge(P->g, rep, crep, P->level, P->type, wave, &max_wave, tmp, ctl);
     }
     if (st == PR_OK) st = ev.mark(4, s);
+    P->max_wave = max_wave;
     if (st == PR_OK) {
       NvtxRange r("prgb layout");
       st = build_layout(P, crep, wave, max_wave, tmp, ctl);
@@ -219,25 +308,128 @@ static pr_status pr_partition_create_body(const pr_graph* g, uint32_t flags, voi
       if (st == PR_OK) st = copy_waves(P->waves, ctl);
     }
   }
-  if (st == PR_OK) {
-    // the class boundary and grid shape an earlier tuning chose
-    int32_t tc = kCtaCompMax, tb = 4, tl = 1;
-    tuned_defaults(&tc, &tb, &tl);
-    if (tc != P->cta_max || tb != P->coop_blocks || tl != P->balance) retune_levels(P, tc, tb, tl);
-    else split_fx_ranges(P);
-  }
-  if (st != PR_OK) {
-    delete P->keep;
-    delete P;
-    return st;
-  }
-  *out = P;
-  return PR_OK;
+  return finish_partition(P, st, out);
 }
 
 pr_status pr_partition_create(const pr_graph* g, uint32_t flags, void* stream, pr_partition** out) {
   prgb::NvtxRange nvtx("prgb partition");
   return prgb::note_status(pr_partition_create_body(g, flags, stream, out));
+}
+
+static pr_status pr_partition_save_body(const pr_partition* part, const char* path, void* stream) {
+  if (!part || !path) return PR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const pr_partition_s* P = part;
+  const int32_t n = P->g.n;
+  PartFileHeader h = {};
+  memcpy(h.magic, kPartMagic, sizeof(h.magic));
+  h.version = kPartVersion;
+  h.header_bytes = sizeof(h);
+  h.n = n;
+  h.m = P->g.m;
+  h.n_comp = P->n_comp;
+  h.n_levels = P->n_levels;
+  h.max_wave = P->max_wave;
+  {
+    Arena tmp(s);
+    Ctl* ctl = nullptr;
+    PRGB_TRY(tmp.alloc(&ctl, 1));
+    PRGB_TRY(init_ctl(ctl, s));
+    PRGB_TRY(graph_digest(P->g, tmp, &h.graph_digest));
+    PRGB_TRY(partition_digest(n, P->comp_id, P->type, P->level, P->wave, P->n_comp, P->n_levels, P->max_wave, false,
+                              tmp, ctl, &h.part_digest));
+  }
+  IoBuf b((size_t)n * 4);
+  if (!b.p) return PR_ENOMEM;
+  FILE* f = fopen(path, "wb");
+  if (!f) return PR_EINVAL;
+  pr_status st = fwrite(&h, sizeof(h), 1, f) == 1 ? PR_OK : PR_EINVAL;
+  if (st == PR_OK) st = write_dev(f, P->comp_id, (size_t)n * 4, b, s);
+  if (st == PR_OK) st = write_dev(f, P->level, (size_t)n * 4, b, s);
+  if (st == PR_OK) st = write_dev(f, P->wave, (size_t)n * 4, b, s);
+  if (st == PR_OK) st = write_dev(f, P->type, (size_t)n, b, s);
+  if (fclose(f) != 0 && st == PR_OK) st = PR_EINVAL;
+  if (st != PR_OK) remove(path);
+  return st;
+}
+
+pr_status pr_partition_save(const pr_partition* part, const char* path, void* stream) {
+  prgb::NvtxRange nvtx("prgb partition_save");
+  return prgb::note_status(pr_partition_save_body(part, path, stream));
+}
+
+static pr_status pr_partition_load_body(const pr_graph* g, const char* path, uint32_t flags, void* stream,
+                                        pr_partition** out) {
+  if (!out) return PR_EINVAL;
+  *out = nullptr;
+  if (!g || !path || flags != 0) return PR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  tune_pool();
+  FileCloser fc{fopen(path, "rb")};
+  if (!fc.f) return PR_EINVAL;
+  PartFileHeader h;
+  if (fread(&h, sizeof(h), 1, fc.f) != 1) return PR_EINVAL;
+  const int32_t n = g->g.n;
+  if (memcmp(h.magic, kPartMagic, sizeof(h.magic)) != 0 || h.version != kPartVersion ||
+      h.header_bytes != sizeof(h) || h.n != n || h.m != g->g.m || h.zero != 0)
+    return PR_EINVAL;
+  // every vertex lies in one component of one level (none of either when n = 0)
+  const int32_t lo = n > 0 ? 1 : 0;
+  if (h.n_comp < lo || h.n_comp > n || h.n_levels < lo || h.n_levels > n || h.max_wave < 0) return PR_EINVAL;
+  IoBuf b((size_t)n * 4);
+  if (!b.p) return PR_ENOMEM;
+  pr_partition_s* P = new (std::nothrow) pr_partition_s;
+  if (!P) return PR_ENOMEM;
+  P->stream = s;
+  P->keep = new (std::nothrow) Arena(s);
+  if (!P->keep) {
+    delete P;
+    return PR_ENOMEM;
+  }
+  P->g = g->g;
+  P->max_wave = h.max_wave;
+  pr_status st = PR_OK;
+  {
+    Arena tmp(s);
+    Ctl* ctl = nullptr;
+    int32_t *saved = nullptr, *crep = nullptr;
+    uint64_t gd = 0, pd = 0;
+    if (st == PR_OK) st = tmp.alloc(&ctl, 1);
+    if (st == PR_OK) st = P->keep->alloc(&P->comp_id, (size_t)n);
+    if (st == PR_OK) st = P->keep->alloc(&P->type, (size_t)n);
+    if (st == PR_OK) st = P->keep->alloc(&P->level, (size_t)n);
+    if (st == PR_OK) st = P->keep->alloc(&P->wave, (size_t)n);
+    if (st == PR_OK) st = tmp.alloc(&saved, (size_t)n);
+    if (st == PR_OK) st = tmp.alloc(&crep, (size_t)n);
+    if (st == PR_OK) st = read_dev(fc.f, saved, (size_t)n * 4, b, s);
+    if (st == PR_OK) st = read_dev(fc.f, P->level, (size_t)n * 4, b, s);
+    if (st == PR_OK) st = read_dev(fc.f, P->wave, (size_t)n * 4, b, s);
+    if (st == PR_OK) st = read_dev(fc.f, P->type, (size_t)n, b, s);
+    if (st == PR_OK && fgetc(fc.f) != EOF) st = PR_EINVAL;
+    if (st == PR_OK) st = init_ctl(ctl, s);
+    if (st == PR_OK) st = graph_digest(P->g, tmp, &gd);
+    if (st == PR_OK && gd != h.graph_digest) st = PR_EINVAL;
+    if (st == PR_OK)
+      st = partition_digest(n, saved, P->type, P->level, P->wave, h.n_comp, h.n_levels, h.max_wave, true, tmp, ctl,
+                            &pd);
+    // the range checks' verdict comes before any kernel indexes with the arrays
+    if (st == PR_OK) st = finish_sync(s, ctl, nullptr);
+    if (st == PR_OK && pd != h.part_digest) st = PR_EINVAL;
+    if (st == PR_OK) st = smallest_members(n, h.n_comp, saved, crep, tmp);
+    if (st == PR_OK) {
+      NvtxRange r("prgb layout");
+      st = build_layout(P, crep, P->wave, h.max_wave, tmp, ctl);
+    }
+    if (st == PR_OK && (P->n_comp != h.n_comp || P->n_levels != h.n_levels)) st = PR_EINVAL;
+    if (st == PR_OK) st = check_same_ids(n, P->comp_id, saved, ctl, s);
+    if (st == PR_OK) st = finish_sync(s, ctl, nullptr);
+  }
+  return finish_partition(P, st, out);
+}
+
+pr_status pr_partition_load(const pr_graph* g, const char* path, uint32_t flags, void* stream, pr_partition** out) {
+  prgb::NvtxRange nvtx("prgb partition_load");
+  return prgb::note_status(pr_partition_load_body(g, path, flags, stream, out));
 }
 
 pr_status pr_partition_timing_get(const pr_partition* part, pr_partition_timing* out) {

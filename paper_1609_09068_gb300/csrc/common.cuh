@@ -562,6 +562,11 @@ struct pr_partition_s {
   int32_t* fxs_wbase = nullptr;
   uint8_t* fxs_wcnt = nullptr;
   uint2* fxs_words = nullptr;
+  // the sub-level wave of every vertex (longest path to a sink in the
+  // condensation) and its maximum: with comp_id, type and level, all that
+  // pr_partition_save writes
+  int32_t* wave = nullptr;
+  int32_t max_wave = 0;
   // PR_PARTITION_TIMING: phase times (pr_partition_timing order) and counts
   bool timed = false;
   float phase_ms[6] = {0, 0, 0, 0, 0, 0};
