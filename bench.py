@@ -100,6 +100,9 @@ def parse():
                     help="for profilers: prepare and partition the workload, run this many FP64 solves, exit")
     ap.add_argument("--shape", default=None,
                     help="cta_max,coop_blocks,balance of --profile-solves (default: the autotuner's choice)")
+    ap.add_argument("--partition-io", action="store_true",
+                    help="time pr_partition_create against pr_partition_save and pr_partition_load "
+                         "on the web_like, deep_dag and large graphs; one JSON line")
     ap.add_argument("--cpu-parallel-worker", action="store_true",
                     help="internal: time the multi-core CPU baseline and print one JSON line")
     return ap.parse_args()
@@ -1005,8 +1008,61 @@ def profile_solves(args):
     return 0
 
 
+def partition_io(args):
+    """Partition files: for each graph, the wall time of pr_partition_create
+    against pr_partition_save and pr_partition_load of the same partition
+    (each call synchronises; medians of 5 calls, 3 for the large graph, after
+    one untimed call of each), the file's size, and whether the loaded
+    partition equals the created one."""
+    import torch
+    import paper_1609_09068_gb300 as prgb
+    prgb.load_library()
+
+    def med(f, k):
+        ts = []
+        for _ in range(k):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = f()
+            ts.append((time.perf_counter() - t) * 1e3)
+        return statistics.median(ts), r
+
+    out = {}
+    for name in ("web", "deep", "large"):
+        try:
+            if name == "large":
+                from graphgen.large import web_like_device
+                rowptr, col, _ = web_like_device(seed=4, n=args.large_n)
+            else:
+                g = gg.config(name)
+                rowptr, col = torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.col).cuda()
+            G = prgb.graph(rowptr, col)
+            k = 3 if name == "large" else 5
+            with tempfile.TemporaryDirectory() as d:
+                path = os.path.join(d, "part.bin")
+                P = prgb.partition(G)
+                create_ms, P = med(lambda: prgb.partition(G), k)
+                P.save(path)
+                save_ms, _ = med(lambda: P.save(path), k)
+                prgb.load_partition(G, path)
+                load_ms, L = med(lambda: prgb.load_partition(G, path), k)
+                same = all(bool(torch.equal(a, b)) for a, b in zip(P.query(), L.query()))
+                out[name] = {"n": int(rowptr.numel() - 1), "edges": int(col.numel()),
+                             "create_ms": round(create_ms, 2), "save_ms": round(save_ms, 2),
+                             "load_ms": round(load_ms, 2), "file_bytes": os.path.getsize(path),
+                             "loaded_equals_created": same}
+            del G, P, L, rowptr, col
+            torch.cuda.empty_cache()
+        except Exception as e:  # report the failure, keep the other graphs
+            out[name] = {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
+    print(json.dumps({"metric": "partition_io", "unit": "ms", "graphs": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.partition_io:
+        return partition_io(args)
     if args.profile_solves > 0:
         return profile_solves(args)
     if args.cpu_parallel_worker:
