@@ -14,8 +14,11 @@
  * third.  Calls that read the graph take a prepared pr_graph handle made
  * once from the caller's CSR by pr_graph_create (validation, loop removal
  * and the in-adjacency are done once and shared by the partition, the
- * global series and the residual) rather than the CSR itself.  pr_global_power is the paper's baseline (the power series on the
- * whole graph, Sec. 4.3.2) and pr_residual_l1 evaluates the residual of the
+ * global series and the residual) rather than the CSR itself.
+ * pr_partition_save and pr_partition_load keep a partition in a file and
+ * rebuild it for the same graph without the component search.
+ * pr_global_power is the paper's baseline (the power series on the whole
+ * graph, Sec. 4.3.2) and pr_residual_l1 evaluates the residual of the
  * defining system.
  *
  * Conventions shared by every entry point
