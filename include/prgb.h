@@ -271,8 +271,9 @@ pr_status pr_partition_create(const pr_graph *g, uint32_t flags, void *stream, p
  * Format (little endian): a 64-byte header -- magic "PRGBPART", format
  * version 1 (uint32), header size 64 (uint32), n and the loop-free edge
  * count (int64 each), a 64-bit digest of the graph's loop-free edge set, a
- * 64-bit digest of the arrays below, the component count, level count and
- * largest sub-level wave (int32 each), 4 bytes of zero -- then for every
+ * 64-bit digest of the arrays below and the three counts that follow, the
+ * component count, level count and largest sub-level wave (int32 each), 4
+ * bytes of zero -- then for every
  * vertex in the graph's vertex order its component id, its level (Def. 3.3),
  * its sub-level wave (int32 arrays of n entries each; a wave orders the
  * vertices of a CAC topologically) and its type PR_TYPE_* (uint8 array):

@@ -105,6 +105,15 @@ static_assert(sizeof(PartFileHeader) == 64, "the partition file header is 64 byt
 static const char kPartMagic[8] = {'P', 'R', 'G', 'B', 'P', 'A', 'R', 'T'};
 constexpr uint32_t kPartVersion = 1;
 
+// the arrays' digest with the header's three counts folded in, so that a
+// damaged count is refused like a damaged array entry
+static uint64_t counts_digest(uint64_t arrays, int32_t n_comp, int32_t n_levels, int32_t max_wave) {
+  const uint64_t counts[3] = {(uint32_t)n_comp, (uint32_t)n_levels, (uint32_t)max_wave};
+  uint64_t x = arrays;
+  for (uint64_t v : counts) x ^= v + 0x9E3779B97F4A7C15ull + (x << 6) + (x >> 2);
+  return x;
+}
+
 struct FileCloser {
   FILE* f;
   ~FileCloser() {
@@ -336,8 +345,10 @@ static pr_status pr_partition_save_body(const pr_partition* part, const char* pa
     PRGB_TRY(tmp.alloc(&ctl, 1));
     PRGB_TRY(init_ctl(ctl, s));
     PRGB_TRY(graph_digest(P->g, tmp, &h.graph_digest));
+    uint64_t pd = 0;
     PRGB_TRY(partition_digest(n, P->comp_id, P->type, P->level, P->wave, P->n_comp, P->n_levels, P->max_wave, false,
-                              tmp, ctl, &h.part_digest));
+                              tmp, ctl, &pd));
+    h.part_digest = counts_digest(pd, h.n_comp, h.n_levels, h.max_wave);
   }
   IoBuf b((size_t)n * 4);
   if (!b.p) return PR_ENOMEM;
@@ -414,7 +425,7 @@ static pr_status pr_partition_load_body(const pr_graph* g, const char* path, uin
                             &pd);
     // the range checks' verdict comes before any kernel indexes with the arrays
     if (st == PR_OK) st = finish_sync(s, ctl, nullptr);
-    if (st == PR_OK && pd != h.part_digest) st = PR_EINVAL;
+    if (st == PR_OK && counts_digest(pd, h.n_comp, h.n_levels, h.max_wave) != h.part_digest) st = PR_EINVAL;
     if (st == PR_OK) st = smallest_members(n, h.n_comp, saved, crep, tmp);
     if (st == PR_OK) {
       NvtxRange r("prgb layout");

@@ -99,11 +99,15 @@ def test_refuses_other_graphs_and_damage(prgb, tmp_path):
     # another vertex count
     rp2 = np.concatenate([g.rowptr, g.rowptr[-1:]])
     assert _load_status(prgb, prgb.graph(rp2, g.col), path) == "PR_EINVAL"
-    # damaged files: the magic, a truncated file, a trailing byte; then one
-    # level changed to another level in range (the digest refuses it) and
-    # out of range both ways; a missing file
+    # damaged files: the magic, a truncated file, a trailing byte, a count
+    # (the header's counts sit at bytes 48, 52 and 56; the largest wave made
+    # larger passes every range check, so only the digest refuses it); then
+    # one level changed to another level in range (the digest refuses it)
+    # and out of range both ways; a missing file
     bad = tmp_path / "bad.bin"
-    for data in (b"XRGB" + good[4:], good[:-1], good + b"\0"):
+    mw = np.frombuffer(good, np.int32, 1, 56)[0]
+    grown = good[:56] + np.int32(mw + 1).tobytes() + good[60:]
+    for data in (b"XRGB" + good[4:], good[:-1], good + b"\0", grown):
         bad.write_bytes(data)
         assert _load_status(prgb, G, bad) == "PR_EINVAL"
     lev = np.frombuffer(good, np.int32, n, HEADER + 4 * n).copy()
