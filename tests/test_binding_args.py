@@ -66,3 +66,8 @@ def test_mpnn_calls_reject_short_vectors(no_library):
             fn(p, 0.85, np.ones(9), np.ones(10))
         with pytest.raises(ValueError, match="R has 7 entries"):
             fn(p, 0.85, np.ones(10), np.ones(7))
+
+
+def test_load_partition_takes_a_graph(no_library, tmp_path):
+    with pytest.raises(TypeError, match="takes a Graph"):
+        prgb.load_partition(np.zeros(3, np.int32), tmp_path / "p.bin")
