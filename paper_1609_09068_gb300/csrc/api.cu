@@ -423,7 +423,7 @@ static pr_status pr_partition_load_body(const pr_graph* g, const char* path, uin
     if (st == PR_OK)
       st = partition_digest(n, saved, P->type, P->level, P->wave, h.n_comp, h.n_levels, h.max_wave, true, tmp, ctl,
                             &pd);
-    // the range checks' verdict comes before any kernel indexes with the arrays
+    // the range checks' result comes before any kernel indexes with the arrays
     if (st == PR_OK) st = finish_sync(s, ctl, nullptr);
     if (st == PR_OK && counts_digest(pd, h.n_comp, h.n_levels, h.max_wave) != h.part_digest) st = PR_EINVAL;
     if (st == PR_OK) st = smallest_members(n, h.n_comp, saved, crep, tmp);

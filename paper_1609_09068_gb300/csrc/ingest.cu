@@ -239,7 +239,7 @@ pr_status ingest(const pr_csr* csr, uint32_t flags, DevGraph* g, Arena& keep, Ar
     PRGB_LAUNCH();
   }
   PRGB_TRY(scan_i32(g->outdeg, g->optr, n, tmp));
-  // the loop-free edge count and the validation verdict are needed on the host
+  // the loop-free edge count and the validation result are needed on the host
   int32_t m32 = 0;
   int err = 0;
   PRGB_CUDA(cudaMemcpyAsync(&m32, g->optr + n, 4, cudaMemcpyDeviceToHost, s));
